@@ -1,0 +1,1300 @@
+/*
+ * laue_oracle.c — plain, slow, FP64 CPU oracle for the LaueOT Sinkhorn-EM
+ * hot path (arXiv 2404.06478).
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the tests, the smoke check and
+ * the benchmark's CPU-baseline leg load this library.  It shares no source,
+ * header, table or helper with the CUDA path, and it is deliberately written
+ * as loops over the definitions, with no blocking, fusion or reordering.
+ *
+ * Every function names the passage of the paper it restates.  Readings of
+ * passages that the paper leaves silent, ambiguous or garbled:
+ *   frame       beam e=(0,0,1); detectors are planes given by (centre, normal,
+ *               half size); sample rotation Gamma_t about +y by omega_t.
+ *   ray / lam   r = e - 2(u.e)u for every plane; lambda = 2 d |u.e|, i.e. the
+ *               member of the Friedel pair +-hkl with positive wavelength
+ *               (Eqs. ray_mnt and wavelength_lambda).
+ *   harmonics   reflections n*g0 share one ray; a direction is visible when some
+ *               harmonic has lambda0/n inside the band and reports the largest
+ *               such wavelength.
+ *   cost        C_ij = D^2 |rhat_ij - r_j|^2 = 2 D^2 (1 - rhat.r), so that
+ *               L_ij = kappa - kappa C_ij / (2 D^2) (Eq. update_L up to a
+ *               constant); outlier column C_i0 = c_out, unmatched-model row
+ *               C_0j = 0, corner C_00 = c_out.  Gibbs kernel exp(-C/eps),
+ *               eps in mm^2.
+ *   masses      observed and model spots carry 1; the unmatched-model row
+ *               carries U = ceil(frac |J|), the outlier column O = U + |I| - |J|
+ *               (balance of Section "E-step with Sinkhorn updates"); when O < 0,
+ *               U = |J| - |I| and O = 0.  Per-angle mode applies the same rule
+ *               inside each angle block.
+ *   Sinkhorn    log-domain, start f = g = 0 (x = y = 1), row update first
+ *               (Algorithm BalancedOT).
+ *   Newton      exact gradient/Hessian of sum Q rhat.r in the lab frame (the
+ *               appendix formulas without Gamma and sign); ascent step
+ *               x <- x - (H - iota I)^-1 g, iota = max(0, lmax(H) + hreg |H|_F).
+ *   MM          iota_m = max(0, -lmin(M0_m)); Wahba by SVD with the
+ *               determinant correction; rank(B) < 2 keeps R.
+ */
+#include "laue_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* small linear algebra (row-major 3x3)                                        */
+/* ------------------------------------------------------------------------- */
+
+static void mat_vec(const double A[9], const double v[3], double out[3]) {
+    for (int a = 0; a < 3; ++a)
+        out[a] = A[3 * a + 0] * v[0] + A[3 * a + 1] * v[1] + A[3 * a + 2] * v[2];
+}
+
+static void matT_vec(const double A[9], const double v[3], double out[3]) {
+    for (int a = 0; a < 3; ++a)
+        out[a] = A[0 + a] * v[0] + A[3 + a] * v[1] + A[6 + a] * v[2];
+}
+
+static void mat_mul(const double A[9], const double B[9], double C[9]) {
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * a + k] * B[3 * k + b];
+            C[3 * a + b] = s;
+        }
+}
+
+static double dot3(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+static double det3(const double A[9]) {
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+           A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+static void cross3(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Solve A y = b by the adjugate (Cramer); returns 0 if A is singular. */
+static int solve3(const double A[9], const double b[3], double y[3]) {
+    double det = det3(A);
+    if (det == 0.0 || !isfinite(det)) return 0;
+    double inv[9];
+    inv[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+    inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    inv[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+    inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    inv[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+    inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    mat_vec(inv, b, y);
+    return 1;
+}
+
+/* Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (textbook).
+ * evals ascending; evecs columns (row-major storage, column k = vector k). */
+void orc_sym3_eig(const double Ain[9], double evals[3], double evecs[9]) {
+    double A[9], V[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    memcpy(A, Ain, sizeof(A));
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        double tot = off + A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+        if (off <= 1e-300 || off <= 1e-32 * tot) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                double apq = A[3 * p + q];
+                if (apq == 0.0) continue;
+                double theta = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                /* A <- J^T A J with J the rotation in the (p,q) plane */
+                for (int k = 0; k < 3; ++k) {
+                    double akp = A[3 * k + p], akq = A[3 * k + q];
+                    A[3 * k + p] = c * akp - s * akq;
+                    A[3 * k + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double apk = A[3 * p + k], aqk = A[3 * q + k];
+                    A[3 * p + k] = c * apk - s * aqk;
+                    A[3 * q + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double vkp = V[3 * k + p], vkq = V[3 * k + q];
+                    V[3 * k + p] = c * vkp - s * vkq;
+                    V[3 * k + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    /* sort ascending */
+    int idx[3] = {0, 1, 2};
+    double d[3] = {A[0], A[4], A[8]};
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+            if (d[idx[b]] < d[idx[a]]) { int tmp = idx[a]; idx[a] = idx[b]; idx[b] = tmp; }
+    for (int k = 0; k < 3; ++k) {
+        evals[k] = d[idx[k]];
+        for (int a = 0; a < 3; ++a) evecs[3 * a + k] = V[3 * a + idx[k]];
+    }
+}
+
+/* One-sided (Hestenes) Jacobi SVD of a 3x3 matrix: B = U diag(S) V^T,
+ * S descending.  Columns of U for zero singular values are completed to an
+ * orthonormal basis. */
+void orc_svd3(const double B[9], double U[9], double S[3], double V[9]) {
+    double A[9], W[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    memcpy(A, B, sizeof(A));
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        int rotated = 0;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                double alpha = 0, beta = 0, gamma = 0;
+                for (int k = 0; k < 3; ++k) {
+                    alpha += A[3 * k + p] * A[3 * k + p];
+                    beta += A[3 * k + q] * A[3 * k + q];
+                    gamma += A[3 * k + p] * A[3 * k + q];
+                }
+                if (gamma == 0.0 || fabs(gamma) <= 1e-15 * sqrt(alpha * beta)) continue;
+                rotated = 1;
+                double zeta = (beta - alpha) / (2.0 * gamma);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                for (int k = 0; k < 3; ++k) {
+                    double ap = A[3 * k + p], aq = A[3 * k + q];
+                    A[3 * k + p] = c * ap - s * aq;
+                    A[3 * k + q] = s * ap + c * aq;
+                    double wp = W[3 * k + p], wq = W[3 * k + q];
+                    W[3 * k + p] = c * wp - s * wq;
+                    W[3 * k + q] = s * wp + c * wq;
+                }
+            }
+        if (!rotated) break;
+    }
+    double sv[3];
+    for (int k = 0; k < 3; ++k)
+        sv[k] = sqrt(A[k] * A[k] + A[3 + k] * A[3 + k] + A[6 + k] * A[6 + k]);
+    int idx[3] = {0, 1, 2};
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+            if (sv[idx[b]] > sv[idx[a]]) { int tmp = idx[a]; idx[a] = idx[b]; idx[b] = tmp; }
+    double smax = sv[idx[0]];
+    int nz = 0;
+    for (int k = 0; k < 3; ++k) {
+        int src = idx[k];
+        S[k] = sv[src];
+        for (int a = 0; a < 3; ++a) V[3 * a + k] = W[3 * a + src];
+        if (S[k] > 1e-300 && S[k] > 1e-15 * smax) {
+            for (int a = 0; a < 3; ++a) U[3 * a + k] = A[3 * a + src] / S[k];
+            ++nz;
+        } else {
+            for (int a = 0; a < 3; ++a) U[3 * a + k] = 0.0;
+        }
+    }
+    /* complete U where singular values vanish */
+    if (nz == 2) {
+        double u0[3] = {U[0], U[3], U[6]}, u1[3] = {U[1], U[4], U[7]}, u2[3];
+        cross3(u0, u1, u2);
+        for (int a = 0; a < 3; ++a) U[3 * a + 2] = u2[a];
+    } else if (nz < 2) {
+        double u0[3];
+        if (nz == 1) {
+            u0[0] = U[0]; u0[1] = U[3]; u0[2] = U[6];
+        } else {
+            u0[0] = 1; u0[1] = 0; u0[2] = 0;
+        }
+        double tmp[3] = {1, 0, 0};
+        if (fabs(u0[0]) > 0.9) { tmp[0] = 0; tmp[1] = 1; }
+        double u1[3], u2[3];
+        cross3(u0, tmp, u1);
+        double n1 = sqrt(dot3(u1, u1));
+        for (int a = 0; a < 3; ++a) u1[a] /= n1;
+        cross3(u0, u1, u2);
+        for (int a = 0; a < 3; ++a) {
+            U[3 * a + 0] = u0[a];
+            U[3 * a + 1] = u1[a];
+            U[3 * a + 2] = u2[a];
+        }
+    }
+}
+
+/* Appendix "Wahba's problem", Algorithm Wahba: B = sum w a b^T, B = U S V^T,
+ * R = U diag(1, 1, det U det V) V^T.  Returns 0 (R untouched) when rank B < 2. */
+int orc_wahba(const double B[9], double R[9]) {
+    double U[9], S[3], V[9];
+    orc_svd3(B, U, S, V);
+    if (!(S[0] > 0.0) || S[1] <= 1e-12 * S[0]) return 0;
+    double s = det3(U) * det3(V);
+    double M[9] = {1, 0, 0, 0, 1, 0, 0, 0, s};
+    double UM[9], Vt[9];
+    mat_mul(U, M, UM);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Vt[3 * a + b] = V[3 * b + a];
+    mat_mul(UM, Vt, R);
+    return 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* geometry                                                                    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    double e[3];
+    double lam_min, lam_max, D;
+    int n_det;
+    double ctr[4][3], nrm[4][3], half[4];
+} geom_t;
+
+static void geom_unpack(const double* g, geom_t* G) {
+    for (int a = 0; a < 3; ++a) G->e[a] = g[a];
+    G->lam_min = g[3];
+    G->lam_max = g[4];
+    G->D = g[5];
+    G->n_det = (int)g[6];
+    if (G->n_det > 4) G->n_det = 4;
+    for (int k = 0; k < G->n_det; ++k) {
+        const double* q = g + 7 + 7 * k;
+        for (int a = 0; a < 3; ++a) {
+            G->ctr[k][a] = q[a];
+            G->nrm[k][a] = q[3 + a];
+        }
+        G->half[k] = q[6];
+    }
+}
+
+/* Section "Tomography experiments": Gamma_t, rotation about +y by omega. */
+void orc_gamma(double omega, double G[9]) {
+    double c = cos(omega), s = sin(omega);
+    G[0] = c;  G[1] = 0; G[2] = s;
+    G[3] = 0;  G[4] = 1; G[5] = 0;
+    G[6] = -s; G[7] = 0; G[8] = c;
+}
+
+static int gcd_int(int a, int b) {
+    a = abs(a); b = abs(b);
+    while (b) { int t = a % b; a = b; b = t; }
+    return a;
+}
+
+static int allowed_hkl(int h, int k, int l, int centering) {
+    if (h == 0 && k == 0 && l == 0) return 0;
+    if (centering == 1) return ((h + k + l) % 2 + 2) % 2 == 0;           /* I: h+k+l even */
+    if (centering == 2) {                                                 /* F: unmixed */
+        int ph = (h % 2 + 2) % 2, pk = (k % 2 + 2) % 2, pl = (l % 2 + 2) % 2;
+        return ph == pk && pk == pl;
+    }
+    return 1;                                                             /* P */
+}
+
+typedef struct { int g0[3]; int n2; int nh; double w[3]; double d0; } refl_t;
+
+static int refl_cmp(const void* A, const void* B) {
+    const refl_t* a = (const refl_t*)A;
+    const refl_t* b = (const refl_t*)B;
+    if (a->n2 != b->n2) return a->n2 < b->n2 ? -1 : 1;
+    for (int k = 0; k < 3; ++k)
+        if (a->g0[k] != b->g0[k]) return a->g0[k] > b->g0[k] ? -1 : 1;
+    return 0;
+}
+
+/* Section "Crystallographic planes" (d = a / sqrt(h^2+k^2+l^2)) and the
+ * plausible plane set of Section "Tomography experiments": one entry per ray
+ * direction.  The Friedel pair +-hkl shares the ray; harmonics n*g0 share it
+ * too.  Order: |g0|^2 ascending, then g0 (h, k, l) descending. */
+int orc_reflections(double a, int hmax, int centering, int cap,
+                    double* w, double* d0, int* nharm, int* hkl0) {
+    int maxn = (2 * hmax + 1) * (2 * hmax + 1) * (2 * hmax + 1);
+    refl_t* list = (refl_t*)malloc(sizeof(refl_t) * (size_t)maxn);
+    int n = 0;
+    for (int h = -hmax; h <= hmax; ++h)
+        for (int k = -hmax; k <= hmax; ++k)
+            for (int l = -hmax; l <= hmax; ++l) {
+                if (h == 0 && k == 0 && l == 0) continue;
+                if (gcd_int(gcd_int(h, k), l) != 1) continue;
+                int first = h != 0 ? h : (k != 0 ? k : l);
+                if (first < 0) continue;      /* one of each Friedel pair */
+                int pmax = abs(h);
+                if (abs(k) > pmax) pmax = abs(k);
+                if (abs(l) > pmax) pmax = abs(l);
+                int mult[64], nm = 0;
+                for (int m = 1; m * pmax <= hmax && nm < 64; ++m)
+                    if (allowed_hkl(m * h, m * k, m * l, centering)) mult[nm++] = m;
+                if (nm == 0) continue;
+                /* allowed multipliers must be m0, 2 m0, ..., nm m0 */
+                for (int q = 0; q < nm; ++q)
+                    if (mult[q] != (q + 1) * mult[0]) { free(list); return -1; }
+                refl_t* R = &list[n++];
+                R->g0[0] = mult[0] * h;
+                R->g0[1] = mult[0] * k;
+                R->g0[2] = mult[0] * l;
+                R->n2 = R->g0[0] * R->g0[0] + R->g0[1] * R->g0[1] + R->g0[2] * R->g0[2];
+                R->nh = nm;
+                double pn = sqrt((double)(h * h + k * k + l * l));
+                R->w[0] = h / pn; R->w[1] = k / pn; R->w[2] = l / pn;
+                R->d0 = a / sqrt((double)R->n2);
+            }
+    qsort(list, (size_t)n, sizeof(refl_t), refl_cmp);
+    for (int m = 0; m < n && m < cap; ++m) {
+        for (int q = 0; q < 3; ++q) {
+            w[3 * m + q] = list[m].w[q];
+            if (hkl0) hkl0[3 * m + q] = list[m].g0[q];
+        }
+        d0[m] = list[m].d0;
+        nharm[m] = list[m].nh;
+    }
+    free(list);
+    return n;
+}
+
+/* Eqs. ray_mnt, s_mnt, wavelength and the cut model_spot_cut for one
+ * (angle, grain, plane).  Returns 1 if visible.  *margin is the smallest
+ * relative distance of any in/out decision from its threshold. */
+static int ray_one(const geom_t* G, const double Gam[9], const double R[9], const double x[3],
+                   const double w[3], double d0, int nh,
+                   double r[3], double* lam, double s[3], int* det, double c[3], double* margin) {
+    double v[3], u[3];
+    mat_vec(R, w, v);
+    mat_vec(Gam, v, u);
+    mat_vec(Gam, x, c);
+    double ue = dot3(u, G->e);
+    for (int a = 0; a < 3; ++a) r[a] = G->e[a] - 2.0 * ue * u[a];
+    double lam0 = 2.0 * d0 * fabs(ue);
+    double mrg = INFINITY;
+    int in_band = 0;
+    *lam = lam0;
+    for (int n = 1; n <= nh; ++n) {
+        double ln = lam0 / n;
+        double m1 = fabs(ln - G->lam_min) / G->lam_min;
+        double m2 = fabs(ln - G->lam_max) / G->lam_max;
+        if (m1 < mrg) mrg = m1;
+        if (m2 < mrg) mrg = m2;
+        if (!in_band && ln >= G->lam_min && ln <= G->lam_max) {
+            in_band = 1;
+            *lam = ln;
+        }
+    }
+    int best = -1;
+    double best_tau = INFINITY;
+    for (int k = 0; k < G->n_det; ++k) {
+        double den = dot3(G->nrm[k], r);
+        if (den == 0.0) continue;
+        double gc[3] = {G->ctr[k][0] - c[0], G->ctr[k][1] - c[1], G->ctr[k][2] - c[2]};
+        double tau = dot3(G->nrm[k], gc) / den;
+        if (!(tau > 0.0)) continue;
+        double sk[3], dist = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            sk[a] = c[a] + tau * r[a];
+            double da = fabs(sk[a] - G->ctr[k][a]);
+            if (da > dist) dist = da;
+        }
+        double m3 = fabs(G->half[k] - dist) / G->half[k];
+        if (m3 < mrg) mrg = m3;
+        if (dist < G->half[k] && tau < best_tau) {
+            best_tau = tau;
+            best = k;
+            for (int a = 0; a < 3; ++a) s[a] = sk[a];
+        }
+    }
+    *det = best;
+    *margin = mrg;
+    return in_band && best >= 0;
+}
+
+/* Forward Laue model + cut (Eqs. ray_mnt, s_mnt, model_spot_cut): every
+ * (t, n, m); visible spots are listed sorted by (t, n, m).  Writes at most cap
+ * spots; returns the number of visible spots. */
+long orc_forward(const double* geom, const double* w, const double* d0, const int* nharm, int M,
+                 const double* R, const double* x, int N, const double* omega, int T,
+                 long cap, int* J_off, int* grain, int* plane, double* ray4, double* spot3,
+                 int* det, double* center3, signed char* vis_all, double* margin_all) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    long J = 0;
+    for (int t = 0; t < T; ++t) {
+        double Gam[9];
+        orc_gamma(omega[t], Gam);
+        if (J_off) J_off[t] = (int)J;
+        for (int n = 0; n < N; ++n)
+            for (int m = 0; m < M; ++m) {
+                double r[3], lam, s[3], c[3], mrg;
+                int dk;
+                int vis = ray_one(&G, Gam, R + 9 * n, x + 3 * n, w + 3 * m, d0[m], nharm[m],
+                                  r, &lam, s, &dk, c, &mrg);
+                long flat = ((long)t * N + n) * M + m;
+                if (vis_all) vis_all[flat] = (signed char)vis;
+                if (margin_all) margin_all[flat] = mrg;
+                if (!vis) continue;
+                if (J < cap) {
+                    grain[J] = n;
+                    plane[J] = m;
+                    for (int a = 0; a < 3; ++a) {
+                        ray4[4 * J + a] = r[a];
+                        spot3[3 * J + a] = s[a];
+                        center3[3 * J + a] = c[a];
+                    }
+                    ray4[4 * J + 3] = lam;
+                    det[J] = dk;
+                }
+                ++J;
+            }
+    }
+    if (J_off) J_off[T] = (int)J;
+    return J;
+}
+
+/* Rays and grain centres of a frozen model-spot list at new poses (the list
+ * stays fixed during multi-grain fitting, Section "Assignments with outlier
+ * and missing spots"). */
+void orc_refresh(const double* geom, const double* w, const double* d0, const int* nharm,
+                 const double* R, const double* x, const double* omega, int T,
+                 const int* J_off, const int* grain, const int* plane,
+                 double* ray4, double* center3) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    for (int t = 0; t < T; ++t) {
+        double Gam[9];
+        orc_gamma(omega[t], Gam);
+        for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+            int n = grain[j], m = plane[j];
+            double v[3], u[3], c[3];
+            mat_vec(R + 9 * n, w + 3 * m, v);
+            mat_vec(Gam, v, u);
+            mat_vec(Gam, x + 3 * n, c);
+            double ue = dot3(u, G.e);
+            for (int a = 0; a < 3; ++a) {
+                ray4[4 * j + a] = G.e[a] - 2.0 * ue * u[a];
+                center3[3 * j + a] = c[a];
+            }
+            double lam0 = 2.0 * d0[m] * fabs(ue), lam = lam0;
+            for (int k = 1; k <= nharm[m]; ++k)
+                if (lam0 / k >= G.lam_min && lam0 / k <= G.lam_max) { lam = lam0 / k; break; }
+            ray4[4 * j + 3] = lam;
+        }
+    }
+}
+
+/* Section "The likelihood": ray estimate rhat_ij = (s_i - c_j)/|s_i - c_j| and
+ * the pair cost C_ij = D^2 |rhat_ij - r_j|^2. */
+double orc_pair_cost(const double* p, const double* c, const double* r, double D) {
+    double d[3] = {p[0] - c[0], p[1] - c[1], p[2] - c[2]};
+    double tau = sqrt(dot3(d, d));
+    double e2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double q = d[a] / tau - r[a];
+        e2 += q * q;
+    }
+    return D * D * e2;
+}
+
+/* ------------------------------------------------------------------------- */
+/* E-step: balanced entropic OT with dustbins                                  */
+/* ------------------------------------------------------------------------- */
+
+/* log-sum-exp of n values, two passes (max, then sum); -inf for an empty or
+ * all -inf list. */
+static double lse(const double* v, int n) {
+    double m = -INFINITY;
+    for (int k = 0; k < n; ++k)
+        if (v[k] > m) m = v[k];
+    if (m == -INFINITY) return -INFINITY;
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += exp(v[k] - m);
+    return m + log(s);
+}
+
+static double ceil_frac(double frac, long n) { return ceil(frac * (double)n - 1e-9); }
+
+/* Section "E-step with Sinkhorn updates": T_b (unmatched model spots) is the
+ * user variable, T_a = T_b - b^T 1 + a^T 1 balances the problem. */
+void orc_masses(int mode, double frac, int T, const int* I_off, const int* J_off,
+                double* U, double* O) {
+    int nd = mode ? T : 1;
+    for (int d = 0; d < nd; ++d) {
+        long nI = mode ? I_off[d + 1] - I_off[d] : I_off[T];
+        long nJ = mode ? J_off[d + 1] - J_off[d] : J_off[T];
+        double u = ceil_frac(frac, nJ);
+        double o = u + (double)nI - (double)nJ;
+        if (o < 0) {
+            u = (double)(nJ - nI);
+            o = 0;
+        }
+        U[d] = u;
+        O[d] = o;
+    }
+}
+
+static double logm(double m) { return m > 0 ? log(m) : -INFINITY; }
+
+/* Algorithm BalancedOT in the log domain on the extended matrix (observed
+ * rows + unmatched-model row 0, model columns + outlier column 0), blocked by
+ * angle (Q_ij = 0 unless t_i = t_j).  Runs exactly n_iter iterations, or
+ * fewer when tol > 0 and the largest row-marginal violation drops below tol.
+ * warm != 0 starts from the given potentials.  Returns iterations done. */
+int orc_sinkhorn(double D, int T, const int* I_off, const double* p,
+                 const int* J_off, const double* c, const double* r,
+                 double eps, double c_out, int mode, double frac, int n_iter, double tol,
+                 int warm, double* f, double* g, double* fd, double* gd) {
+    int nI = I_off[T], nJ = J_off[T];
+    int nd = mode ? T : 1;
+    double* U = (double*)malloc(sizeof(double) * nd);
+    double* O = (double*)malloc(sizeof(double) * nd);
+    orc_masses(mode, frac, T, I_off, J_off, U, O);
+    if (!warm) {
+        for (int i = 0; i < nI; ++i) f[i] = 0.0;
+        for (int j = 0; j < nJ; ++j) g[j] = 0.0;
+        for (int d = 0; d < nd; ++d) fd[d] = gd[d] = 0.0;
+    }
+    int big = (nI > nJ ? nI : nJ) + 2;
+    double* buf = (double*)malloc(sizeof(double) * big);
+    int it;
+    for (it = 0; it < n_iter; ++it) {
+        /* row update: observed rows, then the unmatched-model rows (both from g) */
+        for (int t = 0; t < T; ++t) {
+            int dd = mode ? t : 0;
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                int n = 0;
+                for (int j = J_off[t]; j < J_off[t + 1]; ++j)
+                    buf[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                buf[n++] = (gd[dd] - c_out) / eps;
+                f[i] = -eps * lse(buf, n);
+            }
+        }
+        for (int d = 0; d < nd; ++d) {
+            int j0 = mode ? J_off[d] : 0, j1 = mode ? J_off[d + 1] : nJ;
+            int n = 0;
+            for (int j = j0; j < j1; ++j) buf[n++] = g[j] / eps;
+            buf[n++] = (gd[d] - c_out) / eps;
+            fd[d] = eps * logm(U[d]) - eps * lse(buf, n);
+        }
+        /* column update: model columns, then the outlier columns (both from f) */
+        for (int t = 0; t < T; ++t) {
+            int dd = mode ? t : 0;
+            for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+                int n = 0;
+                for (int i = I_off[t]; i < I_off[t + 1]; ++i)
+                    buf[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                buf[n++] = fd[dd] / eps;
+                g[j] = -eps * lse(buf, n);
+            }
+        }
+        for (int d = 0; d < nd; ++d) {
+            int i0 = mode ? I_off[d] : 0, i1 = mode ? I_off[d + 1] : nI;
+            int n = 0;
+            for (int i = i0; i < i1; ++i) buf[n++] = (f[i] - c_out) / eps;
+            buf[n++] = (fd[d] - c_out) / eps;
+            gd[d] = eps * logm(O[d]) - eps * lse(buf, n);
+        }
+        if (tol > 0.0) {
+            double err[2];
+            orc_harvest(D, T, I_off, p, J_off, c, r, eps, c_out, mode, frac, f, g, fd, gd,
+                        NULL, NULL, err, NULL, NULL);
+            if (err[0] < tol) { ++it; break; }
+        }
+    }
+    free(buf);
+    free(U);
+    free(O);
+    return it;
+}
+
+/* Plan read-out: Q = exp((f + g - C)/eps) on the extended matrix.  assign[i]
+ * is the argmax of row i over its block's model spots and the outlier column
+ * (-1); ties go to the lowest index, the outlier column only wins when it is
+ * strictly larger.  margin[i] = (top1 - top2)/a_i.  err[0] = largest row
+ * violation, err[1] = largest column violation (dust rows/columns relative to
+ * their mass).  q[j] = sum_i Q_ij and v[j] = sum_i Q_ij rhat_ij over observed
+ * rows.  Any output pointer may be NULL. */
+void orc_harvest(double D, int T, const int* I_off, const double* p,
+                 const int* J_off, const double* c, const double* r,
+                 double eps, double c_out, int mode, double frac,
+                 const double* f, const double* g, const double* fd, const double* gd,
+                 int* assign, double* margin, double* err, double* q, double* v) {
+    int nJ = J_off[T];
+    int nd = mode ? T : 1;
+    double* U = (double*)malloc(sizeof(double) * nd);
+    double* O = (double*)malloc(sizeof(double) * nd);
+    orc_masses(mode, frac, T, I_off, J_off, U, O);
+    double* colsum = (double*)calloc((size_t)nJ + 1, sizeof(double));
+    double* drow = (double*)calloc((size_t)nd, sizeof(double));
+    double* dcol = (double*)calloc((size_t)nd, sizeof(double));
+    double row_err = 0.0;
+    if (q) for (int j = 0; j < nJ; ++j) q[j] = 0.0;
+    if (v) for (int j = 0; j < 3 * nJ; ++j) v[j] = 0.0;
+    for (int t = 0; t < T; ++t) {
+        int dd = mode ? t : 0;
+        for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+            double rs = 0.0, top1 = -1.0, top2 = -1.0;
+            int arg = -1;
+            for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+                double Cij = orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D);
+                double Qij = exp((f[i] + g[j] - Cij) / eps);
+                rs += Qij;
+                colsum[j] += Qij;
+                if (q) q[j] += Qij;
+                if (v) {
+                    double d[3] = {p[3 * i] - c[3 * j], p[3 * i + 1] - c[3 * j + 1],
+                                   p[3 * i + 2] - c[3 * j + 2]};
+                    double tau = sqrt(dot3(d, d));
+                    for (int a = 0; a < 3; ++a) v[3 * j + a] += Qij * d[a] / tau;
+                }
+                if (Qij > top1) { top2 = top1; top1 = Qij; arg = j; }
+                else if (Qij > top2) top2 = Qij;
+            }
+            double Qi0 = exp((f[i] + gd[dd] - c_out) / eps);
+            rs += Qi0;
+            dcol[dd] += Qi0;
+            if (Qi0 > top1) { top2 = top1; top1 = Qi0; arg = -1; }
+            else if (Qi0 > top2) top2 = Qi0;
+            if (top2 < 0) top2 = 0.0;
+            if (assign) assign[i] = arg;
+            if (margin) margin[i] = top1 - top2;
+            double e = fabs(rs - 1.0);
+            if (e > row_err) row_err = e;
+        }
+        for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+            double Q0j = exp((fd[dd] + g[j]) / eps);
+            colsum[j] += Q0j;
+            drow[dd] += Q0j;
+        }
+    }
+    for (int d = 0; d < nd; ++d) {
+        double Q00 = exp((fd[d] + gd[d] - c_out) / eps);
+        drow[d] += Q00;
+        dcol[d] += Q00;
+    }
+    double col_err = 0.0;
+    for (int j = 0; j < nJ; ++j) {
+        double e = fabs(colsum[j] - 1.0);
+        if (e > col_err) col_err = e;
+    }
+    for (int d = 0; d < nd; ++d) {
+        if (U[d] > 0) {
+            double e = fabs(drow[d] - U[d]) / U[d];
+            if (e > row_err) row_err = e;
+        }
+        if (O[d] > 0) {
+            double e = fabs(dcol[d] - O[d]) / O[d];
+            if (e > col_err) col_err = e;
+        }
+    }
+    if (err) { err[0] = row_err; err[1] = col_err; }
+    free(colsum); free(drow); free(dcol); free(U); free(O);
+}
+
+/* ------------------------------------------------------------------------- */
+/* M-step: Newton on positions, MM (Wahba) on orientations                     */
+/* ------------------------------------------------------------------------- */
+
+typedef double (*qfun_t)(void* ctx, int i, int j);
+
+typedef struct {
+    const double *p, *cE, *rE, *f, *g;
+    double eps, D;
+} qpot_ctx;
+
+/* Q_ij of a converged E-step from its potentials and the E-step costs. */
+static double q_from_potentials(void* vctx, int i, int j) {
+    qpot_ctx* ctx = (qpot_ctx*)vctx;
+    double C = orc_pair_cost(ctx->p + 3 * i, ctx->cE + 3 * j, ctx->rE + 3 * j, ctx->D);
+    return exp((ctx->f[i] + ctx->g[j] - C) / ctx->eps);
+}
+
+/* Phi(x) = sum_{j in J_n} sum_{i in I_tj} Q_ij rhat_ij(x).r_j */
+static double newton_objective(const geom_t* G, const double* omega, const int* I_off,
+                               const double* p, const int* js, int nj, const int* jt,
+                               const double* rE, qfun_t qf, void* qc, const double x[3]) {
+    (void)G;
+    double phi = 0.0;
+    for (int k = 0; k < nj; ++k) {
+        int j = js[k], t = jt[k];
+        double Gam[9], c[3];
+        orc_gamma(omega[t], Gam);
+        mat_vec(Gam, x, c);
+        for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+            double Q = qf(qc, i, j);
+            if (Q == 0.0) continue;
+            double d[3] = {p[3 * i] - c[0], p[3 * i + 1] - c[1], p[3 * i + 2] - c[2]};
+            double tau = sqrt(dot3(d, d));
+            phi += Q * dot3(d, rE + 3 * j) / tau;
+        }
+    }
+    return phi;
+}
+
+/* Appendix "M-steps", grain position: Newton iterations (Algorithm
+ * LauePosNewton) with the exact gradient and Hessian of Phi in the lab frame:
+ *   dPhi/dc   = -(r - (rhat.r) rhat) / tau
+ *   d2Phi/dc2 = (3 (rhat.r) rhat rhat^T - rhat r^T - r rhat^T - (rhat.r) I) / tau^2
+ * with c = Gamma_t x. */
+static void newton_grain(const geom_t* G, const double* omega, const int* I_off, const double* p,
+                         const int* js, int nj, const int* jt, const double* rE,
+                         qfun_t qf, void* qc, int n_newton, double tol_x, double hreg,
+                         double x[3], double* stats) {
+    int k;
+    double last = 0.0;
+    stats[6] = newton_objective(G, omega, I_off, p, js, nj, jt, rE, qf, qc, x);
+    for (k = 0; k < n_newton; ++k) {
+        double gx[3] = {0, 0, 0}, Hx[9] = {0};
+        for (int q = 0; q < nj; ++q) {
+            int j = js[q], t = jt[q];
+            double Gam[9], c[3];
+            orc_gamma(omega[t], Gam);
+            mat_vec(Gam, x, c);
+            const double* r = rE + 3 * j;
+            double gc[3] = {0, 0, 0}, Hc[9] = {0};
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                double Q = qf(qc, i, j);
+                if (Q == 0.0) continue;
+                double d[3] = {p[3 * i] - c[0], p[3 * i + 1] - c[1], p[3 * i + 2] - c[2]};
+                double tau = sqrt(dot3(d, d));
+                double rh[3] = {d[0] / tau, d[1] / tau, d[2] / tau};
+                double rr = dot3(rh, r);
+                for (int a = 0; a < 3; ++a) gc[a] += -Q * (r[a] - rr * rh[a]) / tau;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        double h = 3.0 * rr * rh[a] * rh[b] - rh[a] * r[b] - r[a] * rh[b] -
+                                   (a == b ? rr : 0.0);
+                        Hc[3 * a + b] += Q * h / (tau * tau);
+                    }
+            }
+            /* back to x: g_x = Gamma^T g_c, H_x = Gamma^T H_c Gamma */
+            double tmp[3], HG[9], GtHG[9], GamT[9];
+            matT_vec(Gam, gc, tmp);
+            for (int a = 0; a < 3; ++a) gx[a] += tmp[a];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) GamT[3 * a + b] = Gam[3 * b + a];
+            mat_mul(Hc, Gam, HG);
+            mat_mul(GamT, HG, GtHG);
+            for (int a = 0; a < 9; ++a) Hx[a] += GtHG[a];
+        }
+        double fro = 0.0;
+        for (int a = 0; a < 9; ++a) fro += Hx[a] * Hx[a];
+        fro = sqrt(fro);
+        if (!(fro > 0.0)) break;
+        double ev[3], evec[9];
+        orc_sym3_eig(Hx, ev, evec);
+        double iota = ev[2] + hreg * fro;
+        if (iota < 0.0) iota = 0.0;
+        double A[9];
+        memcpy(A, Hx, sizeof(A));
+        A[0] -= iota; A[4] -= iota; A[8] -= iota;
+        double dx[3];
+        if (!solve3(A, gx, dx)) break;
+        for (int a = 0; a < 3; ++a) x[a] -= dx[a];
+        last = sqrt(dot3(dx, dx));
+        if (last < tol_x) { ++k; break; }
+    }
+    stats[0] = k;
+    stats[2] = last;
+    stats[7] = newton_objective(G, omega, I_off, p, js, nj, jt, rE, qf, qc, x);
+}
+
+/* sum_m w_m^T R^T M0_m R w_m over the planes touched by the grain */
+static double mm_objective(const double* M0, const int* planes, int np, const double* w,
+                           const double R[9]) {
+    double s = 0.0;
+    for (int k = 0; k < np; ++k) {
+        double Rw[3], MRw[3];
+        mat_vec(R, w + 3 * planes[k], Rw);
+        mat_vec(M0 + 9 * k, Rw, MRw);
+        s += dot3(Rw, MRw);
+    }
+    return s;
+}
+
+/* Appendix "M-steps", grain rotation (Eqs. M0, Mm, majmin_step; Algorithm
+ * LaueRotMM):  M0_m = -sum_{j in J_n & J_m} Gamma^T (v_j e^T + e v_j^T) Gamma
+ * with v_j = sum_i Q_ij rhat_ij at the current position, M_m = M0_m + iota_m I,
+ * then R^{k+1} = Wahba(M_m R^k w_m, w_m, 1). */
+static void mm_grain(const geom_t* G, const double* omega, const int* I_off, const double* p,
+                     const double* w, const int* js, int nj, const int* jt, const int* jm,
+                     qfun_t qf, void* qc, int n_mm, double tol_R, const double x[3],
+                     double R[9], double* stats) {
+    int* planes = (int*)malloc(sizeof(int) * (nj + 1));
+    double* M0 = (double*)calloc((size_t)9 * (nj + 1), sizeof(double));
+    int np = 0;
+    for (int q = 0; q < nj; ++q) {
+        int j = js[q], t = jt[q], m = jm[q];
+        double Gam[9], c[3];
+        orc_gamma(omega[t], Gam);
+        mat_vec(Gam, x, c);
+        double vj[3] = {0, 0, 0};
+        for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+            double Q = qf(qc, i, j);
+            if (Q == 0.0) continue;
+            double d[3] = {p[3 * i] - c[0], p[3 * i + 1] - c[1], p[3 * i + 2] - c[2]};
+            double tau = sqrt(dot3(d, d));
+            for (int a = 0; a < 3; ++a) vj[a] += Q * d[a] / tau;
+        }
+        int slot = -1;
+        for (int k = 0; k < np; ++k)
+            if (planes[k] == m) { slot = k; break; }
+        if (slot < 0) { slot = np; planes[np++] = m; }
+        double A[9], GamT[9], AG[9], GtAG[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                A[3 * a + b] = vj[a] * G->e[b] + G->e[a] * vj[b];
+                GamT[3 * a + b] = Gam[3 * b + a];
+            }
+        mat_mul(A, Gam, AG);
+        mat_mul(GamT, AG, GtAG);
+        for (int a = 0; a < 9; ++a) M0[9 * slot + a] -= GtAG[a];
+    }
+    double* Mm = (double*)malloc(sizeof(double) * 9 * (np + 1));
+    for (int k = 0; k < np; ++k) {
+        double ev[3], evec[9];
+        orc_sym3_eig(M0 + 9 * k, ev, evec);
+        double iota = ev[0] < 0.0 ? -ev[0] : 0.0;
+        for (int a = 0; a < 9; ++a) Mm[9 * k + a] = M0[9 * k + a];
+        Mm[9 * k + 0] += iota; Mm[9 * k + 4] += iota; Mm[9 * k + 8] += iota;
+    }
+    stats[4] = mm_objective(M0, planes, np, w, R);
+    int it;
+    double last = 0.0;
+    for (it = 0; it < n_mm; ++it) {
+        double B[9] = {0};
+        for (int k = 0; k < np; ++k) {
+            const double* wm = w + 3 * planes[k];
+            double Rw[3], a[3];
+            mat_vec(R, wm, Rw);
+            mat_vec(Mm + 9 * k, Rw, a);
+            for (int u = 0; u < 3; ++u)
+                for (int b = 0; b < 3; ++b) B[3 * u + b] += a[u] * wm[b];
+        }
+        double Rn[9];
+        if (!orc_wahba(B, Rn)) break;
+        double dr = 0.0;
+        for (int a = 0; a < 9; ++a) dr += (Rn[a] - R[a]) * (Rn[a] - R[a]);
+        last = sqrt(dr);
+        memcpy(R, Rn, sizeof(Rn));
+        if (last < tol_R) { ++it; break; }
+    }
+    stats[1] = it;
+    stats[3] = last;
+    stats[5] = mm_objective(M0, planes, np, w, R);
+    free(planes); free(M0); free(Mm);
+}
+
+typedef struct { int* js; int* jt; int* jm; int n; } grain_list;
+
+static void build_grain_lists(int T, const int* J_off, const int* grain, const int* plane, int N,
+                              grain_list* L) {
+    for (int n = 0; n < N; ++n) L[n].n = 0;
+    int nJ = J_off[T];
+    for (int j = 0; j < nJ; ++j) L[grain[j]].n++;
+    for (int n = 0; n < N; ++n) {
+        L[n].js = (int*)malloc(sizeof(int) * (L[n].n + 1));
+        L[n].jt = (int*)malloc(sizeof(int) * (L[n].n + 1));
+        L[n].jm = (int*)malloc(sizeof(int) * (L[n].n + 1));
+        L[n].n = 0;
+    }
+    for (int t = 0; t < T; ++t)
+        for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+            grain_list* g = &L[grain[j]];
+            g->js[g->n] = j;
+            g->jt[g->n] = t;
+            g->jm[g->n] = plane[j];
+            g->n++;
+        }
+}
+
+static void free_grain_lists(grain_list* L, int N) {
+    for (int n = 0; n < N; ++n) { free(L[n].js); free(L[n].jt); free(L[n].jm); }
+}
+
+/* Section "The M-step updates": per grain, Newton on x_n (with R^k), then MM
+ * on R_n (with x^{k+1}); Q stays the E-step plan.  stats[8 n + .] =
+ * {newton steps, mm steps, last |dx|, last |dR|_F, MM objective before,
+ *  MM objective after, Phi before Newton, Phi after Newton}. */
+int orc_mstep(const double* geom, const double* w, const double* omega, int T,
+              const int* I_off, const double* p, const int* J_off,
+              const int* grain, const int* plane, int N,
+              const double* cE, const double* rE,
+              const double* f, const double* g, double eps,
+              int n_newton, int n_mm, double tol_x, double tol_R, double hreg,
+              double* R, double* x, double* stats) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    qpot_ctx qc = {p, cE, rE, f, g, eps, G.D};
+    grain_list* L = (grain_list*)malloc(sizeof(grain_list) * (N + 1));
+    build_grain_lists(T, J_off, grain, plane, N, L);
+    double st[8];
+    for (int n = 0; n < N; ++n) {
+        memset(st, 0, sizeof(st));
+        newton_grain(&G, omega, I_off, p, L[n].js, L[n].n, L[n].jt, rE, q_from_potentials, &qc,
+                     n_newton, tol_x, hreg, x + 3 * n, st);
+        mm_grain(&G, omega, I_off, p, w, L[n].js, L[n].n, L[n].jt, L[n].jm, q_from_potentials,
+                 &qc, n_mm, tol_R, x + 3 * n, R + 9 * n, st);
+        if (stats) memcpy(stats + 8 * n, st, sizeof(st));
+    }
+    free_grain_lists(L, N);
+    free(L);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* EM driver with deterministic annealing                                      */
+/* ------------------------------------------------------------------------- */
+
+/* Section "Deterministic annealing": eps_init = 100 eps_final, geometric
+ * cooling that reaches eps_final at step ceil(0.75 n_em), then held. */
+double orc_eps_schedule(double eps_final, int n_em, int k) {
+    int K = (int)ceil(0.75 * n_em);
+    if (K < 1 || k >= K) return eps_final;
+    return eps_final * pow(100.0, 1.0 - (double)k / (double)K);
+}
+
+/* Algorithm LaueOT (multi-grain fitting) with a fixed number of EM steps:
+ * refresh rays -> BalancedOT -> LauePosNewton -> LaueRotMM -> cool.  A final
+ * E-step at the last poses gives the plan read-out. */
+int orc_em(const double* geom, const double* w, const double* d0, const int* nharm,
+           const double* omega, int T, const int* I_off, const double* p,
+           const int* J_off, const int* grain, const int* plane, int N,
+           double* R, double* x, double eps_final, int n_em, int n_sinkhorn,
+           double c_out, int mode, double frac, int n_newton, int n_mm,
+           double tol_x, double tol_R, double hreg,
+           double* f, double* g, double* fd, double* gd, int* assign, double* margin) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    int nJ = J_off[T];
+    double* ray4 = (double*)malloc(sizeof(double) * 4 * (nJ + 1));
+    double* c3 = (double*)malloc(sizeof(double) * 3 * (nJ + 1));
+    double* r3 = (double*)malloc(sizeof(double) * 3 * (nJ + 1));
+    for (int k = 0; k <= n_em; ++k) {
+        double eps = orc_eps_schedule(eps_final, n_em, k < n_em ? k : n_em);
+        orc_refresh(geom, w, d0, nharm, R, x, omega, T, J_off, grain, plane, ray4, c3);
+        for (int j = 0; j < nJ; ++j)
+            for (int a = 0; a < 3; ++a) r3[3 * j + a] = ray4[4 * j + a];
+        orc_sinkhorn(G.D, T, I_off, p, J_off, c3, r3, eps, c_out, mode, frac, n_sinkhorn, 0.0, 0,
+                     f, g, fd, gd);
+        if (k == n_em) {
+            orc_harvest(G.D, T, I_off, p, J_off, c3, r3, eps, c_out, mode, frac, f, g, fd, gd,
+                        assign, margin, NULL, NULL, NULL);
+            break;
+        }
+        orc_mstep(geom, w, omega, T, I_off, p, J_off, grain, plane, N, c3, r3, f, g, eps,
+                  n_newton, n_mm, tol_x, tol_R, hreg, R, x, NULL);
+    }
+    free(ray4); free(c3); free(r3);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Single-grain fitting (Algorithm SingleLaueOT)                               */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    const double* Q;      /* dense rows: Q[k * nIt_max + (i - I_off[t])] */
+    const int* jpos;      /* global model index -> row k */
+    const int* I_off;
+    const int* jt;
+    int stride;
+} qdense_ctx;
+
+static double q_dense(void* vctx, int i, int j) {
+    qdense_ctx* c = (qdense_ctx*)vctx;
+    int k = c->jpos[j];
+    int t = c->jt[k];
+    return c->Q[(long)k * c->stride + (i - c->I_off[t])];
+}
+
+/* Appendix "Single-grain fitting" (Eq. elbo_single): row-normalised E-step
+ * Q_ij = K_ij / (sum_{j'} K_ij' + K_i0), K = exp(-C/eps), over the model spots
+ * of the grain at angle t_i. */
+static void single_estep(double D, const int* I_off, const double* p, int nj, const int* jt,
+                         const double* c3, const double* r3, double eps, double c_out,
+                         int stride, double* Q, int T) {
+    double* buf = (double*)malloc(sizeof(double) * (nj + 2));
+    for (int t = 0; t < T; ++t) {
+        for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+            int n = 0;
+            for (int k = 0; k < nj; ++k)
+                if (jt[k] == t) buf[n++] = -orc_pair_cost(p + 3 * i, c3 + 3 * k, r3 + 3 * k, D) / eps;
+            buf[n++] = -c_out / eps;
+            double l = lse(buf, n);
+            for (int k = 0; k < nj; ++k)
+                if (jt[k] == t)
+                    Q[(long)k * stride + (i - I_off[t])] =
+                        exp(-orc_pair_cost(p + 3 * i, c3 + 3 * k, r3 + 3 * k, D) / eps - l);
+        }
+    }
+    free(buf);
+}
+
+/* Algorithm SingleLaueOT for S starts.  The model-spot list of a start is
+ * frozen at its starting pose (as for prototypes); k_max annealed EM steps
+ * with the row-normalised E-step, n_newton Newton and n_mm MM steps each.
+ * The candidate filter (Section "Selection of Prototypes", f_out) uses the
+ * spots visible at the final pose: a model ray is unmatched when its column
+ * mass q_j < 0.5 at eps_final; keep[s] = (#unmatched < f_out |J|). */
+int orc_single_fit(const double* geom, const double* w, const double* d0, const int* nharm, int M,
+                   const double* omega, int T, const int* I_off, const double* p,
+                   int S, const double* R0, const double* x0,
+                   double eps_final, int k_max, double c_out,
+                   int n_newton, int n_mm, double tol_x, double tol_R, double hreg,
+                   double f_out, double* R_out, double* x_out, int* keep, double* unmatched) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    int stride = 1;
+    for (int t = 0; t < T; ++t)
+        if (I_off[t + 1] - I_off[t] > stride) stride = I_off[t + 1] - I_off[t];
+    long cap = (long)M * T;
+    int* Joff = (int*)malloc(sizeof(int) * (T + 1));
+    int* gr = (int*)malloc(sizeof(int) * cap);
+    int* pl = (int*)malloc(sizeof(int) * cap);
+    int* dk = (int*)malloc(sizeof(int) * cap);
+    double* ray4 = (double*)malloc(sizeof(double) * 4 * cap);
+    double* s3 = (double*)malloc(sizeof(double) * 3 * cap);
+    double* c3 = (double*)malloc(sizeof(double) * 3 * cap);
+    double* r3 = (double*)malloc(sizeof(double) * 3 * cap);
+    int* jt = (int*)malloc(sizeof(int) * cap);
+    int* jpos = (int*)malloc(sizeof(int) * cap);
+    int* js = (int*)malloc(sizeof(int) * cap);
+    double* Q = (double*)malloc(sizeof(double) * cap * stride);
+    for (int s = 0; s < S; ++s) {
+        double R[9], x[3];
+        memcpy(R, R0 + 9 * s, sizeof(R));
+        memcpy(x, x0 + 3 * s, sizeof(x));
+        long nj = orc_forward(geom, w, d0, nharm, M, R, x, 1, omega, T, cap, Joff, gr, pl, ray4,
+                              s3, dk, c3, NULL, NULL);
+        for (int t = 0; t < T; ++t)
+            for (int j = Joff[t]; j < Joff[t + 1]; ++j) { jt[j] = t; jpos[j] = j; js[j] = j; }
+        qdense_ctx qc = {Q, jpos, I_off, jt, stride};
+        for (int k = 0; k < k_max; ++k) {
+            double eps = orc_eps_schedule(eps_final, k_max, k);
+            orc_refresh(geom, w, d0, nharm, R, x, omega, T, Joff, gr, pl, ray4, c3);
+            for (long j = 0; j < nj; ++j)
+                for (int a = 0; a < 3; ++a) r3[3 * j + a] = ray4[4 * j + a];
+            single_estep(G.D, I_off, p, (int)nj, jt, c3, r3, eps, c_out, stride, Q, T);
+            double st[8];
+            newton_grain(&G, omega, I_off, p, js, (int)nj, jt, r3, q_dense, &qc, n_newton, tol_x,
+                         hreg, x, st);
+            mm_grain(&G, omega, I_off, p, w, js, (int)nj, jt, pl, q_dense, &qc, n_mm, tol_R, x, R,
+                     st);
+        }
+        memcpy(R_out + 9 * s, R, sizeof(R));
+        memcpy(x_out + 3 * s, x, sizeof(x));
+        /* candidate filter at the final pose */
+        long nf = orc_forward(geom, w, d0, nharm, M, R, x, 1, omega, T, cap, Joff, gr, pl, ray4,
+                              s3, dk, c3, NULL, NULL);
+        for (int t = 0; t < T; ++t)
+            for (int j = Joff[t]; j < Joff[t + 1]; ++j) jt[j] = t;
+        for (long j = 0; j < nf; ++j)
+            for (int a = 0; a < 3; ++a) r3[3 * j + a] = ray4[4 * j + a];
+        single_estep(G.D, I_off, p, (int)nf, jt, c3, r3, eps_final, c_out, stride, Q, T);
+        int nun = 0;
+        for (long j = 0; j < nf; ++j) {
+            int t = jt[j];
+            double qj = 0.0;
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) qj += Q[j * stride + (i - I_off[t])];
+            if (qj < 0.5) ++nun;
+        }
+        if (unmatched) unmatched[s] = nf > 0 ? (double)nun / (double)nf : 1.0;
+        if (keep) keep[s] = nf > 0 && (double)nun < f_out * (double)nf;
+    }
+    free(Joff); free(gr); free(pl); free(dk); free(ray4); free(s3); free(c3); free(r3);
+    free(jt); free(jpos); free(js); free(Q);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* SPOT prototype selection                                                    */
+/* ------------------------------------------------------------------------- */
+
+/* Appendix "Selection of prototypes": grain-to-spot matrix, read as the gain
+ * over the outlier baseline
+ *   Lbar_in = max(0, LSE_{j in J_n, t_j = t_i}(-C_ij/eps_s) + c_out/eps_s),
+ * dense I x Nc (row-major), from the spots each candidate makes at its pose. */
+int orc_spot_matrix(const double* geom, const double* w, const double* d0, const int* nharm, int M,
+                    const double* omega, int T, const int* I_off, const double* p,
+                    int Nc, const double* R, const double* x, double eps_s, double c_out,
+                    double* Lbar) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    int nI = I_off[T];
+    long cap = (long)M * T;
+    int* Joff = (int*)malloc(sizeof(int) * (T + 1));
+    int* gr = (int*)malloc(sizeof(int) * cap);
+    int* pl = (int*)malloc(sizeof(int) * cap);
+    int* dk = (int*)malloc(sizeof(int) * cap);
+    double* ray4 = (double*)malloc(sizeof(double) * 4 * cap);
+    double* s3 = (double*)malloc(sizeof(double) * 3 * cap);
+    double* c3 = (double*)malloc(sizeof(double) * 3 * cap);
+    double* buf = (double*)malloc(sizeof(double) * (cap + 1));
+    for (int n = 0; n < Nc; ++n) {
+        orc_forward(geom, w, d0, nharm, M, R + 9 * n, x + 3 * n, 1, omega, T, cap, Joff, gr, pl,
+                    ray4, s3, dk, c3, NULL, NULL);
+        for (int t = 0; t < T; ++t)
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                int k = 0;
+                for (int j = Joff[t]; j < Joff[t + 1]; ++j) {
+                    double r[3] = {ray4[4 * j], ray4[4 * j + 1], ray4[4 * j + 2]};
+                    buf[k++] = -orc_pair_cost(p + 3 * i, c3 + 3 * j, r, G.D) / eps_s;
+                }
+                double val = k ? lse(buf, k) + c_out / eps_s : 0.0;
+                Lbar[(long)i * Nc + n] = val > 0.0 ? val : 0.0;
+            }
+    }
+    (void)nI;
+    free(Joff); free(gr); free(pl); free(dk); free(ray4); free(s3); free(c3); free(buf);
+    return 0;
+}
+
+/* f(S) = sum_i max_{n in S} Lbar_in  (closed form of Eq. prototype_function
+ * when the source weights are free on S), f(empty) = 0. */
+static double spot_value(int I, int Nc, const double* Lbar, const int* S, int k) {
+    double tot = 0.0;
+    for (int i = 0; i < I; ++i) {
+        double best = 0.0;
+        for (int q = 0; q < k; ++q) {
+            double v = Lbar[(long)i * Nc + S[q]];
+            if (v > best) best = v;
+        }
+        tot += best;
+    }
+    return tot;
+}
+
+/* Algorithm LaueSpotGreedy by the naive definition: at every step recompute
+ * f(S u {n}) - f(S) for every candidate not yet chosen; ties go to the lowest
+ * index.  gain[k] = increment of step k+1, F[k] = cumulative value. */
+int orc_spot_greedy(int I, int Nc, const double* Lbar, int kmax,
+                    int* order, double* gain, double* F) {
+    int* S = (int*)malloc(sizeof(int) * (kmax + 1));
+    char* used = (char*)calloc((size_t)Nc + 1, 1);
+    double fS = 0.0;
+    int k;
+    for (k = 0; k < kmax && k < Nc; ++k) {
+        int best = -1;
+        double bestg = -1.0;
+        for (int n = 0; n < Nc; ++n) {
+            if (used[n]) continue;
+            S[k] = n;
+            double gn = spot_value(I, Nc, Lbar, S, k + 1) - fS;
+            if (gn > bestg) { bestg = gn; best = n; }
+        }
+        S[k] = best;
+        used[best] = 1;
+        fS += bestg;
+        order[k] = best;
+        gain[k] = bestg;
+        F[k] = fS;
+    }
+    free(S);
+    free(used);
+    return k;
+}
+
+/* Eq. spot_ngrains read on the increments Delta_k (gain[k-1]): the largest
+ * drop, k* = argmax_{2 <= k <= K} Delta_k - Delta_{k+1} with Delta_{K+1} = 0;
+ * k* = K when K < 2.  Ties go to the smallest k. */
+int orc_kstar(int K, const double* gain) {
+    if (K < 2) return K;
+    int best = 2;
+    double bv = -INFINITY;
+    for (int k = 2; k <= K; ++k) {
+        double dk = gain[k - 1];
+        double dk1 = k < K ? gain[k] : 0.0;
+        if (dk - dk1 > bv) { bv = dk - dk1; best = k; }
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint: gradient of the OT-weighted spot cost                              */
+/* ------------------------------------------------------------------------- */
+
+/* E_n(R, x) = sum_{j in J_n} sum_{i in I_tj} Q_ij C_ij(R, x) with Q_ij fixed by
+ * the potentials and the costs at the E-step (cE, rE). */
+void orc_grain_objective(const double* geom, const double* w, const double* omega, int T,
+                         const int* I_off, const double* p, const int* J_off,
+                         const int* grain, const int* plane, int N,
+                         const double* cE, const double* rE,
+                         const double* f, const double* g, double eps,
+                         const double* R, const double* x, double* En) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    for (int n = 0; n < N; ++n) En[n] = 0.0;
+    for (int t = 0; t < T; ++t) {
+        double Gam[9];
+        orc_gamma(omega[t], Gam);
+        for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+            int n = grain[j], m = plane[j];
+            double v[3], u[3], c[3], r[3];
+            mat_vec(R + 9 * n, w + 3 * m, v);
+            mat_vec(Gam, v, u);
+            mat_vec(Gam, x + 3 * n, c);
+            double ue = dot3(u, G.e);
+            for (int a = 0; a < 3; ++a) r[a] = G.e[a] - 2.0 * ue * u[a];
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                double CE = orc_pair_cost(p + 3 * i, cE + 3 * j, rE + 3 * j, G.D);
+                double Q = exp((f[i] + g[j] - CE) / eps);
+                En[n] += Q * orc_pair_cost(p + 3 * i, c, r, G.D);
+            }
+        }
+    }
+}
+
+/* Analytic gradient of E_n at the E-step poses (Danskin: Q held fixed) with
+ * respect to a left-multiplicative axis-angle perturbation R <- exp([w]x) R
+ * and to x:
+ *   dC/dc     = (2 D^2 / tau) (r - (rhat.r) rhat),   c = Gamma x
+ *   dC/dr     = 2 D^2 (r - rhat)
+ *   dr/du     = -2 (u e^T + (u.e) I),  du/dw = -Gamma [R w_m]x
+ * grad[6 n + 0..2] = dE_n/dw, grad[6 n + 3..5] = dE_n/dx. */
+void orc_grain_grad(const double* geom, const double* w, const double* omega, int T,
+                    const int* I_off, const double* p, const int* J_off,
+                    const int* grain, const int* plane, int N,
+                    const double* f, const double* g, double eps,
+                    const double* R, const double* x, double* grad) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    double D2 = G.D * G.D;
+    for (int k = 0; k < 6 * N; ++k) grad[k] = 0.0;
+    for (int t = 0; t < T; ++t) {
+        double Gam[9];
+        orc_gamma(omega[t], Gam);
+        for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+            int n = grain[j], m = plane[j];
+            double v[3], u[3], c[3], r[3];
+            mat_vec(R + 9 * n, w + 3 * m, v);
+            mat_vec(Gam, v, u);
+            mat_vec(Gam, x + 3 * n, c);
+            double ue = dot3(u, G.e);
+            for (int a = 0; a < 3; ++a) r[a] = G.e[a] - 2.0 * ue * u[a];
+            double gr[3] = {0, 0, 0}, gc[3] = {0, 0, 0};
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                double C = orc_pair_cost(p + 3 * i, c, r, G.D);
+                double Q = exp((f[i] + g[j] - C) / eps);
+                if (Q == 0.0) continue;
+                double d[3] = {p[3 * i] - c[0], p[3 * i + 1] - c[1], p[3 * i + 2] - c[2]};
+                double tau = sqrt(dot3(d, d));
+                double rh[3] = {d[0] / tau, d[1] / tau, d[2] / tau};
+                double rr = dot3(rh, r);
+                for (int a = 0; a < 3; ++a) {
+                    gc[a] += Q * 2.0 * D2 / tau * (r[a] - rr * rh[a]);
+                    gr[a] += Q * 2.0 * D2 * (r[a] - rh[a]);
+                }
+            }
+            /* x part: Gamma^T dC/dc */
+            double gx[3];
+            matT_vec(Gam, gc, gx);
+            /* rotation part: y^T = (dC/dr)^T dr/du = -2 ((gr.u) e + (u.e) gr)^T and
+             * dE/dw = y^T (-Gamma [v]x) = v x (Gamma^T y) */
+            double y[3];
+            double gu = dot3(gr, u);
+            for (int a = 0; a < 3; ++a) y[a] = -2.0 * (gu * G.e[a] + ue * gr[a]);
+            double Gty[3], gw[3];
+            matT_vec(Gam, y, Gty);
+            cross3(v, Gty, gw);
+            for (int a = 0; a < 3; ++a) {
+                grad[6 * n + a] += gw[a];
+                grad[6 * n + 3 + a] += gx[a];
+            }
+        }
+    }
+}

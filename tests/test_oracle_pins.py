@@ -1,0 +1,512 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: a worked
+example printed in the paper or derived from Bragg's law, closed forms,
+invariants, a library routine (LAPACK, the Hungarian algorithm, an LP solver)
+or brute force on tiny inputs.  None of these runs on a GPU.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synthgen as sg
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+GEOM = sg.Geometry()
+TINY = sg.CONFIGS["tiny"]
+
+
+def _rotvec(w):
+    th = float(np.linalg.norm(w))
+    if th == 0.0:
+        return np.eye(3)
+    k = np.asarray(w) / th
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(th) * K + (1 - math.cos(th)) * K @ K
+
+
+def _cubic_group():
+    mats = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product([1, -1], repeat=3):
+            S = np.zeros((3, 3))
+            for r, c in enumerate(perm):
+                S[r, c] = signs[r]
+            if np.linalg.det(S) > 0:
+                mats.append(S)
+    return mats
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    planes = oracle.reflections(TINY.a, TINY.hmax, TINY.centering)
+    rng = sg.workload_seed(TINY)
+    R, x = sg.random_grains(TINY, rng)
+    om = sg.omegas(TINY)
+    fw = oracle.forward(GEOM, planes, R, x, om)
+    obs = sg.observe(GEOM, TINY, fw["t"], fw["det"], fw["spot"], rng)
+    return dict(planes=planes, R=R, x=x, om=om, fw=fw, obs=obs)
+
+
+# ---------------------------------------------------------------- reflections
+
+def test_reflection_table_covers_every_allowed_hkl_once():
+    """Brute force: every allowed hkl within the bound is n * g0 of exactly one
+    direction (up to the Friedel sign), n <= nharm, and no two directions are
+    parallel."""
+    for hmax, count in ((4, 145), (6, 433)):
+        P = oracle.reflections(2.87, hmax, 1)
+        assert len(P.w) == count
+        g0 = P.hkl0
+        seen = {}
+        for m in range(len(g0)):
+            for n in range(1, P.nharm[m] + 1):
+                for s in (1, -1):
+                    key = tuple(int(v) for v in s * n * g0[m])
+                    seen[key] = seen.get(key, 0) + 1
+        allowed = {(h, k, l) for h, k, l in itertools.product(range(-hmax, hmax + 1), repeat=3)
+                   if (h, k, l) != (0, 0, 0) and (h + k + l) % 2 == 0}
+        assert set(seen) == allowed
+        assert all(v == 1 for v in seen.values())
+        W = P.w
+        cosines = np.abs(W @ W.T) - np.eye(len(W))
+        assert cosines.max() < 1 - 1e-9
+        np.testing.assert_allclose(P.d0, 2.87 / np.linalg.norm(g0, axis=1), rtol=1e-14)
+
+
+# -------------------------------------------------------------------- forward
+
+def test_forward_worked_example():
+    gold = json.load(open(os.path.join(GOLD, "forward_worked_example.json")))
+    P = oracle.reflections(gold["lattice_a"], 4, 1)
+    m = [i for i, h in enumerate(P.hkl0) if list(h) == gold["hkl0"]]
+    assert len(m) == 1
+    sub = oracle.Planes(P.w[m], P.d0[m], P.nharm[m], P.hkl0[m])
+    assert sub.d0[0] == pytest.approx(gold["d0"], rel=1e-12)
+    fw = oracle.forward(GEOM, sub, np.eye(3)[None], np.zeros((1, 3)), np.zeros(1))
+    assert fw["J_off"][-1] == 1
+    assert fw["ray"][0, 3] == pytest.approx(gold["lambda"], rel=1e-12)
+    np.testing.assert_allclose(fw["ray"][0, :3], gold["ray"], atol=1e-12)
+    np.testing.assert_allclose(fw["spot"][0], gold["spot"], atol=1e-9)
+    assert fw["det"][0] == gold["detector"]
+
+
+def test_gamma_is_rotation_about_y():
+    G0 = oracle.gamma(0.0)
+    np.testing.assert_allclose(G0, np.eye(3), atol=0)
+    for om in (0.3, 2.0, -1.1):
+        G = oracle.gamma(om)
+        np.testing.assert_allclose(G @ G.T, np.eye(3), atol=1e-15)
+        assert np.linalg.det(G) == pytest.approx(1.0, abs=1e-15)
+        np.testing.assert_allclose(G @ [0, 1, 0], [0, 1, 0], atol=1e-15)
+        # right-handed: a small positive rotation about y takes +z towards +x
+    assert (oracle.gamma(0.1) @ [0, 0, 1])[0] > 0
+
+
+def test_forward_spots_satisfy_laue_and_bragg(tiny):
+    """Every visible spot: unit ray; Laue condition k_out = k_in - 2(k_in.g)g with
+    g = Gamma R w_m; Bragg n lambda = 2 d sin(theta) with theta read from the
+    scattering angle; spot on its detector plane, inside the square, on the ray
+    from the grain centre."""
+    fw, P, R, x, om = tiny["fw"], tiny["planes"], tiny["R"], tiny["x"], tiny["om"]
+    e = np.array(GEOM.beam)
+    assert fw["J_off"][-1] > 100
+    for j in range(fw["J_off"][-1]):
+        t, n, m = fw["t"][j], fw["grain"][j], fw["plane"][j]
+        r, lam = fw["ray"][j, :3], fw["ray"][j, 3]
+        assert np.linalg.norm(r) == pytest.approx(1.0, abs=1e-14)
+        Gm = oracle.gamma(om[t])
+        g = Gm @ R[n] @ P.w[m]
+        np.testing.assert_allclose(r, e - 2 * (e @ g) * g, atol=1e-13)
+        theta = 0.5 * math.acos(np.clip(e @ r, -1, 1))
+        ok = [k for k in range(1, P.nharm[m] + 1)
+              if abs(k * lam - 2 * P.d0[m] * math.sin(theta)) < 1e-9]
+        assert ok, (j, lam)
+        assert GEOM.lam_min <= lam <= GEOM.lam_max
+        det = GEOM.detectors[fw["det"][j]]
+        s = fw["spot"][j]
+        assert s[2] == pytest.approx(det.centre[2], abs=1e-9)
+        assert abs(s[0]) < det.half and abs(s[1]) < det.half
+        c = Gm @ x[n]
+        np.testing.assert_allclose(fw["center"][j], c, atol=1e-13)
+        d = s - c
+        assert np.linalg.norm(np.cross(d, r)) < 1e-9 and d @ r > 0
+
+
+def test_forward_invariant_under_cubic_symmetry(tiny):
+    """The spot multiset of a cubic grain does not change under R -> R S for the
+    24 proper rotations of the cube (Section 'Pre-processing': the search is
+    restricted by the crystal symmetries)."""
+    P, R, x, om = tiny["planes"], tiny["R"], tiny["x"], tiny["om"]
+    base = oracle.forward(GEOM, P, R[:2], x[:2], om)
+    key = lambda fw: np.array(sorted(map(tuple, np.round(
+        np.c_[fw["t"], fw["grain"], fw["spot"], fw["ray"][:, 3]], 8))))
+    k0 = key(base)
+    for S in _cubic_group():
+        fw = oracle.forward(GEOM, P, R[:2] @ S, x[:2], om)
+        np.testing.assert_allclose(key(fw), k0, atol=2e-8)
+
+
+def test_sigma_conversion_matches_paper():
+    gold = json.load(open(os.path.join(GOLD, "sigma_conversion.json")))
+    for case in gold["cases"]:
+        deg = math.degrees(case["sigma_mm"] / case["distance_mm"])
+        assert round(deg, gold["printed_digits"]) == case["sigma_deg"]
+
+
+def test_outlier_cost_is_three_sigma_pair_cost():
+    """c_out is the pair cost of a ray 3 sigma away: ~9 sigma_mm^2 for small
+    angles, and exactly D^2 |a - b|^2 for unit rays 3 sigma_ang apart."""
+    c = oracle.c_out_for(0.5, 200.0)
+    assert c == pytest.approx(9 * 0.25, rel=1e-5)
+    ang = 3 * 0.5 / 200.0
+    a = np.array([0, 0, 1.0]); b = np.array([math.sin(ang), 0, math.cos(ang)])
+    assert c == pytest.approx(200.0 ** 2 * np.sum((a - b) ** 2), rel=1e-9)
+
+
+# ----------------------------------------------------------------------- cost
+
+def test_noiseless_truth_has_zero_cost(tiny):
+    fw = tiny["fw"]
+    for j in range(fw["J_off"][-1]):
+        C = oracle.pair_cost(fw["spot"][j], fw["center"][j], fw["ray"][j, :3], GEOM.D)
+        assert C < 1e-20
+
+
+def test_cost_is_angle_between_rays():
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        p = rng.normal(size=3) * 100; c = rng.normal(size=3)
+        r = rng.normal(size=3); r /= np.linalg.norm(r)
+        a = (p - c) / np.linalg.norm(p - c)
+        ang = math.atan2(np.linalg.norm(np.cross(a, r)), a @ r)
+        assert oracle.pair_cost(p, c, r, 200.0) == pytest.approx(
+            2 * 200.0 ** 2 * (1 - math.cos(ang)), rel=1e-9, abs=1e-9)
+
+
+# ------------------------------------------------------------------- Sinkhorn
+
+def _plan(D, p, I_off, J_off, c, r, eps, cout, f, g):
+    """Dense real-pair block of the plan from potentials (for the tests)."""
+    Q = np.zeros((len(p), len(c)))
+    T = len(I_off) - 1
+    for t in range(T):
+        for i in range(I_off[t], I_off[t + 1]):
+            for j in range(J_off[t], J_off[t + 1]):
+                Q[i, j] = math.exp((f[i] + g[j] - oracle.pair_cost(p[i], c[j], r[j], D)) / eps)
+    return Q
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sinkhorn_marginals_converge(tiny, mode):
+    fw, obs = tiny["fw"], tiny["obs"]
+    cout = oracle.c_out_for(0.5, GEOM.D)
+    f, g, fd, gd, it = oracle.sinkhorn(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"],
+                                       fw["ray"][:, :3], 1.0, cout, mode, 0.4, 5000, 1e-12)
+    assert it < 5000
+    h = oracle.harvest(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3],
+                       1.0, cout, mode, 0.4, f, g, fd, gd)
+    assert h["row_err"] < 1e-10 and h["col_err"] < 1e-10
+
+
+def test_sinkhorn_single_pair_closed_form():
+    """|I| = |J| = 1 in one block: U = O = 1 and the 2 x 2 extended plan has
+    Q_11 Q_00 / (Q_10 Q_01) = exp(-(C + c_out - c_out - 0)/eps), hence
+    Q_11 = 1 / (1 + exp(C / (2 eps)))."""
+    p = np.array([[3.0, -2.0, -200.0]]); c = np.array([[0.5, 0.2, -0.1]])
+    r = np.array([[0.02, -0.01, -1.0]]); r /= np.linalg.norm(r)
+    C = oracle.pair_cost(p[0], c[0], r[0], 200.0)
+    for eps in (0.5, 2.0, 10.0):
+        f, g, fd, gd, _ = oracle.sinkhorn(200.0, p, [0, 1], [0, 1], c, r, eps, 2.25, 0, 0.4,
+                                          10000, 1e-14)
+        Q11 = math.exp((f[0] + g[0] - C) / eps)
+        assert Q11 == pytest.approx(1 / (1 + math.exp(C / (2 * eps))), rel=1e-10)
+
+
+def test_sinkhorn_large_eps_is_independent_coupling():
+    """One angle block, eps -> inf: Q -> a b^T / sum(a) on the extended matrix."""
+    rng = np.random.default_rng(1)
+    nI, nJ = 7, 5
+    p = np.c_[rng.uniform(-50, 50, (nI, 2)), -200 * np.ones(nI)]
+    c = rng.uniform(-2, 2, (nJ, 3))
+    r = np.c_[rng.normal(size=(nJ, 2)) * 0.2, -np.ones(nJ)]
+    r /= np.linalg.norm(r, axis=1, keepdims=True)
+    U, O = oracle.masses(0, 0.4, [0, nI], [0, nJ])
+    f, g, fd, gd, _ = oracle.sinkhorn(200.0, p, [0, nI], [0, nJ], c, r, 1e12, 2.25, 0, 0.4, 5000, 1e-13)
+    Q = _plan(200.0, p, [0, nI], [0, nJ], c, r, 1e12, 2.25, f, g)
+    np.testing.assert_allclose(Q, 1.0 / (nI + U[0]), rtol=1e-6)
+
+
+def test_sinkhorn_small_eps_matches_hungarian():
+    """eps -> 0: the plan's row argmax equals the optimal assignment of the
+    capacity-expanded square problem (rows: observed + U copies of the
+    unmatched-model source; columns: model + O copies of the outlier sink),
+    solved by the Hungarian algorithm and checked by brute force when tiny."""
+    from scipy.optimize import linear_sum_assignment
+    rng = np.random.default_rng(7)
+    for trial in range(6):
+        T = 2
+        nIt = [rng.integers(2, 5) for _ in range(T)]
+        nJt = [rng.integers(2, 4) for _ in range(T)]
+        I_off = np.r_[0, np.cumsum(nIt)]; J_off = np.r_[0, np.cumsum(nJt)]
+        nI, nJ = I_off[-1], J_off[-1]
+        c = rng.uniform(-2, 2, (nJ, 3))
+        r = np.c_[rng.normal(size=(nJ, 2)) * 0.1, -np.ones(nJ)]
+        r /= np.linalg.norm(r, axis=1, keepdims=True)
+        p = np.zeros((nI, 3))
+        for t in range(T):
+            for i in range(I_off[t], I_off[t + 1]):
+                j = rng.integers(J_off[t], J_off[t + 1])
+                tau = (-200 - c[j, 2]) / r[j, 2]
+                p[i] = c[j] + tau * r[j] + np.r_[rng.normal(size=2) * 1.5, 0]
+        cout = 2.25
+        U, O = oracle.masses(0, 0.4, I_off, J_off)
+        U, O = int(U[0]), int(O[0])
+        BIG = 1e6
+        n = nI + U
+        Cm = np.full((n, n), BIG)
+        for t in range(T):
+            for i in range(I_off[t], I_off[t + 1]):
+                for j in range(J_off[t], J_off[t + 1]):
+                    Cm[i, j] = oracle.pair_cost(p[i], c[j], r[j], 200.0)
+        Cm[:nI, nJ:] = cout
+        Cm[nI:, :nJ] = 0.0
+        Cm[nI:, nJ:] = cout
+        rows, cols = linear_sum_assignment(Cm)
+        ref = np.where(cols[:nI] < nJ, cols[:nI], -1)
+        if n <= 8:
+            best = min(itertools.permutations(range(n)), key=lambda s: sum(Cm[a, s[a]] for a in range(n)))
+            assert sum(Cm[a, best[a]] for a in range(n)) == pytest.approx(Cm[rows, cols].sum())
+        # unique optimum required for an argmax comparison
+        eps = 0.01
+        f, g, fd, gd, _ = oracle.sinkhorn(200.0, p, I_off, J_off, c, r, eps, cout, 0, 0.4, 200000, 1e-9)
+        h = oracle.harvest(200.0, p, I_off, J_off, c, r, eps, cout, 0, 0.4, f, g, fd, gd)
+        np.testing.assert_array_equal(h["assign"], ref)
+
+
+def test_per_angle_equals_global_for_one_block(tiny):
+    fw, obs = tiny["fw"], tiny["obs"]
+    t0 = 3
+    i0, i1 = obs.I_off[t0], obs.I_off[t0 + 1]
+    j0, j1 = fw["J_off"][t0], fw["J_off"][t0 + 1]
+    args = (GEOM.D, obs.p[i0:i1], [0, i1 - i0], [0, j1 - j0], fw["center"][j0:j1],
+            fw["ray"][j0:j1, :3], 1.0, 2.25)
+    a = oracle.sinkhorn(*args, 0, 0.4, 50)
+    b = oracle.sinkhorn(*args, 1, 0.4, 50)
+    for u, v in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(u, v)
+
+
+# --------------------------------------------------------------------- M-step
+
+def test_sym3_eig_matches_lapack():
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        A = rng.normal(size=(3, 3)); A = A + A.T
+        ev, V = oracle.sym3_eig(A)
+        np.testing.assert_allclose(ev, np.linalg.eigvalsh(A), atol=1e-12)
+        np.testing.assert_allclose(A @ V, V @ np.diag(ev), atol=1e-11)
+
+
+def test_svd3_matches_lapack():
+    rng = np.random.default_rng(4)
+    for k in range(20):
+        B = rng.normal(size=(3, 3))
+        if k % 4 == 0:
+            B[:, 2] = B[:, 0] + B[:, 1]  # rank 2
+        U, S, V = oracle.svd3(B)
+        np.testing.assert_allclose(S, np.linalg.svd(B, compute_uv=False), atol=1e-12)
+        np.testing.assert_allclose(U @ np.diag(S) @ V.T, B, atol=1e-12)
+        np.testing.assert_allclose(U.T @ U, np.eye(3), atol=1e-12)
+
+
+def test_wahba_recovers_rotation_exactly():
+    """Kabsch: noiseless correspondences a_k = R b_k give R back, including
+    the determinant correction when the unconstrained optimum is a reflection."""
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        Rt = sg.random_rotations(1, rng)[0]
+        b = rng.normal(size=(6, 3)); a = b @ Rt.T
+        w = rng.uniform(0.5, 2, 6)
+        B = (w[:, None, None] * a[:, :, None] * b[:, None, :]).sum(0)
+        np.testing.assert_allclose(oracle.wahba(B), Rt, atol=1e-12)
+    # planar data: rank 2, the reflection branch must be excluded
+    b = np.c_[rng.normal(size=(5, 2)), np.zeros(5)]
+    Rt = sg.random_rotations(1, rng)[0]
+    B = (Rt @ b.T) @ b
+    Rh = oracle.wahba(B)
+    assert np.linalg.det(Rh) == pytest.approx(1.0)
+    np.testing.assert_allclose(Rh @ b.T, Rt @ b.T, atol=1e-12)
+    # rank 1 keeps R (returns None)
+    assert oracle.wahba(np.outer([1, 2, 3], [0, 1, 0])) is None
+
+
+def _noiseless_assignment(seed=0):
+    planes = oracle.reflections(TINY.a, TINY.hmax, TINY.centering)
+    rng = np.random.default_rng(seed)
+    R, x = sg.random_grains(TINY, rng)
+    om = sg.omegas(TINY)
+    fw = oracle.forward(GEOM, planes, R, x, om)
+    # observed = the true spots themselves, in model order (no noise/outliers)
+    p = fw["spot"].copy()
+    I_off = fw["J_off"].copy()
+    return planes, R, x, om, fw, p, I_off
+
+
+def test_newton_recovers_true_position_with_ground_truth_plan():
+    """Q = the true assignment (pure assignment problem: no dustbin mass, small
+    eps): Newton moves a displaced grain back to the true x within 3 steps."""
+    planes, R, x, om, fw, p, I_off = _noiseless_assignment(0)
+    c, r = fw["center"], fw["ray"][:, :3]
+    f, g, fd, gd, _ = oracle.sinkhorn(GEOM.D, p, I_off, fw["J_off"], c, r, 0.05, 2.25, 0, 0.0,
+                                      2000, 1e-12)
+    Q = _plan(GEOM.D, p, I_off, fw["J_off"], c, r, 0.05, 2.25, f, g)
+    np.testing.assert_allclose(np.diag(Q), 1.0, atol=1e-9)
+    rng = np.random.default_rng(11)
+    x0 = x + rng.normal(size=x.shape) * 0.2
+    R1, x1, st = oracle.mstep(GEOM, planes, om, p, I_off, fw["J_off"], fw["grain"], fw["plane"],
+                              c, r, f, g, 0.05, R, x0, n_newton=3, n_mm=0)
+    np.testing.assert_allclose(x1, x, atol=1e-7)
+
+
+def test_newton_gradient_matches_finite_differences():
+    """The Newton objective Phi(x) = sum Q rhat.r: the gradient the step uses is
+    checked through the adjoint's x-part (dE/dx = -2 D^2 dPhi/dx)."""
+    planes, R, x, om, fw, p, I_off = _noiseless_assignment(1)
+    rng = np.random.default_rng(12)
+    p = p + np.c_[rng.normal(size=(len(p), 2)) * 0.5, np.zeros(len(p))]
+    c, r = fw["center"], fw["ray"][:, :3]
+    args = (GEOM, planes, om, p, I_off, fw["J_off"], fw["grain"], fw["plane"])
+    f, g, fd, gd, _ = oracle.sinkhorn(GEOM.D, p, I_off, fw["J_off"], c, r, 2.0, 2.25, 0, 0.4, 100)
+    G = oracle.grain_grad(*args, f, g, 2.0, R, x)
+    h = 1e-6
+    FD = np.zeros_like(G)
+    for k in range(6):
+        e = np.zeros(6); e[k] = h
+        Rp = np.array([_rotvec(e[:3]) @ a for a in R]); Rm = np.array([_rotvec(-e[:3]) @ a for a in R])
+        Ep = oracle.grain_objective(*args, c, r, f, g, 2.0, Rp, x + e[3:])
+        Em = oracle.grain_objective(*args, c, r, f, g, 2.0, Rm, x - e[3:])
+        FD[:, k] = (Ep - Em) / (2 * h)
+    assert np.abs(G - FD).max() <= 1e-7 * np.abs(G).max()
+
+
+def test_mm_never_decreases_objective(tiny):
+    """Majorisation-minimisation is monotone (appendix 'Grain rotation')."""
+    P, R, x, om, fw, obs = (tiny[k] for k in ("planes", "R", "x", "om", "fw", "obs"))
+    rng = np.random.default_rng(9)
+    Rp = np.array([_rotvec(rng.normal(size=3) * 0.01) @ a for a in R])
+    ray, ce = oracle.refresh(GEOM, P, Rp, x, om, fw["J_off"], fw["grain"], fw["plane"])
+    f, g, fd, gd, _ = oracle.sinkhorn(GEOM.D, obs.p, obs.I_off, fw["J_off"], ce, ray[:, :3], 3.0,
+                                      2.25, 0, 0.4, 100)
+    for k_mm in (1, 2, 4):
+        _, _, st = oracle.mstep(GEOM, P, om, obs.p, obs.I_off, fw["J_off"], fw["grain"], fw["plane"],
+                                ce, ray[:, :3], f, g, 3.0, Rp, x, n_newton=0, n_mm=k_mm)
+        assert np.all(st[:, 5] >= st[:, 4] - 1e-9 * np.abs(st[:, 4]))
+
+
+def test_em_fixed_point_at_noiseless_truth():
+    """Noiseless data, grains at the truth, plan without dustbin mass: the EM
+    step leaves the poses where they are."""
+    planes, R, x, om, fw, p, I_off = _noiseless_assignment(2)
+    out = oracle.em(GEOM, planes, om, p, I_off, fw["J_off"], fw["grain"], fw["plane"], R, x,
+                    eps_final=1e-4, n_em=2, n_sinkhorn=300, c_out=2.25, mode=0, frac=0.0)
+    np.testing.assert_allclose(out["x"], x, atol=1e-9)
+    np.testing.assert_allclose(out["R"], R, atol=1e-10)
+    np.testing.assert_array_equal(out["assign"], np.arange(len(p)))
+
+
+def test_em_recovers_perturbed_grains(tiny):
+    """Tiny workload with noise and outliers: EM from poses perturbed by
+    ~0.2 deg / 0.1 mm ends within 0.05 deg of the true orientations; with 0.5 mm
+    spot noise over 10 rotations the positions are noise-limited (< 0.5 mm)."""
+    P, R, x, om, fw, obs = (tiny[k] for k in ("planes", "R", "x", "om", "fw", "obs"))
+    rng = np.random.default_rng(21)
+    Rp = np.array([_rotvec(rng.normal(size=3) * 0.002) @ a for a in R])
+    xp = x + rng.normal(size=x.shape) * 0.1
+    out = oracle.em(GEOM, P, om, obs.p, obs.I_off, fw["J_off"], fw["grain"], fw["plane"], Rp, xp,
+                    eps_final=1.0, n_em=10, n_sinkhorn=100, c_out=oracle.c_out_for(0.5, GEOM.D))
+    for Ra, Rb in zip(out["R"], R):
+        ang = math.degrees(math.acos(np.clip((np.trace(Ra.T @ Rb) - 1) / 2, -1, 1)))
+        assert ang < 0.05
+    assert np.abs(out["x"] - x).max() < 0.5
+
+
+# ----------------------------------------------------------------------- SPOT
+
+def test_spot_closed_form_equals_lp():
+    """f(S) = sum_i max_{n in S} Lbar_in equals the LP max <Lbar, P> over plans
+    with P 1 = a and support on S (source weights free)."""
+    from scipy.optimize import linprog
+    rng = np.random.default_rng(0)
+    nI, Nc = 6, 4
+    Lbar = np.maximum(0, rng.normal(size=(nI, Nc)))
+    for S in ([0], [1, 3], [0, 2, 3]):
+        nv = nI * len(S)
+        cvec = -np.array([Lbar[i, n] for i in range(nI) for n in S])
+        A = np.zeros((nI, nv))
+        for i in range(nI):
+            A[i, i * len(S):(i + 1) * len(S)] = 1
+        res = linprog(cvec, A_eq=A, b_eq=np.ones(nI), bounds=(0, None), method="highs")
+        order, gain, F = oracle.spot_greedy(Lbar[:, S], len(S))
+        assert -res.fun == pytest.approx(F[-1], rel=1e-12)
+
+
+def test_spot_greedy_submodular_guarantees():
+    """Greedy gains are non-increasing (submodularity), each prefix is the
+    greedy answer for the smaller cardinality, and the value is at least
+    (1 - 1/e) of the exhaustive optimum (Nemhauser et al.)."""
+    rng = np.random.default_rng(1)
+    for trial in range(5):
+        nI, Nc = 15, 10
+        Lbar = np.maximum(0, rng.normal(size=(nI, Nc)) + 0.3)
+        order, gain, F = oracle.spot_greedy(Lbar, Nc)
+        assert np.all(np.diff(gain) <= 1e-12)
+        for k in range(1, 5):
+            o2, _, _ = oracle.spot_greedy(Lbar, k)
+            np.testing.assert_array_equal(o2, order[:k])
+            best = max(np.maximum.reduce([Lbar[:, n] for n in S]).sum()
+                       for S in itertools.combinations(range(Nc), k))
+            assert F[k - 1] >= (1 - 1 / math.e) * best - 1e-12
+            # the first step is exact
+            if k == 1:
+                assert F[0] == pytest.approx(best)
+
+
+def test_kstar_finds_true_count_on_duplicates(tiny):
+    """Candidates = the true grains, perturbed duplicates and random grains: the
+    largest drop of the greedy increments sits at the true grain count."""
+    P, R, x, om, obs = (tiny[k] for k in ("planes", "R", "x", "om", "obs"))
+    rng = np.random.default_rng(5)
+    dup_R = np.array([_rotvec(rng.normal(size=3) * 0.003) @ a for a in R])
+    dup_x = x + rng.normal(size=x.shape) * 0.05
+    rnd_R, rnd_x = sg.random_grains(TINY, rng)
+    cR = np.concatenate([dup_R, rnd_R, R]); cx = np.concatenate([dup_x, rnd_x, x])
+    Lbar = oracle.spot_matrix(GEOM, P, om, obs.p, obs.I_off, cR, cx, 1.0, 2.25)
+    order, gain, F = oracle.spot_greedy(Lbar, len(cR))
+    k = oracle.kstar(gain)
+    assert k == len(R)
+    chosen = order[:k] % len(R)
+    assert sorted(chosen) == list(range(len(R)))
+
+
+# ------------------------------------------------------------ single-grain fit
+
+def test_single_fit_recovers_near_starts_and_filter_rejects_random(tiny):
+    """Algorithm SingleLaueOT: a start within ~1 deg / 0.5 mm of a true grain
+    converges to it and passes the f_out filter; random starts fail it."""
+    P, R, x, om, obs = (tiny[k] for k in ("planes", "R", "x", "om", "obs"))
+    rng = np.random.default_rng(31)
+    R0 = np.array([_rotvec(rng.normal(size=3) * math.radians(1.0) / math.sqrt(3)) @ a for a in R])
+    x0 = x + rng.normal(size=x.shape) * 0.5
+    Ro, xo, keep, unm = oracle.single_fit(GEOM, P, om, obs.p, obs.I_off, R0, x0, 1.0, 20, 2.25)
+    for Ra, Rb in zip(Ro, R):
+        assert math.degrees(math.acos(np.clip((np.trace(Ra.T @ Rb) - 1) / 2, -1, 1))) < 0.1
+    assert keep.all() and np.abs(xo - x).max() < 0.5
+    Rr, xr = sg.random_grains(TINY, rng)
+    _, _, keep_r, unm_r = oracle.single_fit(GEOM, P, om, obs.p, obs.I_off, Rr, xr, 1.0, 20, 2.25)
+    assert not keep_r.any() and unm_r.min() > 0.5
