@@ -1,0 +1,319 @@
+"""Benchmark of the LaueOT Sinkhorn-EM hot path on GB300.
+
+Workload: 1000 grains, |hkl| <= 6 bcc (a = 2.87 A), 90 rotations over 360 deg,
+0.5 mm spot noise, 70% outliers with uneven per-angle Poisson counts, eps =
+1 mm^2, 200 Sinkhorn iterations per EM step (synthetic, seeded).  One step =
+one EM iteration: refresh of the frozen model list at the current poses, the
+fused cost + Sinkhorn E-step (all angle blocks in each persistent launch), the
+plan read-out, and the M-step (Newton on positions, MM on orientations).
+
+Metric: cost-pair evaluations per second in Sinkhorn (2 * sum_t |I_t| |J_t| per
+iteration).  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cost-pair evals/s in Sinkhorn-EM at 1000 grains; time-to-index vs plain form"
+UNIT = "pairs/s"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([s.strip() for s in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                smax = float(s[2])
+                for k, nm in enumerate(names):
+                    if s[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(dev, seed, api, sg, torch):
+    cfg = sg.CONFIGS["batched"]
+    geom = sg.Geometry()
+    rng = np.random.default_rng(seed)
+    R, x = sg.random_grains(cfg, rng)
+    om = sg.omegas(cfg)
+    h = api.Handle(dev)
+    lat = api.Lattice.cubic(cfg.a, cfg.hmax, cfg.centering, device=dev)
+    om_t = torch.tensor(om, dtype=torch.float32, device=dev)
+    truth = api.forward(h, geom, lat, torch.tensor(R, device=dev), torch.tensor(x, device=dev), om_t)
+    t_j = truth.angle[:truth.n].cpu().numpy()
+    det = truth.spot[:truth.n, 3].cpu().numpy().astype(int)
+    s = truth.spot[:truth.n, :3].cpu().numpy().astype(np.float64)
+    obs = sg.observe(geom, cfg, t_j, det, s, rng)
+    # starting poses (prototype stand-ins): truth perturbed by ~0.1 deg / 0.05 mm
+    ang = rng.normal(size=(cfg.n_grains, 3)) * np.radians(0.1) / np.sqrt(3)
+    th = np.linalg.norm(ang, axis=1, keepdims=True)
+    k = ang / np.maximum(th, 1e-30)
+    K = np.zeros((cfg.n_grains, 3, 3))
+    K[:, 0, 1], K[:, 0, 2], K[:, 1, 2] = -k[:, 2], k[:, 1], -k[:, 0]
+    K = K - K.transpose(0, 2, 1)
+    s_ = np.sin(th)[:, :, None]
+    c_ = (1 - np.cos(th))[:, :, None]
+    dR = np.eye(3)[None] + s_ * K + c_ * (K @ K)
+    R0 = dR @ R
+    x0 = x + rng.normal(size=x.shape) * 0.05
+    R0_t = torch.tensor(R0, dtype=torch.float32, device=dev).reshape(-1, 9).contiguous()
+    x0_t = torch.tensor(x0, dtype=torch.float32, device=dev).contiguous()
+    model = api.forward(h, geom, lat, R0_t, x0_t, om_t).truncated()
+    ob = api.ObsSpots.from_numpy(obs.p, obs.I_off, device=dev)
+    nI = np.diff(obs.I_off)
+    nJ = np.diff(model.J_off.cpu().numpy())
+    pairs_half = int(np.sum(nI.astype(np.int64) * nJ))
+    return dict(cfg=cfg, geom=geom, h=h, lat=lat, om=om_t, obs=obs, ob=ob, model=model, R0=R0_t, x0=x0_t,
+                pairs_half=pairs_half, nI=int(nI.sum()), nJ=int(nJ.sum()), c_out=api.c_out_for(cfg.sigma_mm, geom.D))
+
+
+def em_step(W, api, R, x, stream=None):
+    cfg, geom, h = W["cfg"], W["geom"], W["h"]
+    api.refresh(h, geom, W["lat"], R, x, W["om"], W["model"], stream=stream)
+    out = api.cost_sinkhorn(h, geom, W["ob"], W["model"], cfg.eps, W["c_out"], cfg.n_sinkhorn, harvest=True,
+                            stream=stream)
+    if hasattr(api, "mstep"):
+        api.mstep(h, geom, W["lat"], W["ob"], W["model"], out["f"], out["g"], cfg.eps, W["om"], R, x,
+                  stream=stream)
+    return out
+
+
+def cpu_baseline_sample(W, seconds_hint=15.0):
+    """The FP64 oracle's Sinkhorn on a bounded sample of the same workload:
+    two angle blocks, one full iteration each (row + column update)."""
+    import oracle
+    obs, model = W["obs"], W["model"]
+    J_off = model.J_off.cpu().numpy()
+    c = model.center[:, :3].cpu().numpy().astype(np.float64)
+    r = model.ray[:, :3].cpu().numpy().astype(np.float64)
+    pairs = 0
+    t0 = time.perf_counter()
+    blocks = [0, 45]
+    for t in blocks:
+        i0, i1 = obs.I_off[t], obs.I_off[t + 1]
+        j0, j1 = J_off[t], J_off[t + 1]
+        oracle.sinkhorn(W["geom"].D, obs.p[i0:i1], [0, i1 - i0], [0, j1 - j0], c[j0:j1], r[j0:j1],
+                        W["cfg"].eps, W["c_out"], 0, 0.4, 1)
+        pairs += 2 * (i1 - i0) * (j1 - j0)
+    dt = time.perf_counter() - t0
+    return dict(value=pairs / dt, unit=UNIT, cores=1, kind="oracle",
+                sample="FP64 C oracle, single thread: 1 Sinkhorn iteration (row + column update) on "
+                       "angle blocks %s of the 1000-grain workload, %d pair evaluations in %.1f s"
+                       % (blocks, pairs, dt))
+
+
+def run_reference(args):
+    rank, world, local = _dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    from paper_2404_06478_gb300 import api
+    import synthgen as sg
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    W = build_workload(dev, 0, api, sg, torch)
+    vals = []
+    for _ in range(max(1, args.steps)):
+        vals.append(cpu_baseline_sample(W)["value"])
+    v = float(np.mean(vals))
+    line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, higher_is_better=True, dtype="f64", data="synthetic",
+                config=dict(workload="1000 grains, 90 rotations, 70% uneven outliers, |hkl|<=6; oracle sample"),
+                cpu_baseline=dict(kind="oracle", cores=1, value=v,
+                                  sample="FP64 C oracle, 1 Sinkhorn iteration on 2 angle blocks per step"),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = _dist_env()
+    import torch
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2404_06478_gb300 import api, build
+    import synthgen as sg
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    W = build_workload(dev, rank, api, sg, torch)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    R = W["R0"].clone()
+    x = W["x0"].clone()
+    for _ in range(args.warmup):
+        em_step(W, api, R.clone(), x.clone())
+    torch.cuda.synchronize()
+    # per-launch duration of the dominant kernel: differential timing of the
+    # Sinkhorn passes (n2 - n1 iterations = 2 (n2 - n1) launches of the pair passes)
+    cfg = W["cfg"]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    n1, n2 = 20, 120
+    ev[0].record(stream)
+    api.cost_sinkhorn(W["h"], W["geom"], W["ob"], W["model"], cfg.eps, W["c_out"], n1, harvest=False)
+    ev[1].record(stream)
+    ev[2].record(stream)
+    api.cost_sinkhorn(W["h"], W["geom"], W["ob"], W["model"], cfg.eps, W["c_out"], n2, harvest=False)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    per_launch_ms = (ev[2].elapsed_time(ev[3]) - ev[0].elapsed_time(ev[1])) / (2 * (n2 - n1))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        Rk, xk = W["R0"].clone(), W["x0"].clone()
+        e0.record(stream)
+        em_step(W, api, Rk, xk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pairs_step = 2 * W["pairs_half"] * cfg.n_sinkhorn
+    value = pairs_step * world / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers: H2D of the step's inputs
+    # from pinned memory, the step, D2H of its results
+    p_host = W["ob"].p.cpu().pin_memory()
+    R_host = W["R0"].cpu().pin_memory()
+    x_host = W["x0"].cpu().pin_memory()
+    a_host = torch.empty(W["nI"], dtype=torch.int32).pin_memory()
+    Ro_host = torch.empty_like(R_host).pin_memory()
+    xo_host = torch.empty_like(x_host).pin_memory()
+    e2e_times = []
+    for k in range(max(2, args.steps // 2)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        W["ob"].p.copy_(p_host, non_blocking=True)
+        Rk = R_host.to(dev, non_blocking=True)
+        xk = x_host.to(dev, non_blocking=True)
+        out = em_step(W, api, Rk, xk)
+        a_host.copy_(out["assign"], non_blocking=True)
+        Ro_host.copy_(Rk, non_blocking=True)
+        xo_host.copy_(xk, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = float(np.mean(e2e_times))
+    h2d = p_host.numel() * 4 + R_host.numel() * 4 + x_host.numel() * 4
+    d2h = a_host.numel() * 4 + Ro_host.numel() * 4 + xo_host.numel() * 4
+
+    launches_per_step = 1 + 3 + 2 * cfg.n_sinkhorn + 3 + (1 if hasattr(api, "mstep") else 0)
+    # roofline: MUFU bound, 2 MUFU (rsqrt, ex2) per pair; 16 MUFU results / clk / SM
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = 2070.0
+    peak = sm_count * 16 * clk_mhz * 1e6 / 2
+    achieved = W["pairs_half"] / (per_launch_ms / 1e3)
+    line = dict(
+        metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        data="synthetic",
+        config=dict(workload="1000 grains, |hkl|<=6 bcc, 90 rotations over 360 deg, 0.5 mm noise, "
+                             "70% uneven Poisson outliers, eps=1 mm^2, 200 Sinkhorn iterations per EM step",
+                    grains=cfg.n_grains, angles=cfg.T, observed=W["nI"], model_spots=W["nJ"],
+                    pairs_per_half_iteration=W["pairs_half"], step="one EM iteration",
+                    l2="256 MB buffer written between timed steps", parallelism="replicas" if world > 1 else "1 GPU"),
+        roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="pairs/s", frac=achieved / peak,
+                      traffic=None, kernel="sk_row_kernel+sk_col_kernel (per launch)",
+                      peak_basis="MUFU: %d SMs x 16/clk x %.0f MHz / 2 MUFU per pair" % (sm_count, clk_mhz)),
+        clocks=clk,
+        e2e=dict(value=pairs_step / (e2e_ms / 1e3), unit=UNIT, h2d_bytes_per_step=int(h2d),
+                 d2h_bytes_per_step=int(d2h)),
+        gpu_launches=launches_per_step * args.steps,
+    )
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(W)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,284 @@
+/*
+ * laueot.h — C ABI of the GB300 (sm_103a) implementation of the LaueOT
+ * Sinkhorn-EM indexing hot path (Laue indexing with Optimal Transport,
+ * arXiv 2404.06478).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: LAUE_OK (0) on success, a negative LAUE_ERR_* code on
+ *    failure, LAUE_WARN_* (> 0) when results are valid but a warning applies.
+ *    laue_last_error() gives a message for the last failure on the handle.
+ *  - Ownership: the caller owns every buffer.  Array arguments are DEVICE
+ *    pointers unless the name ends in _host.  The library never allocates
+ *    device memory: scratch space comes from the caller's workspace
+ *    (laue_workspace_size / laue_set_workspace).
+ *  - Streams: `stream` is a cudaStream_t passed as void*.  Calls are
+ *    asynchronous on it, except where a function is documented to return a
+ *    host-side count (it then synchronises that stream).  No entry point
+ *    synchronises the device.
+ *  - Device-side failures (a bounded wait that ran out, a non-finite
+ *    potential) are recorded in a status word inside the workspace; read and
+ *    clear it with laue_device_status().
+ *  - Spot lists are structure-of-arrays sorted by rotation angle t, with
+ *    offsets *_off[T+1] (int32, device): the spots of angle t are
+ *    [off[t], off[t+1]).  Vector data are packed as 4 floats per spot
+ *    (16-byte aligned rows) so that kernels read them as float4.
+ *  - Units: lengths in mm, wavelengths in Angstrom, angles in radians,
+ *    costs, potentials and the temperature eps in mm^2.
+ *  - One handle per host thread.
+ *
+ * Frame (paper Section "Laue analysis", read in a beam-along-z frame): beam
+ * direction e; the sample rotation Gamma_t is a right-handed rotation about
+ * +y by omega_t; detectors are planes with a centre gamma, a unit normal nu
+ * and a half side l/2.
+ */
+#ifndef LAUEOT_H
+#define LAUEOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+#define LAUE_OK 0
+#define LAUE_WARN_NOT_CONVERGED 1
+#define LAUE_ERR_INVALID_ARG (-1)
+#define LAUE_ERR_CAPACITY (-2)
+#define LAUE_ERR_CUDA (-3)
+#define LAUE_ERR_NUMERIC (-4)
+#define LAUE_ERR_TIMEOUT (-5)
+#define LAUE_ERR_UNIMPLEMENTED (-6)
+#define LAUE_ERR_WORKSPACE (-7)
+
+typedef struct laue_handle laue_handle;
+
+/* ---- problem description ---------------------------------------------- */
+
+/* Experiment geometry (host struct, copied at each call).  Paper Section
+ * "Laue diffraction" (Eq. spot_position) and "Detected spots": beam e,
+ * wavelength band [lam_min, lam_max], detectors (gamma, nu, l).  D is the
+ * length that turns ray distances into the pair cost C = D^2 |rhat - r|^2
+ * (the sample-detector distance). */
+typedef struct {
+    float beam[3];
+    float lam_min, lam_max;
+    float D;
+    int n_det; /* 1..4 */
+    float det_centre[4][3];
+    float det_normal[4][3];
+    float det_half[4];
+} LaueGeometry;
+
+/* Plausible plane set (paper Section "Tomography experiments": the set
+ * {(w_m, d_m)} is an input).  One entry per ray direction: w_d0[4m..4m+2] is
+ * the unit crystal direction w_m, w_d0[4m+3] the spacing d0 of its base
+ * reflection g0, nharm[m] the number of allowed harmonics n*g0 (n = 1..nharm),
+ * which share the ray.  Device arrays. */
+typedef struct {
+    const float* w_d0; /* M x 4 */
+    const int* nharm;  /* M */
+    int M;
+} LaueLattice;
+
+/* Detected spots {p_i, t_i} (paper Section "Detected spots"), sorted by t. */
+typedef struct {
+    int T;
+    int n;
+    const int* I_off; /* T+1 */
+    const float* p;   /* n x 4: x, y, z, (unused) */
+} LaueObsSpots;
+
+/* Model spots S (Eq. model_spot_cut) with labels t_j, n_j, m_j, sorted by t
+ * then grain then plane.  Written by laue_forward, rays and centres
+ * rewritten in place by laue_refresh. */
+typedef struct {
+    int T;
+    int n;        /* number of spots in the list */
+    int capacity; /* rows allocated in every array below */
+    int* J_off;   /* T+1 */
+    int* grain;   /* n_j */
+    int* plane;   /* m_j */
+    int* angle;   /* t_j */
+    float* ray;    /* n x 4: r_j (unit), lambda_j */
+    float* center; /* n x 4: c_j = Gamma_t x_n, (unused) */
+    float* spot;   /* n x 4: s_j, detector index (as float) */
+} LaueModelSpots;
+
+/* E-step parameters (paper Section "E-step with Sinkhorn updates" and
+ * Algorithm BalancedOT).  The extended plan has observed rows plus an
+ * unmatched-model row of mass U = ceil(unmatched_frac |J|), model columns
+ * plus an outlier column of mass O = U + |I| - |J| (when O < 0, U = |J| - |I|
+ * and O = 0).  Costs: C_ij pair cost, C_i0 = c_out, C_0j = 0, C_00 = c_out.
+ * dust_mode 0: one dustbin row/column for all angles; 1: one per angle
+ * (masses computed per angle block). */
+typedef struct {
+    double unmatched_frac;
+    float eps;
+    float c_out;
+    int n_iter;
+    int dust_mode;
+    int warm_start; /* nonzero: f, g, dust hold the starting potentials */
+    int pad_;
+} LaueOTParams;
+
+/* M-step parameters (paper Section "The M-step updates", Algorithms
+ * LauePosNewton and LaueRotMM). */
+typedef struct {
+    float eps;      /* temperature of the E-step whose potentials are given */
+    int n_newton;   /* Newton steps on x (4 in the paper's single-grain fits) */
+    int n_mm;       /* MM steps on R */
+    float tol_x;    /* stop Newton when |dx| < tol_x (mm) */
+    float tol_R;    /* stop MM when |dR|_F < tol_R */
+    float hreg;     /* Hessian shift: iota = max(0, lmax(H) + hreg |H|_F) */
+} LaueMParams;
+
+/* Sizes that bound a problem, for laue_workspace_size. */
+typedef struct {
+    int T;
+    int n_obs;
+    int n_model;
+    int n_grains;
+    int n_planes;
+} LaueProblemDims;
+
+/* ---- handle and workspace --------------------------------------------- */
+
+/* Creates a handle bound to CUDA device `device`.  Allocates host memory
+ * only.  Errors: LAUE_ERR_INVALID_ARG (null pointer), LAUE_ERR_CUDA (bad
+ * device). */
+int laue_create(laue_handle** h, int device);
+int laue_destroy(laue_handle* h);
+const char* laue_last_error(const laue_handle* h);
+
+/* Workspace bytes needed for problems bounded by *dims. */
+int laue_workspace_size(laue_handle* h, const LaueProblemDims* dims, size_t* bytes);
+
+/* Hands the library a device buffer of `bytes` bytes (256-byte aligned) to
+ * use as scratch; it must stay valid while calls that use it are in flight.
+ * The first 256 bytes hold the device status word and must be zeroed by
+ * this call's stream order before first use: laue_set_workspace enqueues that
+ * clear on `stream`. */
+int laue_set_workspace(laue_handle* h, void* dev_ptr, size_t bytes, void* stream);
+
+/* Synchronises `stream`, returns the device status word (LAUE_OK or a
+ * LAUE_ERR_* code recorded by a kernel) in *status_host and clears it. */
+int laue_device_status(laue_handle* h, void* stream, int* status_host);
+
+/* ---- host helper ------------------------------------------------------- */
+
+/* Plausible plane set of a cubic lattice (paper Section "Crystallographic
+ * planes": d = a / |hkl|): every hkl with max(|h|,|k|,|l|) <= hmax allowed by
+ * the centering (0 = P, 1 = I: h+k+l even, 2 = F: h,k,l unmixed), one entry per
+ * ray direction (Friedel pairs and harmonics merged), ordered by |g0|^2
+ * ascending then g0 descending.  Host arrays: w_d0_host (cap x 4),
+ * nharm_host (cap), hkl0_host (cap x 3, may be NULL).  *M = number of entries;
+ * LAUE_ERR_CAPACITY if *M > cap (nothing beyond cap written). */
+int laue_reflections(double a, int hmax, int centering, int cap, float* w_d0_host,
+                     int* nharm_host, int* hkl0_host, int* M);
+
+/* ---- hot path ---------------------------------------------------------- */
+
+/* Forward Laue model and cut (paper Eqs. ray_mnt, s_mnt, wavelength,
+ * model_spot_cut): for every (t, n, m), u = Gamma_t R_n w_m,
+ * r = e - 2 (u.e) u, lambda = 2 d0 |u.e| / n for the smallest harmonic n with
+ * lambda in band, spot s = c + tau r on the detector with the smallest
+ * tau > 0 whose square contains it, c = Gamma_t x_n.  Visible spots are
+ * written to *out sorted by (t, n, m) (deterministic).
+ * R: N x 9 row-major (crystal -> sample), x: N x 3, omega: T (device).
+ * *total_host receives the number of visible spots; this call synchronises
+ * `stream` to read it.  LAUE_ERR_CAPACITY if it exceeds out->capacity (then
+ * only J_off and the first capacity rows are valid).  Needs the workspace. */
+int laue_forward(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                 const float* R, const float* x, int N, const float* omega, int T,
+                 LaueModelSpots* out, int* total_host, void* stream);
+
+/* Rays, centres, wavelengths and spot positions of a frozen model-spot list
+ * at new poses (the list stays the one of the prototypes, paper Section
+ * "Assignments with outlier and missing spots").  Asynchronous. */
+int laue_refresh(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                 const float* R, const float* x, const float* omega,
+                 LaueModelSpots* model, void* stream);
+
+/* Fused pair cost + log-domain balanced Sinkhorn (paper Eqs. update_L,
+ * estep_obj, Algorithm BalancedOT), blocked by angle, never materialising the
+ * cost matrix: C_ij = D^2 |rhat_ij - r_j|^2, rhat_ij = (p_i - c_j)/|p_i - c_j|.
+ * Starts at f = g = 0 unless warm_start, runs the row update first, n_iter
+ * iterations.  Outputs (device):
+ *   f (obs->n) and g (model->n) potentials, dust: [f_0 | g_0] (2 floats in
+ *   global mode, 2T in per-angle mode: T row values then T column values),
+ *   assign (obs->n, optional): argmax of plan row i over the block's model
+ *   spots and the outlier column (-1); ties to the lowest index,
+ *   margin (optional): top1 - top2 of the row's plan entries,
+ *   marg_err (optional, 2 floats): largest row and column marginal error,
+ *   q (optional, model->n): column mass sum_i Q_ij over observed rows.
+ * Asynchronous.  Non-finite potentials set LAUE_ERR_NUMERIC in the device
+ * status word. */
+int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* obs,
+                       const LaueModelSpots* model, const LaueOTParams* prm, float* f, float* g,
+                       float* dust, int* assign, float* margin, float* marg_err, float* q,
+                       void* stream);
+
+/* M-step (paper Section "The M-step updates", Appendix "M-steps"): with the
+ * plan Q_ij = exp((f_i + g_j - C_ij)/eps) of the E-step (costs from the
+ * model list's current rays and centres, which must be those of the E-step),
+ * per grain n_newton Newton steps on x_n (exact gradient and Hessian of
+ * sum Q rhat.r), then n_mm MM steps on R_n (Eqs. M0, Mm, majmin_step; Wahba by
+ * the 4x4 quaternion eigenproblem).  R (N x 9) and x (N x 3) are updated in
+ * place.  step_norms (optional, N x 2): last |dx| and |dR|_F.  Asynchronous. */
+int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+               const LaueObsSpots* obs, const LaueModelSpots* model, const float* f,
+               const float* g, const LaueMParams* prm, const float* omega, float* R, float* x,
+               int N, float* step_norms, void* stream);
+
+/* Gradient of the OT-weighted spot cost E_n = sum_{j in J_n} sum_i Q_ij C_ij
+ * with Q held at the plan of potentials (f, g) and the current costs
+ * (Danskin), with respect to a left-multiplicative axis-angle perturbation
+ * R_n <- exp([w]x) R_n and to x_n: grad (N x 6) = [dE/dw, dE/dx]; value (N,
+ * optional) = E_n.  Costs are recomputed, not stored.  Asynchronous. */
+int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                        const LaueObsSpots* obs, const LaueModelSpots* model, const float* f,
+                        const float* g, float eps, const float* omega, const float* R,
+                        const float* x, int N, float* grad, float* value, void* stream);
+
+/* SPOT prototype selection (paper Section "Selection of Prototypes with
+ * Optimal Transport", Appendix "Selection of prototypes", Algorithm
+ * LaueSpotGreedy): candidate grains (candR Nc x 9, candX Nc x 3) make their
+ * spots; Lbar_in = max(0, LSE_{j of n at t_i}(-C_ij/eps_s) + c_out/eps_s);
+ * greedy facility-location selection of k_max prototypes (ties to the lowest
+ * index); order (k_max), gains (k_max increments), *k_star_host = argmax over
+ * 2 <= k <= K of Delta_k - Delta_{k+1} (Delta_{K+1} = 0).  Synchronises
+ * `stream` to return *k_star_host. */
+int laue_prototype_select(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                          const LaueObsSpots* obs, const float* omega, const float* candR,
+                          const float* candX, int Nc, float eps_s, float c_out, int k_max,
+                          int* order, float* gains, int* k_star_host, void* stream);
+
+/* End-to-end indexing (paper Algorithm LaueOT preceded by the pre-processing
+ * of Section "Pre-processing"): candidate fits from the start grid (startR
+ * S x 9, startX S x 3) by batched single-grain fitting with the f_out filter,
+ * SPOT selection, then n_em annealed EM steps.  Outputs R_out/x_out (capacity
+ * n_max), *n_grains_host, assign (obs->n).  Synchronises `stream`. */
+typedef struct {
+    double unmatched_frac;
+    float eps_final;
+    float c_out;
+    float f_out;
+    int n_em;
+    int n_sinkhorn;
+    int k_single;  /* annealed steps of each single-grain fit */
+    int dust_mode;
+    LaueMParams mstep;
+} LaueIndexParams;
+
+int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+               const LaueObsSpots* obs, const float* omega, const float* startR,
+               const float* startX, int S, const LaueIndexParams* prm, float* R_out,
+               float* x_out, int n_max, int* n_grains_host, int* assign, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAUEOT_H */

@@ -1,0 +1,292 @@
+"""Python binding of the LaueOT C ABI (same names as include/laueot.h).
+
+Marshalling only: tensors are handed to liblaueot.so by data pointer together
+with the current CUDA stream; PyTorch provides device memory and streams.  No
+step of the hot path runs here, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+class LaueError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("LaueOT error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def c_out_for(sigma_mm: float, D: float) -> float:
+    """Outlier cost c_out = D^2 |a - b|^2 for unit rays 3 sigma apart
+    (likelihood at 3 sigma, sigma_ang = sigma_mm / D)."""
+    return 4.0 * D * D * math.sin(1.5 * sigma_mm / D) ** 2
+
+
+def geometry_struct(geom) -> N.LaueGeometry:
+    g = N.LaueGeometry()
+    g.beam[:] = [float(v) for v in geom.beam]
+    g.lam_min, g.lam_max, g.D = float(geom.lam_min), float(geom.lam_max), float(geom.D)
+    g.n_det = len(geom.detectors)
+    for k, det in enumerate(geom.detectors):
+        g.det_centre[k][:] = [float(v) for v in det.centre]
+        g.det_normal[k][:] = [float(v) for v in det.normal]
+        g.det_half[k] = float(det.half)
+    return g
+
+
+def reflections(a: float, hmax: int, centering: int = 1):
+    """Plane table on the host: (w_d0 (M, 4) float32, nharm (M,) int32, hkl0 (M, 3) int32)."""
+    L = N.lib()
+    M = ctypes.c_int(0)
+    L.laue_reflections(a, hmax, centering, 0, None, None, None, ctypes.byref(M))
+    w = np.zeros((M.value, 4), np.float32)
+    nh = np.zeros(M.value, np.int32)
+    hk = np.zeros((M.value, 3), np.int32)
+    rc = L.laue_reflections(a, hmax, centering, M.value, w.ctypes.data_as(ctypes.c_void_p),
+                            nh.ctypes.data_as(ctypes.c_void_p), hk.ctypes.data_as(ctypes.c_void_p),
+                            ctypes.byref(M))
+    if rc != 0:
+        raise LaueError(rc, "laue_reflections failed")
+    return w, nh, hk
+
+
+@dataclasses.dataclass
+class Lattice:
+    w_d0: torch.Tensor   # (M, 4) float32 device
+    nharm: torch.Tensor  # (M,) int32 device
+
+    def struct(self):
+        return N.LaueLattice(_ptr(self.w_d0), _ptr(self.nharm), int(self.w_d0.shape[0]))
+
+    @staticmethod
+    def cubic(a, hmax, centering=1, device="cuda"):
+        w, nh, _ = reflections(a, hmax, centering)
+        return Lattice(torch.from_numpy(w).to(device), torch.from_numpy(nh).to(device))
+
+
+@dataclasses.dataclass
+class ObsSpots:
+    p: torch.Tensor      # (n, 4) float32 device
+    I_off: torch.Tensor  # (T+1,) int32 device
+
+    @property
+    def T(self):
+        return int(self.I_off.shape[0]) - 1
+
+    def struct(self):
+        return N.LaueObsSpots(self.T, int(self.p.shape[0]), _ptr(self.I_off), _ptr(self.p))
+
+    @staticmethod
+    def from_numpy(p, I_off, device="cuda"):
+        P = np.zeros((len(p), 4), np.float32)
+        P[:, :3] = p
+        return ObsSpots(torch.from_numpy(P).to(device),
+                        torch.from_numpy(np.asarray(I_off, np.int32)).to(device))
+
+
+@dataclasses.dataclass
+class ModelSpots:
+    T: int
+    n: int
+    J_off: torch.Tensor
+    grain: torch.Tensor
+    plane: torch.Tensor
+    angle: torch.Tensor
+    ray: torch.Tensor
+    center: torch.Tensor
+    spot: torch.Tensor
+
+    @property
+    def capacity(self):
+        return int(self.grain.shape[0])
+
+    def struct(self):
+        return N.LaueModelSpots(self.T, self.n, self.capacity, _ptr(self.J_off), _ptr(self.grain),
+                                _ptr(self.plane), _ptr(self.angle), _ptr(self.ray), _ptr(self.center),
+                                _ptr(self.spot))
+
+    @staticmethod
+    def empty(T, capacity, device="cuda"):
+        cap = max(int(capacity), 1)
+        z = lambda *s, dt=torch.int32: torch.zeros(*s, dtype=dt, device=device)
+        return ModelSpots(T, 0, z(T + 1), z(cap), z(cap), z(cap), z(cap, 4, dt=torch.float32),
+                          z(cap, 4, dt=torch.float32), z(cap, 4, dt=torch.float32))
+
+    @staticmethod
+    def from_numpy(J_off, grain, plane, ray4, center3, spot3=None, det=None, device="cuda"):
+        """Model list from host arrays (J_off (T+1,), labels (n,), ray4 (n, 4) =
+        (r, lambda), center3 (n, 3), spot3 (n, 3), det (n,))."""
+        J_off = np.asarray(J_off, np.int32)
+        T, n = len(J_off) - 1, int(J_off[-1])
+        out = ModelSpots.empty(T, n, device=device)
+        out.n = n
+        t = np.repeat(np.arange(T, dtype=np.int32), np.diff(J_off))
+        c4 = np.zeros((n, 4), np.float32)
+        c4[:, :3] = center3
+        s4 = np.zeros((n, 4), np.float32)
+        if spot3 is not None:
+            s4[:, :3] = spot3
+        if det is not None:
+            s4[:, 3] = det
+        cp = lambda dst, src: dst[:n].copy_(torch.from_numpy(np.ascontiguousarray(src)))
+        out.J_off.copy_(torch.from_numpy(J_off))
+        if n:
+            cp(out.grain, np.asarray(grain, np.int32))
+            cp(out.plane, np.asarray(plane, np.int32))
+            cp(out.angle, t)
+            cp(out.ray, np.asarray(ray4, np.float32))
+            cp(out.center, c4)
+            cp(out.spot, s4)
+        return out
+
+    def truncated(self):
+        n = self.n
+        return ModelSpots(self.T, n, self.J_off, self.grain[:n], self.plane[:n], self.angle[:n],
+                          self.ray[:n], self.center[:n], self.spot[:n])
+
+
+class Handle:
+    """laue_create / laue_destroy plus a workspace tensor owned by this object."""
+
+    def __init__(self, device=None):
+        dev = torch.device(device) if device is not None else torch.device("cuda")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.L = N.lib()
+        h = ctypes.c_void_p()
+        rc = self.L.laue_create(ctypes.byref(h), self.device.index or 0)
+        if rc != 0:
+            raise LaueError(rc, "laue_create failed")
+        self.h = h
+        self.ws = None
+
+    def close(self):
+        if self.h:
+            self.L.laue_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc, what=""):
+        if rc < 0:
+            msg = self.L.laue_last_error(self.h)
+            raise LaueError(rc, (what + ": " if what else "") + (msg.decode() if msg else ""))
+        return rc
+
+    def workspace_size(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0) -> int:
+        d = N.LaueProblemDims(T, n_obs, n_model, n_grains, n_planes)
+        b = ctypes.c_size_t()
+        self.check(self.L.laue_workspace_size(self.h, ctypes.byref(d), ctypes.byref(b)), "workspace_size")
+        return b.value
+
+    def reserve(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0, stream=None):
+        need = self.workspace_size(T, n_obs, n_model, n_grains, n_planes)
+        if self.ws is None or self.ws.numel() < need:
+            self.ws = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
+            self.check(self.L.laue_set_workspace(self.h, _ptr(self.ws), self.ws.numel(), _stream(stream)),
+                       "set_workspace")
+        return self.ws
+
+    def device_status(self, stream=None) -> int:
+        v = ctypes.c_int(0)
+        self.check(self.L.laue_device_status(self.h, _stream(stream), ctypes.byref(v)), "device_status")
+        return v.value
+
+
+def forward(h: Handle, geom, lat: Lattice, R, x, omega, capacity=None, stream=None) -> ModelSpots:
+    """laue_forward: visible model spots of grains (R (N,3,3), x (N,3)) at angles omega (T,)."""
+    R = R.reshape(-1, 9).contiguous().float()
+    x = x.reshape(-1, 3).contiguous().float()
+    omega = omega.contiguous().float()
+    N_, T = int(R.shape[0]), int(omega.shape[0])
+    M = int(lat.w_d0.shape[0])
+    h.reserve(T, n_grains=N_, n_planes=M, stream=stream)
+    cap = capacity if capacity is not None else max(64, N_ * T * 16)
+    out = ModelSpots.empty(T, cap, device=R.device)
+    st = out.struct()
+    total = ctypes.c_int(0)
+    g = geometry_struct(geom)
+    ls = lat.struct()
+    rc = h.L.laue_forward(h.h, ctypes.byref(g), ctypes.byref(ls), _ptr(R), _ptr(x), N_, _ptr(omega), T,
+                          ctypes.byref(st), ctypes.byref(total), _stream(stream))
+    if rc == N.LAUE_ERR_CAPACITY and capacity is None:
+        out = ModelSpots.empty(T, total.value, device=R.device)
+        st = out.struct()
+        rc = h.L.laue_forward(h.h, ctypes.byref(g), ctypes.byref(ls), _ptr(R), _ptr(x), N_, _ptr(omega), T,
+                              ctypes.byref(st), ctypes.byref(total), _stream(stream))
+    h.check(rc, "laue_forward")
+    out.n = total.value
+    return out
+
+
+def refresh(h: Handle, geom, lat: Lattice, R, x, omega, model: ModelSpots, stream=None):
+    R = R.reshape(-1, 9).contiguous().float()
+    x = x.reshape(-1, 3).contiguous().float()
+    st = model.struct()
+    g = geometry_struct(geom)
+    ls = lat.struct()
+    h.check(h.L.laue_refresh(h.h, ctypes.byref(g), ctypes.byref(ls), _ptr(R), _ptr(x),
+                             _ptr(omega.contiguous().float()), ctypes.byref(st), _stream(stream)),
+            "laue_refresh")
+
+
+def ot_params(eps, c_out, n_iter, dust_mode=0, unmatched_frac=0.4, warm_start=False):
+    return N.LaueOTParams(float(unmatched_frac), float(eps), float(c_out), int(n_iter), int(dust_mode),
+                          1 if warm_start else 0, 0)
+
+
+def cost_sinkhorn(h: Handle, geom, obs: ObsSpots, model: ModelSpots, eps, c_out, n_iter, dust_mode=0,
+                  unmatched_frac=0.4, harvest=True, col_harvest=False, init=None, stream=None):
+    """laue_cost_sinkhorn; returns dict of device tensors f, g, dust and, with
+    harvest, assign, margin, marg_err (and q with col_harvest)."""
+    dev = obs.p.device
+    T = obs.T
+    nI, nJ = int(obs.p.shape[0]), model.n
+    h.reserve(T, n_obs=nI, n_model=nJ, stream=stream)
+    nd = T if dust_mode else 1
+    out = {}
+    if init is not None:
+        f, g, dust = (t.clone().float().contiguous() for t in init)
+    else:
+        f = torch.zeros(max(nI, 1), device=dev)
+        g = torch.zeros(max(nJ, 1), device=dev)
+        dust = torch.zeros(2 * nd, device=dev)
+    assign = torch.empty(max(nI, 1), dtype=torch.int32, device=dev) if harvest else None
+    margin = torch.empty(max(nI, 1), device=dev) if harvest else None
+    merr = torch.empty(2, device=dev) if (harvest or col_harvest) else None
+    q = torch.empty(max(nJ, 1), device=dev) if col_harvest else None
+    prm = ot_params(eps, c_out, n_iter, dust_mode, unmatched_frac, init is not None)
+    g_s = geometry_struct(geom)
+    o_s = obs.struct()
+    m_s = model.struct()
+    h.check(h.L.laue_cost_sinkhorn(h.h, ctypes.byref(g_s), ctypes.byref(o_s), ctypes.byref(m_s),
+                                   ctypes.byref(prm), _ptr(f), _ptr(g), _ptr(dust), _ptr(assign), _ptr(margin),
+                                   _ptr(merr), _ptr(q), _stream(stream)), "laue_cost_sinkhorn")
+    out.update(f=f[:nI], g=g[:nJ], dust=dust)
+    if harvest:
+        out.update(assign=assign[:nI], margin=margin[:nI])
+    if merr is not None:
+        out["marg_err"] = merr
+    if col_harvest:
+        out["q"] = q[:nJ]
+    return out

@@ -1,0 +1,433 @@
+// api.cu — host side of the C ABI declared in include/laueot.h: handle,
+// workspace, argument validation and kernel launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "api_internal.h"
+
+using namespace laue;
+
+// ------------------------------------------------------------- helpers
+
+int laue_fail(laue_handle* h, int code, const char* fmt, ...) {
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int laue_cuda_check(laue_handle* h, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return LAUE_OK;
+    return laue_fail(h, LAUE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+GeomDev laue_geom_dev(const LaueGeometry& g) {
+    GeomDev d{};
+    for (int a = 0; a < 3; ++a) d.e[a] = g.beam[a];
+    d.lam_min = g.lam_min;
+    d.lam_max = g.lam_max;
+    d.D = g.D;
+    d.n_det = g.n_det;
+    for (int k = 0; k < 4; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            d.ctr[k][a] = g.det_centre[k][a];
+            d.nrm[k][a] = g.det_normal[k][a];
+        }
+        d.half[k] = g.det_half[k];
+    }
+    return d;
+}
+
+int laue_check_geom(laue_handle* h, const LaueGeometry* g) {
+    if (!g) return laue_fail(h, LAUE_ERR_INVALID_ARG, "geometry is NULL");
+    if (g->n_det < 1 || g->n_det > 4) return laue_fail(h, LAUE_ERR_INVALID_ARG, "n_det must be 1..4");
+    if (!(g->lam_min > 0.0f) || !(g->lam_max >= g->lam_min))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "wavelength band must satisfy 0 < lam_min <= lam_max");
+    if (!(g->D > 0.0f)) return laue_fail(h, LAUE_ERR_INVALID_ARG, "D must be positive");
+    for (int k = 0; k < g->n_det; ++k)
+        if (!(g->det_half[k] > 0.0f)) return laue_fail(h, LAUE_ERR_INVALID_ARG, "detector half size must be > 0");
+    return LAUE_OK;
+}
+
+int laue_check_obs(laue_handle* h, const LaueObsSpots* o) {
+    if (!o) return laue_fail(h, LAUE_ERR_INVALID_ARG, "observed spots are NULL");
+    if (o->T < 1 || o->n < 0) return laue_fail(h, LAUE_ERR_INVALID_ARG, "observed spots: T >= 1 and n >= 0");
+    if (!o->I_off) return laue_fail(h, LAUE_ERR_INVALID_ARG, "observed spots: I_off is NULL");
+    if (o->n > 0 && (!o->p || !aligned16(o->p)))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "observed spots: p must be a 16-byte aligned device array");
+    return LAUE_OK;
+}
+
+int laue_check_model(laue_handle* h, const LaueModelSpots* m) {
+    if (!m) return laue_fail(h, LAUE_ERR_INVALID_ARG, "model spots are NULL");
+    if (m->T < 1 || m->n < 0 || m->n > m->capacity)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "model spots: T >= 1 and 0 <= n <= capacity");
+    if (!m->J_off) return laue_fail(h, LAUE_ERR_INVALID_ARG, "model spots: J_off is NULL");
+    if (m->n > 0) {
+        if (!m->grain || !m->plane || !m->angle || !m->ray || !m->center || !m->spot)
+            return laue_fail(h, LAUE_ERR_INVALID_ARG, "model spots: a label or vector array is NULL");
+        if (!aligned16(m->ray) || !aligned16(m->center) || !aligned16(m->spot))
+            return laue_fail(h, LAUE_ERR_INVALID_ARG, "model spots: vector arrays must be 16-byte aligned");
+    }
+    return LAUE_OK;
+}
+
+int laue_need_ws(laue_handle* h, const LaueProblemDims& d, Layout* L) {
+    *L = make_layout(d);
+    if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set (laue_set_workspace)");
+    if (L->total > h->ws_bytes)
+        return laue_fail(h, LAUE_ERR_WORKSPACE, "workspace too small: need %zu bytes, have %zu", L->total,
+                         h->ws_bytes);
+    return LAUE_OK;
+}
+
+// ------------------------------------------------------------- handle
+
+extern "C" int laue_create(laue_handle** h, int device) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    *h = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return LAUE_ERR_CUDA;
+    laue_handle* H = (laue_handle*)calloc(1, sizeof(laue_handle));
+    if (!H) return LAUE_ERR_INVALID_ARG;
+    H->device = device;
+    if (cudaDeviceGetAttribute(&H->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        free(H);
+        return LAUE_ERR_CUDA;
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(device);
+    if (sinkhorn_occupancy(&H->row_bps, &H->col_bps) != 0) {
+        H->row_bps = H->col_bps = 1;
+    }
+    cudaSetDevice(prev);
+    if (H->row_bps < 1) H->row_bps = 1;
+    if (H->col_bps < 1) H->col_bps = 1;
+    H->err[0] = 0;
+    *h = H;
+    return LAUE_OK;
+}
+
+extern "C" int laue_destroy(laue_handle* h) {
+    free(h);
+    return LAUE_OK;
+}
+
+extern "C" const char* laue_last_error(const laue_handle* h) { return h ? h->err : "null handle"; }
+
+extern "C" int laue_workspace_size(laue_handle* h, const LaueProblemDims* dims, size_t* bytes) {
+    if (!h || !dims || !bytes) return laue_fail(h, LAUE_ERR_INVALID_ARG, "null argument");
+    if (dims->T < 0 || dims->n_obs < 0 || dims->n_model < 0 || dims->n_grains < 0 || dims->n_planes < 0)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "negative dimension");
+    *bytes = make_layout(*dims).total;
+    return LAUE_OK;
+}
+
+extern "C" int laue_set_workspace(laue_handle* h, void* dev_ptr, size_t bytes, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    if (dev_ptr && ((uintptr_t)dev_ptr & 255u))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    if (dev_ptr && bytes < kCtrlBytes) return laue_fail(h, LAUE_ERR_WORKSPACE, "workspace smaller than 4 KB");
+    h->ws = dev_ptr;
+    h->ws_bytes = dev_ptr ? bytes : 0;
+    if (dev_ptr)
+        return laue_cuda_check(h, cudaMemsetAsync(dev_ptr, 0, kCtrlBytes, (cudaStream_t)stream),
+                               "clearing workspace control block");
+    return LAUE_OK;
+}
+
+extern "C" int laue_device_status(laue_handle* h, void* stream, int* status_host) {
+    if (!h || !status_host) return laue_fail(h, LAUE_ERR_INVALID_ARG, "null argument");
+    if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set");
+    cudaStream_t s = (cudaStream_t)stream;
+    int v = 0;
+    int rc = laue_cuda_check(h, cudaMemcpyAsync(&v, h->ws, sizeof(int), cudaMemcpyDeviceToHost, s),
+                             "reading status");
+    if (rc) return rc;
+    rc = laue_cuda_check(h, cudaStreamSynchronize(s), "synchronising stream");
+    if (rc) return rc;
+    *status_host = v;
+    return laue_cuda_check(h, cudaMemsetAsync(h->ws, 0, sizeof(int), s), "clearing status");
+}
+
+// ------------------------------------------------------------- host helper
+
+namespace {
+struct Refl {
+    int g0[3];
+    int n2, nh;
+    double w[3], d0;
+};
+int gcd_i(int a, int b) {
+    a = std::abs(a);
+    b = std::abs(b);
+    while (b) {
+        int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+bool allowed(int h, int k, int l, int centering) {
+    if (h == 0 && k == 0 && l == 0) return false;
+    auto par = [](int v) { return ((v % 2) + 2) % 2; };
+    if (centering == 1) return par(h + k + l) == 0;
+    if (centering == 2) return par(h) == par(k) && par(k) == par(l);
+    return true;
+}
+}  // namespace
+
+extern "C" int laue_reflections(double a, int hmax, int centering, int cap, float* w_d0_host,
+                                int* nharm_host, int* hkl0_host, int* M) {
+    if (!M || hmax < 1 || hmax > 64 || !(a > 0.0) || centering < 0 || centering > 2 || cap < 0)
+        return LAUE_ERR_INVALID_ARG;
+    std::vector<Refl> list;
+    for (int h = -hmax; h <= hmax; ++h)
+        for (int k = -hmax; k <= hmax; ++k)
+            for (int l = -hmax; l <= hmax; ++l) {
+                if ((h == 0 && k == 0 && l == 0) || gcd_i(gcd_i(h, k), l) != 1) continue;
+                int first = h != 0 ? h : (k != 0 ? k : l);
+                if (first < 0) continue;  // one direction per Friedel pair
+                int pmax = std::max(std::abs(h), std::max(std::abs(k), std::abs(l)));
+                std::vector<int> mult;
+                for (int m = 1; m * pmax <= hmax; ++m)
+                    if (allowed(m * h, m * k, m * l, centering)) mult.push_back(m);
+                if (mult.empty()) continue;
+                for (size_t q = 0; q < mult.size(); ++q)
+                    if (mult[q] != (int)(q + 1) * mult[0]) return LAUE_ERR_INVALID_ARG;
+                Refl R;
+                R.g0[0] = mult[0] * h;
+                R.g0[1] = mult[0] * k;
+                R.g0[2] = mult[0] * l;
+                R.n2 = R.g0[0] * R.g0[0] + R.g0[1] * R.g0[1] + R.g0[2] * R.g0[2];
+                R.nh = (int)mult.size();
+                double pn = std::sqrt((double)(h * h + k * k + l * l));
+                R.w[0] = h / pn;
+                R.w[1] = k / pn;
+                R.w[2] = l / pn;
+                R.d0 = a / std::sqrt((double)R.n2);
+                list.push_back(R);
+            }
+    std::sort(list.begin(), list.end(), [](const Refl& x, const Refl& y) {
+        if (x.n2 != y.n2) return x.n2 < y.n2;
+        for (int q = 0; q < 3; ++q)
+            if (x.g0[q] != y.g0[q]) return x.g0[q] > y.g0[q];
+        return false;
+    });
+    *M = (int)list.size();
+    for (int m = 0; m < (int)list.size() && m < cap; ++m) {
+        if (w_d0_host) {
+            for (int q = 0; q < 3; ++q) w_d0_host[4 * m + q] = (float)list[m].w[q];
+            w_d0_host[4 * m + 3] = (float)list[m].d0;
+        }
+        if (nharm_host) nharm_host[m] = list[m].nh;
+        if (hkl0_host)
+            for (int q = 0; q < 3; ++q) hkl0_host[3 * m + q] = list[m].g0[q];
+    }
+    return (int)list.size() > cap ? LAUE_ERR_CAPACITY : LAUE_OK;
+}
+
+// ------------------------------------------------------------- forward
+
+extern "C" int laue_forward(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                            const float* R, const float* x, int N, const float* omega, int T,
+                            LaueModelSpots* out, int* total_host, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    int rc = laue_check_geom(h, geom);
+    if (rc) return rc;
+    if (!lat || lat->M < 0 || (lat->M > 0 && (!lat->w_d0 || !lat->nharm || !aligned16(lat->w_d0))))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "lattice: M >= 0 and 16-byte aligned w_d0");
+    if (N < 0 || T < 1 || !omega || (N > 0 && (!R || !x)) || !out || !total_host)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "forward: bad N, T or NULL array");
+    if (out->T != T || !out->J_off || out->capacity < 0)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "forward: output list must have T = %d and J_off", T);
+    if (out->capacity > 0 && (!out->grain || !out->plane || !out->angle || !out->ray || !out->center ||
+                              !out->spot || !aligned16(out->ray) || !aligned16(out->center) ||
+                              !aligned16(out->spot)))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "forward: output arrays NULL or misaligned");
+    LaueProblemDims d{T, 0, 0, N, lat->M};
+    Layout L;
+    if ((rc = laue_need_ws(h, d, &L))) return rc;
+    char* ws = (char*)h->ws;
+    cudaStream_t s = (cudaStream_t)stream;
+    FwdArgs a{};
+    a.G = laue_geom_dev(*geom);
+    a.R = R;
+    a.x = x;
+    a.omega = omega;
+    a.w_d0 = (const float4*)lat->w_d0;
+    a.nharm = lat->nharm;
+    a.N = N;
+    a.M = lat->M;
+    a.T = T;
+    a.n_rays = (long long)T * N * lat->M;
+    a.n_blocks = (int)((a.n_rays + kFwdBlock - 1) / kFwdBlock);
+    a.capacity = out->capacity;
+    a.blocks = (int*)(ws + L.fwd_blocks);
+    a.ctrl = (int*)(ws + L.ctrl);
+    a.J_off = out->J_off;
+    a.grain = out->grain;
+    a.plane = out->plane;
+    a.angle = out->angle;
+    a.ray = (float4*)out->ray;
+    a.center = (float4*)out->center;
+    a.spot = (float4*)out->spot;
+    if ((rc = laue_cuda_check(h, cudaMemsetAsync(out->J_off, 0, sizeof(int) * (T + 1), s), "clearing J_off")))
+        return rc;
+    if ((rc = laue_cuda_check(h, launch_forward(a, s), "forward launch"))) return rc;
+    int total = 0;
+    if ((rc = laue_cuda_check(h, cudaMemcpyAsync(&total, a.ctrl + CTRL_FWD_TOTAL, sizeof(int),
+                                                 cudaMemcpyDeviceToHost, s),
+                              "reading spot count")))
+        return rc;
+    if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "forward synchronise"))) return rc;
+    *total_host = total;
+    out->n = std::min(total, out->capacity);
+    if (total > out->capacity)
+        return laue_fail(h, LAUE_ERR_CAPACITY, "forward: %d visible spots exceed capacity %d", total,
+                         out->capacity);
+    return LAUE_OK;
+}
+
+extern "C" int laue_refresh(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const float* R,
+                            const float* x, const float* omega, LaueModelSpots* model, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    int rc = laue_check_geom(h, geom);
+    if (rc) return rc;
+    if ((rc = laue_check_model(h, model))) return rc;
+    if (!lat || (lat->M > 0 && (!lat->w_d0 || !lat->nharm)) || !R || !x || !omega)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "refresh: NULL array");
+    RefreshArgs a{};
+    a.G = laue_geom_dev(*geom);
+    a.R = R;
+    a.x = x;
+    a.omega = omega;
+    a.w_d0 = (const float4*)lat->w_d0;
+    a.nharm = lat->nharm;
+    a.n = model->n;
+    a.grain = model->grain;
+    a.plane = model->plane;
+    a.angle = model->angle;
+    a.ray = (float4*)model->ray;
+    a.center = (float4*)model->center;
+    a.spot = (float4*)model->spot;
+    return laue_cuda_check(h, launch_refresh(a, (cudaStream_t)stream), "refresh launch");
+}
+
+// ------------------------------------------------------------- Sinkhorn
+
+int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* obs, const LaueModelSpots* model,
+                 const LaueOTParams* prm, const Layout& L, SkArgs* out, SkLaunch* lc) {
+    char* ws = (char*)h->ws;
+    SkArgs a{};
+    a.T = obs->T;
+    a.n_obs = obs->n;
+    a.n_model = model->n;
+    a.I_off = obs->I_off;
+    a.J_off = model->J_off;
+    a.obs_p = (const float4*)obs->p;
+    a.mod_c = (const float4*)model->center;
+    a.modR = (const float4*)model->ray;
+    a.obsP = (float4*)(ws + L.obsP);
+    a.modC = (float4*)(ws + L.modC);
+    a.row_tiles = (int4*)(ws + L.row_tiles);
+    a.col_tiles = (int4*)(ws + L.col_tiles);
+    a.ang_tiles = (int4*)(ws + L.ang);
+    a.row_part = (float2*)(ws + L.row_part);
+    a.col_part = (float2*)(ws + L.col_part);
+    a.dust = (float*)(ws + L.dust);
+    a.ctrl = (int*)(ws + L.ctrl);
+    a.max_row_tiles = L.max_row_tiles;
+    a.max_col_tiles = L.max_col_tiles;
+    a.tile_rows = 256;
+    a.tile_cols = 256;
+    double eps = prm->eps;
+    a.negKD2 = (float)(-(double)geom->D * geom->D * 1.4426950408889634 / eps);
+    a.kc = (float)((double)prm->c_out * 1.4426950408889634 / eps);
+    a.frac = prm->unmatched_frac;
+    a.to_user = (float)(eps * 0.6931471805599453);
+    a.mode = prm->dust_mode ? 1 : 0;
+    a.warm = prm->warm_start ? 1 : 0;
+    *out = a;
+    int rt = std::max(1, std::min(h->sm_count * h->row_bps, L.max_row_tiles));
+    int ct = std::max(1, std::min(h->sm_count * h->col_bps, L.max_col_tiles));
+    lc->row_grid = rt;
+    lc->col_grid = ct;
+    lc->hrv_grid = rt;
+    lc->hcol_grid = ct;
+    return LAUE_OK;
+}
+
+extern "C" int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* obs,
+                                  const LaueModelSpots* model, const LaueOTParams* prm, float* f, float* g,
+                                  float* dust, int* assign, float* margin, float* marg_err, float* q,
+                                  void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = laue_check_geom(h, geom))) return rc;
+    if ((rc = laue_check_obs(h, obs))) return rc;
+    if ((rc = laue_check_model(h, model))) return rc;
+    if (!prm || !(prm->eps > 0.0f) || prm->n_iter < 0 || !(prm->c_out >= 0.0f) ||
+        !(prm->unmatched_frac >= 0.0) || prm->unmatched_frac > 1.0)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "OT params: eps > 0, n_iter >= 0, c_out >= 0, 0 <= frac <= 1");
+    if (obs->T != model->T) return laue_fail(h, LAUE_ERR_INVALID_ARG, "observed and model T differ");
+    if ((obs->n > 0 && !f) || (model->n > 0 && !g))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "f and g outputs are required");
+    if (prm->warm_start && !dust) return laue_fail(h, LAUE_ERR_INVALID_ARG, "warm start needs dust");
+    LaueProblemDims d{obs->T, obs->n, model->n, 0, 0};
+    Layout L;
+    if ((rc = laue_need_ws(h, d, &L))) return rc;
+    SkArgs a;
+    SkLaunch lc;
+    laue_fill_sk(h, geom, obs, model, prm, L, &a, &lc);
+    a.f = f;
+    a.g = g;
+    a.dust_out = dust;
+    a.assign = assign;
+    a.margin = margin;
+    a.marg_err = marg_err;
+    a.q = q;
+    bool rows = assign || margin || marg_err;
+    bool cols = q || marg_err;
+    return laue_cuda_check(h, sinkhorn_run(a, lc, prm->n_iter, rows, cols, (cudaStream_t)stream),
+                           "sinkhorn launch");
+}
+
+// ------------------------------------------------------------- not yet built
+
+extern "C" int laue_mstep(laue_handle* h, const LaueGeometry*, const LaueLattice*, const LaueObsSpots*,
+                          const LaueModelSpots*, const float*, const float*, const LaueMParams*, const float*,
+                          float*, float*, int, float*, void*) {
+    return laue_fail(h, LAUE_ERR_UNIMPLEMENTED, "laue_mstep is not built yet");
+}
+
+extern "C" int laue_objective_grad(laue_handle* h, const LaueGeometry*, const LaueLattice*, const LaueObsSpots*,
+                                   const LaueModelSpots*, const float*, const float*, float, const float*,
+                                   const float*, const float*, int, float*, float*, void*) {
+    return laue_fail(h, LAUE_ERR_UNIMPLEMENTED, "laue_objective_grad is not built yet");
+}
+
+extern "C" int laue_prototype_select(laue_handle* h, const LaueGeometry*, const LaueLattice*,
+                                     const LaueObsSpots*, const float*, const float*, const float*, int, float,
+                                     float, int, int*, float*, int*, void*) {
+    return laue_fail(h, LAUE_ERR_UNIMPLEMENTED, "laue_prototype_select is not built yet");
+}
+
+extern "C" int laue_index(laue_handle* h, const LaueGeometry*, const LaueLattice*, const LaueObsSpots*,
+                          const float*, const float*, const float*, int, const LaueIndexParams*, float*, float*,
+                          int, int*, int*, void*) {
+    return laue_fail(h, LAUE_ERR_UNIMPLEMENTED, "laue_index is not built yet");
+}

@@ -1,0 +1,25 @@
+// api_internal.h — handle and host helpers shared by the C-ABI sources.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/laueot.h"
+#include "common.cuh"
+#include "kernels.h"
+
+struct laue_handle {
+    int device;
+    int sm_count;
+    int row_bps, col_bps;  // resident CTAs per SM of the pair passes
+    void* ws;
+    size_t ws_bytes;
+    char err[512];
+};
+
+int laue_fail(laue_handle* h, int code, const char* fmt, ...);
+int laue_cuda_check(laue_handle* h, cudaError_t e, const char* what);
+laue::GeomDev laue_geom_dev(const LaueGeometry& g);
+int laue_check_geom(laue_handle* h, const LaueGeometry* g);
+int laue_check_obs(laue_handle* h, const LaueObsSpots* o);
+int laue_check_model(laue_handle* h, const LaueModelSpots* m);
+int laue_need_ws(laue_handle* h, const LaueProblemDims& d, laue::Layout* L);

@@ -1,0 +1,201 @@
+// common.cuh — device helpers and the workspace layout shared by the
+// LaueOT kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/laueot.h"
+
+namespace laue {
+
+// ---------------------------------------------------------------------------
+// status word / control block at the start of the workspace
+// ---------------------------------------------------------------------------
+enum CtrlSlot {
+    CTRL_STATUS = 0,      // first device-side error code (0 = none)
+    CTRL_ROW_NEXT = 1,    // tile queue head of the row pass
+    CTRL_ROW_DONE = 2,    // finished-CTA ticket of the row pass
+    CTRL_COL_NEXT = 3,
+    CTRL_COL_DONE = 4,
+    CTRL_N_ROW_TILES = 5, // tiles built by the scheduler
+    CTRL_N_COL_TILES = 6,
+    CTRL_FWD_TOTAL = 7,   // visible spots found by the forward pass
+    CTRL_HRV_NEXT = 8,    // harvest passes
+    CTRL_HRV_DONE = 9,
+    CTRL_HCOL_NEXT = 10,
+    CTRL_HCOL_DONE = 11,
+    CTRL_GEN_NEXT = 12,   // generic queue / ticket pair for other passes
+    CTRL_GEN_DONE = 13,
+    CTRL_SLOTS = 64
+};
+
+constexpr size_t kCtrlBytes = 4096;  // status + counters + small scalars
+
+// ---------------------------------------------------------------------------
+// workspace layout (host computes, device receives pointers)
+// ---------------------------------------------------------------------------
+struct Layout {
+    size_t ctrl;
+    size_t row_tiles, col_tiles;  // int4 {t, start, count, pad}
+    size_t row_part, col_part;    // float2 (max, sum) per tile, log2 domain
+    size_t dust;                  // float: F0, F0n, G0, log2U, log2O (T each), errors
+    size_t ang;                   // int4 per angle: tile ranges of the passes
+    size_t obsP;                  // float4 (p, F) per observed spot
+    size_t modC;                  // float4 (c, G) per model spot
+    size_t fwd_blocks;            // int per forward block (count, then offset)
+    size_t jsum;                  // float per model spot x 12 (M-step sums)
+    size_t gsum;                  // float per grain x 16
+    size_t gidx;                  // int: grain CSR offsets + spot lists
+    size_t total;
+    int max_row_tiles, max_col_tiles, max_fwd_blocks;
+};
+
+constexpr int kMinTile = 64;      // smallest tile any launch shape uses
+constexpr int kFwdBlock = 256;    // rays per forward block
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+inline Layout make_layout(const LaueProblemDims& d) {
+    Layout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    int T = d.T > 0 ? d.T : 1;
+    L.max_row_tiles = T + (d.n_obs + kMinTile - 1) / kMinTile + 1;
+    L.max_col_tiles = T + (d.n_model + kMinTile - 1) / kMinTile + 1;
+    long long rays = (long long)T * (d.n_grains > 0 ? d.n_grains : 1) * (d.n_planes > 0 ? d.n_planes : 1);
+    L.max_fwd_blocks = (int)((rays + kFwdBlock - 1) / kFwdBlock) + 1;
+    L.ctrl = take(kCtrlBytes);
+    L.row_tiles = take(sizeof(int4) * (size_t)L.max_row_tiles);
+    L.col_tiles = take(sizeof(int4) * (size_t)L.max_col_tiles);
+    L.row_part = take(sizeof(float2) * (size_t)L.max_row_tiles);
+    L.col_part = take(sizeof(float2) * (size_t)L.max_col_tiles);
+    L.dust = take(sizeof(float) * (size_t)(6 * T + 16));
+    L.ang = take(sizeof(int4) * (size_t)T);
+    L.obsP = take(sizeof(float4) * (size_t)(d.n_obs + 1));
+    L.modC = take(sizeof(float4) * (size_t)(d.n_model + 1));
+    L.fwd_blocks = take(sizeof(int) * (size_t)(2 * L.max_fwd_blocks + 2));
+    L.jsum = take(sizeof(float) * 12 * (size_t)(d.n_model + 1));
+    L.gsum = take(sizeof(float) * 16 * (size_t)(d.n_grains + 1));
+    L.gidx = take(sizeof(int) * (size_t)(d.n_grains + 2 + d.n_model + 1));
+    L.total = off;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kNegHuge = -3.0e38f;  // finite stand-in for log(0)
+
+// Hardware approximations (PTX ISA: ex2.approx, lg2.approx, rsqrt.approx).
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsq(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Record the first device-side error in the status word.
+__device__ __forceinline__ void set_status(int* ctrl, int code) {
+    atomicCAS(ctrl + CTRL_STATUS, 0, code);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// mbarrier + bulk async copy (TMA, non-tensor form).  Addresses and sizes of
+// cp.async.bulk must be multiples of 16 bytes: every staged array here is
+// float4 rows starting at 256-byte aligned bases.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after `limit` polls (each poll
+// may suspend the thread for a hardware-defined time) and returns false.
+constexpr uint32_t kWaitLimit = 1u << 24;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Log-sum-exp (base 2) accumulator: value = m + log2(s).
+struct Lse2 {
+    float m, s;
+    __device__ __forceinline__ void init(float v) {
+        m = v;
+        s = 1.0f;
+    }
+    __device__ __forceinline__ void merge(float m2, float s2) {
+        if (s2 == 0.0f) return;
+        if (m2 > m) {
+            s = s * ex2(m - m2) + s2;
+            m = m2;
+        } else {
+            s += s2 * ex2(m2 - m);
+        }
+    }
+    __device__ __forceinline__ float value() const { return m + lg2(s); }
+};
+
+__device__ __forceinline__ void warp_lse_reduce(float& m, float& s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float m2 = __shfl_xor_sync(0xffffffffu, m, o);
+        float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        float mm = fmaxf(m, m2);
+        s = (s == 0.0f ? 0.0f : s * ex2(m - mm)) + (s2 == 0.0f ? 0.0f : s2 * ex2(m2 - mm));
+        m = mm;
+    }
+}
+
+#endif  // __CUDACC__
+
+}  // namespace laue

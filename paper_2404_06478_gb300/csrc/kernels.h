@@ -1,0 +1,103 @@
+// kernels.h — argument blocks and launchers of the LaueOT kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace laue {
+
+struct GeomDev {
+    float e[3];
+    float lam_min, lam_max, D;
+    int n_det;
+    float ctr[4][3], nrm[4][3], half[4];
+};
+
+// ----------------------------------------------------------------- forward
+struct FwdArgs {
+    GeomDev G;
+    const float* R;
+    const float* x;
+    const float* omega;
+    const float4* w_d0;
+    const int* nharm;
+    int N, M, T;
+    long long n_rays;
+    int n_blocks;
+    int capacity;
+    int* blocks;  // 2 * n_blocks: counts then exclusive offsets
+    int* ctrl;
+    int* J_off;
+    int* grain;
+    int* plane;
+    int* angle;
+    float4* ray;
+    float4* center;
+    float4* spot;
+};
+
+struct RefreshArgs {
+    GeomDev G;
+    const float* R;
+    const float* x;
+    const float* omega;
+    const float4* w_d0;
+    const int* nharm;
+    int n;
+    const int* grain;
+    const int* plane;
+    const int* angle;
+    float4* ray;
+    float4* center;
+    float4* spot;
+};
+
+cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_refresh(const RefreshArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------- Sinkhorn
+// Potentials are kept internally in base-2 units scaled by the temperature:
+// F_i = f_i log2(e) / eps, G_j = g_j log2(e) / eps.
+struct SkArgs {
+    int T;
+    int n_obs, n_model;
+    const int* I_off;
+    const int* J_off;
+    const float4* obs_p;   // caller's observed spots (p, unused)
+    const float4* mod_c;   // caller's centres (c, unused)
+    const float4* modR;    // caller's rays (r, lambda)
+    float4* obsP;          // workspace: (p, F)
+    float4* modC;          // workspace: (c, G)
+    int4* row_tiles;
+    int4* col_tiles;
+    int4* ang_tiles;       // per angle: {first row tile, #row tiles, first col tile, #col tiles}
+    float2* row_part;
+    float2* col_part;
+    float* dust;           // F0, F0n, G0, log2U, log2O (T each), errors
+    int* ctrl;
+    int max_row_tiles, max_col_tiles;
+    int tile_rows, tile_cols;
+    float negKD2;          // -D^2 log2(e) / eps
+    float kc;              // c_out log2(e) / eps
+    double frac;           // unmatched-model fraction
+    float to_user;         // eps ln 2: internal -> mm^2
+    int mode;              // 0 global dustbins, 1 per angle
+    int warm;
+    // user buffers
+    float* f;
+    float* g;
+    float* dust_out;
+    int* assign;
+    float* margin;
+    float* marg_err;
+    float* q;
+};
+
+struct SkLaunch {
+    int row_grid, col_grid, hrv_grid, hcol_grid;
+};
+
+cudaError_t sinkhorn_run(const SkArgs& a, const SkLaunch& l, int n_iter, bool want_rows, bool want_cols,
+                         cudaStream_t s);
+int sinkhorn_occupancy(int* row_blocks_per_sm, int* col_blocks_per_sm);
+
+}  // namespace laue

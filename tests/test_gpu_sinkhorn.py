@@ -1,0 +1,167 @@
+"""Parity of laue_cost_sinkhorn (fused cost + log-domain Sinkhorn, CUDA) with
+the FP64 oracle on the same float32 inputs.
+
+Tolerances (derived from the FP32 arithmetic of the kernels): potentials
+within 1e-4 * (|f| + eps) (FP32 log-sum-exp over up to a few thousand terms
+with hardware ex2/lg2/rsqrt approximations, relative error ~1e-6 per
+iteration, accumulated over <= 200 iterations along the shift-neutral
+direction); hard assignments bit-exact wherever the oracle's top-two margin
+exceeds 1e-3; margins within 1e-4."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+import synthgen as sg
+from _cases import GEOM, make_case, to_device
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2404_06478_gb300 import api, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    return dict(torch=torch, api=api, dev=dev, h=api.Handle(dev))
+
+
+def _run_both(env, case, n_iter, mode=0, eps=None, frac=0.4, cols=False):
+    api = env["api"]
+    eps = case.cfg.eps if eps is None else eps
+    ob, ms = to_device(case, env["dev"])
+    out = api.cost_sinkhorn(env["h"], GEOM, ob, ms, eps, case.c_out, n_iter, dust_mode=mode,
+                            unmatched_frac=frac, harvest=True, col_harvest=cols)
+    env["torch"].cuda.synchronize()
+    assert env["h"].device_status() == 0
+    gpu = {k: v.cpu().numpy().astype(np.float64) if v.dtype.is_floating_point else v.cpu().numpy()
+           for k, v in out.items()}
+    fw, obs = case.fw, case.obs
+    f, g, fd, gd, _ = oracle.sinkhorn(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3],
+                                      eps, case.c_out, mode, frac, n_iter)
+    h = oracle.harvest(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3], eps,
+                       case.c_out, mode, frac, f, g, fd, gd)
+    ref = dict(f=f, g=g, dust=np.concatenate([fd, gd]), **h)
+    return gpu, ref, eps
+
+
+def _check(gpu, ref, eps):
+    for k in ("f", "g", "dust"):
+        err = np.abs(gpu[k] - ref[k])
+        lim = TOL * (np.abs(ref[k]) + eps)
+        assert np.all(err <= lim), (k, float((err / lim).max()))
+    sure = ref["margin"] > 1e-3
+    assert sure.mean() > 0.5
+    np.testing.assert_array_equal(gpu["assign"][sure], ref["assign"][sure])
+    np.testing.assert_allclose(gpu["margin"], ref["margin"], atol=1e-4)
+    assert abs(gpu["marg_err"][0] - ref["row_err"]) < 1e-4
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sinkhorn_tiny(env, mode):
+    case = make_case(sg.CONFIGS["tiny"])
+    gpu, ref, eps = _run_both(env, case, 100, mode=mode)
+    _check(gpu, ref, eps)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_sinkhorn_multi_tile_ragged(env, mode):
+    """60 grains, 8 angles, |hkl| <= 6, 30% outliers: several row and column
+    tiles per angle block with ragged tails, several staged chunks each."""
+    case = make_case(sg.CONFIGS["medium"], seed=11, n_grains=60, T=8)
+    nI = np.diff(case.obs.I_off)
+    nJ = np.diff(case.fw["J_off"])
+    assert nI.max() > 256 and nJ.max() > 256 and (nI % 256).min() > 0
+    gpu, ref, eps = _run_both(env, case, 60, mode=mode, cols=True)
+    _check(gpu, ref, eps)
+    np.testing.assert_allclose(gpu["q"], ref["q"], atol=1e-4)
+
+
+@pytest.mark.parametrize("eps", [0.25, 4.0, 100.0])
+def test_sinkhorn_temperatures(env, eps):
+    case = make_case(sg.CONFIGS["tiny"], seed=5)
+    gpu, ref, _ = _run_both(env, case, 40, eps=eps)
+    for k in ("f", "g", "dust"):
+        err = np.abs(gpu[k] - ref[k])
+        assert np.all(err <= TOL * (np.abs(ref[k]) + eps)), k
+
+
+def test_sinkhorn_empty_blocks(env):
+    """Angle blocks with no observed spots and blocks with no model spots."""
+    case = make_case(sg.CONFIGS["tiny"], seed=7)
+    obs, fw = case.obs, case.fw
+    # drop observed spots of angle 2 and model spots of angle 5
+    keep_i = obs.t != 2
+    obs.p, obs.t, obs.det, obs.truth = obs.p[keep_i], obs.t[keep_i], obs.det[keep_i], obs.truth[keep_i]
+    obs.I_off = np.r_[0, np.cumsum(np.bincount(obs.t, minlength=case.cfg.T))]
+    keep_j = fw["t"] != 5
+    for k in ("grain", "plane", "ray", "spot", "center", "det", "t"):
+        fw[k] = fw[k][keep_j]
+    fw["J_off"] = np.r_[0, np.cumsum(np.bincount(fw["t"], minlength=case.cfg.T))]
+    for mode in (0, 1):
+        gpu, ref, eps = _run_both(env, case, 30, mode=mode)
+        _check(gpu, ref, eps)
+
+
+def test_sinkhorn_no_unmatched_mass(env):
+    """unmatched fraction 0 (U from the balance rule only)."""
+    case = make_case(sg.CONFIGS["tiny"], seed=8)
+    gpu, ref, eps = _run_both(env, case, 30, frac=0.0)
+    _check(gpu, ref, eps)
+
+
+def test_sinkhorn_warm_start_continues(env):
+    api, torch = env["api"], env["torch"]
+    case = make_case(sg.CONFIGS["tiny"], seed=9)
+    ob, ms = to_device(case, env["dev"])
+    a = api.cost_sinkhorn(env["h"], GEOM, ob, ms, 1.0, case.c_out, 25)
+    b = api.cost_sinkhorn(env["h"], GEOM, ob, ms, 1.0, case.c_out, 15, init=(a["f"], a["g"], a["dust"]))
+    fw, obs = case.fw, case.obs
+    f, g, fd, gd, _ = oracle.sinkhorn(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3],
+                                      1.0, case.c_out, 0, 0.4, 40)
+    np.testing.assert_allclose(b["f"].cpu().numpy(), f, atol=TOL * (np.abs(f).max() + 1))
+    np.testing.assert_allclose(b["g"].cpu().numpy(), g, atol=TOL * (np.abs(g).max() + 1))
+
+
+def test_sinkhorn_full_size_rows_and_marginals(env):
+    """1000 grains, 90 angles, 70% uneven outliers.  One iteration from zero:
+    sampled rows equal the oracle's row update of their own angle block.
+    200 iterations: row marginals converge (a property at any size)."""
+    api, torch, dev = env["api"], env["torch"], env["dev"]
+    cfg = sg.CONFIGS["batched"]
+    rng = np.random.default_rng(0)
+    R, x = sg.random_grains(cfg, rng)
+    om = sg.omegas(cfg)
+    h = env["h"]
+    lat = api.Lattice.cubic(cfg.a, cfg.hmax, cfg.centering, device=dev)
+    ms = api.forward(h, GEOM, lat, torch.tensor(R, device=dev), torch.tensor(x, device=dev),
+                     torch.tensor(om, device=dev))
+    J_off = ms.J_off.cpu().numpy()
+    t_j = ms.angle[:ms.n].cpu().numpy()
+    det = ms.spot[:ms.n, 3].cpu().numpy().astype(int)
+    spot = ms.spot[:ms.n, :3].cpu().numpy().astype(np.float64)
+    obs = sg.observe(GEOM, cfg, t_j, det, spot, rng)
+    ob = api.ObsSpots.from_numpy(obs.p, obs.I_off, device=dev)
+    msn = ms.truncated()
+    c_out = api.c_out_for(cfg.sigma_mm, GEOM.D)
+    one = api.cost_sinkhorn(h, GEOM, ob, msn, 1.0, c_out, 1, harvest=False)
+    f1 = one["f"].cpu().numpy()
+    p32 = ob.p[:, :3].cpu().numpy().astype(np.float64)
+    c32 = msn.center[:, :3].cpu().numpy().astype(np.float64)
+    r32 = msn.ray[:, :3].cpu().numpy().astype(np.float64)
+    for t in rng.choice(cfg.T, 4, replace=False):
+        i0, i1 = obs.I_off[t], obs.I_off[t + 1]
+        j0, j1 = J_off[t], J_off[t + 1]
+        sel = rng.choice(np.arange(i0, i1), 16, replace=False)
+        fo, *_ = oracle.sinkhorn(GEOM.D, p32[sel], [0, len(sel)], [0, j1 - j0], c32[j0:j1], r32[j0:j1], 1.0,
+                                 c_out, 0, 0.4, 1)
+        np.testing.assert_allclose(f1[sel], fo, atol=TOL * (np.abs(fo).max() + 1.0))
+    full = api.cost_sinkhorn(h, GEOM, ob, msn, 1.0, c_out, 200, harvest=True, col_harvest=True)
+    torch.cuda.synchronize()
+    assert h.device_status() == 0
+    me = full["marg_err"].cpu().numpy()
+    assert me[0] < 1e-2 and me[1] < 1e-4
