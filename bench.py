@@ -88,8 +88,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(dev, seed, api, sg, torch):
+def build_workload(dev, seed, api, sg, torch, grains=None, angles=None):
+    import dataclasses
     cfg = sg.CONFIGS["batched"]
+    if grains or angles:
+        cfg = dataclasses.replace(cfg, n_grains=grains or cfg.n_grains, T=angles or cfg.T)
     geom = sg.Geometry()
     rng = np.random.default_rng(seed)
     R, x = sg.random_grains(cfg, rng)
@@ -191,6 +194,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grains", type=int, default=None, help="smaller case for profiling (not a bench line)")
+    ap.add_argument("--angles", type=int, default=None, help="smaller case for profiling (not a bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -207,7 +212,7 @@ def main():
         dist.barrier()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    W = build_workload(dev, rank, api, sg, torch)
+    W = build_workload(dev, rank, api, sg, torch, args.grains, args.angles)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     R = W["R0"].clone()
@@ -283,23 +288,30 @@ def main():
     d2h = a_host.numel() * 4 + Ro_host.numel() * 4 + xo_host.numel() * 4
 
     launches_per_step = 1 + 3 + 2 * cfg.n_sinkhorn + 3 + (1 if hasattr(api, "mstep") else 0)
-    # roofline: MUFU bound, 2 MUFU (rsqrt, ex2) per pair; 16 MUFU results / clk / SM
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    clk_mhz = 2070.0
-    peak = sm_count * 16 * clk_mhz * 1e6 / 2
+    # roofline: the pair evaluation needs 15 FP32 lane-ops (3 sub, 3 for |d|^2,
+    # 3 for d*s - r, 3 for |e|^2, 1 fold, 1 shift, 1 accumulate), 1 MUFU rsqrt and
+    # 1 MUFU ex2; the peak is the slowest of the three pipes, each measured on
+    # this device by laue_alu_peaks
+    pk_ = W["h"].alu_peaks()
+    fp32 = max(pk_["ffma"], pk_["ffma2"])
+    peak = min(fp32 / 15.0, pk_["ex2"], pk_["rsqrt"])
+    bound_by = min((fp32 / 15.0, "fp32"), (pk_["ex2"], "mufu_ex2"), (pk_["rsqrt"], "mufu_rsqrt"))[1]
     achieved = W["pairs_half"] / (per_launch_ms / 1e3)
     line = dict(
         metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
         data="synthetic",
-        config=dict(workload="1000 grains, |hkl|<=6 bcc, 90 rotations over 360 deg, 0.5 mm noise, "
-                             "70% uneven Poisson outliers, eps=1 mm^2, 200 Sinkhorn iterations per EM step",
+        config=dict(workload="%d grains, |hkl|<=6 bcc, %d rotations over 360 deg, 0.5 mm noise, "
+                             "70%% uneven Poisson outliers, eps=1 mm^2, 200 Sinkhorn iterations per EM step"
+                             % (cfg.n_grains, cfg.T),
                     grains=cfg.n_grains, angles=cfg.T, observed=W["nI"], model_spots=W["nJ"],
                     pairs_per_half_iteration=W["pairs_half"], step="one EM iteration",
                     l2="256 MB buffer written between timed steps", parallelism="replicas" if world > 1 else "1 GPU"),
         roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="pairs/s", frac=achieved / peak,
                       traffic=None, kernel="sk_row_kernel+sk_col_kernel (per launch)",
-                      peak_basis="MUFU: %d SMs x 16/clk x %.0f MHz / 2 MUFU per pair" % (sm_count, clk_mhz)),
+                      peak_basis="min(FP32 lane-ops/s / 15, MUFU ex2/s, MUFU rsqrt/s), measured by "
+                                 "laue_alu_peaks; binding pipe: %s" % bound_by,
+                      pipes={k: v for k, v in pk_.items()}),
         clocks=clk,
         e2e=dict(value=pairs_step / (e2e_ms / 1e3), unit=UNIT, h2d_bytes_per_step=int(h2d),
                  d2h_bytes_per_step=int(d2h)),

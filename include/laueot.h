@@ -167,6 +167,13 @@ int laue_set_workspace(laue_handle* h, void* dev_ptr, size_t bytes, void* stream
  * LAUE_ERR_* code recorded by a kernel) in *status_host and clears it. */
 int laue_device_status(laue_handle* h, void* stream, int* status_host);
 
+/* Measurement helper (no counterpart in the paper): throughput of the
+ * arithmetic pipes the pair passes use, measured on this device by
+ * microbenchmark kernels.  out_host[0..5] = FP32 FMA ops/s, packed f32x2 FMA
+ * ops/s (2 per instruction), MUFU ex2/s, MUFU rsqrt/s, MUFU lg2/s, SM count.
+ * Synchronises `stream`.  Needs the workspace. */
+int laue_alu_peaks(laue_handle* h, double* out_host, void* stream);
+
 /* ---- host helper ------------------------------------------------------- */
 
 /* Plausible plane set of a cubic lattice (paper Section "Crystallographic

@@ -76,6 +76,7 @@ SIGNATURES = {
     "laue_set_workspace": [_vp, _vp, ctypes.c_size_t, _vp],
     "laue_device_status": [_vp, _vp, _pi],
     "laue_reflections": [_d, _i, _i, _i, _vp, _vp, _vp, _pi],
+    "laue_alu_peaks": [_vp, _vp, _vp],
     "laue_forward": [_vp, _P(LaueGeometry), _P(LaueLattice), _vp, _vp, _i, _vp, _i, _P(LaueModelSpots), _pi, _vp],
     "laue_refresh": [_vp, _P(LaueGeometry), _P(LaueLattice), _vp, _vp, _vp, _P(LaueModelSpots), _vp],
     "laue_cost_sinkhorn": [_vp, _P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams),

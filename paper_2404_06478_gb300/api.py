@@ -207,6 +207,13 @@ class Handle:
                        "set_workspace")
         return self.ws
 
+    def alu_peaks(self, stream=None) -> dict:
+        """Measured pipe throughputs (ops/s) of this device."""
+        self.reserve(1, stream=stream)
+        out = (ctypes.c_double * 6)()
+        self.check(self.L.laue_alu_peaks(self.h, out, _stream(stream)), "alu_peaks")
+        return dict(ffma=out[0], ffma2=out[1], ex2=out[2], rsqrt=out[3], lg2=out[4], sm_count=int(out[5]))
+
     def device_status(self, stream=None) -> int:
         v = ctypes.c_int(0)
         self.check(self.L.laue_device_status(self.h, _stream(stream), ctypes.byref(v)), "device_status")

@@ -340,9 +340,15 @@ int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* o
     a.J_off = model->J_off;
     a.obs_p = (const float4*)obs->p;
     a.mod_c = (const float4*)model->center;
-    a.modR = (const float4*)model->ray;
-    a.obsP = (float4*)(ws + L.obsP);
-    a.modC = (float4*)(ws + L.modC);
+    a.mod_r = (const float4*)model->ray;
+    a.obsX = (float4*)(ws + L.obsX);
+    a.obsY = (float4*)(ws + L.obsY);
+    a.modX = (float4*)(ws + L.modX);
+    a.modY = (float4*)(ws + L.modY);
+    a.modZ = (float4*)(ws + L.modZ);
+    a.modW = (float4*)(ws + L.modW);
+    a.I2_off = (int*)(ws + L.pairoff);
+    a.J2_off = a.I2_off + (obs->T + 1);
     a.row_tiles = (int4*)(ws + L.row_tiles);
     a.col_tiles = (int4*)(ws + L.col_tiles);
     a.ang_tiles = (int4*)(ws + L.ang);
@@ -352,7 +358,7 @@ int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* o
     a.ctrl = (int*)(ws + L.ctrl);
     a.max_row_tiles = L.max_row_tiles;
     a.max_col_tiles = L.max_col_tiles;
-    a.tile_rows = 256;
+    a.tile_rows = 256;  // row pairs per tile (one per thread)
     a.tile_cols = 256;
     double eps = prm->eps;
     a.negKD2 = (float)(-(double)geom->D * geom->D * 1.4426950408889634 / eps);

@@ -41,17 +41,19 @@ struct Layout {
     size_t row_part, col_part;    // float2 (max, sum) per tile, log2 domain
     size_t dust;                  // float: F0, F0n, G0, log2U, log2O (T each), errors
     size_t ang;                   // int4 per angle: tile ranges of the passes
-    size_t obsP;                  // float4 (p, F) per observed spot
-    size_t modC;                  // float4 (c, G) per model spot
+    size_t obsX, obsY;            // pair-interleaved observed spots (see sinkhorn.cu)
+    size_t modX, modY, modZ, modW;// pair-interleaved model spots
+    size_t pairoff;               // int: I2_off[T+1], J2_off[T+1] (pair offsets)
     size_t fwd_blocks;            // int per forward block (count, then offset)
     size_t jsum;                  // float per model spot x 12 (M-step sums)
     size_t gsum;                  // float per grain x 16
     size_t gidx;                  // int: grain CSR offsets + spot lists
     size_t total;
     int max_row_tiles, max_col_tiles, max_fwd_blocks;
+    int max_obs_pairs, max_mod_pairs;
 };
 
-constexpr int kMinTile = 64;      // smallest tile any launch shape uses
+constexpr int kMinTile = 64;      // smallest tile (in spot pairs) any launch shape uses
 constexpr int kFwdBlock = 256;    // rays per forward block
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -65,8 +67,8 @@ inline Layout make_layout(const LaueProblemDims& d) {
         return o;
     };
     int T = d.T > 0 ? d.T : 1;
-    L.max_row_tiles = T + (d.n_obs + kMinTile - 1) / kMinTile + 1;
-    L.max_col_tiles = T + (d.n_model + kMinTile - 1) / kMinTile + 1;
+    L.max_row_tiles = T + (d.n_obs / 2 + kMinTile - 1) / kMinTile + 1;
+    L.max_col_tiles = T + (d.n_model / 2 + kMinTile - 1) / kMinTile + 1;
     long long rays = (long long)T * (d.n_grains > 0 ? d.n_grains : 1) * (d.n_planes > 0 ? d.n_planes : 1);
     L.max_fwd_blocks = (int)((rays + kFwdBlock - 1) / kFwdBlock) + 1;
     L.ctrl = take(kCtrlBytes);
@@ -76,8 +78,16 @@ inline Layout make_layout(const LaueProblemDims& d) {
     L.col_part = take(sizeof(float2) * (size_t)L.max_col_tiles);
     L.dust = take(sizeof(float) * (size_t)(6 * T + 16));
     L.ang = take(sizeof(int4) * (size_t)T);
-    L.obsP = take(sizeof(float4) * (size_t)(d.n_obs + 1));
-    L.modC = take(sizeof(float4) * (size_t)(d.n_model + 1));
+    size_t ip = (size_t)(d.n_obs + T + 2) / 2 + 1, jp = (size_t)(d.n_model + T + 2) / 2 + 1;
+    L.max_obs_pairs = (int)ip;
+    L.max_mod_pairs = (int)jp;
+    L.obsX = take(sizeof(float4) * ip);
+    L.obsY = take(sizeof(float4) * ip);
+    L.modX = take(sizeof(float4) * jp);
+    L.modY = take(sizeof(float4) * jp);
+    L.modZ = take(sizeof(float4) * jp);
+    L.modW = take(sizeof(float4) * jp);
+    L.pairoff = take(sizeof(int) * (size_t)(2 * T + 4));
     L.fwd_blocks = take(sizeof(int) * (size_t)(2 * L.max_fwd_blocks + 2));
     L.jsum = take(sizeof(float) * 12 * (size_t)(d.n_model + 1));
     L.gsum = take(sizeof(float) * 16 * (size_t)(d.n_grains + 1));
@@ -194,6 +204,46 @@ __device__ __forceinline__ void warp_lse_reduce(float& m, float& s) {
         s = (s == 0.0f ? 0.0f : s * ex2(m - mm)) + (s2 == 0.0f ? 0.0f : s2 * ex2(m2 - mm));
         m = mm;
     }
+}
+
+// Packed pairs of floats for the sm_100+ f32x2 instructions (PTX fma/add/
+// mul .rn.f32x2): the low half is the first element.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ f2 dup(float a) { return pk(a, a); }
+__device__ __forceinline__ float lo(f2 v) {
+    float a;
+    asm("mov.b64 {%0, _}, %1;" : "=f"(a) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi(f2 v) {
+    float b;
+    asm("mov.b64 {_, %0}, %1;" : "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
 #endif  // __CUDACC__

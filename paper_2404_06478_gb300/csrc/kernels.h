@@ -64,9 +64,16 @@ struct SkArgs {
     const int* J_off;
     const float4* obs_p;   // caller's observed spots (p, unused)
     const float4* mod_c;   // caller's centres (c, unused)
-    const float4* modR;    // caller's rays (r, lambda)
-    float4* obsP;          // workspace: (p, F)
-    float4* modC;          // workspace: (c, G)
+    const float4* mod_r;   // caller's rays (r, lambda)
+    // workspace, pair-interleaved (angle blocks padded to even counts):
+    float4* obsX;          // {px_a, px_b, py_a, py_b}
+    float4* obsY;          // {pz_a, pz_b, F_a, F_b}
+    float4* modX;          // {-cx_a, -cx_b, -cy_a, -cy_b}
+    float4* modY;          // {-cz_a, -cz_b, G_a, G_b}
+    float4* modZ;          // {-rx_a, -rx_b, -ry_a, -ry_b}
+    float4* modW;          // {-rz_a, -rz_b, 0, 0}
+    int* I2_off;           // T+1 pair offsets of the observed blocks
+    int* J2_off;           // T+1 pair offsets of the model blocks
     int4* row_tiles;
     int4* col_tiles;
     int4* ang_tiles;       // per angle: {first row tile, #row tiles, first col tile, #col tiles}
@@ -98,6 +105,9 @@ struct SkLaunch {
 
 cudaError_t sinkhorn_run(const SkArgs& a, const SkLaunch& l, int n_iter, bool want_rows, bool want_cols,
                          cudaStream_t s);
+cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s);
+cudaError_t sinkhorn_iterate(const SkArgs& a, const SkLaunch& l, int n_iter, cudaStream_t s);
+cudaError_t sinkhorn_finish(const SkArgs& a, const SkLaunch& l, bool want_rows, bool want_cols, cudaStream_t s);
 int sinkhorn_occupancy(int* row_blocks_per_sm, int* col_blocks_per_sm);
 
 }  // namespace laue

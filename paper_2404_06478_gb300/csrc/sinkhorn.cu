@@ -13,13 +13,23 @@
 // with e2_ij = |rhat_ij - r_j|^2 and kc = c_out log2(e)/eps.  The cost matrix
 // is never stored: every pass recomputes e2 from the spot coordinates.
 //
-// Each pass is one persistent launch over all angle blocks: CTAs pull tiles
-// (angle t, first row, count) from a queue the scheduler kernel built on the
-// device in longest-block-first order.  A tile keeps one row (column) per
-// thread in registers and streams the other side of its angle block through
-// shared memory in chunks loaded by the bulk-copy engine (cp.async.bulk) into
-// a two-stage mbarrier pipeline.  The last CTA to finish a pass combines the
-// per-tile partial log-sum-exps into the dustbin potentials:
+// Layout.  The workspace holds the spots as pairs: each angle block is padded
+// to an even count and element pairs (a, b) are interleaved into float4 rows
+// such as {x_a, x_b, y_a, y_b}, so one 16-byte shared-memory load yields two
+// packed operands for the f32x2 FMA/ADD/MUL instructions.  Model centres and
+// rays are stored negated (d = p + (-c), e = d/|d| + (-r)).  Padding entries
+// carry a potential of -3e38, which makes their plan entries exactly 0.
+//
+// Passes.  Each pass is one persistent launch over all angle blocks: CTAs pull
+// tiles (angle t, first pair, count) from a queue the scheduler kernel built
+// on the device in longest-block-first order.  A thread keeps one PAIR of rows
+// (row pass) or columns (column pass) in registers and streams the other side
+// of its angle block, as pairs, through shared memory in chunks loaded by the
+// bulk-copy engine (cp.async.bulk) into a two-stage mbarrier pipeline: every
+// staged pair feeds 4 pair evaluations.  The log-sum-exps are online, in
+// groups of 4 staged pairs (8 values) per max/rescale step.  The last CTA to
+// finish a pass combines the per-tile partial log-sum-exps into the dustbin
+// potentials:
 //   end of a row pass:    F_0 <- F_0(next), then G_0 from the new F and F_0
 //   end of a column pass: F_0(next) from the new G and G_0
 // which reproduces the sequential order of the algorithm exactly.
@@ -28,9 +38,10 @@
 
 namespace laue {
 
-constexpr int kTPB = 256;    // threads per CTA = rows (columns) per tile
-constexpr int kChunk = 256;  // spots staged per chunk
-constexpr int kGroup = 8;    // pairs per max-then-sum group of the online LSE
+constexpr int kTPB = 256;     // threads per CTA = row (column) pairs per tile
+constexpr int kChunk = 128;   // staged pairs per chunk (256 spots)
+constexpr int kGroup = 4;     // staged pairs per max-then-sum group
+constexpr float kPadFar = 1.0e6f;
 
 struct DustPtrs {
     float *F0, *F0n, *G0, *log2U, *log2O, *err;
@@ -47,20 +58,68 @@ __device__ __forceinline__ DustPtrs dust_ptrs(float* base, int T) {
     return d;
 }
 
-// |rhat - r|^2 with rhat = (p - c)/|p - c|: no cancellation for close rays.
-__device__ __forceinline__ float ray_e2(float px, float py, float pz, float cx, float cy, float cz,
-                                        float rx, float ry, float rz) {
-    float dx = px - cx, dy = py - cy, dz = pz - cz;
-    float q = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float s = rsq(q);
-    float ex = fmaf(dx, s, -rx), ey = fmaf(dy, s, -ry), ez = fmaf(dz, s, -rz);
-    return fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+// Packed pair value base + K |(p - c)/|p - c| - r|^2 for two pairs at once;
+// nc = -c, nr = -r.  13 packed instructions and 2 MUFU rsqrt.
+__device__ __forceinline__ f2 pair_v2(f2 px, f2 py, f2 pz, f2 ncx, f2 ncy, f2 ncz, f2 nrx, f2 nry, f2 nrz,
+                                      f2 K2, f2 base) {
+    f2 dx = add2(px, ncx), dy = add2(py, ncy), dz = add2(pz, ncz);
+    f2 q = mul2(dx, dx);
+    q = fma2(dy, dy, q);
+    q = fma2(dz, dz, q);
+    f2 s = pk(rsq(lo(q)), rsq(hi(q)));
+    f2 ex = fma2(dx, s, nrx), ey = fma2(dy, s, nry), ez = fma2(dz, s, nrz);
+    f2 e2 = mul2(ex, ex);
+    e2 = fma2(ey, ey, e2);
+    e2 = fma2(ez, ez, e2);
+    return fma2(e2, K2, base);
 }
 
+// Online base-2 log-sum-exp state of one row: running max m and two packed
+// partial sums S (relative to m).
+struct RowLse {
+    float m;
+    f2 S;
+    f2 nm;  // {-m, -m}
+    __device__ __forceinline__ void init(float v) {
+        m = v;
+        S = pk(1.0f, 0.0f);
+        nm = dup(-v);
+    }
+    // fold 8 values (4 packed) in: one max / rescale, 8 MUFU ex2
+    __device__ __forceinline__ void add4(const f2 (&v)[kGroup]) {
+        float c1 = max3(lo(v[0]), hi(v[0]), lo(v[1]));
+        float c2 = max3(hi(v[1]), lo(v[2]), hi(v[2]));
+        float cm = max3(c1, c2, fmaxf(lo(v[3]), hi(v[3])));
+        if (cm > m) {
+            float sc = ex2(m - cm);
+            S = mul2(S, dup(sc));
+            m = cm;
+            nm = dup(-cm);
+        }
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g) {
+            f2 t = add2(v[g], nm);
+            S = add2(S, pk(ex2(lo(t)), ex2(hi(t))));
+        }
+    }
+    __device__ __forceinline__ void add1(f2 v) {
+        float cm = fmaxf(lo(v), hi(v));
+        if (cm > m) {
+            float sc = ex2(m - cm);
+            S = mul2(S, dup(sc));
+            m = cm;
+            nm = dup(-cm);
+        }
+        f2 t = add2(v, nm);
+        S = add2(S, pk(ex2(lo(t)), ex2(hi(t))));
+    }
+    __device__ __forceinline__ float value() const { return m + lg2(lo(S) + hi(S)); }
+};
+
 // ---------------------------------------------------------------- scheduler
-// One CTA.  Builds the row and column tile queues (angles by descending work,
-// tiles of one angle contiguous), per-angle tile ranges, the log2 masses of
-// the dustbins, and clears the queue counters.
+// One CTA.  Pair offsets of the padded blocks, row and column tile queues
+// (angles by descending work, tiles of one angle contiguous), per-angle tile
+// ranges, log2 masses of the dustbins; clears the queue counters.
 __global__ void __launch_bounds__(1024) sk_schedule_kernel(SkArgs a) {
     const int T = a.T;
     int* order_r = (int*)a.row_part;  // scratch until the passes run
@@ -80,19 +139,28 @@ __global__ void __launch_bounds__(1024) sk_schedule_kernel(SkArgs a) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        int ip = 0, jp = 0;
+        for (int t = 0; t < T; ++t) {
+            a.I2_off[t] = ip;
+            a.J2_off[t] = jp;
+            ip += (a.I_off[t + 1] - a.I_off[t] + 1) / 2;
+            jp += (a.J_off[t + 1] - a.J_off[t] + 1) / 2;
+        }
+        a.I2_off[T] = ip;
+        a.J2_off[T] = jp;
         int nr = 0, nc = 0;
         for (int k = 0; k < T; ++k) {
             int t = order_r[k];
-            int ni = a.I_off[t + 1] - a.I_off[t];
-            int cnt = (ni + a.tile_rows - 1) / a.tile_rows;
+            int np = (a.I_off[t + 1] - a.I_off[t] + 1) / 2;
+            int cnt = (np + a.tile_rows - 1) / a.tile_rows;
             a.ang_tiles[t].x = nr;
             a.ang_tiles[t].y = cnt;
             nr += cnt;
         }
         for (int k = 0; k < T; ++k) {
             int t = order_c[k];
-            int nj = a.J_off[t + 1] - a.J_off[t];
-            int cnt = (nj + a.tile_cols - 1) / a.tile_cols;
+            int np = (a.J_off[t + 1] - a.J_off[t] + 1) / 2;
+            int cnt = (np + a.tile_cols - 1) / a.tile_cols;
             a.ang_tiles[t].z = nc;
             a.ang_tiles[t].w = cnt;
             nc += cnt;
@@ -110,13 +178,13 @@ __global__ void __launch_bounds__(1024) sk_schedule_kernel(SkArgs a) {
     __syncthreads();
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
         int4 at = a.ang_tiles[t];
-        int i0 = a.I_off[t], ni = a.I_off[t + 1] - i0;
+        int i0 = a.I2_off[t], ni = a.I2_off[t + 1] - i0;
         for (int k = 0; k < at.y; ++k) {
             int idx = at.x + k;
             if (idx < a.max_row_tiles)
                 a.row_tiles[idx] = make_int4(t, i0 + k * a.tile_rows, min(a.tile_rows, ni - k * a.tile_rows), 0);
         }
-        int j0 = a.J_off[t], nj = a.J_off[t + 1] - j0;
+        int j0 = a.J2_off[t], nj = a.J2_off[t + 1] - j0;
         for (int k = 0; k < at.w; ++k) {
             int idx = at.z + k;
             if (idx < a.max_col_tiles)
@@ -140,19 +208,70 @@ __global__ void __launch_bounds__(1024) sk_schedule_kernel(SkArgs a) {
     }
 }
 
+// Angle block of element k of a list with offsets off[T+1] (binary search).
+__device__ __forceinline__ int block_of(const int* __restrict__ off, int T, int k) {
+    int lo_ = 0, hi_ = T;
+    while (hi_ - lo_ > 1) {
+        int mid = (lo_ + hi_) >> 1;
+        if (off[mid] <= k) lo_ = mid;
+        else hi_ = mid;
+    }
+    return lo_;
+}
+
 // ------------------------------------------------------------------- pack
-// Workspace copies (p, F) and (c, G); F, G from the caller's potentials on a
-// warm start, else 0.
+// Pair-interleaved workspace copies; F, G from the caller's potentials on a
+// warm start, else 0.  The thread of the last element of an odd block also
+// writes the padding slot.
 __global__ void sk_pack_kernel(SkArgs a) {
     const float s = 1.0f / a.to_user;  // mm^2 -> base-2 internal units
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < a.n_obs) {
+        int t = block_of(a.I_off, a.T, k);
+        int l = k - a.I_off[t];
+        int q = a.I2_off[t] + (l >> 1), lane = l & 1;
         float4 p = a.obs_p[k];
-        a.obsP[k] = make_float4(p.x, p.y, p.z, a.warm ? a.f[k] * s : 0.0f);
+        float* X = (float*)&a.obsX[q];
+        float* Y = (float*)&a.obsY[q];
+        X[lane] = p.x;
+        X[2 + lane] = p.y;
+        Y[lane] = p.z;
+        Y[2 + lane] = a.warm ? a.f[k] * s : 0.0f;
+        if (lane == 0 && k + 1 == a.I_off[t + 1]) {
+            X[1] = 0.0f;
+            X[3] = 0.0f;
+            Y[1] = kPadFar;
+            Y[3] = kNegHuge;
+        }
     }
     if (k < a.n_model) {
+        int t = block_of(a.J_off, a.T, k);
+        int l = k - a.J_off[t];
+        int q = a.J2_off[t] + (l >> 1), lane = l & 1;
         float4 c = a.mod_c[k];
-        a.modC[k] = make_float4(c.x, c.y, c.z, a.warm ? a.g[k] * s : 0.0f);
+        float4 r = a.mod_r[k];
+        float* X = (float*)&a.modX[q];
+        float* Y = (float*)&a.modY[q];
+        float* Z = (float*)&a.modZ[q];
+        float* W = (float*)&a.modW[q];
+        X[lane] = -c.x;
+        X[2 + lane] = -c.y;
+        Y[lane] = -c.z;
+        Y[2 + lane] = a.warm ? a.g[k] * s : 0.0f;
+        Z[lane] = -r.x;
+        Z[2 + lane] = -r.y;
+        W[lane] = -r.z;
+        W[2 + lane] = 0.0f;
+        if (lane == 0 && k + 1 == a.J_off[t + 1]) {
+            X[1] = 0.0f;
+            X[3] = 0.0f;
+            Y[1] = 0.0f;
+            Y[3] = kNegHuge;
+            Z[1] = 0.0f;
+            Z[3] = 0.0f;
+            W[1] = -1.0f;
+            W[3] = 0.0f;
+        }
     }
     if (k == 0) {
         DustPtrs D = dust_ptrs(a.dust, a.T);
@@ -170,15 +289,19 @@ __global__ void __launch_bounds__(1024) sk_init_dust_kernel(SkArgs a) {
     DustPtrs D = dust_ptrs(a.dust, a.T);
     int nd = a.mode ? a.T : 1;
     for (int d = 0; d < nd; ++d) {
-        int j0 = a.mode ? a.J_off[d] : 0, j1 = a.mode ? a.J_off[d + 1] : a.n_model;
+        int q0 = a.mode ? a.J2_off[d] : 0, q1 = a.mode ? a.J2_off[d + 1] : a.J2_off[a.T];
         float m = kNegHuge, s = 0.0f;
-        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-            float v = a.modC[j].w;
-            if (v > m) {
-                s = s * ex2(m - v) + 1.0f;
-                m = v;
-            } else {
-                s += ex2(v - m);
+        for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+            float4 y = a.modY[q];
+            for (int lane = 0; lane < 2; ++lane) {
+                float v = lane ? y.w : y.z;
+                if (v <= kNegHuge) continue;  // padding
+                if (v > m) {
+                    s = s * ex2(m - v) + 1.0f;
+                    m = v;
+                } else {
+                    s += ex2(v - m);
+                }
             }
         }
         warp_lse_reduce(m, s);
@@ -198,28 +321,30 @@ __global__ void __launch_bounds__(1024) sk_init_dust_kernel(SkArgs a) {
 }
 
 // ------------------------------------------------------ staged chunk pipeline
-struct Stage2 {
-    float4 a[2][kChunk];
-    float4 b[2][kChunk];
+struct Stage {
+    float4 s[4][2][kChunk];  // up to 4 arrays x 2 stages
     uint64_t bar[2];
     int tile;
     int last;
     float red_m[kTPB / 32], red_s[kTPB / 32];
 };
 
-// Thread 0 issues the bulk copies of chunk `ch` (one or two arrays) into the
+struct Srcs {
+    const float4* p[4];
+    int n;  // number of arrays (2 or 4)
+};
+
+// Thread 0 issues the bulk copies of chunk `ch` of every source array into
 // stage ch & 1.
-__device__ __forceinline__ void issue_chunk(Stage2& S, int ch, const float4* srcA, const float4* srcB,
-                                            int base, int n_total) {
+__device__ __forceinline__ void issue_chunk(Stage& S, int ch, const Srcs& src, int base, int n_total) {
     int st = ch & 1;
     int n = min(kChunk, n_total - ch * kChunk);
     uint32_t bytes = (uint32_t)n * 16u;
-    mbar_expect_tx(&S.bar[st], srcB ? 2u * bytes : bytes);
-    bulk_g2s(S.a[st], srcA + base + ch * kChunk, bytes, &S.bar[st]);
-    if (srcB) bulk_g2s(S.b[st], srcB + base + ch * kChunk, bytes, &S.bar[st]);
+    mbar_expect_tx(&S.bar[st], bytes * (uint32_t)src.n);
+    for (int k = 0; k < src.n; ++k) bulk_g2s(S.s[k][st], src.p[k] + base + ch * kChunk, bytes, &S.bar[st]);
 }
 
-__device__ __forceinline__ void block_lse(Stage2& S, float& m, float& s) {
+__device__ __forceinline__ void block_lse(Stage& S, float& m, float& s) {
     warp_lse_reduce(m, s);
     int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
@@ -238,7 +363,7 @@ __device__ __forceinline__ void block_lse(Stage2& S, float& m, float& s) {
     __syncthreads();
 }
 
-__device__ __forceinline__ float block_max(Stage2& S, float v) {
+__device__ __forceinline__ float block_max(Stage& S, float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) S.red_m[threadIdx.x >> 5] = v;
@@ -249,16 +374,15 @@ __device__ __forceinline__ float block_max(Stage2& S, float v) {
     return r;
 }
 
-// Pipeline of one tile: streams n_total spots of (srcA[, srcB]) starting at
-// `base` through shared memory and calls body(stage, count, offset) for each
-// chunk.
-// Returns false (uniformly) when a bounded wait ran out.
+// Streams n_total pairs of every source array (from pair index `base`) through
+// shared memory and calls body(stage, count, offset) per chunk.  Returns false
+// (uniformly across the CTA) when a bounded wait ran out.
 template <class Body>
-__device__ __forceinline__ bool stream_tile(Stage2& S, uint32_t (&parity)[2], const float4* srcA,
-                                            const float4* srcB, int base, int n_total, Body body) {
+__device__ __forceinline__ bool stream_tile(Stage& S, uint32_t (&parity)[2], const Srcs& src, int base,
+                                            int n_total, Body body) {
     int nch = (n_total + kChunk - 1) / kChunk;
     if (threadIdx.x == 0) {
-        for (int c = 0; c < nch && c < 2; ++c) issue_chunk(S, c, srcA, srcB, base, n_total);
+        for (int c = 0; c < nch && c < 2; ++c) issue_chunk(S, c, src, base, n_total);
     }
     bool ok_all = true;
     for (int ch = 0; ch < nch; ++ch) {
@@ -270,18 +394,16 @@ __device__ __forceinline__ bool stream_tile(Stage2& S, uint32_t (&parity)[2], co
             ok_all = false;
             // let copies already in flight land before the CTA leaves
             if (threadIdx.x == 0) {
-                for (int c = ch + 1; c < nch && c < ch + 2; ++c) {
-                    mbar_wait_bounded(&S.bar[c & 1], parity[c & 1]);
-                }
+                for (int c = ch + 1; c < nch && c < ch + 2; ++c) mbar_wait_bounded(&S.bar[c & 1], parity[c & 1]);
             }
             break;
         }
-        if (threadIdx.x == 0 && ch + 2 < nch) issue_chunk(S, ch + 2, srcA, srcB, base, n_total);
+        if (threadIdx.x == 0 && ch + 2 < nch) issue_chunk(S, ch + 2, src, base, n_total);
     }
     return ok_all;
 }
 
-__device__ __forceinline__ void init_stage(Stage2& S) {
+__device__ __forceinline__ void init_stage(Stage& S) {
     if (threadIdx.x == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
@@ -291,7 +413,7 @@ __device__ __forceinline__ void init_stage(Stage2& S) {
 }
 
 // Tile queue: thread 0 takes the next tile index; -1 when the queue is empty.
-__device__ __forceinline__ int next_tile(Stage2& S, int* counter, int n_tiles) {
+__device__ __forceinline__ int next_tile(Stage& S, int* counter, int n_tiles) {
     if (threadIdx.x == 0) {
         int t = atomicAdd(counter, 1);
         S.tile = t < n_tiles ? t : -1;
@@ -303,7 +425,7 @@ __device__ __forceinline__ int next_tile(Stage2& S, int* counter, int n_tiles) {
 }
 
 // Completion ticket: true in exactly one CTA, the last one to finish.
-__device__ __forceinline__ bool last_cta(Stage2& S, int* done) {
+__device__ __forceinline__ bool last_cta(Stage& S, int* done) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -316,103 +438,126 @@ __device__ __forceinline__ bool last_cta(Stage2& S, int* done) {
     return last;
 }
 
-// Online base-2 log-sum-exp over one staged chunk for a row held in registers
-// (px, py, pz); A = (c, G), B = (r, lambda).
-__device__ __forceinline__ void row_chunk(const float4* __restrict__ A, const float4* __restrict__ B, int n,
-                                          float px, float py, float pz, float negK, float& m, float& s) {
+__device__ __forceinline__ void lse_merge_into(float& m, float& s, float m2, float s2) {
+    Lse2 L;
+    L.m = m;
+    L.s = s;
+    L.merge(m2, s2);
+    m = L.m;
+    s = L.s;
+}
+
+// Row pair (two observed spots) against the staged model pairs of one chunk.
+struct RowPair {
+    f2 pxa, pya, pza, pxb, pyb, pzb;
+    RowLse A, B;
+};
+
+__device__ __forceinline__ void row_chunk(RowPair& R, const float4* __restrict__ sX, const float4* __restrict__ sY,
+                                          const float4* __restrict__ sZ, const float4* __restrict__ sW, int n,
+                                          f2 K2) {
     int k = 0;
     for (; k + kGroup <= n; k += kGroup) {
-        float v[kGroup];
+        f2 va[kGroup], vb[kGroup];
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u) {
-            float4 c = A[k + u];
-            float4 r = B[k + u];
-            v[u] = fmaf(ray_e2(px, py, pz, c.x, c.y, c.z, r.x, r.y, r.z), negK, c.w);
+        for (int g = 0; g < kGroup; ++g) {
+            ulonglong2 X = *(const ulonglong2*)&sX[k + g];
+            ulonglong2 Y = *(const ulonglong2*)&sY[k + g];
+            ulonglong2 Z = *(const ulonglong2*)&sZ[k + g];
+            ulonglong2 W = *(const ulonglong2*)&sW[k + g];
+            va[g] = pair_v2(R.pxa, R.pya, R.pza, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y);
+            vb[g] = pair_v2(R.pxb, R.pyb, R.pzb, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y);
         }
-        float cm = v[0];
-#pragma unroll
-        for (int u = 1; u < kGroup; ++u) cm = fmaxf(cm, v[u]);
-        if (cm > m) {
-            s *= ex2(m - cm);
-            m = cm;
-        }
-#pragma unroll
-        for (int u = 0; u < kGroup; ++u) s += ex2(v[u] - m);
+        R.A.add4(va);
+        R.B.add4(vb);
     }
     for (; k < n; ++k) {
-        float4 c = A[k];
-        float4 r = B[k];
-        float v = fmaf(ray_e2(px, py, pz, c.x, c.y, c.z, r.x, r.y, r.z), negK, c.w);
-        if (v > m) {
-            s *= ex2(m - v);
-            m = v;
-        }
-        s += ex2(v - m);
+        ulonglong2 X = *(const ulonglong2*)&sX[k];
+        ulonglong2 Y = *(const ulonglong2*)&sY[k];
+        ulonglong2 Z = *(const ulonglong2*)&sZ[k];
+        ulonglong2 W = *(const ulonglong2*)&sW[k];
+        R.A.add1(pair_v2(R.pxa, R.pya, R.pza, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y));
+        R.B.add1(pair_v2(R.pxb, R.pyb, R.pzb, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y));
     }
 }
 
-// Same for a column held in registers (c, r); A = (p, F).
-__device__ __forceinline__ void col_chunk(const float4* __restrict__ A, int n, float cx, float cy, float cz,
-                                          float rx, float ry, float rz, float negK, float& m, float& s) {
+// Column pair (two model spots) against the staged observed pairs.
+struct ColPair {
+    f2 ncxa, ncya, ncza, nrxa, nrya, nrza;
+    f2 ncxb, ncyb, nczb, nrxb, nryb, nrzb;
+    RowLse A, B;
+};
+
+__device__ __forceinline__ void col_chunk(ColPair& C, const float4* __restrict__ sX, const float4* __restrict__ sY,
+                                          int n, f2 K2) {
     int k = 0;
     for (; k + kGroup <= n; k += kGroup) {
-        float v[kGroup];
+        f2 va[kGroup], vb[kGroup];
 #pragma unroll
-        for (int u = 0; u < kGroup; ++u) {
-            float4 p = A[k + u];
-            v[u] = fmaf(ray_e2(p.x, p.y, p.z, cx, cy, cz, rx, ry, rz), negK, p.w);
+        for (int g = 0; g < kGroup; ++g) {
+            ulonglong2 X = *(const ulonglong2*)&sX[k + g];
+            ulonglong2 Y = *(const ulonglong2*)&sY[k + g];
+            va[g] = pair_v2(X.x, X.y, Y.x, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, K2, Y.y);
+            vb[g] = pair_v2(X.x, X.y, Y.x, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, K2, Y.y);
         }
-        float cm = v[0];
-#pragma unroll
-        for (int u = 1; u < kGroup; ++u) cm = fmaxf(cm, v[u]);
-        if (cm > m) {
-            s *= ex2(m - cm);
-            m = cm;
-        }
-#pragma unroll
-        for (int u = 0; u < kGroup; ++u) s += ex2(v[u] - m);
+        C.A.add4(va);
+        C.B.add4(vb);
     }
     for (; k < n; ++k) {
-        float4 p = A[k];
-        float v = fmaf(ray_e2(p.x, p.y, p.z, cx, cy, cz, rx, ry, rz), negK, p.w);
-        if (v > m) {
-            s *= ex2(m - v);
-            m = v;
-        }
-        s += ex2(v - m);
+        ulonglong2 X = *(const ulonglong2*)&sX[k];
+        ulonglong2 Y = *(const ulonglong2*)&sY[k];
+        C.A.add1(pair_v2(X.x, X.y, Y.x, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, K2, Y.y));
+        C.B.add1(pair_v2(X.x, X.y, Y.x, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, K2, Y.y));
     }
 }
 
 // --------------------------------------------------------------- row pass
 __global__ void __launch_bounds__(kTPB) sk_row_kernel(SkArgs a) {
-    __shared__ __align__(128) Stage2 S;
+    __shared__ __align__(128) Stage S;
     init_stage(S);
     uint32_t parity[2] = {0u, 0u};
     DustPtrs D = dust_ptrs(a.dust, a.T);
     const int n_tiles = a.ctrl[CTRL_N_ROW_TILES];
+    const f2 K2 = dup(a.negKD2);
+    const Srcs src{{a.modX, a.modY, a.modZ, a.modW}, 4};
     while (true) {
         int tile = next_tile(S, a.ctrl + CTRL_ROW_NEXT, n_tiles);
         if (tile < 0) break;
         int4 td = a.row_tiles[tile];
         int t = td.x;
-        int i = td.y + threadIdx.x;
+        int q = td.y + threadIdx.x;
         bool valid = (int)threadIdx.x < td.z;
-        int j0 = a.J_off[t], nj = a.J_off[t + 1] - j0;
+        int ni = a.I_off[t + 1] - a.I_off[t];
+        bool vb = valid && 2 * (q - a.I2_off[t]) + 1 < ni;
+        int j0 = a.J2_off[t], nj = a.J2_off[t + 1] - j0;
         float dustv = D.G0[a.mode ? t : 0] - a.kc;
-        float4 p = valid ? a.obsP[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float m = dustv, s = 1.0f;
-        const float negK = a.negKD2;
-        bool ok = stream_tile(S, parity, a.modC, a.modR, j0, nj, [&](int st, int n, int) {
-            if (valid) row_chunk(S.a[st], S.b[st], n, p.x, p.y, p.z, negK, m, s);
+        float4 X = valid ? a.obsX[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 Y = valid ? a.obsY[q] : make_float4(0.f, 0.f, kPadFar, kPadFar);
+        RowPair R;
+        R.pxa = dup(X.x);
+        R.pya = dup(X.z);
+        R.pza = dup(Y.x);
+        R.pxb = dup(X.y);
+        R.pyb = dup(X.w);
+        R.pzb = dup(Y.y);
+        R.A.init(dustv);
+        R.B.init(dustv);
+        bool ok = stream_tile(S, parity, src, j0, nj, [&](int st, int n, int) {
+            if (valid) row_chunk(R, S.s[0][st], S.s[1][st], S.s[2][st], S.s[3][st], n, K2);
         });
         if (!ok) {
             if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
             break;
         }
-        float F = -(m + lg2(s));
-        if (valid) a.obsP[i] = make_float4(p.x, p.y, p.z, F);
+        float Fa = -R.A.value(), Fb = -R.B.value();
+        if (valid) *(float2*)&a.obsY[q].z = make_float2(Fa, vb ? Fb : kNegHuge);
         // tile partial of LSE2(F_i - kc) for the outlier column update
-        float pm = valid ? F - a.kc : kNegHuge, ps = valid ? 1.0f : 0.0f;
+        float pm = kNegHuge, ps = 0.0f;
+        if (valid) {
+            pm = Fa - a.kc;
+            ps = 1.0f;
+            if (vb) lse_merge_into(pm, ps, Fb - a.kc, 1.0f);
+        }
         block_lse(S, pm, ps);
         if (threadIdx.x == 0) a.row_part[tile] = make_float2(pm, ps);
     }
@@ -434,12 +579,7 @@ __global__ void __launch_bounds__(kTPB) sk_row_kernel(SkArgs a) {
         float m = kNegHuge, s = 0.0f;
         for (int k = threadIdx.x; k < n_tiles; k += blockDim.x) {
             float2 pp = a.row_part[k];
-            Lse2 L;
-            L.m = m;
-            L.s = s;
-            L.merge(pp.x, pp.y);
-            m = L.m;
-            s = L.s;
+            lse_merge_into(m, s, pp.x, pp.y);
         }
         block_lse(S, m, s);
         if (threadIdx.x == 0) {
@@ -456,35 +596,61 @@ __global__ void __launch_bounds__(kTPB) sk_row_kernel(SkArgs a) {
     }
 }
 
+__device__ __forceinline__ void load_col_pair(const SkArgs& a, int q, ColPair& C) {
+    float4 X = a.modX[q], Y = a.modY[q], Z = a.modZ[q], W = a.modW[q];
+    C.ncxa = dup(X.x);
+    C.ncya = dup(X.z);
+    C.ncza = dup(Y.x);
+    C.nrxa = dup(Z.x);
+    C.nrya = dup(Z.z);
+    C.nrza = dup(W.x);
+    C.ncxb = dup(X.y);
+    C.ncyb = dup(X.w);
+    C.nczb = dup(Y.y);
+    C.nrxb = dup(Z.y);
+    C.nryb = dup(Z.w);
+    C.nrzb = dup(W.y);
+}
+
 // ------------------------------------------------------------ column pass
 __global__ void __launch_bounds__(kTPB) sk_col_kernel(SkArgs a) {
-    __shared__ __align__(128) Stage2 S;
+    __shared__ __align__(128) Stage S;
     init_stage(S);
     uint32_t parity[2] = {0u, 0u};
     DustPtrs D = dust_ptrs(a.dust, a.T);
     const int n_tiles = a.ctrl[CTRL_N_COL_TILES];
+    const f2 K2 = dup(a.negKD2);
+    const Srcs src{{a.obsX, a.obsY, nullptr, nullptr}, 2};
     while (true) {
         int tile = next_tile(S, a.ctrl + CTRL_COL_NEXT, n_tiles);
         if (tile < 0) break;
         int4 td = a.col_tiles[tile];
         int t = td.x;
-        int j = td.y + threadIdx.x;
+        int q = td.y + threadIdx.x;
         bool valid = (int)threadIdx.x < td.z;
-        int i0 = a.I_off[t], ni = a.I_off[t + 1] - i0;
-        float4 c = valid ? a.modC[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 r = valid ? a.modR[j] : make_float4(0.f, 0.f, 1.f, 0.f);
-        float m = D.F0[a.mode ? t : 0], s = 1.0f;  // unmatched-model row, C_0j = 0
-        const float negK = a.negKD2;
-        bool ok = stream_tile(S, parity, a.obsP, nullptr, i0, ni, [&](int st, int n, int) {
-            if (valid) col_chunk(S.a[st], n, c.x, c.y, c.z, r.x, r.y, r.z, negK, m, s);
+        int nj = a.J_off[t + 1] - a.J_off[t];
+        bool vb = valid && 2 * (q - a.J2_off[t]) + 1 < nj;
+        int i0 = a.I2_off[t], ni = a.I2_off[t + 1] - i0;
+        ColPair C;
+        if (valid) load_col_pair(a, q, C);
+        float dz = D.F0[a.mode ? t : 0];  // unmatched-model row, C_0j = 0
+        C.A.init(dz);
+        C.B.init(dz);
+        bool ok = stream_tile(S, parity, src, i0, ni, [&](int st, int n, int) {
+            if (valid) col_chunk(C, S.s[0][st], S.s[1][st], n, K2);
         });
         if (!ok) {
             if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
             break;
         }
-        float G = -(m + lg2(s));
-        if (valid) a.modC[j] = make_float4(c.x, c.y, c.z, G);
-        float pm = valid ? G : kNegHuge, ps = valid ? 1.0f : 0.0f;
+        float Ga = -C.A.value(), Gb = -C.B.value();
+        if (valid) *(float2*)&a.modY[q].z = make_float2(Ga, vb ? Gb : kNegHuge);
+        float pm = kNegHuge, ps = 0.0f;
+        if (valid) {
+            pm = Ga;
+            ps = 1.0f;
+            if (vb) lse_merge_into(pm, ps, Gb, 1.0f);
+        }
         block_lse(S, pm, ps);
         if (threadIdx.x == 0) a.col_part[tile] = make_float2(pm, ps);
     }
@@ -505,12 +671,7 @@ __global__ void __launch_bounds__(kTPB) sk_col_kernel(SkArgs a) {
         float m = kNegHuge, s = 0.0f;
         for (int k = threadIdx.x; k < n_tiles; k += blockDim.x) {
             float2 pp = a.col_part[k];
-            Lse2 L;
-            L.m = m;
-            L.s = s;
-            L.merge(pp.x, pp.y);
-            m = L.m;
-            s = L.s;
+            lse_merge_into(m, s, pp.x, pp.y);
         }
         block_lse(S, m, s);
         if (threadIdx.x == 0) {
@@ -530,48 +691,75 @@ __global__ void __launch_bounds__(kTPB) sk_col_kernel(SkArgs a) {
 // Plan read-out per observed spot with the final potentials: argmax over the
 // block's model spots and the outlier column (ties to the lowest index, the
 // outlier column only when strictly larger), top1 - top2 margin in plan
-// units, and the row-marginal error.
+// units, and the row-marginal error.  Scalar bookkeeping; once per E-step.
+struct Top2 {
+    float m, s, b1, b2;
+    int arg;
+    __device__ __forceinline__ void init() {
+        m = kNegHuge;
+        s = 0.0f;
+        b1 = kNegHuge;
+        b2 = kNegHuge;
+        arg = -1;
+    }
+    __device__ __forceinline__ void add(float v, int j) {
+        if (v > m) {
+            s = s * ex2(m - v) + 1.0f;
+            m = v;
+        } else {
+            s += ex2(v - m);
+        }
+        if (v > b1) {  // strict: ties keep the lowest index
+            b2 = b1;
+            b1 = v;
+            arg = j;
+        } else if (v > b2) {
+            b2 = v;
+        }
+    }
+};
+
 __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
-    __shared__ __align__(128) Stage2 S;
+    __shared__ __align__(128) Stage S;
     init_stage(S);
     uint32_t parity[2] = {0u, 0u};
     DustPtrs D = dust_ptrs(a.dust, a.T);
     const int n_tiles = a.ctrl[CTRL_N_ROW_TILES];
+    const f2 K2 = dup(a.negKD2);
+    const Srcs src{{a.modX, a.modY, a.modZ, a.modW}, 4};
     float my_err = 0.0f;
     while (true) {
         int tile = next_tile(S, a.ctrl + CTRL_HRV_NEXT, n_tiles);
         if (tile < 0) break;
         int4 td = a.row_tiles[tile];
         int t = td.x;
-        int i = td.y + threadIdx.x;
+        int q = td.y + threadIdx.x;
         bool valid = (int)threadIdx.x < td.z;
-        int j0 = a.J_off[t], nj = a.J_off[t + 1] - j0;
+        int ni = a.I_off[t + 1] - a.I_off[t];
+        int lrow = 2 * (q - a.I2_off[t]);
+        bool vb = valid && lrow + 1 < ni;
+        int jbase = a.J_off[t], j0 = a.J2_off[t], nj = a.J2_off[t + 1] - j0;
         float dustv = D.G0[a.mode ? t : 0] - a.kc;
-        float4 p = valid ? a.obsP[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float m = kNegHuge, s = 0.0f, b1 = kNegHuge, b2 = kNegHuge;
-        int arg = -1;
-        const float negK = a.negKD2;
-        bool ok = stream_tile(S, parity, a.modC, a.modR, j0, nj, [&](int st, int n, int off) {
+        float4 X = valid ? a.obsX[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 Y = valid ? a.obsY[q] : make_float4(0.f, 0.f, kPadFar, kPadFar);
+        f2 pxa = dup(X.x), pya = dup(X.z), pza = dup(Y.x), pxb = dup(X.y), pyb = dup(X.w), pzb = dup(Y.y);
+        Top2 A, B;
+        A.init();
+        B.init();
+        bool ok = stream_tile(S, parity, src, j0, nj, [&](int st, int n, int off) {
             if (!valid) return;
-            const float4* A = S.a[st];
-            const float4* B = S.b[st];
             for (int k = 0; k < n; ++k) {
-                float4 c = A[k];
-                float4 r = B[k];
-                float v = fmaf(ray_e2(p.x, p.y, p.z, c.x, c.y, c.z, r.x, r.y, r.z), negK, c.w);
-                if (v > m) {
-                    s = s * ex2(m - v) + 1.0f;
-                    m = v;
-                } else {
-                    s += ex2(v - m);
-                }
-                if (v > b1) {  // strict: ties keep the lowest index
-                    b2 = b1;
-                    b1 = v;
-                    arg = j0 + off + k;
-                } else if (v > b2) {
-                    b2 = v;
-                }
+                ulonglong2 Xm = *(const ulonglong2*)&S.s[0][st][k];
+                ulonglong2 Ym = *(const ulonglong2*)&S.s[1][st][k];
+                ulonglong2 Zm = *(const ulonglong2*)&S.s[2][st][k];
+                ulonglong2 Wm = *(const ulonglong2*)&S.s[3][st][k];
+                f2 va = pair_v2(pxa, pya, pza, Xm.x, Xm.y, Ym.x, Zm.x, Zm.y, Wm.x, K2, Ym.y);
+                f2 vv = pair_v2(pxb, pyb, pzb, Xm.x, Xm.y, Ym.x, Zm.x, Zm.y, Wm.x, K2, Ym.y);
+                int j = jbase + 2 * (off + k);
+                A.add(lo(va), j);
+                A.add(hi(va), j + 1);  // padding slots have -3e38 and never win
+                B.add(lo(vv), j);
+                B.add(hi(vv), j + 1);
             }
         });
         if (!ok) {
@@ -579,23 +767,27 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
             break;
         }
         if (valid) {
-            if (dustv > b1) {  // outlier column last, only when strictly larger
-                b2 = b1;
-                b1 = dustv;
-                arg = -1;
-            } else if (dustv > b2) {
-                b2 = dustv;
+            int i = a.I_off[t] + lrow;
+            for (int lane = 0; lane < 2; ++lane) {
+                if (lane == 1 && !vb) break;
+                Top2& P = lane ? B : A;
+                float F = lane ? Y.w : Y.z;
+                if (dustv > P.b1) {  // outlier column last, only when strictly larger
+                    P.b2 = P.b1;
+                    P.b1 = dustv;
+                    P.arg = -1;
+                } else if (dustv > P.b2) {
+                    P.b2 = dustv;
+                }
+                Lse2 L;
+                L.m = P.m;
+                L.s = P.s;
+                L.merge(dustv, 1.0f);
+                float rs = ex2(F + L.value());
+                my_err = fmaxf(my_err, fabsf(rs - 1.0f));
+                if (a.assign) a.assign[i + lane] = P.arg;
+                if (a.margin) a.margin[i + lane] = ex2(F + P.b1) - (P.b2 > kNegHuge ? ex2(F + P.b2) : 0.0f);
             }
-            // row sum including the outlier column
-            Lse2 L;
-            L.m = m;
-            L.s = s;
-            L.merge(dustv, 1.0f);
-            float F = p.w;
-            float rs = ex2(F + L.value());
-            my_err = fmaxf(my_err, fabsf(rs - 1.0f));
-            if (a.assign) a.assign[i] = arg;
-            if (a.margin) a.margin[i] = ex2(F + b1) - (b2 > kNegHuge ? ex2(F + b2) : 0.0f);
         }
     }
     float e = block_max(S, my_err);
@@ -617,36 +809,50 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
 // Column mass q_j = sum_i Q_ij over observed rows and the column-marginal
 // error with the final potentials.
 __global__ void __launch_bounds__(kTPB) sk_harvest_col_kernel(SkArgs a) {
-    __shared__ __align__(128) Stage2 S;
+    __shared__ __align__(128) Stage S;
     init_stage(S);
     uint32_t parity[2] = {0u, 0u};
     DustPtrs D = dust_ptrs(a.dust, a.T);
     const int n_tiles = a.ctrl[CTRL_N_COL_TILES];
+    const f2 K2 = dup(a.negKD2);
+    const Srcs src{{a.obsX, a.obsY, nullptr, nullptr}, 2};
     float my_err = 0.0f;
     while (true) {
         int tile = next_tile(S, a.ctrl + CTRL_HCOL_NEXT, n_tiles);
         if (tile < 0) break;
         int4 td = a.col_tiles[tile];
         int t = td.x;
-        int j = td.y + threadIdx.x;
+        int q = td.y + threadIdx.x;
         bool valid = (int)threadIdx.x < td.z;
-        int i0 = a.I_off[t], ni = a.I_off[t + 1] - i0;
-        float4 c = valid ? a.modC[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 r = valid ? a.modR[j] : make_float4(0.f, 0.f, 1.f, 0.f);
-        float m = kNegHuge, s = 0.0f;
-        const float negK = a.negKD2;
-        bool ok = stream_tile(S, parity, a.obsP, nullptr, i0, ni, [&](int st, int n, int) {
-            if (valid) col_chunk(S.a[st], n, c.x, c.y, c.z, r.x, r.y, r.z, negK, m, s);
+        int nj = a.J_off[t + 1] - a.J_off[t];
+        int lcol = 2 * (q - a.J2_off[t]);
+        bool vb = valid && lcol + 1 < nj;
+        int i0 = a.I2_off[t], ni = a.I2_off[t + 1] - i0;
+        ColPair C;
+        if (valid) load_col_pair(a, q, C);
+        C.A.init(kNegHuge);
+        C.B.init(kNegHuge);
+        C.A.S = pk(0.0f, 0.0f);
+        C.B.S = pk(0.0f, 0.0f);
+        bool ok = stream_tile(S, parity, src, i0, ni, [&](int st, int n, int) {
+            if (valid) col_chunk(C, S.s[0][st], S.s[1][st], n, K2);
         });
         if (!ok) {
             if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
             break;
         }
         if (valid) {
-            float qj = s > 0.0f ? ex2(c.w + m + lg2(s)) : 0.0f;
-            if (a.q) a.q[j] = qj;
-            float q0 = ex2(c.w + D.F0[a.mode ? t : 0]);
-            my_err = fmaxf(my_err, fabsf(qj + q0 - 1.0f));
+            float4 Ym = a.modY[q];
+            float F0 = D.F0[a.mode ? t : 0];
+            for (int lane = 0; lane < 2; ++lane) {
+                if (lane == 1 && !vb) break;
+                RowLse& L = lane ? C.B : C.A;
+                float G = lane ? Ym.w : Ym.z;
+                float ssum = lo(L.S) + hi(L.S);
+                float qj = ssum > 0.0f ? ex2(G + L.m + lg2(ssum)) : 0.0f;
+                if (a.q) a.q[a.J_off[t] + lcol + lane] = qj;
+                my_err = fmaxf(my_err, fabsf(qj + ex2(G + F0) - 1.0f));
+            }
         }
     }
     float e = block_max(S, my_err);
@@ -664,12 +870,16 @@ __global__ void sk_finish_kernel(SkArgs a, int have_rows, int have_cols) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     bool bad = false;
     if (k < a.n_obs) {
-        float v = a.obsP[k].w;
+        int t = block_of(a.I_off, a.T, k);
+        int l = k - a.I_off[t];
+        float v = ((const float*)&a.obsY[a.I2_off[t] + (l >> 1)])[2 + (l & 1)];
         bad |= !isfinite(v);
         a.f[k] = v * a.to_user;
     }
     if (k < a.n_model) {
-        float v = a.modC[k].w;
+        int t = block_of(a.J_off, a.T, k);
+        int l = k - a.J_off[t];
+        float v = ((const float*)&a.modY[a.J2_off[t] + (l >> 1)])[2 + (l & 1)];
         bad |= !isfinite(v);
         a.g[k] = v * a.to_user;
     }
@@ -695,23 +905,42 @@ __global__ void sk_clear_err_kernel(SkArgs a) {
     D.err[0] = D.err[1] = D.err[2] = D.err[3] = 0.0f;
 }
 
-cudaError_t sinkhorn_run(const SkArgs& a, const SkLaunch& l, int n_iter, bool want_rows, bool want_cols,
-                         cudaStream_t s) {
+cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s) {
     int nmax = a.n_obs > a.n_model ? a.n_obs : a.n_model;
-    int pack_blocks = (nmax + 255) / 256;
-    if (pack_blocks < 1) pack_blocks = 1;
+    int blocks = (nmax + 255) / 256;
+    if (blocks < 1) blocks = 1;
     sk_schedule_kernel<<<1, 1024, 0, s>>>(a);
-    sk_pack_kernel<<<pack_blocks, 256, 0, s>>>(a);
+    sk_pack_kernel<<<blocks, 256, 0, s>>>(a);
     sk_init_dust_kernel<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t sinkhorn_iterate(const SkArgs& a, const SkLaunch& l, int n_iter, cudaStream_t s) {
     for (int it = 0; it < n_iter; ++it) {
         sk_row_kernel<<<l.row_grid, kTPB, 0, s>>>(a);
         sk_col_kernel<<<l.col_grid, kTPB, 0, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t sinkhorn_finish(const SkArgs& a, const SkLaunch& l, bool want_rows, bool want_cols, cudaStream_t s) {
+    int nmax = a.n_obs > a.n_model ? a.n_obs : a.n_model;
+    int blocks = (nmax + 255) / 256;
+    if (blocks < 1) blocks = 1;
     if (want_rows || want_cols) sk_clear_err_kernel<<<1, 1, 0, s>>>(a);
     if (want_rows) sk_harvest_row_kernel<<<l.hrv_grid, kTPB, 0, s>>>(a);
     if (want_cols) sk_harvest_col_kernel<<<l.hcol_grid, kTPB, 0, s>>>(a);
-    sk_finish_kernel<<<pack_blocks, 256, 0, s>>>(a, want_rows ? 1 : 0, want_cols ? 1 : 0);
+    sk_finish_kernel<<<blocks, 256, 0, s>>>(a, want_rows ? 1 : 0, want_cols ? 1 : 0);
     return cudaGetLastError();
+}
+
+cudaError_t sinkhorn_run(const SkArgs& a, const SkLaunch& l, int n_iter, bool want_rows, bool want_cols,
+                         cudaStream_t s) {
+    cudaError_t e = sinkhorn_prepare(a, s);
+    if (e != cudaSuccess) return e;
+    e = sinkhorn_iterate(a, l, n_iter, s);
+    if (e != cudaSuccess) return e;
+    return sinkhorn_finish(a, l, want_rows, want_cols, s);
 }
 
 int sinkhorn_occupancy(int* row_blocks_per_sm, int* col_blocks_per_sm) {
