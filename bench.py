@@ -287,7 +287,10 @@ def main():
     h2d = p_host.numel() * 4 + R_host.numel() * 4 + x_host.numel() * 4
     d2h = a_host.numel() * 4 + Ro_host.numel() * 4 + xo_host.numel() * 4
 
-    launches_per_step = 1 + 3 + 2 * cfg.n_sinkhorn + 3 + (1 if hasattr(api, "mstep") else 0)
+    # refresh 1; Sinkhorn: schedule, pack, dust init, 2 per iteration, clear, harvest, finish;
+    # M-step: schedule, pack, dust init, segment count + scan, init, 2 per Newton step,
+    # MM pair + MM grain, norms
+    launches_per_step = 1 + (3 + 2 * cfg.n_sinkhorn + 3) + (3 + 2 + 1 + 2 * 4 + 2 + 1)
     # roofline: the pair evaluation needs 15 FP32 lane-ops (3 sub, 3 for |d|^2,
     # 3 for d*s - r, 3 for |e|^2, 1 fold, 1 shift, 1 accumulate), 1 MUFU rsqrt and
     # 1 MUFU ex2; the peak is the slowest of the three pipes, each measured on

@@ -250,6 +250,15 @@ int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, const LaueLatt
                         const float* g, float eps, const float* omega, const float* R,
                         const float* x, int N, float* grad, float* value, void* stream);
 
+/* Rotation parameterisation used with laue_objective_grad (no counterpart in
+ * the paper): R = exp([w]x) R0 for axis-angle w (N x 3) and base rotations R0
+ * (N x 9); JlT (optional, N x 9) receives the transpose of the left Jacobian
+ * of SO(3) at w, which turns the left-perturbation gradient returned by
+ * laue_objective_grad at R into the gradient with respect to w.
+ * Asynchronous. */
+int laue_axis_angle(laue_handle* h, const float* w, const float* R0, float* R, float* JlT, int N,
+                    void* stream);
+
 /* SPOT prototype selection (paper Section "Selection of Prototypes with
  * Optimal Transport", Appendix "Selection of prototypes", Algorithm
  * LaueSpotGreedy): candidate grains (candR Nc x 9, candX Nc x 3) make their

@@ -85,6 +85,7 @@ SIGNATURES = {
                    _P(LaueMParams), _vp, _vp, _vp, _i, _vp, _vp],
     "laue_objective_grad": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots),
                             _vp, _vp, _f, _vp, _vp, _vp, _i, _vp, _vp, _vp],
+    "laue_axis_angle": [_vp, _vp, _vp, _vp, _vp, _i, _vp],
     "laue_prototype_select": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                               _f, _f, _i, _vp, _vp, _pi, _vp],
     "laue_index": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,

@@ -297,3 +297,47 @@ def cost_sinkhorn(h: Handle, geom, obs: ObsSpots, model: ModelSpots, eps, c_out,
     if col_harvest:
         out["q"] = q[:nJ]
     return out
+
+
+def mparams(eps, n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3):
+    return N.LaueMParams(float(eps), int(n_newton), int(n_mm), float(tol_x), float(tol_R), float(hreg))
+
+
+def mstep(h: Handle, geom, lat: Lattice, obs: ObsSpots, model: ModelSpots, f, g, eps, omega, R, x,
+          n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, step_norms=None, stream=None):
+    """laue_mstep: updates R ((N, 9) or (N, 3, 3) float32, contiguous) and x
+    ((N, 3)) in place from the E-step potentials f, g (model must hold the
+    E-step rays and centres)."""
+    N_ = int(x.shape[0])
+    h.reserve(obs.T, n_obs=int(obs.p.shape[0]), n_model=model.n, n_grains=N_,
+              n_planes=int(lat.w_d0.shape[0]), stream=stream)
+    prm = mparams(eps, n_newton, n_mm, tol_x, tol_R, hreg)
+    g_s, o_s, m_s, l_s = geometry_struct(geom), obs.struct(), model.struct(), lat.struct()
+    h.check(h.L.laue_mstep(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), ctypes.byref(m_s),
+                           _ptr(f), _ptr(g), ctypes.byref(prm), _ptr(omega), _ptr(R), _ptr(x), N_,
+                           _ptr(step_norms), _stream(stream)), "laue_mstep")
+
+
+def objective_grad(h: Handle, geom, lat: Lattice, obs: ObsSpots, model: ModelSpots, f, g, eps, omega, R, x,
+                   stream=None):
+    """laue_objective_grad: (grad (N, 6) = [dE/dw, dE/dx], value (N,))."""
+    N_ = int(x.shape[0])
+    h.reserve(obs.T, n_obs=int(obs.p.shape[0]), n_model=model.n, n_grains=N_,
+              n_planes=int(lat.w_d0.shape[0]), stream=stream)
+    grad = torch.empty(max(N_, 1), 6, device=x.device)
+    val = torch.empty(max(N_, 1), device=x.device)
+    g_s, o_s, m_s, l_s = geometry_struct(geom), obs.struct(), model.struct(), lat.struct()
+    h.check(h.L.laue_objective_grad(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s),
+                                    ctypes.byref(m_s), _ptr(f), _ptr(g), float(eps), _ptr(omega), _ptr(R),
+                                    _ptr(x), N_, _ptr(grad), _ptr(val), _stream(stream)), "laue_objective_grad")
+    return grad[:N_], val[:N_]
+
+
+def axis_angle(h: Handle, w, R0, with_jacobian=False, stream=None):
+    """laue_axis_angle: R = exp([w]x) R0 and optionally J_l(w)^T."""
+    N_ = int(w.shape[0])
+    R = torch.empty(max(N_, 1), 9, device=w.device)
+    J = torch.empty(max(N_, 1), 9, device=w.device) if with_jacobian else None
+    h.check(h.L.laue_axis_angle(h.h, _ptr(w.contiguous()), _ptr(R0.reshape(-1, 9).contiguous()), _ptr(R),
+                                _ptr(J), N_, _stream(stream)), "laue_axis_angle")
+    return (R[:N_], J[:N_]) if with_jacobian else R[:N_]

@@ -414,16 +414,113 @@ extern "C" int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, cons
 
 // ------------------------------------------------------------- not yet built
 
-extern "C" int laue_mstep(laue_handle* h, const LaueGeometry*, const LaueLattice*, const LaueObsSpots*,
-                          const LaueModelSpots*, const float*, const float*, const LaueMParams*, const float*,
-                          float*, float*, int, float*, void*) {
-    return laue_fail(h, LAUE_ERR_UNIMPLEMENTED, "laue_mstep is not built yet");
+extern "C" int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const LaueObsSpots* obs,
+                          const LaueModelSpots* model, const float* f, const float* g, const LaueMParams* prm,
+                          const float* omega, float* R, float* x, int N, float* step_norms, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = laue_check_geom(h, geom))) return rc;
+    if ((rc = laue_check_obs(h, obs))) return rc;
+    if ((rc = laue_check_model(h, model))) return rc;
+    if (obs->T != model->T) return laue_fail(h, LAUE_ERR_INVALID_ARG, "observed and model T differ");
+    if (!prm || !(prm->eps > 0.0f) || prm->n_newton < 0 || prm->n_mm < 0)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "M-step params: eps > 0, n_newton >= 0, n_mm >= 0");
+    if (!lat || lat->M < 1 || !lat->w_d0 || !aligned16(lat->w_d0))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "lattice: M >= 1 and aligned w_d0");
+    if (N < 0 || (N > 0 && (!R || !x)) || !omega || (obs->n > 0 && !f) || (model->n > 0 && !g))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "M-step: NULL array or N < 0");
+    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M};
+    Layout L;
+    if ((rc = laue_need_ws(h, d, &L))) return rc;
+    MsArgs m{};
+    SkLaunch lc;
+    LaueOTParams op{0.4, prm->eps, 0.0f, 0, 0, 1, 0};
+    laue_fill_sk(h, geom, obs, model, &op, L, &m.sk, &lc);
+    m.sk.f = const_cast<float*>(f);
+    m.sk.g = const_cast<float*>(g);
+    m.sk.dust_out = nullptr;
+    m.sk.warm = 1;
+    char* ws = (char*)h->ws;
+    m.sk.dust = (float*)(ws + L.dust);
+    m.w_d0 = (const float4*)lat->w_d0;
+    m.M = lat->M;
+    m.omega = omega;
+    m.T = obs->T;
+    m.N = N;
+    m.n_model = model->n;
+    m.J_off = model->J_off;
+    m.grain = model->grain;
+    m.plane = model->plane;
+    m.angle = model->angle;
+    m.R = R;
+    m.x = x;
+    m.jsum = (float*)(ws + L.jsum);
+    m.seg = (int*)(ws + L.gidx);
+    m.gstate = (float*)(ws + L.gsum);
+    m.step_norms = step_norms;
+    m.tol_x = prm->tol_x;
+    m.tol_R = prm->tol_R;
+    m.hreg = prm->hreg;
+    m.n_newton = prm->n_newton;
+    m.n_mm = prm->n_mm;
+    for (int k = 0; k < 3; ++k) m.e[k] = geom->beam[k];
+    return laue_cuda_check(h, mstep_run(m, lc, (cudaStream_t)stream), "mstep launch");
 }
 
-extern "C" int laue_objective_grad(laue_handle* h, const LaueGeometry*, const LaueLattice*, const LaueObsSpots*,
-                                   const LaueModelSpots*, const float*, const float*, float, const float*,
-                                   const float*, const float*, int, float*, float*, void*) {
-    return laue_fail(h, LAUE_ERR_UNIMPLEMENTED, "laue_objective_grad is not built yet");
+extern "C" int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                                   const LaueObsSpots* obs, const LaueModelSpots* model, const float* f,
+                                   const float* g, float eps, const float* omega, const float* R, const float* x,
+                                   int N, float* grad, float* value, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = laue_check_geom(h, geom))) return rc;
+    if ((rc = laue_check_obs(h, obs))) return rc;
+    if ((rc = laue_check_model(h, model))) return rc;
+    if (obs->T != model->T) return laue_fail(h, LAUE_ERR_INVALID_ARG, "observed and model T differ");
+    if (!(eps > 0.0f)) return laue_fail(h, LAUE_ERR_INVALID_ARG, "eps must be > 0");
+    if (!lat || lat->M < 1 || !lat->w_d0 || !aligned16(lat->w_d0))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "lattice: M >= 1 and aligned w_d0");
+    if (N < 0 || (N > 0 && (!R || !x || !grad)) || !omega || (obs->n > 0 && !f) || (model->n > 0 && !g))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "objective_grad: NULL array or N < 0");
+    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M};
+    Layout L;
+    if ((rc = laue_need_ws(h, d, &L))) return rc;
+    MsArgs m{};
+    SkLaunch lc;
+    LaueOTParams op{0.4, eps, 0.0f, 0, 0, 1, 0};
+    laue_fill_sk(h, geom, obs, model, &op, L, &m.sk, &lc);
+    m.sk.f = const_cast<float*>(f);
+    m.sk.g = const_cast<float*>(g);
+    m.sk.dust_out = nullptr;
+    m.sk.warm = 1;
+    char* ws = (char*)h->ws;
+    m.w_d0 = (const float4*)lat->w_d0;
+    m.M = lat->M;
+    m.omega = omega;
+    m.T = obs->T;
+    m.N = N;
+    m.n_model = model->n;
+    m.J_off = model->J_off;
+    m.grain = model->grain;
+    m.plane = model->plane;
+    m.angle = model->angle;
+    m.R = const_cast<float*>(R);
+    m.x = const_cast<float*>(x);
+    m.jsum = (float*)(ws + L.jsum);
+    m.seg = (int*)(ws + L.gidx);
+    m.gstate = (float*)(ws + L.gsum);
+    for (int k = 0; k < 3; ++k) m.e[k] = geom->beam[k];
+    m.D2 = geom->D * geom->D;
+    m.grad = grad;
+    m.value = value;
+    return laue_cuda_check(h, grad_run(m, lc, (cudaStream_t)stream), "objective_grad launch");
+}
+
+extern "C" int laue_axis_angle(laue_handle* h, const float* w, const float* R0, float* R, float* JlT, int N,
+                               void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    if (N < 0 || (N > 0 && (!w || !R0 || !R))) return laue_fail(h, LAUE_ERR_INVALID_ARG, "axis_angle: bad arguments");
+    return laue_cuda_check(h, axis_angle_run(w, R0, R, JlT, N, (cudaStream_t)stream), "axis_angle launch");
 }
 
 extern "C" int laue_prototype_select(laue_handle* h, const LaueGeometry*, const LaueLattice*,

@@ -91,7 +91,7 @@ inline Layout make_layout(const LaueProblemDims& d) {
     L.fwd_blocks = take(sizeof(int) * (size_t)(2 * L.max_fwd_blocks + 2));
     L.jsum = take(sizeof(float) * 12 * (size_t)(d.n_model + 1));
     L.gsum = take(sizeof(float) * 16 * (size_t)(d.n_grains + 1));
-    L.gidx = take(sizeof(int) * (size_t)(d.n_grains + 2 + d.n_model + 1));
+    L.gidx = take(sizeof(int) * ((size_t)T * (d.n_grains + 1) + 16));
     L.total = off;
     return L;
 }

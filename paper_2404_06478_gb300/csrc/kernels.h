@@ -110,4 +110,33 @@ cudaError_t sinkhorn_iterate(const SkArgs& a, const SkLaunch& l, int n_iter, cud
 cudaError_t sinkhorn_finish(const SkArgs& a, const SkLaunch& l, bool want_rows, bool want_cols, cudaStream_t s);
 int sinkhorn_occupancy(int* row_blocks_per_sm, int* col_blocks_per_sm);
 
+// ------------------------------------------------------------------ M-step
+struct MsArgs {
+    SkArgs sk;              // layout, tiles and pair-interleaved copies (F, G of the E-step)
+    const float4* w_d0;     // plane directions (M)
+    int M;
+    const float* omega;
+    int T, N, n_model;
+    const int* J_off;
+    const int* grain;
+    const int* plane;
+    const int* angle;
+    float* R;               // N x 9, in/out
+    float* x;               // N x 3, in/out
+    float* jsum;            // 12 floats per model spot
+    int* seg;               // T x (N + 1) segment starts
+    float* gstate;          // 4 floats per grain
+    float* step_norms;      // optional N x 2
+    float tol_x, tol_R, hreg;
+    int n_newton, n_mm;
+    float e[3];
+    float D2;               // D^2 (adjoint)
+    float* grad;            // N x 6 (adjoint)
+    float* value;           // N (adjoint, optional)
+};
+
+cudaError_t mstep_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s);
+cudaError_t grad_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s);
+cudaError_t axis_angle_run(const float* w, const float* R0, float* R, float* JlT, int N, cudaStream_t s);
+
 }  // namespace laue

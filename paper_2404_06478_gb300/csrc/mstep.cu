@@ -1,0 +1,605 @@
+// mstep.cu — M-step of Sinkhorn-EM (paper Section "The M-step updates",
+// Appendix "M-steps for grain position and rotation", Algorithms
+// LauePosNewton, LaueRotMM and Wahba).
+//
+// The plan is never stored: Q_ij = 2^(F_i + G_j - K e2_ij) is recomputed from
+// the E-step potentials and the E-step rays/centres of the model list (the
+// pair-interleaved workspace copies made by the Sinkhorn pack kernel), pairs
+// with Q_ij < 2^-40 are skipped, and the geometric terms use the current
+// positions.  Per model spot a pass over its angle block accumulates, in
+// registers:
+//   Newton  g_c = sum_i Q (-(r - (rhat.r) rhat) / tau)
+//           H_c = sum_i Q (3 (rhat.r) rhat rhat^T - rhat r^T - r rhat^T - (rhat.r) I) / tau^2
+//           (exact gradient / Hessian of sum Q rhat.r w.r.t. c = Gamma_t x)
+//   MM      v_j = sum_i Q rhat_ij
+// Per-grain kernels then reduce the spots of a grain in a fixed order (angle
+// by angle through a (t, n) segment table), solve the regularised Newton step
+// x <- x - (H - iota I)^-1 g, iota = max(0, lmax(H) + hreg |H|_F), and run the
+// majorisation-minimisation on R with M0_m = -sum Gamma^T (v e^T + e v^T) Gamma,
+// M_m = M0_m + max(0, -lmin(M0_m)) I and R <- Wahba(M_m R w_m, w_m): the Wahba
+// step maximises tr(R^T B), B = sum a b^T, through the top eigenvector of
+// Horn's 4x4 symmetric matrix (a unit quaternion).
+#include "pairs.cuh"
+
+namespace laue {
+
+constexpr float kQSkip = -40.0f;  // log2 of the smallest plan entry kept
+
+__device__ __forceinline__ void gamma_t(float om, float& c, float& s) { sincosf(om, &s, &c); }
+
+// Gamma = [[c, 0, s], [0, 1, 0], [-s, 0, c]]: v_lab = Gamma v, Gamma^T v_lab.
+__device__ __forceinline__ void gam_apply(float c, float s, const float* v, float* o) {
+    o[0] = c * v[0] + s * v[2];
+    o[1] = v[1];
+    o[2] = -s * v[0] + c * v[2];
+}
+__device__ __forceinline__ void gamT_apply(float c, float s, const float* v, float* o) {
+    o[0] = c * v[0] - s * v[2];
+    o[1] = v[1];
+    o[2] = s * v[0] + c * v[2];
+}
+
+// Symmetric 3x3 stored as (xx, xy, xz, yy, yz, zz).
+__device__ __forceinline__ void sym_full(const float* h, float* A) {
+    A[0] = h[0]; A[1] = h[1]; A[2] = h[2];
+    A[3] = h[1]; A[4] = h[3]; A[5] = h[4];
+    A[6] = h[2]; A[7] = h[4]; A[8] = h[5];
+}
+
+// Gamma^T A Gamma for symmetric A given as 6 values.
+__device__ __forceinline__ void sym_gamT_gam(float c, float s, const float* h, float* out) {
+    float A[9], T1[9];
+    sym_full(h, A);
+    // T1 = A Gamma
+    for (int r = 0; r < 3; ++r) {
+        T1[3 * r + 0] = A[3 * r + 0] * c - A[3 * r + 2] * s;
+        T1[3 * r + 1] = A[3 * r + 1];
+        T1[3 * r + 2] = A[3 * r + 0] * s + A[3 * r + 2] * c;
+    }
+    // out = Gamma^T T1
+    float O[9];
+    for (int col = 0; col < 3; ++col) {
+        O[0 + col] = c * T1[0 + col] - s * T1[6 + col];
+        O[3 + col] = T1[3 + col];
+        O[6 + col] = s * T1[0 + col] + c * T1[6 + col];
+    }
+    out[0] = O[0]; out[1] = O[1]; out[2] = O[2]; out[3] = O[4]; out[4] = O[5]; out[5] = O[8];
+}
+
+// Cyclic Jacobi eigen-decomposition of an n x n symmetric matrix (n = 3, 4),
+// in place; V receives the eigenvectors as columns.
+template <int n>
+__device__ void jacobi(float* A, float* V) {
+    for (int a = 0; a < n * n; ++a) V[a] = (a % (n + 1) == 0) ? 1.0f : 0.0f;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        float off = 0.0f, tot = 0.0f;
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                float v = A[n * p + q] * A[n * p + q];
+                tot += v;
+                if (p != q) off += v;
+            }
+        if (off <= 1e-14f * tot || off == 0.0f) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                float apq = A[n * p + q];
+                if (apq == 0.0f) continue;
+                float theta = (A[n * q + q] - A[n * p + p]) / (2.0f * apq);
+                float t = (theta >= 0.0f ? 1.0f : -1.0f) / (fabsf(theta) + sqrtf(theta * theta + 1.0f));
+                float c = rsqrtf(t * t + 1.0f), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    float akp = A[n * k + p], akq = A[n * k + q];
+                    A[n * k + p] = c * akp - s * akq;
+                    A[n * k + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    float apk = A[n * p + k], aqk = A[n * q + k];
+                    A[n * p + k] = c * apk - s * aqk;
+                    A[n * q + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    float vkp = V[n * k + p], vkq = V[n * k + q];
+                    V[n * k + p] = c * vkp - s * vkq;
+                    V[n * k + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+// Rotation maximising tr(R^T B) (Wahba, B = sum a b^T) from the top
+// eigenvector of Horn's matrix with S = B^T.  Returns false when the top
+// eigenvalue is (nearly) degenerate, i.e. rank(B) < 2.
+__device__ bool wahba_horn(const float* B, float* R) {
+    float S[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) S[3 * a + b] = B[3 * b + a];
+    float Sxx = S[0], Sxy = S[1], Sxz = S[2], Syx = S[3], Syy = S[4], Syz = S[5], Szx = S[6], Szy = S[7],
+          Szz = S[8];
+    float Nm[16] = {Sxx + Syy + Szz, Syz - Szy,        Szx - Sxz,        Sxy - Syx,
+                    Syz - Szy,       Sxx - Syy - Szz,  Sxy + Syx,        Szx + Sxz,
+                    Szx - Sxz,       Sxy + Syx,        -Sxx + Syy - Szz, Syz + Szy,
+                    Sxy - Syx,       Szx + Sxz,        Syz + Szy,        -Sxx - Syy + Szz};
+    float V[16];
+    jacobi<4>(Nm, V);
+    int top = 0;
+    for (int k = 1; k < 4; ++k)
+        if (Nm[5 * k] > Nm[5 * top]) top = k;
+    float l1 = Nm[5 * top], l2 = -3.0e38f, scale = 0.0f;
+    for (int k = 0; k < 4; ++k) {
+        scale = fmaxf(scale, fabsf(Nm[5 * k]));
+        if (k != top) l2 = fmaxf(l2, Nm[5 * k]);
+    }
+    if (!(scale > 0.0f) || l1 - l2 <= 1e-6f * scale) return false;
+    float w = V[0 * 4 + top], x = V[1 * 4 + top], y = V[2 * 4 + top], z = V[3 * 4 + top];
+    float nq = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= nq; x *= nq; y *= nq; z *= nq;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+    return true;
+}
+
+// ------------------------------------------------------- segment table
+// seg[t (N+1) + n] = first model spot of grain n at angle t (the list is sorted
+// by (t, n, m)); seg[t (N+1) + N] = J_off[t+1].
+__global__ void ms_seg_count_kernel(MsArgs m) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m.n_model) return;
+    atomicAdd(&m.seg[m.angle[j] * (m.N + 1) + m.grain[j]], 1);
+}
+
+__global__ void ms_seg_scan_kernel(MsArgs m) {
+    int t = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    int* s = m.seg + t * (m.N + 1);
+    int acc = m.J_off[t];
+    for (int n = 0; n < m.N; ++n) {
+        int c = s[n];
+        s[n] = acc;
+        acc += c;
+    }
+    s[m.N] = acc;
+}
+
+__global__ void ms_init_kernel(MsArgs m) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= m.N) return;
+    m.gstate[4 * n + 0] = 1.0f;  // Newton still active
+    m.gstate[4 * n + 1] = 0.0f;  // last |dx|
+    m.gstate[4 * n + 2] = 0.0f;  // last |dR|_F
+}
+
+// ------------------------------------------------------------ pair pass
+// mode 0: Newton sums (9 floats in the x frame), mode 1: v_j (3 floats, lab),
+// mode 2: adjoint of the OT-weighted cost (gradient w.r.t. axis-angle and x,
+// and the spot's share of the objective; 7 floats).
+struct MsCol {
+    int j, n, t;
+    bool ok;
+    float cg, sg;
+    float c[3];   // current centre Gamma_t x_n
+    float r[3];   // E-step ray
+    float acc[9];
+};
+
+__device__ __forceinline__ void ms_pair(MsCol& C, int mode, float px, float py, float pz, float v) {
+    if (!C.ok || v < kQSkip) return;
+    float Q = ex2(v);
+    float d0 = px - C.c[0], d1 = py - C.c[1], d2 = pz - C.c[2];
+    float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+    float h0 = d0 * is, h1 = d1 * is, h2 = d2 * is;
+    if (mode == 2) {
+        // adjoint: sum Q (r - (rhat.r) rhat)/tau, sum Q (r - rhat), sum Q |rhat - r|^2
+        float rr = h0 * C.r[0] + h1 * C.r[1] + h2 * C.r[2];
+        float qs = Q * is;
+        C.acc[0] += qs * (C.r[0] - rr * h0);
+        C.acc[1] += qs * (C.r[1] - rr * h1);
+        C.acc[2] += qs * (C.r[2] - rr * h2);
+        float e0 = C.r[0] - h0, e1 = C.r[1] - h1, e2 = C.r[2] - h2;
+        C.acc[3] += Q * e0;
+        C.acc[4] += Q * e1;
+        C.acc[5] += Q * e2;
+        C.acc[6] += Q * (e0 * e0 + e1 * e1 + e2 * e2);
+        return;
+    }
+    if (mode == 1) {
+        C.acc[0] += Q * h0;
+        C.acc[1] += Q * h1;
+        C.acc[2] += Q * h2;
+        return;
+    }
+    float rr = h0 * C.r[0] + h1 * C.r[1] + h2 * C.r[2];
+    float qs = Q * is;
+    C.acc[0] -= qs * (C.r[0] - rr * h0);
+    C.acc[1] -= qs * (C.r[1] - rr * h1);
+    C.acc[2] -= qs * (C.r[2] - rr * h2);
+    float q2 = qs * is;
+    float h[3] = {h0, h1, h2};
+    int k = 3;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b) {
+            float e = 3.0f * rr * h[a] * h[b] - h[a] * C.r[b] - C.r[a] * h[b] - (a == b ? rr : 0.0f);
+            C.acc[k++] += q2 * e;
+        }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
+    const SkArgs& a = m.sk;
+    __shared__ __align__(128) Stage S;
+    init_stage(S);
+    uint32_t parity[2] = {0u, 0u};
+    const int n_tiles = a.ctrl[CTRL_N_COL_TILES];
+    const f2 K2 = dup(a.negKD2);
+    const Srcs src{{a.obsX, a.obsY, nullptr, nullptr}, 2};
+    while (true) {
+        int tile = next_tile(S, a.ctrl + CTRL_GEN_NEXT, n_tiles);
+        if (tile < 0) break;
+        int4 td = a.col_tiles[tile];
+        int t = td.x;
+        int q = td.y + threadIdx.x;
+        bool valid = (int)threadIdx.x < td.z;
+        int nj = a.J_off[t + 1] - a.J_off[t];
+        int lcol = 2 * (q - a.J2_off[t]);
+        int i0 = a.I2_off[t], ni = a.I2_off[t + 1] - i0;
+        float cg, sg;
+        gamma_t(m.omega[t], cg, sg);
+        ColPair P;
+        MsCol A, B;
+        float Ga = kNegHuge, Gb = kNegHuge;
+        A.ok = B.ok = false;
+        if (valid) {
+            load_col_pair(a, q, P);
+            float4 Y = a.modY[q];
+            float4 Z = a.modZ[q];
+            float4 W = a.modW[q];
+            Ga = Y.z;
+            Gb = Y.w;
+            for (int lane = 0; lane < 2; ++lane) {
+                MsCol& C = lane ? B : A;
+                C.ok = lcol + lane < nj;
+                if (!C.ok) continue;
+                C.j = a.J_off[t] + lcol + lane;
+                C.n = m.grain[C.j];
+                C.t = t;
+                if (MODE == 0 && m.gstate[4 * C.n] == 0.0f) C.ok = false;  // converged grain
+                gam_apply(cg, sg, m.x + 3 * C.n, C.c);
+                C.r[0] = -(lane ? Z.y : Z.x);
+                C.r[1] = -(lane ? Z.w : Z.z);
+                C.r[2] = -(lane ? W.y : W.x);
+                for (int k = 0; k < 9; ++k) C.acc[k] = 0.0f;
+            }
+        }
+        const f2 Gpa = dup(Ga), Gpb = dup(Gb);
+        bool ok = stream_tile(S, parity, src, i0, ni, [&](int st, int n, int) {
+            if (!valid) return;
+            const float4* sX = S.s[0][st];
+            const float4* sY = S.s[1][st];
+            for (int k = 0; k < n; ++k) {
+                ulonglong2 X = *(const ulonglong2*)&sX[k];
+                ulonglong2 Y = *(const ulonglong2*)&sY[k];
+                // E-step plan exponents of the 2 x 2 pairs: F_i + G_j - K e2
+                f2 va = add2(pair_v2(X.x, X.y, Y.x, P.ncxa, P.ncya, P.ncza, P.nrxa, P.nrya, P.nrza, K2, Y.y), Gpa);
+                f2 vb = add2(pair_v2(X.x, X.y, Y.x, P.ncxb, P.ncyb, P.nczb, P.nrxb, P.nryb, P.nrzb, K2, Y.y), Gpb);
+                float m4 = fmaxf(fmaxf(lo(va), hi(va)), fmaxf(lo(vb), hi(vb)));
+                if (m4 < kQSkip) continue;
+                float4 x4 = sX[k], y4 = sY[k];
+                ms_pair(A, MODE, x4.x, x4.z, y4.x, lo(va));
+                ms_pair(A, MODE, x4.y, x4.w, y4.y, hi(va));
+                ms_pair(B, MODE, x4.x, x4.z, y4.x, lo(vb));
+                ms_pair(B, MODE, x4.y, x4.w, y4.y, hi(vb));
+            }
+        });
+        if (!ok) {
+            if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
+            break;
+        }
+        if (valid) {
+            for (int lane = 0; lane < 2; ++lane) {
+                MsCol& C = lane ? B : A;
+                if (lcol + lane >= nj) continue;
+                float* o = m.jsum + 12 * (size_t)(a.J_off[t] + lcol + lane);
+                if (MODE == 2) {
+                    // per-spot gradient: x part Gamma^T dC/dc, rotation part
+                    // v x (Gamma^T y), y = -2 ((gr.u) e + (u.e) gr), u = Gamma R w_m
+                    float D2x2 = 2.0f * m.D2;
+                    float gc[3] = {D2x2 * C.acc[0], D2x2 * C.acc[1], D2x2 * C.acc[2]};
+                    float gr[3] = {D2x2 * C.acc[3], D2x2 * C.acc[4], D2x2 * C.acc[5]};
+                    float gx[3];
+                    gamT_apply(cg, sg, gc, gx);
+                    const float* Rn = m.R + 9 * C.n;
+                    float4 wd = m.w_d0[m.plane[C.j]];
+                    float v[3], u[3];
+                    for (int r = 0; r < 3; ++r) v[r] = Rn[3 * r] * wd.x + Rn[3 * r + 1] * wd.y + Rn[3 * r + 2] * wd.z;
+                    gam_apply(cg, sg, v, u);
+                    float gu = gr[0] * u[0] + gr[1] * u[1] + gr[2] * u[2];
+                    float ue = u[0] * m.e[0] + u[1] * m.e[1] + u[2] * m.e[2];
+                    float y[3], Gy[3];
+                    for (int r = 0; r < 3; ++r) y[r] = -2.0f * (gu * m.e[r] + ue * gr[r]);
+                    gamT_apply(cg, sg, y, Gy);
+                    o[0] = v[1] * Gy[2] - v[2] * Gy[1];
+                    o[1] = v[2] * Gy[0] - v[0] * Gy[2];
+                    o[2] = v[0] * Gy[1] - v[1] * Gy[0];
+                    o[3] = gx[0];
+                    o[4] = gx[1];
+                    o[5] = gx[2];
+                    o[6] = m.D2 * C.acc[6];
+                    if (!C.ok)
+                        for (int k = 0; k < 7; ++k) o[k] = 0.0f;
+                } else if (MODE == 1) {
+                    o[9] = C.ok ? C.acc[0] : 0.0f;
+                    o[10] = C.ok ? C.acc[1] : 0.0f;
+                    o[11] = C.ok ? C.acc[2] : 0.0f;
+                } else if (C.ok) {
+                    float gx[3];
+                    gamT_apply(cg, sg, C.acc, gx);
+                    float hx[6];
+                    sym_gamT_gam(cg, sg, C.acc + 3, hx);
+                    for (int k = 0; k < 3; ++k) o[k] = gx[k];
+                    for (int k = 0; k < 6; ++k) o[3 + k] = hx[k];
+                } else {
+                    for (int k = 0; k < 9; ++k) o[k] = 0.0f;
+                }
+            }
+        }
+    }
+    if (!last_cta(S, a.ctrl + CTRL_GEN_DONE)) return;
+    if (threadIdx.x == 0) {
+        a.ctrl[CTRL_GEN_NEXT] = 0;
+        a.ctrl[CTRL_GEN_DONE] = 0;
+    }
+}
+
+// ------------------------------------------------------- Newton per grain
+// One warp per grain: fixed-order reduction of the grain's spot sums, then the
+// regularised Newton step on x.
+__global__ void ms_newton_grain_kernel(MsArgs m) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= m.N) return;
+    int n = warp;
+    if (m.gstate[4 * n] == 0.0f) return;
+    float s[9];
+    for (int k = 0; k < 9; ++k) s[k] = 0.0f;
+    for (int t = lane; t < m.T; t += 32) {
+        int j0 = m.seg[t * (m.N + 1) + n], j1 = m.seg[t * (m.N + 1) + n + 1];
+        for (int j = j0; j < j1; ++j)
+            for (int k = 0; k < 9; ++k) s[k] += m.jsum[12 * (size_t)j + k];
+    }
+    for (int k = 0; k < 9; ++k)
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if (lane != 0) return;
+    float H[9], Hc[9], V[9];
+    sym_full(s + 3, H);
+    float fro = 0.0f;
+    for (int k = 0; k < 9; ++k) fro += H[k] * H[k];
+    fro = sqrtf(fro);
+    if (!(fro > 0.0f)) {
+        m.gstate[4 * n] = 0.0f;
+        return;
+    }
+    for (int k = 0; k < 9; ++k) Hc[k] = H[k];
+    jacobi<3>(Hc, V);
+    float lmax = fmaxf(Hc[0], fmaxf(Hc[4], Hc[8]));
+    float iota = fmaxf(0.0f, lmax + m.hreg * fro);
+    H[0] -= iota;
+    H[4] -= iota;
+    H[8] -= iota;
+    float det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                H[2] * (H[3] * H[7] - H[4] * H[6]);
+    if (det == 0.0f || !isfinite(det)) {
+        m.gstate[4 * n] = 0.0f;
+        return;
+    }
+    float inv[9];
+    inv[0] = (H[4] * H[8] - H[5] * H[7]) / det;
+    inv[1] = (H[2] * H[7] - H[1] * H[8]) / det;
+    inv[2] = (H[1] * H[5] - H[2] * H[4]) / det;
+    inv[3] = (H[5] * H[6] - H[3] * H[8]) / det;
+    inv[4] = (H[0] * H[8] - H[2] * H[6]) / det;
+    inv[5] = (H[2] * H[3] - H[0] * H[5]) / det;
+    inv[6] = (H[3] * H[7] - H[4] * H[6]) / det;
+    inv[7] = (H[1] * H[6] - H[0] * H[7]) / det;
+    inv[8] = (H[0] * H[4] - H[1] * H[3]) / det;
+    float dx[3];
+    for (int a = 0; a < 3; ++a) dx[a] = inv[3 * a] * s[0] + inv[3 * a + 1] * s[1] + inv[3 * a + 2] * s[2];
+    float nrm = sqrtf(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
+    for (int a = 0; a < 3; ++a) m.x[3 * n + a] -= dx[a];
+    m.gstate[4 * n + 1] = nrm;
+    if (nrm < m.tol_x) m.gstate[4 * n] = 0.0f;
+}
+
+// ----------------------------------------------------------- MM per grain
+constexpr int kMmThreads = 128;
+
+__global__ void __launch_bounds__(kMmThreads) ms_mm_grain_kernel(MsArgs m) {
+    extern __shared__ float sh[];
+    float* M6 = sh;                        // M planes x 6 (M0, then M_m)
+    float* red = sh + 6 * m.M;             // kMmThreads x 9
+    __shared__ float Rs[9];
+    __shared__ int stop;
+    int n = blockIdx.x;
+    for (int k = threadIdx.x; k < 6 * m.M; k += blockDim.x) M6[k] = 0.0f;
+    if (threadIdx.x < 9) Rs[threadIdx.x] = m.R[9 * n + threadIdx.x];
+    __syncthreads();
+    const float e[3] = {m.e[0], m.e[1], m.e[2]};
+    for (int t = 0; t < m.T; ++t) {
+        int j0 = m.seg[t * (m.N + 1) + n], j1 = m.seg[t * (m.N + 1) + n + 1];
+        float cg, sg;
+        gamma_t(m.omega[t], cg, sg);
+        for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {  // distinct planes within (t, n)
+            const float* v = m.jsum + 12 * (size_t)j + 9;
+            float A[6] = {2 * v[0] * e[0], v[0] * e[1] + e[0] * v[1], v[0] * e[2] + e[0] * v[2],
+                          2 * v[1] * e[1], v[1] * e[2] + e[1] * v[2], 2 * v[2] * e[2]};
+            float G[6];
+            sym_gamT_gam(cg, sg, A, G);
+            float* dst = M6 + 6 * m.plane[j];
+            for (int k = 0; k < 6; ++k) dst[k] -= G[k];
+        }
+        __syncthreads();
+    }
+    // shift each plane's matrix to positive semi-definite
+    for (int p = threadIdx.x; p < m.M; p += blockDim.x) {
+        float A[9], V[9];
+        sym_full(M6 + 6 * p, A);
+        jacobi<3>(A, V);
+        float lmin = fminf(A[0], fminf(A[4], A[8]));
+        float iota = lmin < 0.0f ? -lmin : 0.0f;
+        M6[6 * p + 0] += iota;
+        M6[6 * p + 3] += iota;
+        M6[6 * p + 5] += iota;
+    }
+    if (threadIdx.x == 0) stop = 0;
+    __syncthreads();
+    float last = 0.0f;
+    for (int it = 0; it < m.n_mm; ++it) {
+        float B[9];
+        for (int k = 0; k < 9; ++k) B[k] = 0.0f;
+        for (int p = threadIdx.x; p < m.M; p += blockDim.x) {
+            float4 wd = m.w_d0[p];
+            float w[3] = {wd.x, wd.y, wd.z};
+            float Rw[3], a[3], Mf[9];
+            for (int r = 0; r < 3; ++r) Rw[r] = Rs[3 * r] * w[0] + Rs[3 * r + 1] * w[1] + Rs[3 * r + 2] * w[2];
+            sym_full(M6 + 6 * p, Mf);
+            for (int r = 0; r < 3; ++r) a[r] = Mf[3 * r] * Rw[0] + Mf[3 * r + 1] * Rw[1] + Mf[3 * r + 2] * Rw[2];
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) B[3 * r + c] += a[r] * w[c];
+        }
+        for (int k = 0; k < 9; ++k) red[9 * threadIdx.x + k] = B[k];
+        __syncthreads();
+        for (int w = kMmThreads / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w)
+                for (int k = 0; k < 9; ++k) red[9 * threadIdx.x + k] += red[9 * (threadIdx.x + w) + k];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            float Rn[9];
+            if (!wahba_horn(red, Rn)) {
+                stop = 1;
+            } else {
+                float d = 0.0f;
+                for (int k = 0; k < 9; ++k) d += (Rn[k] - Rs[k]) * (Rn[k] - Rs[k]);
+                last = sqrtf(d);
+                for (int k = 0; k < 9; ++k) Rs[k] = Rn[k];
+                if (last < m.tol_R) stop = 1;
+            }
+        }
+        __syncthreads();
+        if (stop) break;
+    }
+    if (threadIdx.x < 9) m.R[9 * n + threadIdx.x] = Rs[threadIdx.x];
+    if (threadIdx.x == 0) m.gstate[4 * n + 2] = last;
+}
+
+__global__ void ms_norms_kernel(MsArgs m) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= m.N || !m.step_norms) return;
+    m.step_norms[2 * n] = m.gstate[4 * n + 1];
+    m.step_norms[2 * n + 1] = m.gstate[4 * n + 2];
+}
+
+// One warp per grain: fixed-order sum of the per-spot gradients and values.
+__global__ void ms_grad_grain_kernel(MsArgs m) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= m.N) return;
+    int n = warp;
+    float s[7];
+    for (int k = 0; k < 7; ++k) s[k] = 0.0f;
+    for (int t = lane; t < m.T; t += 32) {
+        int j0 = m.seg[t * (m.N + 1) + n], j1 = m.seg[t * (m.N + 1) + n + 1];
+        for (int j = j0; j < j1; ++j)
+            for (int k = 0; k < 7; ++k) s[k] += m.jsum[12 * (size_t)j + k];
+    }
+    for (int k = 0; k < 7; ++k)
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if (lane != 0) return;
+    for (int k = 0; k < 6; ++k) m.grad[6 * n + k] = s[k];
+    if (m.value) m.value[n] = s[6];
+}
+
+static cudaError_t seg_table(const MsArgs& m, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(m.seg, 0, sizeof(int) * (size_t)m.T * (m.N + 1), s);
+    if (e != cudaSuccess) return e;
+    if (m.n_model > 0) ms_seg_count_kernel<<<(m.n_model + 255) / 256, 256, 0, s>>>(m);
+    ms_seg_scan_kernel<<<m.T, 32, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t grad_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s) {
+    cudaError_t e = sinkhorn_prepare(m.sk, s);
+    if (e != cudaSuccess) return e;
+    if ((e = seg_table(m, s)) != cudaSuccess) return e;
+    if (m.N > 0) ms_init_kernel<<<(m.N + 255) / 256, 256, 0, s>>>(m);
+    ms_pair_kernel<2><<<l.col_grid, kTPB, 0, s>>>(m);
+    if (m.N > 0) ms_grad_grain_kernel<<<(m.N * 32 + 127) / 128, 128, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+// R = exp([w]x) R0 (Rodrigues) and, optionally, the transpose of the left
+// Jacobian of SO(3) at w, J_l(w)^T, which maps a left-perturbation gradient
+// to the gradient with respect to w:
+//   J_l(w) = I + (1 - cos th)/th^2 [w]x + (th - sin th)/th^3 [w]x^2.
+__global__ void axis_angle_kernel(const float* w, const float* R0, float* R, float* JlT, int N) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float a = w[3 * n], b = w[3 * n + 1], c = w[3 * n + 2];
+    float th2 = a * a + b * b + c * c, th = sqrtf(th2);
+    float A, B, C2;  // sin th / th, (1 - cos th)/th^2, (th - sin th)/th^3
+    if (th < 1e-4f) {
+        A = 1.0f - th2 / 6.0f;
+        B = 0.5f - th2 / 24.0f;
+        C2 = 1.0f / 6.0f - th2 / 120.0f;
+    } else {
+        float sn, cs;
+        sincosf(th, &sn, &cs);
+        A = sn / th;
+        B = (1.0f - cs) / th2;
+        C2 = (th - sn) / (th2 * th);
+    }
+    float K[9] = {0.0f, -c, b, c, 0.0f, -a, -b, a, 0.0f}, K2[9];
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q) K2[3 * r + q] = K[3 * r] * K[q] + K[3 * r + 1] * K[3 + q] + K[3 * r + 2] * K[6 + q];
+    float E[9];
+    for (int k = 0; k < 9; ++k) E[k] = (k % 4 == 0 ? 1.0f : 0.0f) + A * K[k] + B * K2[k];
+    const float* P = R0 + 9 * n;
+    for (int r = 0; r < 3; ++r)
+        for (int q = 0; q < 3; ++q)
+            R[9 * n + 3 * r + q] = E[3 * r] * P[q] + E[3 * r + 1] * P[3 + q] + E[3 * r + 2] * P[6 + q];
+    if (JlT) {
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q) {
+                float jl = (r == q ? 1.0f : 0.0f) + B * K[3 * r + q] + C2 * K2[3 * r + q];
+                JlT[9 * n + 3 * q + r] = jl;  // transpose
+            }
+    }
+}
+
+cudaError_t axis_angle_run(const float* w, const float* R0, float* R, float* JlT, int N, cudaStream_t s) {
+    if (N > 0) axis_angle_kernel<<<(N + 127) / 128, 128, 0, s>>>(w, R0, R, JlT, N);
+    return cudaGetLastError();
+}
+
+cudaError_t mstep_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s) {
+    cudaError_t e = sinkhorn_prepare(m.sk, s);  // schedule + pair-interleaved copies with F, G
+    if (e != cudaSuccess) return e;
+    if ((e = seg_table(m, s)) != cudaSuccess) return e;
+    if (m.N > 0) ms_init_kernel<<<(m.N + 255) / 256, 256, 0, s>>>(m);
+    for (int k = 0; k < m.n_newton; ++k) {
+        ms_pair_kernel<0><<<l.col_grid, kTPB, 0, s>>>(m);
+        if (m.N > 0) ms_newton_grain_kernel<<<(m.N * 32 + 127) / 128, 128, 0, s>>>(m);
+    }
+    if (m.n_mm > 0 && m.N > 0) {
+        ms_pair_kernel<1><<<l.col_grid, kTPB, 0, s>>>(m);
+        size_t shm = sizeof(float) * (6 * (size_t)m.M + 9 * kMmThreads);
+        if (shm > 48 * 1024) {
+            e = cudaFuncSetAttribute(ms_mm_grain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            if (e != cudaSuccess) return e;
+        }
+        ms_mm_grain_kernel<<<m.N, kMmThreads, shm, s>>>(m);
+    }
+    if (m.N > 0) ms_norms_kernel<<<(m.N + 255) / 256, 256, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+}  // namespace laue

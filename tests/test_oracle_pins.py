@@ -510,3 +510,28 @@ def test_single_fit_recovers_near_starts_and_filter_rejects_random(tiny):
     Rr, xr = sg.random_grains(TINY, rng)
     _, _, keep_r, unm_r = oracle.single_fit(GEOM, P, om, obs.p, obs.I_off, Rr, xr, 1.0, 20, 2.25)
     assert not keep_r.any() and unm_r.min() > 0.5
+
+
+def test_adjoint_gradient_fd_50_grains_20_rotations():
+    """The adjoint configuration (50 grains, 20 rotations): the oracle's analytic
+    gradient of sum Q C equals FP64 central differences with h = 1e-6."""
+    cfg = sg.CONFIGS["adjoint"]
+    P = oracle.reflections(cfg.a, cfg.hmax, cfg.centering)
+    rng = sg.workload_seed(cfg)
+    R, x = sg.random_grains(cfg, rng)
+    om = sg.omegas(cfg)
+    fw = oracle.forward(GEOM, P, R, x, om)
+    obs = sg.observe(GEOM, cfg, fw["t"], fw["det"], fw["spot"], rng)
+    c, r = fw["center"], fw["ray"][:, :3]
+    f, g, fd, gd, _ = oracle.sinkhorn(GEOM.D, obs.p, obs.I_off, fw["J_off"], c, r, 2.0, 2.25, 0, 0.4, 30)
+    args = (GEOM, P, om, obs.p, obs.I_off, fw["J_off"], fw["grain"], fw["plane"])
+    G = oracle.grain_grad(*args, f, g, 2.0, R, x)
+    h = 1e-6
+    FD = np.zeros_like(G)
+    for k in range(6):
+        e = np.zeros(6); e[k] = h
+        Rp = np.array([_rotvec(e[:3]) @ a for a in R]); Rm = np.array([_rotvec(-e[:3]) @ a for a in R])
+        Ep = oracle.grain_objective(*args, c, r, f, g, 2.0, Rp, x + e[3:])
+        Em = oracle.grain_objective(*args, c, r, f, g, 2.0, Rm, x - e[3:])
+        FD[:, k] = (Ep - Em) / (2 * h)
+    assert np.abs(G - FD).max() <= 1e-6 * np.abs(G).max()
