@@ -1,0 +1,126 @@
+"""Multi-grain Sinkhorn-EM driver (paper Algorithm LaueOT, Section "The LaueOT
+solver") over the C ABI, with deterministic annealing (Section "Deterministic
+annealing") and optional capture of the whole solve as one CUDA graph.
+
+Each EM step: refresh the frozen model list at the current poses
+(laue_refresh), E-step at temperature eps_k (laue_cost_sinkhorn, fixed number
+of Sinkhorn iterations from f = g = 0), M-step (laue_mstep).  A final E-step
+at the last poses gives the hard assignment.  The temperature schedule starts
+at 100 eps_final and cools geometrically to eps_final at step ceil(0.75 n_em),
+then holds.  The host only enqueues work: no step reads device data back.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import torch
+
+from . import api
+
+
+def eps_schedule(eps_final: float, n_em: int, k: int, factor: float = 100.0) -> float:
+    """eps_k = eps_final * factor^(1 - k/K) for k < K = ceil(0.75 n_em), then
+    eps_final (factor 1: no annealing)."""
+    K = int(math.ceil(0.75 * n_em))
+    if K < 1 or k >= K:
+        return float(eps_final)
+    return float(eps_final) * float(factor) ** (1.0 - k / K)
+
+
+@dataclasses.dataclass
+class EMConfig:
+    eps_final: float = 1.0
+    n_em: int = 20
+    n_sinkhorn: int = 100
+    c_out: float = 2.25
+    dust_mode: int = 0
+    unmatched_frac: float = 0.4
+    n_newton: int = 4
+    n_mm: int = 4
+    tol_x: float = 1e-6
+    tol_R: float = 1e-9
+    hreg: float = 1e-3
+    anneal_factor: float = 100.0  # eps_init / eps_final
+
+
+class EMSolver:
+    """Runs Algorithm LaueOT for fixed observed spots and a frozen model list.
+
+    R (N, 9) and x (N, 3) float32 device tensors are updated in place."""
+
+    def __init__(self, h: api.Handle, geom, lat: api.Lattice, obs: api.ObsSpots, model: api.ModelSpots,
+                 omega: torch.Tensor, cfg: EMConfig):
+        self.h, self.geom, self.lat, self.obs, self.model = h, geom, lat, obs, model
+        self.omega = omega.contiguous().float()
+        self.cfg = cfg
+        self.graph = None
+        self.out = None
+
+    def e_step(self, R, x, eps, harvest=False):
+        c = self.cfg
+        api.refresh(self.h, self.geom, self.lat, R, x, self.omega, self.model)
+        return api.cost_sinkhorn(self.h, self.geom, self.obs, self.model, eps, c.c_out, c.n_sinkhorn,
+                                 dust_mode=c.dust_mode, unmatched_frac=c.unmatched_frac, harvest=harvest)
+
+    def m_step(self, R, x, out, eps):
+        c = self.cfg
+        api.mstep(self.h, self.geom, self.lat, self.obs, self.model, out["f"], out["g"], eps, self.omega, R, x,
+                  n_newton=c.n_newton, n_mm=c.n_mm, tol_x=c.tol_x, tol_R=c.tol_R, hreg=c.hreg)
+
+    def step(self, R, x, k):
+        eps = eps_schedule(self.cfg.eps_final, self.cfg.n_em, k, self.cfg.anneal_factor)
+        out = self.e_step(R, x, eps)
+        self.m_step(R, x, out, eps)
+        return out
+
+    def _run(self, R, x):
+        for k in range(self.cfg.n_em):
+            self.step(R, x, k)
+        return self.e_step(R, x, self.cfg.eps_final, harvest=True)
+
+    def reserve(self, n_grains):
+        """Size the workspace for every call of the solve (before any capture)."""
+        h, obs, model = self.h, self.obs, self.model
+        h.reserve(obs.T, n_obs=int(obs.p.shape[0]), n_model=model.n, n_grains=int(n_grains),
+                  n_planes=int(self.lat.w_d0.shape[0]))
+
+    def run(self, R, x, use_graph=False):
+        """Full annealed solve; returns the final plan read-out (assign,
+        margin, f, g, dust)."""
+        if not use_graph:
+            return self._run(R, x)
+        if self.graph is None:
+            self.reserve(x.shape[0])
+            self._R, self._x = R, x
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    self.out = self._run(self._R, self._x)
+            torch.cuda.current_stream().wait_stream(s)
+            self.graph = g
+        if R.data_ptr() != self._R.data_ptr():
+            self._R.copy_(R)
+            self._x.copy_(x)
+        self.graph.replay()
+        if R.data_ptr() != self._R.data_ptr():
+            R.copy_(self._R)
+            x.copy_(self._x)
+        return self.out
+
+
+def step_graph(solver: EMSolver, R, x, eps):
+    """CUDA graph of one EM iteration at a fixed temperature (refresh,
+    E-step with read-out, M-step) on the tensors R, x."""
+    solver.reserve(x.shape[0])
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            out = solver.e_step(R, x, eps, harvest=True)
+            solver.m_step(R, x, out, eps)
+    torch.cuda.current_stream().wait_stream(s)
+    return g, out
