@@ -142,7 +142,19 @@ typedef struct {
     int n_model;
     int n_grains;
     int n_planes;
+    int n_starts; /* nonzero when laue_single_fit will run */
 } LaueProblemDims;
+
+/* Single-grain fit parameters (paper Appendix "Single-grain fitting",
+ * Algorithm SingleLaueOT; filter f_out of Section "Selection of Prototypes
+ * with Optimal Transport"). */
+typedef struct {
+    float eps_final; /* final temperature; eps anneals from 100 eps_final */
+    float c_out;
+    float f_out;     /* keep a fit when #unmatched rays < f_out |J| */
+    int k_max;       /* annealed EM steps per start */
+    LaueMParams mstep;
+} LaueSingleParams;
 
 /* ---- handle and workspace --------------------------------------------- */
 
@@ -258,6 +270,24 @@ int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, const LaueLatt
  * Asynchronous. */
 int laue_axis_angle(laue_handle* h, const float* w, const float* R0, float* R, float* JlT, int N,
                     void* stream);
+
+/* Batched single-grain fitting (paper Section "Single-grain fitting",
+ * Appendix "Single-grain fitting", Eq. elbo_single, Algorithm SingleLaueOT)
+ * from S starts (startR S x 9, startX S x 3): per start, the model spots
+ * visible at the start pose are listed and frozen; k_max annealed EM steps
+ * with the row-normalised E-step Q_ij = exp(-C_ij/eps) / (sum_j' exp(-C_ij'/eps)
+ * + exp(-c_out/eps)) over the grain's spots at t_i, each followed by
+ * mstep.n_newton Newton and mstep.n_mm MM steps.  Filter at the final pose: a
+ * ray is unmatched when its column mass sum_i Q_ij at eps_final is < 0.5;
+ * keep[s] = 1 when #unmatched < f_out |J| and |J| > 0.  Outputs (device):
+ * R_out (S x 9), x_out (S x 3), keep (S, int), unmatched (S, fraction,
+ * optional).  A start with more than 2048 visible spots is fitted on the first
+ * 2048 only, not kept, and sets LAUE_ERR_CAPACITY in the status word.
+ * Needs the workspace sized with n_starts > 0.  Asynchronous. */
+int laue_single_fit(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                    const LaueObsSpots* obs, const float* omega, const float* startR,
+                    const float* startX, int S, const LaueSingleParams* prm, float* R_out,
+                    float* x_out, int* keep, float* unmatched, void* stream);
 
 /* SPOT prototype selection (paper Section "Selection of Prototypes with
  * Optimal Transport", Appendix "Selection of prototypes", Algorithm

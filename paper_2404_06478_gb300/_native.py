@@ -56,7 +56,11 @@ class LaueMParams(ctypes.Structure):
 
 
 class LaueProblemDims(ctypes.Structure):
-    _fields_ = [("T", _i), ("n_obs", _i), ("n_model", _i), ("n_grains", _i), ("n_planes", _i)]
+    _fields_ = [("T", _i), ("n_obs", _i), ("n_model", _i), ("n_grains", _i), ("n_planes", _i), ("n_starts", _i)]
+
+
+class LaueSingleParams(ctypes.Structure):
+    _fields_ = [("eps_final", _f), ("c_out", _f), ("f_out", _f), ("k_max", _i), ("mstep", LaueMParams)]
 
 
 class LaueIndexParams(ctypes.Structure):
@@ -86,6 +90,8 @@ SIGNATURES = {
     "laue_objective_grad": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots),
                             _vp, _vp, _f, _vp, _vp, _vp, _i, _vp, _vp, _vp],
     "laue_axis_angle": [_vp, _vp, _vp, _vp, _vp, _i, _vp],
+    "laue_single_fit": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
+                        _P(LaueSingleParams), _vp, _vp, _vp, _vp, _vp],
     "laue_prototype_select": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                               _f, _f, _i, _vp, _vp, _pi, _vp],
     "laue_index": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,

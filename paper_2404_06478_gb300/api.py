@@ -193,14 +193,14 @@ class Handle:
             raise LaueError(rc, (what + ": " if what else "") + (msg.decode() if msg else ""))
         return rc
 
-    def workspace_size(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0) -> int:
-        d = N.LaueProblemDims(T, n_obs, n_model, n_grains, n_planes)
+    def workspace_size(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0, n_starts=0) -> int:
+        d = N.LaueProblemDims(T, n_obs, n_model, n_grains, n_planes, n_starts)
         b = ctypes.c_size_t()
         self.check(self.L.laue_workspace_size(self.h, ctypes.byref(d), ctypes.byref(b)), "workspace_size")
         return b.value
 
-    def reserve(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0, stream=None):
-        need = self.workspace_size(T, n_obs, n_model, n_grains, n_planes)
+    def reserve(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0, n_starts=0, stream=None):
+        need = self.workspace_size(T, n_obs, n_model, n_grains, n_planes, n_starts)
         if self.ws is None or self.ws.numel() < need:
             self.ws = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
             self.check(self.L.laue_set_workspace(self.h, _ptr(self.ws), self.ws.numel(), _stream(stream)),
@@ -341,3 +341,23 @@ def axis_angle(h: Handle, w, R0, with_jacobian=False, stream=None):
     h.check(h.L.laue_axis_angle(h.h, _ptr(w.contiguous()), _ptr(R0.reshape(-1, 9).contiguous()), _ptr(R),
                                 _ptr(J), N_, _stream(stream)), "laue_axis_angle")
     return (R[:N_], J[:N_]) if with_jacobian else R[:N_]
+
+
+def single_fit(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, R0, x0, eps_final, k_max, c_out,
+               f_out=0.1, n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, stream=None):
+    """laue_single_fit: (R (S, 9), x (S, 3), keep (S,) bool, unmatched (S,))."""
+    R0 = R0.reshape(-1, 9).contiguous().float()
+    x0 = x0.reshape(-1, 3).contiguous().float()
+    S = int(R0.shape[0])
+    h.reserve(obs.T, n_obs=int(obs.p.shape[0]), n_planes=int(lat.w_d0.shape[0]), n_starts=S, stream=stream)
+    Ro = torch.empty(max(S, 1), 9, device=R0.device)
+    xo = torch.empty(max(S, 1), 3, device=R0.device)
+    keep = torch.empty(max(S, 1), dtype=torch.int32, device=R0.device)
+    unm = torch.empty(max(S, 1), device=R0.device)
+    prm = N.LaueSingleParams(float(eps_final), float(c_out), float(f_out), int(k_max),
+                             mparams(eps_final, n_newton, n_mm, tol_x, tol_R, hreg))
+    g_s, o_s, l_s = geometry_struct(geom), obs.struct(), lat.struct()
+    h.check(h.L.laue_single_fit(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), _ptr(omega), _ptr(R0),
+                                _ptr(x0), S, ctypes.byref(prm), _ptr(Ro), _ptr(xo), _ptr(keep), _ptr(unm),
+                                _stream(stream)), "laue_single_fit")
+    return Ro[:S], xo[:S], keep[:S].bool(), unm[:S]

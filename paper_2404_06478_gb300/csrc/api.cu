@@ -85,7 +85,7 @@ int laue_check_model(laue_handle* h, const LaueModelSpots* m) {
 }
 
 int laue_need_ws(laue_handle* h, const LaueProblemDims& d, Layout* L) {
-    *L = make_layout(d);
+    *L = make_layout(d, h->sm_count);
     if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set (laue_set_workspace)");
     if (L->total > h->ws_bytes)
         return laue_fail(h, LAUE_ERR_WORKSPACE, "workspace too small: need %zu bytes, have %zu", L->total,
@@ -132,7 +132,7 @@ extern "C" int laue_workspace_size(laue_handle* h, const LaueProblemDims* dims, 
     if (!h || !dims || !bytes) return laue_fail(h, LAUE_ERR_INVALID_ARG, "null argument");
     if (dims->T < 0 || dims->n_obs < 0 || dims->n_model < 0 || dims->n_grains < 0 || dims->n_planes < 0)
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "negative dimension");
-    *bytes = make_layout(*dims).total;
+    *bytes = make_layout(*dims, h->sm_count).total;
     return LAUE_OK;
 }
 
@@ -258,7 +258,7 @@ extern "C" int laue_forward(laue_handle* h, const LaueGeometry* geom, const Laue
                               !out->spot || !aligned16(out->ray) || !aligned16(out->center) ||
                               !aligned16(out->spot)))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "forward: output arrays NULL or misaligned");
-    LaueProblemDims d{T, 0, 0, N, lat->M};
+    LaueProblemDims d{T, 0, 0, N, lat->M, 0};
     Layout L;
     if ((rc = laue_need_ws(h, d, &L))) return rc;
     char* ws = (char*)h->ws;
@@ -393,7 +393,7 @@ extern "C" int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, cons
     if ((obs->n > 0 && !f) || (model->n > 0 && !g))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "f and g outputs are required");
     if (prm->warm_start && !dust) return laue_fail(h, LAUE_ERR_INVALID_ARG, "warm start needs dust");
-    LaueProblemDims d{obs->T, obs->n, model->n, 0, 0};
+    LaueProblemDims d{obs->T, obs->n, model->n, 0, 0, 0};
     Layout L;
     if ((rc = laue_need_ws(h, d, &L))) return rc;
     SkArgs a;
@@ -429,7 +429,7 @@ extern "C" int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLa
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "lattice: M >= 1 and aligned w_d0");
     if (N < 0 || (N > 0 && (!R || !x)) || !omega || (obs->n > 0 && !f) || (model->n > 0 && !g))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "M-step: NULL array or N < 0");
-    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M};
+    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M, 0};
     Layout L;
     if ((rc = laue_need_ws(h, d, &L))) return rc;
     MsArgs m{};
@@ -482,7 +482,7 @@ extern "C" int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, con
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "lattice: M >= 1 and aligned w_d0");
     if (N < 0 || (N > 0 && (!R || !x || !grad)) || !omega || (obs->n > 0 && !f) || (model->n > 0 && !g))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "objective_grad: NULL array or N < 0");
-    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M};
+    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M, 0};
     Layout L;
     if ((rc = laue_need_ws(h, d, &L))) return rc;
     MsArgs m{};
@@ -521,6 +521,59 @@ extern "C" int laue_axis_angle(laue_handle* h, const float* w, const float* R0, 
     if (!h) return LAUE_ERR_INVALID_ARG;
     if (N < 0 || (N > 0 && (!w || !R0 || !R))) return laue_fail(h, LAUE_ERR_INVALID_ARG, "axis_angle: bad arguments");
     return laue_cuda_check(h, axis_angle_run(w, R0, R, JlT, N, (cudaStream_t)stream), "axis_angle launch");
+}
+
+extern "C" int laue_single_fit(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                               const LaueObsSpots* obs, const float* omega, const float* startR,
+                               const float* startX, int S, const LaueSingleParams* prm, float* R_out,
+                               float* x_out, int* keep, float* unmatched, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = laue_check_geom(h, geom))) return rc;
+    if ((rc = laue_check_obs(h, obs))) return rc;
+    if (obs->T > kSfMaxT) return laue_fail(h, LAUE_ERR_INVALID_ARG, "single fit supports at most %d angles", kSfMaxT);
+    if (!lat || lat->M < 1 || lat->M > 65535 || !lat->w_d0 || !lat->nharm || !aligned16(lat->w_d0))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "lattice: 1 <= M <= 65535 and aligned w_d0");
+    if (!prm || !(prm->eps_final > 0.0f) || prm->k_max < 0 || prm->mstep.n_newton < 0 || prm->mstep.n_mm < 0)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "single-fit params: eps_final > 0, k_max >= 0");
+    if (S < 0 || (S > 0 && (!startR || !startX || !R_out || !x_out || !keep)) || !omega)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "single fit: NULL array or S < 0");
+    LaueProblemDims d{obs->T, obs->n, 0, 0, lat->M, 1};
+    Layout L;
+    if ((rc = laue_need_ws(h, d, &L))) return rc;
+    char* ws = (char*)h->ws;
+    SfArgs a{};
+    a.G = laue_geom_dev(*geom);
+    a.w_d0 = (const float4*)lat->w_d0;
+    a.nharm = lat->nharm;
+    a.M = lat->M;
+    a.omega = omega;
+    a.T = obs->T;
+    a.I_off = obs->I_off;
+    a.p = (const float4*)obs->p;
+    a.R0 = startR;
+    a.x0 = startX;
+    a.S = S;
+    a.R_out = R_out;
+    a.x_out = x_out;
+    a.keep = keep;
+    a.unmatched = unmatched;
+    a.eps_final = prm->eps_final;
+    a.c_out = prm->c_out;
+    a.f_out = prm->f_out;
+    a.tol_x = prm->mstep.tol_x;
+    a.tol_R = prm->mstep.tol_R;
+    a.hreg = prm->mstep.hreg;
+    a.k_max = prm->k_max;
+    a.n_newton = prm->mstep.n_newton;
+    a.n_mm = prm->mstep.n_mm;
+    a.scratch = (float*)(ws + L.sfs);
+    a.cap = kSfCap;
+    a.icap = kSfIcap;
+    a.ctrl = (int*)(ws + L.ctrl);
+    a.queue = a.ctrl + CTRL_SF_NEXT;
+    int ctas = h->sm_count * kSfCtasPerSm;
+    return laue_cuda_check(h, single_fit_run(a, ctas, (cudaStream_t)stream), "single fit launch");
 }
 
 extern "C" int laue_prototype_select(laue_handle* h, const LaueGeometry*, const LaueLattice*,

@@ -27,6 +27,8 @@ enum CtrlSlot {
     CTRL_HCOL_DONE = 11,
     CTRL_GEN_NEXT = 12,   // generic queue / ticket pair for other passes
     CTRL_GEN_DONE = 13,
+    CTRL_SF_NEXT = 14,    // single-grain fit start queue / ticket
+    CTRL_SF_DONE = 15,
     CTRL_SLOTS = 64
 };
 
@@ -47,7 +49,8 @@ struct Layout {
     size_t fwd_blocks;            // int per forward block (count, then offset)
     size_t jsum;                  // float per model spot x 12 (M-step sums)
     size_t gsum;                  // float per grain x 16
-    size_t gidx;                  // int: grain CSR offsets + spot lists
+    size_t gidx;                  // int: (t, grain) segment table
+    size_t sfs;                   // float: per-CTA scratch of the single-grain fits
     size_t total;
     int max_row_tiles, max_col_tiles, max_fwd_blocks;
     int max_obs_pairs, max_mod_pairs;
@@ -58,7 +61,7 @@ constexpr int kFwdBlock = 256;    // rays per forward block
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-inline Layout make_layout(const LaueProblemDims& d) {
+inline Layout make_layout(const LaueProblemDims& d, int sm_count) {
     Layout L{};
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -92,6 +95,9 @@ inline Layout make_layout(const LaueProblemDims& d) {
     L.jsum = take(sizeof(float) * 12 * (size_t)(d.n_model + 1));
     L.gsum = take(sizeof(float) * 16 * (size_t)(d.n_grains + 1));
     L.gidx = take(sizeof(int) * ((size_t)T * (d.n_grains + 1) + 16));
+    // single-grain fits: 10 floats per listed spot + cached row normalisers, per CTA
+    size_t sf_ctas = d.n_starts > 0 ? (size_t)sm_count * 4 : 0;
+    L.sfs = take(sizeof(float) * ((size_t)2048 * 10 + 4096) * sf_ctas);
     L.total = off;
     return L;
 }

@@ -136,6 +136,39 @@ struct MsArgs {
 };
 
 cudaError_t mstep_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s);
+
+// ------------------------------------------------------- single-grain fits
+constexpr int kSfMaxT = 1024;       // angles a fit supports
+constexpr int kSfCtasPerSm = 4;
+constexpr int kSfCap = 2048;        // listed spots per start
+constexpr int kSfIcap = 4096;       // cached row normalisers per angle block
+
+struct SfArgs {
+    GeomDev G;
+    const float4* w_d0;
+    const int* nharm;
+    int M;
+    const float* omega;
+    int T;
+    const int* I_off;
+    const float4* p;
+    const float* R0;
+    const float* x0;
+    int S;
+    float* R_out;
+    float* x_out;
+    int* keep;
+    float* unmatched;
+    float eps_final, c_out, f_out, tol_x, tol_R, hreg;
+    int k_max, n_newton, n_mm;
+    float* scratch;
+    int cap, icap;
+    int* queue;  // 2 ints: start queue head, completion ticket
+    int* ctrl;
+};
+
+size_t single_fit_scratch_floats(int cap, int icap, int ctas);
+cudaError_t single_fit_run(const SfArgs& a, int ctas, cudaStream_t s);
 cudaError_t grad_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s);
 cudaError_t axis_angle_run(const float* w, const float* R0, float* R, float* JlT, int N, cudaStream_t s);
 
