@@ -142,7 +142,9 @@ typedef struct {
     int n_model;
     int n_grains;
     int n_planes;
-    int n_starts; /* nonzero when laue_single_fit will run */
+    int n_starts;     /* nonzero when laue_single_fit will run */
+    int n_candidates; /* candidates of laue_prototype_select (its sparse matrix
+                         uses the workspace beyond laue_workspace_size) */
 } LaueProblemDims;
 
 /* Single-grain fit parameters (paper Appendix "Single-grain fitting",
@@ -290,17 +292,25 @@ int laue_single_fit(laue_handle* h, const LaueGeometry* geom, const LaueLattice*
                     float* x_out, int* keep, float* unmatched, void* stream);
 
 /* SPOT prototype selection (paper Section "Selection of Prototypes with
- * Optimal Transport", Appendix "Selection of prototypes", Algorithm
- * LaueSpotGreedy): candidate grains (candR Nc x 9, candX Nc x 3) make their
- * spots; Lbar_in = max(0, LSE_{j of n at t_i}(-C_ij/eps_s) + c_out/eps_s);
- * greedy facility-location selection of k_max prototypes (ties to the lowest
- * index); order (k_max), gains (k_max increments), *k_star_host = argmax over
- * 2 <= k <= K of Delta_k - Delta_{k+1} (Delta_{K+1} = 0).  Synchronises
- * `stream` to return *k_star_host. */
+ * Optimal Transport", Appendix "Selection of prototypes", Eqs.
+ * prototype_function, prototype_loss, spot_ngrains, Algorithm LaueSpotGreedy):
+ * candidate grains (candR Nc x 9, candX Nc x 3) make their spots (same cut as
+ * laue_forward); the grain-to-spot matrix, read as the gain over the outlier
+ * baseline, Lbar_in = max(0, LSE_{j of n at t_i}(-C_ij/eps_s) + c_out/eps_s), is
+ * built sparse by candidate; greedy facility-location selection of k_max
+ * prototypes maximising f(S) = sum_i max_{n in S} Lbar_in (ties to the lowest
+ * index); order (k_max, device, -1 once no candidate is left), gains (k_max,
+ * device: the increments Delta_k), *k_star_host = argmax over 2 <= k <= K of
+ * Delta_k - Delta_{k+1} with Delta_{K+1} = 0 (K = k_max; k* = K when K < 2).
+ * The sparse matrix (8 bytes per nonzero) lives in the workspace beyond
+ * laue_workspace_size (with n_candidates = Nc); *nnz_host (optional) receives
+ * its nonzero count, and LAUE_ERR_CAPACITY is returned when it does not fit.
+ * Synchronises `stream`. */
 int laue_prototype_select(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
                           const LaueObsSpots* obs, const float* omega, const float* candR,
                           const float* candX, int Nc, float eps_s, float c_out, int k_max,
-                          int* order, float* gains, int* k_star_host, void* stream);
+                          int* order, float* gains, int* k_star_host, long long* nnz_host,
+                          void* stream);
 
 /* End-to-end indexing (paper Algorithm LaueOT preceded by the pre-processing
  * of Section "Pre-processing"): candidate fits from the start grid (startR

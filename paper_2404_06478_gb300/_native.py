@@ -56,7 +56,8 @@ class LaueMParams(ctypes.Structure):
 
 
 class LaueProblemDims(ctypes.Structure):
-    _fields_ = [("T", _i), ("n_obs", _i), ("n_model", _i), ("n_grains", _i), ("n_planes", _i), ("n_starts", _i)]
+    _fields_ = [("T", _i), ("n_obs", _i), ("n_model", _i), ("n_grains", _i), ("n_planes", _i), ("n_starts", _i),
+                ("n_candidates", _i)]
 
 
 class LaueSingleParams(ctypes.Structure):
@@ -93,7 +94,7 @@ SIGNATURES = {
     "laue_single_fit": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                         _P(LaueSingleParams), _vp, _vp, _vp, _vp, _vp],
     "laue_prototype_select": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
-                              _f, _f, _i, _vp, _vp, _pi, _vp],
+                              _f, _f, _i, _vp, _vp, _pi, _P(ctypes.c_longlong), _vp],
     "laue_index": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                    _P(LaueIndexParams), _vp, _vp, _i, _pi, _vp, _vp],
 }

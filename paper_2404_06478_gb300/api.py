@@ -193,14 +193,15 @@ class Handle:
             raise LaueError(rc, (what + ": " if what else "") + (msg.decode() if msg else ""))
         return rc
 
-    def workspace_size(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0, n_starts=0) -> int:
-        d = N.LaueProblemDims(T, n_obs, n_model, n_grains, n_planes, n_starts)
+    def workspace_size(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0, n_starts=0, n_candidates=0) -> int:
+        d = N.LaueProblemDims(T, n_obs, n_model, n_grains, n_planes, n_starts, n_candidates)
         b = ctypes.c_size_t()
         self.check(self.L.laue_workspace_size(self.h, ctypes.byref(d), ctypes.byref(b)), "workspace_size")
         return b.value
 
-    def reserve(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0, n_starts=0, stream=None):
-        need = self.workspace_size(T, n_obs, n_model, n_grains, n_planes, n_starts)
+    def reserve(self, T, n_obs=0, n_model=0, n_grains=0, n_planes=0, n_starts=0, n_candidates=0, extra=0,
+                stream=None):
+        need = self.workspace_size(T, n_obs, n_model, n_grains, n_planes, n_starts, n_candidates) + int(extra)
         if self.ws is None or self.ws.numel() < need:
             self.ws = torch.empty(need + 256, dtype=torch.uint8, device=self.device)
             self.check(self.L.laue_set_workspace(self.h, _ptr(self.ws), self.ws.numel(), _stream(stream)),
@@ -361,3 +362,30 @@ def single_fit(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, R0, x0, eps_
                                 _ptr(x0), S, ctypes.byref(prm), _ptr(Ro), _ptr(xo), _ptr(keep), _ptr(unm),
                                 _stream(stream)), "laue_single_fit")
     return Ro[:S], xo[:S], keep[:S].bool(), unm[:S]
+
+
+def prototype_select(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, candR, candX, eps_s, c_out, k_max,
+                     stream=None):
+    """laue_prototype_select: (order (k_max,) int32, gains (k_max,), k_star)."""
+    candR = candR.reshape(-1, 9).contiguous().float()
+    candX = candX.reshape(-1, 3).contiguous().float()
+    Nc = int(candR.shape[0])
+    dev = candR.device
+    order = torch.empty(max(k_max, 1), dtype=torch.int32, device=dev)
+    gains = torch.empty(max(k_max, 1), device=dev)
+    extra = 1 << 20
+    for attempt in range(3):
+        h.reserve(obs.T, n_obs=int(obs.p.shape[0]), n_planes=int(lat.w_d0.shape[0]), n_starts=1,
+                  n_candidates=max(Nc, 1), extra=extra, stream=stream)
+        ks = ctypes.c_int(0)
+        nnz = ctypes.c_longlong(0)
+        g_s, o_s, l_s = geometry_struct(geom), obs.struct(), lat.struct()
+        rc = h.L.laue_prototype_select(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), _ptr(omega),
+                                       _ptr(candR), _ptr(candX), Nc, float(eps_s), float(c_out), int(k_max),
+                                       _ptr(order), _ptr(gains), ctypes.byref(ks), ctypes.byref(nnz), _stream(stream))
+        if rc == N.LAUE_ERR_CAPACITY and nnz.value > 0:
+            extra = 8 * nnz.value + (1 << 20)
+            continue
+        h.check(rc, "laue_prototype_select")
+        return order[:k_max], gains[:k_max], ks.value
+    h.check(rc, "laue_prototype_select")

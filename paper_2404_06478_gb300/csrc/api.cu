@@ -258,7 +258,7 @@ extern "C" int laue_forward(laue_handle* h, const LaueGeometry* geom, const Laue
                               !out->spot || !aligned16(out->ray) || !aligned16(out->center) ||
                               !aligned16(out->spot)))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "forward: output arrays NULL or misaligned");
-    LaueProblemDims d{T, 0, 0, N, lat->M, 0};
+    LaueProblemDims d{T, 0, 0, N, lat->M, 0, 0};
     Layout L;
     if ((rc = laue_need_ws(h, d, &L))) return rc;
     char* ws = (char*)h->ws;
@@ -393,7 +393,7 @@ extern "C" int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, cons
     if ((obs->n > 0 && !f) || (model->n > 0 && !g))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "f and g outputs are required");
     if (prm->warm_start && !dust) return laue_fail(h, LAUE_ERR_INVALID_ARG, "warm start needs dust");
-    LaueProblemDims d{obs->T, obs->n, model->n, 0, 0, 0};
+    LaueProblemDims d{obs->T, obs->n, model->n, 0, 0, 0, 0};
     Layout L;
     if ((rc = laue_need_ws(h, d, &L))) return rc;
     SkArgs a;
@@ -429,7 +429,7 @@ extern "C" int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLa
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "lattice: M >= 1 and aligned w_d0");
     if (N < 0 || (N > 0 && (!R || !x)) || !omega || (obs->n > 0 && !f) || (model->n > 0 && !g))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "M-step: NULL array or N < 0");
-    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M, 0};
+    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M, 0, 0};
     Layout L;
     if ((rc = laue_need_ws(h, d, &L))) return rc;
     MsArgs m{};
@@ -482,7 +482,7 @@ extern "C" int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, con
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "lattice: M >= 1 and aligned w_d0");
     if (N < 0 || (N > 0 && (!R || !x || !grad)) || !omega || (obs->n > 0 && !f) || (model->n > 0 && !g))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "objective_grad: NULL array or N < 0");
-    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M, 0};
+    LaueProblemDims d{obs->T, obs->n, model->n, N, lat->M, 0, 0};
     Layout L;
     if ((rc = laue_need_ws(h, d, &L))) return rc;
     MsArgs m{};
@@ -538,7 +538,7 @@ extern "C" int laue_single_fit(laue_handle* h, const LaueGeometry* geom, const L
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "single-fit params: eps_final > 0, k_max >= 0");
     if (S < 0 || (S > 0 && (!startR || !startX || !R_out || !x_out || !keep)) || !omega)
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "single fit: NULL array or S < 0");
-    LaueProblemDims d{obs->T, obs->n, 0, 0, lat->M, 1};
+    LaueProblemDims d{obs->T, obs->n, 0, 0, lat->M, 1, 0};
     Layout L;
     if ((rc = laue_need_ws(h, d, &L))) return rc;
     char* ws = (char*)h->ws;
@@ -576,10 +576,89 @@ extern "C" int laue_single_fit(laue_handle* h, const LaueGeometry* geom, const L
     return laue_cuda_check(h, single_fit_run(a, ctas, (cudaStream_t)stream), "single fit launch");
 }
 
-extern "C" int laue_prototype_select(laue_handle* h, const LaueGeometry*, const LaueLattice*,
-                                     const LaueObsSpots*, const float*, const float*, const float*, int, float,
-                                     float, int, int*, float*, int*, void*) {
-    return laue_fail(h, LAUE_ERR_UNIMPLEMENTED, "laue_prototype_select is not built yet");
+static SfArgs fill_sf(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const LaueObsSpots* obs,
+                      const float* omega, const float* R, const float* x, int S, float c_out, const Layout& L) {
+    char* ws = (char*)h->ws;
+    SfArgs a{};
+    a.G = laue_geom_dev(*geom);
+    a.w_d0 = (const float4*)lat->w_d0;
+    a.nharm = lat->nharm;
+    a.M = lat->M;
+    a.omega = omega;
+    a.T = obs->T;
+    a.I_off = obs->I_off;
+    a.p = (const float4*)obs->p;
+    a.R0 = R;
+    a.x0 = x;
+    a.S = S;
+    a.c_out = c_out;
+    a.scratch = (float*)(ws + L.sfs);
+    a.cap = kSfCap;
+    a.icap = kSfIcap;
+    a.ctrl = (int*)(ws + L.ctrl);
+    a.queue = a.ctrl + CTRL_SF_NEXT;
+    return a;
+}
+
+extern "C" int laue_prototype_select(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                                     const LaueObsSpots* obs, const float* omega, const float* candR,
+                                     const float* candX, int Nc, float eps_s, float c_out, int k_max, int* order,
+                                     float* gains, int* k_star_host, long long* nnz_host, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = laue_check_geom(h, geom))) return rc;
+    if ((rc = laue_check_obs(h, obs))) return rc;
+    if (obs->T > kSfMaxT) return laue_fail(h, LAUE_ERR_INVALID_ARG, "at most %d angles", kSfMaxT);
+    if (!lat || lat->M < 1 || lat->M > 65535 || !lat->w_d0 || !lat->nharm || !aligned16(lat->w_d0))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "lattice: 1 <= M <= 65535 and aligned w_d0");
+    if (Nc < 0 || k_max < 0 || (Nc > 0 && (!candR || !candX)) || (k_max > 0 && (!order || !gains)) ||
+        !k_star_host || !omega || !(eps_s > 0.0f))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "prototype_select: bad arguments");
+    LaueProblemDims d{obs->T, obs->n, 0, 0, lat->M, 1, Nc > 0 ? Nc : 1};
+    Layout L;
+    if ((rc = laue_need_ws(h, d, &L))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* ws = (char*)h->ws;
+    SfArgs a = fill_sf(h, geom, lat, obs, omega, candR, candX, Nc, c_out, L);
+    SpotArgs sp{};
+    int* ip = (int*)(ws + L.spot);
+    sp.eps_s = eps_s;
+    sp.count = ip;
+    sp.row_ptr = ip + Nc;
+    sp.chosen = sp.row_ptr + Nc + 1;
+    int blocks = h->sm_count * 4;
+    sp.part_i = sp.chosen + Nc;
+    sp.part_g = (float*)(sp.part_i + blocks);
+    sp.tick = (int*)(sp.part_g + blocks);
+    sp.cur = sp.tick + 1;
+    sp.kstar = sp.tick + 2;
+    sp.nnz_total = (long long*)(((uintptr_t)(sp.tick + 4) + 7) & ~(uintptr_t)7);
+    sp.best = (float*)(sp.nnz_total + 2);
+    int ctas = h->sm_count * kSfCtasPerSm;
+    if ((rc = laue_cuda_check(h, spot_matrix_run(a, sp, ctas, true, s), "spot count"))) return rc;
+    long long nnz = 0;
+    if ((rc = laue_cuda_check(h, cudaMemcpyAsync(&nnz, sp.nnz_total, sizeof(long long), cudaMemcpyDeviceToHost, s),
+                              "reading nnz")))
+        return rc;
+    if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "spot synchronise"))) return rc;
+    if (nnz_host) *nnz_host = nnz;
+    size_t tail = h->ws_bytes - L.total;
+    if ((size_t)nnz * 8 + 512 > tail)
+        return laue_fail(h, LAUE_ERR_CAPACITY, "prototype_select: %lld nonzeros need %zu more workspace bytes", nnz,
+                         (size_t)nnz * 8 + 512 - tail);
+    sp.col = (int*)(ws + L.total);
+    sp.val = (float*)(ws + align_up(L.total + sizeof(int) * (size_t)nnz, 256));
+    sp.order = order;
+    sp.gains = gains;
+    if ((rc = laue_cuda_check(h, spot_matrix_run(a, sp, ctas, false, s), "spot fill"))) return rc;
+    if ((rc = laue_cuda_check(h, spot_greedy_run(sp, obs->n, Nc, k_max, h->sm_count, s), "spot greedy"))) return rc;
+    int ks = 0;
+    if ((rc = laue_cuda_check(h, cudaMemcpyAsync(&ks, sp.kstar, sizeof(int), cudaMemcpyDeviceToHost, s),
+                              "reading k*")))
+        return rc;
+    if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "spot synchronise"))) return rc;
+    *k_star_host = ks;
+    return LAUE_OK;
 }
 
 extern "C" int laue_index(laue_handle* h, const LaueGeometry*, const LaueLattice*, const LaueObsSpots*,

@@ -51,6 +51,7 @@ struct Layout {
     size_t gsum;                  // float per grain x 16
     size_t gidx;                  // int: (t, grain) segment table
     size_t sfs;                   // float: per-CTA scratch of the single-grain fits
+    size_t spot;                  // SPOT: counts, row pointers, flags, partials, best
     size_t total;
     int max_row_tiles, max_col_tiles, max_fwd_blocks;
     int max_obs_pairs, max_mod_pairs;
@@ -98,6 +99,9 @@ inline Layout make_layout(const LaueProblemDims& d, int sm_count) {
     // single-grain fits: 10 floats per listed spot + cached row normalisers, per CTA
     size_t sf_ctas = d.n_starts > 0 ? (size_t)sm_count * 4 : 0;
     L.sfs = take(sizeof(float) * ((size_t)2048 * 10 + 4096) * sf_ctas);
+    L.spot = take(d.n_candidates > 0 ? sizeof(int) * (4 * (size_t)d.n_candidates + 16 + 2 * (size_t)sm_count * 4 + 64) +
+                                           sizeof(float) * (size_t)(d.n_obs + 1)
+                                     : 0);
     L.total = off;
     return L;
 }

@@ -167,7 +167,28 @@ struct SfArgs {
     int* ctrl;
 };
 
+// SPOT prototype selection
+struct SpotArgs {
+    float eps_s;
+    int* count;          // Nc
+    int* row_ptr;        // Nc + 1
+    int* col;            // nnz observed indices
+    float* val;          // nnz values
+    long long* nnz_total;
+    float* best;         // n_obs: max_{n in S} Lbar_in
+    int* chosen;         // Nc
+    float* part_g;       // per-block partial argmax
+    int* part_i;
+    int* tick;
+    int* cur;
+    int* order;          // k_max
+    float* gains;        // k_max
+    int* kstar;
+};
+
 size_t single_fit_scratch_floats(int cap, int icap, int ctas);
+cudaError_t spot_matrix_run(const SfArgs& a, const SpotArgs& sp, int ctas, bool count_only, cudaStream_t s);
+cudaError_t spot_greedy_run(const SpotArgs& sp, int n_obs, int Nc, int k_max, int sm_count, cudaStream_t s);
 cudaError_t single_fit_run(const SfArgs& a, int ctas, cudaStream_t s);
 cudaError_t grad_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s);
 cudaError_t axis_angle_run(const float* w, const float* R0, float* R, float* JlT, int N, cudaStream_t s);

@@ -401,6 +401,211 @@ __global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- SPOT
+// Appendix "Selection of prototypes" (Algorithm LaueSpotGreedy): grain-to-spot
+// matrix read as the gain over the outlier baseline,
+//   Lbar_in = max(0, LSE_{j of n at t_i}(-C_ij / eps_s) + c_out / eps_s),
+// stored sparse by candidate (CSR, rows in (t, i) order), then the greedy
+// facility-location selection f(S) = sum_i max_{n in S} Lbar_in.
+
+// One candidate per CTA.  count_only: nnz per candidate; else fill the CSR.
+__global__ void __launch_bounds__(kSfThreads) spot_matrix_kernel(SfArgs a, SpotArgs sp, int count_only) {
+    __shared__ SfShared S;
+    __shared__ int wcnt[kSfThreads / 32];
+    __shared__ int nnz;
+    SfScratch Z = sf_slice(a, blockIdx.x);
+    const float log2e = 1.4426950408889634f;
+    const float negK = -a.G.D * a.G.D * log2e / sp.eps_s, kc = a.c_out * log2e / sp.eps_s;
+    for (int n = blockIdx.x; n < a.S; n += gridDim.x) {
+        if (threadIdx.x < 9) S.R[threadIdx.x] = a.R0[9 * n + threadIdx.x];
+        if (threadIdx.x < 3) S.x[threadIdx.x] = a.x0[3 * n + threadIdx.x];
+        if (threadIdx.x == 0) nnz = 0;
+        __syncthreads();
+        sf_cut(a, S, Z);
+        if (S.overflow && threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_CAPACITY);
+        sf_refresh(a, S, Z);
+        int base = count_only ? 0 : sp.row_ptr[n];
+        for (int t = 0; t < a.T; ++t) {
+            int j0 = S.t_off[t], j1 = S.t_off[t + 1];
+            if (j0 == j1) continue;
+            for (int i0 = a.I_off[t]; i0 < a.I_off[t + 1]; i0 += blockDim.x) {
+                int i = i0 + threadIdx.x;
+                float val = 0.0f;
+                if (i < a.I_off[t + 1]) {
+                    float4 p = a.p[i];
+                    Lse2 L;
+                    L.m = kNegHuge;
+                    L.s = 0.0f;
+                    for (int j = j0; j < j1; ++j) L.merge(negK * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j), 1.0f);
+                    val = (L.value() + kc) * 0.6931471805599453f;
+                }
+                bool nz = val > 0.0f;
+                unsigned ball = __ballot_sync(0xffffffffu, nz);
+                int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+                if (lane == 0) wcnt[w] = __popc(ball);
+                __syncthreads();
+                int before = 0, total = 0;
+                for (int k = 0; k < kSfThreads / 32; ++k) {
+                    if (k < w) before += wcnt[k];
+                    total += wcnt[k];
+                }
+                if (nz && !count_only) {
+                    int pos = base + nnz + before + __popc(ball & ((1u << lane) - 1u));
+                    sp.col[pos] = i;
+                    sp.val[pos] = val;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) nnz += total;
+                __syncthreads();
+            }
+        }
+        if (count_only && threadIdx.x == 0) sp.count[n] = nnz;
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of the per-candidate counts by one CTA; row_ptr[Nc] = nnz.
+__global__ void __launch_bounds__(1024) spot_scan_kernel(SpotArgs sp, int Nc) {
+    __shared__ long long part[1024];
+    int per = (Nc + 1023) / 1024;
+    int b0 = threadIdx.x * per, b1 = min(Nc, b0 + per);
+    long long s = 0;
+    for (int b = b0; b < b1; ++b) s += sp.count[b];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int k = 0; k < 1024; ++k) {
+            long long v = part[k];
+            part[k] = acc;
+            acc += v;
+        }
+        sp.row_ptr[Nc] = (int)(acc > 0x7fffffff ? 0x7fffffff : acc);
+        sp.nnz_total[0] = acc;
+    }
+    __syncthreads();
+    long long acc = part[threadIdx.x];
+    for (int b = b0; b < b1; ++b) {
+        sp.row_ptr[b] = (int)acc;
+        acc += sp.count[b];
+    }
+}
+
+__global__ void spot_init_kernel(SpotArgs sp, int n_obs, int Nc) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n_obs) sp.best[k] = 0.0f;
+    if (k < Nc) sp.chosen[k] = 0;
+    if (k == 0) {
+        sp.tick[0] = 0;
+    }
+}
+
+// gain_n = sum over the candidate's entries of max(0, Lbar_in - best_i);
+// one warp per candidate, then a grid argmax (largest gain, lowest index).
+__global__ void __launch_bounds__(256) spot_gain_kernel(SpotArgs sp, int Nc, int step) {
+    __shared__ float bg[8];
+    __shared__ int bi[8];
+    __shared__ int last;
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    float g = -1.0f;
+    int gi = 0x7fffffff;
+    for (int n = warp; n < Nc; n += (gridDim.x * blockDim.x) >> 5) {
+        float s = 0.0f;
+        if (!sp.chosen[n]) {
+            for (int e = sp.row_ptr[n] + lane; e < sp.row_ptr[n + 1]; e += 32)
+                s += fmaxf(0.0f, sp.val[e] - sp.best[sp.col[e]]);
+        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (sp.chosen[n]) s = -1.0f;
+        if (s > g || (s == g && n < gi)) {
+            g = s;
+            gi = n;
+        }
+    }
+    // warp lanes hold identical (g, gi); reduce warps of the block
+    int w = threadIdx.x >> 5;
+    if (lane == 0) {
+        bg[w] = g;
+        bi[w] = gi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+            if (bg[k] > g || (bg[k] == g && bi[k] < gi)) {
+                g = bg[k];
+                gi = bi[k];
+            }
+        sp.part_g[blockIdx.x] = g;
+        sp.part_i[blockIdx.x] = gi;
+        __threadfence();
+        last = atomicAdd(sp.tick, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    float G = -1.0f;
+    int I = 0x7fffffff;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+        float pg = sp.part_g[b];
+        int pi = sp.part_i[b];
+        if (pg > G || (pg == G && pi < I)) {
+            G = pg;
+            I = pi;
+        }
+    }
+    if (I < Nc) {
+        sp.order[step] = I;
+        sp.gains[step] = G < 0.0f ? 0.0f : G;
+        sp.chosen[I] = 1;
+    } else {
+        sp.order[step] = -1;
+        sp.gains[step] = 0.0f;
+    }
+    sp.cur[0] = I < Nc ? I : -1;
+    sp.tick[0] = 0;
+}
+
+__global__ void spot_update_kernel(SpotArgs sp) {
+    int n = sp.cur[0];
+    if (n < 0) return;
+    for (int e = sp.row_ptr[n] + blockIdx.x * blockDim.x + threadIdx.x; e < sp.row_ptr[n + 1];
+         e += gridDim.x * blockDim.x)
+        sp.best[sp.col[e]] = fmaxf(sp.best[sp.col[e]], sp.val[e]);
+}
+
+// Eq. spot_ngrains read on the increments: k* = argmax_{2 <= k <= K}
+// Delta_k - Delta_{k+1} (Delta_{K+1} = 0), K < 2 gives K.
+__global__ void spot_kstar_kernel(SpotArgs sp, int K) {
+    int best = K < 2 ? K : 2;
+    float bv = -3.0e38f;
+    for (int k = 2; k <= K; ++k) {
+        float d = sp.gains[k - 1] - (k < K ? sp.gains[k] : 0.0f);
+        if (d > bv) {
+            bv = d;
+            best = k;
+        }
+    }
+    sp.kstar[0] = best;
+}
+
+cudaError_t spot_matrix_run(const SfArgs& a, const SpotArgs& sp, int ctas, bool count_only, cudaStream_t s) {
+    if (a.S > 0) spot_matrix_kernel<<<ctas, kSfThreads, 0, s>>>(a, sp, count_only ? 1 : 0);
+    if (count_only) spot_scan_kernel<<<1, 1024, 0, s>>>(sp, a.S);
+    return cudaGetLastError();
+}
+
+cudaError_t spot_greedy_run(const SpotArgs& sp, int n_obs, int Nc, int k_max, int sm_count, cudaStream_t s) {
+    int nmax = n_obs > Nc ? n_obs : Nc;
+    spot_init_kernel<<<(nmax + 255) / 256 + 1, 256, 0, s>>>(sp, n_obs, Nc);
+    int blocks = sm_count * 4;
+    for (int k = 0; k < k_max; ++k) {
+        spot_gain_kernel<<<blocks, 256, 0, s>>>(sp, Nc, k);
+        spot_update_kernel<<<64, 256, 0, s>>>(sp);
+    }
+    spot_kstar_kernel<<<1, 1, 0, s>>>(sp, k_max);
+    return cudaGetLastError();
+}
+
 size_t single_fit_scratch_floats(int cap, int icap, int ctas) { return ((size_t)cap * 10 + icap) * ctas; }
 
 cudaError_t single_fit_run(const SfArgs& a, int ctas, cudaStream_t s) {
