@@ -313,10 +313,17 @@ int laue_prototype_select(laue_handle* h, const LaueGeometry* geom, const LaueLa
                           void* stream);
 
 /* End-to-end indexing (paper Algorithm LaueOT preceded by the pre-processing
- * of Section "Pre-processing"): candidate fits from the start grid (startR
- * S x 9, startX S x 3) by batched single-grain fitting with the f_out filter,
- * SPOT selection, then n_em annealed EM steps.  Outputs R_out/x_out (capacity
- * n_max), *n_grains_host, assign (obs->n).  Synchronises `stream`. */
+ * of Section "Pre-processing"): batched single-grain fits from the S starts
+ * (startR S x 9, startX S x 3) with k_single annealed steps and the f_out
+ * filter (laue_single_fit); SPOT selection over the kept fits at eps_final
+ * with k_max = min(#kept, n_max) (laue_prototype_select); the model list of
+ * the k* prototypes (laue_forward); n_em annealed EM steps (eps from
+ * 100 eps_final down to eps_final at step ceil(0.75 n_em), n_sinkhorn
+ * iterations each, then laue_mstep) and a final E-step at eps_final.
+ * Outputs: R_out / x_out (capacity n_max grains), *n_grains_host = k*, and
+ * assign (obs->n): the grain of each observed spot's argmax model spot, -1
+ * for the outlier column.  Needs laue_index_workspace_size bytes.
+ * Synchronises `stream`. */
 typedef struct {
     double unmatched_frac;
     float eps_final;
@@ -324,10 +331,13 @@ typedef struct {
     float f_out;
     int n_em;
     int n_sinkhorn;
-    int k_single;  /* annealed steps of each single-grain fit */
+    int k_single; /* annealed steps of each single-grain fit */
     int dust_mode;
     LaueMParams mstep;
 } LaueIndexParams;
+
+int laue_index_workspace_size(laue_handle* h, int T, int n_obs, int S, int n_max, int n_planes,
+                              size_t* bytes);
 
 int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
                const LaueObsSpots* obs, const float* omega, const float* startR,

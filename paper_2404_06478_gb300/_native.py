@@ -95,6 +95,7 @@ SIGNATURES = {
                         _P(LaueSingleParams), _vp, _vp, _vp, _vp, _vp],
     "laue_prototype_select": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                               _f, _f, _i, _vp, _vp, _pi, _P(ctypes.c_longlong), _vp],
+    "laue_index_workspace_size": [_vp, _i, _i, _i, _i, _i, _P(ctypes.c_size_t)],
     "laue_index": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                    _P(LaueIndexParams), _vp, _vp, _i, _pi, _vp, _vp],
 }

@@ -389,3 +389,33 @@ def prototype_select(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, candR,
         h.check(rc, "laue_prototype_select")
         return order[:k_max], gains[:k_max], ks.value
     h.check(rc, "laue_prototype_select")
+
+
+def index(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, startR, startX, eps_final, c_out, n_max,
+          n_em=20, n_sinkhorn=100, k_single=20, f_out=0.1, unmatched_frac=0.4, dust_mode=0, n_newton=4, n_mm=4,
+          tol_x=1e-6, tol_R=1e-9, hreg=1e-3, stream=None):
+    """laue_index: (R (k*, 9), x (k*, 3), assign (n_obs,) grain per observed spot)."""
+    startR = startR.reshape(-1, 9).contiguous().float()
+    startX = startX.reshape(-1, 3).contiguous().float()
+    S = int(startR.shape[0])
+    dev = startR.device
+    nI = int(obs.p.shape[0])
+    b = ctypes.c_size_t()
+    h.check(h.L.laue_index_workspace_size(h.h, obs.T, nI, S, int(n_max), int(lat.w_d0.shape[0]), ctypes.byref(b)),
+            "laue_index_workspace_size")
+    if h.ws is None or h.ws.numel() < b.value:
+        h.ws = torch.empty(b.value + 256, dtype=torch.uint8, device=dev)
+        h.check(h.L.laue_set_workspace(h.h, _ptr(h.ws), h.ws.numel(), _stream(stream)), "set_workspace")
+    R = torch.empty(int(n_max), 9, device=dev)
+    x = torch.empty(int(n_max), 3, device=dev)
+    assign = torch.empty(max(nI, 1), dtype=torch.int32, device=dev)
+    prm = N.LaueIndexParams(float(unmatched_frac), float(eps_final), float(c_out), float(f_out), int(n_em),
+                            int(n_sinkhorn), int(k_single), int(dust_mode),
+                            mparams(eps_final, n_newton, n_mm, tol_x, tol_R, hreg))
+    ng = ctypes.c_int(0)
+    g_s, o_s, l_s = geometry_struct(geom), obs.struct(), lat.struct()
+    h.check(h.L.laue_index(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), _ptr(omega), _ptr(startR),
+                           _ptr(startX), S, ctypes.byref(prm), _ptr(R), _ptr(x), int(n_max), ctypes.byref(ng),
+                           _ptr(assign), _stream(stream)), "laue_index")
+    k = ng.value
+    return R[:k], x[:k], assign[:nI]

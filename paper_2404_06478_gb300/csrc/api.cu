@@ -660,9 +660,3 @@ extern "C" int laue_prototype_select(laue_handle* h, const LaueGeometry* geom, c
     *k_star_host = ks;
     return LAUE_OK;
 }
-
-extern "C" int laue_index(laue_handle* h, const LaueGeometry*, const LaueLattice*, const LaueObsSpots*,
-                          const float*, const float*, const float*, int, const LaueIndexParams*, float*, float*,
-                          int, int*, int*, void*) {
-    return laue_fail(h, LAUE_ERR_UNIMPLEMENTED, "laue_index is not built yet");
-}
