@@ -242,6 +242,35 @@ int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, const LaueObsSp
                        float* dust, int* assign, float* margin, float* marg_err, float* q,
                        void* stream);
 
+/* The same E-step as laue_cost_sinkhorn (same arguments and outputs, no
+ * handle) for callers that cannot allocate device memory: code that runs
+ * while a stream is being captured into a CUDA graph, where an allocation
+ * would break or synchronise the capture; hard real-time loops, where the
+ * implicit device synchronisation of cudaMalloc stalls the pipeline; plugins
+ * hosted by a framework that owns every device allocation.  This entry point
+ * has no counterpart in the paper.
+ *
+ * Scratch: a fixed 64 MiB array in device memory owned by this library
+ * module, reserved on every GPU where the module is loaded and held there
+ * until the process exits; the call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  It fits problems whose E-step
+ * layout (laue_workspace_size with only T, n_obs, n_model set, up to the
+ * E-step regions) is at most 64 MiB, about 1.5 million observed plus 1 million
+ * model spots; larger problems return LAUE_ERR_CAPACITY before any launch.
+ * The first call on a device looks the array's device address up (with that
+ * device current) and caches it: make that first call before any stream
+ * capture begins.  Every call on a device shares the one array, which keeps
+ * the previous call's contents (the call clears its counters and status word
+ * itself): calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Runs on the current
+ * device; `stream` must belong to it.  status (optional, one device int)
+ * receives the device status word (LAUE_OK or a LAUE_ERR_* code) in stream
+ * order.  Asynchronous. */
+int laue_cost_sinkhorn_noalloc(const LaueGeometry* geom, const LaueObsSpots* obs,
+                               const LaueModelSpots* model, const LaueOTParams* prm, float* f,
+                               float* g, float* dust, int* assign, float* margin, float* marg_err,
+                               float* q, int* status, void* stream);
+
 /* M-step (paper Section "The M-step updates", Appendix "M-steps"): with the
  * plan Q_ij = exp((f_i + g_j - C_ij)/eps) of the E-step (costs from the
  * model list's current rays and centres, which must be those of the E-step),

@@ -86,6 +86,8 @@ SIGNATURES = {
     "laue_refresh": [_vp, _P(LaueGeometry), _P(LaueLattice), _vp, _vp, _vp, _P(LaueModelSpots), _vp],
     "laue_cost_sinkhorn": [_vp, _P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams),
                            _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "laue_cost_sinkhorn_noalloc": [_P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams),
+                                   _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "laue_mstep": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots), _vp, _vp,
                    _P(LaueMParams), _vp, _vp, _vp, _i, _vp, _vp],
     "laue_objective_grad": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots),

@@ -419,3 +419,17 @@ def index(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, startR, startX, e
                            _ptr(assign), _stream(stream)), "laue_index")
     k = ng.value
     return R[:k], x[:k], assign[:nI]
+
+
+def cost_sinkhorn_noalloc(geom, obs: ObsSpots, model: ModelSpots, eps, c_out, n_iter, f, g, dust, assign=None,
+                          margin=None, marg_err=None, q=None, status=None, dust_mode=0, unmatched_frac=0.4,
+                          stream=None):
+    """laue_cost_sinkhorn_noalloc: the E-step into caller-allocated outputs,
+    with the library's fixed device scratch (no allocation by the library).
+    Returns the status code of the call."""
+    L = N.lib()
+    prm = ot_params(eps, c_out, n_iter, dust_mode, unmatched_frac, False)
+    g_s, o_s, m_s = geometry_struct(geom), obs.struct(), model.struct()
+    return L.laue_cost_sinkhorn_noalloc(ctypes.byref(g_s), ctypes.byref(o_s), ctypes.byref(m_s), ctypes.byref(prm),
+                                        _ptr(f), _ptr(g), _ptr(dust), _ptr(assign), _ptr(margin), _ptr(marg_err),
+                                        _ptr(q), _ptr(status), _stream(stream))

@@ -23,3 +23,5 @@ int laue_check_geom(laue_handle* h, const LaueGeometry* g);
 int laue_check_obs(laue_handle* h, const LaueObsSpots* o);
 int laue_check_model(laue_handle* h, const LaueModelSpots* m);
 int laue_need_ws(laue_handle* h, const LaueProblemDims& d, laue::Layout* L);
+int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* obs, const LaueModelSpots* model,
+                 const LaueOTParams* prm, const laue::Layout& L, laue::SkArgs* out, laue::SkLaunch* lc);
