@@ -41,7 +41,7 @@ struct Layout {
     size_t ctrl;
     size_t row_tiles, col_tiles;  // int4 {t, start, count, pad}
     size_t row_part, col_part;    // float2 (max, sum) per tile, log2 domain
-    size_t dust;                  // float: F0, F0n, G0, log2U, log2O (T each), errors
+    size_t dust;                  // float: F0, F0n, G0, log2U, log2O, Fmax, Gmax (T each), errors
     size_t ang;                   // int4 per angle: tile ranges of the passes
     size_t obsX, obsY;            // pair-interleaved observed spots (see sinkhorn.cu)
     size_t modX, modY, modZ, modW;// pair-interleaved model spots
@@ -80,7 +80,7 @@ inline Layout make_layout(const LaueProblemDims& d, int sm_count) {
     L.col_tiles = take(sizeof(int4) * (size_t)L.max_col_tiles);
     L.row_part = take(sizeof(float2) * (size_t)L.max_row_tiles);
     L.col_part = take(sizeof(float2) * (size_t)L.max_col_tiles);
-    L.dust = take(sizeof(float) * (size_t)(6 * T + 16));
+    L.dust = take(sizeof(float) * (size_t)(8 * T + 16));
     L.ang = take(sizeof(int4) * (size_t)T);
     size_t ip = (size_t)(d.n_obs + T + 2) / 2 + 1, jp = (size_t)(d.n_model + T + 2) / 2 + 1;
     L.max_obs_pairs = (int)ip;

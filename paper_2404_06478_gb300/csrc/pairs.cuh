@@ -15,7 +15,7 @@ constexpr int kGroup = 4;     // staged pairs per max-then-sum group
 constexpr float kPadFar = 1.0e6f;
 
 struct DustPtrs {
-    float *F0, *F0n, *G0, *log2U, *log2O, *err;
+    float *F0, *F0n, *G0, *log2U, *log2O, *Fmax, *Gmax, *err;
 };
 
 __device__ __forceinline__ DustPtrs dust_ptrs(float* base, int T) {
@@ -25,7 +25,9 @@ __device__ __forceinline__ DustPtrs dust_ptrs(float* base, int T) {
     d.G0 = base + 2 * T;
     d.log2U = base + 3 * T;
     d.log2O = base + 4 * T;
-    d.err = base + 5 * T;
+    d.Fmax = base + 5 * T;  // per-angle max of F (row potentials)
+    d.Gmax = base + 6 * T;  // per-angle max of G (column potentials)
+    d.err = base + 7 * T;
     return d;
 }
 
@@ -153,8 +155,39 @@ __device__ __forceinline__ float block_max(Stage& S, float v) {
 }
 
 // Streams n_total pairs of every source array (from pair index `base`) through
-// shared memory and calls body(stage, count, offset) per chunk.  Returns false
-// (uniformly across the CTA) when a bounded wait ran out.
+// shared memory; per chunk, prep(stage, count) runs on all threads, a barrier
+// makes its writes visible, then body(stage, count, offset) runs.  Returns
+// false (uniformly across the CTA) when a bounded wait ran out.
+template <class Prep, class Body>
+__device__ __forceinline__ bool stream_tile_prep(Stage& S, uint32_t (&parity)[2], const Srcs& src, int base,
+                                                 int n_total, Prep prep, Body body) {
+    int nch = (n_total + kChunk - 1) / kChunk;
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < nch && c < 2; ++c) issue_chunk(S, c, src, base, n_total);
+    }
+    bool ok_all = true;
+    for (int ch = 0; ch < nch; ++ch) {
+        int st = ch & 1;
+        int n = min(kChunk, n_total - ch * kChunk);
+        bool ok = mbar_wait_bounded(&S.bar[st], parity[st]);
+        parity[st] ^= 1u;
+        if (ok) prep(st, n);
+        if (__syncthreads_or(!ok)) {
+            ok_all = false;
+            // let copies already in flight land before the CTA leaves
+            if (threadIdx.x == 0) {
+                for (int c = ch + 1; c < nch && c < ch + 2; ++c) mbar_wait_bounded(&S.bar[c & 1], parity[c & 1]);
+            }
+            break;
+        }
+        body(st, n, ch * kChunk);
+        __syncthreads();
+        if (threadIdx.x == 0 && ch + 2 < nch) issue_chunk(S, ch + 2, src, base, n_total);
+    }
+    return ok_all;
+}
+
+// Same without a prep step.
 template <class Body>
 __device__ __forceinline__ bool stream_tile(Stage& S, uint32_t (&parity)[2], const Srcs& src, int base,
                                             int n_total, Body body) {
@@ -170,7 +203,6 @@ __device__ __forceinline__ bool stream_tile(Stage& S, uint32_t (&parity)[2], con
         if (ok) body(st, min(kChunk, n_total - ch * kChunk), ch * kChunk);
         if (__syncthreads_or(!ok)) {
             ok_all = false;
-            // let copies already in flight land before the CTA leaves
             if (threadIdx.x == 0) {
                 for (int c = ch + 1; c < nch && c < ch + 2; ++c) mbar_wait_bounded(&S.bar[c & 1], parity[c & 1]);
             }

@@ -287,6 +287,76 @@ __device__ __forceinline__ void col_chunk(ColPair& C, const float4* __restrict__
     }
 }
 
+// Fast path of the passes: the staged potentials are shifted by the block's
+// maximum (prep step), so every exponent is <= 0 and the sums need no running
+// maximum: per staged pair, 2 x 13 packed instructions, 4 MUFU ex2 and 2
+// packed adds for 4 pair evaluations.
+__device__ __forceinline__ void row_chunk_sum(const RowPair& R, const float4* __restrict__ sX,
+                                              const float4* __restrict__ sY, const float4* __restrict__ sZ,
+                                              const float4* __restrict__ sW, int n, f2 K2, f2& Sa, f2& Sb) {
+#pragma unroll 4
+    for (int k = 0; k < n; ++k) {
+        ulonglong2 X = *(const ulonglong2*)&sX[k];
+        ulonglong2 Y = *(const ulonglong2*)&sY[k];
+        ulonglong2 Z = *(const ulonglong2*)&sZ[k];
+        ulonglong2 W = *(const ulonglong2*)&sW[k];
+        f2 va = pair_v2(R.pxa, R.pya, R.pza, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y);
+        f2 vb = pair_v2(R.pxb, R.pyb, R.pzb, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y);
+        Sa = add2(Sa, pk(ex2(lo(va)), ex2(hi(va))));
+        Sb = add2(Sb, pk(ex2(lo(vb)), ex2(hi(vb))));
+    }
+}
+
+__device__ __forceinline__ void col_chunk_sum(const ColPair& C, const float4* __restrict__ sX,
+                                              const float4* __restrict__ sY, int n, f2 K2, f2& Sa, f2& Sb) {
+#pragma unroll 4
+    for (int k = 0; k < n; ++k) {
+        ulonglong2 X = *(const ulonglong2*)&sX[k];
+        ulonglong2 Y = *(const ulonglong2*)&sY[k];
+        f2 va = pair_v2(X.x, X.y, Y.x, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, K2, Y.y);
+        f2 vb = pair_v2(X.x, X.y, Y.x, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, K2, Y.y);
+        Sa = add2(Sa, pk(ex2(lo(va)), ex2(hi(va))));
+        Sb = add2(Sb, pk(ex2(lo(vb)), ex2(hi(vb))));
+    }
+}
+
+constexpr float kTinySum = 1.0e-30f;  // below ~2^-100 the fast sum is recomputed exactly
+
+// Exact row log-sum-exp from global memory (running maximum), for rows whose
+// shifted sum underflowed.
+__device__ float row_exact(const SkArgs& a, int t, f2 px, f2 py, f2 pz, float dustv, f2 K2) {
+    RowLse L;
+    L.init(dustv);
+    for (int q = a.J2_off[t]; q < a.J2_off[t + 1]; ++q) {
+        float4 x = a.modX[q], y = a.modY[q], z = a.modZ[q], w = a.modW[q];
+        L.add1(pair_v2(px, py, pz, pk(x.x, x.y), pk(x.z, x.w), pk(y.x, y.y), pk(z.x, z.y), pk(z.z, z.w),
+                       pk(w.x, w.y), K2, pk(y.z, y.w)));
+    }
+    return L.value();
+}
+
+__device__ float col_exact(const SkArgs& a, int t, f2 ncx, f2 ncy, f2 ncz, f2 nrx, f2 nry, f2 nrz, float dz, f2 K2) {
+    RowLse L;
+    L.init(dz);
+    for (int q = a.I2_off[t]; q < a.I2_off[t + 1]; ++q) {
+        float4 x = a.obsX[q], y = a.obsY[q];
+        L.add1(pair_v2(pk(x.x, x.y), pk(x.z, x.w), pk(y.x, y.y), ncx, ncy, ncz, nrx, nry, nrz, K2, pk(y.z, y.w)));
+    }
+    return L.value();
+}
+
+// Per-angle maximum of the potentials written by a pass, from the per-tile
+// partial log-sum-exps (their running maxima).
+__device__ void block_maxima(const float2* part, const int4* ang, int T, bool rows, float add, float* out) {
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        int4 at = ang[t];
+        int first = rows ? at.x : at.z, cnt = rows ? at.y : at.w;
+        float m = kNegHuge;
+        for (int k = 0; k < cnt; ++k) m = fmaxf(m, part[first + k].x);
+        out[t] = m > kNegHuge ? m + add : kNegHuge;
+    }
+}
+
 // --------------------------------------------------------------- row pass
 __global__ void __launch_bounds__(kTPB) sk_row_kernel(SkArgs a) {
     __shared__ __align__(128) Stage S;
@@ -316,16 +386,27 @@ __global__ void __launch_bounds__(kTPB) sk_row_kernel(SkArgs a) {
         R.pxb = dup(X.y);
         R.pyb = dup(X.w);
         R.pzb = dup(Y.y);
-        R.A.init(dustv);
-        R.B.init(dustv);
-        bool ok = stream_tile(S, parity, src, j0, nj, [&](int st, int n, int) {
-            if (valid) row_chunk(R, S.s[0][st], S.s[1][st], S.s[2][st], S.s[3][st], n, K2);
-        });
+        const float shift = fmaxf(D.Gmax[t], dustv);
+        f2 Sa = pk(ex2(dustv - shift), 0.0f), Sb = Sa;
+        bool ok = stream_tile_prep(
+            S, parity, src, j0, nj,
+            [&](int st, int n) {
+                for (int k = threadIdx.x; k < n; k += kTPB) {
+                    float4& y = S.s[1][st][k];
+                    y.z -= shift;
+                    y.w -= shift;
+                }
+            },
+            [&](int st, int n, int) {
+                if (valid) row_chunk_sum(R, S.s[0][st], S.s[1][st], S.s[2][st], S.s[3][st], n, K2, Sa, Sb);
+            });
         if (!ok) {
             if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
             break;
         }
-        float Fa = -R.A.value(), Fb = -R.B.value();
+        float sa = lo(Sa) + hi(Sa), sb = lo(Sb) + hi(Sb);
+        float Fa = valid ? (sa > kTinySum ? -(shift + lg2(sa)) : -row_exact(a, t, R.pxa, R.pya, R.pza, dustv, K2)) : 0.0f;
+        float Fb = vb ? (sb > kTinySum ? -(shift + lg2(sb)) : -row_exact(a, t, R.pxb, R.pyb, R.pzb, dustv, K2)) : 0.0f;
         if (valid) *(float2*)&a.obsY[q].z = make_float2(Fa, vb ? Fb : kNegHuge);
         // tile partial of LSE2(F_i - kc) for the outlier column update
         float pm = kNegHuge, ps = 0.0f;
@@ -366,6 +447,7 @@ __global__ void __launch_bounds__(kTPB) sk_row_kernel(SkArgs a) {
             D.G0[0] = D.log2O[0] - L.value();
         }
     }
+    block_maxima(a.row_part, a.ang_tiles, a.T, true, a.kc, D.Fmax);
     if (threadIdx.x == 0) {
         a.ctrl[CTRL_ROW_NEXT] = 0;
         a.ctrl[CTRL_ROW_DONE] = 0;
@@ -394,16 +476,31 @@ __global__ void __launch_bounds__(kTPB) sk_col_kernel(SkArgs a) {
         ColPair C;
         if (valid) load_col_pair(a, q, C);
         float dz = D.F0[a.mode ? t : 0];  // unmatched-model row, C_0j = 0
-        C.A.init(dz);
-        C.B.init(dz);
-        bool ok = stream_tile(S, parity, src, i0, ni, [&](int st, int n, int) {
-            if (valid) col_chunk(C, S.s[0][st], S.s[1][st], n, K2);
-        });
+        const float shift = fmaxf(D.Fmax[t], dz);
+        f2 Sa = pk(ex2(dz - shift), 0.0f), Sb = Sa;
+        bool ok = stream_tile_prep(
+            S, parity, src, i0, ni,
+            [&](int st, int n) {
+                for (int k = threadIdx.x; k < n; k += kTPB) {
+                    float4& y = S.s[1][st][k];
+                    y.z -= shift;
+                    y.w -= shift;
+                }
+            },
+            [&](int st, int n, int) {
+                if (valid) col_chunk_sum(C, S.s[0][st], S.s[1][st], n, K2, Sa, Sb);
+            });
         if (!ok) {
             if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
             break;
         }
-        float Ga = -C.A.value(), Gb = -C.B.value();
+        float sa = lo(Sa) + hi(Sa), sb = lo(Sb) + hi(Sb);
+        float Ga = valid ? (sa > kTinySum ? -(shift + lg2(sa))
+                                          : -col_exact(a, t, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, dz, K2))
+                         : 0.0f;
+        float Gb = vb ? (sb > kTinySum ? -(shift + lg2(sb))
+                                       : -col_exact(a, t, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, dz, K2))
+                      : 0.0f;
         if (valid) *(float2*)&a.modY[q].z = make_float2(Ga, vb ? Gb : kNegHuge);
         float pm = kNegHuge, ps = 0.0f;
         if (valid) {
@@ -441,6 +538,7 @@ __global__ void __launch_bounds__(kTPB) sk_col_kernel(SkArgs a) {
             D.F0n[0] = D.log2U[0] - L.value();
         }
     }
+    block_maxima(a.col_part, a.ang_tiles, a.T, false, 0.0f, D.Gmax);
     if (threadIdx.x == 0) {
         a.ctrl[CTRL_COL_NEXT] = 0;
         a.ctrl[CTRL_COL_DONE] = 0;
@@ -665,6 +763,24 @@ __global__ void sk_clear_err_kernel(SkArgs a) {
     D.err[0] = D.err[1] = D.err[2] = D.err[3] = 0.0f;
 }
 
+// Per-angle maximum of the starting G (padding excluded), for the first row pass.
+__global__ void __launch_bounds__(256) sk_init_gmax_kernel(SkArgs a) {
+    __shared__ float red[8];
+    int t = blockIdx.x;
+    float m = kNegHuge;
+    for (int q = a.J2_off[t] + threadIdx.x; q < a.J2_off[t + 1]; q += blockDim.x) {
+        float4 y = a.modY[q];
+        m = fmaxf(m, fmaxf(y.z, y.w));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < 8; ++k) m = fmaxf(m, red[k]);
+        dust_ptrs(a.dust, a.T).Gmax[t] = m;
+    }
+}
+
 cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s) {
     int nmax = a.n_obs > a.n_model ? a.n_obs : a.n_model;
     int blocks = (nmax + 255) / 256;
@@ -672,6 +788,7 @@ cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s) {
     sk_schedule_kernel<<<1, 1024, 0, s>>>(a);
     sk_pack_kernel<<<blocks, 256, 0, s>>>(a);
     sk_init_dust_kernel<<<1, 1024, 0, s>>>(a);
+    if (a.T > 0) sk_init_gmax_kernel<<<a.T, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
