@@ -271,6 +271,24 @@ int laue_cost_sinkhorn_noalloc(const LaueGeometry* geom, const LaueObsSpots* obs
                                float* g, float* dust, int* assign, float* margin, float* marg_err,
                                float* q, int* status, void* stream);
 
+/* Autotuner of the pair passes (no counterpart in the paper): times each
+ * launch shape of the row and column passes of laue_cost_sinkhorn on this
+ * problem (shape v: {256, 128, 256 with a 64-register cap, 128 with a
+ * 64-register cap} threads per CTA, one row/column pair per thread; the tile
+ * size follows the CTA width), n_iter passes each after one warm-up
+ * iteration, and keeps the fastest row and column shapes in the handle for
+ * later calls.  choice_host (optional, 2 ints): the chosen row and column
+ * shapes; ms_host (optional, 2 x 4 floats): mean milliseconds per row and
+ * column pass of each shape.  Needs the workspace of laue_cost_sinkhorn plus
+ * 4 (n_obs + n_model + 2T + 8) bytes.  Synchronises `stream`. */
+int laue_autotune(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* obs,
+                  const LaueModelSpots* model, const LaueOTParams* prm, int n_iter, int* choice_host,
+                  float* ms_host, void* stream);
+
+/* Sets the launch shapes (0..3, as for laue_autotune) of the row and column
+ * passes used by later calls on the handle; shape 0 is the default. */
+int laue_set_launch_shape(laue_handle* h, int row_shape, int col_shape);
+
 /* M-step (paper Section "The M-step updates", Appendix "M-steps"): with the
  * plan Q_ij = exp((f_i + g_j - C_ij)/eps) of the E-step (costs from the
  * model list's current rays and centres, which must be those of the E-step),

@@ -88,6 +88,9 @@ SIGNATURES = {
                            _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "laue_cost_sinkhorn_noalloc": [_P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams),
                                    _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "laue_autotune": [_vp, _P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams), _i, _vp,
+                      _vp, _vp],
+    "laue_set_launch_shape": [_vp, _i, _i],
     "laue_mstep": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots), _vp, _vp,
                    _P(LaueMParams), _vp, _vp, _vp, _i, _vp, _vp],
     "laue_objective_grad": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots),

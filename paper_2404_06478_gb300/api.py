@@ -215,6 +215,9 @@ class Handle:
         self.check(self.L.laue_alu_peaks(self.h, out, _stream(stream)), "alu_peaks")
         return dict(ffma=out[0], ffma2=out[1], ex2=out[2], rsqrt=out[3], lg2=out[4], sm_count=int(out[5]))
 
+    def set_launch_shape(self, row_shape, col_shape):
+        self.check(self.L.laue_set_launch_shape(self.h, int(row_shape), int(col_shape)), "set_launch_shape")
+
     def device_status(self, stream=None) -> int:
         v = ctypes.c_int(0)
         self.check(self.L.laue_device_status(self.h, _stream(stream), ctypes.byref(v)), "device_status")
@@ -433,3 +436,20 @@ def cost_sinkhorn_noalloc(geom, obs: ObsSpots, model: ModelSpots, eps, c_out, n_
     return L.laue_cost_sinkhorn_noalloc(ctypes.byref(g_s), ctypes.byref(o_s), ctypes.byref(m_s), ctypes.byref(prm),
                                         _ptr(f), _ptr(g), _ptr(dust), _ptr(assign), _ptr(margin), _ptr(marg_err),
                                         _ptr(q), _ptr(status), _stream(stream))
+
+
+def autotune(h: Handle, geom, obs: ObsSpots, model: ModelSpots, eps, c_out, n_iter=3, dust_mode=0,
+             unmatched_frac=0.4, stream=None):
+    """laue_autotune: picks the fastest launch shapes of the Sinkhorn passes
+    for this problem; returns (row shape, column shape, per-shape ms)."""
+    T = obs.T
+    nI, nJ = int(obs.p.shape[0]), model.n
+    base = h.workspace_size(T, n_obs=nI, n_model=nJ)
+    h.reserve(T, n_obs=nI, n_model=nJ, extra=4 * (nI + nJ + 2 * T + 8) + 4096, stream=stream)
+    prm = ot_params(eps, c_out, 1, dust_mode, unmatched_frac, False)
+    ch = (ctypes.c_int * 2)()
+    ms = (ctypes.c_float * 8)()
+    g_s, o_s, m_s = geometry_struct(geom), obs.struct(), model.struct()
+    h.check(h.L.laue_autotune(h.h, ctypes.byref(g_s), ctypes.byref(o_s), ctypes.byref(m_s), ctypes.byref(prm),
+                              int(n_iter), ch, ms, _stream(stream)), "laue_autotune")
+    return ch[0], ch[1], [(ms[2 * v], ms[2 * v + 1]) for v in range(4)]

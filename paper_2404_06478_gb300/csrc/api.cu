@@ -110,12 +110,10 @@ extern "C" int laue_create(laue_handle** h, int device) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(device);
-    if (sinkhorn_occupancy(&H->row_bps, &H->col_bps) != 0) {
-        H->row_bps = H->col_bps = 1;
-    }
+    if (sinkhorn_occupancy(H->row_occ, H->col_occ) != 0)
+        for (int v = 0; v < kSkVariants; ++v) H->row_occ[v] = H->col_occ[v] = 1;
     cudaSetDevice(prev);
-    if (H->row_bps < 1) H->row_bps = 1;
-    if (H->col_bps < 1) H->col_bps = 1;
+    H->row_variant = H->col_variant = 0;
     H->err[0] = 0;
     *h = H;
     return LAUE_OK;
@@ -358,8 +356,8 @@ int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* o
     a.ctrl = (int*)(ws + L.ctrl);
     a.max_row_tiles = L.max_row_tiles;
     a.max_col_tiles = L.max_col_tiles;
-    a.tile_rows = 256;  // row pairs per tile (one per thread)
-    a.tile_cols = 256;
+    a.tile_rows = sk_variant_threads(h->row_variant);  // row pairs per tile (one per thread)
+    a.tile_cols = sk_variant_threads(h->col_variant);
     double eps = prm->eps;
     a.negKD2 = (float)(-(double)geom->D * geom->D * 1.4426950408889634 / eps);
     a.kc = (float)((double)prm->c_out * 1.4426950408889634 / eps);
@@ -368,12 +366,14 @@ int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* o
     a.mode = prm->dust_mode ? 1 : 0;
     a.warm = prm->warm_start ? 1 : 0;
     *out = a;
-    int rt = std::max(1, std::min(h->sm_count * h->row_bps, L.max_row_tiles));
-    int ct = std::max(1, std::min(h->sm_count * h->col_bps, L.max_col_tiles));
+    lc->row_variant = h->row_variant;
+    lc->col_variant = h->col_variant;
+    int rt = std::max(1, std::min(h->sm_count * h->row_occ[h->row_variant], L.max_row_tiles));
+    int ct = std::max(1, std::min(h->sm_count * h->col_occ[h->col_variant], L.max_col_tiles));
     lc->row_grid = rt;
     lc->col_grid = ct;
-    lc->hrv_grid = rt;
-    lc->hcol_grid = ct;
+    lc->hrv_grid = std::max(1, std::min(h->sm_count * 3, L.max_row_tiles));
+    lc->hcol_grid = std::max(1, std::min(h->sm_count * 3, L.max_col_tiles));
     return LAUE_OK;
 }
 
@@ -412,6 +412,89 @@ extern "C" int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, cons
                            "sinkhorn launch");
 }
 
+// ------------------------------------------------------------- autotuner
+
+extern "C" int laue_set_launch_shape(laue_handle* h, int row_shape, int col_shape) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    if (row_shape < 0 || row_shape >= kSkVariants || col_shape < 0 || col_shape >= kSkVariants)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "launch shape must be 0..%d", kSkVariants - 1);
+    h->row_variant = row_shape;
+    h->col_variant = col_shape;
+    return LAUE_OK;
+}
+
+extern "C" int laue_autotune(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* obs,
+                             const LaueModelSpots* model, const LaueOTParams* prm, int n_iter, int* choice_host,
+                             float* ms_host, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = laue_check_geom(h, geom))) return rc;
+    if ((rc = laue_check_obs(h, obs))) return rc;
+    if ((rc = laue_check_model(h, model))) return rc;
+    if (!prm || !(prm->eps > 0.0f) || obs->T != model->T || n_iter < 1)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "autotune: bad parameters");
+    LaueProblemDims d{obs->T, obs->n, model->n, 0, 0, 0, 0};
+    Layout L;
+    if ((rc = laue_need_ws(h, d, &L))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* ws = (char*)h->ws;
+    float* f_tmp = (float*)(ws + L.fwd_blocks);  // scratch potentials beyond the E-step regions
+    size_t need = L.fwd_blocks + sizeof(float) * ((size_t)obs->n + model->n + 2 * obs->T + 8);
+    if (need > h->ws_bytes) return laue_fail(h, LAUE_ERR_WORKSPACE, "autotune: workspace too small");
+    float* g_tmp = f_tmp + obs->n + 1;
+    float* d_tmp = g_tmp + model->n + 1;
+    cudaEvent_t e0, e1;
+    if ((rc = laue_cuda_check(h, cudaEventCreate(&e0), "event"))) return rc;
+    if ((rc = laue_cuda_check(h, cudaEventCreate(&e1), "event"))) return rc;
+    float best_row = 3e38f, best_col = 3e38f;
+    int row_v = 0, col_v = 0;
+    int save_r = h->row_variant, save_c = h->col_variant;
+    for (int v = 0; v < kSkVariants && rc == LAUE_OK; ++v) {
+        // each shape with its own tile size: rebuild the schedule, warm up, time the passes
+        h->row_variant = v;
+        h->col_variant = v;
+        SkArgs a;
+        SkLaunch lc;
+        laue_fill_sk(h, geom, obs, model, prm, L, &a, &lc);
+        a.f = f_tmp;
+        a.g = g_tmp;
+        a.dust_out = d_tmp;
+        a.warm = 0;
+        if ((rc = laue_cuda_check(h, sinkhorn_prepare(a, s), "autotune prepare"))) break;
+        sinkhorn_iterate(a, lc, 1, s);
+        float ms = 0.0f;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < n_iter; ++k) sinkhorn_row_pass(a, lc, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_host) ms_host[2 * v] = ms / n_iter;
+        if (ms < best_row) { best_row = ms; row_v = v; }
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < n_iter; ++k) sinkhorn_col_pass(a, lc, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_host) ms_host[2 * v + 1] = ms / n_iter;
+        if (ms < best_col) { best_col = ms; col_v = v; }
+        rc = laue_cuda_check(h, cudaGetLastError(), "autotune passes");
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LAUE_OK) {
+        h->row_variant = save_r;
+        h->col_variant = save_c;
+        return rc;
+    }
+    h->row_variant = row_v;
+    h->col_variant = col_v;
+    if (choice_host) {
+        choice_host[0] = row_v;
+        choice_host[1] = col_v;
+    }
+    return LAUE_OK;
+}
+
 // ------------------------------------------------------------- not yet built
 
 extern "C" int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const LaueObsSpots* obs,
@@ -436,6 +519,8 @@ extern "C" int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLa
     SkLaunch lc;
     LaueOTParams op{0.4, prm->eps, 0.0f, 0, 0, 1, 0};
     laue_fill_sk(h, geom, obs, model, &op, L, &m.sk, &lc);
+    m.sk.tile_cols = 256;  // the M-step pair kernel runs 256 threads per column tile
+    lc.col_grid = std::max(1, std::min(h->sm_count * 3, L.max_col_tiles));
     m.sk.f = const_cast<float*>(f);
     m.sk.g = const_cast<float*>(g);
     m.sk.dust_out = nullptr;
@@ -489,6 +574,8 @@ extern "C" int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, con
     SkLaunch lc;
     LaueOTParams op{0.4, eps, 0.0f, 0, 0, 1, 0};
     laue_fill_sk(h, geom, obs, model, &op, L, &m.sk, &lc);
+    m.sk.tile_cols = 256;  // the M-step pair kernel runs 256 threads per column tile
+    lc.col_grid = std::max(1, std::min(h->sm_count * 3, L.max_col_tiles));
     m.sk.f = const_cast<float*>(f);
     m.sk.g = const_cast<float*>(g);
     m.sk.dust_out = nullptr;

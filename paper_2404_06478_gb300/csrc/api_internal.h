@@ -10,7 +10,8 @@
 struct laue_handle {
     int device;
     int sm_count;
-    int row_bps, col_bps;  // resident CTAs per SM of the pair passes
+    int row_occ[laue::kSkVariants], col_occ[laue::kSkVariants];  // resident CTAs per SM of each launch shape
+    int row_variant, col_variant;  // launch shapes in use (the autotuner's choice)
     void* ws;
     size_t ws_bytes;
     char err[512];

@@ -99,8 +99,11 @@ struct SkArgs {
     float* q;
 };
 
+constexpr int kSkVariants = 4;  // launch shapes of the pair passes (see sinkhorn.cu)
+
 struct SkLaunch {
     int row_grid, col_grid, hrv_grid, hcol_grid;
+    int row_variant, col_variant;
 };
 
 cudaError_t sinkhorn_run(const SkArgs& a, const SkLaunch& l, int n_iter, bool want_rows, bool want_cols,
@@ -108,7 +111,10 @@ cudaError_t sinkhorn_run(const SkArgs& a, const SkLaunch& l, int n_iter, bool wa
 cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s);
 cudaError_t sinkhorn_iterate(const SkArgs& a, const SkLaunch& l, int n_iter, cudaStream_t s);
 cudaError_t sinkhorn_finish(const SkArgs& a, const SkLaunch& l, bool want_rows, bool want_cols, cudaStream_t s);
-int sinkhorn_occupancy(int* row_blocks_per_sm, int* col_blocks_per_sm);
+int sinkhorn_occupancy(int* row_blocks_per_sm, int* col_blocks_per_sm);  // kSkVariants entries each
+int sk_variant_threads(int v);
+void sinkhorn_row_pass(const SkArgs& a, const SkLaunch& l, cudaStream_t s);
+void sinkhorn_col_pass(const SkArgs& a, const SkLaunch& l, cudaStream_t s);
 
 // ------------------------------------------------------------------ M-step
 struct MsArgs {

@@ -29,7 +29,8 @@ constexpr int kMaxDevices = 64;
 struct StaticDevice {
     bool ready;
     void* scratch;  // device address of g_static_scratch on this device
-    int sm_count, row_bps, col_bps;
+    int sm_count;
+    int row_occ[kSkVariants], col_occ[kSkVariants];
 };
 
 StaticDevice g_devices[kMaxDevices];
@@ -47,12 +48,10 @@ int static_device(StaticDevice** out) {
         if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) return LAUE_ERR_CUDA;
         int sm = 0;
         if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LAUE_ERR_CUDA;
-        int r = 1, c = 1;
-        if (sinkhorn_occupancy(&r, &c) != 0) r = c = 1;
+        if (sinkhorn_occupancy(d.row_occ, d.col_occ) != 0)
+            for (int v = 0; v < kSkVariants; ++v) d.row_occ[v] = d.col_occ[v] = 1;
         d.scratch = p;
         d.sm_count = sm;
-        d.row_bps = r > 0 ? r : 1;
-        d.col_bps = c > 0 ? c : 1;
         d.ready = true;
     }
     *out = &d;
@@ -82,8 +81,11 @@ extern "C" int laue_cost_sinkhorn_noalloc(const LaueGeometry* geom, const LaueOb
     laue_handle h{};  // a view of the static scratch; nothing is allocated
     h.device = 0;
     h.sm_count = d->sm_count;
-    h.row_bps = d->row_bps;
-    h.col_bps = d->col_bps;
+    for (int v = 0; v < kSkVariants; ++v) {
+        h.row_occ[v] = d->row_occ[v];
+        h.col_occ[v] = d->col_occ[v];
+    }
+    h.row_variant = h.col_variant = 0;
     h.ws = d->scratch;
     h.ws_bytes = kStaticScratchBytes;
     cudaStream_t s = (cudaStream_t)stream;

@@ -9,7 +9,7 @@
 
 namespace laue {
 
-constexpr int kTPB = 256;     // threads per CTA = row (column) pairs per tile
+constexpr int kTPB = 256;     // widest CTA of the pair passes (one row/column pair per thread)
 constexpr int kChunk = 128;   // staged pairs per chunk (256 spots)
 constexpr int kGroup = 4;     // staged pairs per max-then-sum group
 constexpr float kPadFar = 1.0e6f;
@@ -136,7 +136,7 @@ __device__ __forceinline__ void block_lse(Stage& S, float& m, float& s) {
         Lse2 L;
         L.m = kNegHuge;
         L.s = 0.0f;
-        for (int k = 0; k < kTPB / 32; ++k) L.merge(S.red_m[k], S.red_s[k]);
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) L.merge(S.red_m[k], S.red_s[k]);
         m = L.m;
         s = L.s;
     }
@@ -149,7 +149,7 @@ __device__ __forceinline__ float block_max(Stage& S, float v) {
     if ((threadIdx.x & 31) == 0) S.red_m[threadIdx.x >> 5] = v;
     __syncthreads();
     float r = S.red_m[0];
-    for (int k = 1; k < kTPB / 32; ++k) r = fmaxf(r, S.red_m[k]);
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = fmaxf(r, S.red_m[k]);
     __syncthreads();
     return r;
 }

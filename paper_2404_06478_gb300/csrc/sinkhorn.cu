@@ -358,7 +358,8 @@ __device__ void block_maxima(const float2* part, const int4* ang, int T, bool ro
 }
 
 // --------------------------------------------------------------- row pass
-__global__ void __launch_bounds__(kTPB) sk_row_kernel(SkArgs a) {
+template <int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
     __shared__ __align__(128) Stage S;
     init_stage(S);
     uint32_t parity[2] = {0u, 0u};
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(kTPB) sk_row_kernel(SkArgs a) {
         bool ok = stream_tile_prep(
             S, parity, src, j0, nj,
             [&](int st, int n) {
-                for (int k = threadIdx.x; k < n; k += kTPB) {
+                for (int k = threadIdx.x; k < n; k += TPB) {
                     float4& y = S.s[1][st][k];
                     y.z -= shift;
                     y.w -= shift;
@@ -455,7 +456,8 @@ __global__ void __launch_bounds__(kTPB) sk_row_kernel(SkArgs a) {
 }
 
 // ------------------------------------------------------------ column pass
-__global__ void __launch_bounds__(kTPB) sk_col_kernel(SkArgs a) {
+template <int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
     __shared__ __align__(128) Stage S;
     init_stage(S);
     uint32_t parity[2] = {0u, 0u};
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(kTPB) sk_col_kernel(SkArgs a) {
         bool ok = stream_tile_prep(
             S, parity, src, i0, ni,
             [&](int st, int n) {
-                for (int k = threadIdx.x; k < n; k += kTPB) {
+                for (int k = threadIdx.x; k < n; k += TPB) {
                     float4& y = S.s[1][st][k];
                     y.z -= shift;
                     y.w -= shift;
@@ -792,10 +794,28 @@ cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Launch shapes of the pair passes the autotuner chooses from:
+// {threads per CTA (= pairs per tile), minimum resident CTAs per SM}.
+typedef void (*SkKernel)(SkArgs);
+static const SkKernel kRowKernels[kSkVariants] = {sk_row_kernel<256, 1>, sk_row_kernel<128, 1>, sk_row_kernel<256, 4>,
+                                                  sk_row_kernel<128, 8>};
+static const SkKernel kColKernels[kSkVariants] = {sk_col_kernel<256, 1>, sk_col_kernel<128, 1>, sk_col_kernel<256, 4>,
+                                                  sk_col_kernel<128, 8>};
+
+int sk_variant_threads(int v) { return (v == 1 || v == 3) ? 128 : 256; }
+
+void sinkhorn_row_pass(const SkArgs& a, const SkLaunch& l, cudaStream_t s) {
+    kRowKernels[l.row_variant]<<<l.row_grid, sk_variant_threads(l.row_variant), 0, s>>>(a);
+}
+
+void sinkhorn_col_pass(const SkArgs& a, const SkLaunch& l, cudaStream_t s) {
+    kColKernels[l.col_variant]<<<l.col_grid, sk_variant_threads(l.col_variant), 0, s>>>(a);
+}
+
 cudaError_t sinkhorn_iterate(const SkArgs& a, const SkLaunch& l, int n_iter, cudaStream_t s) {
     for (int it = 0; it < n_iter; ++it) {
-        sk_row_kernel<<<l.row_grid, kTPB, 0, s>>>(a);
-        sk_col_kernel<<<l.col_grid, kTPB, 0, s>>>(a);
+        sinkhorn_row_pass(a, l, s);
+        sinkhorn_col_pass(a, l, s);
     }
     return cudaGetLastError();
 }
@@ -821,11 +841,15 @@ cudaError_t sinkhorn_run(const SkArgs& a, const SkLaunch& l, int n_iter, bool wa
 }
 
 int sinkhorn_occupancy(int* row_blocks_per_sm, int* col_blocks_per_sm) {
-    int r = 0, c = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, sk_row_kernel, kTPB, 0) != cudaSuccess) return -1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, sk_col_kernel, kTPB, 0) != cudaSuccess) return -1;
-    *row_blocks_per_sm = r;
-    *col_blocks_per_sm = c;
+    for (int v = 0; v < kSkVariants; ++v) {
+        int r = 0, c = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kRowKernels[v], sk_variant_threads(v), 0) != cudaSuccess)
+            return -1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, kColKernels[v], sk_variant_threads(v), 0) != cudaSuccess)
+            return -1;
+        row_blocks_per_sm[v] = r > 0 ? r : 1;
+        col_blocks_per_sm[v] = c > 0 ? c : 1;
+    }
     return 0;
 }
 

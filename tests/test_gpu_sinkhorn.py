@@ -165,3 +165,27 @@ def test_sinkhorn_full_size_rows_and_marginals(env):
     assert h.device_status() == 0
     me = full["marg_err"].cpu().numpy()
     assert me[0] < 1e-2 and me[1] < 1e-4
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+def test_sinkhorn_every_launch_shape(env, shape):
+    """Each launch shape of the autotuner (CTA width 256/128, with and without
+    the 64-register cap) gives the same results."""
+    case = make_case(sg.CONFIGS["medium"], seed=12, n_grains=60, T=8)
+    env["h"].set_launch_shape(shape, (shape + 1) % 4)
+    try:
+        gpu, ref, eps = _run_both(env, case, 40, mode=shape % 2, cols=True)
+    finally:
+        env["h"].set_launch_shape(0, 0)
+    _check(gpu, ref, eps)
+
+
+def test_autotune_picks_valid_shapes(env):
+    api = env["api"]
+    case = make_case(sg.CONFIGS["medium"], seed=13, n_grains=100, T=12)
+    ob, ms = to_device(case, env["dev"])
+    h = api.Handle(env["dev"])
+    r, c, times = api.autotune(h, GEOM, ob, ms, 1.0, case.c_out, n_iter=2)
+    assert 0 <= r < 4 and 0 <= c < 4
+    assert all(a > 0 and b > 0 for a, b in times)
+    assert times[r][0] == min(a for a, _ in times) and times[c][1] == min(b for _, b in times)
