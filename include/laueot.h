@@ -391,6 +391,34 @@ int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
                const float* startX, int S, const LaueIndexParams* prm, float* R_out,
                float* x_out, int n_max, int* n_grains_host, int* assign, void* stream);
 
+/* ---- learned proposal (an addition beside the paper's method) ---------- */
+
+/* The paper proposes candidate grains by single-grain fits from a grid of
+ * starts (Section "Pre-processing").  The calls below add a learned
+ * proposal: a set encoder (per-spot MLP of three 256-wide ReLU layers, masked
+ * mean and max pooling, a two-layer head emitting 8 hypotheses of 6-D
+ * rotation + 3-D position) that reads a seed-conditioned set of observed
+ * spots and proposes poses for those fits.  Its per-spot layers run in BF16
+ * on the tensor cores with FP32 accumulation.  The paper has no counterpart
+ * for any of these calls. */
+
+/* BF16 GEMM on the tcgen05 tensor cores: D[m][n] = sum_k A[m][k] B[n][k].
+ * A: M x K BF16, row-major with leading dimension lda (elements); B: N x K
+ * BF16 with ldb.  M % 128 == 0, N % bn == 0 with bn in {64, 128, 256},
+ * K % 64 == 0, (K / 64) % splits == 0, lda, ldb % 8 == 0, all pointers
+ * 16-byte aligned.  mode 0: D_f32 receives `splits` FP32 partial products
+ * (split s covers K range [s K/splits, (s+1) K/splits)) at D_f32 + s M N,
+ * row-major M x N.  mode 1: relu(acc + bias[n]) rounded to BF16 (nearest
+ * even) into D_bf16 (M x N row-major) and/or DT_bf16 (N rows of leading
+ * dimension ldt >= M: DT[n][m]); splits must be 1.  mode 2: acc where the
+ * BF16 mask[m][n] (M x N row-major) is > 0, else 0, same outputs.
+ * Asynchronous on `stream`; device memory is the caller's.  Needs the
+ * workspace (status word).  Errors: LAUE_ERR_INVALID_ARG for shapes,
+ * alignment or a missing output. */
+int laue_gemm_bf16(laue_handle* h, const void* A, long long lda, const void* B, long long ldb, int M,
+                   int N, int K, int bn, int splits, int mode, const float* bias, const void* mask,
+                   float* D_f32, void* D_bf16, void* DT_bf16, long long ldt, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -457,3 +457,21 @@ def scene_seeds(label, I_off, W, per_scene, key, tries=64):
                     out[s * per_scene + j] = i
                     break
     return out
+
+
+def gemm_tn(A, B, mode=0, bias=None, mask=None, splits=1, round_out=True):
+    """Reference of the tensor-core GEMM: D = A B^T in FP64 over the given
+    operand values.  mode 0 returns the `splits` partial products over equal
+    K ranges (splits, M, N); mode 1 bf16(relu(D + bias)); mode 2
+    bf16(D where mask > 0, else 0); round_out=False skips the BF16 rounding."""
+    A = np.asarray(A, np.float64)
+    B = np.asarray(B, np.float64)
+    K = A.shape[1]
+    if mode == 0:
+        ks = K // splits
+        return np.stack([A[:, s * ks:(s + 1) * ks] @ B[:, s * ks:(s + 1) * ks].T for s in range(splits)])
+    D = A @ B.T
+    rnd = bf16 if round_out else (lambda a: a)
+    if mode == 1:
+        return rnd(np.maximum(D + np.asarray(bias, np.float64)[None, :], 0.0))
+    return rnd(np.where(np.asarray(mask) > 0, D, 0.0))

@@ -103,6 +103,8 @@ SIGNATURES = {
     "laue_index_workspace_size": [_vp, _i, _i, _i, _i, _i, _P(ctypes.c_size_t)],
     "laue_index": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                    _P(LaueIndexParams), _vp, _vp, _i, _pi, _vp, _vp],
+    "laue_gemm_bf16": [_vp, _vp, ctypes.c_longlong, _vp, ctypes.c_longlong, _i, _i, _i, _i, _i, _i, _vp, _vp,
+                       _vp, _vp, _vp, ctypes.c_longlong, _vp],
 }
 
 
