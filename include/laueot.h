@@ -419,6 +419,107 @@ int laue_gemm_bf16(laue_handle* h, const void* A, long long lda, const void* B, 
                    int N, int K, int bn, int splits, int mode, const float* bias, const void* mask,
                    float* D_f32, void* D_bf16, void* DT_bf16, long long ldt, void* stream);
 
+/* Sizes of the set encoder's buffers (host helpers, no device work).
+ * Parameter vector (FP32, laue_lp_param_count() values): W1 (256 x 64), b1,
+ * W2 (256 x 256), b2, W3 (256 x 256), b3, W4 (256 x 512), b4, W5 (72 x 256),
+ * b5; weights row-major [out][in].  Network buffer: laue_lp_net_bytes()
+ * bytes of device memory holding the parameters, Adam moments, gradients,
+ * BF16 weight copies and split-K partials.  Batch buffer for n_sets sets:
+ * laue_lp_batch_bytes(n_sets) bytes (features, activations, errors, head
+ * arrays); both 256-byte aligned and owned by the caller.
+ * laue_lp_batch_offset(n_sets, region) is the byte offset of a region of
+ * the batch buffer (-1 if unknown): 0 X (n_sets*128 x 64 BF16 features),
+ * 1 X^T, 2 seed frames F (n_sets x 9 FP32, row-major, columns n0 a1 a2),
+ * 3 valid elements per set (int), 4 R_loc targets (n_sets x 9), 5 position
+ * targets (n_sets x 3, x / 2.5 mm), 6 set valid flags (FP32), 7 network
+ * outputs O (n_sets x 72: 8 hypotheses of 6-D rotation + 3-D position),
+ * 8 per-set losses, 9 per-set best rotation error, 10 best hypothesis
+ * (int), 11 H1, 12 H3 (n_sets*128 x 256 BF16), 13 pooled features
+ * (n_sets x 512 FP32), 14 dL/dO, 15 dL/dZ3 (BF16). */
+size_t laue_lp_param_count(void);
+size_t laue_lp_net_bytes(void);
+size_t laue_lp_batch_bytes(int n_sets);
+long long laue_lp_batch_offset(int n_sets, int region);
+
+/* Loads parameters (host FP32 vector) into a network buffer, clears the
+ * Adam state and step counter and writes the BF16 weight copies.
+ * Synchronises `stream` (the host copy is pageable). */
+int laue_lp_net_init(laue_handle* h, void* net, const float* params_host, void* stream);
+
+/* Copies the parameters and/or the last gradients (laue_lp_param_count()
+ * FP32 each; either pointer may be NULL) to the host.  Synchronises. */
+int laue_lp_net_params(laue_handle* h, const void* net, float* params_host, float* grads_host,
+                       void* stream);
+
+/* Training scenes simulated by the forward model (Eqs. ray_mnt, s_mnt,
+ * wavelength, model_spot_cut).  Counter-based Philox4x32-10 draws, keyed by
+ * `seed`: per scene s < S a window start t0 in [0, T - W] and a grain count
+ * in [gmin, gmax]; per grain g < Gmax a uniform rotation (Shoemake) into
+ * grainR[(s Gmax + g) 9] and a position uniform in the cube of side cube_mm
+ * into grainX.  Virtual angle v = s W + k has rotation omega[t0 + k]
+ * (written to omega_v[v]); its spots are the grains' visible spots with
+ * N(0, sigma_mm^2) noise on x and y (dropped if pushed off the detector),
+ * followed by floor(outlier_ratio n_true + u) uniform outliers.  Outputs:
+ * I_off (S W + 1), p (float4 x, y, z, 0 per spot, 16-byte aligned) and
+ * label (s Gmax + g, or -1 for an outlier), at most `capacity` spots
+ * (beyond it the status word records LAUE_ERR_CAPACITY and the list is
+ * cut).  scene_i32 is scratch of 4 S W + 2 S ints (grain counts, window
+ * starts, per-angle counts).  Planes must number at most 65535.
+ * Asynchronous; nothing is read back. */
+int laue_lp_scene(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const float* omega,
+                  int T, int W, int S, int Gmax, int gmin, int gmax, float cube_mm, float sigma_mm,
+                  double outlier_ratio, unsigned long long seed, float* grainR, float* grainX,
+                  int* scene_i32, int* I_off, float* omega_v, float* p, int* label, int capacity,
+                  void* stream);
+
+/* Seeds of a training batch: per scene s and set j < per_scene, the first
+ * inlier among up to 64 spots of the scene drawn uniformly by Philox (or
+ * -1); the window of set (s, j) is [s W, (s+1) W).  Outputs seeds, wlo,
+ * whi (S per_scene ints each).  Asynchronous. */
+int laue_lp_scene_seeds(laue_handle* h, const int* I_off, const int* label, int W, int S, int per_scene,
+                        unsigned long long seed, int* seeds, int* wlo, int* whi, void* stream);
+
+/* Seed-conditioned sets.  Spots p (float4, 16-byte aligned) sorted by angle
+ * with offsets I_off (n_angles + 1), rotation angles omega (n_angles), at
+ * most n_cap spots.  For set b: seed spot seeds[b] (-1: an empty set) and
+ * window of angles [wlo[b], whi[b]).  Each spot's sample-frame axis is
+ * n = Gamma_t^T u with u parallel to p/|p| - e (the plane normal of a
+ * reflection off a grain at the origin, Eq. ray_mnt); the set holds the
+ * seed and the 127 spots of the window whose axes are nearest the seed's
+ * (distance 1 - |n.n0|, ties by index), as 64 BF16 features in the seed
+ * frame [n0, a1, n0 x a1] (a1: unit part of +y orthogonal to n0), written
+ * to the batch buffer (regions 0-3).  With label (spot -> grain, -1 for an
+ * outlier) and grainR / grainX (9 and 3 FP32 per grain), the targets
+ * R_loc = F0^T R and x / 2.5 mm and the valid flags are written too.
+ * axes_scratch: 16 n_cap bytes.  ids (n_sets x 128 ints, -1 for padding)
+ * may be NULL.  Asynchronous. */
+int laue_lp_sets(laue_handle* h, const LaueGeometry* geom, const float* p, const int* I_off,
+                 const float* omega, int n_angles, int n_cap, const int* seeds, const int* wlo,
+                 const int* whi, int n_sets, const int* label, const float* grainR,
+                 const float* grainX, void* axes_scratch, void* batch, int* ids, void* stream);
+
+/* Network forward over the sets in the batch buffer: per-spot layers as
+ * BF16 tcgen05 GEMMs with FP32 accumulation and fused bias + ReLU, masked
+ * mean and max pooling, FP32 head; outputs O in batch region 7.
+ * Asynchronous. */
+int laue_lp_forward(laue_handle* h, const void* net, void* batch, int n_sets, void* stream);
+
+/* One training step on the sets and targets in the batch buffer: forward;
+ * per set the loss min_h L_h + 0.05 mean_h L_h with L_h = min over the 24
+ * cube rotations S of ||GS(o_h) - R_loc S||_F^2 + 0.1 ||xhat_h - x||^2,
+ * averaged over the valid sets; backward (head in FP32, per-spot layers on
+ * the tensor cores, errors rounded to BF16); Adam (beta 0.9, 0.999,
+ * eps 1e-8, learning rate lr; lr = 0 leaves the parameters unchanged).
+ * Losses, best errors and hypotheses land in batch regions 8-10, gradients
+ * in the network buffer.  Asynchronous. */
+int laue_lp_train_step(laue_handle* h, void* net, void* batch, int n_sets, float lr, void* stream);
+
+/* Proposals from the outputs O: per set and hypothesis h, R = F0 GS(o_h)
+ * (row-major 3x3, R_out n_sets x 8 x 9) and x = 2.5 mm o_h[6:9] (x_out
+ * n_sets x 8 x 3); empty sets give the identity and 0.  Asynchronous. */
+int laue_lp_decode(laue_handle* h, const void* batch, int n_sets, float* R_out, float* x_out,
+                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

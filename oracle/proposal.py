@@ -373,29 +373,72 @@ def normal_pair(x0, x1):
     return rad * np.cos(2.0 * math.pi * u2), rad * np.sin(2.0 * math.pi * u2)
 
 
-TAG_NOISE, TAG_COUNT, TAG_OUTLIER, TAG_SEED = 0, 1, 2, 3
+TAG_NOISE, TAG_COUNT, TAG_OUTLIER, TAG_SEED, TAG_SCENE, TAG_GRAIN = 0, 1, 2, 3, 4, 5
 ALL = 0xFFFFFFFF
 
 
-def training_scene(geom, planes, omega_v, W, R, x, n_g, key, sigma, outlier_ratio):
-    """Training scenes built from the forward model (FP64), one per run of W
-    consecutive entries of omega_v (S = len(omega_v) / W scenes).
+def uniform_int(x, n):
+    """Integer in [0, n) from a uint32 word: ((x >> 8) n) >> 24 (exact)."""
+    return int((int(x) >> 8) * int(n)) >> 24
 
-    Scene s holds grains R[s, :n_g[s]], x[s, :n_g[s]] (R (S, Gmax, 3, 3), x
-    (S, Gmax, 3)).  At virtual angle v = s W + k, every spot of the forward
-    model (Eqs. ray_mnt, s_mnt, wavelength, model_spot_cut) of grain g and
-    plane m gets detector noise sigma * (z1, z2) with (z1, z2) = normal_pair of
-    Philox words 0, 1 of counter (v, g, m, TAG_NOISE); spots pushed off their
-    detector are dropped.  Then floor(ratio * n_true_v + u) outliers follow
-    (u from word 0 of (v, ALL, 0, TAG_COUNT)); outlier k takes detector
-    floor(u0 n_det) and position centre + half (2 u1 - 1, 2 u2 - 1) from
-    words 0-2 of (v, ALL, k, TAG_OUTLIER).  Order: true spots by (g, m), then
-    outliers.  Returns p (n, 3), t (n,) virtual angle, label (n,) scene-local
-    grain or -1, I_off (S W + 1,)."""
+
+def shoemake(u1, u2, u3):
+    """Uniform rotation from three uniforms (Shoemake, Graphics Gems III,
+    1992): q = (sqrt(1-u1) sin 2 pi u2, sqrt(1-u1) cos 2 pi u2,
+    sqrt(u1) sin 2 pi u3, sqrt(u1) cos 2 pi u3) as (x, y, z, w)."""
+    a, b = math.sqrt(1.0 - u1), math.sqrt(u1)
+    qx, qy = a * math.sin(2 * math.pi * u2), a * math.cos(2 * math.pi * u2)
+    qz, qw = b * math.sin(2 * math.pi * u3), b * math.cos(2 * math.pi * u3)
+    return np.array([
+        [1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qz * qw), 2 * (qx * qz + qy * qw)],
+        [2 * (qx * qy + qz * qw), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qx * qw)],
+        [2 * (qx * qz - qy * qw), 2 * (qy * qz + qx * qw), 1 - 2 * (qx * qx + qy * qy)]])
+
+
+def scene_params(S, Gmax, gmin, gmax, T, W, key, cube):
+    """Per scene s: window start t0 = uniform_int(word 0, T - W + 1) and grain
+    count n_g = gmin + uniform_int(word 1, gmax - gmin + 1) from counter
+    (s, ALL, 0, TAG_SCENE); per grain g < Gmax: R = shoemake of words 0-2 of
+    (s, g, 0, TAG_GRAIN), x = cube (u - 1/2) from words 0-2 of
+    (s, g, 1, TAG_GRAIN)."""
+    key = np.asarray(key, np.uint32)
+    t0 = np.zeros(S, np.int64)
+    n_g = np.zeros(S, np.int64)
+    R = np.zeros((S, Gmax, 3, 3))
+    x = np.zeros((S, Gmax, 3))
+    for s in range(S):
+        w = philox4x32(np.array([s, ALL, 0, TAG_SCENE], np.uint32), key)
+        t0[s] = uniform_int(w[0], T - W + 1)
+        n_g[s] = gmin + uniform_int(w[1], gmax - gmin + 1)
+        for g in range(Gmax):
+            wr = philox4x32(np.array([s, g, 0, TAG_GRAIN], np.uint32), key)
+            R[s, g] = shoemake(uniform01(wr[0]), uniform01(wr[1]), uniform01(wr[2]))
+            wx = philox4x32(np.array([s, g, 1, TAG_GRAIN], np.uint32), key)
+            x[s, g] = cube * (uniform01(wx[:3]) - 0.5)
+    return t0, n_g, R, x
+
+
+def training_scene(geom, planes, omega, t0, W, R, x, n_g, key, sigma, outlier_ratio):
+    """Training scenes built from the forward model (FP64).  Scene s covers
+    the W rotation angles omega[t0[s]:t0[s]+W]: virtual angle v = s W + k
+    has omega_v = omega[t0[s] + k] and holds grains R[s, :n_g[s]],
+    x[s, :n_g[s]] (R (S, Gmax, 3, 3), x (S, Gmax, 3)).
+
+    At virtual angle v, every spot of the forward model (Eqs. ray_mnt, s_mnt,
+    wavelength, model_spot_cut) of grain g and plane m gets detector noise
+    sigma * (z1, z2) with (z1, z2) = normal_pair of Philox words 0, 1 of
+    counter (v, g, m, TAG_NOISE); spots pushed off their detector are
+    dropped.  Then floor(ratio * n_true_v + u) outliers follow (u from word 0
+    of (v, ALL, 0, TAG_COUNT)); outlier k takes detector floor(u0 n_det) and
+    position centre + half (2 u1 - 1, 2 u2 - 1) from words 0-2 of
+    (v, ALL, k, TAG_OUTLIER).  Order: true spots by (g, m), then outliers.
+    Returns p (n, 3), label (n,) global grain s Gmax + g or -1, I_off
+    (S W + 1,) and omega_v (S W,)."""
     from . import forward as orc_forward
     key = np.asarray(key, np.uint32)
-    S = len(omega_v) // W
-    P, T, L = [], [], []
+    S, Gmax = R.shape[0], R.shape[1]
+    omega_v = np.concatenate([np.asarray(omega)[t0[s]:t0[s] + W] for s in range(S)])
+    P, L = [], []
     for v in range(S * W):
         s = v // W
         ng = int(n_g[s])
@@ -430,17 +473,16 @@ def training_scene(geom, planes, omega_v, W, R, x, n_g, key, sigma, outlier_rati
                 po[i] = (d.centre[0] + d.half * (2.0 * uniform01(wo[i, 1]) - 1.0),
                          d.centre[1] + d.half * (2.0 * uniform01(wo[i, 2]) - 1.0), d.centre[2])
         P.append(np.concatenate([p, po]))
-        T.append(np.full(len(p) + n_out, v))
-        L.append(np.concatenate([g, -np.ones(n_out, np.int64)]))
-    cnt = np.array([len(a) for a in T])
+        L.append(np.concatenate([s * Gmax + g, -np.ones(n_out, np.int64)]))
+    cnt = np.array([len(a) for a in L])
     I_off = np.concatenate([[0], np.cumsum(cnt)])
-    return np.concatenate(P), np.concatenate(T), np.concatenate(L), I_off
+    return np.concatenate(P), np.concatenate(L), I_off, omega_v
 
 
 def scene_seeds(label, I_off, W, per_scene, key, tries=64):
     """Seed of set j of scene s: the first inlier among spots chosen
-    uniformly (floor(u n_s), u from word 0 of (s, j, q, TAG_SEED), q = 0,
-    1, ...) within the scene; -1 when none of `tries` draws is an inlier."""
+    uniformly (uniform_int(word 0 of (s, j, q, TAG_SEED), n_s), q = 0, 1,
+    ...) within the scene; -1 when none of `tries` draws is an inlier."""
     key = np.asarray(key, np.uint32)
     S = (len(I_off) - 1) // W
     out = -np.ones(S * per_scene, np.int64)
@@ -451,8 +493,8 @@ def scene_seeds(label, I_off, W, per_scene, key, tries=64):
             if ns == 0:
                 continue
             for q in range(tries):
-                u = uniform01(philox4x32(np.array([s, j, q, TAG_SEED], np.uint32), key)[0])
-                i = lo + min(int(u * ns), ns - 1)
+                w = philox4x32(np.array([s, j, q, TAG_SEED], np.uint32), key)
+                i = lo + uniform_int(w[0], ns)
                 if label[i] >= 0:
                     out[s * per_scene + j] = i
                     break

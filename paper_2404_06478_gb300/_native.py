@@ -103,9 +103,28 @@ SIGNATURES = {
     "laue_index_workspace_size": [_vp, _i, _i, _i, _i, _i, _P(ctypes.c_size_t)],
     "laue_index": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                    _P(LaueIndexParams), _vp, _vp, _i, _pi, _vp, _vp],
+    "laue_lp_net_init": [_vp, _vp, _vp, _vp],
+    "laue_lp_net_params": [_vp, _vp, _vp, _vp, _vp],
+    "laue_lp_scene": [_vp, _P(LaueGeometry), _P(LaueLattice), _vp, _i, _i, _i, _i, _i, _i, _f, _f, _d,
+                      ctypes.c_ulonglong, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp],
+    "laue_lp_scene_seeds": [_vp, _vp, _vp, _i, _i, _i, ctypes.c_ulonglong, _vp, _vp, _vp, _vp],
+    "laue_lp_sets": [_vp, _P(LaueGeometry), _vp, _vp, _vp, _i, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp,
+                     _vp],
+    "laue_lp_forward": [_vp, _vp, _vp, _i, _vp],
+    "laue_lp_train_step": [_vp, _vp, _vp, _i, _f, _vp],
+    "laue_lp_decode": [_vp, _vp, _i, _vp, _vp, _vp],
     "laue_gemm_bf16": [_vp, _vp, ctypes.c_longlong, _vp, ctypes.c_longlong, _i, _i, _i, _i, _i, _i, _vp, _vp,
                        _vp, _vp, _vp, ctypes.c_longlong, _vp],
 }
+
+
+# host helpers that return sizes and offsets rather than a status
+SIZE_FUNCTIONS = [
+    ("laue_lp_param_count", [], ctypes.c_size_t),
+    ("laue_lp_net_bytes", [], ctypes.c_size_t),
+    ("laue_lp_batch_bytes", [_i], ctypes.c_size_t),
+    ("laue_lp_batch_offset", [_i, _i], ctypes.c_longlong),
+]
 
 
 def lib():
@@ -121,9 +140,13 @@ def lib():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_char_p if name == "laue_last_error" else ctypes.c_int
+        for name, args, res in SIZE_FUNCTIONS:
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
         _lib = L
     return _lib
 
 
 def exported_symbols():
-    return list(SIGNATURES)
+    return list(SIGNATURES) + [n for n, _, _ in SIZE_FUNCTIONS]

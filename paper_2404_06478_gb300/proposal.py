@@ -28,3 +28,180 @@ def gemm_bf16(h: api.Handle, A: torch.Tensor, B: torch.Tensor, mode: int = 0, bn
                             api._ptr(bias), api._ptr(mask), api._ptr(out_f32), api._ptr(out), api._ptr(outT), ldt,
                             api._stream(stream))
     h.check(rc, "gemm_bf16")
+
+
+# ---------------------------------------------------------------- set encoder
+KSET, NF, NHYP, NOUT = 128, 64, 8, 72
+REGIONS = dict(X=0, Xt=1, F=2, nvalid=3, Rt=4, xt=5, svalid=6, O=7, loss=8, dbest=9, hbest=10, H1=11, H3=12,
+               pool=13, dO=14, dZ3=15)
+PARAM_SHAPES = [("W1", (256, 64)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),
+                ("b3", (256,)), ("W4", (256, 512)), ("b4", (256,)), ("W5", (72, 256)), ("b5", (72,))]
+
+
+def _aligned(nbytes, device, align=256):
+    """A uint8 device buffer of nbytes whose data pointer is `align`-aligned."""
+    raw = torch.empty(nbytes + align, dtype=torch.uint8, device=device)
+    off = (-raw.data_ptr()) % align
+    return raw, raw[off:off + nbytes]
+
+
+def init_params(seed: int):
+    """He-normal weights for the ReLU layers, 1/fan_in variance for the output
+    layer, zero biases (FP32 vector in the library's parameter order)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, shape in PARAM_SHAPES:
+        if name.startswith("b"):
+            out.append(np.zeros(shape, np.float32))
+        else:
+            gain = 1.0 if name == "W5" else 2.0
+            out.append((rng.standard_normal(shape) * (gain / shape[1]) ** 0.5).astype(np.float32))
+    return np.concatenate([a.reshape(-1) for a in out])
+
+
+def unpack_params(vec):
+    """Parameter vector -> dict of arrays in PARAM_SHAPES order."""
+    out, o = {}, 0
+    for name, shape in PARAM_SHAPES:
+        n = 1
+        for d in shape:
+            n *= d
+        out[name] = vec[o:o + n].reshape(shape)
+        o += n
+    return out
+
+
+class Network:
+    """Parameters, Adam state and gradients of the set encoder in one device
+    buffer owned by this object."""
+
+    def __init__(self, h: api.Handle, params=None, seed: int = 0, stream=None):
+        import ctypes
+        import numpy as np
+        self.h, self.L = h, h.L
+        if h.ws is None:
+            h.reserve(1, stream=stream)
+        self.n_params = int(self.L.laue_lp_param_count())
+        self._raw, self.buf = _aligned(int(self.L.laue_lp_net_bytes()), h.device)
+        vec = init_params(seed) if params is None else np.ascontiguousarray(params, np.float32)
+        assert vec.size == self.n_params
+        h.check(self.L.laue_lp_net_init(h.h, api._ptr(self.buf), vec.ctypes.data_as(ctypes.c_void_p),
+                                        api._stream(stream)), "lp_net_init")
+
+    def params(self, stream=None):
+        import ctypes
+        import numpy as np
+        out = np.zeros(self.n_params, np.float32)
+        self.h.check(self.L.laue_lp_net_params(self.h.h, api._ptr(self.buf), out.ctypes.data_as(ctypes.c_void_p),
+                                               None, api._stream(stream)), "lp_net_params")
+        return out
+
+    def grads(self, stream=None):
+        import ctypes
+        import numpy as np
+        out = np.zeros(self.n_params, np.float32)
+        self.h.check(self.L.laue_lp_net_params(self.h.h, api._ptr(self.buf), None, out.ctypes.data_as(ctypes.c_void_p),
+                                               api._stream(stream)), "lp_net_params")
+        return out
+
+
+class Batch:
+    """Device buffer for n_sets seed-conditioned sets and their activations."""
+
+    def __init__(self, h: api.Handle, n_sets: int):
+        self.h, self.L, self.n = h, h.L, int(n_sets)
+        self._raw, self.buf = _aligned(int(self.L.laue_lp_batch_bytes(self.n)), h.device)
+        self.ids = torch.empty(self.n * KSET, dtype=torch.int32, device=h.device)
+
+    def region(self, name, dtype, shape):
+        off = int(self.L.laue_lp_batch_offset(self.n, REGIONS[name]))
+        item = torch.empty(0, dtype=dtype).element_size()
+        n = 1
+        for d in shape:
+            n *= d
+        return self.buf[off:off + n * item].view(dtype).view(*shape)
+
+    def outputs(self):
+        return self.region("O", torch.float32, (self.n, NOUT))
+
+    def features(self):
+        return self.region("X", torch.bfloat16, (self.n, KSET, NF))
+
+    def frames(self):
+        return self.region("F", torch.float32, (self.n, 3, 3))
+
+
+def make_sets(h: api.Handle, geom, p4: torch.Tensor, I_off: torch.Tensor, omega: torch.Tensor, seeds, wlo, whi,
+              batch: Batch, axes: torch.Tensor, label=None, grainR=None, grainX=None, stream=None):
+    """Seed-conditioned sets of spots p4 (n, 4) sorted by angle (I_off)."""
+    import ctypes
+    n_angles = omega.numel()
+    g = api.geometry_struct(geom)
+    rc = h.L.laue_lp_sets(h.h, ctypes.byref(g), api._ptr(p4), api._ptr(I_off), api._ptr(omega), n_angles, p4.shape[0],
+                          api._ptr(seeds), api._ptr(wlo), api._ptr(whi), batch.n, api._ptr(label), api._ptr(grainR),
+                          api._ptr(grainX), api._ptr(axes), api._ptr(batch.buf), api._ptr(batch.ids),
+                          api._stream(stream))
+    h.check(rc, "lp_sets")
+
+
+def forward(h: api.Handle, net: Network, batch: Batch, stream=None):
+    h.check(h.L.laue_lp_forward(h.h, api._ptr(net.buf), api._ptr(batch.buf), batch.n, api._stream(stream)),
+            "lp_forward")
+    return batch.outputs()
+
+
+def train_step(h: api.Handle, net: Network, batch: Batch, lr: float, stream=None):
+    h.check(h.L.laue_lp_train_step(h.h, api._ptr(net.buf), api._ptr(batch.buf), batch.n, float(lr),
+                                   api._stream(stream)), "lp_train_step")
+
+
+def decode(h: api.Handle, batch: Batch, stream=None):
+    """Proposals (n_sets * 8, 9) rotations and (n_sets * 8, 3) positions."""
+    R = torch.empty(batch.n * NHYP, 9, dtype=torch.float32, device=h.device)
+    x = torch.empty(batch.n * NHYP, 3, dtype=torch.float32, device=h.device)
+    h.check(h.L.laue_lp_decode(h.h, api._ptr(batch.buf), batch.n, api._ptr(R), api._ptr(x), api._stream(stream)),
+            "lp_decode")
+    return R, x
+
+
+class Scenes:
+    """Device buffers of a batch of training scenes (S scenes of W angles,
+    at most Gmax grains each) and of their seeds."""
+
+    def __init__(self, h: api.Handle, S: int, W: int, Gmax: int, per_scene: int, capacity: int):
+        dev = h.device
+        self.h, self.S, self.W, self.Gmax, self.per_scene, self.capacity = h, S, W, Gmax, per_scene, capacity
+        self.grainR = torch.empty(S * Gmax, 9, dtype=torch.float32, device=dev)
+        self.grainX = torch.empty(S * Gmax, 3, dtype=torch.float32, device=dev)
+        self.scene_i32 = torch.empty(4 * S * W + 2 * S, dtype=torch.int32, device=dev)
+        self.I_off = torch.empty(S * W + 1, dtype=torch.int32, device=dev)
+        self.omega_v = torch.empty(S * W, dtype=torch.float32, device=dev)
+        self.p4 = torch.empty(capacity, 4, dtype=torch.float32, device=dev)
+        self.label = torch.empty(capacity, dtype=torch.int32, device=dev)
+        self.axes = torch.empty(capacity, 4, dtype=torch.float32, device=dev)
+        B = S * per_scene
+        self.seeds = torch.empty(B, dtype=torch.int32, device=dev)
+        self.wlo = torch.empty(B, dtype=torch.int32, device=dev)
+        self.whi = torch.empty(B, dtype=torch.int32, device=dev)
+
+    def generate(self, geom, lat: api.Lattice, omega: torch.Tensor, seed: int, gmin: int, gmax: int,
+                 cube_mm=5.0, sigma_mm=0.5, outlier_ratio=0.7, stream=None):
+        import ctypes
+        h = self.h
+        g = api.geometry_struct(geom)
+        ls = lat.struct()
+        rc = h.L.laue_lp_scene(h.h, ctypes.byref(g), ctypes.byref(ls), api._ptr(omega), omega.numel(), self.W, self.S, self.Gmax, gmin,
+                               gmax, float(cube_mm), float(sigma_mm), float(outlier_ratio), int(seed),
+                               api._ptr(self.grainR), api._ptr(self.grainX), api._ptr(self.scene_i32),
+                               api._ptr(self.I_off), api._ptr(self.omega_v), api._ptr(self.p4), api._ptr(self.label),
+                               self.capacity, api._stream(stream))
+        h.check(rc, "lp_scene")
+        rc = h.L.laue_lp_scene_seeds(h.h, api._ptr(self.I_off), api._ptr(self.label), self.W, self.S,
+                                     self.per_scene, int(seed), api._ptr(self.seeds), api._ptr(self.wlo),
+                                     api._ptr(self.whi), api._stream(stream))
+        h.check(rc, "lp_scene_seeds")
+
+    def sets(self, geom, batch: Batch, stream=None):
+        make_sets(self.h, geom, self.p4, self.I_off, self.omega_v, self.seeds, self.wlo, self.whi, batch, self.axes,
+                  label=self.label, grainR=self.grainR, grainX=self.grainX, stream=stream)

@@ -20,7 +20,7 @@ def native():
 
 def _declared():
     text = open(os.path.join(ROOT, "include", "laueot.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(laue_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*|size_t|long long)\s+(laue_\w+)\s*\(", text, re.M)))
 
 
 def test_header_declares_the_boundary():

@@ -266,31 +266,43 @@ def test_adam_first_step_closed_form():
     np.testing.assert_allclose(P2["w"], -0.05 * np.sign(G2["w"]), rtol=1e-12)
 
 
+def test_scene_params_distribution():
+    S, G = 400, 8
+    key = np.array([3, 4], np.uint32)
+    t0, n_g, R, x = op.scene_params(S, G, 2, 6, 90, 10, key, 5.0)
+    assert t0.min() >= 0 and t0.max() <= 80 and n_g.min() >= 2 and n_g.max() <= 6
+    assert set(n_g.tolist()) == {2, 3, 4, 5, 6}
+    Rf = R.reshape(-1, 3, 3)
+    np.testing.assert_allclose(np.einsum("nji,njk->nik", Rf, Rf), np.broadcast_to(np.eye(3), Rf.shape), atol=1e-12)
+    np.testing.assert_allclose(np.linalg.det(Rf), 1.0, atol=1e-12)
+    # uniform on SO(3): E[R] = 0 and E[tr R] = 0 (Haar measure)
+    assert np.abs(Rf.mean(0)).max() < 0.05
+    assert abs(np.trace(Rf, axis1=1, axis2=2).mean()) < 0.06
+    assert np.abs(x).max() <= 2.5 and abs(x.mean()) < 0.1
+
+
 def test_training_scene_noiseless_matches_forward(planes):
-    rng = np.random.default_rng(13)
     S, G, W = 3, 4, 10
-    R = sg.random_rotations(S * G, rng).reshape(S, G, 3, 3)
-    x = rng.uniform(-2.5, 2.5, (S, G, 3))
-    n_g = np.array([4, 0, 2])
-    om = sg.omegas(BATCHED)
-    omega_v = np.concatenate([om[0:W], om[30:30 + W], om[80:90]])
     key = np.array([17, 99], np.uint32)
-    p, t, lab, I_off = op.training_scene(GEOM, planes, omega_v, W, R, x, n_g, key, 0.0, 0.7)
+    om = sg.omegas(BATCHED)
+    t0, n_g, R, x = op.scene_params(S, G, 0, G, len(om), W, key, 5.0)
+    n_g = np.array([4, 0, 2])
+    p, lab, I_off, omega_v = op.training_scene(GEOM, planes, om, t0, W, R, x, n_g, key, 0.0, 0.7)
     assert I_off[-1] == len(p)
     for v in range(S * W):
         s = v // W
+        assert omega_v[v] == om[t0[s] + v % W]
         sl = slice(I_off[v], I_off[v + 1])
         inl = lab[sl] >= 0
         f = oracle.forward(GEOM, planes, R[s, :n_g[s]].reshape(-1, 9), x[s, :n_g[s]], np.array([omega_v[v]]))
         assert inl.sum() == len(f["spot"])
-        np.testing.assert_array_equal(lab[sl][inl], f["grain"])
+        np.testing.assert_array_equal(lab[sl][inl], s * G + f["grain"])
         np.testing.assert_allclose(p[sl][inl], f["spot"], atol=1e-12)
         n_out = int((~inl).sum())
         u = op.uniform01(op.philox4x32(np.array([v, op.ALL, 0, op.TAG_COUNT], np.uint32), key)[0])
         assert n_out == math.floor(0.7 * inl.sum() + u)
         po = p[sl][~inl]
         assert np.all(np.abs(po[:, :2]) < 128.0) and np.all(np.abs(np.abs(po[:, 2]) - 200.0) == 0)
-        assert (t[sl] == v).all()
     assert (lab[I_off[W]:I_off[2 * W]] < 0).all()
     seeds = op.scene_seeds(lab, I_off, W, 5, key)
     for s in range(S):
@@ -303,15 +315,12 @@ def test_training_scene_noiseless_matches_forward(planes):
 
 
 def test_training_scene_noise_statistics(planes):
-    rng = np.random.default_rng(14)
     S, G, W = 2, 30, 10
-    R = sg.random_rotations(S * G, rng).reshape(S, G, 3, 3)
-    x = np.zeros((S, G, 3))
-    om = sg.omegas(BATCHED)
-    omega_v = np.concatenate([om[0:W], om[40:40 + W]])
     key = np.array([5, 6], np.uint32)
-    p0, _, l0, _ = op.training_scene(GEOM, planes, omega_v, W, R, x, np.array([G, G]), key, 0.0, 0.0)
-    p1, _, l1, _ = op.training_scene(GEOM, planes, omega_v, W, R, x, np.array([G, G]), key, 0.5, 0.0)
+    om = sg.omegas(BATCHED)
+    t0, n_g, R, x = op.scene_params(S, G, G, G, len(om), W, key, 0.0)
+    p0, l0, _, _ = op.training_scene(GEOM, planes, om, t0, W, R, x, n_g, key, 0.0, 0.0)
+    p1, l1, _, _ = op.training_scene(GEOM, planes, om, t0, W, R, x, n_g, key, 0.5, 0.0)
     # same counter -> same spot; keep the spots that stayed on the detector
     assert len(p1) <= len(p0) and len(p1) > 0.95 * len(p0)
     d = []
