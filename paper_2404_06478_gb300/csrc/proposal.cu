@@ -347,8 +347,14 @@ __global__ void __launch_bounds__(kSetThreads) sets_kernel(SetsArgs a) {
     __shared__ int wcnt[kSetThreads / 32];
     __shared__ int nsel_s, ties_s;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int n_total = a.I_off[a.n_angles];
     for (int b = blockIdx.x; b < a.B; b += gridDim.x) {
-        const int i0 = a.seeds[b];
+        int i0 = a.seeds[b];
+        const int wl = min(max(a.wlo[b], 0), a.n_angles), wh = min(max(a.whi[b], wl), a.n_angles);
+        if (i0 >= n_total) {
+            if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_INVALID_ARG);
+            i0 = -1;
+        }
         const size_t row0 = (size_t)b * KSET;
         if (i0 < 0) {
             for (int j = threadIdx.x; j < KSET * NF; j += blockDim.x) {
@@ -370,7 +376,7 @@ __global__ void __launch_bounds__(kSetThreads) sets_kernel(SetsArgs a) {
         const float4 s0 = a.axes[i0];
         const float3 n0 = make_float3(s0.x, s0.y, s0.z);
         const int t0 = __float_as_int(s0.w);
-        const int lo = a.I_off[a.wlo[b]], hi = a.I_off[a.whi[b]];
+        const int lo = a.I_off[wl], hi = a.I_off[wh];
         const int count = hi - lo - ((i0 >= lo && i0 < hi) ? 1 : 0);
         const int K = min(KSET - 1, count);
         uint32_t tau = 0xFFFFFFFFu;

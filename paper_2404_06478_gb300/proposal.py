@@ -111,6 +111,8 @@ class Batch:
 
     def __init__(self, h: api.Handle, n_sets: int):
         self.h, self.L, self.n = h, h.L, int(n_sets)
+        if h.ws is None:
+            h.reserve(1)
         self._raw, self.buf = _aligned(int(self.L.laue_lp_batch_bytes(self.n)), h.device)
         self.ids = torch.empty(self.n * KSET, dtype=torch.int32, device=h.device)
 
@@ -171,6 +173,8 @@ class Scenes:
 
     def __init__(self, h: api.Handle, S: int, W: int, Gmax: int, per_scene: int, capacity: int):
         dev = h.device
+        if h.ws is None:
+            h.reserve(1)
         self.h, self.S, self.W, self.Gmax, self.per_scene, self.capacity = h, S, W, Gmax, per_scene, capacity
         self.grainR = torch.empty(S * Gmax, 9, dtype=torch.float32, device=dev)
         self.grainX = torch.empty(S * Gmax, 3, dtype=torch.float32, device=dev)
