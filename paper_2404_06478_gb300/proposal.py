@@ -209,3 +209,50 @@ class Scenes:
     def sets(self, geom, batch: Batch, stream=None):
         make_sets(self.h, geom, self.p4, self.I_off, self.omega_v, self.seeds, self.wlo, self.whi, batch, self.axes,
                   label=self.label, grainR=self.grainR, grainX=self.grainX, stream=stream)
+
+
+def propose(h: api.Handle, net: Network, geom, obs: api.ObsSpots, omega: torch.Tensor, seeds, window: int = 10,
+            batch: Batch | None = None, stream=None):
+    """Candidate poses from the set encoder: for each seed spot (indices into
+    obs, chosen by the caller) the set of its window of `window` rotation
+    angles starting window//2 - 1 before the seed's angle (clipped to the
+    scan), the network's 8 hypotheses decoded to (R, x).  Returns R (n*8, 9)
+    and x (n*8, 3) on the device."""
+    import numpy as np
+    dev = h.device
+    seeds = np.asarray(seeds, np.int64)
+    I_off = obs.I_off.cpu().numpy().astype(np.int64)
+    T = len(I_off) - 1
+    t = np.searchsorted(I_off, seeds, side="right") - 1
+    lo = np.clip(t - (window // 2 - 1), 0, T)
+    hi = np.clip(lo + window, 0, T)
+    lo = np.clip(hi - window, 0, T)
+    n = len(seeds)
+    if batch is None or batch.n != n:
+        batch = Batch(h, n)
+    ti = lambda a: torch.tensor(a, dtype=torch.int32, device=dev)
+    axes = torch.empty(obs.p.shape[0], 4, dtype=torch.float32, device=dev)
+    make_sets(h, geom, obs.p, obs.I_off, omega, ti(seeds), ti(lo), ti(hi), batch, axes, stream=stream)
+    forward(h, net, batch, stream=stream)
+    return decode(h, batch, stream=stream)
+
+
+def train(h: api.Handle, geom, lat: api.Lattice, omega: torch.Tensor, steps: int, gmin: int = 1, gmax: int = 1,
+          S: int = 64, per_scene: int = 32, W: int = 10, lr: float = 1e-3, seed: int = 0, net: Network | None = None,
+          cube_mm: float = 5.0, sigma_mm: float = 0.5, outlier_ratio: float = 0.7, stream=None):
+    """Trains the set encoder on scenes the forward model simulates: every
+    step draws S fresh scenes of gmin..gmax grains (Philox keyed by seed and
+    step), builds per_scene seed-conditioned sets per scene and takes one
+    Adam step with a cosine-decayed learning rate.  Returns the network."""
+    import math
+    net = net if net is not None else Network(h, seed=seed, stream=stream)
+    cap = S * W * (max(gmax, 1) * 48 + 64)
+    sc = Scenes(h, S, W, max(gmax, 1), per_scene, cap)
+    batch = Batch(h, S * per_scene)
+    for it in range(steps):
+        lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * it / max(steps, 1)))
+        sc.generate(geom, lat, omega, (int(seed) << 32) + it + 1, gmin, gmax, cube_mm, sigma_mm, outlier_ratio,
+                    stream=stream)
+        sc.sets(geom, batch, stream=stream)
+        train_step(h, net, batch, lr_t, stream=stream)
+    return net
