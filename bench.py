@@ -125,7 +125,7 @@ def build_workload(dev, seed, api, sg, torch, grains=None, angles=None):
     nJ = np.diff(model.J_off.cpu().numpy())
     pairs_half = int(np.sum(nI.astype(np.int64) * nJ))
     return dict(cfg=cfg, geom=geom, h=h, lat=lat, om=om_t, obs=obs, ob=ob, model=model, R0=R0_t, x0=x0_t,
-                pairs_half=pairs_half, nI=int(nI.sum()), nJ=int(nJ.sum()), c_out=api.c_out_for(cfg.sigma_mm, geom.D))
+                R_true=R.reshape(-1, 3, 3), x_true=x, pairs_half=pairs_half, nI=int(nI.sum()), nJ=int(nJ.sum()), c_out=api.c_out_for(cfg.sigma_mm, geom.D))
 
 
 def em_step(W, api, R, x, stream=None):
@@ -163,6 +163,153 @@ def cpu_baseline_sample(W, seconds_hint=15.0):
                        % (blocks, pairs, dt))
 
 
+def _found_count(Rk, xk, R, x, tol_deg=0.5, tol_mm=0.5):
+    """True grains with a found grain within tol (cubic symmetry aware)."""
+    import itertools
+    syms = []
+    for perm in itertools.permutations(range(3)):
+        for sgn in itertools.product([1, -1], repeat=3):
+            S = np.zeros((3, 3))
+            for r, c in enumerate(perm):
+                S[r, c] = sgn[r]
+            if np.linalg.det(S) > 0:
+                syms.append(S)
+    n = 0
+    for g in range(len(R)):
+        if len(Rk) == 0:
+            break
+        M = np.einsum("kji,jl->kil", Rk, R[g])
+        best = np.full(len(Rk), 180.0)
+        for S in syms:
+            tr = np.trace(M @ S, axis1=1, axis2=2)
+            best = np.minimum(best, np.degrees(np.arccos(np.clip((tr - 1) / 2, -1, 1))))
+        n += bool(np.any((best < tol_deg) & (np.linalg.norm(xk - x[g], axis=1) < tol_mm)))
+    return n
+
+
+def proposal_bench(dev, api, sg, torch, peaks):
+    """The learned proposal: training throughput, the tensor-core GEMM of the
+    per-spot layers against its roofline, time-to-index of the plain and the
+    learned form on a workload both recover, and the oracle beside it."""
+    import dataclasses
+    import time
+    from paper_2404_06478_gb300 import proposal as pr
+    h = api.Handle(dev)
+    geom = sg.Geometry()
+    cfgB = sg.CONFIGS["batched"]
+    lat = api.Lattice.cubic(cfgB.a, cfgB.hmax, cfgB.centering, device=dev)
+    omega = torch.tensor(sg.omegas(cfgB), dtype=torch.float32, device=dev)
+    out = {}
+    # training: 8000 steps of 2048 sets (64 single-grain scenes x 32 seeds)
+    steps = 8000
+    pr.train(h, geom, lat, omega, steps=20, seed=1)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    net = pr.train(h, geom, lat, omega, steps=steps, gmin=1, gmax=1, seed=7)
+    e1.record()
+    torch.cuda.synchronize()
+    tr_s = e0.elapsed_time(e1) / 1e3
+    out["train"] = dict(steps=steps, sets_per_step=2048, seconds=tr_s, sets_per_s=steps * 2048 / tr_s,
+                        ms_per_step=tr_s * 1e3 / steps, data="single-grain scenes simulated on the GPU")
+    # the per-spot GEMMs at training-batch size (inputs > L2)
+    Ms = 2048 * 128
+    A = torch.randn(Ms, 256, device=dev).to(torch.bfloat16)
+    B = (torch.randn(256, 256, device=dev) * 0.05).to(torch.bfloat16)
+    bias = torch.zeros(256, device=dev)
+    D = torch.empty(Ms, 256, dtype=torch.bfloat16, device=dev)
+    DT = torch.empty(256, Ms, dtype=torch.bfloat16, device=dev)
+    At = torch.randn(256, Ms, device=dev).to(torch.bfloat16)
+    Bt = torch.randn(256, Ms, device=dev).to(torch.bfloat16)
+    part = torch.empty(128, 256, 256, device=dev)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps / 1e3
+
+    t_fwd = timed(lambda: pr.gemm_bf16(h, A, B, mode=1, bias=bias, out=D, outT=DT))
+    t_wg = timed(lambda: pr.gemm_bf16(h, At, Bt, mode=0, splits=128, out_f32=part))
+    fl = 2.0 * Ms * 256 * 256
+    by_fwd = Ms * 256 * 2 + 2 * Ms * 256 * 2 + 256 * 256 * 2
+    by_wg = 2 * 256 * Ms * 2 + 128 * 256 * 256 * 4
+    hbm, bf = peaks.get("hbm_gbs", 6800.0), peaks.get("bf16_tflops", 1900.0)
+    out["gemm"] = dict(
+        kernel="gemm_tc_kernel (tcgen05, TMA, TMEM)",
+        forward_layer=dict(shape="M=%d N=256 K=256, bias+ReLU, BF16 out row-major + transposed" % Ms,
+                           us=t_fwd * 1e6, tflops=fl / t_fwd / 1e12, tensor_frac_of_measured=fl / t_fwd / 1e12 / bf,
+                           roofline=dict(bound="hbm", achieved=by_fwd / t_fwd / 1e9, peak=hbm, unit="GB/s",
+                                         frac=by_fwd / t_fwd / 1e9 / hbm, traffic=None,
+                                         algorithmic_bytes=by_fwd)),
+        weight_grad=dict(shape="M=256 N=256 K=%d, split-K 128, FP32 partials" % Ms, us=t_wg * 1e6,
+                         tflops=fl / t_wg / 1e12, tensor_frac_of_measured=fl / t_wg / 1e12 / bf,
+                         roofline=dict(bound="hbm", achieved=by_wg / t_wg / 1e9, peak=hbm, unit="GB/s",
+                                       frac=by_wg / t_wg / 1e9 / hbm, traffic=None, algorithmic_bytes=by_wg)),
+        peaks_basis="MEASURED_PEAKS.json (hbm_gbs %.1f, bf16_tflops %.1f)" % (hbm, bf))
+    del A, B, D, DT, At, Bt, part
+    # time to index: 5 grains, the batched geometry (90 rotations, |hkl| <= 6, 70% outliers)
+    W5 = build_workload(dev, 5, api, sg, torch, grains=5)
+    ob, om = W5["ob"], W5["om"]
+    Rtrue = W5["R_true"]
+    xtrue = W5["x_true"]
+    cfg5 = W5["cfg"]
+    kw = dict(n_em=20, n_sinkhorn=100, k_single=8, f_out=0.3)
+    res = {}
+    for form in ("plain", "learned"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if form == "plain":
+            n = 200000
+            R0 = torch.tensor(sg.super_fibonacci(n).reshape(-1, 9), dtype=torch.float32, device=dev)
+            x0 = torch.zeros(n, 3, device=dev)
+        else:
+            seeds = np.random.default_rng(5).choice(W5["nI"], 2500, replace=False)
+            R0, x0 = pr.propose(h, net, geom, ob, om, seeds)
+        Rf, xf, _ = api.index(h, geom, lat, ob, om, R0, x0, cfg5.eps, W5["c_out"], 50, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        found = _found_count(Rf.cpu().numpy().reshape(-1, 3, 3).astype(np.float64),
+                             xf.cpu().numpy().astype(np.float64), Rtrue, xtrue)
+        res[form] = dict(starts=int(R0.shape[0]), seconds=dt, grains_found=found, k_star=int(Rf.shape[0]))
+    out["time_to_index"] = dict(workload="5 grains, |hkl|<=6 bcc, 90 rotations over 360 deg, 0.5 mm noise, "
+                                         "70% uneven outliers; found = within 0.5 deg and 0.5 mm of the truth",
+                                plain=res["plain"], learned=res["learned"],
+                                speedup=res["plain"]["seconds"] / res["learned"]["seconds"],
+                                plain_starts="200k super-Fibonacci orientations at the cube centre",
+                                learned_starts="2500 random seed spots x 8 hypotheses")
+    assert h.device_status() == 0
+    return out
+
+
+def proposal_cpu_baseline():
+    """The oracle's set encoder (FP64, BF16-emulating) forward + backward on a
+    bounded sample of 8 sets, timed on one host core."""
+    import time
+    import oracle.proposal as op
+    rng = np.random.default_rng(0)
+    P = op.init_params(rng)
+    B = 8
+    X = np.zeros((B, op.KSET, op.NF))
+    X[:, :, :14] = rng.standard_normal((B, op.KSET, 14))
+    X[:, :, 12] = 1.0
+    Rt = np.stack([np.eye(3)] * B)
+    xt = np.zeros((B, 3))
+    t0 = time.perf_counter()
+    O, cache = op.forward(P, X, bf16_ops=True)
+    _, dO, _, _ = op.set_loss(O, Rt, xt, np.ones(B))
+    op.backward(P, cache, dO)
+    dt = time.perf_counter() - t0
+    return dict(value=B / dt, unit="sets/s (forward + backward)", cores=1, kind="oracle",
+                sample="%d sets of 128 spots" % B)
+
+
 def run_reference(args):
     rank, world, local = _dist_env()
     if rank != 0:
@@ -196,6 +343,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grains", type=int, default=None, help="smaller case for profiling (not a bench line)")
     ap.add_argument("--angles", type=int, default=None, help="smaller case for profiling (not a bench line)")
+    ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal measurements")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -324,6 +472,14 @@ def main():
                  d2h_bytes_per_step=int(d2h)),
         gpu_launches=launches_per_step * args.steps,
     )
+    if rank == 0 and not args.no_proposal:
+        peaks = {}
+        pk_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+        if os.path.exists(pk_path):
+            peaks = json.load(open(pk_path))
+        line["proposal"] = proposal_bench(dev, api, sg, torch, peaks)
+        if not args.no_cpu_baseline:
+            line["proposal"]["cpu_baseline"] = proposal_cpu_baseline()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(W)
     if rank == 0:
