@@ -344,9 +344,28 @@ def main():
     ap.add_argument("--grains", type=int, default=None, help="smaller case for profiling (not a bench line)")
     ap.add_argument("--angles", type=int, default=None, help="smaller case for profiling (not a bench line)")
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal measurements")
+    ap.add_argument("--only-proposal-train", type=int, default=0,
+                    help="run only this many set-encoder training steps (profiling; not a bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_proposal_train:
+        import torch
+        from paper_2404_06478_gb300 import api, build, proposal as pr
+        import synthgen as sg
+        build.build()
+        dev = torch.device("cuda", 0)
+        h = api.Handle(dev)
+        cfgB = sg.CONFIGS["batched"]
+        lat = api.Lattice.cubic(cfgB.a, cfgB.hmax, cfgB.centering, device=dev)
+        omega = torch.tensor(sg.omegas(cfgB), dtype=torch.float32, device=dev)
+        t0 = time.perf_counter()
+        pr.train(h, sg.Geometry(), lat, omega, steps=args.only_proposal_train, seed=3)
+        torch.cuda.synchronize()
+        assert h.device_status() == 0
+        print(json.dumps(dict(proposal_train_steps=args.only_proposal_train, sets_per_step=2048,
+                              seconds=time.perf_counter() - t0)))
+        return 0
     rank, world, local = _dist_env()
     import torch
     import torch.distributed as dist

@@ -428,15 +428,16 @@ int laue_gemm_bf16(laue_handle* h, const void* A, long long lda, const void* B, 
  * laue_lp_batch_bytes(n_sets) bytes (features, activations, errors, head
  * arrays); both 256-byte aligned and owned by the caller.
  * laue_lp_batch_offset(n_sets, region) is the byte offset of a region of
- * the batch buffer (-1 if unknown): 0 X (n_sets*128 x 64 BF16 features),
+ * the batch buffer (-1 if unknown): 0 X (n_sets*set_size x 64 BF16 features),
  * 1 X^T, 2 seed frames F (n_sets x 9 FP32, row-major, columns n0 a1 a2),
  * 3 valid elements per set (int), 4 R_loc targets (n_sets x 9), 5 position
  * targets (n_sets x 3, x / 2.5 mm), 6 set valid flags (FP32), 7 network
  * outputs O (n_sets x 72: 8 hypotheses of 6-D rotation + 3-D position),
  * 8 per-set losses, 9 per-set best rotation error, 10 best hypothesis
- * (int), 11 H1, 12 H3 (n_sets*128 x 256 BF16), 13 pooled features
+ * (int), 11 H1, 12 H3 (n_sets*set_size x 256 BF16), 13 pooled features
  * (n_sets x 512 FP32), 14 dL/dO, 15 dL/dZ3 (BF16). */
 size_t laue_lp_param_count(void);
+size_t laue_lp_set_size(void); /* spots per set (the seed + its nearest neighbours) */
 size_t laue_lp_net_bytes(void);
 size_t laue_lp_batch_bytes(int n_sets);
 long long laue_lp_batch_offset(int n_sets, int region);
@@ -485,13 +486,13 @@ int laue_lp_scene_seeds(laue_handle* h, const int* I_off, const int* label, int 
  * window of angles [wlo[b], whi[b]).  Each spot's sample-frame axis is
  * n = Gamma_t^T u with u parallel to p/|p| - e (the plane normal of a
  * reflection off a grain at the origin, Eq. ray_mnt); the set holds the
- * seed and the 127 spots of the window whose axes are nearest the seed's
+ * seed and the laue_lp_set_size() - 1 spots of the window whose axes are nearest the seed's
  * (distance 1 - |n.n0|, ties by index), as 64 BF16 features in the seed
  * frame [n0, a1, n0 x a1] (a1: unit part of +y orthogonal to n0), written
  * to the batch buffer (regions 0-3).  With label (spot -> grain, -1 for an
  * outlier) and grainR / grainX (9 and 3 FP32 per grain), the targets
  * R_loc = F0^T R and x / 2.5 mm and the valid flags are written too.
- * axes_scratch: 16 n_cap bytes.  ids (n_sets x 128 ints, -1 for padding)
+ * axes_scratch: 16 n_cap bytes.  ids (n_sets x set_size ints, -1 for padding)
  * may be NULL.  Asynchronous. */
 int laue_lp_sets(laue_handle* h, const LaueGeometry* geom, const float* p, const int* I_off,
                  const float* omega, int n_angles, int n_cap, const int* seeds, const int* wlo,

@@ -121,6 +121,7 @@ SIGNATURES = {
 # host helpers that return sizes and offsets rather than a status
 SIZE_FUNCTIONS = [
     ("laue_lp_param_count", [], ctypes.c_size_t),
+    ("laue_lp_set_size", [], ctypes.c_size_t),
     ("laue_lp_net_bytes", [], ctypes.c_size_t),
     ("laue_lp_batch_bytes", [_i], ctypes.c_size_t),
     ("laue_lp_batch_offset", [_i, _i], ctypes.c_longlong),

@@ -6,7 +6,7 @@
 //
 // One CTA computes one 128 x BN tile (BN = 64, 128 or 256) over a range of K
 // (split-K along gridDim.z).  Warp 0, lane 0 streams 128 x 64 and BN x 64
-// operand tiles into a four-stage shared-memory ring with TMA
+// operand tiles into a two- or four-stage shared-memory ring with TMA
 // (cp.async.bulk.tensor, 128-byte swizzle); warp 1, lane 0 issues
 // tcgen05.mma (M = 128, N = BN, K = 16 per instruction) into a BN-column
 // FP32 accumulator in tensor memory and releases each stage with
@@ -32,7 +32,6 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;  // one 128-byte swizzle row of BF16
-constexpr int kStages = 4;
 constexpr int kThreads = 128;
 constexpr uint32_t kAStage = kBM * kBK * 2;
 
@@ -109,7 +108,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// kStages ring slots: 4 for long K ranges; 2 for K <= 256 (four k-blocks),
+// which halves the shared memory so that two CTAs share an SM and one CTA's
+// epilogue overlaps the other's loads.
+template <int kStages>
+__global__ void __launch_bounds__(kThreads, kStages == 2 ? 2 : 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmArgs a) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
@@ -266,7 +269,9 @@ bool make_tmap(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols, 
 
 }  // namespace
 
-size_t gemm_tc_smem(int BN) { return 1024 + (size_t)kStages * (kAStage + (size_t)BN * kBK * 2); }
+static int stages_for(int nkb) { return nkb <= 4 ? 2 : 4; }
+
+size_t gemm_tc_smem(int BN, int stages) { return 1024 + (size_t)stages * (kAStage + (size_t)BN * kBK * 2); }
 
 int gemm_tc_check(const GemmOperands& op, const GemmArgs& a, int splits) {
     if (!(a.BN == 64 || a.BN == 128 || a.BN == 256)) return LAUE_ERR_INVALID_ARG;
@@ -292,11 +297,19 @@ cudaError_t gemm_tc_run(const GemmOperands& op, GemmArgs a, int splits, cudaStre
         !make_tmap(&tB, op.B, (uint64_t)a.N, (uint64_t)a.K, op.ldb, (uint32_t)a.BN))
         return cudaErrorInvalidValue;
     a.kb_per_split = a.K / kBK / splits;
-    size_t smem = gemm_tc_smem(a.BN);
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    int stages = stages_for(a.kb_per_split);
+    size_t smem = gemm_tc_smem(a.BN, stages);
     dim3 grid(a.M / kBM, a.N / a.BN, splits);
-    gemm_tc_kernel<<<grid, kThreads, smem, s>>>(tA, tB, a);
+    cudaError_t e;
+    if (stages == 2) {
+        e = cudaFuncSetAttribute(gemm_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        gemm_tc_kernel<2><<<grid, kThreads, smem, s>>>(tA, tB, a);
+    } else {
+        e = cudaFuncSetAttribute(gemm_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        gemm_tc_kernel<4><<<grid, kThreads, smem, s>>>(tA, tB, a);
+    }
     return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ struct GemmArgs {
     int* ctrl;                  // status word
 };
 
-size_t gemm_tc_smem(int BN);
+size_t gemm_tc_smem(int BN, int stages);
 int gemm_tc_check(const GemmOperands& op, const GemmArgs& a, int splits);
 cudaError_t gemm_tc_run(const GemmOperands& op, GemmArgs a, int splits, cudaStream_t s);
 

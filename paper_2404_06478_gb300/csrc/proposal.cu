@@ -10,7 +10,7 @@
 //                    wavelength, model_spot_cut) with detector noise and
 //                    uniform outliers, seeds drawn among the inliers;
 //   sets             sample-frame spot axes (u parallel to rhat - e, n =
-//                    Gamma_t^T u), the 127 nearest axes to the seed's in its
+//                    Gamma_t^T u), the KSET - 1 nearest axes to the seed's in its
 //                    rotation window by a three-round radix select, features
 //                    in the seed frame (BF16, row-major and transposed);
 //   network          per-spot layers on the tcgen05 GEMM (gemm_tc.cu),
@@ -785,32 +785,37 @@ __global__ void loss_kernel(const float* O, const float* Rt, const float* xt, co
 }
 
 // dZ3 = (dmean / nv on valid rows + dmax at the argmax row) where H3 > 0,
-// rounded to BF16, written row-major and transposed (staged in shared memory)
+// rounded to BF16, written row-major and transposed (staged in shared memory
+// 128 rows at a time)
+constexpr int kTileRows = 128;
 constexpr int kTileLd = WIDTH + 2;
 __global__ void __launch_bounds__(WIDTH) pool_backward_kernel(const __nv_bfloat16* H3, const int* nvalid,
                                                               const int* amax, const float* dPool, int B,
                                                               long long Ms, __nv_bfloat16* dZ3,
                                                               __nv_bfloat16* dZ3t) {
-    extern __shared__ __nv_bfloat16 tile[];  // KSET x kTileLd
+    extern __shared__ __nv_bfloat16 tile[];  // kTileRows x kTileLd
     for (int b = blockIdx.x; b < B; b += gridDim.x) {
         int c = threadIdx.x, nv = nvalid[b];
         float dm = nv > 0 ? dPool[(size_t)b * 2 * WIDTH + c] / (float)nv : 0.0f;
         float dx = dPool[(size_t)b * 2 * WIDTH + WIDTH + c];
         int am = amax[(size_t)b * WIDTH + c];
-        for (int e = 0; e < KSET; ++e) {
-            size_t row = (size_t)b * KSET + e;
-            float v = (e < nv ? dm : 0.0f) + (nv > 0 && e == am ? dx : 0.0f);
-            float h = bf(H3[row * WIDTH + c]);
-            __nv_bfloat16 z = __float2bfloat16_rn(h > 0.0f ? v : 0.0f);
-            dZ3[row * WIDTH + c] = z;
-            tile[e * kTileLd + c] = z;
+        for (int e0 = 0; e0 < KSET; e0 += kTileRows) {
+            for (int q = 0; q < kTileRows; ++q) {
+                int e = e0 + q;
+                size_t row = (size_t)b * KSET + e;
+                float v = (e < nv ? dm : 0.0f) + (nv > 0 && e == am ? dx : 0.0f);
+                float h = bf(H3[row * WIDTH + c]);
+                __nv_bfloat16 z = __float2bfloat16_rn(h > 0.0f ? v : 0.0f);
+                dZ3[row * WIDTH + c] = z;
+                tile[q * kTileLd + c] = z;
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < kTileRows * WIDTH; idx += blockDim.x) {
+                int cc = idx / kTileRows, q = idx % kTileRows;
+                dZ3t[(size_t)cc * Ms + (size_t)b * KSET + e0 + q] = tile[q * kTileLd + cc];
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < KSET * WIDTH; idx += blockDim.x) {
-            int cc = idx / KSET, e = idx % KSET;
-            dZ3t[(size_t)cc * Ms + (size_t)b * KSET + e] = tile[e * kTileLd + cc];
-        }
-        __syncthreads();
     }
 }
 
@@ -891,9 +896,10 @@ cudaError_t upload_syms() {
 }
 
 int splits_for(int B) {
-    // K = B KSET rows = 2 B blocks of 64; the largest power of two <= 128 dividing 2 B
+    // K = B KSET rows = B KSET / 64 blocks of 64; the largest power of two <= 128 dividing them
+    long long kb = (long long)B * KSET / 64;
     int s = 1;
-    while (s * 2 <= kMaxSplits && (2 * B) % (s * 2) == 0) s *= 2;
+    while (s * 2 <= kMaxSplits && kb % (s * 2) == 0) s *= 2;
     return s;
 }
 
@@ -989,7 +995,7 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
                    nullptr, 0, nullptr, 0, s)))
         return e;
     // pooling -> dZ3
-    size_t tsm = (size_t)KSET * kTileLd * 2;
+    size_t tsm = (size_t)kTileRows * kTileLd * 2;
     if ((e = cudaFuncSetAttribute(pool_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)))
         return e;
     pool_backward_kernel<<<B, WIDTH, tsm, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), bt.at<int>(L.amax),
@@ -1049,6 +1055,7 @@ using namespace laue;
 using namespace laue::lp;
 
 extern "C" size_t laue_lp_param_count(void) { return kParams; }
+extern "C" size_t laue_lp_set_size(void) { return KSET; }
 extern "C" size_t laue_lp_net_bytes(void) { return net_layout().total; }
 extern "C" size_t laue_lp_batch_bytes(int n_sets) { return n_sets > 0 ? batch_layout(n_sets).total : 0; }
 

@@ -9,7 +9,7 @@
 namespace laue {
 namespace lp {
 
-constexpr int KSET = 128;   // spots per set: the seed + 127 neighbours
+constexpr int KSET = 128;   // spots per set: the seed + 127 neighbours (a multiple of 128)
 constexpr int NF = 64;      // feature width (14 used)
 constexpr int WIDTH = 256;  // per-spot MLP width
 constexpr int HEADW = 256;  // head hidden width

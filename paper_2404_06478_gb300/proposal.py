@@ -31,7 +31,8 @@ def gemm_bf16(h: api.Handle, A: torch.Tensor, B: torch.Tensor, mode: int = 0, bn
 
 
 # ---------------------------------------------------------------- set encoder
-KSET, NF, NHYP, NOUT = 128, 64, 8, 72
+NF, NHYP, NOUT = 64, 8, 72
+KSET = 128  # spots per set; equals laue_lp_set_size() of the library (checked by the tests)
 REGIONS = dict(X=0, Xt=1, F=2, nvalid=3, Rt=4, xt=5, svalid=6, O=7, loss=8, dbest=9, hbest=10, H1=11, H3=12,
                pool=13, dO=14, dZ3=15)
 PARAM_SHAPES = [("W1", (256, 64)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),

@@ -56,3 +56,12 @@ def test_invalid_arguments_rejected_without_gpu(native):
     assert L.laue_reflections(2.87, 4, 1, 0, None, None, None, ctypes.byref(M)) == native.LAUE_ERR_CAPACITY
     assert M.value == 145
     assert L.laue_create(None, 0) == native.LAUE_ERR_INVALID_ARG
+
+
+def test_set_encoder_sizes_match_the_oracle(native):
+    import oracle.proposal as op
+    from paper_2404_06478_gb300 import proposal as pr
+    L = native.lib()
+    assert L.laue_lp_set_size() == op.KSET == pr.KSET
+    assert L.laue_lp_param_count() == sum(int(np.prod(s)) for _, s in op.PARAM_SHAPES)
+    assert [n for n, _ in op.PARAM_SHAPES] == [n for n, _ in pr.PARAM_SHAPES]
