@@ -236,6 +236,8 @@ def proposal_bench(dev, api, sg, torch, peaks):
         return a.elapsed_time(b) / reps / 1e3
 
     t_fwd = timed(lambda: pr.gemm_bf16(h, A, B, mode=1, bias=bias, out=D, outT=DT))
+    # context for write-heavy kernels: a plain fill of the same output bytes
+    t_fill = timed(lambda: DT.fill_(1.0))
     t_wg = timed(lambda: pr.gemm_bf16(h, At, Bt, mode=0, splits=128, out_f32=part))
     fl = 2.0 * Ms * 256 * 256
     by_fwd = Ms * 256 * 2 + 2 * Ms * 256 * 2 + 256 * 256 * 2
@@ -252,7 +254,10 @@ def proposal_bench(dev, api, sg, torch, peaks):
                          tflops=fl / t_wg / 1e12, tensor_frac_of_measured=fl / t_wg / 1e12 / bf,
                          roofline=dict(bound="hbm", achieved=by_wg / t_wg / 1e9, peak=hbm, unit="GB/s",
                                        frac=by_wg / t_wg / 1e9 / hbm, traffic=None, algorithmic_bytes=by_wg)),
-        peaks_basis="MEASURED_PEAKS.json (hbm_gbs %.1f, bf16_tflops %.1f)" % (hbm, bf))
+        peaks_basis="MEASURED_PEAKS.json (hbm_gbs %.1f, bf16_tflops %.1f)" % (hbm, bf),
+        write_only_GBs=DT.numel() * 2 / t_fill / 1e9,
+        write_note="a plain fill (torch) of one output array runs at write_only_GBs: the forward layer "
+                   "writes 2 bytes per input byte, so its floor is set by HBM writes, not by the copy peak")
     del A, B, D, DT, At, Bt, part
     # time to index: 5 grains, the batched geometry (90 rotations, |hkl| <= 6, 70% outliers)
     W5 = build_workload(dev, 5, api, sg, torch, grains=5)

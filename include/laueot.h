@@ -412,12 +412,15 @@ int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
  * even) into D_bf16 (M x N row-major) and/or DT_bf16 (N rows of leading
  * dimension ldt >= M: DT[n][m]); splits must be 1.  mode 2: acc where the
  * BF16 mask[m][n] (M x N row-major) is > 0, else 0, same outputs.
+ * Modes 1 and 2 with N = 256, K in {64, 256} run a persistent,
+ * warp-specialised kernel (weights resident in shared memory, two tensor-
+ * memory accumulators); flags bit 0 forces the one-tile-per-CTA kernel.
  * Asynchronous on `stream`; device memory is the caller's.  Needs the
  * workspace (status word).  Errors: LAUE_ERR_INVALID_ARG for shapes,
  * alignment or a missing output. */
 int laue_gemm_bf16(laue_handle* h, const void* A, long long lda, const void* B, long long ldb, int M,
                    int N, int K, int bn, int splits, int mode, const float* bias, const void* mask,
-                   float* D_f32, void* D_bf16, void* DT_bf16, long long ldt, void* stream);
+                   float* D_f32, void* D_bf16, void* DT_bf16, long long ldt, int flags, void* stream);
 
 /* Sizes of the set encoder's buffers (host helpers, no device work).
  * Parameter vector (FP32, laue_lp_param_count() values): W1 (256 x 64), b1,

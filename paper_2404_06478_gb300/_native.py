@@ -114,7 +114,7 @@ SIGNATURES = {
     "laue_lp_train_step": [_vp, _vp, _vp, _i, _f, _vp],
     "laue_lp_decode": [_vp, _vp, _i, _vp, _vp, _vp],
     "laue_gemm_bf16": [_vp, _vp, ctypes.c_longlong, _vp, ctypes.c_longlong, _i, _i, _i, _i, _i, _i, _vp, _vp,
-                       _vp, _vp, _vp, ctypes.c_longlong, _vp],
+                       _vp, _vp, _vp, ctypes.c_longlong, _i, _vp],
 }
 
 

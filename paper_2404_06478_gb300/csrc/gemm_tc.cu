@@ -108,6 +108,46 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+__device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Epilogue of 32 accumulator columns of row m (modes 1 and 2).  Measured:
+// staging these stores through shared memory for 16-byte coalesced writes
+// gains nothing here, because the layer is bound by HBM write bandwidth
+// (a plain fill of the same bytes runs at about 3.8 TB/s).
+__device__ __forceinline__ void epilogue32(const GemmArgs& a, int m, int n, float* v) {
+    if (a.mode == 1) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + a.bias[n + j], 0.0f);
+    } else {
+        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + (size_t)m * a.N + n);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint4 w = mk[q];
+            uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                uint32_t lo = ws[h] & 0xFFFFu, hi = ws[h] >> 16;
+                if (!(lo != 0u && (lo & 0x8000u) == 0u)) v[8 * q + 2 * h] = 0.0f;
+                if (!(hi != 0u && (hi & 0x8000u) == 0u)) v[8 * q + 2 * h + 1] = 0.0f;
+            }
+        }
+    }
+    if (a.Dh) {
+        uint4* dst = reinterpret_cast<uint4*>(a.Dh + (size_t)m * a.N + n);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            dst[q] = make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
+                                pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+    }
+    if (a.DhT) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a.DhT[(size_t)(n + j) * a.ldt + m] = __float2bfloat16_rn(v[j]);
+    }
+}
+
 // kStages ring slots: 4 for long K ranges; 2 for K <= 256 (four k-blocks),
 // which halves the shared memory so that two CTAs share an SM and one CTA's
 // epilogue overlaps the other's loads.
@@ -198,35 +238,7 @@ __global__ void __launch_bounds__(kThreads, kStages == 2 ? 2 : 1)
             for (int j = 0; j < 8; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
             continue;
         }
-        if (a.mode == 1) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + a.bias[n + j], 0.0f);
-        } else {
-            const uint4* mk = reinterpret_cast<const uint4*>(a.mask + (size_t)m * a.N + n);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint4 w = mk[q];
-                uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    // a BF16 value is positive iff its sign bit is clear and it is not zero
-                    uint32_t lo = ws[h] & 0xFFFFu, hi = ws[h] >> 16;
-                    if (!(lo != 0u && (lo & 0x8000u) == 0u)) v[8 * q + 2 * h] = 0.0f;
-                    if (!(hi != 0u && (hi & 0x8000u) == 0u)) v[8 * q + 2 * h + 1] = 0.0f;
-                }
-            }
-        }
-        if (a.Dh) {
-            uint4* dst = reinterpret_cast<uint4*>(a.Dh + (size_t)m * a.N + n);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                dst[q] = make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
-                                    pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
-        }
-        if (a.DhT) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) a.DhT[(size_t)(n + j) * a.ldt + m] = __float2bfloat16_rn(v[j]);
-        }
+        epilogue32(a, m, n, v);
     }
     tc_fence_before();
     __syncthreads();
@@ -234,6 +246,132 @@ __global__ void __launch_bounds__(kThreads, kStages == 2 ? 2 : 1)
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN)
                      : "memory");
+    }
+}
+
+// Persistent, warp-specialised form for the per-spot layers (N = 256,
+// K = 64 KB, modes 1 and 2).  The 256 x K weight operand is loaded once per
+// CTA and stays in shared memory; 128-row tiles of A stream through a
+// four-stage ring; two 256-column FP32 accumulators fill all of tensor
+// memory, so the epilogue of one tile runs while the next is multiplied.
+// Warp 0 (one lane) loads, warp 1 (one lane) issues the MMAs, warps 2-5
+// drain the accumulators (warp w reads tensor-memory lanes 32 (w % 4) ..).
+constexpr int kPThreads = 192;
+constexpr int kPStages = 4;
+constexpr uint32_t kBBlock = 256u * kBK * 2;  // one 64-wide k-block of the 256-row weight operand
+
+template <int KB>
+__global__ void __launch_bounds__(kPThreads, 1)
+    gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                              GemmArgs a, int n_tiles) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t a_full[kPStages], a_empty[kPStages], b_full, acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_base_s;
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sB = smem;
+    uint8_t* sA = smem + KB * kBBlock;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kPStages; ++s) {
+            mbar_init(&a_full[s], 1);
+            mbar_init(&a_empty[s], 1);
+        }
+        mbar_init(&b_full, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 128);
+        }
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_s)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_s;
+
+    if (warp == 0 && lane == 0) {
+        mbar_expect_tx(&b_full, KB * kBBlock);
+        for (int kb = 0; kb < KB; ++kb) tma_load_2d(sB + kb * kBBlock, &tmB, kb * kBK, 0, &b_full);
+        int g = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+            for (int kb = 0; kb < KB; ++kb, ++g) {
+                int s = g % kPStages;
+                uint32_t ph = (uint32_t)(g / kPStages) & 1u;
+                if (g >= kPStages && !mbar_wait_bounded(&a_empty[s], ph ^ 1u)) {
+                    set_status(a.ctrl, LAUE_ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&a_full[s], kAStage);
+                tma_load_2d(sA + s * kAStage, &tmA, kb * kBK, tile * kBM, &a_full[s]);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16(kBM, 256);
+        bool ok = mbar_wait_bounded(&b_full, 0);
+        if (!ok) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
+        tc_fence_after();
+        int g = 0, i = 0;
+        for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++i) {
+            int buf = i & 1, u = i >> 1;
+            if (u >= 1 && !mbar_wait_bounded(&acc_empty[buf], (uint32_t)(u & 1) ^ 1u)) {
+                set_status(a.ctrl, LAUE_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)buf * 256u;
+            for (int kb = 0; kb < KB; ++kb, ++g) {
+                int s = g % kPStages;
+                uint32_t ph = (uint32_t)(g / kPStages) & 1u;
+                if (!mbar_wait_bounded(&a_full[s], ph)) {
+                    set_status(a.ctrl, LAUE_ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                uint32_t aBase = smem_u32(sA + s * kAStage), bBase = smem_u32(sB + kb * kBBlock);
+#pragma unroll
+                for (int k = 0; k < kBK / 16; ++k)
+                    tc_mma(d, sdesc_sw128(aBase + 32u * k), sdesc_sw128(bBase + 32u * k), idesc,
+                           (kb > 0 || k > 0) ? 1u : 0u);
+                tc_commit(&a_empty[s]);
+            }
+            tc_commit(&acc_full[buf]);
+        }
+    } else if (warp >= 2) {
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
+            int buf = i & 1, u = i >> 1;
+            if (!mbar_wait_bounded(&acc_full[buf], (uint32_t)(u & 1))) {
+                if (lane == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            const int m = tile * kBM + row;
+            for (int c0 = 0; c0 < 256; c0 += 32) {
+                float v[32];
+                tc_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u + (uint32_t)c0, v);
+                epilogue32(a, m, c0, v);
+            }
+            tc_fence_before();
+            mbar_arrive1(&acc_empty[buf]);
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
     }
 }
 
@@ -291,11 +429,43 @@ int gemm_tc_check(const GemmOperands& op, const GemmArgs& a, int splits) {
     return LAUE_OK;
 }
 
+static int sm_count_cached() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 1;
+    }
+    return sms;
+}
+
+template <int KB>
+static cudaError_t launch_persistent(const CUtensorMap& tA, const CUtensorMap& tB, const GemmArgs& a,
+                                     cudaStream_t s) {
+    size_t smem = 1024 + (size_t)KB * kBBlock + (size_t)kPStages * kAStage;
+    // one CTA per SM: it holds all 512 tensor-memory columns, so a second CTA
+    // on the SM would wait in tcgen05.alloc; ask for more than half the SM's
+    // shared memory so that the scheduler never co-locates two
+    if (smem < 120 * 1024) smem = 120 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_persistent_kernel<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int n_tiles = a.M / kBM;
+    int grid = n_tiles < sm_count_cached() ? n_tiles : sm_count_cached();
+    gemm_tc_persistent_kernel<KB><<<grid, kPThreads, smem, s>>>(tA, tB, a, n_tiles);
+    return cudaGetLastError();
+}
+
 cudaError_t gemm_tc_run(const GemmOperands& op, GemmArgs a, int splits, cudaStream_t s) {
     CUtensorMap tA, tB;
     if (!make_tmap(&tA, op.A, (uint64_t)a.M, (uint64_t)a.K, op.lda, kBM) ||
         !make_tmap(&tB, op.B, (uint64_t)a.N, (uint64_t)a.K, op.ldb, (uint32_t)a.BN))
         return cudaErrorInvalidValue;
+    if (!a.simple && a.mode != 0 && splits == 1 && a.N == 256 && a.BN == 256) {
+        if (a.K == 64) return launch_persistent<1>(tA, tB, a, s);
+        if (a.K == 256) return launch_persistent<4>(tA, tB, a, s);
+    }
     a.kb_per_split = a.K / kBK / splits;
     int stages = stages_for(a.kb_per_split);
     size_t smem = gemm_tc_smem(a.BN, stages);
@@ -319,7 +489,8 @@ using namespace laue;
 
 extern "C" int laue_gemm_bf16(laue_handle* h, const void* A, long long lda, const void* B, long long ldb, int M,
                               int N, int K, int bn, int splits, int mode, const float* bias, const void* mask,
-                              float* D_f32, void* D_bf16, void* DT_bf16, long long ldt, void* stream) {
+                              float* D_f32, void* D_bf16, void* DT_bf16, long long ldt, int flags,
+                              void* stream) {
     if (!h) return LAUE_ERR_INVALID_ARG;
     if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set");
     if (!A || !B || lda <= 0 || ldb <= 0) return laue_fail(h, LAUE_ERR_INVALID_ARG, "null or empty operand");
@@ -337,6 +508,7 @@ extern "C" int laue_gemm_bf16(laue_handle* h, const void* A, long long lda, cons
     a.DhT = (__nv_bfloat16*)DT_bf16;
     a.ldt = ldt;
     a.ctrl = (int*)h->ws;
+    a.simple = (flags & 1) ? 1 : 0;
     if (gemm_tc_check(op, a, splits) != LAUE_OK)
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "gemm: M %% 128, N %% bn, K %% 64, splits | K/64, ld %% 8, alignment");
     return laue_cuda_check(h, gemm_tc_run(op, a, splits, (cudaStream_t)stream), "gemm launch");

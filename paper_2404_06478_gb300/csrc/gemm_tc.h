@@ -26,6 +26,7 @@ struct GemmArgs {
     __nv_bfloat16* DhT;         // modes 1, 2: [N][ldt] or null
     long long ldt;
     int* ctrl;                  // status word
+    int simple;                 // 1: always the one-tile-per-CTA kernel
 };
 
 size_t gemm_tc_smem(int BN, int stages);

@@ -13,7 +13,7 @@ from . import api
 
 def gemm_bf16(h: api.Handle, A: torch.Tensor, B: torch.Tensor, mode: int = 0, bn: int = 256, splits: int = 1,
               bias: torch.Tensor | None = None, mask: torch.Tensor | None = None, out_f32=None, out=None,
-              outT=None, stream=None):
+              outT=None, simple: bool = False, stream=None):
     """D[m][n] = sum_k A[m][k] B[n][k] on the tcgen05 tensor cores (BF16 in,
     FP32 accumulate).  mode 0 writes `splits` FP32 partials into out_f32
     (splits, M, N); mode 1 relu(D + bias) and mode 2 D * (mask > 0) as BF16
@@ -26,7 +26,7 @@ def gemm_bf16(h: api.Handle, A: torch.Tensor, B: torch.Tensor, mode: int = 0, bn
     ldt = outT.stride(0) if outT is not None else 0
     rc = h.L.laue_gemm_bf16(h.h, api._ptr(A), A.stride(0), api._ptr(B), B.stride(0), M, N, K, bn, splits, mode,
                             api._ptr(bias), api._ptr(mask), api._ptr(out_f32), api._ptr(out), api._ptr(outT), ldt,
-                            api._stream(stream))
+                            1 if simple else 0, api._stream(stream))
     h.check(rc, "gemm_bf16")
 
 

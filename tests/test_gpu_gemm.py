@@ -65,9 +65,13 @@ def _mostly_equal(got, ref):
     return np.mean(got != ref) < 2e-3
 
 
+@pytest.mark.parametrize("simple", [False, True])
 @pytest.mark.parametrize("mode", [1, 2])
-@pytest.mark.parametrize("M,N,K,bn", [(256, 256, 256, 256), (384, 128, 64, 128), (128, 64, 512, 64)])
-def test_gemm_bf16_epilogues(env, mode, M, N, K, bn):
+@pytest.mark.parametrize("M,N,K,bn", [(256, 256, 256, 256), (384, 128, 64, 128), (128, 64, 512, 64),
+                                      (640, 256, 64, 256), (49152, 256, 256, 256)])
+def test_gemm_bf16_epilogues(env, mode, M, N, K, bn, simple):
+    """N = 256 with K = 64 or 256 runs the persistent kernel unless `simple`;
+    49152 rows give every persistent CTA several tiles (both accumulators)."""
     torch = env["torch"]
     rng = np.random.default_rng(M + 3 * N + 5 * K + mode)
     A, B = _bf(rng, (M, K)), _bf(rng, (N, K), 0.1)
@@ -78,7 +82,8 @@ def test_gemm_bf16_epilogues(env, mode, M, N, K, bn):
     out = torch.full((M, N), float("nan"), dtype=torch.bfloat16, device=env["dev"])
     outT = torch.full((N, ldt), float("nan"), dtype=torch.bfloat16, device=env["dev"])
     env["pr"].gemm_bf16(env["h"], _dev(env, A), _dev(env, B), mode=mode, bn=bn,
-                        bias=_dev(env, bias, torch.float32), mask=_dev(env, mask), out=out, outT=outT)
+                        bias=_dev(env, bias, torch.float32), mask=_dev(env, mask), out=out, outT=outT,
+                        simple=simple)
     torch.cuda.synchronize()
     assert env["h"].device_status() == 0
     ref = op.gemm_tn(A, B, mode, bias=bias, mask=mask)
