@@ -284,3 +284,91 @@ def test_training_reduces_the_loss(env):
     torch.cuda.synchronize()
     assert h.device_status() == 0
     assert np.mean(last) < 0.8 * np.mean(first), (np.mean(first), np.mean(last))
+
+
+def test_sets_edge_cases(env):
+    """Empty sets (seed -1), windows with fewer candidates than a set holds,
+    a window holding only the seed, duplicated spots (equal distances: the
+    lower index wins) and windows clipped at the ends of the scan."""
+    torch, pr, h = env["torch"], env["pr"], env["h"]
+    rng = np.random.default_rng(31)
+    T = 6
+    counts = np.array([3, 1, 0, 200, 150, 2])
+    I_off = np.concatenate([[0], np.cumsum(counts)])
+    n = int(I_off[-1])
+    p = np.zeros((n, 3))
+    p[:, 0] = rng.uniform(-120, 120, n)
+    p[:, 1] = rng.uniform(-120, 120, n)
+    p[:, 2] = np.where(rng.random(n) < 0.8, -200.0, 200.0)
+    # duplicates: spots 10..19 repeat spot 9 of angle 3 exactly (equal distances)
+    p[10:20] = p[9]
+    t = np.repeat(np.arange(T), counts)
+    om = np.radians(np.arange(T) * 4.0)
+    seeds = np.array([-1, 0, 3, 9, 100, 350, 353, 9])
+    wlo = np.array([0, 0, 1, 3, 0, 4, 5, 0])
+    whi = np.array([6, 1, 2, 4, 6, 6, 6, 6])
+    dev = env["dev"]
+    p4 = np.zeros((n, 4), np.float32)
+    p4[:, :3] = p
+    ti = lambda a: torch.tensor(np.asarray(a), dtype=torch.int32, device=dev)
+    batch = pr.Batch(h, len(seeds))
+    axes = torch.empty(n, 4, dtype=torch.float32, device=dev)
+    pr.make_sets(h, GEOM, torch.tensor(p4, device=dev), ti(I_off), torch.tensor(om, dtype=torch.float32,
+                                                                                 device=dev),
+                 ti(seeds), ti(wlo), ti(whi), batch, axes)
+    torch.cuda.synchronize()
+    assert h.device_status() == 0
+    X, ids, F = op.make_sets(p4[:, :3].astype(np.float64), t, om, seeds, wlo, whi)
+    gids = batch.ids.cpu().numpy().reshape(len(seeds), op.KSET)
+    nval = batch.region("nvalid", torch.int32, (len(seeds),)).cpu().numpy()
+    for b in range(len(seeds)):
+        assert nval[b] == (ids[b] >= 0).sum()
+        if b in (0, 1, 2, 6):  # fewer candidates than the set holds: the whole window
+            np.testing.assert_array_equal(np.sort(gids[b][gids[b] >= 0]), np.sort(ids[b][ids[b] >= 0]))
+    assert nval[0] == 0 and nval[1] == 3 and nval[2] == 1
+    # the duplicates of spot 9 are at distance 0 from seed 9 and come first, by index
+    assert set(gids[3][1:11].tolist()) == set(range(10, 20))
+    assert list(gids[7][1:11]) == list(range(10, 20))
+    X0 = batch.features().float().cpu().numpy()
+    assert not X0[0].any()
+
+
+def test_sets_full_size_sampled(env):
+    """Sets of the 1000-grain, 90-rotation, 70%-outlier workload (about 132k
+    candidate spots per window) on sampled seeds: the oracle's set and the
+    GPU's agree up to ties at the selection boundary, features match."""
+    torch, pr, h = env["torch"], env["pr"], env["h"]
+    from _cases import make_case
+    case = make_case(BATCHED, seed=0)
+    p, I_off = case.obs.p, case.obs.I_off
+    t = np.repeat(np.arange(BATCHED.T), np.diff(I_off))
+    rng = np.random.default_rng(41)
+    seeds = rng.choice(len(p), 12, replace=False)
+    seeds[0] = I_off[1] - 1   # a seed in the first angles: window clipped at the start
+    seeds[1] = len(p) - 1     # and at the end
+    ob = env["api"].ObsSpots.from_numpy(p, I_off, device=env["dev"])
+    om = torch.tensor(case.om, dtype=torch.float32, device=env["dev"])
+    batch = pr.Batch(h, len(seeds))
+    pr.propose(h, pr.Network(h, seed=0), GEOM, ob, om, seeds, batch=batch)
+    torch.cuda.synchronize()
+    assert h.device_status() == 0
+    T = BATCHED.T
+    tt = np.searchsorted(I_off, seeds, side="right") - 1
+    lo = np.clip(tt - 4, 0, T)
+    hi = np.clip(lo + 10, 0, T)
+    lo = np.clip(hi - 10, 0, T)
+    X, ids, F = op.make_sets(p, t, case.om, seeds, lo, hi)
+    n = op.spot_axes(p, t, case.om)
+    gids = batch.ids.cpu().numpy().reshape(len(seeds), op.KSET)
+    gX = batch.features().float().cpu().numpy()
+    for b, i0 in enumerate(seeds):
+        a, o = set(gids[b].tolist()), set(ids[b].tolist())
+        dist = lambda i: 1.0 - abs(n[i] @ n[i0])
+        kth = max(dist(i) for i in o if i != i0)
+        for i in a ^ o:
+            assert abs(dist(i) - kth) < 2e-6
+        for e, i in enumerate(gids[b]):
+            if i in o:
+                eo = int(np.nonzero(ids[b] == i)[0][0])
+                np.testing.assert_allclose(gX[b, e], op.bf16(X[b, eo]), rtol=2 ** -7, atol=1e-6)
+    np.testing.assert_allclose(batch.frames().cpu().numpy(), F, atol=2e-6)
