@@ -200,8 +200,8 @@ def proposal_bench(dev, api, sg, torch, peaks):
     lat = api.Lattice.cubic(cfgB.a, cfgB.hmax, cfgB.centering, device=dev)
     omega = torch.tensor(sg.omegas(cfgB), dtype=torch.float32, device=dev)
     out = {}
-    # training: 8000 steps of 2048 sets (64 single-grain scenes x 32 seeds)
-    steps = 8000
+    # training: 20000 steps of 2048 sets (64 single-grain scenes x 32 seeds)
+    steps = 20000
     pr.train(h, geom, lat, omega, steps=20, seed=1)  # warm-up
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

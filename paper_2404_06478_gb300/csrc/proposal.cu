@@ -157,20 +157,35 @@ __global__ void __launch_bounds__(256) scene_count_kernel(SceneArgs a) {
     }
 }
 
-__global__ void scene_scan_kernel(SceneArgs a) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int nv = a.S * a.W, acc = 0;
-    for (int v = 0; v < nv; ++v) {
-        a.I_off[v] = acc;
-        acc += a.counts[2 * v] + a.counts[2 * v + 1];
+// exclusive offsets of the per-angle counts, staged through shared memory in
+// chunks of 1024 (one block)
+__global__ void __launch_bounds__(1024) scene_scan_kernel(SceneArgs a) {
+    __shared__ int cnt[1024];
+    __shared__ int carry;
+    int nv = a.S * a.W;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nv; base += 1024) {
+        int v = base + threadIdx.x;
+        cnt[threadIdx.x] = v < nv ? a.counts[2 * v] + a.counts[2 * v + 1] : 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = carry, n = min(1024, nv - base);
+            for (int k = 0; k < n; ++k) {
+                int c = cnt[k];
+                cnt[k] = acc;
+                acc += c;
+            }
+            carry = acc;
+        }
+        __syncthreads();
+        if (v < nv) a.I_off[v] = min(cnt[threadIdx.x], a.capacity);
+        __syncthreads();
     }
-    if (acc > a.capacity) {
-        set_status(a.ctrl, LAUE_ERR_CAPACITY);
-        // keep the list consistent: angles past the capacity hold nothing
-        for (int v = 0; v < nv; ++v) a.I_off[v] = min(a.I_off[v], a.capacity);
-        acc = a.capacity;
+    if (threadIdx.x == 0) {
+        if (carry > a.capacity) set_status(a.ctrl, LAUE_ERR_CAPACITY);
+        a.I_off[nv] = min(carry, a.capacity);
     }
-    a.I_off[nv] = acc;
 }
 
 __global__ void __launch_bounds__(256) scene_write_kernel(SceneArgs a) {
@@ -556,7 +571,10 @@ __global__ void __launch_bounds__(WIDTH) pool_kernel(const __nv_bfloat16* H3, co
 
 // Small FP32 GEMM for the head: C[m][n] = epi(sum_k A(m, k) B(k, n)) with
 // A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn]; epilogue: + bias[n],
-// relu, multiply by (mask[m ldm + n] > 0); C[m ldc + n].  Fixed-order sums.
+// relu, multiply by (mask[m ldm + n] > 0); C[m ldc + n].  64 x 64 tiles, 4 x 4
+// outputs per thread; with splits > 1 each z-slice of the grid sums one K
+// range into part[z][m][n] and a second kernel adds the slices in order and
+// applies the epilogue.  Fixed-order sums throughout.
 struct SgemmArgs {
     const float* A;
     long long sam, sak;
@@ -569,74 +587,119 @@ struct SgemmArgs {
     int relu;
     const float* mask;
     long long ldm;
+    float* part;
+    int splits;
 };
 
+__device__ __forceinline__ float sg_epi(const SgemmArgs& g, int m, int n, float v) {
+    if (g.bias) v += g.bias[n];
+    if (g.relu) v = fmaxf(v, 0.0f);
+    if (g.mask && !(g.mask[m * g.ldm + n] > 0.0f)) v = 0.0f;
+    return v;
+}
+
 __global__ void __launch_bounds__(256) sgemm_kernel(SgemmArgs g) {
-    __shared__ float As[32][33], Bs[32][33];
-    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-    int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
-    float acc[4] = {0, 0, 0, 0};
-    for (int k0 = 0; k0 < g.K; k0 += 32) {
-        for (int r = ty; r < 32; r += 8) {
-            int m = m0 + r, k = k0 + tx;
-            As[r][tx] = (m < g.M && k < g.K) ? g.A[m * g.sam + k * g.sak] : 0.0f;
-            int kk = k0 + r, n = n0 + tx;
-            Bs[r][tx] = (kk < g.K && n < g.N) ? g.B[kk * g.sbk + n * g.sbn] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            float bv = Bs[k][tx];
+    __shared__ float As[16][64 + 4], Bs[16][64 + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int kc = (g.K + g.splits - 1) / g.splits;
+    const int kbeg = blockIdx.z * kc, kend = min(g.K, kbeg + kc);
+    float acc[4][4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fmaf(As[ty + 8 * q][k], bv, acc[q]);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int k0 = kbeg; k0 < kend; k0 += 16) {
+        for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
+            int kk = idx >> 6, mm = idx & 63;
+            int k = k0 + kk;
+            As[kk][mm] = (m0 + mm < g.M && k < kend) ? g.A[(m0 + mm) * g.sam + k * g.sak] : 0.0f;
+            Bs[kk][mm] = (n0 + mm < g.N && k < kend) ? g.B[k * g.sbk + (n0 + mm) * g.sbn] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
-    int n = n0 + tx;
-    if (n >= g.N) return;
-    for (int q = 0; q < 4; ++q) {
-        int m = m0 + ty + 8 * q;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int m = m0 + ty * 4 + i;
         if (m >= g.M) continue;
-        float v = acc[q];
-        if (g.bias) v += g.bias[n];
-        if (g.relu) v = fmaxf(v, 0.0f);
-        if (g.mask && !(g.mask[m * g.ldm + n] > 0.0f)) v = 0.0f;
-        g.C[m * g.ldc + n] = v;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int n = n0 + tx * 4 + j;
+            if (n >= g.N) continue;
+            if (g.splits > 1) g.part[((size_t)blockIdx.z * g.M + m) * g.N + n] = acc[i][j];
+            else g.C[m * g.ldc + n] = sg_epi(g, m, n, acc[i][j]);
+        }
     }
+}
+
+__global__ void sgemm_finish_kernel(SgemmArgs g) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)g.M * g.N) return;
+    int m = (int)(idx / g.N), n = (int)(idx % g.N);
+    float v = 0.0f;
+    for (int z = 0; z < g.splits; ++z) v += g.part[((size_t)z * g.M + m) * g.N + n];
+    g.C[m * g.ldc + n] = sg_epi(g, m, n, v);
 }
 
 cudaError_t sgemm(const float* A, long long sam, long long sak, const float* B, long long sbk, long long sbn,
                   float* C, long long ldc, int M, int N, int K, const float* bias, int relu, const float* mask,
-                  long long ldm, cudaStream_t s) {
-    SgemmArgs g{A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, bias, relu, mask, ldm};
-    dim3 grid((N + 31) / 32, (M + 31) / 32);
+                  long long ldm, cudaStream_t s, float* part = nullptr, int splits = 1) {
+    SgemmArgs g{A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, bias, relu, mask, ldm, part, part ? splits : 1};
+    dim3 grid((N + 63) / 64, (M + 63) / 64, g.splits);
     sgemm_kernel<<<grid, 256, 0, s>>>(g);
+    if (g.splits > 1) {
+        long long n = (long long)M * N;
+        sgemm_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g);
+    }
     return cudaGetLastError();
 }
 
-// column sums: out[n] = sum_m A[m lda + n] (fixed order over m)
-__global__ void colsum_kernel(const float* A, long long lda, int M, int N, float* out) {
+// column sums out[n] = sum_m A[m lda + n]: per z-slice partial sums over a
+// row range, then the slices added in order
+__global__ void colsum_partial_kernel(const float* A, long long lda, int M, int N, int splits, float* part) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
+    int mc = (M + splits - 1) / splits, m0 = blockIdx.y * mc, m1 = min(M, m0 + mc);
     float s = 0.0f;
-    for (int m = 0; m < M; ++m) s += A[m * lda + n];
-    out[n] = s;
+    for (int m = m0; m < m1; ++m) s += A[m * lda + n];
+    part[(size_t)blockIdx.y * N + n] = s;
 }
 
-// row sums of a BF16 [rows][ld] array over the first n columns, one CTA per row
+// row sums of a BF16 [rows][ld] array over its first n columns (n even):
+// blockIdx.y splits each row into equal chunks (BF16 pairs), one partial per
+// (row, chunk) in part[row][chunk]; the partials are added in order by
+// split_reduce over the transposed view
 __global__ void __launch_bounds__(256) rowsum_bf16_kernel(const __nv_bfloat16* A, long long ld, long long n,
-                                                          float* out) {
+                                                          int chunks, float* part) {
     __shared__ float red[256];
-    const __nv_bfloat16* r = A + (size_t)blockIdx.x * ld;
+    const __nv_bfloat162* r = reinterpret_cast<const __nv_bfloat162*>(A + (size_t)blockIdx.x * ld);
+    long long np = n / 2, cp = (np + chunks - 1) / chunks;
+    long long j0 = (long long)blockIdx.y * cp, j1 = min(np, j0 + cp);
     float s = 0.0f;
-    for (long long j = threadIdx.x; j < n; j += blockDim.x) s += bf(r[j]);
+    for (long long j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+        float2 f = __bfloat1622float2(r[j]);
+        s += f.x + f.y;
+    }
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
 }
 
 // sum of split-K partials: out[j] = sum_s part[s n + j]
@@ -785,34 +848,51 @@ __global__ void loss_kernel(const float* O, const float* Rt, const float* xt, co
 }
 
 // dZ3 = (dmean / nv on valid rows + dmax at the argmax row) where H3 > 0,
-// rounded to BF16, written row-major and transposed (staged in shared memory
-// 128 rows at a time)
+// rounded to BF16, written row-major and transposed.  Per set, 128 rows at a
+// time: each thread handles 8 channels of a row with 16-byte loads and
+// stores, the tile is staged in shared memory, and the transposed copy is
+// written as 16-byte runs of 8 consecutive rows of one channel.
 constexpr int kTileRows = 128;
 constexpr int kTileLd = WIDTH + 2;
-__global__ void __launch_bounds__(WIDTH) pool_backward_kernel(const __nv_bfloat16* H3, const int* nvalid,
-                                                              const int* amax, const float* dPool, int B,
-                                                              long long Ms, __nv_bfloat16* dZ3,
-                                                              __nv_bfloat16* dZ3t) {
+__global__ void __launch_bounds__(256) pool_backward_kernel(const __nv_bfloat16* H3, const int* nvalid,
+                                                            const int* amax, const float* dPool, int B, long long Ms,
+                                                            __nv_bfloat16* dZ3, __nv_bfloat16* dZ3t) {
     extern __shared__ __nv_bfloat16 tile[];  // kTileRows x kTileLd
+    __shared__ float dm_s[WIDTH], dx_s[WIDTH];
+    __shared__ int am_s[WIDTH];
+    const int c8 = (threadIdx.x & 31) * 8, r0 = threadIdx.x >> 5;
     for (int b = blockIdx.x; b < B; b += gridDim.x) {
-        int c = threadIdx.x, nv = nvalid[b];
-        float dm = nv > 0 ? dPool[(size_t)b * 2 * WIDTH + c] / (float)nv : 0.0f;
-        float dx = dPool[(size_t)b * 2 * WIDTH + WIDTH + c];
-        int am = amax[(size_t)b * WIDTH + c];
+        const int nv = nvalid[b];
+        for (int c = threadIdx.x; c < WIDTH; c += blockDim.x) {
+            dm_s[c] = nv > 0 ? dPool[(size_t)b * 2 * WIDTH + c] / (float)nv : 0.0f;
+            dx_s[c] = nv > 0 ? dPool[(size_t)b * 2 * WIDTH + WIDTH + c] : 0.0f;
+            am_s[c] = amax[(size_t)b * WIDTH + c];
+        }
+        __syncthreads();
         for (int e0 = 0; e0 < KSET; e0 += kTileRows) {
-            for (int q = 0; q < kTileRows; ++q) {
-                int e = e0 + q;
-                size_t row = (size_t)b * KSET + e;
-                float v = (e < nv ? dm : 0.0f) + (nv > 0 && e == am ? dx : 0.0f);
-                float h = bf(H3[row * WIDTH + c]);
-                __nv_bfloat16 z = __float2bfloat16_rn(h > 0.0f ? v : 0.0f);
-                dZ3[row * WIDTH + c] = z;
-                tile[q * kTileLd + c] = z;
+            for (int r = r0; r < kTileRows; r += 8) {
+                const int e = e0 + r;
+                const size_t row = (size_t)b * KSET + e;
+                uint4 hv = *reinterpret_cast<const uint4*>(H3 + row * WIDTH + c8);
+                const __nv_bfloat16* hh = reinterpret_cast<const __nv_bfloat16*>(&hv);
+                __align__(16) __nv_bfloat16 z[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    int c = c8 + j;
+                    float v = (e < nv ? dm_s[c] : 0.0f) + (e == am_s[c] ? dx_s[c] : 0.0f);
+                    z[j] = __float2bfloat16_rn(bf(hh[j]) > 0.0f ? v : 0.0f);
+                    tile[r * kTileLd + c] = z[j];
+                }
+                *reinterpret_cast<uint4*>(dZ3 + row * WIDTH + c8) = *reinterpret_cast<const uint4*>(z);
             }
             __syncthreads();
-            for (int idx = threadIdx.x; idx < kTileRows * WIDTH; idx += blockDim.x) {
-                int cc = idx / kTileRows, q = idx % kTileRows;
-                dZ3t[(size_t)cc * Ms + (size_t)b * KSET + e0 + q] = tile[q * kTileLd + cc];
+            for (int idx = threadIdx.x; idx < WIDTH * (kTileRows / 8); idx += blockDim.x) {
+                int c = idx / (kTileRows / 8), q0 = (idx % (kTileRows / 8)) * 8;
+                __align__(16) __nv_bfloat16 z[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) z[k] = tile[(q0 + k) * kTileLd + c];
+                *reinterpret_cast<uint4*>(dZ3t + (size_t)c * Ms + (size_t)b * KSET + e0 + q0) =
+                    *reinterpret_cast<const uint4*>(z);
             }
             __syncthreads();
         }
@@ -982,15 +1062,19 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
     float* dZ4 = bt.at<float>(L.dZ4);
     float* pool = bt.at<float>(L.pool);
     // head
-    if ((e = sgemm(dO, 1, NOUT, H4, HEADW, 1, n.G + oW5, HEADW, NOUT, HEADW, B, nullptr, 0, nullptr, 0, s)))
+    const int ks = B >= 64 ? 8 : 1;  // split the long reductions over the sets
+    if ((e = sgemm(dO, 1, NOUT, H4, HEADW, 1, n.G + oW5, HEADW, NOUT, HEADW, B, nullptr, 0, nullptr, 0, s, n.part,
+                   ks)))
         return e;
-    colsum_kernel<<<1, NOUT, 0, s>>>(dO, NOUT, B, NOUT, n.G + ob5);
+    colsum_partial_kernel<<<dim3(1, 32), NOUT, 0, s>>>(dO, NOUT, B, NOUT, 32, n.part);
+    split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, NOUT, n.G + ob5);
     if ((e = sgemm(dO, NOUT, 1, n.P + oW5, HEADW, 1, dZ4, HEADW, B, HEADW, NOUT, nullptr, 0, H4, HEADW, s)))
         return e;
     if ((e = sgemm(dZ4, 1, HEADW, pool, 2 * WIDTH, 1, n.G + oW4, 2 * WIDTH, HEADW, 2 * WIDTH, B, nullptr, 0,
-                   nullptr, 0, s)))
+                   nullptr, 0, s, n.part, ks)))
         return e;
-    colsum_kernel<<<1, HEADW, 0, s>>>(dZ4, HEADW, B, HEADW, n.G + ob4);
+    colsum_partial_kernel<<<dim3(1, 32), HEADW, 0, s>>>(dZ4, HEADW, B, HEADW, 32, n.part);
+    split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, HEADW, n.G + ob4);
     if ((e = sgemm(dZ4, HEADW, 1, n.P + oW4, 2 * WIDTH, 1, bt.at<float>(L.dPool), 2 * WIDTH, B, 2 * WIDTH, HEADW,
                    nullptr, 0, nullptr, 0, s)))
         return e;
@@ -998,7 +1082,7 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
     size_t tsm = (size_t)kTileRows * kTileLd * 2;
     if ((e = cudaFuncSetAttribute(pool_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)))
         return e;
-    pool_backward_kernel<<<B, WIDTH, tsm, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), bt.at<int>(L.amax),
+    pool_backward_kernel<<<B, 256, tsm, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), bt.at<int>(L.amax),
                                                bt.at<float>(L.dPool), B, Ms, bfp(L.dZ3), bfp(L.dZ3t));
     if ((e = cudaGetLastError())) return e;
     // dZ2 = (dZ3 W3) * (H2 > 0), dZ1 = (dZ2 W2) * (H1 > 0)
@@ -1041,7 +1125,8 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
             return e;
         long long nw = (long long)WIDTH * layers[l].N;
         split_reduce_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(n.part, splits, nw, n.G + layers[l].oW);
-        rowsum_bf16_kernel<<<WIDTH, 256, 0, s>>>(bfp(layers[l].A), Ms, Ms, n.G + layers[l].ob);
+        rowsum_bf16_kernel<<<dim3(WIDTH, 32), 256, 0, s>>>(bfp(layers[l].A), Ms, Ms, 32, n.part);
+        split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, WIDTH, n.G + layers[l].ob);
         if ((e = cudaGetLastError())) return e;
     }
     return cudaSuccess;
@@ -1153,7 +1238,7 @@ extern "C" int laue_lp_scene(laue_handle* h, const LaueGeometry* geom, const Lau
     int ng = S * Gmax;
     scene_params_kernel<<<(ng + 255) / 256, 256, 0, s>>>(a);
     scene_count_kernel<<<S * W, 256, 0, s>>>(a);
-    scene_scan_kernel<<<1, 32, 0, s>>>(a);
+    scene_scan_kernel<<<1, 1024, 0, s>>>(a);
     scene_write_kernel<<<S * W, 256, 0, s>>>(a);
     return laue_cuda_check(h, cudaGetLastError(), "scene launch");
 }

@@ -188,9 +188,11 @@ def test_forward_matches_oracle(env):
     assert np.mean(H3 != cache["H3"]) < 1e-2
 
 
-def test_gradients_match_oracle(env):
+@pytest.mark.parametrize("B", [24, 96])
+def test_gradients_match_oracle(env, B):
+    """B = 96 takes the split reductions of the head's weight gradients."""
     torch, pr, h = env["torch"], env["pr"], env["h"]
-    X, F, Rt, xt, valid = _oracle_batch(env, seed=9)
+    X, F, Rt, xt, valid = _oracle_batch(env, B=B, seed=9)
     B = X.shape[0]
     Pd, vec = _oracle_params(env, 4)
     net = pr.Network(h, params=vec)
