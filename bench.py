@@ -29,6 +29,24 @@ METRIC = "cost-pair evals/s in Sinkhorn-EM at 1000 grains; time-to-index vs plai
 UNIT = "pairs/s"
 
 
+def max_over_ranks(value, world, device):
+    """The largest value over the ranks: the job's step time is the slowest
+    replica's."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms):
+    """Whole-job throughput: every rank processes units_per_rank per step
+    (weak scaling), the job takes the slowest rank's ms."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def _dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -426,13 +444,9 @@ def main():
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)), world, dev)
     pairs_step = 2 * W["pairs_half"] * cfg.n_sinkhorn
-    value = pairs_step * world / (ms / 1e3)
+    value = job_value(pairs_step, world, ms)
 
     # end to end through the C ABI with host buffers: H2D of the step's inputs
     # from pinned memory, the step, D2H of its results
