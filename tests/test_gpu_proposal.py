@@ -188,9 +188,11 @@ def test_forward_matches_oracle(env):
     assert np.mean(H3 != cache["H3"]) < 1e-2
 
 
-@pytest.mark.parametrize("B", [24, 96])
+@pytest.mark.parametrize("B", [24, 96, 384])
 def test_gradients_match_oracle(env, B):
-    """B = 96 takes the split reductions of the head's weight gradients."""
+    """B = 96 and 384 take the split reductions of the head's weight
+    gradients; 384 sets also spread the weight-gradient GEMMs over split-K
+    partials and every persistent CTA over several tiles."""
     torch, pr, h = env["torch"], env["pr"], env["h"]
     X, F, Rt, xt, valid = _oracle_batch(env, B=B, seed=9)
     B = X.shape[0]
