@@ -475,6 +475,25 @@ def main():
     h2d = p_host.numel() * 4 + R_host.numel() * 4 + x_host.numel() * 4
     d2h = a_host.numel() * 4 + Ro_host.numel() * 4 + xo_host.numel() * 4
 
+    # the adjoint of the OT-weighted cost at the same size: gradient with
+    # respect to every grain's axis-angle and position, costs recomputed
+    out_sk = api.cost_sinkhorn(W["h"], W["geom"], W["ob"], W["model"], cfg.eps, W["c_out"], cfg.n_sinkhorn,
+                               harvest=False)
+    api.objective_grad(W["h"], W["geom"], W["lat"], W["ob"], W["model"], out_sk["f"], out_sk["g"], cfg.eps,
+                       W["om"], W["R0"], W["x0"])
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(5):
+        api.objective_grad(W["h"], W["geom"], W["lat"], W["ob"], W["model"], out_sk["f"], out_sk["g"], cfg.eps,
+                           W["om"], W["R0"], W["x0"])
+    eb.record(stream)
+    torch.cuda.synchronize()
+    adj_ms = ea.elapsed_time(eb) / 5
+    adjoint = dict(ms_per_call=adj_ms, pairs_per_s=W["pairs_half"] / (adj_ms / 1e3),
+                   grains=cfg.n_grains, note="gradient of sum_ij Q_ij C_ij wrt each grain's axis-angle and "
+                                             "position (Q from 200 Sinkhorn iterations, costs recomputed)")
+
     # refresh 1; Sinkhorn: schedule, pack, dust init, G maxima, 2 per iteration, clear, harvest,
     # finish; M-step: schedule, pack, dust init, G maxima, segment count + scan, init, 2 per Newton step,
     # MM pair + MM grain, norms
@@ -509,6 +528,8 @@ def main():
         e2e=dict(value=pairs_step / (e2e_ms / 1e3), unit=UNIT, h2d_bytes_per_step=int(h2d),
                  d2h_bytes_per_step=int(d2h)),
         gpu_launches=launches_per_step * args.steps,
+        em_iterations_per_s=1e3 / ms,
+        adjoint=adjoint,
     )
     if rank == 0 and not args.no_proposal:
         peaks = {}

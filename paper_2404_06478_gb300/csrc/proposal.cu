@@ -598,46 +598,53 @@ __device__ __forceinline__ float sg_epi(const SgemmArgs& g, int m, int n, float 
     return v;
 }
 
+// 128 x 128 tile per CTA, 8 x 8 outputs per thread, K in steps of 8.
 __global__ void __launch_bounds__(256) sgemm_kernel(SgemmArgs g) {
-    __shared__ float As[16][64 + 4], Bs[16][64 + 4];
+    __shared__ __align__(16) float As[8][128], Bs[8][128];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 128;
     const int kc = (g.K + g.splits - 1) / g.splits;
     const int kbeg = blockIdx.z * kc, kend = min(g.K, kbeg + kc);
-    float acc[4][4];
+    float acc[8][8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
-    for (int k0 = kbeg; k0 < kend; k0 += 16) {
-        for (int idx = threadIdx.x; idx < 16 * 64; idx += 256) {
-            int kk = idx >> 6, mm = idx & 63;
-            int k = k0 + kk;
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    for (int k0 = kbeg; k0 < kend; k0 += 8) {
+        // consecutive threads walk the contiguous index of each operand
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int idx = threadIdx.x + 256 * r;
+            int kk = g.sak == 1 ? (idx & 7) : (idx >> 7), mm = g.sak == 1 ? (idx >> 3) : (idx & 127), k = k0 + kk;
             As[kk][mm] = (m0 + mm < g.M && k < kend) ? g.A[(m0 + mm) * g.sam + k * g.sak] : 0.0f;
+            kk = g.sbk == 1 ? (idx & 7) : (idx >> 7);
+            mm = g.sbk == 1 ? (idx >> 3) : (idx & 127);
+            k = k0 + kk;
             Bs[kk][mm] = (n0 + mm < g.N && k < kend) ? g.B[k * g.sbk + (n0 + mm) * g.sbn] : 0.0f;
         }
         __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
+        for (int kk = 0; kk < 8; ++kk) {
+            float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+            float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+            float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
+            float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
+            float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int m = m0 + ty * 4 + i;
+    for (int i = 0; i < 8; ++i) {
+        int m = m0 + ty * 8 + i;
         if (m >= g.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int n = n0 + tx * 4 + j;
+        for (int j = 0; j < 8; ++j) {
+            int n = n0 + tx * 8 + j;
             if (n >= g.N) continue;
             if (g.splits > 1) g.part[((size_t)blockIdx.z * g.M + m) * g.N + n] = acc[i][j];
             else g.C[m * g.ldc + n] = sg_epi(g, m, n, acc[i][j]);
@@ -657,8 +664,15 @@ __global__ void sgemm_finish_kernel(SgemmArgs g) {
 cudaError_t sgemm(const float* A, long long sam, long long sak, const float* B, long long sbk, long long sbn,
                   float* C, long long ldc, int M, int N, int K, const float* bias, int relu, const float* mask,
                   long long ldm, cudaStream_t s, float* part = nullptr, int splits = 1) {
+    // split K (when a scratch buffer is given) until the grid covers the SMs
+    // twice, keeping at least 64 K per split
+    if (part && splits <= 1) {
+        int tiles = ((N + 127) / 128) * ((M + 127) / 128);
+        splits = 1;
+        while (tiles * splits < 2 * 152 && K / (splits * 2) >= 64 && splits < 64) splits *= 2;
+    }
     SgemmArgs g{A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, bias, relu, mask, ldm, part, part ? splits : 1};
-    dim3 grid((N + 63) / 64, (M + 63) / 64, g.splits);
+    dim3 grid((N + 127) / 128, (M + 127) / 128, g.splits);
     sgemm_kernel<<<grid, 256, 0, s>>>(g);
     if (g.splits > 1) {
         long long n = (long long)M * N;
@@ -1045,11 +1059,12 @@ cudaError_t forward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaStr
     pool_kernel<<<B, WIDTH, 0, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), B, bt.at<float>(L.pool), bt.at<int>(L.amax));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // head (FP32): H4 = relu(pool W4^T + b4), O = H4 W5^T + b5
+    float* hs = bt.at<float>(L.hscr);
     if ((e = sgemm(bt.at<float>(L.pool), 2 * WIDTH, 1, n.P + oW4, 1, 2 * WIDTH, bt.at<float>(L.H4), HEADW, B, HEADW,
-                   2 * WIDTH, n.P + ob4, 1, nullptr, 0, s)) != cudaSuccess)
+                   2 * WIDTH, n.P + ob4, 1, nullptr, 0, s, hs, 0)) != cudaSuccess)
         return e;
     return sgemm(bt.at<float>(L.H4), HEADW, 1, n.P + oW5, 1, HEADW, bt.at<float>(L.O), NOUT, B, NOUT, HEADW,
-                 n.P + ob5, 0, nullptr, 0, s);
+                 n.P + ob5, 0, nullptr, 0, s, hs, 0);
 }
 
 cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaStream_t s) {
@@ -1062,21 +1077,20 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
     float* dZ4 = bt.at<float>(L.dZ4);
     float* pool = bt.at<float>(L.pool);
     // head
-    const int ks = B >= 64 ? 8 : 1;  // split the long reductions over the sets
-    if ((e = sgemm(dO, 1, NOUT, H4, HEADW, 1, n.G + oW5, HEADW, NOUT, HEADW, B, nullptr, 0, nullptr, 0, s, n.part,
-                   ks)))
+    float* hs = bt.at<float>(L.hscr);
+    if ((e = sgemm(dO, 1, NOUT, H4, HEADW, 1, n.G + oW5, HEADW, NOUT, HEADW, B, nullptr, 0, nullptr, 0, s, hs, 0)))
         return e;
     colsum_partial_kernel<<<dim3(1, 32), NOUT, 0, s>>>(dO, NOUT, B, NOUT, 32, n.part);
     split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, NOUT, n.G + ob5);
-    if ((e = sgemm(dO, NOUT, 1, n.P + oW5, HEADW, 1, dZ4, HEADW, B, HEADW, NOUT, nullptr, 0, H4, HEADW, s)))
+    if ((e = sgemm(dO, NOUT, 1, n.P + oW5, HEADW, 1, dZ4, HEADW, B, HEADW, NOUT, nullptr, 0, H4, HEADW, s, hs, 0)))
         return e;
     if ((e = sgemm(dZ4, 1, HEADW, pool, 2 * WIDTH, 1, n.G + oW4, 2 * WIDTH, HEADW, 2 * WIDTH, B, nullptr, 0,
-                   nullptr, 0, s, n.part, ks)))
+                   nullptr, 0, s, hs, 0)))
         return e;
     colsum_partial_kernel<<<dim3(1, 32), HEADW, 0, s>>>(dZ4, HEADW, B, HEADW, 32, n.part);
     split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, HEADW, n.G + ob4);
     if ((e = sgemm(dZ4, HEADW, 1, n.P + oW4, 2 * WIDTH, 1, bt.at<float>(L.dPool), 2 * WIDTH, B, 2 * WIDTH, HEADW,
-                   nullptr, 0, nullptr, 0, s)))
+                   nullptr, 0, nullptr, 0, s, hs, 0)))
         return e;
     // pooling -> dZ3
     size_t tsm = (size_t)kTileRows * kTileLd * 2;

@@ -66,7 +66,7 @@ inline NetLayout net_layout() {
 // Batch buffer (bytes) for B sets of KSET spots (Ms = B KSET rows).
 struct BatchLayout {
     size_t X, Xt, H1, H1t, H2, H2t, H3, dZ3, dZ3t, dZ2, dZ2t, dZ1t;  // BF16 per-spot arrays
-    size_t F, nvalid, Rt, xt, svalid, pool, amax, H4, O, dO, dZ4, dPool, loss, dbest, hbest, inv_nval;
+    size_t F, nvalid, Rt, xt, svalid, pool, amax, H4, O, dO, dZ4, dPool, loss, dbest, hbest, inv_nval, hscr;
     size_t total;
     long long Ms;
 };
@@ -104,6 +104,11 @@ inline BatchLayout batch_layout(int B) {
     L.dbest = take((size_t)B * 4);
     L.hbest = take((size_t)B * 4);
     L.inv_nval = take(256);
+    // split-K partial sums of the head GEMMs: at most 8 x (B x 256), 4 x (B x 512)
+    // or 64 x (256 x 512) floats
+    size_t hs = (size_t)B * 2048;
+    if (hs < (size_t)64 * HEADW * 2 * WIDTH) hs = (size_t)64 * HEADW * 2 * WIDTH;
+    L.hscr = take(hs * 4);
     L.total = o;
     return L;
 }
