@@ -375,18 +375,17 @@ __global__ void __launch_bounds__(kPThreads, 1)
     }
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 lookup_encode() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        return (PFN_cuTensorMapEncodeTiled_v12000)p;
+    return nullptr;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = lookup_encode();  // thread-safe one-time lookup
     return fn;
 }
 
@@ -429,15 +428,16 @@ int gemm_tc_check(const GemmOperands& op, const GemmArgs& a, int splits) {
     return LAUE_OK;
 }
 
-static int sm_count_cached() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 1;
+static int sm_count_current() {
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!sms[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        sms[dev] = v;
     }
-    return sms;
+    return sms[dev];
 }
 
 template <int KB>
@@ -452,7 +452,8 @@ static cudaError_t launch_persistent(const CUtensorMap& tA, const CUtensorMap& t
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int n_tiles = a.M / kBM;
-    int grid = n_tiles < sm_count_cached() ? n_tiles : sm_count_cached();
+    int sms = sm_count_current();
+    int grid = n_tiles < sms ? n_tiles : sms;
     gemm_tc_persistent_kernel<KB><<<grid, kPThreads, smem, s>>>(tA, tB, a, n_tiles);
     return cudaGetLastError();
 }

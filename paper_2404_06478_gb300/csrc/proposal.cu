@@ -738,12 +738,20 @@ __global__ void count_valid_kernel(const float* svalid, int B, float* inv_nval) 
     if (threadIdx.x == 0) inv_nval[0] = 1.0f / fmaxf(red[0], 1.0f);
 }
 
-// The 24 proper rotations of the cube in the order of itertools
-// (permutations of (0, 1, 2), then sign triples), kept when det = +1:
-// S[r][perm[r]] = sign[r].  Stored per symmetry and column c as the row
-// index pinv[c] and its sign.
-__constant__ signed char c_sym_row[24][3];
-__constant__ signed char c_sym_sgn[24][3];
+// The 24 proper rotations of the cube, S[r][perm[r]] = sign[r], in the order
+// permutations of (0, 1, 2) (lexicographic) x sign triples (+ before -, last
+// index fastest), kept when det = +1.  Stored per symmetry and column c as the
+// row that holds column c's nonzero and its sign.
+__constant__ signed char c_sym_row[24][3] = {
+    {0, 1, 2}, {0, 1, 2}, {0, 1, 2}, {0, 1, 2}, {0, 2, 1}, {0, 2, 1},
+    {0, 2, 1}, {0, 2, 1}, {1, 0, 2}, {1, 0, 2}, {1, 0, 2}, {1, 0, 2},
+    {2, 0, 1}, {2, 0, 1}, {2, 0, 1}, {2, 0, 1}, {1, 2, 0}, {1, 2, 0},
+    {1, 2, 0}, {1, 2, 0}, {2, 1, 0}, {2, 1, 0}, {2, 1, 0}, {2, 1, 0}};
+__constant__ signed char c_sym_sgn[24][3] = {
+    {1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}, {1, -1, 1}, {1, 1, -1},
+    {-1, 1, 1}, {-1, -1, -1}, {1, 1, -1}, {-1, 1, 1}, {1, -1, 1}, {-1, -1, -1},
+    {1, 1, 1}, {-1, 1, -1}, {-1, -1, 1}, {1, -1, -1}, {1, 1, 1}, {-1, -1, 1},
+    {1, -1, -1}, {-1, 1, -1}, {-1, 1, 1}, {1, -1, 1}, {1, 1, -1}, {-1, -1, -1}};
 
 __device__ void gram_schmidt(const float* o, float* R) {  // R row-major, columns e1 e2 e3
     float na = sqrtf(o[0] * o[0] + o[1] * o[1] + o[2] * o[2]);
@@ -961,32 +969,6 @@ __global__ void decode_kernel(const float* O, const float* F, const int* nvalid,
                 nvalid[b] > 0 ? F0[3 * r] * Rh[c] + F0[3 * r + 1] * Rh[3 + c] + F0[3 * r + 2] * Rh[6 + c]
                               : (r == c ? 1.0f : 0.0f);
     for (int q = 0; q < 3; ++q) xout[3 * (size_t)idx + q] = nvalid[b] > 0 ? XSCALE * o[6 + q] : 0.0f;
-}
-
-bool g_sym_ready = false;
-cudaError_t upload_syms() {
-    if (g_sym_ready) return cudaSuccess;
-    signed char row[24][3], sgn[24][3];
-    int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    int n = 0;
-    for (int p = 0; p < 6; ++p)
-        for (int sb = 0; sb < 8; ++sb) {
-            int s[3] = {(sb & 4) ? -1 : 1, (sb & 2) ? -1 : 1, (sb & 1) ? -1 : 1};
-            int* pm = perms[p];
-            // det of S[r][pm[r]] = s[r]: sign of the permutation times the signs
-            int inv = (pm[0] > pm[1]) + (pm[0] > pm[2]) + (pm[1] > pm[2]);
-            int det = ((inv & 1) ? -1 : 1) * s[0] * s[1] * s[2];
-            if (det < 0) continue;
-            for (int r = 0; r < 3; ++r) {
-                row[n][pm[r]] = (signed char)r;
-                sgn[n][pm[r]] = (signed char)s[r];
-            }
-            ++n;
-        }
-    cudaError_t e = cudaMemcpyToSymbol(c_sym_row, row, sizeof(row));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_sym_sgn, sgn, sizeof(sgn));
-    if (e == cudaSuccess) g_sym_ready = true;
-    return e;
 }
 
 int splits_for(int B) {
@@ -1332,7 +1314,6 @@ extern "C" int laue_lp_train_step(laue_handle* h, void* net, void* batch, int n_
     if ((rc = lp_need_ws(h))) return rc;
     if (!net || !batch || n_sets <= 0 || !(lr >= 0.0f) || (uintptr_t)batch % 256 || (uintptr_t)net % 256)
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "train arguments");
-    if ((rc = laue_cuda_check(h, upload_syms(), "symmetry table"))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     Net n = net_view(net);
     BatchLayout L = batch_layout(n_sets);
