@@ -29,6 +29,12 @@ METRIC = "cost-pair evals/s in Sinkhorn-EM at 1000 grains; time-to-index vs plai
 UNIT = "pairs/s"
 
 
+# DRAM bytes of one pair-pass launch on the 1000-grain workload, counted by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) for the current kernels: each
+# staged spot array read once, nothing re-read from DRAM
+SK_PASS_DRAM_BYTES = 41652736 + 512
+
+
 def max_over_ranks(value, world, device):
     """The largest value over the ranks: the job's step time is the slowest
     replica's."""
@@ -426,6 +432,17 @@ def main():
     torch.cuda.synchronize()
     per_launch_ms = (ev[2].elapsed_time(ev[3]) - ev[0].elapsed_time(ev[1])) / (2 * (n2 - n1))
 
+    # the whole EM iteration captured once as a CUDA graph on static pose buffers
+    Rs, xs = W["R0"].clone(), W["x0"].clone()
+    cap_stream = torch.cuda.Stream()
+    cap_stream.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap_stream):
+        with torch.cuda.graph(graph, stream=cap_stream):
+            em_step(W, api, Rs, xs)
+    stream.wait_stream(cap_stream)
+    torch.cuda.synchronize()
+
     clocks = ClockSampler(local)
     clocks.start()
     times = []
@@ -435,9 +452,10 @@ def main():
     for k in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        Rk, xk = W["R0"].clone(), W["x0"].clone()
         e0.record(stream)
-        em_step(W, api, Rk, xk)
+        Rs.copy_(W["R0"])
+        xs.copy_(W["x0"])
+        graph.replay()
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -515,12 +533,17 @@ def main():
                              "70%% uneven Poisson outliers, eps=1 mm^2, 200 Sinkhorn iterations per EM step"
                              % (cfg.n_grains, cfg.T),
                     grains=cfg.n_grains, angles=cfg.T, observed=W["nI"], model_spots=W["nJ"],
-                    pairs_per_half_iteration=W["pairs_half"], step="one EM iteration",
+                    pairs_per_half_iteration=W["pairs_half"],
+                    step="one EM iteration (refresh, 200 Sinkhorn iterations with read-out, M-step), replayed as "
+                         "one CUDA graph",
                     l2="256 MB buffer written between timed steps", parallelism="replicas" if world > 1 else "1 GPU",
                     autotuned_shapes={"row": tuned[0], "col": tuned[1],
                                       "ms_per_pass": [[round(r, 3), round(c, 3)] for r, c in tuned[2]]}),
         roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="pairs/s", frac=achieved / peak,
-                      traffic=None, kernel="sk_row_kernel+sk_col_kernel (per launch)",
+                      traffic=SK_PASS_DRAM_BYTES if cfg.n_grains == 1000 else None,
+                      traffic_unit="bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu "
+                                   "capture of this workload; profiles/sk_passes_dram_1000grains_90angles.md)",
+                      kernel="sk_row_kernel+sk_col_kernel (per launch)",
                       peak_basis="min(FP32 lane-ops/s / 14, MUFU ex2/s, MUFU rsqrt/s), measured by "
                                  "laue_alu_peaks; binding pipe: %s" % bound_by,
                       pipes={k: v for k, v in pk_.items()}),
