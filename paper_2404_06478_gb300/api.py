@@ -7,6 +7,7 @@ step of the hot path runs here, and there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import re
 import dataclasses
 import math
 
@@ -406,9 +407,7 @@ def index(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, startR, startX, e
     b = ctypes.c_size_t()
     h.check(h.L.laue_index_workspace_size(h.h, obs.T, nI, S, int(n_max), int(lat.w_d0.shape[0]), ctypes.byref(b)),
             "laue_index_workspace_size")
-    if h.ws is None or h.ws.numel() < b.value:
-        h.ws = torch.empty(b.value + 256, dtype=torch.uint8, device=dev)
-        h.check(h.L.laue_set_workspace(h.h, _ptr(h.ws), h.ws.numel(), _stream(stream)), "set_workspace")
+    need = b.value + 256
     R = torch.empty(int(n_max), 9, device=dev)
     x = torch.empty(int(n_max), 3, device=dev)
     assign = torch.empty(max(nI, 1), dtype=torch.int32, device=dev)
@@ -417,9 +416,25 @@ def index(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, startR, startX, e
                             mparams(eps_final, n_newton, n_mm, tol_x, tol_R, hreg))
     ng = ctypes.c_int(0)
     g_s, o_s, l_s = geometry_struct(geom), obs.struct(), lat.struct()
-    h.check(h.L.laue_index(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), _ptr(omega), _ptr(startR),
-                           _ptr(startX), S, ctypes.byref(prm), _ptr(R), _ptr(x), int(n_max), ctypes.byref(ng),
-                           _ptr(assign), _stream(stream)), "laue_index")
+    # The SPOT matrix's size is known only after the fits (its nonzeros per kept
+    # candidate grow with the spot density); when it does not fit, the library
+    # reports the missing bytes, and the call is repeated once with them added.
+    for attempt in range(3):
+        if h.ws is None or h.ws.numel() < need:
+            h.ws = None
+            h.ws = torch.empty(need, dtype=torch.uint8, device=dev)
+            h.check(h.L.laue_set_workspace(h.h, _ptr(h.ws), h.ws.numel(), _stream(stream)), "set_workspace")
+        rc = h.L.laue_index(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), _ptr(omega), _ptr(startR),
+                            _ptr(startX), S, ctypes.byref(prm), _ptr(R), _ptr(x), int(n_max), ctypes.byref(ng),
+                            _ptr(assign), _stream(stream))
+        if rc == N.LAUE_ERR_CAPACITY and attempt < 2:
+            msg = h.L.laue_last_error(h.h)
+            m = re.search(r"need (\d+) more workspace bytes", msg.decode() if msg else "")
+            if m:
+                need = h.ws.numel() + int(m.group(1)) + (1 << 20)
+                continue
+        h.check(rc, "laue_index")
+        break
     k = ng.value
     return R[:k], x[:k], assign[:nI]
 

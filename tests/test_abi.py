@@ -65,3 +65,60 @@ def test_set_encoder_sizes_match_the_oracle(native):
     assert L.laue_lp_set_size() == op.KSET == pr.KSET
     assert L.laue_lp_param_count() == sum(int(np.prod(s)) for _, s in op.PARAM_SHAPES)
     assert [n for n, _ in op.PARAM_SHAPES] == [n for n, _ in pr.PARAM_SHAPES]
+
+
+def test_index_retries_once_with_the_missing_workspace():
+    """The SPOT matrix's size is known only after the single-grain fits.  When
+    laue_index reports that it does not fit, the binding adds the missing
+    bytes named in the library's message to the workspace and calls again.
+    Host logic only: a stand-in library answers the calls, tensors stay on
+    the CPU."""
+    import torch
+    from paper_2404_06478_gb300 import api
+    from paper_2404_06478_gb300 import _native as N
+
+    class FakeLib:
+        def __init__(self):
+            self.calls, self.ws_sizes = 0, []
+
+        def laue_index_workspace_size(self, h, T, nI, S, n_max, M, out):
+            out._obj.value = 1000
+            return 0
+
+        def laue_set_workspace(self, h, ptr, nbytes, stream):
+            self.ws_sizes.append(nbytes)
+            return 0
+
+        def laue_index(self, *args):
+            self.calls += 1
+            if self.calls == 1:
+                return N.LAUE_ERR_CAPACITY
+            args[12]._obj.value = 2
+            return 0
+
+        def laue_last_error(self, h):
+            return b"prototype_select: 300 nonzeros need 5000 more workspace bytes"
+
+    class FakeHandle:
+        def __init__(self):
+            self.h, self.L, self.ws = None, FakeLib(), None
+
+        def check(self, rc, what=""):
+            if rc < 0:
+                raise api.LaueError(rc, what)
+            return rc
+
+    h = FakeHandle()
+    geom = __import__("synthgen").Geometry()
+    lat = api.Lattice(torch.zeros(8, 4), torch.zeros(8, dtype=torch.int32))
+    obs = api.ObsSpots(torch.zeros(10, 4), torch.tensor([0, 10], dtype=torch.int32))
+    api._stream_saved = api._stream
+    try:
+        api._stream = lambda stream=None: None
+        R, x, a = api.index(h, geom, lat, obs, torch.zeros(1), torch.zeros(3, 9), torch.zeros(3, 3), 1.0, 2.25, 4)
+    finally:
+        api._stream = api._stream_saved
+    assert h.L.calls == 2
+    assert h.L.ws_sizes[0] == 1000 + 256
+    assert h.L.ws_sizes[1] == 1000 + 256 + 5000 + (1 << 20)
+    assert R.shape == (2, 9) and x.shape == (2, 3) and a.shape == (10,)

@@ -148,3 +148,35 @@ def test_index_tiny_configuration(env):
                             for k in range(len(Rf))])) for n in range(len(case.R))]
     found_of_true = np.array(order)
     assert (assign[truth >= 0] == found_of_true[gt]).mean() > 0.9
+
+
+def test_index_grows_the_workspace_for_a_dense_spot_matrix():
+    """A dense SPOT matrix: 400 starts (80 near each of 5 grains of the
+    90-rotation, |hkl| <= 6 geometry) all survive the filter, with ~1000
+    nonzeros each; the call completes with all 5 grains, within 0.5 deg and
+    0.5 mm, on a handle that starts without a workspace.  (The retry that
+    adds missing workspace bytes is tested on the host in test_abi.py.)"""
+    import dataclasses
+    import torch
+    from paper_2404_06478_gb300 import api
+    dev = torch.device("cuda", 0)
+    h = api.Handle(dev)  # a fresh handle: no workspace left over from other tests
+    case = make_case(dataclasses.replace(sg.CONFIGS["batched"], n_grains=5), seed=21)
+    rng = np.random.default_rng(22)
+    R0, x0 = [], []
+    for g in range(5):
+        for _ in range(80):
+            R0.append(_rotvec(rng.normal(size=3) * math.radians(0.3) / math.sqrt(3)) @ case.R[g])
+            x0.append(case.x[g] + rng.normal(size=3) * 0.2)
+    ob = api.ObsSpots.from_numpy(case.obs.p, case.obs.I_off, device=dev)
+    lat = api.Lattice.cubic(case.cfg.a, case.cfg.hmax, case.cfg.centering, device=dev)
+    t = lambda a: torch.tensor(np.asarray(a), dtype=torch.float32, device=dev)
+    R, x, _ = api.index(h, GEOM, lat, ob, t(case.om), t(np.array(R0)), t(np.array(x0)), case.cfg.eps, case.c_out, 50,
+                        n_em=10, n_sinkhorn=60, k_single=8, f_out=0.3)
+    torch.cuda.synchronize()
+    assert h.device_status() == 0
+    Rf = R.cpu().numpy().reshape(-1, 3, 3).astype(np.float64)
+    xf = x.cpu().numpy().astype(np.float64)
+    assert len(Rf) == 5
+    mis, dx = _match(Rf, xf, case.R, case.x)
+    assert np.all(mis < 0.5) and np.all(dx < 0.5), (mis, dx)
