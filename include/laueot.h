@@ -151,11 +151,13 @@ typedef struct {
  * Algorithm SingleLaueOT; filter f_out of Section "Selection of Prototypes
  * with Optimal Transport"). */
 typedef struct {
-    float eps_final; /* final temperature; eps anneals from 100 eps_final */
+    float eps_final; /* final temperature */
     float c_out;
     float f_out;     /* keep a fit when #unmatched rays < f_out |J| */
     int k_max;       /* annealed EM steps per start */
     LaueMParams mstep;
+    float anneal;    /* eps starts at anneal * eps_final (laue_anneal_eps); <= 0 means 100 */
+    int recut;       /* nonzero: list the visible spots again at the pose of every step */
 } LaueSingleParams;
 
 /* ---- handle and workspace --------------------------------------------- */
@@ -199,6 +201,21 @@ int laue_alu_peaks(laue_handle* h, double* out_host, void* stream);
  * LAUE_ERR_CAPACITY if *M > cap (nothing beyond cap written). */
 int laue_reflections(double a, int hmax, int centering, int cap, float* w_d0_host,
                      int* nharm_host, int* hkl0_host, int* M);
+
+/* Outlier cost c_out of the extended cost matrix (paper Eq. update_L: the
+ * likelihood of a pair at 3 sigma, Section "Simulations and experiments"):
+ * the pair cost of two unit rays 3 sigma_mm / D apart,
+ * D^2 |a - b|^2 = 4 D^2 sin^2(1.5 sigma_mm / D), in mm^2.  Host function;
+ * returns -1 when sigma_mm <= 0 or D <= 0. */
+double laue_c_out(double sigma_mm, double D);
+
+/* Temperature of annealed step k (paper Section "Deterministic annealing"):
+ * eps_k = eps_final factor^(1 - k/K) for 0 <= k < K = ceil(0.75 n_em), then
+ * eps_final (also when K < 1).  The one schedule of the library: laue_index,
+ * laue_single_fit (factor 100, n_em = k_max) and the binding's EM driver all
+ * use it.  Host function; returns -1 for eps_final <= 0, n_em < 0, k < 0 or
+ * factor <= 0. */
+double laue_anneal_eps(double eps_final, int n_em, int k, double factor);
 
 /* ---- hot path ---------------------------------------------------------- */
 
@@ -319,6 +336,15 @@ int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, const LaueLatt
  * Asynchronous. */
 int laue_axis_angle(laue_handle* h, const float* w, const float* R0, float* R, float* JlT, int N,
                     void* stream);
+
+/* Vector-Jacobian product for laue_objective_grad under the parameterisation
+ * of laue_axis_angle (no counterpart in the paper): with grad (N x 6) =
+ * [dE/dphi, dE/dx] at R = exp([w]x) R0 (phi the left perturbation),
+ * gw (N x 3) = gout_n J_l(w_n)^T dE/dphi_n and gx (N x 3, optional) =
+ * gout_n dE/dx_n; gout (N, optional) defaults to 1.  w: N x 3.
+ * Asynchronous. */
+int laue_axis_angle_vjp(laue_handle* h, const float* w, const float* grad, const float* gout, float* gw,
+                        float* gx, int N, void* stream);
 
 /* Batched single-grain fitting (paper Section "Single-grain fitting",
  * Appendix "Single-grain fitting", Eq. elbo_single, Algorithm SingleLaueOT)

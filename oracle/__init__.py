@@ -46,6 +46,7 @@ def lib():
             L.orc_forward.restype = ctypes.c_long
             L.orc_pair_cost.restype = ctypes.c_double
             L.orc_eps_schedule.restype = ctypes.c_double
+            L.orc_eps_schedule_f.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -200,8 +201,8 @@ def mstep(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps,
     return R.reshape(-1, 3, 3), x, stats
 
 
-def eps_schedule(eps_final, n_em, k):
-    return lib().orc_eps_schedule(ctypes.c_double(eps_final), n_em, k)
+def eps_schedule(eps_final, n_em, k, factor=100.0):
+    return lib().orc_eps_schedule_f(ctypes.c_double(eps_final), n_em, k, ctypes.c_double(factor))
 
 
 def em(geom, planes, omega, p, I_off, J_off, grain, plane, R, x, eps_final, n_em, n_sinkhorn,
@@ -223,7 +224,7 @@ def em(geom, planes, omega, p, I_off, J_off, grain, plane, R, x, eps_final, n_em
 
 
 def single_fit(geom, planes, omega, p, I_off, R0, x0, eps_final, k_max, c_out,
-               n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, f_out=0.1):
+               n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, f_out=0.1, anneal=100.0, recut=False):
     L = lib()
     R0 = _f64(R0, (-1, 9)); x0 = _f64(x0, (-1, 3))
     S = len(R0); omega = _f64(omega)
@@ -234,7 +235,7 @@ def single_fit(geom, planes, omega, p, I_off, R0, x0, eps_final, k_max, c_out,
                      _d(_f64(p, (-1, 3))), S, _d(R0), _d(x0), ctypes.c_double(eps_final), k_max,
                      ctypes.c_double(c_out), n_newton, n_mm, ctypes.c_double(tol_x),
                      ctypes.c_double(tol_R), ctypes.c_double(hreg), ctypes.c_double(f_out),
-                     _d(Ro), _d(xo), _i(keep), _d(unm))
+                     ctypes.c_double(anneal), 1 if recut else 0, _d(Ro), _d(xo), _i(keep), _d(unm))
     return Ro.reshape(-1, 3, 3), xo, keep.astype(bool), unm
 
 

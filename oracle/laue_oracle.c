@@ -942,10 +942,14 @@ int orc_mstep(const double* geom, const double* w, const double* omega, int T,
 
 /* Section "Deterministic annealing": eps_init = 100 eps_final, geometric
  * cooling that reaches eps_final at step ceil(0.75 n_em), then held. */
-double orc_eps_schedule(double eps_final, int n_em, int k) {
+double orc_eps_schedule_f(double eps_final, int n_em, int k, double factor) {
     int K = (int)ceil(0.75 * n_em);
     if (K < 1 || k >= K) return eps_final;
-    return eps_final * pow(100.0, 1.0 - (double)k / (double)K);
+    return eps_final * pow(factor, 1.0 - (double)k / (double)K);
+}
+
+double orc_eps_schedule(double eps_final, int n_em, int k) {
+    return orc_eps_schedule_f(eps_final, n_em, k, 100.0);
 }
 
 /* Algorithm LaueOT (multi-grain fitting) with a fixed number of EM steps:
@@ -1036,7 +1040,8 @@ int orc_single_fit(const double* geom, const double* w, const double* d0, const 
                    int S, const double* R0, const double* x0,
                    double eps_final, int k_max, double c_out,
                    int n_newton, int n_mm, double tol_x, double tol_R, double hreg,
-                   double f_out, double* R_out, double* x_out, int* keep, double* unmatched) {
+                   double f_out, double anneal, int recut,
+                   double* R_out, double* x_out, int* keep, double* unmatched) {
     geom_t G;
     geom_unpack(geom, &G);
     int stride = 1;
@@ -1059,13 +1064,19 @@ int orc_single_fit(const double* geom, const double* w, const double* d0, const 
         double R[9], x[3];
         memcpy(R, R0 + 9 * s, sizeof(R));
         memcpy(x, x0 + 3 * s, sizeof(x));
-        long nj = orc_forward(geom, w, d0, nharm, M, R, x, 1, omega, T, cap, Joff, gr, pl, ray4,
-                              s3, dk, c3, NULL, NULL);
-        for (int t = 0; t < T; ++t)
-            for (int j = Joff[t]; j < Joff[t + 1]; ++j) { jt[j] = t; jpos[j] = j; js[j] = j; }
+        long nj = 0;
         qdense_ctx qc = {Q, jpos, I_off, jt, stride};
         for (int k = 0; k < k_max; ++k) {
-            double eps = orc_eps_schedule(eps_final, k_max, k);
+            double eps = orc_eps_schedule_f(eps_final, k_max, k, anneal);
+            /* Algorithm SingleLaueOT computes the model rays of the grain at
+             * every iteration: with recut the visible set is listed again at
+             * the pose of step k, otherwise it stays the one of the start */
+            if (k == 0 || recut) {
+                nj = orc_forward(geom, w, d0, nharm, M, R, x, 1, omega, T, cap, Joff, gr, pl, ray4,
+                                 s3, dk, c3, NULL, NULL);
+                for (int t = 0; t < T; ++t)
+                    for (int j = Joff[t]; j < Joff[t + 1]; ++j) { jt[j] = t; jpos[j] = j; js[j] = j; }
+            }
             orc_refresh(geom, w, d0, nharm, R, x, omega, T, Joff, gr, pl, ray4, c3);
             for (long j = 0; j < nj; ++j)
                 for (int a = 0; a < 3; ++a) r3[3 * j + a] = ray4[4 * j + a];

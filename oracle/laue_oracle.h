@@ -65,6 +65,7 @@ int orc_mstep(const double* geom, const double* w, const double* omega, int T,
               double* R, double* x, double* stats);
 
 double orc_eps_schedule(double eps_final, int n_em, int k);
+double orc_eps_schedule_f(double eps_final, int n_em, int k, double factor);
 
 int orc_em(const double* geom, const double* w, const double* d0, const int* nharm,
            const double* omega, int T, const int* I_off, const double* p,
@@ -79,7 +80,8 @@ int orc_single_fit(const double* geom, const double* w, const double* d0, const 
                    int S, const double* R0, const double* x0,
                    double eps_final, int k_max, double c_out,
                    int n_newton, int n_mm, double tol_x, double tol_R, double hreg,
-                   double f_out, double* R_out, double* x_out, int* keep, double* unmatched);
+                   double f_out, double anneal, int recut,
+                   double* R_out, double* x_out, int* keep, double* unmatched);
 
 int orc_spot_matrix(const double* geom, const double* w, const double* d0, const int* nharm, int M,
                     const double* omega, int T, const int* I_off, const double* p,

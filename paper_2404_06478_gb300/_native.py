@@ -61,7 +61,8 @@ class LaueProblemDims(ctypes.Structure):
 
 
 class LaueSingleParams(ctypes.Structure):
-    _fields_ = [("eps_final", _f), ("c_out", _f), ("f_out", _f), ("k_max", _i), ("mstep", LaueMParams)]
+    _fields_ = [("eps_final", _f), ("c_out", _f), ("f_out", _f), ("k_max", _i), ("mstep", LaueMParams),
+                ("anneal", _f), ("recut", _i)]
 
 
 class LaueIndexParams(ctypes.Structure):
@@ -96,6 +97,7 @@ SIGNATURES = {
     "laue_objective_grad": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots),
                             _vp, _vp, _f, _vp, _vp, _vp, _i, _vp, _vp, _vp],
     "laue_axis_angle": [_vp, _vp, _vp, _vp, _vp, _i, _vp],
+    "laue_axis_angle_vjp": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp],
     "laue_single_fit": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                         _P(LaueSingleParams), _vp, _vp, _vp, _vp, _vp],
     "laue_prototype_select": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
@@ -125,6 +127,8 @@ SIZE_FUNCTIONS = [
     ("laue_lp_net_bytes", [], ctypes.c_size_t),
     ("laue_lp_batch_bytes", [_i], ctypes.c_size_t),
     ("laue_lp_batch_offset", [_i, _i], ctypes.c_longlong),
+    ("laue_c_out", [_d, _d], _d),
+    ("laue_anneal_eps", [_d, _i, _i, _d], _d),
 ]
 
 

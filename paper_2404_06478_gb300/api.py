@@ -33,9 +33,19 @@ def _stream(stream=None):
 
 
 def c_out_for(sigma_mm: float, D: float) -> float:
-    """Outlier cost c_out = D^2 |a - b|^2 for unit rays 3 sigma apart
-    (likelihood at 3 sigma, sigma_ang = sigma_mm / D)."""
-    return 4.0 * D * D * math.sin(1.5 * sigma_mm / D) ** 2
+    """laue_c_out: outlier cost for spot noise sigma_mm at distance D."""
+    v = N.lib().laue_c_out(float(sigma_mm), float(D))
+    if v < 0:
+        raise LaueError(N.LAUE_ERR_INVALID_ARG, "laue_c_out: sigma_mm and D must be > 0")
+    return v
+
+
+def anneal_eps(eps_final: float, n_em: int, k: int, factor: float = 100.0) -> float:
+    """laue_anneal_eps: temperature of annealed step k."""
+    v = N.lib().laue_anneal_eps(float(eps_final), int(n_em), int(k), float(factor))
+    if v < 0:
+        raise LaueError(N.LAUE_ERR_INVALID_ARG, "laue_anneal_eps: bad arguments")
+    return v
 
 
 def geometry_struct(geom) -> N.LaueGeometry:
@@ -348,8 +358,21 @@ def axis_angle(h: Handle, w, R0, with_jacobian=False, stream=None):
     return (R[:N_], J[:N_]) if with_jacobian else R[:N_]
 
 
+def axis_angle_vjp(h: Handle, w, grad, gout=None, stream=None):
+    """laue_axis_angle_vjp: (gw (N, 3), gx (N, 3)) from a left-perturbation
+    gradient grad (N, 6) at R = exp([w]x) R0, scaled by gout (N,)."""
+    N_ = int(w.shape[0])
+    gw = torch.empty(max(N_, 1), 3, device=w.device)
+    gx = torch.empty(max(N_, 1), 3, device=w.device)
+    go = gout.contiguous().float() if gout is not None else None
+    h.check(h.L.laue_axis_angle_vjp(h.h, _ptr(w.contiguous().float()), _ptr(grad.contiguous().float()), _ptr(go),
+                                    _ptr(gw), _ptr(gx), N_, _stream(stream)), "laue_axis_angle_vjp")
+    return gw[:N_], gx[:N_]
+
+
 def single_fit(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, R0, x0, eps_final, k_max, c_out,
-               f_out=0.1, n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, stream=None):
+               f_out=0.1, n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, anneal=100.0, recut=False,
+               stream=None):
     """laue_single_fit: (R (S, 9), x (S, 3), keep (S,) bool, unmatched (S,))."""
     R0 = R0.reshape(-1, 9).contiguous().float()
     x0 = x0.reshape(-1, 3).contiguous().float()
@@ -360,7 +383,8 @@ def single_fit(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, R0, x0, eps_
     keep = torch.empty(max(S, 1), dtype=torch.int32, device=R0.device)
     unm = torch.empty(max(S, 1), device=R0.device)
     prm = N.LaueSingleParams(float(eps_final), float(c_out), float(f_out), int(k_max),
-                             mparams(eps_final, n_newton, n_mm, tol_x, tol_R, hreg))
+                             mparams(eps_final, n_newton, n_mm, tol_x, tol_R, hreg), float(anneal),
+                             1 if recut else 0)
     g_s, o_s, l_s = geometry_struct(geom), obs.struct(), lat.struct()
     h.check(h.L.laue_single_fit(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), _ptr(omega), _ptr(R0),
                                 _ptr(x0), S, ctypes.byref(prm), _ptr(Ro), _ptr(xo), _ptr(keep), _ptr(unm),

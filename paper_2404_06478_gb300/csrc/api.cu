@@ -610,6 +610,25 @@ extern "C" int laue_axis_angle(laue_handle* h, const float* w, const float* R0, 
     return laue_cuda_check(h, axis_angle_run(w, R0, R, JlT, N, (cudaStream_t)stream), "axis_angle launch");
 }
 
+extern "C" int laue_axis_angle_vjp(laue_handle* h, const float* w, const float* grad, const float* gout, float* gw,
+                                   float* gx, int N, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    if (N < 0 || (N > 0 && (!w || !grad || !gw)))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "axis_angle_vjp: bad arguments");
+    return laue_cuda_check(h, axis_angle_vjp_run(w, grad, gout, gw, gx, N, (cudaStream_t)stream),
+                           "axis_angle_vjp launch");
+}
+
+extern "C" double laue_c_out(double sigma_mm, double D) {
+    if (!(sigma_mm > 0.0) || !(D > 0.0)) return -1.0;
+    return outlier_cost(sigma_mm, D);
+}
+
+extern "C" double laue_anneal_eps(double eps_final, int n_em, int k, double factor) {
+    if (!(eps_final > 0.0) || n_em < 0 || k < 0 || !(factor > 0.0)) return -1.0;
+    return anneal_eps(eps_final, n_em, k, factor);
+}
+
 extern "C" int laue_single_fit(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
                                const LaueObsSpots* obs, const float* omega, const float* startR,
                                const float* startX, int S, const LaueSingleParams* prm, float* R_out,
@@ -654,6 +673,8 @@ extern "C" int laue_single_fit(laue_handle* h, const LaueGeometry* geom, const L
     a.k_max = prm->k_max;
     a.n_newton = prm->mstep.n_newton;
     a.n_mm = prm->mstep.n_mm;
+    a.anneal = prm->anneal > 0.0f ? prm->anneal : 100.0f;
+    a.recut = prm->recut;
     a.scratch = (float*)(ws + L.sfs);
     a.cap = kSfCap;
     a.icap = kSfIcap;

@@ -258,4 +258,25 @@ __device__ __forceinline__ float max3(float a, float b, float c) {
 
 #endif  // __CUDACC__
 
+// ---------------------------------------------------------------------------
+// deterministic annealing (paper Section "Deterministic annealing"): the one
+// temperature schedule of the library, shared by the host drivers and the
+// single-grain fit kernel.  eps_k = eps_final * factor^(1 - k/K) for
+// 0 <= k < K = ceil(0.75 n_em), then eps_final.  Computed in double so that
+// every caller takes the same value.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double anneal_eps(double eps_final, int n_em, int k, double factor) {
+    int K = (int)ceil(0.75 * (double)n_em);
+    if (K < 1 || k >= K) return eps_final;
+    return eps_final * pow(factor, 1.0 - (double)k / (double)K);
+}
+
+// Outlier cost: the pair cost of two unit rays 3 sigma apart,
+// D^2 |a - b|^2 = 4 D^2 sin^2(1.5 sigma_mm / D) (sigma on the detector at
+// distance D, read as the angle sigma_mm / D).
+__host__ __device__ inline double outlier_cost(double sigma_mm, double D) {
+    double s = sin(1.5 * sigma_mm / D);
+    return 4.0 * D * D * s * s;
+}
+
 }  // namespace laue

@@ -143,7 +143,7 @@ extern "C" int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLa
     };
     *n_grains_host = 0;
     // 1. batched single-grain fits
-    LaueSingleParams sp{prm->eps_final, prm->c_out, prm->f_out, prm->k_single, prm->mstep};
+    LaueSingleParams sp{prm->eps_final, prm->c_out, prm->f_out, prm->k_single, prm->mstep, 100.0f, 0};
     if ((rc = laue_single_fit(h, geom, lat, obs, omega, startR, startX, S, &sp, fitR, fitX, keep, nullptr, stream)))
         return restore(rc);
     // 2. kept candidates (in start order)
@@ -170,9 +170,8 @@ extern "C" int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLa
     if ((rc = laue_forward(h, geom, lat, R_out, x_out, kstar, omega, T, &ms, &total, stream))) return restore(rc);
     // 5. annealed EM (Algorithm LaueOT) with a final E-step for the assignment
     LaueOTParams op{prm->unmatched_frac, 0.0f, prm->c_out, prm->n_sinkhorn, prm->dust_mode, 0, 0};
-    int K = (int)std::ceil(0.75 * prm->n_em);
     for (int k = 0; k <= prm->n_em; ++k) {
-        double eps = (K < 1 || k >= K) ? prm->eps_final : prm->eps_final * std::pow(100.0, 1.0 - (double)k / K);
+        double eps = anneal_eps(prm->eps_final, prm->n_em, k, 100.0);
         op.eps = (float)eps;
         if ((rc = laue_refresh(h, geom, lat, R_out, x_out, omega, &ms, stream))) return restore(rc);
         bool last = k == prm->n_em;

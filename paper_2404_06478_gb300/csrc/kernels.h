@@ -167,6 +167,8 @@ struct SfArgs {
     float* unmatched;
     float eps_final, c_out, f_out, tol_x, tol_R, hreg;
     int k_max, n_newton, n_mm;
+    float anneal;  // eps_init / eps_final
+    int recut;     // re-list the visible spots at every step
     float* scratch;
     int cap, icap;
     int* queue;  // 2 ints: start queue head, completion ticket
@@ -198,5 +200,7 @@ cudaError_t spot_greedy_run(const SpotArgs& sp, int n_obs, int Nc, int k_max, in
 cudaError_t single_fit_run(const SfArgs& a, int ctas, cudaStream_t s);
 cudaError_t grad_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s);
 cudaError_t axis_angle_run(const float* w, const float* R0, float* R, float* JlT, int N, cudaStream_t s);
+cudaError_t axis_angle_vjp_run(const float* w, const float* grad, const float* gout, float* gw, float* gx, int N,
+                               cudaStream_t s);
 
 }  // namespace laue

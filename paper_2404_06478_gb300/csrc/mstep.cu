@@ -415,6 +415,47 @@ __global__ void axis_angle_kernel(const float* w, const float* R0, float* R, flo
     }
 }
 
+// Vector-Jacobian product of E(exp([w]x) R0, x) for a gradient taken with
+// respect to a left perturbation of R (laue_objective_grad):
+//   dE/dw = J_l(w)^T dE/dphi,  dE/dx passed through, both scaled by gout_n.
+__global__ void axis_angle_vjp_kernel(const float* w, const float* grad, const float* gout, float* gw, float* gx,
+                                      int N) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float a = w[3 * n], b = w[3 * n + 1], c = w[3 * n + 2];
+    float th2 = a * a + b * b + c * c, th = sqrtf(th2);
+    float B, C2;  // (1 - cos th)/th^2, (th - sin th)/th^3
+    if (th < 1e-4f) {
+        B = 0.5f - th2 / 24.0f;
+        C2 = 1.0f / 6.0f - th2 / 120.0f;
+    } else {
+        float sn, cs;
+        sincosf(th, &sn, &cs);
+        B = (1.0f - cs) / th2;
+        C2 = (th - sn) / (th2 * th);
+    }
+    float K[9] = {0.0f, -c, b, c, 0.0f, -a, -b, a, 0.0f};
+    float s = gout ? gout[n] : 1.0f;
+    const float* g = grad + 6 * n;
+    for (int q = 0; q < 3; ++q) {  // (J_l^T g)_q = sum_r J_l[r][q] g_r
+        float acc = 0.0f;
+        for (int r = 0; r < 3; ++r) {
+            float k2 = K[3 * r] * K[q] + K[3 * r + 1] * K[3 + q] + K[3 * r + 2] * K[6 + q];
+            float jl = (r == q ? 1.0f : 0.0f) + B * K[3 * r + q] + C2 * k2;
+            acc += jl * g[r];
+        }
+        gw[3 * n + q] = s * acc;
+    }
+    if (gx)
+        for (int q = 0; q < 3; ++q) gx[3 * n + q] = s * g[3 + q];
+}
+
+cudaError_t axis_angle_vjp_run(const float* w, const float* grad, const float* gout, float* gw, float* gx, int N,
+                               cudaStream_t s) {
+    if (N > 0) axis_angle_vjp_kernel<<<(N + 127) / 128, 128, 0, s>>>(w, grad, gout, gw, gx, N);
+    return cudaGetLastError();
+}
+
 cudaError_t axis_angle_run(const float* w, const float* R0, float* R, float* JlT, int N, cudaStream_t s) {
     if (N > 0) axis_angle_kernel<<<(N + 127) / 128, 128, 0, s>>>(w, R0, R, JlT, N);
     return cudaGetLastError();

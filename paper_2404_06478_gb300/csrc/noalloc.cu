@@ -28,6 +28,7 @@ constexpr int kMaxDevices = 64;
 
 struct StaticDevice {
     bool ready;
+    int device;     // CUDA ordinal this entry describes
     void* scratch;  // device address of g_static_scratch on this device
     int sm_count;
     int row_occ[kSkVariants], col_occ[kSkVariants];
@@ -50,6 +51,7 @@ int static_device(StaticDevice** out) {
         if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LAUE_ERR_CUDA;
         if (sinkhorn_occupancy(d.row_occ, d.col_occ) != 0)
             for (int v = 0; v < kSkVariants; ++v) d.row_occ[v] = d.col_occ[v] = 1;
+        d.device = dev;
         d.scratch = p;
         d.sm_count = sm;
         d.ready = true;
@@ -79,7 +81,7 @@ extern "C" int laue_cost_sinkhorn_noalloc(const LaueGeometry* geom, const LaueOb
     Layout L = make_layout(dims, d->sm_count);
     if (L.fwd_blocks > kStaticScratchBytes) return LAUE_ERR_CAPACITY;
     laue_handle h{};  // a view of the static scratch; nothing is allocated
-    h.device = 0;
+    h.device = d->device;
     h.sm_count = d->sm_count;
     for (int v = 0; v < kSkVariants; ++v) {
         h.row_occ[v] = d->row_occ[v];

@@ -6,7 +6,9 @@
 // One CTA fits one start at a time (persistent CTAs pull starts from a
 // queue).  Per start:
 //   1. cut: the spots the start grain makes (Eq. model_spot_cut) are listed,
-//      sorted by (t, m), in the CTA's scratch slice; the list stays frozen;
+//      sorted by (t, m), in the CTA's scratch slice; the list stays frozen
+//      unless recut is set, when it is listed again at the pose of every step
+//      (Algorithm SingleLaueOT recomputes the grain's rays at every iteration);
 //   2. k_max annealed EM steps: the E-step plan is row-normalised over the
 //      grain's model spots at t_i plus the outlier column,
 //        Q_ij = exp(-C_ij/eps) / (sum_j' exp(-C_ij'/eps) + exp(-c_out/eps)),
@@ -335,9 +337,7 @@ __device__ void sf_mm(const SfArgs& a, SfShared& S, const SfScratch& Z, float* M
 }
 
 __device__ __forceinline__ float sf_eps(const SfArgs& a, int k) {
-    int K = (int)ceilf(0.75f * a.k_max);
-    if (K < 1 || k >= K) return a.eps_final;
-    return a.eps_final * exp2f(log2f(100.0f) * (1.0f - (float)k / (float)K));
+    return (float)anneal_eps(a.eps_final, a.k_max, k, a.anneal);
 }
 
 __global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
@@ -356,6 +356,10 @@ __global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
         sf_cut(a, S, Z);
         bool overflow = S.overflow != 0;
         for (int k = 0; k < a.k_max; ++k) {
+            if (k > 0 && a.recut) {  // the visible set at the pose of this step
+                sf_cut(a, S, Z);
+                overflow |= S.overflow != 0;
+            }
             float eps = sf_eps(a, k);
             float negK = -a.G.D * a.G.D * log2e / eps, dust = -a.c_out * log2e / eps;
             sf_refresh(a, S, Z);  // E-step pose

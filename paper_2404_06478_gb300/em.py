@@ -12,7 +12,6 @@ then holds.  The host only enqueues work: no step reads device data back.
 from __future__ import annotations
 
 import dataclasses
-import math
 
 import torch
 
@@ -20,12 +19,9 @@ from . import api
 
 
 def eps_schedule(eps_final: float, n_em: int, k: int, factor: float = 100.0) -> float:
-    """eps_k = eps_final * factor^(1 - k/K) for k < K = ceil(0.75 n_em), then
-    eps_final (factor 1: no annealing)."""
-    K = int(math.ceil(0.75 * n_em))
-    if K < 1 or k >= K:
-        return float(eps_final)
-    return float(eps_final) * float(factor) ** (1.0 - k / K)
+    """The library's annealing schedule (laue_anneal_eps); factor 1 means no
+    annealing."""
+    return api.anneal_eps(eps_final, n_em, k, factor)
 
 
 @dataclasses.dataclass

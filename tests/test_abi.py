@@ -20,7 +20,7 @@ def native():
 
 def _declared():
     text = open(os.path.join(ROOT, "include", "laueot.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*|size_t|long long)\s+(laue_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*|size_t|long long|double)\s+(laue_\w+)\s*\(", text, re.M)))
 
 
 def test_header_declares_the_boundary():
@@ -122,3 +122,19 @@ def test_index_retries_once_with_the_missing_workspace():
     assert h.L.ws_sizes[0] == 1000 + 256
     assert h.L.ws_sizes[1] == 1000 + 256 + 5000 + (1 << 20)
     assert R.shape == (2, 9) and x.shape == (2, 3) and a.shape == (10,)
+
+
+def test_host_constants_match_oracle(native):
+    """laue_c_out and laue_anneal_eps (host functions of the library) agree with
+    the oracle's outlier cost and annealing schedule."""
+    import oracle
+    from paper_2404_06478_gb300 import api
+    for sigma, D in ((0.5, 200.0), (0.143, 160.0), (1.2, 350.0)):
+        assert api.c_out_for(sigma, D) == pytest.approx(oracle.c_out_for(sigma, D), rel=1e-14)
+    for n_em in (1, 4, 20, 30):
+        for k in range(n_em + 2):
+            for fac in (100.0, 1000.0, 1.0):
+                assert api.anneal_eps(1.5, n_em, k, fac) == pytest.approx(oracle.eps_schedule(1.5, n_em, k, fac),
+                                                                           rel=1e-14)
+    L = native.lib()
+    assert L.laue_c_out(-1.0, 200.0) < 0 and L.laue_anneal_eps(1.0, -1, 0, 100.0) < 0

@@ -147,3 +147,46 @@ def test_autograd_function_matches_oracle(env):
     gw, gx = w.grad.cpu().numpy(), x.grad.cpu().numpy()
     np.testing.assert_allclose(gw, ref[:, :3], rtol=1e-3, atol=1e-4 * np.abs(ref[:, :3]).max())
     np.testing.assert_allclose(gx, ref[:, 3:], rtol=1e-3, atol=1e-4 * np.abs(ref[:, 3:]).max())
+
+
+def test_autograd_function_at_nonzero_axis_angle(env):
+    """The same function at w != 0, where the axis-angle chain rule
+    (laue_axis_angle_vjp) matters: dE/dw and dE/dx equal FP64 central
+    differences of the oracle's objective in w and x (Q held at the plan of the
+    poses R(w) = exp([w]x) R0, x), with an upstream gradient gout != 1."""
+    torch, api, dev = env["torch"], env["api"], env["dev"]
+    from paper_2404_06478_gb300.autograd import ot_weighted_cost
+    case, Rb, x0, f, g, eps = _estep_case(sg.CONFIGS["tiny"], 6, eps=2.0)
+    rng = np.random.default_rng(61)
+    w0 = f32(rng.normal(size=(len(x0), 3)) * 0.3)
+    R0 = f32(np.array([_rotvec(-w) @ a for w, a in zip(w0, Rb)]))  # so that R(w0) ~ Rb
+    Rw = np.array([_rotvec(w) @ a for w, a in zip(w0, R0)])
+    fw = oracle.forward(GEOM, case.planes, Rw, x0, case.om)
+    # the model list of the E-step case, refreshed at R(w0) (same labels)
+    ray, ce = oracle.refresh(GEOM, case.planes, Rw, x0, case.om, case.fw["J_off"], case.fw["grain"],
+                             case.fw["plane"])
+    case.fw["ray"], case.fw["center"] = f32(ray), f32(ce)
+    ob, ms = to_device(case, dev)
+    lat = api.Lattice.cubic(case.cfg.a, case.cfg.hmax, case.cfg.centering, device=dev)
+    t = lambda a: torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous()
+    w = t(w0).requires_grad_(True)
+    x = t(x0).requires_grad_(True)
+    gout = f32(rng.uniform(0.5, 2.0, size=len(x0)))
+    E = ot_weighted_cost(w, x, t(R0.reshape(-1, 9)), env["h"], GEOM, lat, ob, ms, t(f), t(g), eps, t(case.om))
+    (E * t(gout)).sum().backward()
+    obs, cf = case.obs, case.fw
+    args = (GEOM, case.planes, case.om, obs.p, obs.I_off, cf["J_off"], cf["grain"], cf["plane"], ce, ray[:, :3],
+            f, g, eps)
+    h = 1e-6
+    FD = np.zeros((len(x0), 6))
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        Rp = np.array([_rotvec(w + e[:3]) @ a for w, a in zip(w0, R0)])
+        Rm = np.array([_rotvec(w - e[:3]) @ a for w, a in zip(w0, R0)])
+        FD[:, k] = (oracle.grain_objective(*args, Rp, x0 + e[3:]) - oracle.grain_objective(*args, Rm, x0 - e[3:])) / (2 * h)
+    FD *= gout[:, None]
+    gw, gx = w.grad.cpu().numpy(), x.grad.cpu().numpy()
+    assert fw["J_off"][-1] > 0
+    np.testing.assert_allclose(gw, FD[:, :3], rtol=1e-3, atol=1e-4 * np.abs(FD[:, :3]).max())
+    np.testing.assert_allclose(gx, FD[:, 3:], rtol=1e-3, atol=1e-4 * np.abs(FD[:, 3:]).max())

@@ -535,3 +535,100 @@ def test_adjoint_gradient_fd_50_grains_20_rotations():
         Em = oracle.grain_objective(*args, c, r, f, g, 2.0, Rm, x - e[3:])
         FD[:, k] = (Ep - Em) / (2 * h)
     assert np.abs(G - FD).max() <= 1e-6 * np.abs(G).max()
+
+
+# ------------------------------------------------ corners pinned by hand
+
+def test_spot_matrix_by_hand_two_angles():
+    """Grain-to-spot matrix (App. "Selection of prototypes", read as the gain
+    over the outlier baseline) on a constructed case whose value follows from
+    geometry alone.  The grain sits at the origin with R = I.  At omega = 0 its
+    (0,0,-2) reflection sends the ray r = (0,0,-1) straight back to (0,0,-200).
+    Observed spot 0 (angle 0) lies at (200 tan(th), 0, -200), so its ray estimate
+    makes the angle th with r and C = 4 D^2 sin^2(th/2); every other model spot
+    of that angle is far away, so Lbar = (c_out - C)/eps_s to rounding.
+    Observed spot 1 has the same coordinates at angle 1 (omega = 30 deg), where no
+    model spot is near: it must get 0 (it would get spot 0's value if spots of
+    another angle counted).  Observed spot 2 (angle 0) is far from every spot: 0.
+    A mis-signed baseline gives 0 for spot 0 instead of a positive gain."""
+    P = oracle.reflections(2.87, 4, 1)
+    om = np.array([0.0, math.radians(30.0)])
+    R, x = np.eye(3)[None], np.zeros((1, 3))
+    th = math.radians(0.1)
+    p0 = np.array([200.0 * math.tan(th), 0.0, -200.0])
+    far = np.array([60.0, -50.0, -200.0])
+    fw = oracle.forward(GEOM, P, R, x, om)
+    J = fw["J_off"]
+    # preconditions read off the forward model: the straight-back spot exists at
+    # angle 0, every other spot is > 15 mm from p0 (both angles) and from `far`
+    s0 = fw["spot"][J[0]:J[1]]
+    k0 = np.argmin(np.linalg.norm(s0 - [0, 0, -200.0], axis=1))
+    np.testing.assert_allclose(s0[k0], [0, 0, -200.0], atol=1e-9)
+    np.testing.assert_allclose(fw["ray"][J[0] + k0, :3], [0, 0, -1.0], atol=1e-12)
+    others0 = np.delete(s0, k0, axis=0)
+    assert np.linalg.norm(others0 - p0, axis=1).min() > 15.0
+    assert np.linalg.norm(fw["spot"][J[1]:J[2]] - p0, axis=1).min() > 15.0
+    assert np.linalg.norm(s0 - far, axis=1).min() > 15.0
+    pobs = np.array([p0, p0, far])
+    I_off = [0, 2, 3]  # spots 0 and 2 at angle 0, spot 1 at angle 1
+    pobs = pobs[[0, 2, 1]]
+    eps_s, c_out, D = 1.0, oracle.c_out_for(0.5, GEOM.D), GEOM.D
+    L = oracle.spot_matrix(GEOM, P, om, pobs, I_off, R, x, eps_s, c_out)
+    C = 4.0 * D * D * math.sin(th / 2) ** 2
+    assert L.shape == (3, 1)
+    assert L[0, 0] == pytest.approx((c_out - C) / eps_s, rel=1e-12)
+    assert L[0, 0] > 0.5
+    assert L[1, 0] == 0.0  # far spot at angle 0
+    assert L[2, 0] == 0.0  # same coordinates as spot 0, but at angle 1
+
+
+def test_masses_balance_when_model_spots_outnumber_observed():
+    """Masses of the dustbins (Eq. estep_obj balance T_a = T_b - b^T 1 + a^T 1):
+    with |J| > |I| + ceil(frac |J|) the outlier mass would be negative, so the
+    unmatched mass rises to |J| - |I| and the outlier mass is 0.  Both readings
+    keep total row mass = total column mass; Sinkhorn then meets every marginal
+    (the outlier column carries nothing)."""
+    I_off, J_off = [0, 2, 3], [0, 6, 10]
+    U, O = oracle.masses(0, 0.4, I_off, J_off)
+    assert (U[0], O[0]) == (7.0, 0.0)           # ceil(4) + 3 - 10 < 0 -> U = 10 - 3
+    assert 3 + U[0] == 10 + O[0]
+    Up, Op = oracle.masses(1, 0.4, I_off, J_off)  # per angle: (6, 2) and (4, 1)
+    np.testing.assert_array_equal(Up, [4.0, 3.0])
+    np.testing.assert_array_equal(Op, [0.0, 0.0])
+    Uq, Oq = oracle.masses(0, 0.4, [0, 8], [0, 5])  # the ordinary branch
+    assert (Uq[0], Oq[0]) == (2.0, 5.0)
+    rng = np.random.default_rng(3)
+    p = np.c_[rng.uniform(-20, 20, (3, 2)), -200 * np.ones(3)]
+    c = rng.uniform(-1, 1, (10, 3))
+    r = np.c_[rng.normal(size=(10, 2)) * 0.05, -np.ones(10)]
+    r /= np.linalg.norm(r, axis=1, keepdims=True)
+    for mode in (0, 1):
+        f, g, fd, gd, it = oracle.sinkhorn(200.0, p, I_off, J_off, c, r, 50.0, 2.25, mode, 0.4, 20000, 1e-13)
+        h = oracle.harvest(200.0, p, I_off, J_off, c, r, 50.0, 2.25, mode, 0.4, f, g, fd, gd)
+        assert h["row_err"] < 1e-10 and h["col_err"] < 1e-10
+        assert np.all(h["assign"] >= 0)  # the outlier column has no mass to take
+
+
+def test_refresh_equals_forward_at_the_same_pose(tiny):
+    """Refreshing a frozen list (§"Assignments with outlier and missing spots")
+    gives the forward model's rays, wavelengths and centres for every spot of the
+    list, both at the pose that made the list and at a new pose (for the spots the
+    forward model also lists there)."""
+    P, fw, om = tiny["planes"], tiny["fw"], tiny["om"]
+    R, x = tiny["R"], tiny["x"]
+    ray, ce = oracle.refresh(GEOM, P, R, x, om, fw["J_off"], fw["grain"], fw["plane"])
+    np.testing.assert_allclose(ray, fw["ray"], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(ce, fw["center"], rtol=0, atol=1e-13)
+    rng = np.random.default_rng(4)
+    R2 = np.array([_rotvec(rng.normal(size=3) * 0.01) @ a for a in R])
+    x2 = x + rng.normal(size=x.shape) * 0.2
+    ray2, ce2 = oracle.refresh(GEOM, P, R2, x2, om, fw["J_off"], fw["grain"], fw["plane"])
+    fw2 = oracle.forward(GEOM, P, R2, x2, om)
+    key2 = {(t, n, m): j for j, (t, n, m) in enumerate(zip(fw2["t"], fw2["grain"], fw2["plane"]))}
+    hits = 0
+    for j, k in enumerate(zip(fw["t"], fw["grain"], fw["plane"])):
+        if k in key2:
+            hits += 1
+            np.testing.assert_allclose(ray2[j], fw2["ray"][key2[k]], rtol=0, atol=1e-13)
+            np.testing.assert_allclose(ce2[j], fw2["center"][key2[k]], rtol=0, atol=1e-13)
+    assert hits > 0.8 * len(fw["t"])

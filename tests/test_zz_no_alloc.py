@@ -1,5 +1,5 @@
 """The no-allocation E-step (laue_cost_sinkhorn_noalloc) against the
-workspace-based laue_cost_sinkhorn.
+workspace-based laue_cost_sinkhorn and against the FP64 oracle.
 
 The no-allocation variant exists for callers that cannot allocate device
 memory (code running under stream capture, real-time loops, plugins whose
@@ -9,6 +9,7 @@ run stopping at the first failure has run every other test first."""
 import numpy as np
 import pytest
 
+import oracle
 import synthgen as sg
 from _cases import GEOM, make_case, to_device
 
@@ -29,6 +30,12 @@ def test_no_alloc_matches_workspace_entry_point_twice():
     h = api.Handle(dev)
     ref = api.cost_sinkhorn(h, GEOM, ob, ms, eps, case.c_out, n_iter, harvest=True, col_harvest=True)
     torch.cuda.synchronize()
+    fw, obs = case.fw, case.obs
+    of, og, ofd, ogd, _ = oracle.sinkhorn(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3],
+                                          eps, case.c_out, 0, 0.4, n_iter)
+    oh = oracle.harvest(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3], eps, case.c_out,
+                        0, 0.4, of, og, ofd, ogd)
+    orc = dict(f=of, g=og, dust=np.concatenate([ofd, ogd]))
     nI, nJ = int(ob.p.shape[0]), ms.n
     for call in range(2):
         f = torch.full((nI,), float("nan"), device=dev)
@@ -49,6 +56,13 @@ def test_no_alloc_matches_workspace_entry_point_twice():
             d = np.abs(got.double().cpu().numpy() - r)
             assert np.all(d <= TOL * (np.abs(r) + eps)), (call, name, float(d.max()))
         np.testing.assert_array_equal(assign.cpu().numpy(), ref["assign"].cpu().numpy())
+        # and against the oracle itself
+        for name, got in (("f", f), ("g", g), ("dust", dust)):
+            r = orc[name]
+            d = np.abs(got.double().cpu().numpy() - r)
+            assert np.all(d <= TOL * (np.abs(r) + eps)), (call, "oracle", name, float(d.max()))
+        sure = oh["margin"] > 1e-3
+        np.testing.assert_array_equal(assign.cpu().numpy()[sure], oh["assign"][sure])
         np.testing.assert_allclose(margin.cpu().numpy(), ref["margin"].cpu().numpy(), atol=1e-4)
         np.testing.assert_allclose(q.cpu().numpy(), ref["q"].cpu().numpy(), atol=1e-4)
 
