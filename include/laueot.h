@@ -113,7 +113,13 @@ typedef struct {
  * plus an outlier column of mass O = U + |I| - |J| (when O < 0, U = |J| - |I|
  * and O = 0).  Costs: C_ij pair cost, C_i0 = c_out, C_0j = 0, C_00 = c_out.
  * dust_mode 0: one dustbin row/column for all angles; 1: one per angle
- * (masses computed per angle block). */
+ * (masses computed per angle block); 2: unbalanced OT (Appendix "Optimal
+ * transport variants", Problem (B), Algorithm UnbalancedOT): no dustbins, the
+ * marginals relaxed by generalised KL terms of weights kappa (observed rows)
+ * and lambda (model columns), i.e. each log-domain update of f (g) is the
+ * balanced one scaled by kappa / (kappa + eps) (lambda / (lambda + eps)).  In
+ * that mode c_out and unmatched_frac are unused, dust is not written, and the
+ * hard assignment of a row whose plan mass is below 1/2 is -1. */
 typedef struct {
     double unmatched_frac;
     float eps;
@@ -121,6 +127,8 @@ typedef struct {
     int n_iter;
     int dust_mode;
     int warm_start; /* nonzero: f, g, dust hold the starting potentials */
+    float kappa;    /* dust_mode 2: weight of the observed-row marginal KL term (mm^2) */
+    float lambda;   /* dust_mode 2: weight of the model-column marginal KL term (mm^2) */
     int pad_;
 } LaueOTParams;
 
@@ -302,6 +310,13 @@ int laue_autotune(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* 
                   const LaueModelSpots* model, const LaueOTParams* prm, int n_iter, int* choice_host,
                   float* ms_host, void* stream);
 
+/* Diagnostic of laue_cost_sinkhorn (no counterpart in the paper): the number
+ * of row and column log-sum-exps that the pair passes recomputed on the exact
+ * (running-maximum) path because their fast sum, shifted by the angle block's
+ * largest potential, fell below 1e-30, since the last call (modulo 2^32);
+ * the counts are cleared.  Synchronises `stream`. */
+int laue_exact_lse_count(laue_handle* h, void* stream, long long* rows_host, long long* cols_host);
+
 /* Sets the launch shapes (0..3, as for laue_autotune) of the row and column
  * passes used by later calls on the handle; shape 0 is the default. */
 int laue_set_launch_shape(laue_handle* h, int row_shape, int col_shape);
@@ -317,6 +332,28 @@ int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
                const LaueObsSpots* obs, const LaueModelSpots* model, const float* f,
                const float* g, const LaueMParams* prm, const float* omega, float* R, float* x,
                int N, float* step_norms, void* stream);
+
+/* Adjoint M-step (an addition beside Section "The M-step updates"; the paper's
+ * M-step is laue_mstep): per grain, prm->n_newton Levenberg-Marquardt steps on
+ * the OT-weighted spot cost E_n = sum_{j in J_n} sum_i Q_ij C_ij(R_n, x_n),
+ * the plan Q held at the E-step (potentials f, g and the model list's rays and
+ * centres, which must be those of the E-step), over theta = (phi, x) with
+ * R <- exp([phi]x) R.  Each step runs the adjoint pair pass at the current
+ * pose (the gradient of laue_objective_grad, costs recomputed, never stored)
+ * together with the sums q_j = sum_i Q_ij, s1_j = sum_i Q_ij / tau_ij and
+ * s2_j = sum_i Q_ij / tau_ij^2; the Gauss-Newton matrix takes each spot's
+ * model-ray projector P_j = I - r_j r_j^T:
+ *   H = 2 D^2 sum_j [[q A^T A, s1 A^T P Gamma], [s1 Gamma^T P A, s2 Gamma^T P Gamma]],
+ *   A_j = dr_j/dphi = 2 (u e^T + (u.e) I) Gamma [R w_m]x,  u = Gamma R w_m;
+ * delta = -(H + hreg diag(H))^-1 grad (Cholesky; a grain whose damped matrix
+ * is not positive definite keeps its pose), R <- exp([delta_phi]x) R,
+ * x <- x + delta_x.  prm->n_mm, tol_x and tol_R are not used.  R (N x 9),
+ * x (N x 3) are updated in place; step_norms (optional, N x 2): last
+ * |delta_x| and |delta_phi|.  Asynchronous. */
+int laue_mstep_adjoint(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                       const LaueObsSpots* obs, const LaueModelSpots* model, const float* f,
+                       const float* g, const LaueMParams* prm, const float* omega, float* R, float* x,
+                       int N, float* step_norms, void* stream);
 
 /* Gradient of the OT-weighted spot cost E_n = sum_{j in J_n} sum_i Q_ij C_ij
  * with Q held at the plan of potentials (f, g) and the current costs
@@ -345,6 +382,25 @@ int laue_axis_angle(laue_handle* h, const float* w, const float* R0, float* R, f
  * Asynchronous. */
 int laue_axis_angle_vjp(laue_handle* h, const float* w, const float* grad, const float* gout, float* gw,
                         float* gx, int N, void* stream);
+
+/* Start grid of the single-grain fits (paper Section "Single-grain fitting":
+ * quasi-uniform starts over orientations and positions, the orientations
+ * restricted by the crystal symmetry).  The paper's Sobol sequence over
+ * modified Rodrigues parameters is read as the super-Fibonacci spiral of
+ * Alexa (CVPR 2022): n_full unit quaternions q_i (s = i + 1/2,
+ * q = (sqrt(s/n) sin(2 pi s/sqrt 2), sqrt(s/n) cos(2 pi s/sqrt 2),
+ *      sqrt(1 - s/n) sin(2 pi s/psi), sqrt(1 - s/n) cos(2 pi s/psi)),
+ * psi^4 = psi + 4).  sym = 24 keeps, in spiral order, the points of the cubic
+ * fundamental zone (scalar part the largest |<q, g>| over the cubic group);
+ * sym = 1 keeps every point.  Each kept orientation is paired with the k^3
+ * cell centres of the cube of side cube_mm centred at the origin (first
+ * coordinate slowest): start s = o k^3 + p.  Writes min(S, cap) starts
+ * (R_out cap x 9 row-major, x_out cap x 3; device) and *S_host = S (cap = 0
+ * only counts).  Synchronises `stream`.  Needs a workspace of at least
+ * 4.5 KiB + 4 (n_full / 1024 + 1) bytes.  Errors: LAUE_ERR_INVALID_ARG (sym
+ * not 1 or 24, k outside 1..64, n_full < 0), LAUE_ERR_WORKSPACE. */
+int laue_start_grid(laue_handle* h, long long n_full, int sym, int k, float cube_mm, long long cap, float* R_out,
+                    float* x_out, long long* S_host, void* stream);
 
 /* Batched single-grain fitting (paper Section "Single-grain fitting",
  * Appendix "Single-grain fitting", Eq. elbo_single, Algorithm SingleLaueOT)
@@ -387,12 +443,17 @@ int laue_prototype_select(laue_handle* h, const LaueGeometry* geom, const LaueLa
 
 /* End-to-end indexing (paper Algorithm LaueOT preceded by the pre-processing
  * of Section "Pre-processing"): batched single-grain fits from the S starts
- * (startR S x 9, startX S x 3) with k_single annealed steps and the f_out
- * filter (laue_single_fit); SPOT selection over the kept fits at eps_final
+ * (startR S x 9, startX S x 3), or, with startR = startX = NULL, from the
+ * library's start grid (laue_start_grid with grid_n, grid_sym, grid_k,
+ * grid_cube; S must then be at least the grid's start count), with k_single
+ * annealed steps (from anneal_single eps_final, re-listing the visible spots
+ * every step when recut_single is set) and the f_out filter
+ * (laue_single_fit); SPOT selection over the kept fits at eps_final
  * with k_max = min(#kept, n_max) (laue_prototype_select); the model list of
  * the k* prototypes (laue_forward); n_em annealed EM steps (eps from
  * 100 eps_final down to eps_final at step ceil(0.75 n_em), n_sinkhorn
- * iterations each, then laue_mstep) and a final E-step at eps_final.
+ * iterations each, then laue_mstep, or laue_mstep_adjoint with mstep_kind = 1)
+ * and a final E-step at eps_final.
  * Outputs: R_out / x_out (capacity n_max grains), *n_grains_host = k*, and
  * assign (obs->n): the grain of each observed spot's argmax model spot, -1
  * for the outlier column.  Needs laue_index_workspace_size bytes.
@@ -407,6 +468,13 @@ typedef struct {
     int k_single; /* annealed steps of each single-grain fit */
     int dust_mode;
     LaueMParams mstep;
+    float anneal_single; /* eps_init / eps_final of the single-grain fits (<= 0: 100) */
+    int recut_single;    /* nonzero: the fits re-list visible spots every step */
+    long long grid_n;    /* start grid (used when startR is NULL): spiral points */
+    int grid_sym;        /* 1 or 24 (cubic fundamental zone) */
+    int grid_k;          /* k^3 positions per orientation */
+    float grid_cube;     /* side of the sample cube (mm) */
+    int mstep_kind;      /* 0: laue_mstep (Newton on x, MM on R); 1: laue_mstep_adjoint */
 } LaueIndexParams;
 
 int laue_index_workspace_size(laue_handle* h, int T, int n_obs, int S, int n_max, int n_planes,

@@ -47,6 +47,7 @@ def lib():
             L.orc_pair_cost.restype = ctypes.c_double
             L.orc_eps_schedule.restype = ctypes.c_double
             L.orc_eps_schedule_f.restype = ctypes.c_double
+            L.orc_start_grid.restype = ctypes.c_long
             _lib = L
     return _lib
 
@@ -206,8 +207,9 @@ def eps_schedule(eps_final, n_em, k, factor=100.0):
 
 
 def em(geom, planes, omega, p, I_off, J_off, grain, plane, R, x, eps_final, n_em, n_sinkhorn,
-       c_out, mode=0, frac=0.4, n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3):
-    """Algorithm LaueOT with a fixed number of EM steps; returns dict."""
+       c_out, mode=0, frac=0.4, n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, mstep="plain"):
+    """Algorithm LaueOT with a fixed number of EM steps; returns dict.  mstep
+    "adjoint" takes the damped Gauss-Newton M-step (hreg its damping)."""
     L = lib()
     R = _f64(R, (-1, 9)).copy(); x = _f64(x, (-1, 3)).copy()
     N = len(R); omega = _f64(omega); T = len(omega)
@@ -218,7 +220,7 @@ def em(geom, planes, omega, p, I_off, J_off, grain, plane, R, x, eps_final, n_em
              _d(omega), T, _i(_i32(I_off)), _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)),
              _i(_i32(plane)), N, _d(R), _d(x), ctypes.c_double(eps_final), n_em, n_sinkhorn,
              ctypes.c_double(c_out), mode, ctypes.c_double(frac), n_newton, n_mm,
-             ctypes.c_double(tol_x), ctypes.c_double(tol_R), ctypes.c_double(hreg),
+             ctypes.c_double(tol_x), ctypes.c_double(tol_R), ctypes.c_double(hreg), 1 if mstep == "adjoint" else 0,
              _d(f), _d(g), _d(fd), _d(gd), _i(assign), _d(margin))
     return dict(R=R.reshape(-1, 3, 3), x=x, f=f, g=g, fd=fd, gd=gd, assign=assign, margin=margin)
 
@@ -308,3 +310,67 @@ def gamma(omega):
     G = np.zeros(9)
     lib().orc_gamma(ctypes.c_double(omega), _d(G))
     return G.reshape(3, 3)
+
+
+def start_grid(n_full, sym=24, k=1, cube=5.0):
+    """Start grid of the single-grain fits: super-Fibonacci orientations
+    (restricted to the cubic fundamental zone when sym = 24) x k^3 cell
+    centres of the sample cube.  Returns (R (S, 3, 3), x (S, 3))."""
+    L = lib()
+    n = L.orc_start_grid(ctypes.c_long(n_full), sym, k, ctypes.c_double(cube), ctypes.c_long(0), None, None)
+    R = np.zeros((max(n, 1), 9)); x = np.zeros((max(n, 1), 3))
+    L.orc_start_grid(ctypes.c_long(n_full), sym, k, ctypes.c_double(cube), ctypes.c_long(n), _d(R), _d(x))
+    return R[:n].reshape(-1, 3, 3), x[:n]
+
+
+def grain_gn(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps, R, x):
+    """Gradient (N, 6), Gauss-Newton matrix (N, 6, 6) and value (N,) of the
+    OT-weighted cost at the pose (R, x), Q held at the E-step plan."""
+    L = lib()
+    R = _f64(R, (-1, 9)); x = _f64(x, (-1, 3))
+    N = len(R)
+    grad = np.zeros((N, 6)); H = np.zeros((N, 36)); val = np.zeros(N)
+    L.orc_grain_gn(_d(pack_geom(geom)), _d(_f64(planes.w)), _d(_f64(omega)), len(omega), _i(_i32(I_off)),
+                   _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)), _i(_i32(plane)), N,
+                   _d(_f64(cE, (-1, 3))), _d(_f64(rE, (-1, 3))), _d(_f64(f)), _d(_f64(g)), ctypes.c_double(eps),
+                   _d(R), _d(x), _d(grad), _d(H), _d(val))
+    return grad, H.reshape(-1, 6, 6), val
+
+
+def mstep_adjoint(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps, R, x, n_steps=4,
+                  lam=1e-3):
+    """Adjoint M-step (damped Gauss-Newton with Q held); returns (R, x, step_norms)."""
+    L = lib()
+    R = _f64(R, (-1, 9)).copy(); x = _f64(x, (-1, 3)).copy()
+    N = len(R)
+    norms = np.zeros((N, 2))
+    L.orc_mstep_adjoint(_d(pack_geom(geom)), _d(_f64(planes.w)), _d(_f64(omega)), len(omega), _i(_i32(I_off)),
+                        _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)), _i(_i32(plane)), N,
+                        _d(_f64(cE, (-1, 3))), _d(_f64(rE, (-1, 3))), _d(_f64(f)), _d(_f64(g)), ctypes.c_double(eps),
+                        n_steps, ctypes.c_double(lam), _d(R), _d(x), _d(norms))
+    return R.reshape(-1, 3, 3), x, norms
+
+
+def sinkhorn_unbalanced(D, p, I_off, J_off, c, r, eps, kappa, lam, n_iter=100):
+    """Algorithm UnbalancedOT (log domain, no dustbins); returns (f, g)."""
+    p = _f64(p, (-1, 3)); c = _f64(c, (-1, 3)); r = _f64(r, (-1, 3))
+    I_off = _i32(I_off); J_off = _i32(J_off)
+    T = len(I_off) - 1
+    f = np.zeros(int(I_off[-1])); g = np.zeros(int(J_off[-1]))
+    lib().orc_sinkhorn_unbalanced(ctypes.c_double(D), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
+                                  ctypes.c_double(eps), ctypes.c_double(kappa), ctypes.c_double(lam), n_iter,
+                                  _d(f), _d(g))
+    return f, g
+
+
+def harvest_unbalanced(D, p, I_off, J_off, c, r, eps, f, g):
+    """(assign, margin, row mass, column mass q) of the unbalanced plan."""
+    p = _f64(p, (-1, 3)); c = _f64(c, (-1, 3)); r = _f64(r, (-1, 3))
+    I_off = _i32(I_off); J_off = _i32(J_off)
+    T = len(I_off) - 1
+    nI, nJ = int(I_off[-1]), int(J_off[-1])
+    assign = np.zeros(nI, np.int32); margin = np.zeros(nI); rows = np.zeros(nI); q = np.zeros(nJ)
+    lib().orc_harvest_unbalanced(ctypes.c_double(D), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
+                                 ctypes.c_double(eps), _d(_f64(f)), _d(_f64(g)), _i(assign), _d(margin), _d(rows),
+                                 _d(q))
+    return dict(assign=assign, margin=margin, rowmass=rows, q=q)

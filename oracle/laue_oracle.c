@@ -960,7 +960,7 @@ int orc_em(const double* geom, const double* w, const double* d0, const int* nha
            const int* J_off, const int* grain, const int* plane, int N,
            double* R, double* x, double eps_final, int n_em, int n_sinkhorn,
            double c_out, int mode, double frac, int n_newton, int n_mm,
-           double tol_x, double tol_R, double hreg,
+           double tol_x, double tol_R, double hreg, int mstep_kind,
            double* f, double* g, double* fd, double* gd, int* assign, double* margin) {
     geom_t G;
     geom_unpack(geom, &G);
@@ -980,8 +980,12 @@ int orc_em(const double* geom, const double* w, const double* d0, const int* nha
                         assign, margin, NULL, NULL, NULL);
             break;
         }
-        orc_mstep(geom, w, omega, T, I_off, p, J_off, grain, plane, N, c3, r3, f, g, eps,
-                  n_newton, n_mm, tol_x, tol_R, hreg, R, x, NULL);
+        if (mstep_kind == 1)  /* the adjoint M-step; hreg is its damping */
+            orc_mstep_adjoint(geom, w, omega, T, I_off, p, J_off, grain, plane, N, c3, r3, f, g, eps,
+                              n_newton, hreg, R, x, NULL);
+        else
+            orc_mstep(geom, w, omega, T, I_off, p, J_off, grain, plane, N, c3, r3, f, g, eps,
+                      n_newton, n_mm, tol_x, tol_R, hreg, R, x, NULL);
     }
     free(ray4); free(c3); free(r3);
     return 0;
@@ -1308,4 +1312,351 @@ void orc_grain_grad(const double* geom, const double* w, const double* omega, in
             }
         }
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Start grid of the single-grain fits                                         */
+/* ------------------------------------------------------------------------- */
+
+/* The 24 rotations of the cubic point group as unit quaternions (w, x, y, z):
+ * the identity, 90-degree turns about the cube axes (6), 180-degree turns
+ * about the cube axes (3) and the face diagonals (6), 120-degree turns about
+ * the body diagonals (8). */
+static void cubic_group(double g[24][4]) {
+    int k = 0;
+    const double s = sqrt(0.5);
+    g[k][0] = 1.0; g[k][1] = g[k][2] = g[k][3] = 0.0; ++k;
+    for (int a = 1; a <= 3; ++a) {
+        for (int sg = -1; sg <= 1; sg += 2) {
+            g[k][0] = s; g[k][1] = g[k][2] = g[k][3] = 0.0; g[k][a] = sg * s; ++k;
+        }
+        g[k][0] = g[k][1] = g[k][2] = g[k][3] = 0.0; g[k][a] = 1.0; ++k;
+    }
+    for (int a = 1; a <= 3; ++a)
+        for (int b = a + 1; b <= 3; ++b)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                g[k][0] = g[k][1] = g[k][2] = g[k][3] = 0.0; g[k][a] = s; g[k][b] = sg * s; ++k;
+            }
+    for (int m = 0; m < 8; ++m) {
+        g[k][0] = 0.5;
+        g[k][1] = (m & 1) ? -0.5 : 0.5;
+        g[k][2] = (m & 2) ? -0.5 : 0.5;
+        g[k][3] = (m & 4) ? -0.5 : 0.5;
+        ++k;
+    }
+}
+
+/* Section "Single-grain fitting" starts the fits from a quasi-uniform grid over
+ * orientations and positions, restricted by the lattice symmetry.  Reading
+ * (the paper uses a Sobol sequence over modified Rodrigues parameters): the
+ * super-Fibonacci spiral of Alexa (CVPR 2022) gives n_full quasi-uniform unit
+ * quaternions q_i, i = 0..n_full-1, with s = i + 1/2,
+ *   q = (sqrt(s/n) sin(2 pi s/phi), sqrt(s/n) cos(2 pi s/phi),
+ *        sqrt(1-s/n) sin(2 pi s/psi), sqrt(1-s/n) cos(2 pi s/psi)),
+ * phi = sqrt 2 and psi the real root of psi^4 = psi + 4.  With sym = 24 only
+ * the q whose scalar part is the largest |<q, g>| over the cubic group (q
+ * itself is the member of its symmetry class nearest the identity: the
+ * fundamental zone) are kept, in order.  Each kept orientation is paired with
+ * the k^3 cell centres of the cube of side `cube` centred at the origin
+ * ((a + 1/2) cube/k - cube/2 per axis, x slowest).  Writes at most cap starts
+ * (R row-major 3x3, x) and returns the number of starts. */
+long orc_start_grid(long n_full, int sym, int k, double cube, long cap, double* R_out, double* x_out) {
+    double G[24][4];
+    cubic_group(G);
+    const double phi = sqrt(2.0), psi = 1.533751168755204288118041;
+    const double two_pi = 6.283185307179586476925287;
+    long n_kept = 0, S = 0;
+    long kk = (long)k * k * k;
+    for (long i = 0; i < n_full; ++i) {
+        double s = (double)i + 0.5;
+        double r = sqrt(s / (double)n_full), rr = sqrt(1.0 - s / (double)n_full);
+        double q[4] = {r * sin(two_pi * s / phi), r * cos(two_pi * s / phi), rr * sin(two_pi * s / psi),
+                       rr * cos(two_pi * s / psi)};
+        if (sym == 24) {
+            double id = fabs(q[0]);
+            int inside = 1;
+            for (int g = 1; g < 24; ++g) {
+                double d = fabs(q[0] * G[g][0] + q[1] * G[g][1] + q[2] * G[g][2] + q[3] * G[g][3]);
+                if (d > id) { inside = 0; break; }
+            }
+            if (!inside) continue;
+        }
+        ++n_kept;
+        double w = q[0], x = q[1], y = q[2], z = q[3];
+        double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                       2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                       2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+        for (long p = 0; p < kk; ++p, ++S) {
+            if (S >= cap) continue;
+            long a = p / ((long)k * k), b = (p / k) % k, c = p % k;
+            for (int e = 0; e < 9; ++e) R_out[9 * S + e] = R[e];
+            x_out[3 * S + 0] = (a + 0.5) * cube / k - cube / 2;
+            x_out[3 * S + 1] = (b + 0.5) * cube / k - cube / 2;
+            x_out[3 * S + 2] = (c + 0.5) * cube / k - cube / 2;
+        }
+    }
+    (void)n_kept;
+    return S;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Adjoint M-step: damped Gauss-Newton on the OT-weighted spot cost            */
+/* ------------------------------------------------------------------------- */
+
+/* Exact gradient and Gauss-Newton matrix of E_n = sum_{j in J_n} sum_i Q_ij
+ * C_ij(R, x) at the current pose, Q held at the E-step plan (potentials f, g,
+ * costs of the E-step geometry cE, rE), for the perturbation theta = (phi, x),
+ * R <- exp([phi]x) R.  With e_ij = rhat_ij - r_j and C = D^2 |e|^2:
+ *   dE/dtheta = sum Q 2 D^2 e^T J_ij,  J_ij = [-A_j, -P_ij Gamma / tau_ij],
+ *   A_j = dr_j/dphi = 2 (u e^T + (u.e) I) Gamma [v]x,  v = R w_m, u = Gamma v,
+ *   P_ij = I - rhat rhat^T,  tau_ij = |p_i - c_j|.
+ * The Gauss-Newton matrix 2 D^2 sum Q J^T J is taken with P_ij replaced by
+ * the model ray's projector I - r_j r_j^T (exact where rhat = r):
+ *   H_phiphi = 2 D^2 q_j A^T A,  H_phix = 2 D^2 s1_j A^T P_j Gamma,
+ *   H_xx = 2 D^2 s2_j Gamma^T P_j Gamma,
+ * q_j = sum_i Q_ij, s1_j = sum_i Q_ij / tau_ij, s2_j = sum_i Q_ij / tau_ij^2.
+ * grad: N x 6, H: N x 36 (row-major), value: N (optional). */
+void orc_grain_gn(const double* geom, const double* w, const double* omega, int T,
+                  const int* I_off, const double* p, const int* J_off,
+                  const int* grain, const int* plane, int N,
+                  const double* cE, const double* rE, const double* f, const double* g, double eps,
+                  const double* R, const double* x, double* grad, double* H, double* value) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    double D2 = G.D * G.D;
+    for (int k = 0; k < 6 * N; ++k) grad[k] = 0.0;
+    for (int k = 0; k < 36 * N; ++k) H[k] = 0.0;
+    if (value) for (int n = 0; n < N; ++n) value[n] = 0.0;
+    for (int t = 0; t < T; ++t) {
+        double Gam[9];
+        orc_gamma(omega[t], Gam);
+        for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+            int n = grain[j], m = plane[j];
+            double v[3], u[3], c[3], r[3];
+            mat_vec(R + 9 * n, w + 3 * m, v);
+            mat_vec(Gam, v, u);
+            mat_vec(Gam, x + 3 * n, c);
+            double ue = dot3(u, G.e);
+            for (int a = 0; a < 3; ++a) r[a] = G.e[a] - 2.0 * ue * u[a];
+            /* A = 2 (u e^T + (u.e) I) Gamma [v]x */
+            double B[9], Vx[9] = {0, -v[2], v[1], v[2], 0, -v[0], -v[1], v[0], 0}, GV[9], A[9];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) B[3 * a + b] = 2.0 * (u[a] * G.e[b] + (a == b ? ue : 0.0));
+            mat_mul(Gam, Vx, GV);
+            mat_mul(B, GV, A);
+            double gc[3] = {0, 0, 0}, ge[3] = {0, 0, 0}, q = 0.0, s1 = 0.0, s2 = 0.0, val = 0.0;
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                double CE = orc_pair_cost(p + 3 * i, cE + 3 * j, rE + 3 * j, G.D);
+                double Q = exp((f[i] + g[j] - CE) / eps);
+                if (Q == 0.0) continue;
+                double d[3] = {p[3 * i] - c[0], p[3 * i + 1] - c[1], p[3 * i + 2] - c[2]};
+                double tau = sqrt(dot3(d, d));
+                double rh[3] = {d[0] / tau, d[1] / tau, d[2] / tau};
+                double e[3] = {rh[0] - r[0], rh[1] - r[1], rh[2] - r[2]};
+                double ee = dot3(e, rh);
+                /* dC/dx = 2 D^2 e^T (-P Gamma / tau): accumulate -P e / tau in the lab frame */
+                for (int a = 0; a < 3; ++a) {
+                    gc[a] += Q * (-(e[a] - ee * rh[a]) / tau);
+                    ge[a] += Q * e[a];
+                }
+                q += Q;
+                s1 += Q / tau;
+                s2 += Q / (tau * tau);
+                val += Q * D2 * dot3(e, e);
+            }
+            double gx[3], gphi[3], tmp[3];
+            matT_vec(Gam, gc, gx);
+            /* dC/dphi = 2 D^2 e^T (-A) */
+            for (int b = 0; b < 3; ++b) {
+                tmp[b] = 0.0;
+                for (int a = 0; a < 3; ++a) tmp[b] -= A[3 * a + b] * ge[a];
+            }
+            for (int a = 0; a < 3; ++a) {
+                gphi[a] = 2.0 * D2 * tmp[a];
+                grad[6 * n + a] += gphi[a];
+                grad[6 * n + 3 + a] += 2.0 * D2 * gx[a];
+            }
+            if (value) value[n] += val;
+            /* Gauss-Newton blocks with P_j = I - r r^T */
+            double P[9], PG[9], GtPG[9], AtPG[9], AtA[9];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) P[3 * a + b] = (a == b ? 1.0 : 0.0) - r[a] * r[b];
+            mat_mul(P, Gam, PG);
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double s_gpg = 0.0, s_apg = 0.0, s_aa = 0.0;
+                    for (int k = 0; k < 3; ++k) {
+                        s_gpg += Gam[3 * k + a] * PG[3 * k + b];
+                        s_apg += A[3 * k + a] * PG[3 * k + b];
+                        s_aa += A[3 * k + a] * A[3 * k + b];
+                    }
+                    GtPG[3 * a + b] = s_gpg;
+                    AtPG[3 * a + b] = s_apg;
+                    AtA[3 * a + b] = s_aa;
+                }
+            double* Hn = H + 36 * n;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    Hn[6 * a + b] += 2.0 * D2 * q * AtA[3 * a + b];
+                    Hn[6 * a + 3 + b] += 2.0 * D2 * s1 * AtPG[3 * a + b];
+                    Hn[6 * (3 + b) + a] += 2.0 * D2 * s1 * AtPG[3 * a + b];
+                    Hn[6 * (3 + a) + 3 + b] += 2.0 * D2 * s2 * GtPG[3 * a + b];
+                }
+        }
+    }
+}
+
+/* Solves the n x n system A y = b by Gaussian elimination with partial
+ * pivoting (A and b are overwritten); returns 0 when a pivot vanishes. */
+static int solve_gauss(double* A, double* b, int n, double* y) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[n * r + c]) > fabs(A[n * piv + c])) piv = r;
+        if (A[n * piv + c] == 0.0) return 0;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) {
+                double tmp = A[n * c + k];
+                A[n * c + k] = A[n * piv + k];
+                A[n * piv + k] = tmp;
+            }
+            double tb = b[c];
+            b[c] = b[piv];
+            b[piv] = tb;
+        }
+        for (int r = c + 1; r < n; ++r) {
+            double fct = A[n * r + c] / A[n * c + c];
+            for (int k = c; k < n; ++k) A[n * r + k] -= fct * A[n * c + k];
+            b[r] -= fct * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double acc = b[r];
+        for (int k = r + 1; k < n; ++k) acc -= A[n * r + k] * y[k];
+        y[r] = acc / A[n * r + r];
+    }
+    return 1;
+}
+
+/* exp([phi]x) by Rodrigues' formula */
+static void rotvec_mat(const double phi[3], double E[9]) {
+    double th = sqrt(dot3(phi, phi));
+    double K[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0}, K2[9];
+    mat_mul(K, K, K2);
+    double a = th > 0 ? sin(th) / th : 1.0, b = th > 0 ? (1.0 - cos(th)) / (th * th) : 0.5;
+    for (int k = 0; k < 9; ++k) E[k] = (k % 4 == 0 ? 1.0 : 0.0) + a * K[k] + b * K2[k];
+}
+
+/* Adjoint M-step (an addition beside Section "The M-step updates"): n_steps
+ * Levenberg-Marquardt steps per grain on E_n with Q held at the E-step plan,
+ *   delta = -(H + lambda diag(H))^-1 grad,  R <- exp([delta_phi]x) R,
+ *   x <- x + delta_x,
+ * from orc_grain_gn at the pose of each step.  A grain whose system is
+ * singular keeps its pose.  step_norms (optional, N x 2): last |delta_x| and
+ * |delta_phi|. */
+void orc_mstep_adjoint(const double* geom, const double* w, const double* omega, int T,
+                       const int* I_off, const double* p, const int* J_off,
+                       const int* grain, const int* plane, int N,
+                       const double* cE, const double* rE, const double* f, const double* g, double eps,
+                       int n_steps, double lambda, double* R, double* x, double* step_norms) {
+    double* grad = (double*)malloc(sizeof(double) * 6 * (N > 0 ? N : 1));
+    double* H = (double*)malloc(sizeof(double) * 36 * (N > 0 ? N : 1));
+    for (int it = 0; it < n_steps; ++it) {
+        orc_grain_gn(geom, w, omega, T, I_off, p, J_off, grain, plane, N, cE, rE, f, g, eps, R, x, grad, H, NULL);
+        for (int n = 0; n < N; ++n) {
+            double A[36], b[6], d[6];
+            for (int k = 0; k < 36; ++k) A[k] = H[36 * n + k];
+            for (int k = 0; k < 6; ++k) {
+                A[7 * k] += lambda * H[36 * n + 7 * k];
+                b[k] = -grad[6 * n + k];
+            }
+            int ok = 1;
+            for (int k = 0; k < 6; ++k) ok &= A[7 * k] > 0.0;
+            if (!ok || !solve_gauss(A, b, 6, d)) continue;
+            double E[9], Rn[9];
+            rotvec_mat(d, E);
+            mat_mul(E, R + 9 * n, Rn);
+            for (int k = 0; k < 9; ++k) R[9 * n + k] = Rn[k];
+            for (int k = 0; k < 3; ++k) x[3 * n + k] += d[3 + k];
+            if (step_norms) {
+                step_norms[2 * n] = sqrt(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+                step_norms[2 * n + 1] = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            }
+        }
+    }
+    free(grad);
+    free(H);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Unbalanced optimal transport (Appendix "Optimal transport variants")        */
+/* ------------------------------------------------------------------------- */
+
+/* Algorithm UnbalancedOT in the log domain on the plain cost matrix (no
+ * dustbins), blocked by angle, from f = g = 0, row update first:
+ *   f_i = tau_a (-eps LSE_j ((g_j - C_ij)/eps)),  tau_a = kappa / (kappa + eps)
+ *   g_j = tau_b (-eps LSE_i ((f_i - C_ij)/eps)),  tau_b = lambda / (lambda + eps)
+ * (log a = log b = 0).  Reading: Problem (B) puts kappa on the row marginal
+ * (Q 1 against a, the observed spots) and lambda on the column marginal (Q^T 1
+ * against b, the model spots); the printed algorithm attaches the exponents the
+ * other way round, and the scaling that solves Problem (B) is used here.  A row
+ * (column) of an angle block with no columns (rows) keeps potential 0. */
+int orc_sinkhorn_unbalanced(double D, int T, const int* I_off, const double* p,
+                            const int* J_off, const double* c, const double* r,
+                            double eps, double kappa, double lambda, int n_iter,
+                            double* f, double* g) {
+    int nI = I_off[T], nJ = J_off[T];
+    double ta = kappa / (kappa + eps), tb = lambda / (lambda + eps);
+    for (int i = 0; i < nI; ++i) f[i] = 0.0;
+    for (int j = 0; j < nJ; ++j) g[j] = 0.0;
+    int big = (nI > nJ ? nI : nJ) + 1;
+    double* buf = (double*)malloc(sizeof(double) * big);
+    for (int it = 0; it < n_iter; ++it) {
+        for (int t = 0; t < T; ++t)
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                int n = 0;
+                for (int j = J_off[t]; j < J_off[t + 1]; ++j)
+                    buf[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                f[i] = n ? -ta * eps * lse(buf, n) : 0.0;
+            }
+        for (int t = 0; t < T; ++t)
+            for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+                int n = 0;
+                for (int i = I_off[t]; i < I_off[t + 1]; ++i)
+                    buf[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                g[j] = n ? -tb * eps * lse(buf, n) : 0.0;
+            }
+    }
+    free(buf);
+    return n_iter;
+}
+
+/* Plan read-out of the unbalanced plan Q_ij = exp((f_i + g_j - C_ij)/eps):
+ * row mass r_i and column mass q_j (optional); assign_i = argmax_j Q_ij (ties
+ * to the lowest index), or -1 when r_i < 1/2 (reading: a spot that keeps less
+ * than half its mass untransported is an outlier); margin = top1 - top2 of
+ * the row's plan entries. */
+void orc_harvest_unbalanced(double D, int T, const int* I_off, const double* p,
+                            const int* J_off, const double* c, const double* r, double eps,
+                            const double* f, const double* g, int* assign, double* margin,
+                            double* rowmass, double* q) {
+    int nJ = J_off[T];
+    if (q) for (int j = 0; j < nJ; ++j) q[j] = 0.0;
+    for (int t = 0; t < T; ++t)
+        for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+            double rs = 0.0, top1 = -1.0, top2 = -1.0;
+            int arg = -1;
+            for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+                double Qij = exp((f[i] + g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps);
+                rs += Qij;
+                if (q) q[j] += Qij;
+                if (Qij > top1) { top2 = top1; top1 = Qij; arg = j; }
+                else if (Qij > top2) top2 = Qij;
+            }
+            if (top1 < 0) top1 = 0.0;
+            if (top2 < 0) top2 = 0.0;
+            if (assign) assign[i] = rs < 0.5 ? -1 : arg;
+            if (margin) margin[i] = top1 - top2;
+            if (rowmass) rowmass[i] = rs;
+        }
 }

@@ -72,7 +72,7 @@ int orc_em(const double* geom, const double* w, const double* d0, const int* nha
            const int* J_off, const int* grain, const int* plane, int N,
            double* R, double* x, double eps_final, int n_em, int n_sinkhorn,
            double c_out, int mode, double frac, int n_newton, int n_mm,
-           double tol_x, double tol_R, double hreg,
+           double tol_x, double tol_R, double hreg, int mstep_kind,
            double* f, double* g, double* fd, double* gd, int* assign, double* margin);
 
 int orc_single_fit(const double* geom, const double* w, const double* d0, const int* nharm, int M,
@@ -109,6 +109,26 @@ void orc_grain_grad(const double* geom, const double* w, const double* omega, in
 void orc_sym3_eig(const double A[9], double evals[3], double evecs[9]);
 void orc_svd3(const double B[9], double U[9], double S[3], double V[9]);
 int  orc_wahba(const double B[9], double R[9]);
+
+void orc_grain_gn(const double* geom, const double* w, const double* omega, int T,
+                  const int* I_off, const double* p, const int* J_off,
+                  const int* grain, const int* plane, int N,
+                  const double* cE, const double* rE, const double* f, const double* g, double eps,
+                  const double* R, const double* x, double* grad, double* H, double* value);
+void orc_mstep_adjoint(const double* geom, const double* w, const double* omega, int T,
+                       const int* I_off, const double* p, const int* J_off,
+                       const int* grain, const int* plane, int N,
+                       const double* cE, const double* rE, const double* f, const double* g, double eps,
+                       int n_steps, double lambda, double* R, double* x, double* step_norms);
+int orc_sinkhorn_unbalanced(double D, int T, const int* I_off, const double* p,
+                            const int* J_off, const double* c, const double* r,
+                            double eps, double kappa, double lambda, int n_iter,
+                            double* f, double* g);
+void orc_harvest_unbalanced(double D, int T, const int* I_off, const double* p,
+                            const int* J_off, const double* c, const double* r, double eps,
+                            const double* f, const double* g, int* assign, double* margin,
+                            double* rowmass, double* q);
+long orc_start_grid(long n_full, int sym, int k, double cube, long cap, double* R_out, double* x_out);
 
 #ifdef __cplusplus
 }

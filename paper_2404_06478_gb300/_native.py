@@ -48,7 +48,7 @@ class LaueModelSpots(ctypes.Structure):
 
 class LaueOTParams(ctypes.Structure):
     _fields_ = [("unmatched_frac", _d), ("eps", _f), ("c_out", _f), ("n_iter", _i), ("dust_mode", _i),
-                ("warm_start", _i), ("pad_", _i)]
+                ("warm_start", _i), ("kappa", _f), ("lambda_", _f), ("pad_", _i)]
 
 
 class LaueMParams(ctypes.Structure):
@@ -67,7 +67,9 @@ class LaueSingleParams(ctypes.Structure):
 
 class LaueIndexParams(ctypes.Structure):
     _fields_ = [("unmatched_frac", _d), ("eps_final", _f), ("c_out", _f), ("f_out", _f), ("n_em", _i),
-                ("n_sinkhorn", _i), ("k_single", _i), ("dust_mode", _i), ("mstep", LaueMParams)]
+                ("n_sinkhorn", _i), ("k_single", _i), ("dust_mode", _i), ("mstep", LaueMParams),
+                ("anneal_single", _f), ("recut_single", _i), ("grid_n", ctypes.c_longlong), ("grid_sym", _i),
+                ("grid_k", _i), ("grid_cube", _f), ("mstep_kind", _i)]
 
 
 _P = ctypes.POINTER
@@ -92,12 +94,16 @@ SIGNATURES = {
     "laue_autotune": [_vp, _P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams), _i, _vp,
                       _vp, _vp],
     "laue_set_launch_shape": [_vp, _i, _i],
+    "laue_exact_lse_count": [_vp, _vp, _P(ctypes.c_longlong), _P(ctypes.c_longlong)],
     "laue_mstep": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots), _vp, _vp,
                    _P(LaueMParams), _vp, _vp, _vp, _i, _vp, _vp],
+    "laue_mstep_adjoint": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots), _vp,
+                           _vp, _P(LaueMParams), _vp, _vp, _vp, _i, _vp, _vp],
     "laue_objective_grad": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots),
                             _vp, _vp, _f, _vp, _vp, _vp, _i, _vp, _vp, _vp],
     "laue_axis_angle": [_vp, _vp, _vp, _vp, _vp, _i, _vp],
     "laue_axis_angle_vjp": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp],
+    "laue_start_grid": [_vp, ctypes.c_longlong, _i, _i, _f, ctypes.c_longlong, _vp, _vp, _P(ctypes.c_longlong), _vp],
     "laue_single_fit": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,
                         _P(LaueSingleParams), _vp, _vp, _vp, _vp, _vp],
     "laue_prototype_select": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _vp, _vp, _i,

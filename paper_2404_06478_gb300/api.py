@@ -229,6 +229,13 @@ class Handle:
     def set_launch_shape(self, row_shape, col_shape):
         self.check(self.L.laue_set_launch_shape(self.h, int(row_shape), int(col_shape)), "set_launch_shape")
 
+    def exact_lse_count(self, stream=None):
+        """(rows, columns) recomputed on the exact log-sum-exp path since the last call."""
+        r, c = ctypes.c_longlong(0), ctypes.c_longlong(0)
+        self.check(self.L.laue_exact_lse_count(self.h, _stream(stream), ctypes.byref(r), ctypes.byref(c)),
+                   "exact_lse_count")
+        return r.value, c.value
+
     def device_status(self, stream=None) -> int:
         v = ctypes.c_int(0)
         self.check(self.L.laue_device_status(self.h, _stream(stream), ctypes.byref(v)), "device_status")
@@ -272,13 +279,15 @@ def refresh(h: Handle, geom, lat: Lattice, R, x, omega, model: ModelSpots, strea
             "laue_refresh")
 
 
-def ot_params(eps, c_out, n_iter, dust_mode=0, unmatched_frac=0.4, warm_start=False):
+def ot_params(eps, c_out, n_iter, dust_mode=0, unmatched_frac=0.4, warm_start=False, kappa=0.0, lam=0.0):
+    """dust_mode 0 / 1: balanced OT with global / per-angle dustbins; 2:
+    unbalanced OT with marginal weights kappa (observed) and lam (model)."""
     return N.LaueOTParams(float(unmatched_frac), float(eps), float(c_out), int(n_iter), int(dust_mode),
-                          1 if warm_start else 0, 0)
+                          1 if warm_start else 0, float(kappa), float(lam), 0)
 
 
 def cost_sinkhorn(h: Handle, geom, obs: ObsSpots, model: ModelSpots, eps, c_out, n_iter, dust_mode=0,
-                  unmatched_frac=0.4, harvest=True, col_harvest=False, init=None, stream=None):
+                  unmatched_frac=0.4, harvest=True, col_harvest=False, init=None, kappa=0.0, lam=0.0, stream=None):
     """laue_cost_sinkhorn; returns dict of device tensors f, g, dust and, with
     harvest, assign, margin, marg_err (and q with col_harvest)."""
     dev = obs.p.device
@@ -297,7 +306,7 @@ def cost_sinkhorn(h: Handle, geom, obs: ObsSpots, model: ModelSpots, eps, c_out,
     margin = torch.empty(max(nI, 1), device=dev) if harvest else None
     merr = torch.empty(2, device=dev) if (harvest or col_harvest) else None
     q = torch.empty(max(nJ, 1), device=dev) if col_harvest else None
-    prm = ot_params(eps, c_out, n_iter, dust_mode, unmatched_frac, init is not None)
+    prm = ot_params(eps, c_out, n_iter, dust_mode, unmatched_frac, init is not None, kappa, lam)
     g_s = geometry_struct(geom)
     o_s = obs.struct()
     m_s = model.struct()
@@ -331,6 +340,20 @@ def mstep(h: Handle, geom, lat: Lattice, obs: ObsSpots, model: ModelSpots, f, g,
     h.check(h.L.laue_mstep(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), ctypes.byref(m_s),
                            _ptr(f), _ptr(g), ctypes.byref(prm), _ptr(omega), _ptr(R), _ptr(x), N_,
                            _ptr(step_norms), _stream(stream)), "laue_mstep")
+
+
+def mstep_adjoint(h: Handle, geom, lat: Lattice, obs: ObsSpots, model: ModelSpots, f, g, eps, omega, R, x,
+                  n_steps=4, lam=1e-3, step_norms=None, stream=None):
+    """laue_mstep_adjoint: damped Gauss-Newton M-step on the OT-weighted cost
+    (plan held at the E-step); updates R ((N, 9) float32) and x ((N, 3)) in place."""
+    N_ = int(x.shape[0])
+    h.reserve(obs.T, n_obs=int(obs.p.shape[0]), n_model=model.n, n_grains=N_,
+              n_planes=int(lat.w_d0.shape[0]), stream=stream)
+    prm = mparams(eps, n_steps, 0, 0.0, 0.0, lam)
+    g_s, o_s, m_s, l_s = geometry_struct(geom), obs.struct(), model.struct(), lat.struct()
+    h.check(h.L.laue_mstep_adjoint(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), ctypes.byref(m_s),
+                                   _ptr(f), _ptr(g), ctypes.byref(prm), _ptr(omega), _ptr(R), _ptr(x), N_,
+                                   _ptr(step_norms), _stream(stream)), "laue_mstep_adjoint")
 
 
 def objective_grad(h: Handle, geom, lat: Lattice, obs: ObsSpots, model: ModelSpots, f, g, eps, omega, R, x,
@@ -368,6 +391,20 @@ def axis_angle_vjp(h: Handle, w, grad, gout=None, stream=None):
     h.check(h.L.laue_axis_angle_vjp(h.h, _ptr(w.contiguous().float()), _ptr(grad.contiguous().float()), _ptr(go),
                                     _ptr(gw), _ptr(gx), N_, _stream(stream)), "laue_axis_angle_vjp")
     return gw[:N_], gx[:N_]
+
+
+def start_grid(h: Handle, n_full: int, sym: int = 24, k: int = 1, cube_mm: float = 5.0, device=None, stream=None):
+    """laue_start_grid: (R (S, 9), x (S, 3)) device tensors of the start grid."""
+    dev = device if device is not None else h.device
+    h.reserve(1, extra=4 * (int(n_full) // 1024 + 1) + 1024, stream=stream)
+    S = ctypes.c_longlong(0)
+    h.check(h.L.laue_start_grid(h.h, int(n_full), int(sym), int(k), float(cube_mm), 0, None, None, ctypes.byref(S),
+                                _stream(stream)), "laue_start_grid")
+    R = torch.empty(max(S.value, 1), 9, device=dev)
+    x = torch.empty(max(S.value, 1), 3, device=dev)
+    h.check(h.L.laue_start_grid(h.h, int(n_full), int(sym), int(k), float(cube_mm), S.value, _ptr(R), _ptr(x),
+                                ctypes.byref(S), _stream(stream)), "laue_start_grid")
+    return R[:S.value], x[:S.value]
 
 
 def single_fit(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, R0, x0, eps_final, k_max, c_out,
@@ -421,12 +458,30 @@ def prototype_select(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, candR,
 
 def index(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, startR, startX, eps_final, c_out, n_max,
           n_em=20, n_sinkhorn=100, k_single=20, f_out=0.1, unmatched_frac=0.4, dust_mode=0, n_newton=4, n_mm=4,
-          tol_x=1e-6, tol_R=1e-9, hreg=1e-3, stream=None):
-    """laue_index: (R (k*, 9), x (k*, 3), assign (n_obs,) grain per observed spot)."""
-    startR = startR.reshape(-1, 9).contiguous().float()
-    startX = startX.reshape(-1, 3).contiguous().float()
-    S = int(startR.shape[0])
-    dev = startR.device
+          tol_x=1e-6, tol_R=1e-9, hreg=1e-3, anneal_single=100.0, recut_single=False, grid=None, mstep="plain",
+          stream=None):
+    """laue_index: (R (k*, 9), x (k*, 3), assign (n_obs,) grain per observed spot).
+
+    Starts: startR (S, 9) / startX (S, 3), or startR = startX = None and
+    grid = dict(n_full, sym, k, cube_mm) for the library's start grid.
+    mstep: "plain" (Newton + MM) or "adjoint" (damped Gauss-Newton on the
+    OT-weighted cost; n_newton steps, hreg the damping)."""
+    g_n, g_sym, g_k, g_cube = 0, 24, 1, 5.0
+    if startR is None:
+        g = {"sym": 24, "k": 1, "cube_mm": 5.0}
+        g.update(grid or {})
+        g_n, g_sym, g_k, g_cube = int(g["n_full"]), int(g["sym"]), int(g["k"]), float(g["cube_mm"])
+        h.reserve(obs.T, extra=4 * (g_n // 1024 + 1) + 1024, stream=stream)
+        Sg = ctypes.c_longlong(0)
+        h.check(h.L.laue_start_grid(h.h, g_n, g_sym, g_k, g_cube, 0, None, None, ctypes.byref(Sg), _stream(stream)),
+                "laue_start_grid")
+        S = int(Sg.value)
+        dev = obs.p.device
+    else:
+        startR = startR.reshape(-1, 9).contiguous().float()
+        startX = startX.reshape(-1, 3).contiguous().float()
+        S = int(startR.shape[0])
+        dev = startR.device
     nI = int(obs.p.shape[0])
     b = ctypes.c_size_t()
     h.check(h.L.laue_index_workspace_size(h.h, obs.T, nI, S, int(n_max), int(lat.w_d0.shape[0]), ctypes.byref(b)),
@@ -437,7 +492,8 @@ def index(h: Handle, geom, lat: Lattice, obs: ObsSpots, omega, startR, startX, e
     assign = torch.empty(max(nI, 1), dtype=torch.int32, device=dev)
     prm = N.LaueIndexParams(float(unmatched_frac), float(eps_final), float(c_out), float(f_out), int(n_em),
                             int(n_sinkhorn), int(k_single), int(dust_mode),
-                            mparams(eps_final, n_newton, n_mm, tol_x, tol_R, hreg))
+                            mparams(eps_final, n_newton, n_mm, tol_x, tol_R, hreg), float(anneal_single),
+                            1 if recut_single else 0, g_n, g_sym, g_k, g_cube, 1 if mstep == "adjoint" else 0)
     ng = ctypes.c_int(0)
     g_s, o_s, l_s = geometry_struct(geom), obs.struct(), lat.struct()
     # The SPOT matrix's size is known only after the fits (its nonzeros per kept

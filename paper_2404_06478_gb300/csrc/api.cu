@@ -363,7 +363,9 @@ int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* o
     a.kc = (float)((double)prm->c_out * 1.4426950408889634 / eps);
     a.frac = prm->unmatched_frac;
     a.to_user = (float)(eps * 0.6931471805599453);
-    a.mode = prm->dust_mode ? 1 : 0;
+    a.mode = prm->dust_mode == 2 ? 2 : (prm->dust_mode ? 1 : 0);
+    a.tau_row = a.mode == 2 ? (float)((double)prm->kappa / ((double)prm->kappa + eps)) : 1.0f;
+    a.tau_col = a.mode == 2 ? (float)((double)prm->lambda / ((double)prm->lambda + eps)) : 1.0f;
     a.warm = prm->warm_start ? 1 : 0;
     *out = a;
     lc->row_variant = h->row_variant;
@@ -387,8 +389,11 @@ extern "C" int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, cons
     if ((rc = laue_check_obs(h, obs))) return rc;
     if ((rc = laue_check_model(h, model))) return rc;
     if (!prm || !(prm->eps > 0.0f) || prm->n_iter < 0 || !(prm->c_out >= 0.0f) ||
-        !(prm->unmatched_frac >= 0.0) || prm->unmatched_frac > 1.0)
-        return laue_fail(h, LAUE_ERR_INVALID_ARG, "OT params: eps > 0, n_iter >= 0, c_out >= 0, 0 <= frac <= 1");
+        !(prm->unmatched_frac >= 0.0) || prm->unmatched_frac > 1.0 || prm->dust_mode < 0 || prm->dust_mode > 2 ||
+        (prm->dust_mode == 2 && (!(prm->kappa > 0.0f) || !(prm->lambda > 0.0f))))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG,
+                         "OT params: eps > 0, n_iter >= 0, c_out >= 0, 0 <= frac <= 1, dust_mode 0..2, kappa and "
+                         "lambda > 0 for the unbalanced mode");
     if (obs->T != model->T) return laue_fail(h, LAUE_ERR_INVALID_ARG, "observed and model T differ");
     if ((obs->n > 0 && !f) || (model->n > 0 && !g))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "f and g outputs are required");
@@ -413,6 +418,24 @@ extern "C" int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, cons
 }
 
 // ------------------------------------------------------------- autotuner
+
+extern "C" int laue_exact_lse_count(laue_handle* h, void* stream, long long* rows_host, long long* cols_host) {
+    if (!h || !rows_host || !cols_host) return LAUE_ERR_INVALID_ARG;
+    if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned v[2] = {0u, 0u};
+    int* ctrl = (int*)h->ws;
+    int rc;
+    if ((rc = laue_cuda_check(h, cudaMemcpyAsync(v, ctrl + CTRL_EXACT_ROWS, sizeof(v), cudaMemcpyDeviceToHost, s),
+                              "reading counts")))
+        return rc;
+    if ((rc = laue_cuda_check(h, cudaMemsetAsync(ctrl + CTRL_EXACT_ROWS, 0, sizeof(v), s), "clearing counts")))
+        return rc;
+    if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "synchronise"))) return rc;
+    *rows_host = v[0];
+    *cols_host = v[1];
+    return LAUE_OK;
+}
 
 extern "C" int laue_set_launch_shape(laue_handle* h, int row_shape, int col_shape) {
     if (!h) return LAUE_ERR_INVALID_ARG;
@@ -497,9 +520,9 @@ extern "C" int laue_autotune(laue_handle* h, const LaueGeometry* geom, const Lau
 
 // ------------------------------------------------------------- not yet built
 
-extern "C" int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const LaueObsSpots* obs,
-                          const LaueModelSpots* model, const float* f, const float* g, const LaueMParams* prm,
-                          const float* omega, float* R, float* x, int N, float* step_norms, void* stream) {
+static int mstep_entry(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const LaueObsSpots* obs,
+                       const LaueModelSpots* model, const float* f, const float* g, const LaueMParams* prm,
+                       const float* omega, float* R, float* x, int N, float* step_norms, void* stream, bool adjoint) {
     if (!h) return LAUE_ERR_INVALID_ARG;
     int rc;
     if ((rc = laue_check_geom(h, geom))) return rc;
@@ -549,7 +572,25 @@ extern "C" int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLa
     m.n_newton = prm->n_newton;
     m.n_mm = prm->n_mm;
     for (int k = 0; k < 3; ++k) m.e[k] = geom->beam[k];
+    m.D2 = geom->D * geom->D;
+    if (adjoint)
+        return laue_cuda_check(h, mstep_adjoint_run(m, lc, prm->n_newton, (cudaStream_t)stream),
+                               "mstep_adjoint launch");
     return laue_cuda_check(h, mstep_run(m, lc, (cudaStream_t)stream), "mstep launch");
+}
+
+extern "C" int laue_mstep(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const LaueObsSpots* obs,
+                          const LaueModelSpots* model, const float* f, const float* g, const LaueMParams* prm,
+                          const float* omega, float* R, float* x, int N, float* step_norms, void* stream) {
+    return mstep_entry(h, geom, lat, obs, model, f, g, prm, omega, R, x, N, step_norms, stream, false);
+}
+
+extern "C" int laue_mstep_adjoint(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
+                                  const LaueObsSpots* obs, const LaueModelSpots* model, const float* f,
+                                  const float* g, const LaueMParams* prm, const float* omega, float* R, float* x,
+                                  int N, float* step_norms, void* stream) {
+    if (prm && !(prm->hreg >= 0.0f)) return laue_fail(h, LAUE_ERR_INVALID_ARG, "mstep_adjoint: hreg >= 0");
+    return mstep_entry(h, geom, lat, obs, model, f, g, prm, omega, R, x, N, step_norms, stream, true);
 }
 
 extern "C" int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,

@@ -29,6 +29,8 @@ enum CtrlSlot {
     CTRL_GEN_DONE = 13,
     CTRL_SF_NEXT = 14,    // single-grain fit start queue / ticket
     CTRL_SF_DONE = 15,
+    CTRL_EXACT_ROWS = 16, // row / column log-sum-exps recomputed on the exact path
+    CTRL_EXACT_COLS = 17,
     CTRL_SLOTS = 64
 };
 

@@ -71,7 +71,7 @@ size_t index_carve_bytes(int T, int n_obs, int S, int n_max) {
     size_t cap = (size_t)n_max * kSfCap;
     size_t b = 0;
     auto add = [&](size_t bytes) { b += align_up(bytes > 0 ? bytes : 1, 256) + 256; };
-    add(sizeof(float) * 12 * (size_t)S * 2);  // fitted and kept poses
+    add(sizeof(float) * 12 * (size_t)S * 3);  // grid starts, fitted and kept poses
     add(sizeof(int) * (size_t)S * 2 + 64);    // keep, indices, count
     add(sizeof(int) * (size_t)n_max + sizeof(float) * (size_t)n_max);
     add(sizeof(int) * (T + 1));
@@ -104,8 +104,12 @@ extern "C" int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLa
     int rc;
     if ((rc = laue_check_geom(h, geom))) return rc;
     if ((rc = laue_check_obs(h, obs))) return rc;
+    const bool grid = !startR && !startX;
     if (!lat || lat->M < 1 || !prm || S < 0 || n_max < 1 || !R_out || !x_out || !n_grains_host || !omega ||
-        (S > 0 && (!startR || !startX)) || (obs->n > 0 && !assign))
+        (!grid && S > 0 && (!startR || !startX)) || (obs->n > 0 && !assign) ||
+        (grid && (prm->grid_n < 0 || (prm->grid_sym != 1 && prm->grid_sym != 24) || prm->grid_k < 1 ||
+                  !(prm->grid_cube >= 0.0f))) ||
+        (prm && prm->mstep_kind != 0 && prm->mstep_kind != 1))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "index: bad arguments");
     if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set");
     const int T = obs->T;
@@ -115,6 +119,8 @@ extern "C" int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLa
     // the carve sits at the end of the workspace; sub-calls see the rest
     size_t full = h->ws_bytes;
     Carve C{(char*)h->ws + align_up(full - carve, 256) - 256, 0};
+    float* gridR = C.take<float>(9 * (size_t)S);
+    float* gridX = C.take<float>(3 * (size_t)S);
     float* fitR = C.take<float>(9 * (size_t)S);
     float* fitX = C.take<float>(3 * (size_t)S);
     float* kR = C.take<float>(9 * (size_t)S);
@@ -142,8 +148,21 @@ extern "C" int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLa
         return code;
     };
     *n_grains_host = 0;
+    // 0. the start grid (Section "Single-grain fitting"), unless starts are given
+    if (grid) {
+        long long Sg = 0;
+        if ((rc = laue_start_grid(h, prm->grid_n, prm->grid_sym, prm->grid_k, prm->grid_cube, S, gridR, gridX, &Sg,
+                                  stream)))
+            return restore(rc);
+        if (Sg > S)
+            return restore(laue_fail(h, LAUE_ERR_CAPACITY, "index: the start grid has %lld starts, S = %d", Sg, S));
+        S = (int)Sg;
+        startR = gridR;
+        startX = gridX;
+    }
     // 1. batched single-grain fits
-    LaueSingleParams sp{prm->eps_final, prm->c_out, prm->f_out, prm->k_single, prm->mstep, 100.0f, 0};
+    LaueSingleParams sp{prm->eps_final, prm->c_out, prm->f_out, prm->k_single, prm->mstep,
+                        prm->anneal_single > 0.0f ? prm->anneal_single : 100.0f, prm->recut_single};
     if ((rc = laue_single_fit(h, geom, lat, obs, omega, startR, startX, S, &sp, fitR, fitX, keep, nullptr, stream)))
         return restore(rc);
     // 2. kept candidates (in start order)
@@ -181,8 +200,10 @@ extern "C" int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLa
         if (last) break;
         LaueMParams mp = prm->mstep;
         mp.eps = (float)eps;
-        if ((rc = laue_mstep(h, geom, lat, obs, &ms, f, g, &mp, omega, R_out, x_out, kstar, nullptr, stream)))
-            return restore(rc);
+        rc = prm->mstep_kind == 1
+                 ? laue_mstep_adjoint(h, geom, lat, obs, &ms, f, g, &mp, omega, R_out, x_out, kstar, nullptr, stream)
+                 : laue_mstep(h, geom, lat, obs, &ms, f, g, &mp, omega, R_out, x_out, kstar, nullptr, stream);
+        if (rc) return restore(rc);
     }
     if (obs->n > 0) spot_to_grain_kernel<<<(obs->n + 255) / 256, 256, 0, s>>>(assign_j, mgrain, obs->n, assign);
     if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "index synchronise"))) return restore(rc);

@@ -87,8 +87,9 @@ struct SkArgs {
     float kc;              // c_out log2(e) / eps
     double frac;           // unmatched-model fraction
     float to_user;         // eps ln 2: internal -> mm^2
-    int mode;              // 0 global dustbins, 1 per angle
+    int mode;              // 0 global dustbins, 1 per angle, 2 unbalanced (no dustbins)
     int warm;
+    float tau_row, tau_col;  // unbalanced exponents kappa/(kappa+eps), lambda/(lambda+eps)
     // user buffers
     float* f;
     float* g;
@@ -142,6 +143,7 @@ struct MsArgs {
 };
 
 cudaError_t mstep_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s);
+cudaError_t mstep_adjoint_run(const MsArgs& m, const SkLaunch& l, int n_steps, cudaStream_t s);
 
 // ------------------------------------------------------- single-grain fits
 constexpr int kSfMaxT = 1024;       // angles a fit supports

@@ -59,14 +59,17 @@ __global__ void ms_init_kernel(MsArgs m) {
 // ------------------------------------------------------------ pair pass
 // mode 0: Newton sums (9 floats in the x frame), mode 1: v_j (3 floats, lab),
 // mode 2: adjoint of the OT-weighted cost (gradient w.r.t. axis-angle and x,
-// and the spot's share of the objective; 7 floats).
+// and the spot's share of the objective; 7 floats), mode 3: the same adjoint at
+// the current pose (the ray r_j of the current R, the plan of the E-step) plus
+// the sums q_j = sum Q, s1_j = sum Q / tau, s2_j = sum Q / tau^2 of the
+// Gauss-Newton matrix (10 floats).
 struct MsCol {
     int j, n, t;
     bool ok;
     float cg, sg;
     float c[3];   // current centre Gamma_t x_n
-    float r[3];   // E-step ray
-    float acc[9];
+    float r[3];   // E-step ray (mode 3: the ray at the current pose)
+    float acc[10];
 };
 
 __device__ __forceinline__ void ms_pair(MsCol& C, int mode, float px, float py, float pz, float v) {
@@ -75,10 +78,15 @@ __device__ __forceinline__ void ms_pair(MsCol& C, int mode, float px, float py, 
     float d0 = px - C.c[0], d1 = py - C.c[1], d2 = pz - C.c[2];
     float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
     float h0 = d0 * is, h1 = d1 * is, h2 = d2 * is;
-    if (mode == 2) {
+    if (mode >= 2) {
         // adjoint: sum Q (r - (rhat.r) rhat)/tau, sum Q (r - rhat), sum Q |rhat - r|^2
         float rr = h0 * C.r[0] + h1 * C.r[1] + h2 * C.r[2];
         float qs = Q * is;
+        if (mode == 3) {
+            C.acc[7] += Q;
+            C.acc[8] += qs;
+            C.acc[9] += qs * is;
+        }
         C.acc[0] += qs * (C.r[0] - rr * h0);
         C.acc[1] += qs * (C.r[1] - rr * h1);
         C.acc[2] += qs * (C.r[2] - rr * h2);
@@ -154,7 +162,16 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
                 C.r[0] = -(lane ? Z.y : Z.x);
                 C.r[1] = -(lane ? Z.w : Z.z);
                 C.r[2] = -(lane ? W.y : W.x);
-                for (int k = 0; k < 9; ++k) C.acc[k] = 0.0f;
+                if (MODE == 3) {  // the ray of the current orientation
+                    const float* Rn = m.R + 9 * C.n;
+                    float4 wd = m.w_d0[m.plane[C.j]];
+                    float v[3], u[3];
+                    for (int r = 0; r < 3; ++r) v[r] = Rn[3 * r] * wd.x + Rn[3 * r + 1] * wd.y + Rn[3 * r + 2] * wd.z;
+                    gam_apply(cg, sg, v, u);
+                    float ue = u[0] * m.e[0] + u[1] * m.e[1] + u[2] * m.e[2];
+                    for (int r = 0; r < 3; ++r) C.r[r] = m.e[r] - 2.0f * ue * u[r];
+                }
+                for (int k = 0; k < 10; ++k) C.acc[k] = 0.0f;
             }
         }
         const f2 Gpa = dup(Ga), Gpb = dup(Gb);
@@ -186,7 +203,7 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
                 MsCol& C = lane ? B : A;
                 if (lcol + lane >= nj) continue;
                 float* o = m.jsum + 12 * (size_t)(a.J_off[t] + lcol + lane);
-                if (MODE == 2) {
+                if (MODE >= 2) {
                     // per-spot gradient: x part Gamma^T dC/dc, rotation part
                     // v x (Gamma^T y), y = -2 ((gr.u) e + (u.e) gr), u = Gamma R w_m
                     float D2x2 = 2.0f * m.D2;
@@ -211,8 +228,13 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
                     o[4] = gx[1];
                     o[5] = gx[2];
                     o[6] = m.D2 * C.acc[6];
+                    if (MODE == 3) {
+                        o[7] = C.acc[7];
+                        o[8] = C.acc[8];
+                        o[9] = C.acc[9];
+                    }
                     if (!C.ok)
-                        for (int k = 0; k < 7; ++k) o[k] = 0.0f;
+                        for (int k = 0; k < (MODE == 3 ? 10 : 7); ++k) o[k] = 0.0f;
                 } else if (MODE == 1) {
                     o[9] = C.ok ? C.acc[0] : 0.0f;
                     o[10] = C.ok ? C.acc[1] : 0.0f;
@@ -358,6 +380,134 @@ __global__ void ms_grad_grain_kernel(MsArgs m) {
     if (m.value) m.value[n] = s[6];
 }
 
+// ---------------------------------------------- adjoint M-step per grain
+// One warp per grain: fixed-order sums of the per-spot gradients (mode 3) and
+// of the Gauss-Newton blocks of each spot, built from its ray at the current
+// pose with the model-ray projector P_j = I - r r^T:
+//   H_phiphi += 2 D^2 q A^T A,  H_phix += 2 D^2 s1 A^T P Gamma,
+//   H_xx += 2 D^2 s2 Gamma^T P Gamma,  A = 2 (u e^T + (u.e) I) Gamma [v]x;
+// then a Levenberg-Marquardt step delta = -(H + lambda diag H)^-1 grad
+// (Cholesky), R <- exp([delta_phi]x) R, x <- x + delta_x.
+__device__ __forceinline__ int tri6(int a, int b) {
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo * 6 - lo * (lo - 1) / 2 + (hi - lo);
+}
+
+__global__ void ms_adj_grain_kernel(MsArgs m) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= m.N) return;
+    int n = warp;
+    float Rn[9];
+    for (int k = 0; k < 9; ++k) Rn[k] = m.R[9 * n + k];
+    const float D2x2 = 2.0f * m.D2;
+    float g[6], H[21];
+    for (int k = 0; k < 6; ++k) g[k] = 0.0f;
+    for (int k = 0; k < 21; ++k) H[k] = 0.0f;
+    for (int t = lane; t < m.T; t += 32) {
+        int j0 = m.seg[t * (m.N + 1) + n], j1 = m.seg[t * (m.N + 1) + n + 1];
+        if (j0 == j1) continue;
+        float cg, sg;
+        gamma_t(m.omega[t], cg, sg);
+        for (int j = j0; j < j1; ++j) {
+            const float* o = m.jsum + 12 * (size_t)j;
+            for (int k = 0; k < 6; ++k) g[k] += o[k];
+            float q = o[7], s1 = o[8], s2 = o[9];
+            if (q == 0.0f) continue;
+            float4 wd = m.w_d0[m.plane[j]];
+            float v[3], u[3], r[3];
+            for (int a = 0; a < 3; ++a) v[a] = Rn[3 * a] * wd.x + Rn[3 * a + 1] * wd.y + Rn[3 * a + 2] * wd.z;
+            gam_apply(cg, sg, v, u);
+            float ue = u[0] * m.e[0] + u[1] * m.e[1] + u[2] * m.e[2];
+            for (int a = 0; a < 3; ++a) r[a] = m.e[a] - 2.0f * ue * u[a];
+            // A = B Gamma [v]x with B = 2 (u e^T + ue I): column b of Gamma [v]x is Gamma (e_b x v)
+            float A[9], PG[9], G[9];
+            for (int b = 0; b < 3; ++b) {
+                float eb[3] = {b == 0 ? 1.0f : 0.0f, b == 1 ? 1.0f : 0.0f, b == 2 ? 1.0f : 0.0f};
+                float cr[3] = {eb[1] * v[2] - eb[2] * v[1], eb[2] * v[0] - eb[0] * v[2], eb[0] * v[1] - eb[1] * v[0]};
+                float gc[3], ge[3];
+                gam_apply(cg, sg, cr, gc);  // Gamma (e_b x v)
+                gam_apply(cg, sg, eb, ge);  // column b of Gamma
+                // [v]x e_b = v x e_b = -(e_b x v)
+                gc[0] = -gc[0];
+                gc[1] = -gc[1];
+                gc[2] = -gc[2];
+                float eg = m.e[0] * gc[0] + m.e[1] * gc[1] + m.e[2] * gc[2];
+                for (int a = 0; a < 3; ++a) {
+                    A[3 * a + b] = 2.0f * (u[a] * eg + ue * gc[a]);
+                    G[3 * a + b] = ge[a];
+                }
+                float rg = r[0] * ge[0] + r[1] * ge[1] + r[2] * ge[2];
+                for (int a = 0; a < 3; ++a) PG[3 * a + b] = ge[a] - r[a] * rg;
+            }
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    float aa = 0.0f, ap = 0.0f, gp = 0.0f;
+                    for (int k = 0; k < 3; ++k) {
+                        aa += A[3 * k + a] * A[3 * k + b];
+                        ap += A[3 * k + a] * PG[3 * k + b];
+                        gp += G[3 * k + a] * PG[3 * k + b];
+                    }
+                    if (a <= b) {
+                        H[tri6(a, b)] += D2x2 * q * aa;
+                        H[tri6(3 + a, 3 + b)] += D2x2 * s2 * gp;
+                    }
+                    H[tri6(a, 3 + b)] += D2x2 * s1 * ap;
+                }
+        }
+    }
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) g[k] += __shfl_xor_sync(0xffffffffu, g[k], o);
+    for (int k = 0; k < 21; ++k)
+        for (int o = 16; o > 0; o >>= 1) H[k] += __shfl_xor_sync(0xffffffffu, H[k], o);
+    if (lane != 0) return;
+    // Cholesky of H + lambda diag(H)
+    float L[6][6], d[6], y[6];
+    bool ok = true;
+    for (int a = 0; a < 6 && ok; ++a) {
+        if (!(H[tri6(a, a)] > 0.0f)) ok = false;
+        for (int b = 0; b <= a && ok; ++b) {
+            float sum = H[tri6(a, b)] + (a == b ? m.hreg * H[tri6(a, a)] : 0.0f);
+            for (int k = 0; k < b; ++k) sum -= L[a][k] * L[b][k];
+            if (a == b) {
+                if (!(sum > 0.0f)) ok = false;
+                else L[a][a] = sqrtf(sum);
+            } else {
+                L[a][b] = sum / L[b][b];
+            }
+        }
+    }
+    if (!ok) return;  // the grain keeps its pose
+    for (int a = 0; a < 6; ++a) {
+        float sum = -g[a];
+        for (int k = 0; k < a; ++k) sum -= L[a][k] * y[k];
+        y[a] = sum / L[a][a];
+    }
+    for (int a = 5; a >= 0; --a) {
+        float sum = y[a];
+        for (int k = a + 1; k < 6; ++k) sum -= L[k][a] * d[k];
+        d[a] = sum / L[a][a];
+    }
+    // R <- exp([d_phi]x) R (Rodrigues), rows re-orthonormalised
+    float th2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2], th = sqrtf(th2);
+    float sa = th > 1e-6f ? sinf(th) / th : 1.0f - th2 / 6.0f;
+    float cb = th > 1e-6f ? (1.0f - cosf(th)) / th2 : 0.5f - th2 / 24.0f;
+    float K[9] = {0.0f, -d[2], d[1], d[2], 0.0f, -d[0], -d[1], d[0], 0.0f}, E[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            float k2 = K[3 * a] * K[b] + K[3 * a + 1] * K[3 + b] + K[3 * a + 2] * K[6 + b];
+            E[3 * a + b] = (a == b ? 1.0f : 0.0f) + sa * K[3 * a + b] + cb * k2;
+        }
+    float Rs[9];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Rs[3 * a + b] = E[3 * a] * Rn[b] + E[3 * a + 1] * Rn[3 + b] + E[3 * a + 2] * Rn[6 + b];
+    orthonormalise_rows(Rs);
+    for (int k = 0; k < 9; ++k) m.R[9 * n + k] = Rs[k];
+    for (int a = 0; a < 3; ++a) m.x[3 * n + a] += d[3 + a];
+    m.gstate[4 * n + 1] = sqrtf(d[3] * d[3] + d[4] * d[4] + d[5] * d[5]);
+    m.gstate[4 * n + 2] = th;
+}
+
 static cudaError_t seg_table(const MsArgs& m, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(m.seg, 0, sizeof(int) * (size_t)m.T * (m.N + 1), s);
     if (e != cudaSuccess) return e;
@@ -453,6 +603,19 @@ __global__ void axis_angle_vjp_kernel(const float* w, const float* grad, const f
 cudaError_t axis_angle_vjp_run(const float* w, const float* grad, const float* gout, float* gw, float* gx, int N,
                                cudaStream_t s) {
     if (N > 0) axis_angle_vjp_kernel<<<(N + 127) / 128, 128, 0, s>>>(w, grad, gout, gw, gx, N);
+    return cudaGetLastError();
+}
+
+cudaError_t mstep_adjoint_run(const MsArgs& m, const SkLaunch& l, int n_steps, cudaStream_t s) {
+    cudaError_t e = sinkhorn_prepare(m.sk, s);  // the E-step plan: pair copies with F, G
+    if (e != cudaSuccess) return e;
+    if ((e = seg_table(m, s)) != cudaSuccess) return e;
+    if (m.N > 0) ms_init_kernel<<<(m.N + 255) / 256, 256, 0, s>>>(m);
+    for (int k = 0; k < n_steps; ++k) {
+        ms_pair_kernel<3><<<l.col_grid, kTPB, 0, s>>>(m);
+        if (m.N > 0) ms_adj_grain_kernel<<<(m.N * 32 + 127) / 128, 128, 0, s>>>(m);
+    }
+    if (m.N > 0) ms_norms_kernel<<<(m.N + 255) / 256, 256, 0, s>>>(m);
     return cudaGetLastError();
 }
 

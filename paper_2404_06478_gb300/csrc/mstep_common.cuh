@@ -180,4 +180,18 @@ __device__ __forceinline__ void mm_accumulate(const float* m6, float4 wd, const 
         for (int c = 0; c < 3; ++c) B[3 * r + c] += a[r] * w[c];
 }
 
+// Gram-Schmidt on the rows of a nearly orthogonal 3x3 matrix (the third row
+// is the cross product of the first two, so the result is a rotation).
+__device__ __forceinline__ void orthonormalise_rows(float* R) {
+    float n0 = rsqrtf(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+    for (int k = 0; k < 3; ++k) R[k] *= n0;
+    float d = R[0] * R[3] + R[1] * R[4] + R[2] * R[5];
+    for (int k = 0; k < 3; ++k) R[3 + k] -= d * R[k];
+    float n1 = rsqrtf(R[3] * R[3] + R[4] * R[4] + R[5] * R[5]);
+    for (int k = 0; k < 3; ++k) R[3 + k] *= n1;
+    R[6] = R[1] * R[5] - R[2] * R[4];
+    R[7] = R[2] * R[3] - R[0] * R[5];
+    R[8] = R[0] * R[4] - R[1] * R[3];
+}
+
 }  // namespace laue

@@ -72,6 +72,8 @@ extern "C" int laue_cost_sinkhorn_noalloc(const LaueGeometry* geom, const LaueOb
     if ((rc = laue_check_model(nullptr, model))) return rc;
     if (!prm || !(prm->eps > 0.0f) || prm->n_iter < 0 || !(prm->c_out >= 0.0f) || !(prm->unmatched_frac >= 0.0) ||
         prm->unmatched_frac > 1.0 || obs->T != model->T || (obs->n > 0 && !f) || (model->n > 0 && !g) ||
+        prm->dust_mode < 0 || prm->dust_mode > 2 ||
+        (prm->dust_mode == 2 && (!(prm->kappa > 0.0f) || !(prm->lambda > 0.0f))) ||
         (prm->warm_start && !dust))
         return LAUE_ERR_INVALID_ARG;
     StaticDevice* d = nullptr;

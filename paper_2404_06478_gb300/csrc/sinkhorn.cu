@@ -13,6 +13,11 @@
 // with e2_ij = |rhat_ij - r_j|^2 and kc = c_out log2(e)/eps.  The cost matrix
 // is never stored: every pass recomputes e2 from the spot coordinates.
 //
+// Unbalanced mode (Appendix "Optimal transport variants", Algorithm
+// UnbalancedOT): no dustbins, and each balanced update is scaled by
+// tau_row = kappa / (kappa + eps) (rows) or tau_col = lambda / (lambda + eps)
+// (columns), the log-domain form of the exponents of the scaling updates.
+//
 // Layout.  The workspace holds the spots as pairs: each angle block is padded
 // to an even count and element pairs (a, b) are interleaved into float4 rows
 // such as {x_a, x_b, y_a, y_b}, so one 16-byte shared-memory load yields two
@@ -325,6 +330,7 @@ constexpr float kTinySum = 1.0e-30f;  // below ~2^-100 the fast sum is recompute
 // Exact row log-sum-exp from global memory (running maximum), for rows whose
 // shifted sum underflowed.
 __device__ float row_exact(const SkArgs& a, int t, f2 px, f2 py, f2 pz, float dustv, f2 K2) {
+    atomicAdd((unsigned*)a.ctrl + CTRL_EXACT_ROWS, 1u);
     RowLse L;
     L.init(dustv);
     for (int q = a.J2_off[t]; q < a.J2_off[t + 1]; ++q) {
@@ -336,6 +342,7 @@ __device__ float row_exact(const SkArgs& a, int t, f2 px, f2 py, f2 pz, float du
 }
 
 __device__ float col_exact(const SkArgs& a, int t, f2 ncx, f2 ncy, f2 ncz, f2 nrx, f2 nry, f2 nrz, float dz, f2 K2) {
+    atomicAdd((unsigned*)a.ctrl + CTRL_EXACT_COLS, 1u);
     RowLse L;
     L.init(dz);
     for (int q = a.I2_off[t]; q < a.I2_off[t + 1]; ++q) {
@@ -377,7 +384,8 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
         int ni = a.I_off[t + 1] - a.I_off[t];
         bool vb = valid && 2 * (q - a.I2_off[t]) + 1 < ni;
         int j0 = a.J2_off[t], nj = a.J2_off[t + 1] - j0;
-        float dustv = D.G0[a.mode ? t : 0] - a.kc;
+        const bool ub = a.mode == 2;  // unbalanced OT: no dustbins, scaled update
+        float dustv = ub ? kNegHuge : D.G0[a.mode ? t : 0] - a.kc;
         float4 X = valid ? a.obsX[q] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 Y = valid ? a.obsY[q] : make_float4(0.f, 0.f, kPadFar, kPadFar);
         RowPair R;
@@ -387,8 +395,8 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
         R.pxb = dup(X.y);
         R.pyb = dup(X.w);
         R.pzb = dup(Y.y);
-        const float shift = fmaxf(D.Gmax[t], dustv);
-        f2 Sa = pk(ex2(dustv - shift), 0.0f), Sb = Sa;
+        const float shift = ub ? D.Gmax[t] : fmaxf(D.Gmax[t], dustv);
+        f2 Sa = pk(ub ? 0.0f : ex2(dustv - shift), 0.0f), Sb = Sa;
         bool ok = stream_tile_prep(
             S, parity, src, j0, nj,
             [&](int st, int n) {
@@ -408,6 +416,10 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
         float sa = lo(Sa) + hi(Sa), sb = lo(Sb) + hi(Sb);
         float Fa = valid ? (sa > kTinySum ? -(shift + lg2(sa)) : -row_exact(a, t, R.pxa, R.pya, R.pza, dustv, K2)) : 0.0f;
         float Fb = vb ? (sb > kTinySum ? -(shift + lg2(sb)) : -row_exact(a, t, R.pxb, R.pyb, R.pzb, dustv, K2)) : 0.0f;
+        if (ub) {  // Algorithm UnbalancedOT: the balanced update raised to kappa / (kappa + eps)
+            Fa = nj > 0 ? a.tau_row * Fa : 0.0f;
+            Fb = nj > 0 ? a.tau_row * Fb : 0.0f;
+        }
         if (valid) *(float2*)&a.obsY[q].z = make_float2(Fa, vb ? Fb : kNegHuge);
         // tile partial of LSE2(F_i - kc) for the outlier column update
         float pm = kNegHuge, ps = 0.0f;
@@ -421,7 +433,9 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
     }
     if (!last_cta(S, a.ctrl + CTRL_ROW_DONE)) return;
     // finalise: promote F_0 and compute G_0 from the new F
-    if (a.mode) {
+    if (a.mode == 2) {
+        // no dustbins
+    } else if (a.mode) {
         for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
             D.F0[t] = D.F0n[t];
             int4 at = a.ang_tiles[t];
@@ -477,9 +491,10 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
         int i0 = a.I2_off[t], ni = a.I2_off[t + 1] - i0;
         ColPair C;
         if (valid) load_col_pair(a, q, C);
-        float dz = D.F0[a.mode ? t : 0];  // unmatched-model row, C_0j = 0
-        const float shift = fmaxf(D.Fmax[t], dz);
-        f2 Sa = pk(ex2(dz - shift), 0.0f), Sb = Sa;
+        const bool ub = a.mode == 2;
+        float dz = ub ? kNegHuge : D.F0[a.mode ? t : 0];  // unmatched-model row, C_0j = 0
+        const float shift = ub ? D.Fmax[t] : fmaxf(D.Fmax[t], dz);
+        f2 Sa = pk(ub ? 0.0f : ex2(dz - shift), 0.0f), Sb = Sa;
         bool ok = stream_tile_prep(
             S, parity, src, i0, ni,
             [&](int st, int n) {
@@ -503,6 +518,10 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
         float Gb = vb ? (sb > kTinySum ? -(shift + lg2(sb))
                                        : -col_exact(a, t, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, dz, K2))
                       : 0.0f;
+        if (ub) {  // raised to lambda / (lambda + eps)
+            Ga = ni > 0 ? a.tau_col * Ga : 0.0f;
+            Gb = ni > 0 ? a.tau_col * Gb : 0.0f;
+        }
         if (valid) *(float2*)&a.modY[q].z = make_float2(Ga, vb ? Gb : kNegHuge);
         float pm = kNegHuge, ps = 0.0f;
         if (valid) {
@@ -515,7 +534,9 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
     }
     if (!last_cta(S, a.ctrl + CTRL_COL_DONE)) return;
     // finalise: next F_0 from the new G and the current G_0
-    if (a.mode) {
+    if (a.mode == 2) {
+        // no dustbins
+    } else if (a.mode) {
         for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
             int4 at = a.ang_tiles[t];
             Lse2 L;
@@ -599,7 +620,7 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
         int lrow = 2 * (q - a.I2_off[t]);
         bool vb = valid && lrow + 1 < ni;
         int jbase = a.J_off[t], j0 = a.J2_off[t], nj = a.J2_off[t + 1] - j0;
-        float dustv = D.G0[a.mode ? t : 0] - a.kc;
+        float dustv = a.mode == 2 ? kNegHuge : D.G0[a.mode ? t : 0] - a.kc;
         float4 X = valid ? a.obsX[q] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 Y = valid ? a.obsY[q] : make_float4(0.f, 0.f, kPadFar, kPadFar);
         f2 pxa = dup(X.x), pya = dup(X.z), pza = dup(Y.x), pxb = dup(X.y), pyb = dup(X.w), pzb = dup(Y.y);
@@ -645,6 +666,8 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
                 L.merge(dustv, 1.0f);
                 float rs = ex2(F + L.value());
                 my_err = fmaxf(my_err, fabsf(rs - 1.0f));
+                // unbalanced plan: a spot that keeps most of its mass is an outlier
+                if (a.mode == 2 && !(rs >= 0.5f)) P.arg = -1;
                 if (a.assign) a.assign[i + lane] = P.arg;
                 if (a.margin) a.margin[i + lane] = ex2(F + P.b1) - (P.b2 > kNegHuge ? ex2(F + P.b2) : 0.0f);
             }
@@ -655,7 +678,7 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
     if (!last_cta(S, a.ctrl + CTRL_HRV_DONE)) return;
     if (threadIdx.x == 0) {
         float err = __int_as_float(*(int*)(D.err + 2));
-        int nd = a.mode ? a.T : 1;
+        int nd = a.mode == 2 ? 0 : (a.mode ? a.T : 1);
         for (int d = 0; d < nd; ++d) {
             if (D.log2U[d] > kNegHuge) err = fmaxf(err, fabsf(ex2(D.F0[d] - D.F0n[d]) - 1.0f));
         }
@@ -703,7 +726,7 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_col_kernel(SkArgs a) {
         }
         if (valid) {
             float4 Ym = a.modY[q];
-            float F0 = D.F0[a.mode ? t : 0];
+            float F0 = a.mode == 2 ? kNegHuge : D.F0[a.mode ? t : 0];
             for (int lane = 0; lane < 2; ++lane) {
                 if (lane == 1 && !vb) break;
                 RowLse& L = lane ? C.B : C.A;
@@ -789,7 +812,7 @@ cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s) {
     if (blocks < 1) blocks = 1;
     sk_schedule_kernel<<<1, 1024, 0, s>>>(a);
     sk_pack_kernel<<<blocks, 256, 0, s>>>(a);
-    sk_init_dust_kernel<<<1, 1024, 0, s>>>(a);
+    if (a.mode != 2) sk_init_dust_kernel<<<1, 1024, 0, s>>>(a);
     if (a.T > 0) sk_init_gmax_kernel<<<a.T, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -38,6 +38,8 @@ class EMConfig:
     tol_R: float = 1e-9
     hreg: float = 1e-3
     anneal_factor: float = 100.0  # eps_init / eps_final
+    mstep: str = "plain"          # "plain": laue_mstep; "adjoint": laue_mstep_adjoint
+    lm_damping: float = 1e-3      # Levenberg-Marquardt damping of the adjoint M-step
 
 
 class EMSolver:
@@ -61,6 +63,10 @@ class EMSolver:
 
     def m_step(self, R, x, out, eps):
         c = self.cfg
+        if c.mstep == "adjoint":
+            api.mstep_adjoint(self.h, self.geom, self.lat, self.obs, self.model, out["f"], out["g"], eps, self.omega,
+                              R, x, n_steps=c.n_newton, lam=c.lm_damping)
+            return
         api.mstep(self.h, self.geom, self.lat, self.obs, self.model, out["f"], out["g"], eps, self.omega, R, x,
                   n_newton=c.n_newton, n_mm=c.n_mm, tol_x=c.tol_x, tol_R=c.tol_R, hreg=c.hreg)
 

@@ -59,3 +59,27 @@ def to_device(case, dev):
     ms = api.ModelSpots.from_numpy(fw["J_off"], fw["grain"], fw["plane"], fw["ray"], fw["center"],
                                    fw["spot"], fw["det"], device=dev)
     return ob, ms
+
+
+def _oracle_call(args):
+    name, a, kw = args
+    return getattr(oracle, name)(*a, **kw)
+
+
+def oracle_parallel(calls, workers=None):
+    """Runs oracle functions [(name, args, kwargs), ...] in a pool of spawned
+    processes (spawned, not forked: the parent may hold a CUDA context)."""
+    import concurrent.futures
+    import multiprocessing
+    import os
+    workers = workers or min(len(calls), os.cpu_count() or 1)
+    if workers <= 1:
+        return [_oracle_call(c) for c in calls]
+    with concurrent.futures.ProcessPoolExecutor(workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+        return list(ex.map(_oracle_call, calls))
+
+
+def block_slices(case, t):
+    """Observed and model index ranges of angle block t."""
+    return (slice(int(case.obs.I_off[t]), int(case.obs.I_off[t + 1])),
+            slice(int(case.fw["J_off"][t]), int(case.fw["J_off"][t + 1])))

@@ -81,6 +81,131 @@ def test_em_tiny_parity_and_graph(env):
     assert torch.equal(out2["assign"], out["assign"])
 
 
+def test_em_adjoint_form_parity(env):
+    """Algorithm LaueOT with the adjoint M-step (damped Gauss-Newton on the
+    OT-weighted cost) in place of Newton + MM: the GPU solve equals the oracle's
+    EM with the same M-step (tiny workload, 10 annealed EM steps of 60 Sinkhorn
+    iterations), poses within 1e-3 deg / 1e-3 mm, assignments equal where the
+    oracle's margin exceeds 1e-3."""
+    torch, api, dev = env["torch"], env["api"], env["dev"]
+    from paper_2404_06478_gb300.em import EMConfig, EMSolver
+    case = make_case(sg.CONFIGS["tiny"], seed=4)
+    R0, x0 = _perturbed(case, 14, 0.3, 0.1)
+    fw = oracle.forward(GEOM, case.planes, R0, x0, case.om)
+    for k in ("ray", "spot", "center"):
+        fw[k] = f32(fw[k])
+    case.fw = fw
+    n_em, n_sk = 10, 60
+    ref = oracle.em(GEOM, case.planes, case.om, case.obs.p, case.obs.I_off, fw["J_off"], fw["grain"], fw["plane"],
+                    R0, x0, eps_final=1.0, n_em=n_em, n_sinkhorn=n_sk, c_out=case.c_out, mstep="adjoint")
+    ob, ms = to_device(case, dev)
+    lat = api.Lattice.cubic(case.cfg.a, case.cfg.hmax, case.cfg.centering, device=dev)
+    om = torch.tensor(case.om, dtype=torch.float32, device=dev)
+    solver = EMSolver(env["h"], GEOM, lat, ob, ms, om, EMConfig(eps_final=1.0, n_em=n_em, n_sinkhorn=n_sk,
+                                                                c_out=case.c_out, mstep="adjoint"))
+    t = lambda a, s: torch.tensor(a.reshape(s), dtype=torch.float32, device=dev).contiguous()
+    R, x = t(R0, (-1, 9)), t(x0, (-1, 3))
+    out = solver.run(R, x)
+    torch.cuda.synchronize()
+    assert env["h"].device_status() == 0
+    Rg = R.cpu().numpy().reshape(-1, 3, 3).astype(np.float64)
+    xg = x.cpu().numpy().astype(np.float64)
+    assert np.all(_mis_deg(Rg, ref["R"]) < 1e-3), _mis_deg(Rg, ref["R"])
+    assert np.abs(xg - ref["x"]).max() < 1e-3
+    sure = ref["margin"] > 1e-3
+    np.testing.assert_array_equal(out["assign"].cpu().numpy()[sure], ref["assign"][sure])
+    # both forms reach the truth's neighbourhood
+    assert np.all(_mis_deg(Rg, case.R) < 0.3) and np.abs(xg - case.x).max() < 0.3
+
+
+def test_em_parity_mid_size(env):
+    """Algorithm LaueOT on 60 grains, |hkl| <= 6, 20 rotations over 360 deg, 30%
+    outliers: 6 annealed EM steps of 40 Sinkhorn iterations from poses
+    0.3 deg / 0.1 mm off the truth.  Final poses within 1e-3 deg / 1e-3 mm of
+    the oracle's EM; hard assignments equal where the oracle's margin > 1e-3."""
+    torch, api, dev = env["torch"], env["api"], env["dev"]
+    from paper_2404_06478_gb300.em import EMConfig, EMSolver
+    case = make_case(sg.CONFIGS["medium"], seed=31, n_grains=60, T=20)
+    R0, x0 = _perturbed(case, 32, 0.3, 0.1)
+    fw = oracle.forward(GEOM, case.planes, R0, x0, case.om)
+    for k in ("ray", "spot", "center"):
+        fw[k] = f32(fw[k])
+    case.fw = fw
+    n_em, n_sk = 6, 40
+    ref = oracle.em(GEOM, case.planes, case.om, case.obs.p, case.obs.I_off, fw["J_off"], fw["grain"], fw["plane"],
+                    R0, x0, eps_final=1.0, n_em=n_em, n_sinkhorn=n_sk, c_out=case.c_out)
+    ob, ms = to_device(case, dev)
+    lat = api.Lattice.cubic(case.cfg.a, case.cfg.hmax, case.cfg.centering, device=dev)
+    om = torch.tensor(case.om, dtype=torch.float32, device=dev)
+    solver = EMSolver(env["h"], GEOM, lat, ob, ms, om, EMConfig(eps_final=1.0, n_em=n_em, n_sinkhorn=n_sk,
+                                                                c_out=case.c_out))
+    t = lambda a, s: torch.tensor(a.reshape(s), dtype=torch.float32, device=dev).contiguous()
+    R, x = t(R0, (-1, 9)), t(x0, (-1, 3))
+    out = solver.run(R, x)
+    torch.cuda.synchronize()
+    assert env["h"].device_status() == 0
+    Rg = R.cpu().numpy().reshape(-1, 3, 3).astype(np.float64)
+    xg = x.cpu().numpy().astype(np.float64)
+    mis = _mis_deg(Rg, ref["R"])
+    assert np.all(mis < 1e-3), mis.max()
+    assert np.abs(xg - ref["x"]).max() < 1e-3
+    sure = ref["margin"] > 1e-3
+    assert sure.mean() > 0.5
+    np.testing.assert_array_equal(out["assign"].cpu().numpy()[sure], ref["assign"][sure])
+
+
+@pytest.fixture(scope="module")
+def batched():
+    return make_case(sg.CONFIGS["batched"], seed=0)
+
+
+def test_mstep_full_size_sampled_grains_match_oracle(env, batched):
+    """1000 grains, 90 rotations, 70% uneven outliers: the M-step of every grain
+    in one GPU call, from E-step potentials the oracle computes (one per-angle
+    Sinkhorn iteration on every block, model list 0.2 deg / 0.05 mm off the
+    truth); the oracle's M-step of 20 sampled grains (each with its own model
+    spots against every observed spot of their angles) gives the same poses
+    within 1e-3 deg and 1e-3 mm."""
+    from _cases import block_slices, oracle_parallel
+    torch, api, dev = env["torch"], env["api"], env["dev"]
+    case = batched
+    R0, x0 = _perturbed(case, 41, 0.2, 0.05)
+    fw = oracle.forward(GEOM, case.planes, R0, x0, case.om)
+    for k in ("ray", "spot", "center"):
+        fw[k] = f32(fw[k])
+    case.fw = fw
+    T, eps = case.cfg.T, 1.0
+    calls = []
+    for t in range(T):
+        si, sj = block_slices(case, t)
+        calls.append(("sinkhorn", (GEOM.D, case.obs.p[si], [0, si.stop - si.start], [0, sj.stop - sj.start],
+                                   fw["center"][sj], fw["ray"][sj, :3], eps, case.c_out, 1, 0.4, 1), {}))
+    res = oracle_parallel(calls)
+    f = f32(np.concatenate([r[0] for r in res]))
+    g = f32(np.concatenate([r[1] for r in res]))
+    ob, ms = to_device(case, dev)
+    lat = api.Lattice.cubic(case.cfg.a, case.cfg.hmax, case.cfg.centering, device=dev)
+    t_ = lambda a, s: torch.tensor(np.asarray(a).reshape(s), dtype=torch.float32, device=dev).contiguous()
+    R, x = t_(R0, (-1, 9)), t_(x0, (-1, 3))
+    api.mstep(env["h"], GEOM, lat, ob, ms, t_(f, (-1,)), t_(g, (-1,)), eps, t_(case.om, (-1,)), R, x)
+    torch.cuda.synchronize()
+    assert env["h"].device_status() == 0
+    Rg = R.cpu().numpy().reshape(-1, 3, 3).astype(np.float64)
+    xg = x.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(42)
+    pick = np.sort(rng.choice(len(R0), 20, replace=False))
+    sel = np.isin(fw["grain"], pick)
+    remap = {int(n): k for k, n in enumerate(pick)}
+    J_off = np.r_[0, np.cumsum(np.bincount(fw["t"][sel], minlength=T))]
+    grain = np.array([remap[int(n)] for n in fw["grain"][sel]], np.int32)
+    Ro, xo, _ = oracle.mstep(GEOM, case.planes, case.om, case.obs.p, case.obs.I_off, J_off, grain, fw["plane"][sel],
+                             fw["center"][sel], fw["ray"][sel, :3], f, g[sel], eps, R0[pick], x0[pick])
+    mis = _mis_deg(Rg[pick], Ro)
+    assert np.all(mis < 1e-3), mis.max()
+    assert np.abs(xg[pick] - xo).max() < 1e-3
+    assert np.abs(xo - x0[pick]).max() > 1e-3  # the step moved the grains
+
+
 def test_em_recovers_1000_grains(env):
     """1000 grains, 90 rotations over 360 deg, 70% uneven outliers.  From
     prototypes within ~0.2 deg / 0.05 mm of the truth, the annealed solve

@@ -190,3 +190,32 @@ def test_autograd_function_at_nonzero_axis_angle(env):
     assert fw["J_off"][-1] > 0
     np.testing.assert_allclose(gw, FD[:, :3], rtol=1e-3, atol=1e-4 * np.abs(FD[:, :3]).max())
     np.testing.assert_allclose(gx, FD[:, 3:], rtol=1e-3, atol=1e-4 * np.abs(FD[:, 3:]).max())
+
+
+@pytest.mark.parametrize("name,n_grains,T,seed", [("tiny", None, None, 21), ("medium", 40, 10, 22)])
+def test_mstep_adjoint_parity(env, name, n_grains, T, seed):
+    """The adjoint M-step (damped Gauss-Newton on the OT-weighted cost, plan
+    held at the E-step) equals the oracle's: 4 steps from poses 0.2 deg /
+    0.1 mm off the truth, within 1e-3 deg and 1e-3 mm, and it moves the grains."""
+    torch, api, dev = env["torch"], env["api"], env["dev"]
+    case, R0, x0, f, g, eps = _estep_case(sg.CONFIGS[name], seed, n_grains, T)
+    ob, ms = to_device(case, dev)
+    lat = api.Lattice.cubic(case.cfg.a, case.cfg.hmax, case.cfg.centering, device=dev)
+    t = lambda a: torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous()
+    R, x = t(R0.reshape(-1, 9)), t(x0)
+    norms = torch.zeros(len(x0), 2, device=dev)
+    api.mstep_adjoint(env["h"], GEOM, lat, ob, ms, t(f), t(g), eps, t(case.om), R, x, n_steps=4, lam=1e-3,
+                      step_norms=norms)
+    torch.cuda.synchronize()
+    assert env["h"].device_status() == 0
+    Rg = R.cpu().numpy().reshape(-1, 3, 3).astype(np.float64)
+    xg = x.cpu().numpy().astype(np.float64)
+    fw, obs = case.fw, case.obs
+    Ro, xo, no = oracle.mstep_adjoint(GEOM, case.planes, case.om, obs.p, obs.I_off, fw["J_off"], fw["grain"],
+                                      fw["plane"], fw["center"], fw["ray"][:, :3], f, g, eps, R0, x0, n_steps=4,
+                                      lam=1e-3)
+    assert np.all(_misorientation_deg(Rg, Ro) < 1e-3), _misorientation_deg(Rg, Ro).max()
+    assert np.abs(xg - xo).max() < 1e-3
+    assert np.abs(xo - x0).max() > 1e-3
+    # the steps shrink: the last step is far below the first move
+    assert float(norms[:, 0].max()) < 0.5 * np.abs(xo - x0).max() + 1e-4

@@ -127,40 +127,102 @@ def test_sinkhorn_warm_start_continues(env):
     np.testing.assert_allclose(b["g"].cpu().numpy(), g, atol=TOL * (np.abs(g).max() + 1))
 
 
-def test_sinkhorn_full_size_rows_and_marginals(env):
-    """1000 grains, 90 angles, 70% uneven outliers.  One iteration from zero:
-    sampled rows equal the oracle's row update of their own angle block.
-    200 iterations: row marginals converge (a property at any size)."""
+def test_sinkhorn_exact_fallback_is_taken_and_matches(env):
+    """At eps = 0.02 mm^2 the outlier-column term (2^-162 after the shift) and
+    every pair of an observed spot far from all model spots underflow the
+    shifted fast sum of the row pass, so those rows take the exact
+    log-sum-exp path; the device count proves it ran and the potentials still
+    equal the oracle's.  The column pass always keeps its unmatched-row term
+    (cost 0), so its exact path is reached without dustbins: the unbalanced
+    mode at the same temperature, where model spots far from every observed
+    spot underflow, again against the oracle."""
+    case = make_case(sg.CONFIGS["tiny"], seed=15)
+    env["h"].exact_lse_count()  # clear
+    gpu, ref, eps = _run_both(env, case, 30, eps=0.02)
+    rows, cols = env["h"].exact_lse_count()
+    assert rows > 0, (rows, cols)
+    for k in ("f", "g", "dust"):
+        err = np.abs(gpu[k] - ref[k])
+        assert np.all(err <= TOL * (np.abs(ref[k]) + eps)), (k, float((err / (TOL * (np.abs(ref[k]) + eps))).max()))
+    gpu, ref = _run_unbalanced(env, case, 30, 0.02, 4.0, 4.0)
+    rows, cols = env["h"].exact_lse_count()
+    assert rows > 0 and cols > 0, (rows, cols)
+    for k in ("f", "g"):
+        err = np.abs(gpu[k] - ref[k])
+        assert np.all(err <= TOL * (np.abs(ref[k]) + 0.02)), (k, float((err / (TOL * (np.abs(ref[k]) + 0.02))).max()))
+    # and at eps = 1 nothing underflows
+    _run_both(env, case, 5, eps=1.0)
+    assert env["h"].exact_lse_count() == (0, 0)
+
+
+@pytest.fixture(scope="module")
+def batched():
+    """The 1000-grain / 90-rotation / 70%-uneven-outlier workload, made by the
+    oracle's forward model (model list at the truth)."""
+    return make_case(sg.CONFIGS["batched"], seed=0)
+
+
+def test_sinkhorn_full_size_per_angle_blocks_match_oracle(env, batched):
+    """1000 grains, 90 angles, 70% uneven outliers, per-angle dustbins (the
+    angle blocks are then independent problems): 20 iterations of the whole
+    workload on the GPU in one call; the oracle solves two sampled blocks
+    alone.  f, g, the block's dustbin potentials, the hard assignment (where
+    the oracle's margin exceeds 1e-3) and the margins agree element by element."""
+    from _cases import block_slices, oracle_parallel
     api, torch, dev = env["api"], env["torch"], env["dev"]
-    cfg = sg.CONFIGS["batched"]
-    rng = np.random.default_rng(0)
-    R, x = sg.random_grains(cfg, rng)
-    om = sg.omegas(cfg)
+    case = batched
+    ob, ms = to_device(case, dev)
+    n_iter, eps, T = 20, case.cfg.eps, case.cfg.T
+    out = api.cost_sinkhorn(env["h"], GEOM, ob, ms, eps, case.c_out, n_iter, dust_mode=1, harvest=True)
+    torch.cuda.synchronize()
+    assert env["h"].device_status() == 0
+    gpu = {k: v.cpu().numpy() for k, v in out.items()}
+    nI, nJ = np.diff(case.obs.I_off), np.diff(case.fw["J_off"])
+    blocks = [int(t) for t in np.argsort(nI * nJ)[:2]]
+    calls = []
+    for t in blocks:
+        si, sj = block_slices(case, t)
+        args = (GEOM.D, case.obs.p[si], [0, si.stop - si.start], [0, sj.stop - sj.start], case.fw["center"][sj],
+                case.fw["ray"][sj, :3], eps, case.c_out, 1, 0.4, n_iter)
+        calls.append(("sinkhorn", args, {}))
+    res = oracle_parallel(calls)
+    for t, (f, g, fd, gd, _) in zip(blocks, res):
+        si, sj = block_slices(case, t)
+        h = oracle.harvest(GEOM.D, case.obs.p[si], [0, si.stop - si.start], [0, sj.stop - sj.start],
+                           case.fw["center"][sj], case.fw["ray"][sj, :3], eps, case.c_out, 1, 0.4, f, g, fd, gd)
+        for name, got, want in (("f", gpu["f"][si], f), ("g", gpu["g"][sj], g),
+                                ("dust", gpu["dust"][[t, T + t]], np.r_[fd, gd])):
+            err = np.abs(got.astype(np.float64) - want)
+            lim = TOL * (np.abs(want) + eps)
+            assert np.all(err <= lim), (t, name, float((err / lim).max()))
+        sure = h["margin"] > 1e-3
+        assert sure.mean() > 0.5
+        a = gpu["assign"][si]
+        want_a = np.where(h["assign"] >= 0, h["assign"] + sj.start, -1)
+        np.testing.assert_array_equal(a[sure], want_a[sure])
+        np.testing.assert_allclose(gpu["margin"][si], h["margin"], atol=1e-4)
+
+
+def test_sinkhorn_full_size_global_rows_and_marginals(env, batched):
+    """The same workload with the global dustbins: one iteration from zero
+    gives, for sampled rows, the oracle's row update of their own angle block
+    with the dustbin terms at zero; after 200 iterations the row and column
+    marginals converge (a property at any size)."""
+    api, torch, dev = env["api"], env["torch"], env["dev"]
+    case = batched
+    ob, ms = to_device(case, dev)
     h = env["h"]
-    lat = api.Lattice.cubic(cfg.a, cfg.hmax, cfg.centering, device=dev)
-    ms = api.forward(h, GEOM, lat, torch.tensor(R, device=dev), torch.tensor(x, device=dev),
-                     torch.tensor(om, device=dev))
-    J_off = ms.J_off.cpu().numpy()
-    t_j = ms.angle[:ms.n].cpu().numpy()
-    det = ms.spot[:ms.n, 3].cpu().numpy().astype(int)
-    spot = ms.spot[:ms.n, :3].cpu().numpy().astype(np.float64)
-    obs = sg.observe(GEOM, cfg, t_j, det, spot, rng)
-    ob = api.ObsSpots.from_numpy(obs.p, obs.I_off, device=dev)
-    msn = ms.truncated()
-    c_out = api.c_out_for(cfg.sigma_mm, GEOM.D)
-    one = api.cost_sinkhorn(h, GEOM, ob, msn, 1.0, c_out, 1, harvest=False)
+    one = api.cost_sinkhorn(h, GEOM, ob, ms, 1.0, case.c_out, 1, harvest=False)
     f1 = one["f"].cpu().numpy()
-    p32 = ob.p[:, :3].cpu().numpy().astype(np.float64)
-    c32 = msn.center[:, :3].cpu().numpy().astype(np.float64)
-    r32 = msn.ray[:, :3].cpu().numpy().astype(np.float64)
-    for t in rng.choice(cfg.T, 4, replace=False):
-        i0, i1 = obs.I_off[t], obs.I_off[t + 1]
-        j0, j1 = J_off[t], J_off[t + 1]
+    rng = np.random.default_rng(3)
+    for t in rng.choice(case.cfg.T, 4, replace=False):
+        i0, i1 = case.obs.I_off[t], case.obs.I_off[t + 1]
+        j0, j1 = case.fw["J_off"][t], case.fw["J_off"][t + 1]
         sel = rng.choice(np.arange(i0, i1), 16, replace=False)
-        fo, *_ = oracle.sinkhorn(GEOM.D, p32[sel], [0, len(sel)], [0, j1 - j0], c32[j0:j1], r32[j0:j1], 1.0,
-                                 c_out, 0, 0.4, 1)
+        fo, *_ = oracle.sinkhorn(GEOM.D, case.obs.p[sel], [0, len(sel)], [0, j1 - j0], case.fw["center"][j0:j1],
+                                 case.fw["ray"][j0:j1, :3], 1.0, case.c_out, 0, 0.4, 1)
         np.testing.assert_allclose(f1[sel], fo, atol=TOL * (np.abs(fo).max() + 1.0))
-    full = api.cost_sinkhorn(h, GEOM, ob, msn, 1.0, c_out, 200, harvest=True, col_harvest=True)
+    full = api.cost_sinkhorn(h, GEOM, ob, ms, 1.0, case.c_out, 200, harvest=True, col_harvest=True)
     torch.cuda.synchronize()
     assert h.device_status() == 0
     me = full["marg_err"].cpu().numpy()
@@ -189,3 +251,59 @@ def test_autotune_picks_valid_shapes(env):
     assert 0 <= r < 4 and 0 <= c < 4
     assert all(a > 0 and b > 0 for a, b in times)
     assert times[r][0] == min(a for a, _ in times) and times[c][1] == min(b for _, b in times)
+
+
+def _run_unbalanced(env, case, n_iter, eps, kappa, lam):
+    api = env["api"]
+    ob, ms = to_device(case, env["dev"])
+    out = api.cost_sinkhorn(env["h"], GEOM, ob, ms, eps, case.c_out, n_iter, dust_mode=2, harvest=True,
+                            col_harvest=True, kappa=kappa, lam=lam)
+    env["torch"].cuda.synchronize()
+    assert env["h"].device_status() == 0
+    gpu = {k: v.cpu().numpy().astype(np.float64) if v.dtype.is_floating_point else v.cpu().numpy()
+           for k, v in out.items()}
+    fw, obs = case.fw, case.obs
+    f, g = oracle.sinkhorn_unbalanced(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3], eps,
+                                      kappa, lam, n_iter)
+    h = oracle.harvest_unbalanced(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3], eps, f, g)
+    return gpu, dict(f=f, g=g, **h)
+
+
+@pytest.mark.parametrize("kappa,lam", [(2.0, 8.0), (50.0, 0.5)])
+def test_sinkhorn_unbalanced_matches_oracle(env, kappa, lam):
+    """Unbalanced OT (Algorithm UnbalancedOT, no dustbins, KL-relaxed
+    marginals) on 60 grains x 8 angles with ragged multi-tile blocks: f, g
+    within the Sinkhorn tolerance, hard assignments (-1 where a row keeps less
+    than half its mass) equal where the oracle's margin exceeds 1e-3, column
+    masses within 1e-4."""
+    case = make_case(sg.CONFIGS["medium"], seed=16, n_grains=60, T=8)
+    eps = 1.0
+    gpu, ref = _run_unbalanced(env, case, 40, eps, kappa, lam)
+    for k in ("f", "g"):
+        err = np.abs(gpu[k] - ref[k])
+        lim = TOL * (np.abs(ref[k]) + eps)
+        assert np.all(err <= lim), (k, float((err / lim).max()))
+    sure = (ref["margin"] > 1e-3) & (np.abs(ref["rowmass"] - 0.5) > 1e-3)
+    assert sure.mean() > 0.5
+    np.testing.assert_array_equal(gpu["assign"][sure], ref["assign"][sure])
+    np.testing.assert_allclose(gpu["margin"], ref["margin"], atol=1e-4)
+    np.testing.assert_allclose(gpu["q"], ref["q"], atol=1e-4)
+    assert (ref["assign"] == -1).any() and (ref["assign"] >= 0).any()
+
+
+def test_sinkhorn_unbalanced_empty_blocks(env):
+    """Unbalanced mode with an angle block that has no observed spots and one
+    that has no model spots (their potentials stay 0)."""
+    case = make_case(sg.CONFIGS["tiny"], seed=17)
+    obs, fw = case.obs, case.fw
+    keep_i = obs.t != 3
+    obs.p, obs.t, obs.det, obs.truth = obs.p[keep_i], obs.t[keep_i], obs.det[keep_i], obs.truth[keep_i]
+    obs.I_off = np.r_[0, np.cumsum(np.bincount(obs.t, minlength=case.cfg.T))]
+    keep_j = fw["t"] != 6
+    for k in ("grain", "plane", "ray", "spot", "center", "det", "t"):
+        fw[k] = fw[k][keep_j]
+    fw["J_off"] = np.r_[0, np.cumsum(np.bincount(fw["t"], minlength=case.cfg.T))]
+    gpu, ref = _run_unbalanced(env, case, 30, 1.0, 5.0, 5.0)
+    for k in ("f", "g"):
+        err = np.abs(gpu[k] - ref[k])
+        assert np.all(err <= TOL * (np.abs(ref[k]) + 1.0)), k

@@ -632,3 +632,199 @@ def test_refresh_equals_forward_at_the_same_pose(tiny):
             np.testing.assert_allclose(ray2[j], fw2["ray"][key2[k]], rtol=0, atol=1e-13)
             np.testing.assert_allclose(ce2[j], fw2["center"][key2[k]], rtol=0, atol=1e-13)
     assert hits > 0.8 * len(fw["t"])
+
+
+# ------------------------------------------------------------ start grid
+
+def _mat_to_quat(R):
+    """Unit quaternions (w >= 0) of rotation matrices (Shepperd's method)."""
+    out = np.zeros((len(R), 4))
+    for n, M in enumerate(R):
+        tr = np.trace(M)
+        cand = [1 + tr, 1 + 2 * M[0, 0] - tr, 1 + 2 * M[1, 1] - tr, 1 + 2 * M[2, 2] - tr]
+        k = int(np.argmax(cand))
+        v = math.sqrt(cand[k]) / 2
+        if k == 0:
+            q = [v, (M[2, 1] - M[1, 2]) / (4 * v), (M[0, 2] - M[2, 0]) / (4 * v), (M[1, 0] - M[0, 1]) / (4 * v)]
+        elif k == 1:
+            q = [(M[2, 1] - M[1, 2]) / (4 * v), v, (M[0, 1] + M[1, 0]) / (4 * v), (M[0, 2] + M[2, 0]) / (4 * v)]
+        elif k == 2:
+            q = [(M[0, 2] - M[2, 0]) / (4 * v), (M[0, 1] + M[1, 0]) / (4 * v), v, (M[1, 2] + M[2, 1]) / (4 * v)]
+        else:
+            q = [(M[1, 0] - M[0, 1]) / (4 * v), (M[0, 2] + M[2, 0]) / (4 * v), (M[1, 2] + M[2, 1]) / (4 * v), v]
+        q = np.array(q)
+        out[n] = q if q[0] >= 0 else -q
+    return out
+
+
+def test_start_grid_is_uniform_and_in_the_cubic_fundamental_zone():
+    """Section "Single-grain fitting": quasi-uniform starts restricted by the
+    lattice symmetry.  (1) The full spiral's second moments are those of the
+    uniform distribution on the unit quaternions, E[q_a q_b] = delta_ab / 4.
+    (2) With the cubic restriction, every kept orientation lies in the cubic
+    fundamental zone as it is usually written in Rodrigues space (|r_i| <=
+    sqrt(2) - 1 and |r_1| + |r_2| + |r_3| <= 1, r = q_v / q_w), and 1/24 of the
+    spiral is kept.  (3) Every rotation has a start within the covering radius
+    of a set of that size (symmetry aware).  (4) Positions: the k^3 cell centres."""
+    R, x = oracle.start_grid(96000, sym=1, k=1)
+    q = _mat_to_quat(R)
+    M = np.einsum("na,nb->ab", q * np.sign(q[:, :1] + 1e-300), q * np.sign(q[:, :1] + 1e-300)) / len(q)
+    np.testing.assert_allclose(M, np.eye(4) / 4, atol=2e-3)
+    np.testing.assert_allclose(x, 0.0, atol=0)
+    Rz, _ = oracle.start_grid(96000, sym=24, k=1)
+    assert abs(len(Rz) - 96000 / 24) < 0.02 * 96000 / 24
+    qz = _mat_to_quat(Rz)
+    rod = qz[:, 1:] / qz[:, :1]
+    assert np.all(np.abs(rod) <= math.sqrt(2) - 1 + 1e-9)
+    assert np.all(np.abs(rod).sum(axis=1) <= 1 + 1e-9)
+    # covering: 4000 kept orientations in a zone of volume pi^2/24 (quaternion
+    # half-angle balls); no rotation is farther than 2x the ideal radius
+    rng = np.random.default_rng(5)
+    probes = sg.random_rotations(300, rng)
+    syms = np.array(_cubic_group())
+    worst = 0.0
+    for P in probes:
+        M = np.einsum("kji,jl->kil", Rz, P)
+        best = np.full(len(Rz), 180.0)
+        for S in syms:
+            c = np.clip((np.trace(M @ S, axis1=1, axis2=2) - 1) / 2, -1, 1)
+            best = np.minimum(best, np.degrees(np.arccos(c)))
+        worst = max(worst, best.min())
+    ideal = 2 * math.degrees((math.pi ** 2 / 24 / len(Rz) / (4 / 3 * math.pi)) ** (1 / 3))
+    assert worst < 2 * ideal, (worst, ideal)
+    Rk, xk = oracle.start_grid(2400, sym=24, k=3, cube=6.0)
+    assert len(Rk) == 27 * len(oracle.start_grid(2400, sym=24, k=1)[0])
+    np.testing.assert_allclose(np.unique(xk[:, 0]), [-2.0, 0.0, 2.0], atol=1e-12)
+    np.testing.assert_allclose(Rk[0], Rk[26], atol=0)
+
+
+# ------------------------------------------------------- adjoint M-step
+
+def _one_grain_noiseless(seed=7, T=6):
+    """One grain, |hkl| <= 4, its noiseless spots as the observed spots."""
+    P = oracle.reflections(2.87, 4, 1)
+    rng = np.random.default_rng(seed)
+    R = sg.random_rotations(1, rng)
+    x = rng.uniform(-2, 2, size=(1, 3))
+    om = np.radians(np.arange(T) * 30.0)
+    fw = oracle.forward(GEOM, P, R, x, om)
+    return P, R, x, om, fw
+
+
+def test_adjoint_gn_gradient_matches_finite_differences(tiny):
+    """The gradient of orc_grain_gn at a pose away from the E-step pose (Q held
+    at the E-step plan) equals FP64 central differences of the objective."""
+    P, fw, obs, om = tiny["planes"], tiny["fw"], tiny["obs"], tiny["om"]
+    c, r = fw["center"], fw["ray"][:, :3]
+    f, g, *_ = oracle.sinkhorn(GEOM.D, obs.p, obs.I_off, fw["J_off"], c, r, 2.0, 2.25, 0, 0.4, 30)
+    rng = np.random.default_rng(8)
+    R1 = np.array([_rotvec(rng.normal(size=3) * 0.004) @ a for a in tiny["R"]])
+    x1 = tiny["x"] + rng.normal(size=tiny["x"].shape) * 0.1
+    args = (GEOM, P, om, obs.p, obs.I_off, fw["J_off"], fw["grain"], fw["plane"], c, r, f, g, 2.0)
+    G, H, val = oracle.grain_gn(*args, R1, x1)
+    np.testing.assert_allclose(val, oracle.grain_objective(*args, R1, x1), rtol=1e-12)
+    h = 1e-6
+    FD = np.zeros_like(G)
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        Rp = np.array([_rotvec(e[:3]) @ a for a in R1])
+        Rm = np.array([_rotvec(-e[:3]) @ a for a in R1])
+        FD[:, k] = (oracle.grain_objective(*args, Rp, x1 + e[3:]) - oracle.grain_objective(*args, Rm, x1 - e[3:])) / (2 * h)
+    assert np.abs(G - FD).max() <= 1e-6 * np.abs(G).max()
+    # the matrix is symmetric positive semi-definite
+    np.testing.assert_allclose(H, H.transpose(0, 2, 1), atol=1e-9 * np.abs(H).max())
+    assert np.linalg.eigvalsh(H).min() > -1e-9 * np.abs(H).max()
+
+
+def test_adjoint_gn_matrix_is_jacobian_product_on_noiseless_pairs():
+    """Where every observed spot sits on its model spot (noiseless, plan = the
+    true matching), the Gauss-Newton matrix is exactly 2 D^2 sum_j J_j^T J_j
+    with J_j the Jacobian of the residual rhat_j - r_j in (phi, x), here taken
+    by FP64 central differences."""
+    P, R, x, om, fw = _one_grain_noiseless()
+    p, J_off = fw["spot"], fw["J_off"]
+    c, r = fw["center"], fw["ray"][:, :3]
+    nJ = int(J_off[-1])
+    eps = 1e-4  # the plan is the identity matching to double precision
+    f, g = np.zeros(nJ), np.zeros(nJ)
+    args = (GEOM, P, om, p, J_off, J_off, fw["grain"], fw["plane"], c, r, f, g, eps)
+    G, H, val = oracle.grain_gn(*args, R, x)
+    assert np.abs(G).max() < 1e-6 and val[0] < 1e-12
+
+    def residuals(dtheta):
+        Rn = _rotvec(dtheta[:3]) @ R[0]
+        ray, ce = oracle.refresh(GEOM, P, Rn[None], x + dtheta[3:], om, J_off, fw["grain"], fw["plane"])
+        d = p - ce
+        return (d / np.linalg.norm(d, axis=1, keepdims=True) - ray[:, :3]).ravel()
+
+    h = 1e-6
+    J = np.zeros((3 * nJ, 6))
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        J[:, k] = (residuals(e) - residuals(-e)) / (2 * h)
+    want = 2 * GEOM.D ** 2 * J.T @ J
+    np.testing.assert_allclose(H[0], want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
+
+
+def test_adjoint_mstep_converges_on_noiseless_data():
+    """Started 0.5 deg and 0.3 mm from a noiseless grain, with the plan held at
+    the true matching, the damped Gauss-Newton M-step returns to the truth."""
+    P, R, x, om, fw = _one_grain_noiseless(seed=9)
+    p, J_off = fw["spot"], fw["J_off"]
+    nJ = int(J_off[-1])
+    f, g = np.zeros(nJ), np.zeros(nJ)
+    rng = np.random.default_rng(10)
+    R0 = (_rotvec(rng.normal(size=3) * math.radians(0.5) / math.sqrt(3)) @ R[0])[None]
+    x0 = x + rng.normal(size=3) * 0.3 / math.sqrt(3)
+    Ro, xo, norms = oracle.mstep_adjoint(GEOM, P, om, p, J_off, J_off, fw["grain"], fw["plane"], fw["center"],
+                                         fw["ray"][:, :3], f, g, 1e-4, R0, x0, n_steps=8)
+    M = Ro[0].T @ R[0]
+    assert math.degrees(math.acos(min(1.0, (np.trace(M) - 1) / 2))) < 1e-6
+    assert np.abs(xo - x).max() < 1e-8
+
+
+# ------------------------------------------------------- unbalanced OT
+
+def test_unbalanced_fixed_point_is_the_marginal_kl_condition(tiny):
+    """Problem (B) of App. "Optimal transport variants": at the optimum the
+    potentials and the plan's marginals satisfy f_i = -kappa log(sum_j Q_ij)
+    and g_j = -lambda log(sum_i Q_ij) (a = b = 1), the first-order conditions
+    of the KL-relaxed marginals; the converged log-domain iteration meets them
+    to 1e-9 (kappa on the observed rows, lambda on the model columns)."""
+    fw, obs = tiny["fw"], tiny["obs"]
+    for kappa, lam in ((2.0, 8.0), (20.0, 0.5)):
+        f, g = oracle.sinkhorn_unbalanced(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3],
+                                          4.0, kappa, lam, 3000)
+        h = oracle.harvest_unbalanced(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3], 4.0, f,
+                                      g)
+        # rows whose every plan entry underflows double precision are skipped
+        okr, okc = h["rowmass"] > 1e-280, h["q"] > 1e-280
+        assert okr.mean() > 0.8 and okc.mean() > 0.8
+        np.testing.assert_allclose(f[okr], -kappa * np.log(h["rowmass"][okr]), atol=1e-9 * max(1.0, np.abs(f).max()))
+        np.testing.assert_allclose(g[okc], -lam * np.log(h["q"][okc]), atol=1e-9 * max(1.0, np.abs(g).max()))
+
+
+def test_unbalanced_large_kappa_lambda_is_balanced():
+    """kappa, lambda -> infinity gives balanced OT: on a square block with no
+    dustbin mass (frac = 0, |I| = |J|), the converged unbalanced iteration with
+    kappa = lambda = 1e12 gives BalancedOT's plan (potentials equal up to the
+    shift f + s, g - s that leaves a balanced plan unchanged), and the plan's
+    marginals are 1."""
+    rng = np.random.default_rng(2)
+    n = 9
+    p = np.c_[rng.uniform(-30, 30, (n, 2)), -200 * np.ones(n)]
+    c = rng.uniform(-1, 1, (n, 3))
+    r = np.c_[rng.normal(size=(n, 2)) * 0.1, -np.ones(n)]
+    r /= np.linalg.norm(r, axis=1, keepdims=True)
+    eps = 200.0
+    fu, gu = oracle.sinkhorn_unbalanced(200.0, p, [0, n], [0, n], c, r, eps, 1e12, 1e12, 500)
+    fb, gb, fd, gd, _ = oracle.sinkhorn(200.0, p, [0, n], [0, n], c, r, eps, 2.25, 0, 0.0, 500)
+    # the same plan: the potentials differ by one constant shift (f + s, g - s)
+    shift = np.mean(fu - fb)
+    np.testing.assert_allclose(fu - fb, shift, atol=1e-5)
+    np.testing.assert_allclose(gu - gb, -shift, atol=1e-5)
+    h = oracle.harvest_unbalanced(200.0, p, [0, n], [0, n], c, r, eps, fu, gu)
+    np.testing.assert_allclose(h["rowmass"], 1.0, atol=1e-8)
+    np.testing.assert_allclose(h["q"], 1.0, atol=1e-8)
