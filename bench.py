@@ -163,28 +163,56 @@ def em_step(W, api, R, x, stream=None):
     return out
 
 
-def cpu_baseline_sample(W, seconds_hint=15.0):
-    """The FP64 oracle's Sinkhorn on a bounded sample of the same workload:
-    two angle blocks, one full iteration each (row + column update)."""
+def oracle_workload(seed=0):
+    """The 1000-grain workload built by the oracle's forward model (same seeds
+    and generator as the GPU workload), for the CPU-baseline legs."""
     import oracle
-    obs, model = W["obs"], W["model"]
-    J_off = model.J_off.cpu().numpy()
-    c = model.center[:, :3].cpu().numpy().astype(np.float64)
-    r = model.ray[:, :3].cpu().numpy().astype(np.float64)
-    pairs = 0
+    import synthgen as sg
+    cfg = sg.CONFIGS["batched"]
+    geom = sg.Geometry()
+    rng = np.random.default_rng(seed)
+    R, x = sg.random_grains(cfg, rng)
+    om = sg.omegas(cfg)
+    P = oracle.reflections(cfg.a, cfg.hmax, cfg.centering)
+    fw = oracle.forward(geom, P, R, x, om)
+    obs = sg.observe(geom, cfg, fw["t"], fw["det"], fw["spot"], rng)
+    return dict(cfg=cfg, geom=geom, fw=fw, obs=obs, c_out=oracle.c_out_for(cfg.sigma_mm, geom.D))
+
+
+def cpu_baseline_sample(OW, threads=1, blocks=(0, 45)):
+    """The FP64 oracle's Sinkhorn on a bounded sample of the 1000-grain
+    workload: one full iteration (row + column update) over the given angle
+    blocks, on `threads` host threads (OpenMP over angle blocks)."""
+    import oracle
+    obs, fw = OW["obs"], OW["fw"]
+    J_off = fw["J_off"]
+    used = oracle.set_threads(threads)
+    sel_i = np.concatenate([np.arange(obs.I_off[t], obs.I_off[t + 1]) for t in blocks])
+    sel_j = np.concatenate([np.arange(J_off[t], J_off[t + 1]) for t in blocks])
+    I_off = np.r_[0, np.cumsum([obs.I_off[t + 1] - obs.I_off[t] for t in blocks])]
+    J_o = np.r_[0, np.cumsum([J_off[t + 1] - J_off[t] for t in blocks])]
+    pairs = 2 * int(np.sum(np.diff(I_off) * np.diff(J_o)))
     t0 = time.perf_counter()
-    blocks = [0, 45]
-    for t in blocks:
-        i0, i1 = obs.I_off[t], obs.I_off[t + 1]
-        j0, j1 = J_off[t], J_off[t + 1]
-        oracle.sinkhorn(W["geom"].D, obs.p[i0:i1], [0, i1 - i0], [0, j1 - j0], c[j0:j1], r[j0:j1],
-                        W["cfg"].eps, W["c_out"], 0, 0.4, 1)
-        pairs += 2 * (i1 - i0) * (j1 - j0)
+    oracle.sinkhorn(OW["geom"].D, obs.p[sel_i], I_off, J_o, fw["center"][sel_j], fw["ray"][sel_j, :3],
+                    OW["cfg"].eps, OW["c_out"], 0, 0.4, 1)
     dt = time.perf_counter() - t0
-    return dict(value=pairs / dt, unit=UNIT, cores=1, kind="oracle",
-                sample="FP64 C oracle, single thread: 1 Sinkhorn iteration (row + column update) on "
-                       "angle blocks %s of the 1000-grain workload, %d pair evaluations in %.1f s"
-                       % (blocks, pairs, dt))
+    oracle.set_threads(1)
+    cpu = _cpu_model()
+    return dict(value=pairs / dt, unit=UNIT, cores=used, kind="oracle", cpu_model=cpu, nproc=os.cpu_count(),
+                sample="FP64 C oracle on %d thread(s) (OpenMP over angle blocks): 1 Sinkhorn iteration (row + column "
+                       "update) on %d of the 90 angle blocks of the 1000-grain workload, %d pair evaluations in %.1f s"
+                       % (used, len(blocks), pairs, dt))
+
+
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "processor name")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def _found_count(Rk, xk, R, x, tol_deg=0.5, tol_mm=0.5):
@@ -340,24 +368,25 @@ def proposal_cpu_baseline():
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper gives no program) timed
+    on the host cores on a bounded sample of the same workload, whose inputs
+    the oracle's own forward model builds.  Rank 0 only."""
     rank, world, local = _dist_env()
     if rank != 0:
         return 0
-    import torch
-    from paper_2404_06478_gb300 import api
-    import synthgen as sg
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    W = build_workload(dev, 0, api, sg, torch)
-    vals = []
+    OW = oracle_workload(0)
+    vals, samples = [], []
     for _ in range(max(1, args.steps)):
-        vals.append(cpu_baseline_sample(W)["value"])
+        r = cpu_baseline_sample(OW, threads=os.cpu_count() or 1)
+        vals.append(r["value"])
+        samples.append(r)
     v = float(np.mean(vals))
+    r = samples[-1]
     line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, higher_is_better=True, dtype="f64", data="synthetic",
                 config=dict(workload="1000 grains, 90 rotations, 70% uneven outliers, |hkl|<=6; oracle sample"),
-                cpu_baseline=dict(kind="oracle", cores=1, value=v,
-                                  sample="FP64 C oracle, 1 Sinkhorn iteration on 2 angle blocks per step"),
+                cpu_baseline=dict(kind="oracle", cores=r["cores"], value=v, cpu_model=r["cpu_model"],
+                                  sample=r["sample"] + " (per step)"),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
     return 0
@@ -563,7 +592,10 @@ def main():
         if not args.no_cpu_baseline:
             line["proposal"]["cpu_baseline"] = proposal_cpu_baseline()
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(W)
+        OW = oracle_workload(0)
+        one = cpu_baseline_sample(OW, threads=1)
+        allc = cpu_baseline_sample(OW, threads=os.cpu_count() or 1)
+        line["cpu_baseline"] = dict(allc, single_thread=dict(value=one["value"], cores=1, sample=one["sample"]))
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -310,12 +310,14 @@ int laue_autotune(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* 
                   const LaueModelSpots* model, const LaueOTParams* prm, int n_iter, int* choice_host,
                   float* ms_host, void* stream);
 
-/* Diagnostic of laue_cost_sinkhorn (no counterpart in the paper): the number
- * of row and column log-sum-exps that the pair passes recomputed on the exact
- * (running-maximum) path because their fast sum, shifted by the angle block's
- * largest potential, fell below 1e-30, since the last call (modulo 2^32);
- * the counts are cleared.  Synchronises `stream`. */
-int laue_exact_lse_count(laue_handle* h, void* stream, long long* rows_host, long long* cols_host);
+/* Device counters (no counterpart in the paper), accumulated since the last
+ * call on the handle's workspace, then cleared; the first n (<= 3) go to
+ * counts_host: [0] row and [1] column log-sum-exps of laue_cost_sinkhorn's pair
+ * passes recomputed on the exact (running-maximum) path because their fast
+ * sum, shifted by the angle block's largest potential, fell below 1e-30
+ * (modulo 2^32); [2] pair evaluations (one cost and one exponential each) of
+ * laue_single_fit.  Synchronises `stream`. */
+int laue_read_counters(laue_handle* h, void* stream, long long* counts_host, int n);
 
 /* Sets the launch shapes (0..3, as for laue_autotune) of the row and column
  * passes used by later calls on the handle; shape 0 is the default. */

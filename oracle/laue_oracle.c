@@ -529,6 +529,18 @@ void orc_masses(int mode, double frac, int T, const int* I_off, const int* J_off
 
 static double logm(double m) { return m > 0 ? log(m) : -INFINITY; }
 
+/* Threads of the Sinkhorn updates (OpenMP builds only; 1 = sequential). */
+static int orc_nthreads = 1;
+
+int orc_set_threads(int n) {
+    orc_nthreads = n > 0 ? n : 1;
+#ifdef _OPENMP
+    return orc_nthreads;
+#else
+    return 1;
+#endif
+}
+
 /* Algorithm BalancedOT in the log domain on the extended matrix (observed
  * rows + unmatched-model row 0, model columns + outlier column 0), blocked by
  * angle (Q_ij = 0 unless t_i = t_j).  Runs exactly n_iter iterations, or
@@ -552,16 +564,24 @@ int orc_sinkhorn(double D, int T, const int* I_off, const double* p,
     double* buf = (double*)malloc(sizeof(double) * big);
     int it;
     for (it = 0; it < n_iter; ++it) {
-        /* row update: observed rows, then the unmatched-model rows (both from g) */
-        for (int t = 0; t < T; ++t) {
-            int dd = mode ? t : 0;
-            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
-                int n = 0;
-                for (int j = J_off[t]; j < J_off[t + 1]; ++j)
-                    buf[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
-                buf[n++] = (gd[dd] - c_out) / eps;
-                f[i] = -eps * lse(buf, n);
+        /* row update: observed rows, then the unmatched-model rows (both from g);
+         * the angle blocks are independent, so with threads they are shared out
+         * (every f_i is still computed by one thread in the same order) */
+#pragma omp parallel num_threads(orc_nthreads) if (orc_nthreads > 1)
+        {
+            double* b = (double*)malloc(sizeof(double) * big);
+#pragma omp for schedule(dynamic)
+            for (int t = 0; t < T; ++t) {
+                int dd = mode ? t : 0;
+                for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                    int n = 0;
+                    for (int j = J_off[t]; j < J_off[t + 1]; ++j)
+                        b[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                    b[n++] = (gd[dd] - c_out) / eps;
+                    f[i] = -eps * lse(b, n);
+                }
             }
+            free(b);
         }
         for (int d = 0; d < nd; ++d) {
             int j0 = mode ? J_off[d] : 0, j1 = mode ? J_off[d + 1] : nJ;
@@ -571,15 +591,21 @@ int orc_sinkhorn(double D, int T, const int* I_off, const double* p,
             fd[d] = eps * logm(U[d]) - eps * lse(buf, n);
         }
         /* column update: model columns, then the outlier columns (both from f) */
-        for (int t = 0; t < T; ++t) {
-            int dd = mode ? t : 0;
-            for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
-                int n = 0;
-                for (int i = I_off[t]; i < I_off[t + 1]; ++i)
-                    buf[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
-                buf[n++] = fd[dd] / eps;
-                g[j] = -eps * lse(buf, n);
+#pragma omp parallel num_threads(orc_nthreads) if (orc_nthreads > 1)
+        {
+            double* b = (double*)malloc(sizeof(double) * big);
+#pragma omp for schedule(dynamic)
+            for (int t = 0; t < T; ++t) {
+                int dd = mode ? t : 0;
+                for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+                    int n = 0;
+                    for (int i = I_off[t]; i < I_off[t + 1]; ++i)
+                        b[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                    b[n++] = fd[dd] / eps;
+                    g[j] = -eps * lse(b, n);
+                }
             }
+            free(b);
         }
         for (int d = 0; d < nd; ++d) {
             int i0 = mode ? I_off[d] : 0, i1 = mode ? I_off[d + 1] : nI;

@@ -128,6 +128,7 @@ void orc_harvest_unbalanced(double D, int T, const int* I_off, const double* p,
                             const int* J_off, const double* c, const double* r, double eps,
                             const double* f, const double* g, int* assign, double* margin,
                             double* rowmass, double* q);
+int orc_set_threads(int n);
 long orc_start_grid(long n_full, int sym, int k, double cube, long cap, double* R_out, double* x_out);
 
 #ifdef __cplusplus

@@ -94,7 +94,7 @@ SIGNATURES = {
     "laue_autotune": [_vp, _P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams), _i, _vp,
                       _vp, _vp],
     "laue_set_launch_shape": [_vp, _i, _i],
-    "laue_exact_lse_count": [_vp, _vp, _P(ctypes.c_longlong), _P(ctypes.c_longlong)],
+    "laue_read_counters": [_vp, _vp, _P(ctypes.c_longlong), _i],
     "laue_mstep": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots), _vp, _vp,
                    _P(LaueMParams), _vp, _vp, _vp, _i, _vp, _vp],
     "laue_mstep_adjoint": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots), _vp,

@@ -229,12 +229,16 @@ class Handle:
     def set_launch_shape(self, row_shape, col_shape):
         self.check(self.L.laue_set_launch_shape(self.h, int(row_shape), int(col_shape)), "set_launch_shape")
 
+    def counters(self, stream=None):
+        """laue_read_counters: dict of the device counters since the last read."""
+        v = (ctypes.c_longlong * 3)()
+        self.check(self.L.laue_read_counters(self.h, _stream(stream), v, 3), "read_counters")
+        return dict(exact_rows=v[0], exact_cols=v[1], fit_pairs=v[2])
+
     def exact_lse_count(self, stream=None):
-        """(rows, columns) recomputed on the exact log-sum-exp path since the last call."""
-        r, c = ctypes.c_longlong(0), ctypes.c_longlong(0)
-        self.check(self.L.laue_exact_lse_count(self.h, _stream(stream), ctypes.byref(r), ctypes.byref(c)),
-                   "exact_lse_count")
-        return r.value, c.value
+        """(rows, columns) recomputed on the exact log-sum-exp path since the last read."""
+        c = self.counters(stream)
+        return c["exact_rows"], c["exact_cols"]
 
     def device_status(self, stream=None) -> int:
         v = ctypes.c_int(0)

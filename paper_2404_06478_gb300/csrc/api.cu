@@ -419,11 +419,11 @@ extern "C" int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, cons
 
 // ------------------------------------------------------------- autotuner
 
-extern "C" int laue_exact_lse_count(laue_handle* h, void* stream, long long* rows_host, long long* cols_host) {
-    if (!h || !rows_host || !cols_host) return LAUE_ERR_INVALID_ARG;
+extern "C" int laue_read_counters(laue_handle* h, void* stream, long long* counts_host, int n) {
+    if (!h || !counts_host || n < 0 || n > 3) return LAUE_ERR_INVALID_ARG;
     if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set");
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned v[2] = {0u, 0u};
+    unsigned v[4] = {0u, 0u, 0u, 0u};  // exact rows, exact columns, fit pairs (64 bits)
     int* ctrl = (int*)h->ws;
     int rc;
     if ((rc = laue_cuda_check(h, cudaMemcpyAsync(v, ctrl + CTRL_EXACT_ROWS, sizeof(v), cudaMemcpyDeviceToHost, s),
@@ -432,8 +432,9 @@ extern "C" int laue_exact_lse_count(laue_handle* h, void* stream, long long* row
     if ((rc = laue_cuda_check(h, cudaMemsetAsync(ctrl + CTRL_EXACT_ROWS, 0, sizeof(v), s), "clearing counts")))
         return rc;
     if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "synchronise"))) return rc;
-    *rows_host = v[0];
-    *cols_host = v[1];
+    long long all[3] = {(long long)v[0], (long long)v[1],
+                        (long long)((unsigned long long)v[2] | ((unsigned long long)v[3] << 32))};
+    for (int k = 0; k < n; ++k) counts_host[k] = all[k];
     return LAUE_OK;
 }
 

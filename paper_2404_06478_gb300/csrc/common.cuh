@@ -31,6 +31,7 @@ enum CtrlSlot {
     CTRL_SF_DONE = 15,
     CTRL_EXACT_ROWS = 16, // row / column log-sum-exps recomputed on the exact path
     CTRL_EXACT_COLS = 17,
+    CTRL_SF_PAIRS = 18,   // 64-bit count (slots 18-19) of single-fit pair evaluations
     CTRL_SLOTS = 64
 };
 

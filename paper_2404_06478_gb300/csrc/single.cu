@@ -168,11 +168,13 @@ __device__ __forceinline__ float sf_e2(const float4& p, const float* c, const fl
     return fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
 }
 
-// Row normaliser (log2) of observed spot p at angle t over the listed spots.
+// Row normaliser (log2) of observed spot p at angle t over the listed spots;
+// npair counts the pair evaluations of the calling thread.
 __device__ __forceinline__ float sf_row_lse(const SfArgs& a, const SfShared& S, const SfScratch& Z, int t,
-                                            const float4& p, float negK, float dust) {
+                                            const float4& p, float negK, float dust, unsigned long long& npair) {
     Lse2 L;
     L.init(dust);
+    npair += (unsigned)(S.t_off[t + 1] - S.t_off[t]);
     for (int j = S.t_off[t]; j < S.t_off[t + 1]; ++j) {
         float v = negK * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j);
         L.merge(v, 1.0f);
@@ -192,7 +194,8 @@ __device__ float sf_block_sum9(SfShared& S, float* v) {
 }
 
 // One Newton step on x with the plan of the E-step costs.
-__device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK, float dust) {
+__device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK, float dust,
+                          unsigned long long& npair) {
     float acc[9];
     for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
     for (int t = 0; t < a.T; ++t) {
@@ -204,7 +207,8 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
         float gc[3] = {0, 0, 0}, hc[6] = {0, 0, 0, 0, 0, 0};
         for (int i = a.I_off[t] + threadIdx.x; i < a.I_off[t + 1]; i += blockDim.x) {
             float4 p = a.p[i];
-            float l = sf_row_lse(a, S, Z, t, p, negK, dust);
+            float l = sf_row_lse(a, S, Z, t, p, negK, dust, npair);
+            npair += (unsigned)(j1 - j0);
             for (int j = j0; j < j1; ++j) {
                 float v = negK * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j) - l;
                 if (v < kSfSkip) continue;
@@ -245,14 +249,16 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
 
 // v_j = sum_i Q_ij rhat_ij (rhat at the current x), or with massonly the
 // column mass q_j, for every listed spot; one warp per spot, fixed order.
-__device__ void sf_columns(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK, float dust, bool massonly) {
+__device__ void sf_columns(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK, float dust, bool massonly,
+                           unsigned long long& npair) {
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int t = 0; t < a.T; ++t) {
         int j0 = S.t_off[t], j1 = S.t_off[t + 1];
         if (j0 == j1) continue;
         int i0 = a.I_off[t], ni = a.I_off[t + 1] - i0;
         int nl = min(ni, a.icap);
-        for (int k = threadIdx.x; k < nl; k += blockDim.x) Z.lse[k] = sf_row_lse(a, S, Z, t, a.p[i0 + k], negK, dust);
+        for (int k = threadIdx.x; k < nl; k += blockDim.x)
+            Z.lse[k] = sf_row_lse(a, S, Z, t, a.p[i0 + k], negK, dust, npair);
         __syncthreads();
         float sg, cg;
         sincosf(a.omega[t], &sg, &cg);
@@ -261,7 +267,8 @@ __device__ void sf_columns(const SfArgs& a, SfShared& S, const SfScratch& Z, flo
             float s0 = 0.f, s1 = 0.f, s2 = 0.f;
             for (int k = lane; k < ni; k += 32) {
                 float4 p = a.p[i0 + k];
-                float l = k < nl ? Z.lse[k] : sf_row_lse(a, S, Z, t, p, negK, dust);
+                float l = k < nl ? Z.lse[k] : sf_row_lse(a, S, Z, t, p, negK, dust, npair);
+                ++npair;
                 float v = negK * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j) - l;
                 if (v < kSfSkip) continue;
                 float Q = ex2(v);
@@ -355,6 +362,7 @@ __global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
         __syncthreads();
         sf_cut(a, S, Z);
         bool overflow = S.overflow != 0;
+        unsigned long long npair = 0;
         for (int k = 0; k < a.k_max; ++k) {
             if (k > 0 && a.recut) {  // the visible set at the pose of this step
                 sf_cut(a, S, Z);
@@ -366,12 +374,12 @@ __global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
             if (threadIdx.x == 0) S.stop = 0;
             __syncthreads();
             for (int q = 0; q < a.n_newton; ++q) {
-                sf_newton(a, S, Z, negK, dust);
+                sf_newton(a, S, Z, negK, dust, npair);
                 if (S.stop) break;
             }
             __syncthreads();
             if (a.n_mm > 0) {
-                sf_columns(a, S, Z, negK, dust, false);
+                sf_columns(a, S, Z, negK, dust, false, npair);
                 sf_mm(a, S, Z, M6);
             }
         }
@@ -380,7 +388,8 @@ __global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
         overflow |= S.overflow != 0;
         sf_refresh(a, S, Z);
         float negK = -a.G.D * a.G.D * log2e / a.eps_final, dust = -a.c_out * log2e / a.eps_final;
-        sf_columns(a, S, Z, negK, dust, true);
+        sf_columns(a, S, Z, negK, dust, true, npair);
+        atomicAdd((unsigned long long*)(a.ctrl + CTRL_SF_PAIRS), npair);
         if (threadIdx.x == 0) {
             int nun = 0;
             for (int j = 0; j < S.n_spots; ++j) nun += Z.v[3 * j] < 0.5f;
