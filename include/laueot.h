@@ -225,6 +225,33 @@ double laue_c_out(double sigma_mm, double D);
  * factor <= 0. */
 double laue_anneal_eps(double eps_final, int n_em, int k, double factor);
 
+/* Reciprocal basis of a lattice with cell edges a, b, c (Angstrom) and angles
+ * alpha, beta, gamma (degrees; paper Section "Crystallographic planes": the
+ * reciprocal vectors g = B hkl, d = 1 / |g|).  Convention: the direct basis has
+ * a1 along x, a2 in the xy plane at gamma from a1, a3 completing the cell;
+ * B_host (3 x 3, row-major) holds b1, b2, b3 as columns with a_i . b_j =
+ * delta_ij (no 2 pi).  A grain's R maps this crystal frame to the sample
+ * frame.  Host function.  LAUE_ERR_INVALID_ARG for a non-positive edge or
+ * angles that do not close a cell. */
+int laue_reciprocal_basis(double a, double b, double c, double alpha_deg, double beta_deg, double gamma_deg,
+                          double* B_host);
+
+/* Plausible plane set of any lattice (the paper takes the set {(w_m, d_m)} as
+ * an input, Section "Tomography experiments"): from the reciprocal basis
+ * B_host (3 x 3 row-major, laue_reciprocal_basis) and a host list of the n
+ * allowed reflections hkl_host (n x 3, e.g. every hkl within a bound that the
+ * space group's reflection conditions allow; order and Friedel mates free).
+ * Reflections on one line through the origin share a ray, so there is one
+ * entry per line: its multiples in the list must be m0, 2 m0, ..., nh m0 of
+ * the line's primitive vector p (first nonzero index positive); the entry's
+ * base reflection is g0 = m0 p, w = B g0 / |B g0|, d0 = 1 / |B g0|, nharm = nh.
+ * Order: |B g0|^2 ascending (equal within 1e-9 relative), then g0
+ * descending.  Outputs as laue_reflections (w_d0_host cap x 4, nharm_host cap,
+ * hkl0_host cap x 3, may be NULL); LAUE_ERR_CAPACITY if *M > cap,
+ * LAUE_ERR_INVALID_ARG when a line's multiples are not of that form. */
+int laue_reflections_hkl(const double* B_host, const int* hkl_host, int n, int cap, float* w_d0_host,
+                         int* nharm_host, int* hkl0_host, int* M);
+
 /* ---- hot path ---------------------------------------------------------- */
 
 /* Forward Laue model and cut (paper Eqs. ray_mnt, s_mnt, wavelength,
@@ -316,8 +343,43 @@ int laue_autotune(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* 
  * passes recomputed on the exact (running-maximum) path because their fast
  * sum, shifted by the angle block's largest potential, fell below 1e-30
  * (modulo 2^32); [2] pair evaluations (one cost and one exponential each) of
- * laue_single_fit.  Synchronises `stream`. */
+ * laue_single_fit; [3] pair evaluations of the row and column passes of
+ * laue_cost_sinkhorn (after the exact skipping).  Synchronises `stream`. */
 int laue_read_counters(laue_handle* h, void* stream, long long* counts_host, int n);
+
+/* Exact underflow skipping in the Sinkhorn pair passes (no counterpart in the
+ * paper; on by default): within each angle block the spots are ordered by
+ * direction, each run of 128 pairs carries a cone bounding its directions,
+ * and a pass skips a (tile, staged chunk) combination when the cones prove
+ * that every shifted exponent is below -130, i.e. every plan entry flushes to
+ * exactly 0; the potentials are bit-identical either way.  enable = 0 turns
+ * the skipping off (the ordering stays).  Read the evaluated pairs with
+ * laue_read_counters. */
+int laue_set_pair_skipping(laue_handle* h, int enable);
+
+/* Sparse E-step (paper Section "Working with sparse assignment matrices":
+ * only the rho nearest neighbours of each spot carry assignment weight).
+ * Support: each model spot j keeps N(j), the rho observed spots of its angle
+ * block with the smallest pair cost C_ij (fewer when the block has fewer;
+ * ties to the lower observed index, costs compared in float); every other
+ * observed-model entry of the plan is 0, the outlier column and the
+ * unmatched-model row stay dense.  Then Algorithm BalancedOT as in
+ * laue_cost_sinkhorn restricted to that support:
+ *   f_i = -eps LSE({(g_j - C_ij)/eps : i in N(j)} u {(g_0 - c_out)/eps})
+ *   g_j = -eps LSE({(f_i - C_ij)/eps : i in N(j)} u {f_0/eps})
+ * with the dustbin updates of laue_cost_sinkhorn, row update first, n_iter
+ * iterations.  Arguments and outputs as for laue_cost_sinkhorn (assign and
+ * margin over the row's support and the outlier column; q over the column's
+ * support); dust_mode 0 or 1 (the unbalanced mode is not offered here);
+ * rho 1..64.  nbr (optional, device, model->n x rho ints): N(j) in order of
+ * increasing cost, -1 past its end.  Needs a workspace of
+ * laue_sparse_workspace_size bytes (16 rho |J| + 16 (|I| + |J|) bytes plus
+ * small tables).  Asynchronous. */
+int laue_sparse_workspace_size(int T, int n_obs, int n_model, int rho, size_t* bytes);
+int laue_cost_sinkhorn_sparse(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* obs,
+                              const LaueModelSpots* model, const LaueOTParams* prm, int rho, float* f,
+                              float* g, float* dust, int* assign, float* margin, float* marg_err, float* q,
+                              int* nbr, void* stream);
 
 /* Sets the launch shapes (0..3, as for laue_autotune) of the row and column
  * passes used by later calls on the handle; shape 0 is the default. */
@@ -392,15 +454,18 @@ int laue_axis_angle_vjp(laue_handle* h, const float* w, const float* grad, const
  * Alexa (CVPR 2022): n_full unit quaternions q_i (s = i + 1/2,
  * q = (sqrt(s/n) sin(2 pi s/sqrt 2), sqrt(s/n) cos(2 pi s/sqrt 2),
  *      sqrt(1 - s/n) sin(2 pi s/psi), sqrt(1 - s/n) cos(2 pi s/psi)),
- * psi^4 = psi + 4).  sym = 24 keeps, in spiral order, the points of the cubic
- * fundamental zone (scalar part the largest |<q, g>| over the cubic group);
- * sym = 1 keeps every point.  Each kept orientation is paired with the k^3
+ * psi^4 = psi + 4).  sym = 24 keeps, in spiral order, the points of the
+ * fundamental zone of the cubic group 432 (scalar part the largest |<q, g>|
+ * over the group), sym = 6 of the trigonal group 32 and sym = 12 of the
+ * hexagonal group 622 (n-fold axis along z, a 2-fold axis along x: the
+ * frame of laue_reciprocal_basis for hexagonal cells); sym = 1 keeps every
+ * point.  Each kept orientation is paired with the k^3
  * cell centres of the cube of side cube_mm centred at the origin (first
  * coordinate slowest): start s = o k^3 + p.  Writes min(S, cap) starts
  * (R_out cap x 9 row-major, x_out cap x 3; device) and *S_host = S (cap = 0
  * only counts).  Synchronises `stream`.  Needs a workspace of at least
  * 4.5 KiB + 4 (n_full / 1024 + 1) bytes.  Errors: LAUE_ERR_INVALID_ARG (sym
- * not 1 or 24, k outside 1..64, n_full < 0), LAUE_ERR_WORKSPACE. */
+ * not 1, 6, 12 or 24, k outside 1..64, n_full < 0), LAUE_ERR_WORKSPACE. */
 int laue_start_grid(laue_handle* h, long long n_full, int sym, int k, float cube_mm, long long cap, float* R_out,
                     float* x_out, long long* S_host, void* stream);
 
@@ -473,7 +538,7 @@ typedef struct {
     float anneal_single; /* eps_init / eps_final of the single-grain fits (<= 0: 100) */
     int recut_single;    /* nonzero: the fits re-list visible spots every step */
     long long grid_n;    /* start grid (used when startR is NULL): spiral points */
-    int grid_sym;        /* 1 or 24 (cubic fundamental zone) */
+    int grid_sym;        /* 1, 6, 12 or 24: the rotation group whose fundamental zone the grid covers */
     int grid_k;          /* k^3 positions per orientation */
     float grid_cube;     /* side of the sample cube (mm) */
     int mstep_kind;      /* 0: laue_mstep (Newton on x, MM on R); 1: laue_mstep_adjoint */

@@ -148,6 +148,16 @@ def pair_cost(p, c, r, D):
     return lib().orc_pair_cost(_d(_f64(p)), _d(_f64(c)), _d(_f64(r)), ctypes.c_double(D))
 
 
+def pair_costs(p, c, r, D):
+    """orc_pair_cost of the rows of (n, 3) arrays p, c, r (broadcast to n)."""
+    p, c, r = np.broadcast_arrays(np.asarray(p, np.float64).reshape(-1, 3), np.asarray(c, np.float64).reshape(-1, 3),
+                                  np.asarray(r, np.float64).reshape(-1, 3))
+    p, c, r = (np.ascontiguousarray(a) for a in (p, c, r))
+    out = np.zeros(len(p))
+    lib().orc_pair_costs(len(p), _d(p), _d(c), _d(r), ctypes.c_double(D), _d(out))
+    return out
+
+
 def masses(mode, frac, I_off, J_off):
     T = len(I_off) - 1
     nd = T if mode else 1
@@ -383,3 +393,47 @@ def set_threads(n):
     """Threads of the oracle's Sinkhorn updates; returns the number in effect
     (1 without OpenMP)."""
     return int(lib().orc_set_threads(int(n)))
+
+
+def reciprocal_basis(a, b, c, alpha, beta, gamma):
+    """Reciprocal basis B (3, 3), columns b1 b2 b3 (Angstrom^-1, no 2 pi)."""
+    B = np.zeros(9)
+    lib().orc_reciprocal_basis(*(ctypes.c_double(v) for v in (a, b, c, alpha, beta, gamma)), _d(B))
+    return B.reshape(3, 3)
+
+
+def reflections_hkl(B, hkl):
+    """Plane table from a reciprocal basis and a list of allowed reflections
+    (n, 3); raises ValueError when a line's multiples are not 1..n of a base."""
+    L = lib()
+    B = _f64(B, (9,))
+    hkl = np.ascontiguousarray(np.asarray(hkl, np.int32).reshape(-1, 3))
+    n = L.orc_reflections_hkl(_d(B), _i(hkl), len(hkl), 0, None, None, None, None)
+    if n < 0:
+        raise ValueError("harmonics of some line are not the multiples 1..n of its base reflection")
+    w = np.zeros((max(n, 1), 3)); d0 = np.zeros(max(n, 1)); nh = np.zeros(max(n, 1), np.int32)
+    h0 = np.zeros((max(n, 1), 3), np.int32)
+    L.orc_reflections_hkl(_d(B), _i(hkl), len(hkl), n, _d(w), _d(d0), _i(nh), _i(h0))
+    return Planes(w[:n], d0[:n], nh[:n], h0[:n])
+
+
+def knn(D, p, I_off, J_off, c, r, rho):
+    """Neighbour sets of the sparse plan: (|J|, rho) observed indices, -1 padded."""
+    p = _f64(p, (-1, 3)); c = _f64(c, (-1, 3)); r = _f64(r, (-1, 3))
+    I_off = _i32(I_off); J_off = _i32(J_off)
+    nbr = np.zeros((max(int(J_off[-1]), 1), rho), np.int32)
+    lib().orc_knn(ctypes.c_double(D), len(I_off) - 1, _i(I_off), _d(p), _i(J_off), _d(c), _d(r), rho, _i(nbr))
+    return nbr[:int(J_off[-1])]
+
+
+def sinkhorn_sparse(D, p, I_off, J_off, c, r, eps, c_out, mode=0, frac=0.4, n_iter=100, rho=32):
+    """BalancedOT restricted to the rho-nearest-neighbour support; (f, g, fd, gd)."""
+    p = _f64(p, (-1, 3)); c = _f64(c, (-1, 3)); r = _f64(r, (-1, 3))
+    I_off = _i32(I_off); J_off = _i32(J_off)
+    T = len(I_off) - 1
+    nd = T if mode else 1
+    f = np.zeros(int(I_off[-1])); g = np.zeros(int(J_off[-1])); fd = np.zeros(nd); gd = np.zeros(nd)
+    lib().orc_sinkhorn_sparse(ctypes.c_double(D), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r), ctypes.c_double(eps),
+                              ctypes.c_double(c_out), mode, ctypes.c_double(frac), n_iter, rho, _d(f), _d(g), _d(fd),
+                              _d(gd))
+    return f, g, fd, gd

@@ -490,6 +490,11 @@ double orc_pair_cost(const double* p, const double* c, const double* r, double D
     return D * D * e2;
 }
 
+/* orc_pair_cost for n pairs (p_k, c_k, r_k), k < n. */
+void orc_pair_costs(int n, const double* p, const double* c, const double* r, double D, double* out) {
+    for (int k = 0; k < n; ++k) out[k] = orc_pair_cost(p + 3 * k, c + 3 * k, r + 3 * k, D);
+}
+
 /* ------------------------------------------------------------------------- */
 /* E-step: balanced entropic OT with dustbins                                  */
 /* ------------------------------------------------------------------------- */
@@ -1373,7 +1378,8 @@ static void cubic_group(double g[24][4]) {
 }
 
 /* Section "Single-grain fitting" starts the fits from a quasi-uniform grid over
- * orientations and positions, restricted by the lattice symmetry.  Reading
+ * orientations and positions, restricted by the lattice symmetry (sym: 1 none,
+ * 24 cubic group 432, 6 trigonal 32, 12 hexagonal 622).  Reading
  * (the paper uses a Sobol sequence over modified Rodrigues parameters): the
  * super-Fibonacci spiral of Alexa (CVPR 2022) gives n_full quasi-uniform unit
  * quaternions q_i, i = 0..n_full-1, with s = i + 1/2,
@@ -1386,9 +1392,31 @@ static void cubic_group(double g[24][4]) {
  * the k^3 cell centres of the cube of side `cube` centred at the origin
  * ((a + 1/2) cube/k - cube/2 per axis, x slowest).  Writes at most cap starts
  * (R row-major 3x3, x) and returns the number of starts. */
+/* The rotations of the trigonal group 32 (D3: order 6) and the hexagonal group
+ * 622 (D6: order 12) with the c axis along z and a 2-fold axis along x (the
+ * hexagonal a1 axis): turns about z by multiples of 360/n degrees, and
+ * 180-degree turns about the axes in the xy plane at multiples of 180/n
+ * degrees (n = 3 or 6), as unit quaternions. */
+static int dihedral_group(int n, double g[24][4]) {
+    int k = 0;
+    const double pi = 3.14159265358979323846;
+    for (int q = 0; q < n; ++q) {
+        double h = pi * q / n;  /* half of the turn 2 pi q / n */
+        g[k][0] = cos(h); g[k][1] = 0.0; g[k][2] = 0.0; g[k][3] = sin(h); ++k;
+    }
+    for (int q = 0; q < n; ++q) {
+        double phi = pi * q / n;
+        g[k][0] = 0.0; g[k][1] = cos(phi); g[k][2] = sin(phi); g[k][3] = 0.0; ++k;
+    }
+    return k;
+}
+
 long orc_start_grid(long n_full, int sym, int k, double cube, long cap, double* R_out, double* x_out) {
     double G[24][4];
-    cubic_group(G);
+    int ng = 24;
+    if (sym == 6) ng = dihedral_group(3, G);
+    else if (sym == 12) ng = dihedral_group(6, G);
+    else cubic_group(G);
     const double phi = sqrt(2.0), psi = 1.533751168755204288118041;
     const double two_pi = 6.283185307179586476925287;
     long n_kept = 0, S = 0;
@@ -1398,10 +1426,10 @@ long orc_start_grid(long n_full, int sym, int k, double cube, long cap, double* 
         double r = sqrt(s / (double)n_full), rr = sqrt(1.0 - s / (double)n_full);
         double q[4] = {r * sin(two_pi * s / phi), r * cos(two_pi * s / phi), rr * sin(two_pi * s / psi),
                        rr * cos(two_pi * s / psi)};
-        if (sym == 24) {
+        if (sym == 24 || sym == 6 || sym == 12) {
             double id = fabs(q[0]);
             int inside = 1;
-            for (int g = 1; g < 24; ++g) {
+            for (int g = 1; g < ng; ++g) {
                 double d = fabs(q[0] * G[g][0] + q[1] * G[g][1] + q[2] * G[g][2] + q[3] * G[g][3]);
                 if (d > id) { inside = 0; break; }
             }
@@ -1685,4 +1713,235 @@ void orc_harvest_unbalanced(double D, int T, const int* I_off, const double* p,
             if (margin) margin[i] = top1 - top2;
             if (rowmass) rowmass[i] = rs;
         }
+}
+
+/* ------------------------------------------------------------------------- */
+/* General lattices (reciprocal basis B, a list of allowed reflections)        */
+/* ------------------------------------------------------------------------- */
+
+/* Reciprocal basis of the lattice (a, b, c, alpha, beta, gamma), Angstrom and
+ * degrees: the direct basis a1 = a x, a2 in the xy plane at gamma from a1,
+ * a3 completing it; B holds the reciprocal vectors b1, b2, b3 as columns
+ * (a_i . b_j = delta_ij, no 2 pi), so that g = B (h, k, l) and d = 1 / |g|
+ * (Section "Crystallographic planes"). */
+void orc_reciprocal_basis(double a, double b, double c, double alpha, double beta, double gamma, double B[9]) {
+    const double deg = 3.14159265358979323846 / 180.0;
+    double ca = cos(alpha * deg), cb = cos(beta * deg), cg = cos(gamma * deg);
+    double sg = sin(gamma * deg);
+    double A[3][3];  /* rows: a1, a2, a3 */
+    A[0][0] = a;      A[0][1] = 0.0;    A[0][2] = 0.0;
+    A[1][0] = b * cg; A[1][1] = b * sg; A[1][2] = 0.0;
+    double c1 = c * cb, c2 = c * (ca - cb * cg) / sg;
+    A[2][0] = c1;     A[2][1] = c2;     A[2][2] = sqrt(c * c - c1 * c1 - c2 * c2);
+    double V = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+               A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    /* b1 = a2 x a3 / V, b2 = a3 x a1 / V, b3 = a1 x a2 / V */
+    double bv[3][3];
+    cross3(A[1], A[2], bv[0]);
+    cross3(A[2], A[0], bv[1]);
+    cross3(A[0], A[1], bv[2]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) B[3 * i + j] = bv[j][i] / V;
+}
+
+typedef struct { int p[3]; int m; double len2; } hkl_item_t;
+
+static int hkl_item_cmp(const void* A, const void* B) {
+    const hkl_item_t* x = (const hkl_item_t*)A;
+    const hkl_item_t* y = (const hkl_item_t*)B;
+    for (int k = 0; k < 3; ++k)
+        if (x->p[k] != y->p[k]) return x->p[k] < y->p[k] ? -1 : 1;
+    return x->m < y->m ? -1 : (x->m > y->m ? 1 : 0);
+}
+
+typedef struct { int g0[3]; double len2; int nh; double w[3]; double d0; } grefl_t;
+
+static int grefl_cmp(const void* A, const void* B) {
+    const grefl_t* a = (const grefl_t*)A;
+    const grefl_t* b = (const grefl_t*)B;
+    double tol = 1e-9 * (a->len2 > b->len2 ? a->len2 : b->len2);
+    if (fabs(a->len2 - b->len2) > tol) return a->len2 < b->len2 ? -1 : 1;
+    for (int k = 0; k < 3; ++k)
+        if (a->g0[k] != b->g0[k]) return a->g0[k] > b->g0[k] ? -1 : 1;
+    return 0;
+}
+
+/* The plausible plane set from a list of allowed reflections (the paper takes
+ * it as an input, Section "Tomography experiments"): reflections on one line
+ * through the origin share a ray (Friedel mates +-hkl and harmonics n hkl);
+ * for each line the multiples present must be m0, 2 m0, ..., nh m0 of its
+ * primitive vector; the entry is g0 = m0 p with p's first nonzero index
+ * positive, w = B g0 / |B g0|, d0 = 1 / |B g0|, nh.  Order: |B g0|^2
+ * ascending (equal within 1e-9 relative), then g0 descending.  Returns the
+ * number of entries, or -1 when a line's multiples are not of that form. */
+int orc_reflections_hkl(const double B[9], const int* hkl, int n, int cap,
+                        double* w, double* d0, int* nharm, int* hkl0) {
+    hkl_item_t* it = (hkl_item_t*)malloc(sizeof(hkl_item_t) * (size_t)(n > 0 ? n : 1));
+    int ni = 0;
+    for (int q = 0; q < n; ++q) {
+        int h = hkl[3 * q], k = hkl[3 * q + 1], l = hkl[3 * q + 2];
+        if (h == 0 && k == 0 && l == 0) continue;
+        int g = gcd_int(gcd_int(h, k), l);
+        int p[3] = {h / g, k / g, l / g};
+        int first = p[0] != 0 ? p[0] : (p[1] != 0 ? p[1] : p[2]);
+        if (first < 0) { p[0] = -p[0]; p[1] = -p[1]; p[2] = -p[2]; }
+        it[ni].p[0] = p[0]; it[ni].p[1] = p[1]; it[ni].p[2] = p[2];
+        it[ni].m = g;
+        ++ni;
+    }
+    qsort(it, (size_t)ni, sizeof(hkl_item_t), hkl_item_cmp);
+    grefl_t* out = (grefl_t*)malloc(sizeof(grefl_t) * (size_t)(ni > 0 ? ni : 1));
+    int no = 0;
+    for (int s = 0; s < ni;) {
+        int e = s;
+        while (e < ni && it[e].p[0] == it[s].p[0] && it[e].p[1] == it[s].p[1] && it[e].p[2] == it[s].p[2]) ++e;
+        /* distinct multiples of this line */
+        int mult[256], nm = 0;
+        for (int q = s; q < e; ++q)
+            if (nm == 0 || it[q].m != mult[nm - 1]) {
+                if (nm >= 256) { free(it); free(out); return -1; }
+                mult[nm++] = it[q].m;
+            }
+        for (int q = 0; q < nm; ++q)
+            if (mult[q] != (q + 1) * mult[0]) { free(it); free(out); return -1; }
+        grefl_t* R = &out[no++];
+        for (int a = 0; a < 3; ++a) R->g0[a] = mult[0] * it[s].p[a];
+        double g[3];
+        for (int a = 0; a < 3; ++a) g[a] = B[3 * a] * R->g0[0] + B[3 * a + 1] * R->g0[1] + B[3 * a + 2] * R->g0[2];
+        R->len2 = dot3(g, g);
+        double len = sqrt(R->len2);
+        for (int a = 0; a < 3; ++a) R->w[a] = g[a] / len;
+        R->d0 = 1.0 / len;
+        R->nh = nm;
+        s = e;
+    }
+    qsort(out, (size_t)no, sizeof(grefl_t), grefl_cmp);
+    for (int m = 0; m < no && m < cap; ++m) {
+        for (int q = 0; q < 3; ++q) {
+            w[3 * m + q] = out[m].w[q];
+            if (hkl0) hkl0[3 * m + q] = out[m].g0[q];
+        }
+        d0[m] = out[m].d0;
+        nharm[m] = out[m].nh;
+    }
+    free(it);
+    free(out);
+    return no;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sparse assignment (Section "Working with sparse assignment matrices")       */
+/* ------------------------------------------------------------------------- */
+
+typedef struct { double c; int i; } knn_item_t;
+
+static int knn_cmp(const void* A, const void* B) {
+    const knn_item_t* a = (const knn_item_t*)A;
+    const knn_item_t* b = (const knn_item_t*)B;
+    if (a->c != b->c) return a->c < b->c ? -1 : 1;
+    return a->i < b->i ? -1 : (a->i > b->i ? 1 : 0);
+}
+
+/* Neighbour sets of the sparse plan.  Reading: each model spot j keeps the
+ * rho observed spots of its angle block with the smallest cost C_ij (ties to
+ * the lower index; all of them when the block has at most rho), so that a
+ * Sinkhorn update costs rho |J| instead of |I| |J|; every other entry of the
+ * plan between observed and model spots is 0, the dustbin row and column
+ * stay dense.  nbr: |J| x rho observed indices, -1 past the block's size. */
+void orc_knn(double D, int T, const int* I_off, const double* p, const int* J_off, const double* c,
+             const double* r, int rho, int* nbr) {
+    int big = 1;
+    for (int t = 0; t < T; ++t)
+        if (I_off[t + 1] - I_off[t] > big) big = I_off[t + 1] - I_off[t];
+    knn_item_t* buf = (knn_item_t*)malloc(sizeof(knn_item_t) * (size_t)big);
+    for (int t = 0; t < T; ++t)
+        for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+            int n = 0;
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                buf[n].c = orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D);
+                buf[n].i = i;
+                ++n;
+            }
+            qsort(buf, (size_t)n, sizeof(knn_item_t), knn_cmp);
+            for (int k = 0; k < rho; ++k) nbr[(long)j * rho + k] = k < n ? buf[k].i : -1;
+        }
+    free(buf);
+}
+
+/* Algorithm BalancedOT (log domain, dustbins as in orc_sinkhorn) with the
+ * observed-model entries of the plan restricted to the neighbour sets:
+ *   f_i = -eps LSE({(g_j - C_ij)/eps : i in N(j)} u {(g_0 - c_out)/eps})
+ *   g_j = -eps LSE({(f_i - C_ij)/eps : i in N(j)} u {f_0 / eps})
+ * and the dustbin updates of orc_sinkhorn.  Runs n_iter iterations from
+ * f = g = 0. */
+int orc_sinkhorn_sparse(double D, int T, const int* I_off, const double* p, const int* J_off,
+                        const double* c, const double* r, double eps, double c_out, int mode, double frac,
+                        int n_iter, int rho, double* f, double* g, double* fd, double* gd) {
+    int nI = I_off[T], nJ = J_off[T];
+    int nd = mode ? T : 1;
+    int* nbr = (int*)malloc(sizeof(int) * ((size_t)nJ * rho + 1));
+    orc_knn(D, T, I_off, p, J_off, c, r, rho, nbr);
+    /* per observed spot: the model spots whose neighbour set holds it */
+    int* rcount = (int*)calloc((size_t)nI + 1, sizeof(int));
+    for (long e = 0; e < (long)nJ * rho; ++e)
+        if (nbr[e] >= 0) ++rcount[nbr[e] + 1];
+    for (int i = 0; i < nI; ++i) rcount[i + 1] += rcount[i];
+    int* rows = (int*)malloc(sizeof(int) * ((size_t)rcount[nI] + 1));
+    int* fill = (int*)calloc((size_t)nI + 1, sizeof(int));
+    for (int j = 0; j < nJ; ++j)
+        for (int k = 0; k < rho; ++k) {
+            int i = nbr[(long)j * rho + k];
+            if (i >= 0) rows[rcount[i] + fill[i]++] = j;
+        }
+    double* U = (double*)malloc(sizeof(double) * nd);
+    double* O = (double*)malloc(sizeof(double) * nd);
+    orc_masses(mode, frac, T, I_off, J_off, U, O);
+    for (int i = 0; i < nI; ++i) f[i] = 0.0;
+    for (int j = 0; j < nJ; ++j) g[j] = 0.0;
+    for (int d = 0; d < nd; ++d) fd[d] = gd[d] = 0.0;
+    int big = (nI > nJ ? nI : nJ) + rho + 2;
+    double* buf = (double*)malloc(sizeof(double) * big);
+    for (int it = 0; it < n_iter; ++it) {
+        for (int t = 0; t < T; ++t) {
+            int dd = mode ? t : 0;
+            for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
+                int n = 0;
+                for (int e = rcount[i]; e < rcount[i + 1]; ++e) {
+                    int j = rows[e];
+                    buf[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                }
+                buf[n++] = (gd[dd] - c_out) / eps;
+                f[i] = -eps * lse(buf, n);
+            }
+        }
+        for (int d = 0; d < nd; ++d) {
+            int j0 = mode ? J_off[d] : 0, j1 = mode ? J_off[d + 1] : nJ;
+            int n = 0;
+            for (int j = j0; j < j1; ++j) buf[n++] = g[j] / eps;
+            buf[n++] = (gd[d] - c_out) / eps;
+            fd[d] = eps * logm(U[d]) - eps * lse(buf, n);
+        }
+        for (int t = 0; t < T; ++t) {
+            int dd = mode ? t : 0;
+            for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
+                int n = 0;
+                for (int k = 0; k < rho; ++k) {
+                    int i = nbr[(long)j * rho + k];
+                    if (i < 0) continue;
+                    buf[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                }
+                buf[n++] = fd[dd] / eps;
+                g[j] = -eps * lse(buf, n);
+            }
+        }
+        for (int d = 0; d < nd; ++d) {
+            int i0 = mode ? I_off[d] : 0, i1 = mode ? I_off[d + 1] : nI;
+            int n = 0;
+            for (int i = i0; i < i1; ++i) buf[n++] = (f[i] - c_out) / eps;
+            buf[n++] = (fd[d] - c_out) / eps;
+            gd[d] = eps * logm(O[d]) - eps * lse(buf, n);
+        }
+    }
+    free(buf); free(U); free(O); free(nbr); free(rcount); free(rows); free(fill);
+    return n_iter;
 }

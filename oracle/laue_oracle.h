@@ -41,6 +41,7 @@ void orc_refresh(const double* geom, const double* w, const double* d0, const in
                  double* ray4, double* center3);
 
 double orc_pair_cost(const double* p, const double* c, const double* r, double D);
+void orc_pair_costs(int n, const double* p, const double* c, const double* r, double D, double* out);
 
 void orc_masses(int mode, double frac, int T, const int* I_off, const int* J_off,
                 double* U, double* O);
@@ -129,6 +130,14 @@ void orc_harvest_unbalanced(double D, int T, const int* I_off, const double* p,
                             const double* f, const double* g, int* assign, double* margin,
                             double* rowmass, double* q);
 int orc_set_threads(int n);
+void orc_reciprocal_basis(double a, double b, double c, double alpha, double beta, double gamma, double B[9]);
+int orc_reflections_hkl(const double B[9], const int* hkl, int n, int cap,
+                        double* w, double* d0, int* nharm, int* hkl0);
+void orc_knn(double D, int T, const int* I_off, const double* p, const int* J_off, const double* c,
+             const double* r, int rho, int* nbr);
+int orc_sinkhorn_sparse(double D, int T, const int* I_off, const double* p, const int* J_off,
+                        const double* c, const double* r, double eps, double c_out, int mode, double frac,
+                        int n_iter, int rho, double* f, double* g, double* fd, double* gd);
 long orc_start_grid(long n_full, int sym, int k, double cube, long cap, double* R_out, double* x_out);
 
 #ifdef __cplusplus

@@ -84,6 +84,8 @@ SIGNATURES = {
     "laue_set_workspace": [_vp, _vp, ctypes.c_size_t, _vp],
     "laue_device_status": [_vp, _vp, _pi],
     "laue_reflections": [_d, _i, _i, _i, _vp, _vp, _vp, _pi],
+    "laue_reciprocal_basis": [_d, _d, _d, _d, _d, _d, _vp],
+    "laue_reflections_hkl": [_vp, _vp, _i, _i, _vp, _vp, _vp, _pi],
     "laue_alu_peaks": [_vp, _vp, _vp],
     "laue_forward": [_vp, _P(LaueGeometry), _P(LaueLattice), _vp, _vp, _i, _vp, _i, _P(LaueModelSpots), _pi, _vp],
     "laue_refresh": [_vp, _P(LaueGeometry), _P(LaueLattice), _vp, _vp, _vp, _P(LaueModelSpots), _vp],
@@ -94,6 +96,10 @@ SIGNATURES = {
     "laue_autotune": [_vp, _P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams), _i, _vp,
                       _vp, _vp],
     "laue_set_launch_shape": [_vp, _i, _i],
+    "laue_set_pair_skipping": [_vp, _i],
+    "laue_sparse_workspace_size": [_i, _i, _i, _i, _P(ctypes.c_size_t)],
+    "laue_cost_sinkhorn_sparse": [_vp, _P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams),
+                                  _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "laue_read_counters": [_vp, _vp, _P(ctypes.c_longlong), _i],
     "laue_mstep": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _P(LaueModelSpots), _vp, _vp,
                    _P(LaueMParams), _vp, _vp, _vp, _i, _vp, _vp],

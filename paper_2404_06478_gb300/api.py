@@ -76,6 +76,36 @@ def reflections(a: float, hmax: int, centering: int = 1):
     return w, nh, hk
 
 
+def reciprocal_basis(a, b, c, alpha, beta, gamma) -> np.ndarray:
+    """laue_reciprocal_basis: B (3, 3), columns b1 b2 b3."""
+    B = np.zeros(9)
+    rc = N.lib().laue_reciprocal_basis(float(a), float(b), float(c), float(alpha), float(beta), float(gamma),
+                                       B.ctypes.data_as(ctypes.c_void_p))
+    if rc != 0:
+        raise LaueError(rc, "laue_reciprocal_basis: bad cell")
+    return B.reshape(3, 3)
+
+
+def reflections_hkl(B, hkl):
+    """laue_reflections_hkl on the host: (w_d0 (M, 4) float32, nharm (M,), hkl0 (M, 3))."""
+    L = N.lib()
+    Bc = np.ascontiguousarray(np.asarray(B, np.float64).reshape(9))
+    hk = np.ascontiguousarray(np.asarray(hkl, np.int32).reshape(-1, 3))
+    M = ctypes.c_int(0)
+    args = (Bc.ctypes.data_as(ctypes.c_void_p), hk.ctypes.data_as(ctypes.c_void_p), len(hk))
+    rc = L.laue_reflections_hkl(*args, 0, None, None, None, ctypes.byref(M))
+    if rc not in (0, N.LAUE_ERR_CAPACITY):
+        raise LaueError(rc, "laue_reflections_hkl failed")
+    w = np.zeros((M.value, 4), np.float32)
+    nh = np.zeros(M.value, np.int32)
+    h0 = np.zeros((M.value, 3), np.int32)
+    rc = L.laue_reflections_hkl(*args, M.value, w.ctypes.data_as(ctypes.c_void_p), nh.ctypes.data_as(ctypes.c_void_p),
+                                h0.ctypes.data_as(ctypes.c_void_p), ctypes.byref(M))
+    if rc != 0:
+        raise LaueError(rc, "laue_reflections_hkl failed")
+    return w, nh, h0
+
+
 @dataclasses.dataclass
 class Lattice:
     w_d0: torch.Tensor   # (M, 4) float32 device
@@ -87,6 +117,12 @@ class Lattice:
     @staticmethod
     def cubic(a, hmax, centering=1, device="cuda"):
         w, nh, _ = reflections(a, hmax, centering)
+        return Lattice(torch.from_numpy(w).to(device), torch.from_numpy(nh).to(device))
+
+    @staticmethod
+    def from_hkl(B, hkl, device="cuda"):
+        """Any lattice: reciprocal basis B and the allowed reflections."""
+        w, nh, _ = reflections_hkl(B, hkl)
         return Lattice(torch.from_numpy(w).to(device), torch.from_numpy(nh).to(device))
 
 
@@ -219,6 +255,14 @@ class Handle:
                        "set_workspace")
         return self.ws
 
+    def reserve_bytes(self, need, stream=None):
+        """Grow the workspace to at least `need` bytes (keeps a larger one)."""
+        if self.ws is None or self.ws.numel() < need:
+            self.ws = torch.empty(int(need) + 256, dtype=torch.uint8, device=self.device)
+            self.check(self.L.laue_set_workspace(self.h, _ptr(self.ws), self.ws.numel(), _stream(stream)),
+                       "set_workspace")
+        return self.ws
+
     def alu_peaks(self, stream=None) -> dict:
         """Measured pipe throughputs (ops/s) of this device."""
         self.reserve(1, stream=stream)
@@ -231,9 +275,12 @@ class Handle:
 
     def counters(self, stream=None):
         """laue_read_counters: dict of the device counters since the last read."""
-        v = (ctypes.c_longlong * 3)()
-        self.check(self.L.laue_read_counters(self.h, _stream(stream), v, 3), "read_counters")
-        return dict(exact_rows=v[0], exact_cols=v[1], fit_pairs=v[2])
+        v = (ctypes.c_longlong * 4)()
+        self.check(self.L.laue_read_counters(self.h, _stream(stream), v, 4), "read_counters")
+        return dict(exact_rows=v[0], exact_cols=v[1], fit_pairs=v[2], pass_pairs=v[3])
+
+    def set_pair_skipping(self, enable: bool):
+        self.check(self.L.laue_set_pair_skipping(self.h, 1 if enable else 0), "set_pair_skipping")
 
     def exact_lse_count(self, stream=None):
         """(rows, columns) recomputed on the exact log-sum-exp path since the last read."""
@@ -324,6 +371,49 @@ def cost_sinkhorn(h: Handle, geom, obs: ObsSpots, model: ModelSpots, eps, c_out,
         out["marg_err"] = merr
     if col_harvest:
         out["q"] = q[:nJ]
+    return out
+
+
+def cost_sinkhorn_sparse(h: Handle, geom, obs: ObsSpots, model: ModelSpots, eps, c_out, n_iter, rho=32,
+                         dust_mode=0, unmatched_frac=0.4, harvest=True, col_harvest=False, init=None,
+                         neighbours=False, stream=None):
+    """laue_cost_sinkhorn_sparse: the E-step on the rho-nearest-neighbour
+    support; returns the outputs of cost_sinkhorn (and nbr with neighbours)."""
+    dev = obs.p.device
+    T = obs.T
+    nI, nJ = int(obs.p.shape[0]), model.n
+    b = ctypes.c_size_t()
+    h.check(h.L.laue_sparse_workspace_size(T, nI, nJ, int(rho), ctypes.byref(b)), "sparse_workspace_size")
+    h.reserve_bytes(b.value, stream=stream)
+    nd = T if dust_mode else 1
+    if init is not None:
+        f, g, dust = (t.clone().float().contiguous() for t in init)
+    else:
+        f = torch.zeros(max(nI, 1), device=dev)
+        g = torch.zeros(max(nJ, 1), device=dev)
+        dust = torch.zeros(2 * nd, device=dev)
+    assign = torch.empty(max(nI, 1), dtype=torch.int32, device=dev) if harvest else None
+    margin = torch.empty(max(nI, 1), device=dev) if harvest else None
+    merr = torch.empty(2, device=dev) if (harvest or col_harvest) else None
+    q = torch.empty(max(nJ, 1), device=dev) if col_harvest else None
+    nbr = torch.empty(max(nJ * int(rho), 1), dtype=torch.int32, device=dev) if neighbours else None
+    prm = ot_params(eps, c_out, n_iter, dust_mode, unmatched_frac, init is not None)
+    g_s = geometry_struct(geom)
+    o_s = obs.struct()
+    m_s = model.struct()
+    h.check(h.L.laue_cost_sinkhorn_sparse(h.h, ctypes.byref(g_s), ctypes.byref(o_s), ctypes.byref(m_s),
+                                          ctypes.byref(prm), int(rho), _ptr(f), _ptr(g), _ptr(dust), _ptr(assign),
+                                          _ptr(margin), _ptr(merr), _ptr(q), _ptr(nbr), _stream(stream)),
+            "laue_cost_sinkhorn_sparse")
+    out = dict(f=f[:nI], g=g[:nJ], dust=dust)
+    if harvest:
+        out.update(assign=assign[:nI], margin=margin[:nI])
+    if merr is not None:
+        out["marg_err"] = merr
+    if col_harvest:
+        out["q"] = q[:nJ]
+    if neighbours:
+        out["nbr"] = nbr[:nJ * int(rho)].view(nJ, int(rho))
     return out
 
 

@@ -114,6 +114,7 @@ extern "C" int laue_create(laue_handle** h, int device) {
         for (int v = 0; v < kSkVariants; ++v) H->row_occ[v] = H->col_occ[v] = 1;
     cudaSetDevice(prev);
     H->row_variant = H->col_variant = 0;
+    H->skip = 1;
     H->err[0] = 0;
     *h = H;
     return LAUE_OK;
@@ -238,6 +239,112 @@ extern "C" int laue_reflections(double a, int hmax, int centering, int cap, floa
     return (int)list.size() > cap ? LAUE_ERR_CAPACITY : LAUE_OK;
 }
 
+extern "C" int laue_reciprocal_basis(double a, double b, double c, double alpha_deg, double beta_deg,
+                                     double gamma_deg, double* B_host) {
+    if (!B_host || !(a > 0.0) || !(b > 0.0) || !(c > 0.0) || !(alpha_deg > 0.0 && alpha_deg < 180.0) ||
+        !(beta_deg > 0.0 && beta_deg < 180.0) || !(gamma_deg > 0.0 && gamma_deg < 180.0))
+        return LAUE_ERR_INVALID_ARG;
+    const double r = 3.14159265358979323846 / 180.0;
+    double ca = std::cos(alpha_deg * r), cb = std::cos(beta_deg * r), cg = std::cos(gamma_deg * r);
+    double sg = std::sin(gamma_deg * r);
+    // direct basis: a1 along x, a2 in the xy plane, a3 completing it
+    double a1[3] = {a, 0.0, 0.0}, a2[3] = {b * cg, b * sg, 0.0};
+    double z1 = c * cb, z2 = c * (ca - cb * cg) / sg, zz = c * c - z1 * z1 - z2 * z2;
+    if (!(zz > 0.0)) return LAUE_ERR_INVALID_ARG;  // the angles do not close a cell
+    double a3[3] = {z1, z2, std::sqrt(zz)};
+    auto cross = [](const double* u, const double* v, double* o) {
+        o[0] = u[1] * v[2] - u[2] * v[1];
+        o[1] = u[2] * v[0] - u[0] * v[2];
+        o[2] = u[0] * v[1] - u[1] * v[0];
+    };
+    double c23[3], c31[3], c12[3];
+    cross(a2, a3, c23);
+    cross(a3, a1, c31);
+    cross(a1, a2, c12);
+    double V = a1[0] * c23[0] + a1[1] * c23[1] + a1[2] * c23[2];
+    for (int i = 0; i < 3; ++i) {  // columns b1 = a2 x a3 / V, b2 = a3 x a1 / V, b3 = a1 x a2 / V
+        B_host[3 * i + 0] = c23[i] / V;
+        B_host[3 * i + 1] = c31[i] / V;
+        B_host[3 * i + 2] = c12[i] / V;
+    }
+    return LAUE_OK;
+}
+
+extern "C" int laue_reflections_hkl(const double* B_host, const int* hkl_host, int n, int cap, float* w_d0_host,
+                                    int* nharm_host, int* hkl0_host, int* M) {
+    if (!M || !B_host || n < 0 || (n > 0 && !hkl_host) || cap < 0) return LAUE_ERR_INVALID_ARG;
+    // every listed reflection on its line through the origin: primitive vector
+    // (first nonzero index positive) and multiplier
+    struct Item {
+        int p[3];
+        int m;
+    };
+    std::vector<Item> items;
+    for (int q = 0; q < n; ++q) {
+        int h = hkl_host[3 * q], k = hkl_host[3 * q + 1], l = hkl_host[3 * q + 2];
+        if (h == 0 && k == 0 && l == 0) continue;
+        int g = gcd_i(gcd_i(h, k), l);
+        Item it{{h / g, k / g, l / g}, g};
+        int first = it.p[0] != 0 ? it.p[0] : (it.p[1] != 0 ? it.p[1] : it.p[2]);
+        if (first < 0)
+            for (int a = 0; a < 3; ++a) it.p[a] = -it.p[a];
+        items.push_back(it);
+    }
+    std::sort(items.begin(), items.end(), [](const Item& x, const Item& y) {
+        for (int a = 0; a < 3; ++a)
+            if (x.p[a] != y.p[a]) return x.p[a] < y.p[a];
+        return x.m < y.m;
+    });
+    struct Ent {
+        int g0[3];
+        double len2, w[3], d0;
+        int nh;
+    };
+    std::vector<Ent> out;
+    for (size_t s = 0; s < items.size();) {
+        size_t e = s;
+        std::vector<int> mult;
+        while (e < items.size() && items[e].p[0] == items[s].p[0] && items[e].p[1] == items[s].p[1] &&
+               items[e].p[2] == items[s].p[2]) {
+            if (mult.empty() || mult.back() != items[e].m) mult.push_back(items[e].m);
+            ++e;
+        }
+        for (size_t q = 0; q < mult.size(); ++q)  // harmonics: m0, 2 m0, ..., nh m0
+            if (mult[q] != (int)(q + 1) * mult[0]) return LAUE_ERR_INVALID_ARG;
+        Ent E;
+        for (int a = 0; a < 3; ++a) E.g0[a] = mult[0] * items[s].p[a];
+        double g[3];
+        for (int a = 0; a < 3; ++a)
+            g[a] = B_host[3 * a] * E.g0[0] + B_host[3 * a + 1] * E.g0[1] + B_host[3 * a + 2] * E.g0[2];
+        E.len2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        if (!(E.len2 > 0.0)) return LAUE_ERR_INVALID_ARG;
+        double len = std::sqrt(E.len2);
+        for (int a = 0; a < 3; ++a) E.w[a] = g[a] / len;
+        E.d0 = 1.0 / len;
+        E.nh = (int)mult.size();
+        out.push_back(E);
+        s = e;
+    }
+    std::sort(out.begin(), out.end(), [](const Ent& x, const Ent& y) {
+        double tol = 1e-9 * std::max(x.len2, y.len2);
+        if (std::fabs(x.len2 - y.len2) > tol) return x.len2 < y.len2;
+        for (int q = 0; q < 3; ++q)
+            if (x.g0[q] != y.g0[q]) return x.g0[q] > y.g0[q];
+        return false;
+    });
+    *M = (int)out.size();
+    for (int m = 0; m < (int)out.size() && m < cap; ++m) {
+        if (w_d0_host) {
+            for (int q = 0; q < 3; ++q) w_d0_host[4 * m + q] = (float)out[m].w[q];
+            w_d0_host[4 * m + 3] = (float)out[m].d0;
+        }
+        if (nharm_host) nharm_host[m] = out[m].nh;
+        if (hkl0_host)
+            for (int q = 0; q < 3; ++q) hkl0_host[3 * m + q] = out[m].g0[q];
+    }
+    return (int)out.size() > cap ? LAUE_ERR_CAPACITY : LAUE_OK;
+}
+
 // ------------------------------------------------------------- forward
 
 extern "C" int laue_forward(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
@@ -347,6 +454,24 @@ int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* o
     a.modW = (float4*)(ws + L.modW);
     a.I2_off = (int*)(ws + L.pairoff);
     a.J2_off = a.I2_off + (obs->T + 1);
+    a.obs_gbase = a.J2_off + (obs->T + 1);
+    a.mod_gbase = a.obs_gbase + (obs->T + 1);
+    {
+        size_t nsp = (size_t)obs->n + model->n + 2;
+        int* pp = (int*)(ws + L.perm);
+        // 2 (n_obs + 1) + 2 (n_model + 1) = 2 nsp ints
+        a.obs_perm = pp;
+        a.obs_pos = pp + obs->n + 1;
+        a.mod_perm = pp + 2 * ((size_t)obs->n + 1);
+        a.mod_pos = a.mod_perm + model->n + 1;
+        a.sort_key = (unsigned*)(ws + L.sortbuf);
+        a.sort_idx = (int*)(a.sort_key + 2 * nsp);
+        a.obs_cone = (float4*)(ws + L.cone);
+        a.mod_cone = a.obs_cone + L.max_obs_gran;
+        a.obs_ext = (float*)(a.mod_cone + L.max_mod_gran);
+        a.mod_ext = a.obs_ext + L.max_obs_gran;
+        a.skip = h->skip;
+    }
     a.row_tiles = (int4*)(ws + L.row_tiles);
     a.col_tiles = (int4*)(ws + L.col_tiles);
     a.ang_tiles = (int4*)(ws + L.ang);
@@ -417,13 +542,77 @@ extern "C" int laue_cost_sinkhorn(laue_handle* h, const LaueGeometry* geom, cons
                            "sinkhorn launch");
 }
 
+// ------------------------------------------------------- sparse Sinkhorn
+
+extern "C" int laue_sparse_workspace_size(int T, int n_obs, int n_model, int rho, size_t* bytes) {
+    if (!bytes || T < 1 || n_obs < 0 || n_model < 0 || rho < 1 || rho > kSparseMaxRho) return LAUE_ERR_INVALID_ARG;
+    *bytes = kCtrlBytes + sparse_workspace_bytes(T, n_obs, n_model, rho);
+    return LAUE_OK;
+}
+
+extern "C" int laue_cost_sinkhorn_sparse(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* obs,
+                                         const LaueModelSpots* model, const LaueOTParams* prm, int rho, float* f,
+                                         float* g, float* dust, int* assign, float* margin, float* marg_err,
+                                         float* q, int* nbr, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    int rc;
+    if ((rc = laue_check_geom(h, geom))) return rc;
+    if ((rc = laue_check_obs(h, obs))) return rc;
+    if ((rc = laue_check_model(h, model))) return rc;
+    if (!prm || !(prm->eps > 0.0f) || prm->n_iter < 0 || !(prm->c_out >= 0.0f) ||
+        !(prm->unmatched_frac >= 0.0) || prm->unmatched_frac > 1.0 || prm->dust_mode < 0 || prm->dust_mode > 1)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG,
+                         "sparse OT params: eps > 0, n_iter >= 0, c_out >= 0, 0 <= frac <= 1, dust_mode 0 or 1");
+    if (rho < 1 || rho > kSparseMaxRho)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "rho must be 1..%d", kSparseMaxRho);
+    if (obs->T != model->T) return laue_fail(h, LAUE_ERR_INVALID_ARG, "observed and model T differ");
+    if ((obs->n > 0 && !f) || (model->n > 0 && !g))
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "f and g outputs are required");
+    if (prm->warm_start && !dust) return laue_fail(h, LAUE_ERR_INVALID_ARG, "warm start needs dust");
+    if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set");
+    size_t need = kCtrlBytes + sparse_workspace_bytes(obs->T, obs->n, model->n, rho);
+    if (need > h->ws_bytes)
+        return laue_fail(h, LAUE_ERR_WORKSPACE, "sparse E-step: workspace of %zu bytes needed", need);
+    SpArgs a{};
+    sparse_carve(a, (char*)h->ws + kCtrlBytes, obs->T, obs->n, model->n, rho);
+    a.T = obs->T;
+    a.n_obs = obs->n;
+    a.n_model = model->n;
+    a.rho = rho;
+    a.I_off = obs->I_off;
+    a.J_off = model->J_off;
+    a.p = (const float4*)obs->p;
+    a.c = (const float4*)model->center;
+    a.r = (const float4*)model->ray;
+    a.ctrl = (int*)h->ws;
+    const double eps = prm->eps;
+    a.negK = (float)(-(double)geom->D * geom->D * 1.4426950408889634 / eps);
+    a.kc = (float)((double)prm->c_out * 1.4426950408889634 / eps);
+    a.frac = prm->unmatched_frac;
+    a.to_user = (float)(eps * 0.6931471805599453);
+    a.mode = prm->dust_mode;
+    a.warm = prm->warm_start ? 1 : 0;
+    a.f = f;
+    a.g = g;
+    a.dust_out = dust;
+    a.assign = assign;
+    a.margin = margin;
+    a.marg_err = marg_err;
+    a.q = q;
+    a.nbr_out = nbr;
+    bool rows = assign || margin || marg_err;
+    bool cols = q || marg_err;
+    return laue_cuda_check(h, sparse_sinkhorn_run(a, prm->n_iter, rows, cols, (cudaStream_t)stream),
+                           "sparse sinkhorn launch");
+}
+
 // ------------------------------------------------------------- autotuner
 
 extern "C" int laue_read_counters(laue_handle* h, void* stream, long long* counts_host, int n) {
-    if (!h || !counts_host || n < 0 || n > 3) return LAUE_ERR_INVALID_ARG;
+    if (!h || !counts_host || n < 0 || n > 4) return LAUE_ERR_INVALID_ARG;
     if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set");
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned v[4] = {0u, 0u, 0u, 0u};  // exact rows, exact columns, fit pairs (64 bits)
+    unsigned v[6] = {0u, 0u, 0u, 0u, 0u, 0u};  // exact rows, exact columns, fit pairs, pass pairs (64 bits)
     int* ctrl = (int*)h->ws;
     int rc;
     if ((rc = laue_cuda_check(h, cudaMemcpyAsync(v, ctrl + CTRL_EXACT_ROWS, sizeof(v), cudaMemcpyDeviceToHost, s),
@@ -432,9 +621,16 @@ extern "C" int laue_read_counters(laue_handle* h, void* stream, long long* count
     if ((rc = laue_cuda_check(h, cudaMemsetAsync(ctrl + CTRL_EXACT_ROWS, 0, sizeof(v), s), "clearing counts")))
         return rc;
     if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "synchronise"))) return rc;
-    long long all[3] = {(long long)v[0], (long long)v[1],
-                        (long long)((unsigned long long)v[2] | ((unsigned long long)v[3] << 32))};
+    long long all[4] = {(long long)v[0], (long long)v[1],
+                        (long long)((unsigned long long)v[2] | ((unsigned long long)v[3] << 32)),
+                        (long long)((unsigned long long)v[4] | ((unsigned long long)v[5] << 32))};
     for (int k = 0; k < n; ++k) counts_host[k] = all[k];
+    return LAUE_OK;
+}
+
+extern "C" int laue_set_pair_skipping(laue_handle* h, int enable) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    h->skip = enable ? 1 : 0;
     return LAUE_OK;
 }
 

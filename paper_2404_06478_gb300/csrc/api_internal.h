@@ -12,6 +12,7 @@ struct laue_handle {
     int sm_count;
     int row_occ[laue::kSkVariants], col_occ[laue::kSkVariants];  // resident CTAs per SM of each launch shape
     int row_variant, col_variant;  // launch shapes in use (the autotuner's choice)
+    int skip;                      // exact underflow skipping in the pair passes (default on)
     void* ws;
     size_t ws_bytes;
     char err[512];

@@ -32,6 +32,8 @@ enum CtrlSlot {
     CTRL_EXACT_ROWS = 16, // row / column log-sum-exps recomputed on the exact path
     CTRL_EXACT_COLS = 17,
     CTRL_SF_PAIRS = 18,   // 64-bit count (slots 18-19) of single-fit pair evaluations
+    CTRL_SK_PAIRS = 20,   // 64-bit count (slots 20-21) of pair evaluations of the Sinkhorn passes
+    CTRL_SP_DONE = 22,    // finished-CTA ticket of the sparse passes
     CTRL_SLOTS = 64
 };
 
@@ -48,7 +50,10 @@ struct Layout {
     size_t ang;                   // int4 per angle: tile ranges of the passes
     size_t obsX, obsY;            // pair-interleaved observed spots (see sinkhorn.cu)
     size_t modX, modY, modZ, modW;// pair-interleaved model spots
-    size_t pairoff;               // int: I2_off[T+1], J2_off[T+1] (pair offsets)
+    size_t pairoff;               // int: I2_off[T+1], J2_off[T+1] (pair offsets), granule bases (2 x (T+1))
+    size_t perm;                  // int: observed and model sort permutations (order -> caller, caller -> order)
+    size_t sortbuf;               // sort keys and indices (two buffers each)
+    size_t cone;                  // float4 + float per granule of kChunk pairs, observed then model
     size_t fwd_blocks;            // int per forward block (count, then offset)
     size_t jsum;                  // float per model spot x 12 (M-step sums)
     size_t gsum;                  // float per grain x 16
@@ -58,6 +63,7 @@ struct Layout {
     size_t total;
     int max_row_tiles, max_col_tiles, max_fwd_blocks;
     int max_obs_pairs, max_mod_pairs;
+    int max_obs_gran, max_mod_gran;
 };
 
 constexpr int kMinTile = 64;      // smallest tile (in spot pairs) any launch shape uses
@@ -94,7 +100,13 @@ inline Layout make_layout(const LaueProblemDims& d, int sm_count) {
     L.modY = take(sizeof(float4) * jp);
     L.modZ = take(sizeof(float4) * jp);
     L.modW = take(sizeof(float4) * jp);
-    L.pairoff = take(sizeof(int) * (size_t)(2 * T + 4));
+    L.pairoff = take(sizeof(int) * (size_t)(4 * T + 8));
+    size_t nsp = (size_t)d.n_obs + d.n_model + 2;
+    L.perm = take(sizeof(int) * 2 * nsp);
+    L.sortbuf = take(sizeof(int) * 4 * nsp);
+    L.max_obs_gran = (int)((ip + 127) / 128) + T + 1;
+    L.max_mod_gran = (int)((jp + 127) / 128) + T + 1;
+    L.cone = take((sizeof(float4) + sizeof(float)) * (size_t)(L.max_obs_gran + L.max_mod_gran) + 64);
     L.fwd_blocks = take(sizeof(int) * (size_t)(2 * L.max_fwd_blocks + 2));
     L.jsum = take(sizeof(float) * 12 * (size_t)(d.n_model + 1));
     L.gsum = take(sizeof(float) * 16 * (size_t)(d.n_grains + 1));

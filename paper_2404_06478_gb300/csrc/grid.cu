@@ -51,9 +51,28 @@ __device__ __forceinline__ bool in_cubic_zone(const double q[4]) {
     return true;
 }
 
+// The dihedral groups D_n (n = 3: trigonal 32, n = 6: hexagonal 622) with
+// the n-fold axis along z and a 2-fold axis along x: turns by 2 pi m / n about
+// z give |<q, g>| = |q_w cos(pi m/n) + q_z sin(pi m/n)|, the 2-fold turns
+// about (cos phi, sin phi, 0), phi = pi m / n, give |q_x cos phi + q_y sin phi|.
+__device__ __forceinline__ bool in_dihedral_zone(const double q[4], int n) {
+    const double pi = 3.14159265358979323846;
+    double id = fabs(q[0]);
+    for (int m = 0; m < n; ++m) {
+        double s, c;
+        sincos(pi * m / n, &s, &c);
+        if (m > 0 && fabs(q[0] * c + q[3] * s) > id) return false;
+        if (fabs(q[1] * c + q[2] * s) > id) return false;
+    }
+    return true;
+}
+
 __device__ __forceinline__ bool grid_keep(long long i, long long n, int sym, double q[4]) {
     spiral_quat(i, n, q);
-    return sym != 24 || in_cubic_zone(q);
+    if (sym == 24) return in_cubic_zone(q);
+    if (sym == 6) return in_dihedral_zone(q, 3);
+    if (sym == 12) return in_dihedral_zone(q, 6);
+    return true;
 }
 
 __global__ void __launch_bounds__(kGridBlock) grid_count_kernel(long long n, int sym, int* counts) {
@@ -144,7 +163,8 @@ using namespace laue;
 extern "C" int laue_start_grid(laue_handle* h, long long n_full, int sym, int k, float cube_mm, long long cap,
                                float* R_out, float* x_out, long long* S_host, void* stream) {
     if (!h) return LAUE_ERR_INVALID_ARG;
-    if (n_full < 0 || n_full > (1LL << 40) || (sym != 1 && sym != 24) || k < 1 || k > 64 || !(cube_mm >= 0.0f) ||
+    if (n_full < 0 || n_full > (1LL << 40) || (sym != 1 && sym != 6 && sym != 12 && sym != 24) || k < 1 || k > 64 ||
+        !(cube_mm >= 0.0f) ||
         cap < 0 || (cap > 0 && (!R_out || !x_out)) || !S_host)
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "start_grid: bad arguments");
     if ((n_full + kGridBlock - 1) / kGridBlock > 0x7fffffffLL)

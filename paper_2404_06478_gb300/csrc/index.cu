@@ -107,7 +107,8 @@ extern "C" int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLa
     const bool grid = !startR && !startX;
     if (!lat || lat->M < 1 || !prm || S < 0 || n_max < 1 || !R_out || !x_out || !n_grains_host || !omega ||
         (!grid && S > 0 && (!startR || !startX)) || (obs->n > 0 && !assign) ||
-        (grid && (prm->grid_n < 0 || (prm->grid_sym != 1 && prm->grid_sym != 24) || prm->grid_k < 1 ||
+        (grid && (prm->grid_n < 0 || (prm->grid_sym != 1 && prm->grid_sym != 6 && prm->grid_sym != 12 &&
+                                      prm->grid_sym != 24) || prm->grid_k < 1 ||
                   !(prm->grid_cube >= 0.0f))) ||
         (prm && prm->mstep_kind != 0 && prm->mstep_kind != 1))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "index: bad arguments");

@@ -74,6 +74,18 @@ struct SkArgs {
     float4* modW;          // {-rz_a, -rz_b, 0, 0}
     int* I2_off;           // T+1 pair offsets of the observed blocks
     int* J2_off;           // T+1 pair offsets of the model blocks
+    // spatial order: within each angle block the spots are packed sorted by the
+    // direction of p (observed) or r (model); perm maps an ordered slot (global
+    // index, block offset + rank) to the caller's index, pos a caller index to
+    // its rank within the block
+    int *obs_perm, *obs_pos, *mod_perm, *mod_pos;
+    unsigned* sort_key;    // 2 (n_obs + n_model) keys (ping-pong)
+    int* sort_idx;         // 2 (n_obs + n_model) indices
+    // cones of the granules (kChunk pairs of one block) for the exact skipping
+    float4 *obs_cone, *mod_cone;
+    float *obs_ext, *mod_ext;
+    int *obs_gbase, *mod_gbase;  // T+1 first granule of each block
+    int skip;              // skip (tile, chunk) pairs whose plan entries all underflow
     int4* row_tiles;
     int4* col_tiles;
     int4* ang_tiles;       // per angle: {first row tile, #row tiles, first col tile, #col tiles}
@@ -99,6 +111,57 @@ struct SkArgs {
     float* marg_err;
     float* q;
 };
+
+// ------------------------------------------------------- sparse Sinkhorn
+// E-step restricted to the rho nearest observed spots of each model spot
+// (sparse.cu).  Potentials in base 2 as for SkArgs, indexed by the caller's
+// spot order.
+struct SpArgs {
+    int T;
+    int n_obs, n_model;
+    int rho;
+    const int* I_off;
+    const int* J_off;
+    const float4* p;       // observed spots (p, unused)
+    const float4* c;       // model centres (c, unused)
+    const float4* r;       // model rays (r, lambda)
+    // workspace
+    int2* cent;            // n_model x rho: {observed index or -1, e2 bits}, by increasing e2
+    int2* rent;            // CSR rows: {model index, e2 bits}, ascending model index
+    int* rptr;             // n_obs + 1 row starts
+    int* rfill;            // n_obs fill counters
+    float* F;              // n_obs
+    float* G;              // n_model
+    float* dust;           // F0, F0n, G0, log2U, log2O (nd each), errors (4)
+    float2* rpart;         // per row tile: LSE of F_i - kc
+    float2* cpart;         // per column tile: LSE of G_j
+    int4* rtile;           // {angle, first row, end row, 0}
+    int4* ctile;           // {angle, first column, end column, 0}
+    int* rt_base;          // T + 1 first row tile of each angle (entry T = row tile count)
+    int* ct_base;          // T + 1
+    int max_rt, max_ct;
+    int* ctrl;
+    float negK;            // -D^2 log2(e) / eps
+    float kc;              // c_out log2(e) / eps
+    double frac;
+    float to_user;
+    int mode;              // 0 global dustbins, 1 per angle
+    int warm;
+    // user buffers
+    float* f;
+    float* g;
+    float* dust_out;
+    int* assign;
+    float* margin;
+    float* marg_err;
+    float* q;
+    int* nbr_out;          // optional n_model x rho neighbour lists
+};
+
+constexpr int kSparseMaxRho = 64;  // neighbour lists live in shared memory while they are built
+size_t sparse_workspace_bytes(int T, int n_obs, int n_model, int rho);
+void sparse_carve(SpArgs& a, char* base, int T, int n_obs, int n_model, int rho);
+cudaError_t sparse_sinkhorn_run(const SpArgs& a, int n_iter, bool rows, bool cols, cudaStream_t s);
 
 constexpr int kSkVariants = 4;  // launch shapes of the pair passes (see sinkhorn.cu)
 

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
                 MsCol& C = lane ? B : A;
                 C.ok = lcol + lane < nj;
                 if (!C.ok) continue;
-                C.j = a.J_off[t] + lcol + lane;
+                C.j = a.mod_perm[a.J_off[t] + lcol + lane];  // the caller's index
                 C.n = m.grain[C.j];
                 C.t = t;
                 if (MODE == 0 && m.gstate[4 * C.n] == 0.0f) C.ok = false;  // converged grain
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
             for (int lane = 0; lane < 2; ++lane) {
                 MsCol& C = lane ? B : A;
                 if (lcol + lane >= nj) continue;
-                float* o = m.jsum + 12 * (size_t)(a.J_off[t] + lcol + lane);
+                float* o = m.jsum + 12 * (size_t)a.mod_perm[a.J_off[t] + lcol + lane];
                 if (MODE >= 2) {
                     // per-spot gradient: x part Gamma^T dC/dc, rotation part
                     // v x (Gamma^T y), y = -2 ((gr.u) e + (u.e) gr), u = Gamma R w_m

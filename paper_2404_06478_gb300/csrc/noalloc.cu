@@ -90,6 +90,7 @@ extern "C" int laue_cost_sinkhorn_noalloc(const LaueGeometry* geom, const LaueOb
         h.col_occ[v] = d->col_occ[v];
     }
     h.row_variant = h.col_variant = 0;
+    h.skip = 1;
     h.ws = d->scratch;
     h.ws_bytes = kStaticScratchBytes;
     cudaStream_t s = (cudaStream_t)stream;

@@ -101,12 +101,16 @@ __device__ __forceinline__ int block_of(const int* __restrict__ off, int T, int 
 }
 
 // ------------------------------------------------------ staged chunk pipeline
+constexpr int kMaxList = 512;  // chunks of one angle block a tile can list for skipping
+
 struct Stage {
     float4 s[4][2][kChunk];  // up to 4 arrays x 2 stages
     uint64_t bar[2];
     int tile;
     int last;
     float red_m[kTPB / 32], red_s[kTPB / 32];
+    int wcnt[kTPB / 32];
+    int list[kMaxList];      // chunks of the streamed side this tile needs
 };
 
 struct Srcs {
@@ -185,6 +189,124 @@ __device__ __forceinline__ bool stream_tile_prep(Stage& S, uint32_t (&parity)[2]
         if (threadIdx.x == 0 && ch + 2 < nch) issue_chunk(S, ch + 2, src, base, n_total);
     }
     return ok_all;
+}
+
+// Same over the chunks list[0..n_list) (in that order) only.
+__device__ __forceinline__ void issue_chunk_at(Stage& S, int st, int ch, const Srcs& src, int base, int n_total) {
+    int n = min(kChunk, n_total - ch * kChunk);
+    uint32_t bytes = (uint32_t)n * 16u;
+    mbar_expect_tx(&S.bar[st], bytes * (uint32_t)src.n);
+    for (int k = 0; k < src.n; ++k) bulk_g2s(S.s[k][st], src.p[k] + base + ch * kChunk, bytes, &S.bar[st]);
+}
+
+template <class Prep, class Body>
+__device__ __forceinline__ bool stream_list_prep(Stage& S, uint32_t (&parity)[2], const Srcs& src, int base,
+                                                 int n_total, int n_list, Prep prep, Body body) {
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < n_list && c < 2; ++c) issue_chunk_at(S, c & 1, S.list[c], src, base, n_total);
+    }
+    bool ok_all = true;
+    for (int c = 0; c < n_list; ++c) {
+        int st = c & 1, ch = S.list[c];
+        int n = min(kChunk, n_total - ch * kChunk);
+        bool ok = mbar_wait_bounded(&S.bar[st], parity[st]);
+        parity[st] ^= 1u;
+        if (ok) prep(st, n);
+        if (__syncthreads_or(!ok)) {
+            ok_all = false;
+            if (threadIdx.x == 0) {
+                for (int k = c + 1; k < n_list && k < c + 2; ++k) mbar_wait_bounded(&S.bar[k & 1], parity[k & 1]);
+            }
+            break;
+        }
+        body(st, n, ch * kChunk);
+        __syncthreads();
+        if (threadIdx.x == 0 && c + 2 < n_list) issue_chunk_at(S, st, S.list[c + 2], src, base, n_total);
+    }
+    return ok_all;
+}
+
+// ------------------------------------- exact underflow skipping (cone bounds)
+// A granule is kChunk pairs of one angle block (the unit of the staged
+// chunks); its cone bounds the directions of its spots: for observed spots
+// the unit vectors p / |p| and the smallest |p|, for model spots the rays r
+// and the largest |c|.  For an observed cone O and a model cone M, every pair
+// has an angle between rhat = (p - c)/|p - c| and r of at least
+//   th = angle(a_O, a_M) - beta_O - beta_M - asin(c_max / p_min)
+// (the direction of p seen from c differs from p/|p| by at most
+// asin(|c| / |p|)), so its cost is at least D^2 (2 sin(th/2))^2.
+struct Cone {
+    float ax, ay, az, beta, ext;  // axis, half-angle (rad), p_min or c_max
+};
+
+__device__ __forceinline__ Cone load_cone(const float4* cone, const float* ext, int g) {
+    float4 c = cone[g];
+    return Cone{c.x, c.y, c.z, c.w, ext[g]};
+}
+
+__device__ __forceinline__ float angle_between(float ax, float ay, float az, float bx, float by, float bz) {
+    float c = ax * bx + ay * by + az * bz;
+    return acosf(fminf(1.0f, fmaxf(-1.0f, c)));
+}
+
+// A cone containing two cones (obs: the smaller p_min, else the larger c_max).
+__device__ __forceinline__ Cone merge_cones(const Cone& a, const Cone& b, bool obs) {
+    float x = a.ax + b.ax, y = a.ay + b.ay, z = a.az + b.az;
+    float n2 = x * x + y * y + z * z;
+    Cone m;
+    if (n2 < 1e-12f) {
+        m = a;
+        m.beta = 3.2f;  // opposite axes: no bound
+    } else {
+        float r = rsqrtf(n2);
+        m.ax = x * r;
+        m.ay = y * r;
+        m.az = z * r;
+        m.beta = fmaxf(angle_between(m.ax, m.ay, m.az, a.ax, a.ay, a.az) + a.beta,
+                       angle_between(m.ax, m.ay, m.az, b.ax, b.ay, b.az) + b.beta) + 1e-5f;
+    }
+    m.ext = obs ? fminf(a.ext, b.ext) : fmaxf(a.ext, b.ext);
+    return m;
+}
+
+// Lower bound of K |rhat - r|^2 (K = D^2 log2(e) / eps) over the pairs of an
+// observed cone and a model cone; 0 when the cones may overlap.
+__device__ __forceinline__ float min_scaled_cost(const Cone& O, const Cone& M, float K) {
+    float sep = angle_between(O.ax, O.ay, O.az, M.ax, M.ay, M.az);
+    float off = O.ext > M.ext ? asinf(M.ext / O.ext) : 1.6f;
+    float th = sep - O.beta - M.beta - off - 1e-4f;
+    if (!(th > 0.0f)) return 0.0f;
+    float s = sinf(0.5f * fminf(th, 3.14159f));
+    return K * 4.0f * s * s;
+}
+
+// Every plan entry of a pair whose shifted exponent is below -kSkipLog2 is
+// flushed to exactly 0 by ex2.approx.ftz (below 2^-126), so the sums are
+// bit-identical with or without the pair.
+constexpr float kSkipLog2 = 130.0f;
+
+// Ordered list (in Stage::list) of the chunks c < nch with need(c); returns
+// its length.  All threads of the CTA call it.
+template <class Need>
+__device__ __forceinline__ int build_chunk_list(Stage& S, int nch, Need need) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int base = 0;
+    for (int c0 = 0; c0 < nch; c0 += blockDim.x) {
+        int c = c0 + threadIdx.x;
+        bool nd = c < nch && need(c);
+        unsigned b = __ballot_sync(0xffffffffu, nd);
+        if (lane == 0) S.wcnt[w] = __popc(b);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int k = 0; k < nw; ++k) {
+            if (k < w) before += S.wcnt[k];
+            total += S.wcnt[k];
+        }
+        if (nd) S.list[base + before + __popc(b & ((1u << lane) - 1u))] = c;
+        base += total;
+        __syncthreads();
+    }
+    return base;
 }
 
 // Same without a prep step.

@@ -74,6 +74,15 @@ __global__ void __launch_bounds__(1024) sk_schedule_kernel(SkArgs a) {
         }
         a.I2_off[T] = ip;
         a.J2_off[T] = jp;
+        int go = 0, gm = 0;
+        for (int t = 0; t < T; ++t) {
+            a.obs_gbase[t] = go;
+            a.mod_gbase[t] = gm;
+            go += (a.I2_off[t + 1] - a.I2_off[t] + kChunk - 1) / kChunk;
+            gm += (a.J2_off[t + 1] - a.J2_off[t] + kChunk - 1) / kChunk;
+        }
+        a.obs_gbase[T] = go;
+        a.mod_gbase[T] = gm;
         int nr = 0, nc = 0;
         for (int k = 0; k < T; ++k) {
             int t = order_r[k];
@@ -134,6 +143,209 @@ __global__ void __launch_bounds__(1024) sk_schedule_kernel(SkArgs a) {
     }
 }
 
+// ------------------------------------------------------- spatial order
+// Within each angle block the spots are ranked by a 23-bit key of their
+// direction (observed: p / |p|, model: the ray r): the cube-map face of the
+// direction and the Morton interleave of its two in-face coordinates at 10
+// bits each.  Spots close on a detector get close ranks, so runs of kChunk
+// pairs are spatially compact and their cones are narrow.  One CTA sorts one
+// block (LSD radix sort, 4-bit digits, stable: ties keep the caller's order).
+__device__ __forceinline__ unsigned spread10(unsigned v) {
+    v &= 1023u;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__device__ __forceinline__ unsigned direction_key(float x, float y, float z) {
+    float ax = fabsf(x), ay = fabsf(y), az = fabsf(z);
+    int face;
+    float m, u, v;
+    if (ax >= ay && ax >= az) {
+        face = x < 0.0f;
+        m = ax;
+        u = y;
+        v = z;
+    } else if (ay >= az) {
+        face = 2 + (y < 0.0f);
+        m = ay;
+        u = x;
+        v = z;
+    } else {
+        face = 4 + (z < 0.0f);
+        m = az;
+        u = x;
+        v = y;
+    }
+    if (!(m > 0.0f)) return 0u;
+    unsigned qu = (unsigned)fminf(1023.0f, fmaxf(0.0f, (u / m + 1.0f) * 512.0f));
+    unsigned qv = (unsigned)fminf(1023.0f, fmaxf(0.0f, (v / m + 1.0f) * 512.0f));
+    return ((unsigned)face << 20) | spread10(qu) | (spread10(qv) << 1);
+}
+
+constexpr int kSortThreads = 1024;
+
+// Blocks 0..T-1 sort the observed blocks, T..2T-1 the model blocks.
+__global__ void __launch_bounds__(kSortThreads) sk_sort_kernel(SkArgs a) {
+    __shared__ int cnt[kSortThreads / 32][16];
+    __shared__ int dbase[16];
+    const bool mod = (int)blockIdx.x >= a.T;
+    const int t = mod ? blockIdx.x - a.T : blockIdx.x;
+    const int* off = mod ? a.J_off : a.I_off;
+    const int b0 = off[t], n = off[t + 1] - b0;
+    const size_t nsp = (size_t)a.n_obs + a.n_model + 2;
+    const size_t side0 = mod ? (size_t)a.n_obs + 1 : 0;
+    unsigned* kbuf[2] = {a.sort_key + side0 + b0, a.sort_key + nsp + side0 + b0};
+    int* ibuf[2] = {a.sort_idx + side0 + b0, a.sort_idx + nsp + side0 + b0};
+    int* perm = (mod ? a.mod_perm : a.obs_perm) + b0;
+    int* pos = (mod ? a.mod_pos : a.obs_pos) + b0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int l = threadIdx.x; l < n; l += kSortThreads) {
+        float4 v = mod ? a.mod_r[b0 + l] : a.obs_p[b0 + l];
+        kbuf[0][l] = direction_key(v.x, v.y, v.z);
+        ibuf[0][l] = l;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 6; ++pass) {
+        const unsigned* sk = kbuf[pass & 1];
+        const int* si = ibuf[pass & 1];
+        unsigned* dk = kbuf[(pass + 1) & 1];
+        int* di = ibuf[(pass + 1) & 1];
+        const int shift = 4 * pass;
+        if (threadIdx.x < 16) dbase[threadIdx.x] = 0;
+        __syncthreads();
+        for (int l = threadIdx.x; l < n; l += kSortThreads) atomicAdd(&dbase[(sk[l] >> shift) & 15u], 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int d = 0; d < 16; ++d) {
+                int c = dbase[d];
+                dbase[d] = acc;
+                acc += c;
+            }
+        }
+        __syncthreads();
+        for (int c0 = 0; c0 < n; c0 += kSortThreads) {
+            int l = c0 + threadIdx.x;
+            bool valid = l < n;
+            unsigned key = valid ? sk[l] : 0u;
+            int idx = valid ? si[l] : 0;
+            int d = valid ? (int)((key >> shift) & 15u) : 16;
+            unsigned mine = 0u;
+            for (int v = 0; v < 16; ++v) {
+                unsigned b = __ballot_sync(0xffffffffu, d == v);
+                if (d == v) mine = b;
+                if (lane == 0) cnt[w][v] = __popc(b);
+            }
+            __syncthreads();
+            if (threadIdx.x < 16) {
+                int acc = dbase[threadIdx.x];
+                for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+                    int c = cnt[ww][threadIdx.x];
+                    cnt[ww][threadIdx.x] = acc;
+                    acc += c;
+                }
+                dbase[threadIdx.x] = acc;
+            }
+            __syncthreads();
+            if (valid) {
+                int p = cnt[w][d] + __popc(mine & ((1u << lane) - 1u));
+                dk[p] = key;
+                di[p] = idx;
+            }
+            __syncthreads();
+        }
+    }
+    // six passes: the sorted order is back in buffer 0
+    for (int l = threadIdx.x; l < n; l += kSortThreads) {
+        int idx = ibuf[0][l];
+        perm[l] = b0 + idx;
+        pos[idx] = l;
+    }
+}
+
+// Cone of each granule (kChunk pairs of one block), one warp per granule:
+// axis = normalised mean direction, half-angle = largest angle from it, and
+// the smallest |p| (observed) or largest |c| (model).
+__global__ void __launch_bounds__(256) sk_cone_kernel(SkArgs a) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    int n_go = a.obs_gbase[a.T], n_gm = a.mod_gbase[a.T];
+    if (warp >= n_go + n_gm) return;
+    const bool mod = warp >= n_go;
+    const int g = mod ? warp - n_go : warp;
+    const int* gb = mod ? a.mod_gbase : a.obs_gbase;
+    const int t = block_of(gb, a.T, g);
+    const int* off = mod ? a.J_off : a.I_off;
+    const int* poff = mod ? a.J2_off : a.I2_off;
+    const int nspots = off[t + 1] - off[t];
+    const int l0 = 2 * kChunk * (g - gb[t]);           // first spot rank of the granule
+    const int l1 = min(nspots, l0 + 2 * kChunk);
+    float d[2 * kChunk / 32][3];
+    float sx = 0.f, sy = 0.f, sz = 0.f, ext = mod ? 0.0f : 3.0e38f;
+    int cntv = 0;
+    for (int k = 0; k < 2 * kChunk / 32; ++k) {
+        int l = l0 + lane + 32 * k;
+        d[k][0] = d[k][1] = d[k][2] = 0.0f;
+        if (l >= l1) continue;
+        int q = poff[t] + (l >> 1), ln = l & 1;
+        float x, y, z;
+        if (mod) {
+            float4 Z = a.modZ[q], W = a.modW[q], X = a.modX[q], Y = a.modY[q];
+            x = -(ln ? Z.y : Z.x);
+            y = -(ln ? Z.w : Z.z);
+            z = -(ln ? W.y : W.x);
+            float cx = ln ? X.y : X.x, cy = ln ? X.w : X.z, cz = ln ? Y.y : Y.x;
+            ext = fmaxf(ext, sqrtf(cx * cx + cy * cy + cz * cz));
+        } else {
+            float4 X = a.obsX[q], Y = a.obsY[q];
+            x = ln ? X.y : X.x;
+            y = ln ? X.w : X.z;
+            z = ln ? Y.y : Y.x;
+            float r = sqrtf(x * x + y * y + z * z);
+            ext = fminf(ext, r);
+        }
+        float r = rsqrtf(fmaxf(x * x + y * y + z * z, 1e-30f));
+        d[k][0] = x * r;
+        d[k][1] = y * r;
+        d[k][2] = z * r;
+        sx += d[k][0];
+        sy += d[k][1];
+        sz += d[k][2];
+        ++cntv;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        ext = mod ? fmaxf(ext, __shfl_xor_sync(0xffffffffu, ext, o)) : fminf(ext, __shfl_xor_sync(0xffffffffu, ext, o));
+    }
+    float n2 = sx * sx + sy * sy + sz * sz;
+    float ax = 0.f, ay = 0.f, az = 1.f;
+    bool degenerate = !(n2 > 1e-12f);
+    if (!degenerate) {
+        float r = rsqrtf(n2);
+        ax = sx * r;
+        ay = sy * r;
+        az = sz * r;
+    }
+    float beta = 0.0f;
+    for (int k = 0; k < 2 * kChunk / 32; ++k) {
+        int l = l0 + lane + 32 * k;
+        if (l >= l1) continue;
+        beta = fmaxf(beta, angle_between(ax, ay, az, d[k][0], d[k][1], d[k][2]));
+    }
+    for (int o = 16; o > 0; o >>= 1) beta = fmaxf(beta, __shfl_xor_sync(0xffffffffu, beta, o));
+    if (lane == 0) {
+        if (degenerate) beta = 3.2f;  // no bound
+        float4* cone = mod ? a.mod_cone : a.obs_cone;
+        float* ex = mod ? a.mod_ext : a.obs_ext;
+        cone[g] = make_float4(ax, ay, az, beta + 1e-5f);
+        ex[g] = ext;
+    }
+}
+
 // ------------------------------------------------------------------- pack
 // Pair-interleaved workspace copies; F, G from the caller's potentials on a
 // warm start, else 0.  The thread of the last element of an odd block also
@@ -143,7 +355,7 @@ __global__ void sk_pack_kernel(SkArgs a) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < a.n_obs) {
         int t = block_of(a.I_off, a.T, k);
-        int l = k - a.I_off[t];
+        int l = a.obs_pos[k];  // rank of the spot in its block's spatial order
         int q = a.I2_off[t] + (l >> 1), lane = l & 1;
         float4 p = a.obs_p[k];
         float* X = (float*)&a.obsX[q];
@@ -152,7 +364,7 @@ __global__ void sk_pack_kernel(SkArgs a) {
         X[2 + lane] = p.y;
         Y[lane] = p.z;
         Y[2 + lane] = a.warm ? a.f[k] * s : 0.0f;
-        if (lane == 0 && k + 1 == a.I_off[t + 1]) {
+        if (lane == 0 && l + 1 == a.I_off[t + 1] - a.I_off[t]) {
             X[1] = 0.0f;
             X[3] = 0.0f;
             Y[1] = kPadFar;
@@ -161,7 +373,7 @@ __global__ void sk_pack_kernel(SkArgs a) {
     }
     if (k < a.n_model) {
         int t = block_of(a.J_off, a.T, k);
-        int l = k - a.J_off[t];
+        int l = a.mod_pos[k];
         int q = a.J2_off[t] + (l >> 1), lane = l & 1;
         float4 c = a.mod_c[k];
         float4 r = a.mod_r[k];
@@ -177,7 +389,7 @@ __global__ void sk_pack_kernel(SkArgs a) {
         Z[2 + lane] = -r.y;
         W[lane] = -r.z;
         W[2 + lane] = 0.0f;
-        if (lane == 0 && k + 1 == a.J_off[t + 1]) {
+        if (lane == 0 && l + 1 == a.J_off[t + 1] - a.J_off[t]) {
             X[1] = 0.0f;
             X[3] = 0.0f;
             Y[1] = 0.0f;
@@ -397,18 +609,41 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
         R.pzb = dup(Y.y);
         const float shift = ub ? D.Gmax[t] : fmaxf(D.Gmax[t], dustv);
         f2 Sa = pk(ub ? 0.0f : ex2(dustv - shift), 0.0f), Sb = Sa;
-        bool ok = stream_tile_prep(
-            S, parity, src, j0, nj,
-            [&](int st, int n) {
-                for (int k = threadIdx.x; k < n; k += TPB) {
-                    float4& y = S.s[1][st][k];
-                    y.z -= shift;
-                    y.w -= shift;
-                }
-            },
-            [&](int st, int n, int) {
-                if (valid) row_chunk_sum(R, S.s[0][st], S.s[1][st], S.s[2][st], S.s[3][st], n, K2, Sa, Sb);
+        auto prep = [&](int st, int n) {
+            for (int k = threadIdx.x; k < n; k += TPB) {
+                float4& y = S.s[1][st][k];
+                y.z -= shift;
+                y.w -= shift;
+            }
+        };
+        auto body = [&](int st, int n, int) {
+            if (valid) row_chunk_sum(R, S.s[0][st], S.s[1][st], S.s[2][st], S.s[3][st], n, K2, Sa, Sb);
+        };
+        // the model chunks this tile of observed spots can see (exact underflow skipping)
+        const int nch = (nj + kChunk - 1) / kChunk;
+        const bool use_list = a.skip && nch > 0 && nch <= kMaxList;
+        int n_list = nch;
+        if (use_list) {
+            const int g0 = a.obs_gbase[t] + (td.y - a.I2_off[t]) / kChunk;
+            const int g1 = a.obs_gbase[t] + (td.y + td.z - 1 - a.I2_off[t]) / kChunk;
+            Cone O = load_cone(a.obs_cone, a.obs_ext, g0);
+            if (g1 != g0) O = merge_cones(O, load_cone(a.obs_cone, a.obs_ext, g1), true);
+            const float K = -a.negKD2;
+            const int mg = a.mod_gbase[t];
+            n_list = build_chunk_list(S, nch, [&](int c) {
+                return min_scaled_cost(O, load_cone(a.mod_cone, a.mod_ext, mg + c), K) <= kSkipLog2;
             });
+        }
+        bool ok = use_list ? stream_list_prep(S, parity, src, j0, nj, n_list, prep, body)
+                           : stream_tile_prep(S, parity, src, j0, nj, prep, body);
+        if (threadIdx.x == 0) {
+            long long np = 0;
+            if (use_list)
+                for (int c = 0; c < n_list; ++c) np += min(kChunk, nj - S.list[c] * kChunk);
+            else
+                np = nj;
+            atomicAdd((unsigned long long*)(a.ctrl + CTRL_SK_PAIRS), (unsigned long long)(4LL * td.z * np));
+        }
         if (!ok) {
             if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
             break;
@@ -495,18 +730,41 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
         float dz = ub ? kNegHuge : D.F0[a.mode ? t : 0];  // unmatched-model row, C_0j = 0
         const float shift = ub ? D.Fmax[t] : fmaxf(D.Fmax[t], dz);
         f2 Sa = pk(ub ? 0.0f : ex2(dz - shift), 0.0f), Sb = Sa;
-        bool ok = stream_tile_prep(
-            S, parity, src, i0, ni,
-            [&](int st, int n) {
-                for (int k = threadIdx.x; k < n; k += TPB) {
-                    float4& y = S.s[1][st][k];
-                    y.z -= shift;
-                    y.w -= shift;
-                }
-            },
-            [&](int st, int n, int) {
-                if (valid) col_chunk_sum(C, S.s[0][st], S.s[1][st], n, K2, Sa, Sb);
+        auto prep = [&](int st, int n) {
+            for (int k = threadIdx.x; k < n; k += TPB) {
+                float4& y = S.s[1][st][k];
+                y.z -= shift;
+                y.w -= shift;
+            }
+        };
+        auto body = [&](int st, int n, int) {
+            if (valid) col_chunk_sum(C, S.s[0][st], S.s[1][st], n, K2, Sa, Sb);
+        };
+        // the observed chunks this tile of model spots can see (exact underflow skipping)
+        const int nch = (ni + kChunk - 1) / kChunk;
+        const bool use_list = a.skip && nch > 0 && nch <= kMaxList;
+        int n_list = nch;
+        if (use_list) {
+            const int g0 = a.mod_gbase[t] + (td.y - a.J2_off[t]) / kChunk;
+            const int g1 = a.mod_gbase[t] + (td.y + td.z - 1 - a.J2_off[t]) / kChunk;
+            Cone M = load_cone(a.mod_cone, a.mod_ext, g0);
+            if (g1 != g0) M = merge_cones(M, load_cone(a.mod_cone, a.mod_ext, g1), false);
+            const float K = -a.negKD2;
+            const int og = a.obs_gbase[t];
+            n_list = build_chunk_list(S, nch, [&](int c) {
+                return min_scaled_cost(load_cone(a.obs_cone, a.obs_ext, og + c), M, K) <= kSkipLog2;
             });
+        }
+        bool ok = use_list ? stream_list_prep(S, parity, src, i0, ni, n_list, prep, body)
+                           : stream_tile_prep(S, parity, src, i0, ni, prep, body);
+        if (threadIdx.x == 0) {
+            long long np = 0;
+            if (use_list)
+                for (int c = 0; c < n_list; ++c) np += min(kChunk, ni - S.list[c] * kChunk);
+            else
+                np = ni;
+            atomicAdd((unsigned long long*)(a.ctrl + CTRL_SK_PAIRS), (unsigned long long)(4LL * td.z * np));
+        }
         if (!ok) {
             if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
             break;
@@ -583,14 +841,16 @@ struct Top2 {
         b2 = kNegHuge;
         arg = -1;
     }
-    __device__ __forceinline__ void add(float v, int j) {
+    // j: the spot's slot in the spatial order; perm maps slots to the caller's
+    // indices, and ties go to the lowest caller index
+    __device__ __forceinline__ void add(float v, int j, const int* perm) {
         if (v > m) {
             s = s * ex2(m - v) + 1.0f;
             m = v;
         } else {
             s += ex2(v - m);
         }
-        if (v > b1) {  // strict: ties keep the lowest index
+        if (v > b1 || (v == b1 && v > kNegHuge && perm[j] < perm[arg])) {
             b2 = b1;
             b1 = v;
             arg = j;
@@ -637,10 +897,10 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
                 f2 va = pair_v2(pxa, pya, pza, Xm.x, Xm.y, Ym.x, Zm.x, Zm.y, Wm.x, K2, Ym.y);
                 f2 vv = pair_v2(pxb, pyb, pzb, Xm.x, Xm.y, Ym.x, Zm.x, Zm.y, Wm.x, K2, Ym.y);
                 int j = jbase + 2 * (off + k);
-                A.add(lo(va), j);
-                A.add(hi(va), j + 1);  // padding slots have -3e38 and never win
-                B.add(lo(vv), j);
-                B.add(hi(vv), j + 1);
+                A.add(lo(va), j, a.mod_perm);
+                A.add(hi(va), j + 1, a.mod_perm);  // padding slots have -3e38 and never win
+                B.add(lo(vv), j, a.mod_perm);
+                B.add(hi(vv), j + 1, a.mod_perm);
             }
         });
         if (!ok) {
@@ -668,8 +928,9 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
                 my_err = fmaxf(my_err, fabsf(rs - 1.0f));
                 // unbalanced plan: a spot that keeps most of its mass is an outlier
                 if (a.mode == 2 && !(rs >= 0.5f)) P.arg = -1;
-                if (a.assign) a.assign[i + lane] = P.arg;
-                if (a.margin) a.margin[i + lane] = ex2(F + P.b1) - (P.b2 > kNegHuge ? ex2(F + P.b2) : 0.0f);
+                int ic = a.obs_perm[i + lane];  // the caller's index of this observed spot
+                if (a.assign) a.assign[ic] = P.arg >= 0 ? a.mod_perm[P.arg] : -1;
+                if (a.margin) a.margin[ic] = ex2(F + P.b1) - (P.b2 > kNegHuge ? ex2(F + P.b2) : 0.0f);
             }
         }
     }
@@ -733,7 +994,7 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_col_kernel(SkArgs a) {
                 float G = lane ? Ym.w : Ym.z;
                 float ssum = lo(L.S) + hi(L.S);
                 float qj = ssum > 0.0f ? ex2(G + L.m + lg2(ssum)) : 0.0f;
-                if (a.q) a.q[a.J_off[t] + lcol + lane] = qj;
+                if (a.q) a.q[a.mod_perm[a.J_off[t] + lcol + lane]] = qj;
                 my_err = fmaxf(my_err, fabsf(qj + ex2(G + F0) - 1.0f));
             }
         }
@@ -754,14 +1015,14 @@ __global__ void sk_finish_kernel(SkArgs a, int have_rows, int have_cols) {
     bool bad = false;
     if (k < a.n_obs) {
         int t = block_of(a.I_off, a.T, k);
-        int l = k - a.I_off[t];
+        int l = a.obs_pos[k];
         float v = ((const float*)&a.obsY[a.I2_off[t] + (l >> 1)])[2 + (l & 1)];
         bad |= !isfinite(v);
         a.f[k] = v * a.to_user;
     }
     if (k < a.n_model) {
         int t = block_of(a.J_off, a.T, k);
-        int l = k - a.J_off[t];
+        int l = a.mod_pos[k];
         float v = ((const float*)&a.modY[a.J2_off[t] + (l >> 1)])[2 + (l & 1)];
         bad |= !isfinite(v);
         a.g[k] = v * a.to_user;
@@ -811,7 +1072,12 @@ cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s) {
     int blocks = (nmax + 255) / 256;
     if (blocks < 1) blocks = 1;
     sk_schedule_kernel<<<1, 1024, 0, s>>>(a);
+    if (a.T > 0) sk_sort_kernel<<<2 * a.T, kSortThreads, 0, s>>>(a);
     sk_pack_kernel<<<blocks, 256, 0, s>>>(a);
+    {
+        int max_gran = (a.n_obs + a.n_model) / (2 * kChunk) + 2 * a.T + 2;  // bound on the granule count
+        sk_cone_kernel<<<(max_gran * 32 + 255) / 256, 256, 0, s>>>(a);
+    }
     if (a.mode != 2) sk_init_dust_kernel<<<1, 1024, 0, s>>>(a);
     if (a.T > 0) sk_init_gmax_kernel<<<a.T, 256, 0, s>>>(a);
     return cudaGetLastError();

@@ -77,6 +77,52 @@ CONFIGS = {
 }
 
 
+@dataclasses.dataclass(frozen=True)
+class Cell:
+    """Unit cell (Angstrom, degrees)."""
+    a: float
+    b: float
+    c: float
+    alpha: float
+    beta: float
+    gamma: float
+
+
+# Ruby (corundum, space group R-3c) in its hexagonal setting
+RUBY = Cell(4.759, 4.759, 12.991, 90.0, 90.0, 120.0)
+
+
+def ruby_hkl(hmax: int = 4, lmax: int = 12) -> np.ndarray:
+    """Reflections (h, k, l) with |h|, |k|, |h + k| <= hmax (the bound on the
+    three hexagonal a-axis indices, which the crystal's rotations permute) and
+    |l| <= lmax, allowed by the reflection conditions of R-3c on hexagonal
+    axes: -h + k + l divisible by 3 (rhombohedral centring), and l even on the
+    three zones with one a-axis index zero (h = 0, k = 0 or h + k = 0: the c
+    glides that the 3-fold axis relates).  Input data of the crystal, not part
+    of the indexing method."""
+    out = []
+    for h in range(-hmax, hmax + 1):
+        for k in range(-hmax, hmax + 1):
+            if abs(h + k) > hmax:
+                continue
+            for l in range(-lmax, lmax + 1):
+                if h == 0 and k == 0 and l == 0:
+                    continue
+                if (-h + k + l) % 3 != 0:
+                    continue
+                if (h == 0 or k == 0 or h + k == 0) and l % 2 != 0:
+                    continue
+                out.append((h, k, l))
+    return np.array(out, np.int32)
+
+
+def bcc_hkl(hmax: int) -> np.ndarray:
+    """Reflections of a body-centred cubic lattice, |h|, |k|, |l| <= hmax, h+k+l even."""
+    r = range(-hmax, hmax + 1)
+    return np.array([(h, k, l) for h in r for k in r for l in r
+                     if (h, k, l) != (0, 0, 0) and (h + k + l) % 2 == 0], np.int32)
+
+
 def omegas(cfg: Config) -> np.ndarray:
     """Rotation angles omega_t = t * span / T (radians)."""
     return np.radians(cfg.span_deg) * np.arange(cfg.T, dtype=np.float64) / cfg.T

@@ -138,3 +138,31 @@ def test_host_constants_match_oracle(native):
                                                                            rel=1e-14)
     L = native.lib()
     assert L.laue_c_out(-1.0, 200.0) < 0 and L.laue_anneal_eps(1.0, -1, 0, 100.0) < 0
+
+
+def test_general_lattice_tables_match_oracle(native):
+    """laue_reciprocal_basis and laue_reflections_hkl (host functions) agree with
+    the oracle's: the hexagonal ruby cell with its R-3c reflections, and a
+    cubic cell given as a list.  Lines whose multiples are not 1..n of a base
+    are rejected."""
+    import oracle
+    import synthgen as sg
+    from paper_2404_06478_gb300 import api
+    c = sg.RUBY
+    B = api.reciprocal_basis(c.a, c.b, c.c, c.alpha, c.beta, c.gamma)
+    Bo = oracle.reciprocal_basis(c.a, c.b, c.c, c.alpha, c.beta, c.gamma)
+    np.testing.assert_allclose(B, Bo, atol=1e-15)
+    for Bm, hkl in ((Bo, sg.ruby_hkl(4, 12)), (np.eye(3) / 2.87, sg.bcc_hkl(6)),
+                    (oracle.reciprocal_basis(5.0, 6.0, 7.0, 80.0, 95.0, 105.0), sg.bcc_hkl(3))):
+        w, nh, h0 = api.reflections_hkl(Bm, hkl)
+        P = oracle.reflections_hkl(Bm, hkl)
+        np.testing.assert_array_equal(h0, P.hkl0)
+        np.testing.assert_array_equal(nh, P.nharm)
+        np.testing.assert_allclose(w[:, :3], P.w, atol=1e-7)
+        np.testing.assert_allclose(w[:, 3], P.d0, rtol=1e-7)
+    with pytest.raises(Exception):
+        api.reflections_hkl(np.eye(3), [[1, 0, 0], [3, 0, 0]])  # 1x and 3x without 2x
+    with pytest.raises(ValueError):
+        oracle.reflections_hkl(np.eye(3), [[1, 0, 0], [3, 0, 0]])
+    with pytest.raises(Exception):
+        api.reciprocal_basis(5.0, 5.0, 5.0, 10.0, 10.0, 170.0)  # angles that close no cell

@@ -828,3 +828,130 @@ def test_unbalanced_large_kappa_lambda_is_balanced():
     h = oracle.harvest_unbalanced(200.0, p, [0, n], [0, n], c, r, eps, fu, gu)
     np.testing.assert_allclose(h["rowmass"], 1.0, atol=1e-8)
     np.testing.assert_allclose(h["q"], 1.0, atol=1e-8)
+
+
+# ------------------------------------------------------- general lattices
+
+def test_reflections_from_hkl_list_equal_the_cubic_table():
+    """The general builder (reciprocal basis + list of allowed reflections)
+    with B = I / a and the body-centred list reproduces the cubic table (entries,
+    spacings, harmonics, order) that its own pins fix."""
+    for hmax in (4, 6):
+        P = oracle.reflections(2.87, hmax, 1)
+        Q = oracle.reflections_hkl(np.eye(3) / 2.87, sg.bcc_hkl(hmax))
+        np.testing.assert_array_equal(Q.hkl0, P.hkl0)
+        np.testing.assert_array_equal(Q.nharm, P.nharm)
+        np.testing.assert_allclose(Q.w, P.w, atol=1e-14)
+        np.testing.assert_allclose(Q.d0, P.d0, rtol=1e-14)
+
+
+def test_hexagonal_reciprocal_basis_and_spacings_closed_form():
+    """Hexagonal cell (ruby): |b1| = |b2| = 2 / (a sqrt 3) at 60 degrees, b3 =
+    (0, 0, 1/c); every entry's spacing obeys the textbook
+    1/d^2 = 4 (h^2 + hk + k^2) / (3 a^2) + l^2 / c^2."""
+    c = sg.RUBY
+    B = oracle.reciprocal_basis(c.a, c.b, c.c, c.alpha, c.beta, c.gamma)
+    b1, b2, b3 = B[:, 0], B[:, 1], B[:, 2]
+    assert np.linalg.norm(b1) == pytest.approx(2 / (c.a * math.sqrt(3)), rel=1e-12)
+    assert np.linalg.norm(b2) == pytest.approx(2 / (c.a * math.sqrt(3)), rel=1e-12)
+    assert math.degrees(math.acos(b1 @ b2 / (np.linalg.norm(b1) * np.linalg.norm(b2)))) == pytest.approx(60.0, abs=1e-9)
+    np.testing.assert_allclose(b3, [0, 0, 1 / c.c], atol=1e-15)
+    P = oracle.reflections_hkl(B, sg.ruby_hkl(4, 12))
+    h, k, l = P.hkl0[:, 0].astype(float), P.hkl0[:, 1].astype(float), P.hkl0[:, 2].astype(float)
+    inv_d2 = 4 * (h * h + h * k + k * k) / (3 * c.a ** 2) + l * l / c.c ** 2
+    np.testing.assert_allclose(P.d0, 1 / np.sqrt(inv_d2), rtol=1e-12)
+    assert len(P.d0) > 50 and P.nharm.max() >= 2
+
+
+def _d3():
+    """The trigonal group 32 with the 3-fold axis along z and a 2-fold axis
+    along x (hexagonal a1), as matrices."""
+    out = []
+    for q in range(3):
+        out.append(_rotvec([0, 0, 2 * math.pi * q / 3]))
+    for q in range(3):
+        phi = math.pi * q / 3
+        out.append(_rotvec(np.array([math.cos(phi), math.sin(phi), 0.0]) * math.pi))
+    return out
+
+
+def test_ruby_spots_are_invariant_under_the_trigonal_group():
+    """With the ruby plane table, a grain at R and at R S for S in the trigonal
+    group 32 make the same spots (the reflection list carries the crystal's
+    symmetry); a 90-degree turn about c, which is not a symmetry of the cell,
+    makes different ones."""
+    c = sg.RUBY
+    B = oracle.reciprocal_basis(c.a, c.b, c.c, c.alpha, c.beta, c.gamma)
+    P = oracle.reflections_hkl(B, sg.ruby_hkl(4, 12))
+    rng = np.random.default_rng(31)
+    R = sg.random_rotations(1, rng)[0]
+    x = np.array([0.3, -0.7, 1.1])
+    om = np.radians(np.arange(8) * 22.5)
+
+    def spots(Rm):
+        fw = oracle.forward(GEOM, P, Rm[None], x[None], om)
+        key = np.c_[fw["t"], np.round(fw["spot"], 6)]
+        return key[np.lexsort(key.T[::-1])]
+
+    ref = spots(R)
+    assert len(ref) > 20
+    for S in _d3():
+        np.testing.assert_allclose(spots(R @ S), ref, atol=1e-6)
+    other = spots(R @ _rotvec([0, 0, math.pi / 2]))
+    assert other.shape != ref.shape or np.abs(other - ref).max() > 1.0
+
+
+@pytest.mark.parametrize("sym,n_axis", [(6, 3), (12, 6)])
+def test_start_grid_dihedral_fundamental_zone(sym, n_axis):
+    """Start grids for the trigonal (32) and hexagonal (622) groups keep 1/6 and
+    1/12 of the spiral, and every kept orientation lies in the group's
+    fundamental zone as it is written in Rodrigues space: |r_z| <= tan(pi / 2n)
+    for the n-fold axis along z and |r . a| <= 1 for every 2-fold axis a in the
+    xy plane at multiples of pi / n from x."""
+    R, _ = oracle.start_grid(60000, sym=sym, k=1)
+    assert abs(len(R) - 60000 / sym) < 0.03 * 60000 / sym
+    q = _mat_to_quat(R)
+    rod = q[:, 1:] / q[:, :1]
+    assert np.all(np.abs(rod[:, 2]) <= math.tan(math.pi / (2 * n_axis)) + 1e-9)
+    for m in range(n_axis):
+        phi = math.pi * m / n_axis
+        assert np.all(np.abs(rod[:, 0] * math.cos(phi) + rod[:, 1] * math.sin(phi)) <= 1 + 1e-9)
+
+
+# ----------------------------------------------- sparse assignment (rho-NN)
+
+def test_knn_sets_are_the_rho_nearest_by_angle(tiny):
+    """Section "Working with sparse assignment matrices": each model spot keeps
+    its rho nearest observed spots of the same angle block.  Checked by brute
+    force on the angle between each ray estimate and the model ray (the cost is
+    2 D^2 (1 - cos) of that angle), ties to the lower index."""
+    fw, obs = tiny["fw"], tiny["obs"]
+    rho = 6
+    nbr = oracle.knn(GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3], rho)
+    for j in range(0, len(fw["t"]), 7):
+        t = fw["t"][j]
+        i0, i1 = obs.I_off[t], obs.I_off[t + 1]
+        d = obs.p[i0:i1] - fw["center"][j]
+        cosang = d @ fw["ray"][j, :3] / np.linalg.norm(d, axis=1)
+        ang = np.arccos(np.clip(cosang, -1, 1))
+        want = np.lexsort((np.arange(i0, i1), ang))[:rho] + i0
+        np.testing.assert_array_equal(nbr[j][:len(want)], want)
+
+
+def test_sparse_sinkhorn_limits(tiny):
+    """With rho at least the largest block the sparse plan is the dense one
+    (same potentials); with rho = 32 at eps = 1 mm^2 every left-out entry is
+    below exp(-100), so the potentials agree with the dense ones to 1e-9."""
+    fw, obs = tiny["fw"], tiny["obs"]
+    args = (GEOM.D, obs.p, obs.I_off, fw["J_off"], fw["center"], fw["ray"][:, :3], 1.0, 2.25, 0, 0.4, 40)
+    fd_, gd_, fdd, gdd, _ = oracle.sinkhorn(*args)
+    big = int(np.diff(obs.I_off).max())
+    fs, gs, fds, gds = oracle.sinkhorn_sparse(*args, rho=big)
+    np.testing.assert_allclose(fs, fd_, atol=1e-12)
+    np.testing.assert_allclose(gs, gd_, atol=1e-12)
+    np.testing.assert_allclose(np.r_[fds, gds], np.r_[fdd, gdd], atol=1e-12)
+    fs, gs, _, _ = oracle.sinkhorn_sparse(*args, rho=32)
+    np.testing.assert_allclose(fs, fd_, atol=1e-9)
+    np.testing.assert_allclose(gs, gd_, atol=1e-9)
+    fs, gs, _, _ = oracle.sinkhorn_sparse(*args, rho=1)
+    assert np.abs(fs - fd_).max() > 1e-6  # a one-neighbour support is a different plan
