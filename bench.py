@@ -684,6 +684,51 @@ def main():
                    grains=cfg.n_grains, note="gradient of sum_ij Q_ij C_ij wrt each grain's axis-angle and "
                                              "position (Q from 200 Sinkhorn iterations, costs recomputed)")
 
+    # the sparse E-step (each model spot keeps its rho = 32 nearest observed
+    # spots) at the same size: set-up (neighbour lists and their transpose)
+    # and per-iteration time, HBM roofline of the passes, and how often its
+    # hard assignment equals the dense plan's
+    rho = 32
+    sp_kw = dict(rho=rho, harvest=True)
+    api.cost_sinkhorn_sparse(W["h"], W["geom"], W["ob"], W["model"], cfg.eps, W["c_out"], 2, **sp_kw)
+    torch.cuda.synchronize()
+    es = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    es[0].record(stream)
+    api.cost_sinkhorn_sparse(W["h"], W["geom"], W["ob"], W["model"], cfg.eps, W["c_out"], 0, **sp_kw)
+    es[1].record(stream)
+    es[2].record(stream)
+    sp = api.cost_sinkhorn_sparse(W["h"], W["geom"], W["ob"], W["model"], cfg.eps, W["c_out"], cfg.n_sinkhorn,
+                                  **sp_kw)
+    es[3].record(stream)
+    torch.cuda.synchronize()
+    assert W["h"].device_status() == 0
+    sp_setup_ms = es[0].elapsed_time(es[1])
+    sp_total_ms = es[2].elapsed_time(es[3])
+    sp_iter_ms = (sp_total_ms - sp_setup_ms) / cfg.n_sinkhorn
+    dn = api.cost_sinkhorn(W["h"], W["geom"], W["ob"], W["model"], cfg.eps, W["c_out"], cfg.n_sinkhorn,
+                           harvest=True)
+    torch.cuda.synchronize()
+    sure = dn["margin"] > 1e-3
+    agree = float((sp["assign"][sure] == dn["assign"][sure]).float().mean())
+    nnz = W["nJ"] * rho
+    sp_bytes = 16.0 * nnz + 8.0 * (W["nI"] + W["nJ"])  # {index, e2} records of both passes, potentials
+    hbm_peak = None
+    pk_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        hbm_peak = json.load(open(pk_path)).get("hbm_gbs")
+    sparse = dict(rho=rho, setup_ms=sp_setup_ms, ms_per_iteration=sp_iter_ms, ms_200_iterations=sp_total_ms,
+                  dense_ms_per_iteration=2 * per_launch_ms,
+                  speedup_per_iteration=2 * per_launch_ms / sp_iter_ms,
+                  assign_agreement_with_dense=agree,
+                  roofline=dict(bound="hbm", bytes_per_iteration=sp_bytes,
+                                achieved_gbs=sp_bytes / (sp_iter_ms / 1e3) / 1e9, peak_gbs=hbm_peak,
+                                frac=(sp_bytes / (sp_iter_ms / 1e3) / 1e9 / hbm_peak) if hbm_peak else None,
+                                note="algorithmic bytes: 8-byte {index, e2} record per support entry in each of "
+                                     "the two passes plus one potential read and written per spot; gathers of "
+                                     "the other side's potentials hit L2"),
+                  note="paper Section 'Working with sparse assignment matrices'; agreement over rows whose dense "
+                       "top-two margin exceeds 1e-3")
+
     # refresh 1; Sinkhorn: schedule, pack, dust init, G maxima, 2 per iteration, clear, harvest,
     # finish; M-step: schedule, pack, dust init, G maxima, segment count + scan, init, 2 per Newton step,
     # MM pair + MM grain, norms
@@ -736,6 +781,7 @@ def main():
                         "plan); the passes skip (tile, chunk) combinations whose plan entries all underflow to "
                         "exactly 0 in FP32 (potentials bit-identical), and evaluate the fraction shown"),
         adjoint=adjoint,
+        sparse_estep=sparse,
     )
     if rank == 0 and not args.no_proposal:
         peaks = {}
