@@ -61,7 +61,16 @@ typedef struct laue_handle laue_handle;
  * "Laue diffraction" (Eq. spot_position) and "Detected spots": beam e,
  * wavelength band [lam_min, lam_max], detectors (gamma, nu, l).  D is the
  * length that turns ray distances into the pair cost C = D^2 |rhat - r|^2
- * (the sample-detector distance). */
+ * (the sample-detector distance).  Detector k is the plane through
+ * det_centre[k] with normal det_normal[k] (any orientation); it holds the
+ * plane points s with |(s - centre).a| < det_half[k] for both in-plane axes
+ * a1 = (y x n)/|y x n| (x when n is along y) and a2 = n x a1, n the unit
+ * normal (for a plane normal to z: the square with edges along x and y).
+ * det_D[k] > 0 is the cost length of the spots on detector k (the paper's
+ * two-detector setups, Appendix "Experimental details", place the detectors
+ * at different distances): the pair cost of model spot j is then
+ * D_j^2 |rhat - r_j|^2 with D_j = det_D of the detector its ray hits, and D
+ * where det_D[k] <= 0. */
 typedef struct {
     float beam[3];
     float lam_min, lam_max;
@@ -70,6 +79,7 @@ typedef struct {
     float det_centre[4][3];
     float det_normal[4][3];
     float det_half[4];
+    float det_D[4];
 } LaueGeometry;
 
 /* Plausible plane set (paper Section "Tomography experiments": the set
@@ -629,7 +639,9 @@ int laue_lp_net_params(laue_handle* h, const void* net, float* params_host, floa
  * label (s Gmax + g, or -1 for an outlier), at most `capacity` spots
  * (beyond it the status word records LAUE_ERR_CAPACITY and the list is
  * cut).  scene_i32 is scratch of 4 S W + 2 S ints (grain counts, window
- * starts, per-angle counts).  Planes must number at most 65535.
+ * starts, per-angle counts).  Planes must number at most 65535, and every
+ * detector's normal must lie along z (the noise and the outliers are drawn in
+ * the detectors' x and y; LAUE_ERR_INVALID_ARG otherwise).
  * Asynchronous; nothing is read back. */
 int laue_lp_scene(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const float* omega,
                   int T, int W, int S, int Gmax, int gmin, int gmax, float cube_mm, float sigma_mm,

@@ -75,8 +75,30 @@ def _i32(a):
 def pack_geom(geom) -> np.ndarray:
     g = [*geom.beam, geom.lam_min, geom.lam_max, geom.D, len(geom.detectors)]
     for det in geom.detectors:
-        g += [*det.centre, *det.normal, det.half]
+        g += [*det.centre, *det.normal, det.half, float(getattr(det, "D", 0.0))]
     return np.asarray(g, dtype=np.float64)
+
+
+def cost_lengths(geom, det):
+    """Cost length D_j of each model spot: the distance of the detector it
+    hits (det[j]), the geometry's D where that detector sets none."""
+    det = _i32(det)
+    out = np.zeros(max(len(det), 1))
+    lib().orc_cost_lengths(_d(pack_geom(geom)), len(det), _i(det), _d(out))
+    return out[:len(det)]
+
+
+def _Dj(D, nJ):
+    """Per-model-spot cost lengths from a scalar or an array."""
+    if np.ndim(D) == 0:
+        return np.full(max(nJ, 1), float(D))
+    D = _f64(D)
+    assert len(D) == nJ, (len(D), nJ)
+    return D if nJ else np.zeros(1)
+
+
+def _det(det):
+    return None if det is None else _i(_i32(det))
 
 
 def c_out_for(sigma_mm: float, D: float) -> float:
@@ -177,7 +199,7 @@ def sinkhorn(D, p, I_off, J_off, c, r, eps, c_out, mode=0, frac=0.4, n_iter=100,
         f = np.zeros(len(p)); g = np.zeros(len(c)); fd = np.zeros(nd); gd = np.zeros(nd); warm = 0
     else:
         f, g, fd, gd = [np.array(a, dtype=np.float64) for a in init]; warm = 1
-    it = L.orc_sinkhorn(ctypes.c_double(D), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
+    it = L.orc_sinkhorn(_d(_Dj(D, len(c))), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
                         ctypes.c_double(eps), ctypes.c_double(c_out), mode, ctypes.c_double(frac),
                         n_iter, ctypes.c_double(tol), warm, _d(f), _d(g), _d(fd), _d(gd))
     return f, g, fd, gd, it
@@ -192,7 +214,7 @@ def harvest(D, p, I_off, J_off, c, r, eps, c_out, mode, frac, f, g, fd, gd):
     nI, nJ = len(p), len(c)
     assign = np.zeros(nI, np.int32); margin = np.zeros(nI); err = np.zeros(2)
     q = np.zeros(nJ); v = np.zeros((nJ, 3))
-    L.orc_harvest(ctypes.c_double(D), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
+    L.orc_harvest(_d(_Dj(D, nJ)), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
                   ctypes.c_double(eps), ctypes.c_double(c_out), mode, ctypes.c_double(frac),
                   _d(_f64(f)), _d(_f64(g)), _d(_f64(fd)), _d(_f64(gd)),
                   _i(assign), _d(margin), _d(err), _d(q), _d(v))
@@ -200,7 +222,7 @@ def harvest(D, p, I_off, J_off, c, r, eps, c_out, mode, frac, f, g, fd, gd):
 
 
 def mstep(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps, R, x,
-          n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3):
+          n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, det=None):
     """One M-step (Newton on x, then MM on R); returns (R, x, stats (N, 8))."""
     L = lib()
     R = _f64(R, (-1, 9)).copy(); x = _f64(x, (-1, 3)).copy()
@@ -208,7 +230,7 @@ def mstep(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps,
     stats = np.zeros((N, 8))
     omega = _f64(omega)
     L.orc_mstep(_d(pack_geom(geom)), _d(_f64(planes.w)), _d(omega), len(omega), _i(_i32(I_off)),
-                _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)), _i(_i32(plane)), N,
+                _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)), _i(_i32(plane)), _det(det), N,
                 _d(_f64(cE, (-1, 3))), _d(_f64(rE, (-1, 3))), _d(_f64(f)), _d(_f64(g)),
                 ctypes.c_double(eps), n_newton, n_mm, ctypes.c_double(tol_x), ctypes.c_double(tol_R),
                 ctypes.c_double(hreg), _d(R), _d(x), _d(stats))
@@ -220,7 +242,8 @@ def eps_schedule(eps_final, n_em, k, factor=100.0):
 
 
 def em(geom, planes, omega, p, I_off, J_off, grain, plane, R, x, eps_final, n_em, n_sinkhorn,
-       c_out, mode=0, frac=0.4, n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, mstep="plain"):
+       c_out, mode=0, frac=0.4, n_newton=4, n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, mstep="plain",
+       det=None):
     """Algorithm LaueOT with a fixed number of EM steps; returns dict.  mstep
     "adjoint" takes the damped Gauss-Newton M-step (hreg its damping)."""
     L = lib()
@@ -231,7 +254,7 @@ def em(geom, planes, omega, p, I_off, J_off, grain, plane, R, x, eps_final, n_em
     assign = np.zeros(nI, np.int32); margin = np.zeros(nI)
     L.orc_em(_d(pack_geom(geom)), _d(_f64(planes.w)), _d(_f64(planes.d0)), _i(_i32(planes.nharm)),
              _d(omega), T, _i(_i32(I_off)), _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)),
-             _i(_i32(plane)), N, _d(R), _d(x), ctypes.c_double(eps_final), n_em, n_sinkhorn,
+             _i(_i32(plane)), _det(det), N, _d(R), _d(x), ctypes.c_double(eps_final), n_em, n_sinkhorn,
              ctypes.c_double(c_out), mode, ctypes.c_double(frac), n_newton, n_mm,
              ctypes.c_double(tol_x), ctypes.c_double(tol_R), ctypes.c_double(hreg), 1 if mstep == "adjoint" else 0,
              _d(f), _d(g), _d(fd), _d(gd), _i(assign), _d(margin))
@@ -279,24 +302,24 @@ def kstar(gain):
     return lib().orc_kstar(len(gain), _d(gain))
 
 
-def grain_objective(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps, R, x):
+def grain_objective(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps, R, x, det=None):
     L = lib()
     R = _f64(R, (-1, 9)); x = _f64(x, (-1, 3)); N = len(R); omega = _f64(omega)
     En = np.zeros(N)
     L.orc_grain_objective(_d(pack_geom(geom)), _d(_f64(planes.w)), _d(omega), len(omega),
                           _i(_i32(I_off)), _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)),
-                          _i(_i32(plane)), N, _d(_f64(cE, (-1, 3))), _d(_f64(rE, (-1, 3))),
+                          _i(_i32(plane)), _det(det), N, _d(_f64(cE, (-1, 3))), _d(_f64(rE, (-1, 3))),
                           _d(_f64(f)), _d(_f64(g)), ctypes.c_double(eps), _d(R), _d(x), _d(En))
     return En
 
 
-def grain_grad(geom, planes, omega, p, I_off, J_off, grain, plane, f, g, eps, R, x):
+def grain_grad(geom, planes, omega, p, I_off, J_off, grain, plane, f, g, eps, R, x, det=None):
     L = lib()
     R = _f64(R, (-1, 9)); x = _f64(x, (-1, 3)); N = len(R); omega = _f64(omega)
     grad = np.zeros((N, 6))
     L.orc_grain_grad(_d(pack_geom(geom)), _d(_f64(planes.w)), _d(omega), len(omega),
                      _i(_i32(I_off)), _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)),
-                     _i(_i32(plane)), N, _d(_f64(f)), _d(_f64(g)), ctypes.c_double(eps), _d(R),
+                     _i(_i32(plane)), _det(det), N, _d(_f64(f)), _d(_f64(g)), ctypes.c_double(eps), _d(R),
                      _d(x), _d(grad))
     return grad
 
@@ -336,7 +359,7 @@ def start_grid(n_full, sym=24, k=1, cube=5.0):
     return R[:n].reshape(-1, 3, 3), x[:n]
 
 
-def grain_gn(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps, R, x):
+def grain_gn(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps, R, x, det=None):
     """Gradient (N, 6), Gauss-Newton matrix (N, 6, 6) and value (N,) of the
     OT-weighted cost at the pose (R, x), Q held at the E-step plan."""
     L = lib()
@@ -344,21 +367,21 @@ def grain_gn(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, e
     N = len(R)
     grad = np.zeros((N, 6)); H = np.zeros((N, 36)); val = np.zeros(N)
     L.orc_grain_gn(_d(pack_geom(geom)), _d(_f64(planes.w)), _d(_f64(omega)), len(omega), _i(_i32(I_off)),
-                   _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)), _i(_i32(plane)), N,
+                   _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)), _i(_i32(plane)), _det(det), N,
                    _d(_f64(cE, (-1, 3))), _d(_f64(rE, (-1, 3))), _d(_f64(f)), _d(_f64(g)), ctypes.c_double(eps),
                    _d(R), _d(x), _d(grad), _d(H), _d(val))
     return grad, H.reshape(-1, 6, 6), val
 
 
 def mstep_adjoint(geom, planes, omega, p, I_off, J_off, grain, plane, cE, rE, f, g, eps, R, x, n_steps=4,
-                  lam=1e-3):
+                  lam=1e-3, det=None):
     """Adjoint M-step (damped Gauss-Newton with Q held); returns (R, x, step_norms)."""
     L = lib()
     R = _f64(R, (-1, 9)).copy(); x = _f64(x, (-1, 3)).copy()
     N = len(R)
     norms = np.zeros((N, 2))
     L.orc_mstep_adjoint(_d(pack_geom(geom)), _d(_f64(planes.w)), _d(_f64(omega)), len(omega), _i(_i32(I_off)),
-                        _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)), _i(_i32(plane)), N,
+                        _d(_f64(p, (-1, 3))), _i(_i32(J_off)), _i(_i32(grain)), _i(_i32(plane)), _det(det), N,
                         _d(_f64(cE, (-1, 3))), _d(_f64(rE, (-1, 3))), _d(_f64(f)), _d(_f64(g)), ctypes.c_double(eps),
                         n_steps, ctypes.c_double(lam), _d(R), _d(x), _d(norms))
     return R.reshape(-1, 3, 3), x, norms
@@ -370,7 +393,7 @@ def sinkhorn_unbalanced(D, p, I_off, J_off, c, r, eps, kappa, lam, n_iter=100):
     I_off = _i32(I_off); J_off = _i32(J_off)
     T = len(I_off) - 1
     f = np.zeros(int(I_off[-1])); g = np.zeros(int(J_off[-1]))
-    lib().orc_sinkhorn_unbalanced(ctypes.c_double(D), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
+    lib().orc_sinkhorn_unbalanced(_d(_Dj(D, len(c))), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
                                   ctypes.c_double(eps), ctypes.c_double(kappa), ctypes.c_double(lam), n_iter,
                                   _d(f), _d(g))
     return f, g
@@ -383,7 +406,7 @@ def harvest_unbalanced(D, p, I_off, J_off, c, r, eps, f, g):
     T = len(I_off) - 1
     nI, nJ = int(I_off[-1]), int(J_off[-1])
     assign = np.zeros(nI, np.int32); margin = np.zeros(nI); rows = np.zeros(nI); q = np.zeros(nJ)
-    lib().orc_harvest_unbalanced(ctypes.c_double(D), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
+    lib().orc_harvest_unbalanced(_d(_Dj(D, nJ)), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r),
                                  ctypes.c_double(eps), _d(_f64(f)), _d(_f64(g)), _i(assign), _d(margin), _d(rows),
                                  _d(q))
     return dict(assign=assign, margin=margin, rowmass=rows, q=q)
@@ -422,7 +445,7 @@ def knn(D, p, I_off, J_off, c, r, rho):
     p = _f64(p, (-1, 3)); c = _f64(c, (-1, 3)); r = _f64(r, (-1, 3))
     I_off = _i32(I_off); J_off = _i32(J_off)
     nbr = np.zeros((max(int(J_off[-1]), 1), rho), np.int32)
-    lib().orc_knn(ctypes.c_double(D), len(I_off) - 1, _i(I_off), _d(p), _i(J_off), _d(c), _d(r), rho, _i(nbr))
+    lib().orc_knn(_d(_Dj(D, int(J_off[-1]))), len(I_off) - 1, _i(I_off), _d(p), _i(J_off), _d(c), _d(r), rho, _i(nbr))
     return nbr[:int(J_off[-1])]
 
 
@@ -433,7 +456,7 @@ def sinkhorn_sparse(D, p, I_off, J_off, c, r, eps, c_out, mode=0, frac=0.4, n_it
     T = len(I_off) - 1
     nd = T if mode else 1
     f = np.zeros(int(I_off[-1])); g = np.zeros(int(J_off[-1])); fd = np.zeros(nd); gd = np.zeros(nd)
-    lib().orc_sinkhorn_sparse(ctypes.c_double(D), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r), ctypes.c_double(eps),
+    lib().orc_sinkhorn_sparse(_d(_Dj(D, int(J_off[-1]))), T, _i(I_off), _d(p), _i(J_off), _d(c), _d(r), ctypes.c_double(eps),
                               ctypes.c_double(c_out), mode, ctypes.c_double(frac), n_iter, rho, _d(f), _d(g), _d(fd),
                               _d(gd))
     return f, g, fd, gd

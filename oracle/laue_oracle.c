@@ -247,8 +247,16 @@ typedef struct {
     double lam_min, lam_max, D;
     int n_det;
     double ctr[4][3], nrm[4][3], half[4];
+    double Dd[4];            /* cost length of each detector */
+    double a1[4][3], a2[4][3];  /* in-plane axes of each detector */
 } geom_t;
 
+/* Packed geometry: beam (3), lam_min, lam_max, D, n_det, then per detector
+ * centre (3), normal (3), half size, cost length (<= 0: D).  A detector's
+ * square is the set of plane points s with |(s - centre).a| < half for both
+ * in-plane axes a1 = (y x n)/|y x n| (x when n is along y) and a2 = n x a1
+ * (n the unit normal): for a detector normal to the beam the axes are x and
+ * y and the square has edges along them. */
 static void geom_unpack(const double* g, geom_t* G) {
     for (int a = 0; a < 3; ++a) G->e[a] = g[a];
     G->lam_min = g[3];
@@ -257,13 +265,45 @@ static void geom_unpack(const double* g, geom_t* G) {
     G->n_det = (int)g[6];
     if (G->n_det > 4) G->n_det = 4;
     for (int k = 0; k < G->n_det; ++k) {
-        const double* q = g + 7 + 7 * k;
+        const double* q = g + 7 + 8 * k;
         for (int a = 0; a < 3; ++a) {
             G->ctr[k][a] = q[a];
             G->nrm[k][a] = q[3 + a];
         }
         G->half[k] = q[6];
+        G->Dd[k] = q[7] > 0.0 ? q[7] : G->D;
+        double nn = sqrt(dot3(G->nrm[k], G->nrm[k]));
+        double n[3] = {G->nrm[k][0] / nn, G->nrm[k][1] / nn, G->nrm[k][2] / nn};
+        double a1[3] = {n[2], 0.0, -n[0]};  /* y x n */
+        double l1 = sqrt(dot3(a1, a1));
+        if (l1 < 1e-12) {
+            a1[0] = 1.0; a1[1] = 0.0; a1[2] = 0.0;
+        } else {
+            for (int a = 0; a < 3; ++a) a1[a] /= l1;
+        }
+        double a2[3] = {n[1] * a1[2] - n[2] * a1[1], n[2] * a1[0] - n[0] * a1[2], n[0] * a1[1] - n[1] * a1[0]};
+        for (int a = 0; a < 3; ++a) {
+            G->a1[k][a] = a1[a];
+            G->a2[k][a] = a2[a];
+        }
     }
+}
+
+/* Cost length of model spot j: the distance of the detector its ray hits
+ * (det[j]), D when the detector is unknown. */
+static double det_D(const geom_t* G, const int* det, long j) {
+    if (det) {
+        int k = det[j];
+        if (k >= 0 && k < G->n_det) return G->Dd[k];
+    }
+    return G->D;
+}
+
+/* Cost lengths of n model spots from their detectors (det_D). */
+void orc_cost_lengths(const double* geom, int n, const int* det, double* out) {
+    geom_t G;
+    geom_unpack(geom, &G);
+    for (int j = 0; j < n; ++j) out[j] = det_D(&G, det, j);
 }
 
 /* Section "Tomography experiments": Gamma_t, rotation about +y by omega. */
@@ -385,12 +425,13 @@ static int ray_one(const geom_t* G, const double Gam[9], const double R[9], cons
         double gc[3] = {G->ctr[k][0] - c[0], G->ctr[k][1] - c[1], G->ctr[k][2] - c[2]};
         double tau = dot3(G->nrm[k], gc) / den;
         if (!(tau > 0.0)) continue;
-        double sk[3], dist = 0.0;
+        double sk[3], ds[3];
         for (int a = 0; a < 3; ++a) {
             sk[a] = c[a] + tau * r[a];
-            double da = fabs(sk[a] - G->ctr[k][a]);
-            if (da > dist) dist = da;
+            ds[a] = sk[a] - G->ctr[k][a];
         }
+        double d1 = fabs(dot3(ds, G->a1[k])), d2 = fabs(dot3(ds, G->a2[k]));
+        double dist = d1 > d2 ? d1 : d2;
         double m3 = fabs(G->half[k] - dist) / G->half[k];
         if (m3 < mrg) mrg = m3;
         if (dist < G->half[k] && tau < best_tau) {
@@ -551,7 +592,7 @@ int orc_set_threads(int n) {
  * angle (Q_ij = 0 unless t_i = t_j).  Runs exactly n_iter iterations, or
  * fewer when tol > 0 and the largest row-marginal violation drops below tol.
  * warm != 0 starts from the given potentials.  Returns iterations done. */
-int orc_sinkhorn(double D, int T, const int* I_off, const double* p,
+int orc_sinkhorn(const double* Dj, int T, const int* I_off, const double* p,
                  const int* J_off, const double* c, const double* r,
                  double eps, double c_out, int mode, double frac, int n_iter, double tol,
                  int warm, double* f, double* g, double* fd, double* gd) {
@@ -581,7 +622,7 @@ int orc_sinkhorn(double D, int T, const int* I_off, const double* p,
                 for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
                     int n = 0;
                     for (int j = J_off[t]; j < J_off[t + 1]; ++j)
-                        b[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                        b[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, Dj[j])) / eps;
                     b[n++] = (gd[dd] - c_out) / eps;
                     f[i] = -eps * lse(b, n);
                 }
@@ -605,7 +646,7 @@ int orc_sinkhorn(double D, int T, const int* I_off, const double* p,
                 for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
                     int n = 0;
                     for (int i = I_off[t]; i < I_off[t + 1]; ++i)
-                        b[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                        b[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, Dj[j])) / eps;
                     b[n++] = fd[dd] / eps;
                     g[j] = -eps * lse(b, n);
                 }
@@ -621,7 +662,7 @@ int orc_sinkhorn(double D, int T, const int* I_off, const double* p,
         }
         if (tol > 0.0) {
             double err[2];
-            orc_harvest(D, T, I_off, p, J_off, c, r, eps, c_out, mode, frac, f, g, fd, gd,
+            orc_harvest(Dj, T, I_off, p, J_off, c, r, eps, c_out, mode, frac, f, g, fd, gd,
                         NULL, NULL, err, NULL, NULL);
             if (err[0] < tol) { ++it; break; }
         }
@@ -639,7 +680,7 @@ int orc_sinkhorn(double D, int T, const int* I_off, const double* p,
  * violation, err[1] = largest column violation (dust rows/columns relative to
  * their mass).  q[j] = sum_i Q_ij and v[j] = sum_i Q_ij rhat_ij over observed
  * rows.  Any output pointer may be NULL. */
-void orc_harvest(double D, int T, const int* I_off, const double* p,
+void orc_harvest(const double* Dj, int T, const int* I_off, const double* p,
                  const int* J_off, const double* c, const double* r,
                  double eps, double c_out, int mode, double frac,
                  const double* f, const double* g, const double* fd, const double* gd,
@@ -661,7 +702,7 @@ void orc_harvest(double D, int T, const int* I_off, const double* p,
             double rs = 0.0, top1 = -1.0, top2 = -1.0;
             int arg = -1;
             for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
-                double Cij = orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D);
+                double Cij = orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, Dj[j]);
                 double Qij = exp((f[i] + g[j] - Cij) / eps);
                 rs += Qij;
                 colsum[j] += Qij;
@@ -724,14 +765,21 @@ typedef double (*qfun_t)(void* ctx, int i, int j);
 
 typedef struct {
     const double *p, *cE, *rE, *f, *g;
-    double eps, D;
+    double eps;
+    const geom_t* G;
+    const int* det;
 } qpot_ctx;
 
-/* Q_ij of a converged E-step from its potentials and the E-step costs. */
+/* M-step weight of pair (i, j): Q_ij of a converged E-step from its
+ * potentials and the E-step costs, times (D_j / D)^2 (the cost of the pair is
+ * D_j^2 |rhat - r|^2 with D_j the distance of model spot j's detector, so the
+ * maximised sum_ij Q_ij D_j^2 rhat.r carries that factor; 1 when every
+ * detector has the cost length D). */
 static double q_from_potentials(void* vctx, int i, int j) {
     qpot_ctx* ctx = (qpot_ctx*)vctx;
-    double C = orc_pair_cost(ctx->p + 3 * i, ctx->cE + 3 * j, ctx->rE + 3 * j, ctx->D);
-    return exp((ctx->f[i] + ctx->g[j] - C) / ctx->eps);
+    double Dj = det_D(ctx->G, ctx->det, j);
+    double C = orc_pair_cost(ctx->p + 3 * i, ctx->cE + 3 * j, ctx->rE + 3 * j, Dj);
+    return exp((ctx->f[i] + ctx->g[j] - C) / ctx->eps) * (Dj / ctx->G->D) * (Dj / ctx->G->D);
 }
 
 /* Phi(x) = sum_{j in J_n} sum_{i in I_tj} Q_ij rhat_ij(x).r_j */
@@ -943,14 +991,14 @@ static void free_grain_lists(grain_list* L, int N) {
  *  MM objective after, Phi before Newton, Phi after Newton}. */
 int orc_mstep(const double* geom, const double* w, const double* omega, int T,
               const int* I_off, const double* p, const int* J_off,
-              const int* grain, const int* plane, int N,
+              const int* grain, const int* plane, const int* det, int N,
               const double* cE, const double* rE,
               const double* f, const double* g, double eps,
               int n_newton, int n_mm, double tol_x, double tol_R, double hreg,
               double* R, double* x, double* stats) {
     geom_t G;
     geom_unpack(geom, &G);
-    qpot_ctx qc = {p, cE, rE, f, g, eps, G.D};
+    qpot_ctx qc = {p, cE, rE, f, g, eps, &G, det};
     grain_list* L = (grain_list*)malloc(sizeof(grain_list) * (N + 1));
     build_grain_lists(T, J_off, grain, plane, N, L);
     double st[8];
@@ -988,7 +1036,7 @@ double orc_eps_schedule(double eps_final, int n_em, int k) {
  * E-step at the last poses gives the plan read-out. */
 int orc_em(const double* geom, const double* w, const double* d0, const int* nharm,
            const double* omega, int T, const int* I_off, const double* p,
-           const int* J_off, const int* grain, const int* plane, int N,
+           const int* J_off, const int* grain, const int* plane, const int* det, int N,
            double* R, double* x, double eps_final, int n_em, int n_sinkhorn,
            double c_out, int mode, double frac, int n_newton, int n_mm,
            double tol_x, double tol_R, double hreg, int mstep_kind,
@@ -999,26 +1047,28 @@ int orc_em(const double* geom, const double* w, const double* d0, const int* nha
     double* ray4 = (double*)malloc(sizeof(double) * 4 * (nJ + 1));
     double* c3 = (double*)malloc(sizeof(double) * 3 * (nJ + 1));
     double* r3 = (double*)malloc(sizeof(double) * 3 * (nJ + 1));
+    double* Dj = (double*)malloc(sizeof(double) * (nJ + 1));
+    for (int j = 0; j < nJ; ++j) Dj[j] = det_D(&G, det, j);
     for (int k = 0; k <= n_em; ++k) {
         double eps = orc_eps_schedule(eps_final, n_em, k < n_em ? k : n_em);
         orc_refresh(geom, w, d0, nharm, R, x, omega, T, J_off, grain, plane, ray4, c3);
         for (int j = 0; j < nJ; ++j)
             for (int a = 0; a < 3; ++a) r3[3 * j + a] = ray4[4 * j + a];
-        orc_sinkhorn(G.D, T, I_off, p, J_off, c3, r3, eps, c_out, mode, frac, n_sinkhorn, 0.0, 0,
+        orc_sinkhorn(Dj, T, I_off, p, J_off, c3, r3, eps, c_out, mode, frac, n_sinkhorn, 0.0, 0,
                      f, g, fd, gd);
         if (k == n_em) {
-            orc_harvest(G.D, T, I_off, p, J_off, c3, r3, eps, c_out, mode, frac, f, g, fd, gd,
+            orc_harvest(Dj, T, I_off, p, J_off, c3, r3, eps, c_out, mode, frac, f, g, fd, gd,
                         assign, margin, NULL, NULL, NULL);
             break;
         }
         if (mstep_kind == 1)  /* the adjoint M-step; hreg is its damping */
-            orc_mstep_adjoint(geom, w, omega, T, I_off, p, J_off, grain, plane, N, c3, r3, f, g, eps,
+            orc_mstep_adjoint(geom, w, omega, T, I_off, p, J_off, grain, plane, det, N, c3, r3, f, g, eps,
                               n_newton, hreg, R, x, NULL);
         else
-            orc_mstep(geom, w, omega, T, I_off, p, J_off, grain, plane, N, c3, r3, f, g, eps,
+            orc_mstep(geom, w, omega, T, I_off, p, J_off, grain, plane, det, N, c3, r3, f, g, eps,
                       n_newton, n_mm, tol_x, tol_R, hreg, R, x, NULL);
     }
-    free(ray4); free(c3); free(r3);
+    free(ray4); free(c3); free(r3); free(Dj);
     return 0;
 }
 
@@ -1032,19 +1082,22 @@ typedef struct {
     const int* I_off;
     const int* jt;
     int stride;
+    const double* wk;     /* (D_k / D)^2 of each ray */
 } qdense_ctx;
 
+/* M-step weight of pair (i, j) in a single-grain fit: Q_ij (D_j / D)^2, as
+ * in q_from_potentials. */
 static double q_dense(void* vctx, int i, int j) {
     qdense_ctx* c = (qdense_ctx*)vctx;
     int k = c->jpos[j];
     int t = c->jt[k];
-    return c->Q[(long)k * c->stride + (i - c->I_off[t])];
+    return c->Q[(long)k * c->stride + (i - c->I_off[t])] * c->wk[k];
 }
 
 /* Appendix "Single-grain fitting" (Eq. elbo_single): row-normalised E-step
  * Q_ij = K_ij / (sum_{j'} K_ij' + K_i0), K = exp(-C/eps), over the model spots
  * of the grain at angle t_i. */
-static void single_estep(double D, const int* I_off, const double* p, int nj, const int* jt,
+static void single_estep(const double* Dk, const int* I_off, const double* p, int nj, const int* jt,
                          const double* c3, const double* r3, double eps, double c_out,
                          int stride, double* Q, int T) {
     double* buf = (double*)malloc(sizeof(double) * (nj + 2));
@@ -1052,13 +1105,13 @@ static void single_estep(double D, const int* I_off, const double* p, int nj, co
         for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
             int n = 0;
             for (int k = 0; k < nj; ++k)
-                if (jt[k] == t) buf[n++] = -orc_pair_cost(p + 3 * i, c3 + 3 * k, r3 + 3 * k, D) / eps;
+                if (jt[k] == t) buf[n++] = -orc_pair_cost(p + 3 * i, c3 + 3 * k, r3 + 3 * k, Dk[k]) / eps;
             buf[n++] = -c_out / eps;
             double l = lse(buf, n);
             for (int k = 0; k < nj; ++k)
                 if (jt[k] == t)
                     Q[(long)k * stride + (i - I_off[t])] =
-                        exp(-orc_pair_cost(p + 3 * i, c3 + 3 * k, r3 + 3 * k, D) / eps - l);
+                        exp(-orc_pair_cost(p + 3 * i, c3 + 3 * k, r3 + 3 * k, Dk[k]) / eps - l);
         }
     }
     free(buf);
@@ -1095,12 +1148,14 @@ int orc_single_fit(const double* geom, const double* w, const double* d0, const 
     int* jpos = (int*)malloc(sizeof(int) * cap);
     int* js = (int*)malloc(sizeof(int) * cap);
     double* Q = (double*)malloc(sizeof(double) * cap * stride);
+    double* Dk = (double*)malloc(sizeof(double) * cap);
+    double* wk = (double*)malloc(sizeof(double) * cap);
     for (int s = 0; s < S; ++s) {
         double R[9], x[3];
         memcpy(R, R0 + 9 * s, sizeof(R));
         memcpy(x, x0 + 3 * s, sizeof(x));
         long nj = 0;
-        qdense_ctx qc = {Q, jpos, I_off, jt, stride};
+        qdense_ctx qc = {Q, jpos, I_off, jt, stride, wk};
         for (int k = 0; k < k_max; ++k) {
             double eps = orc_eps_schedule_f(eps_final, k_max, k, anneal);
             /* Algorithm SingleLaueOT computes the model rays of the grain at
@@ -1111,11 +1166,15 @@ int orc_single_fit(const double* geom, const double* w, const double* d0, const 
                                  s3, dk, c3, NULL, NULL);
                 for (int t = 0; t < T; ++t)
                     for (int j = Joff[t]; j < Joff[t + 1]; ++j) { jt[j] = t; jpos[j] = j; js[j] = j; }
+                for (long j = 0; j < nj; ++j) {
+                    Dk[j] = det_D(&G, dk, j);
+                    wk[j] = (Dk[j] / G.D) * (Dk[j] / G.D);
+                }
             }
             orc_refresh(geom, w, d0, nharm, R, x, omega, T, Joff, gr, pl, ray4, c3);
             for (long j = 0; j < nj; ++j)
                 for (int a = 0; a < 3; ++a) r3[3 * j + a] = ray4[4 * j + a];
-            single_estep(G.D, I_off, p, (int)nj, jt, c3, r3, eps, c_out, stride, Q, T);
+            single_estep(Dk, I_off, p, (int)nj, jt, c3, r3, eps, c_out, stride, Q, T);
             double st[8];
             newton_grain(&G, omega, I_off, p, js, (int)nj, jt, r3, q_dense, &qc, n_newton, tol_x,
                          hreg, x, st);
@@ -1129,9 +1188,11 @@ int orc_single_fit(const double* geom, const double* w, const double* d0, const 
                               s3, dk, c3, NULL, NULL);
         for (int t = 0; t < T; ++t)
             for (int j = Joff[t]; j < Joff[t + 1]; ++j) jt[j] = t;
-        for (long j = 0; j < nf; ++j)
+        for (long j = 0; j < nf; ++j) {
             for (int a = 0; a < 3; ++a) r3[3 * j + a] = ray4[4 * j + a];
-        single_estep(G.D, I_off, p, (int)nf, jt, c3, r3, eps_final, c_out, stride, Q, T);
+            Dk[j] = det_D(&G, dk, j);
+        }
+        single_estep(Dk, I_off, p, (int)nf, jt, c3, r3, eps_final, c_out, stride, Q, T);
         int nun = 0;
         for (long j = 0; j < nf; ++j) {
             int t = jt[j];
@@ -1143,7 +1204,7 @@ int orc_single_fit(const double* geom, const double* w, const double* d0, const 
         if (keep) keep[s] = nf > 0 && (double)nun < f_out * (double)nf;
     }
     free(Joff); free(gr); free(pl); free(dk); free(ray4); free(s3); free(c3); free(r3);
-    free(jt); free(jpos); free(js); free(Q);
+    free(jt); free(jpos); free(js); free(Q); free(Dk); free(wk);
     return 0;
 }
 
@@ -1179,7 +1240,7 @@ int orc_spot_matrix(const double* geom, const double* w, const double* d0, const
                 int k = 0;
                 for (int j = Joff[t]; j < Joff[t + 1]; ++j) {
                     double r[3] = {ray4[4 * j], ray4[4 * j + 1], ray4[4 * j + 2]};
-                    buf[k++] = -orc_pair_cost(p + 3 * i, c3 + 3 * j, r, G.D) / eps_s;
+                    buf[k++] = -orc_pair_cost(p + 3 * i, c3 + 3 * j, r, det_D(&G, dk, j)) / eps_s;
                 }
                 double val = k ? lse(buf, k) + c_out / eps_s : 0.0;
                 Lbar[(long)i * Nc + n] = val > 0.0 ? val : 0.0;
@@ -1258,7 +1319,7 @@ int orc_kstar(int K, const double* gain) {
  * the potentials and the costs at the E-step (cE, rE). */
 void orc_grain_objective(const double* geom, const double* w, const double* omega, int T,
                          const int* I_off, const double* p, const int* J_off,
-                         const int* grain, const int* plane, int N,
+                         const int* grain, const int* plane, const int* det, int N,
                          const double* cE, const double* rE,
                          const double* f, const double* g, double eps,
                          const double* R, const double* x, double* En) {
@@ -1277,9 +1338,10 @@ void orc_grain_objective(const double* geom, const double* w, const double* omeg
             double ue = dot3(u, G.e);
             for (int a = 0; a < 3; ++a) r[a] = G.e[a] - 2.0 * ue * u[a];
             for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
-                double CE = orc_pair_cost(p + 3 * i, cE + 3 * j, rE + 3 * j, G.D);
+                double Dj = det_D(&G, det, j);
+                double CE = orc_pair_cost(p + 3 * i, cE + 3 * j, rE + 3 * j, Dj);
                 double Q = exp((f[i] + g[j] - CE) / eps);
-                En[n] += Q * orc_pair_cost(p + 3 * i, c, r, G.D);
+                En[n] += Q * orc_pair_cost(p + 3 * i, c, r, Dj);
             }
         }
     }
@@ -1294,18 +1356,18 @@ void orc_grain_objective(const double* geom, const double* w, const double* omeg
  * grad[6 n + 0..2] = dE_n/dw, grad[6 n + 3..5] = dE_n/dx. */
 void orc_grain_grad(const double* geom, const double* w, const double* omega, int T,
                     const int* I_off, const double* p, const int* J_off,
-                    const int* grain, const int* plane, int N,
+                    const int* grain, const int* plane, const int* det, int N,
                     const double* f, const double* g, double eps,
                     const double* R, const double* x, double* grad) {
     geom_t G;
     geom_unpack(geom, &G);
-    double D2 = G.D * G.D;
     for (int k = 0; k < 6 * N; ++k) grad[k] = 0.0;
     for (int t = 0; t < T; ++t) {
         double Gam[9];
         orc_gamma(omega[t], Gam);
         for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
             int n = grain[j], m = plane[j];
+            double Dj = det_D(&G, det, j), D2 = Dj * Dj;
             double v[3], u[3], c[3], r[3];
             mat_vec(R + 9 * n, w + 3 * m, v);
             mat_vec(Gam, v, u);
@@ -1314,7 +1376,7 @@ void orc_grain_grad(const double* geom, const double* w, const double* omega, in
             for (int a = 0; a < 3; ++a) r[a] = G.e[a] - 2.0 * ue * u[a];
             double gr[3] = {0, 0, 0}, gc[3] = {0, 0, 0};
             for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
-                double C = orc_pair_cost(p + 3 * i, c, r, G.D);
+                double C = orc_pair_cost(p + 3 * i, c, r, Dj);
                 double Q = exp((f[i] + g[j] - C) / eps);
                 if (Q == 0.0) continue;
                 double d[3] = {p[3 * i] - c[0], p[3 * i + 1] - c[1], p[3 * i + 2] - c[2]};
@@ -1472,12 +1534,11 @@ long orc_start_grid(long n_full, int sym, int k, double cube, long cap, double* 
  * grad: N x 6, H: N x 36 (row-major), value: N (optional). */
 void orc_grain_gn(const double* geom, const double* w, const double* omega, int T,
                   const int* I_off, const double* p, const int* J_off,
-                  const int* grain, const int* plane, int N,
+                  const int* grain, const int* plane, const int* det, int N,
                   const double* cE, const double* rE, const double* f, const double* g, double eps,
                   const double* R, const double* x, double* grad, double* H, double* value) {
     geom_t G;
     geom_unpack(geom, &G);
-    double D2 = G.D * G.D;
     for (int k = 0; k < 6 * N; ++k) grad[k] = 0.0;
     for (int k = 0; k < 36 * N; ++k) H[k] = 0.0;
     if (value) for (int n = 0; n < N; ++n) value[n] = 0.0;
@@ -1486,6 +1547,7 @@ void orc_grain_gn(const double* geom, const double* w, const double* omega, int 
         orc_gamma(omega[t], Gam);
         for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
             int n = grain[j], m = plane[j];
+            double Dj = det_D(&G, det, j), D2 = Dj * Dj;
             double v[3], u[3], c[3], r[3];
             mat_vec(R + 9 * n, w + 3 * m, v);
             mat_vec(Gam, v, u);
@@ -1500,7 +1562,7 @@ void orc_grain_gn(const double* geom, const double* w, const double* omega, int 
             mat_mul(B, GV, A);
             double gc[3] = {0, 0, 0}, ge[3] = {0, 0, 0}, q = 0.0, s1 = 0.0, s2 = 0.0, val = 0.0;
             for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
-                double CE = orc_pair_cost(p + 3 * i, cE + 3 * j, rE + 3 * j, G.D);
+                double CE = orc_pair_cost(p + 3 * i, cE + 3 * j, rE + 3 * j, Dj);
                 double Q = exp((f[i] + g[j] - CE) / eps);
                 if (Q == 0.0) continue;
                 double d[3] = {p[3 * i] - c[0], p[3 * i + 1] - c[1], p[3 * i + 2] - c[2]};
@@ -1610,13 +1672,14 @@ static void rotvec_mat(const double phi[3], double E[9]) {
  * |delta_phi|. */
 void orc_mstep_adjoint(const double* geom, const double* w, const double* omega, int T,
                        const int* I_off, const double* p, const int* J_off,
-                       const int* grain, const int* plane, int N,
+                       const int* grain, const int* plane, const int* det, int N,
                        const double* cE, const double* rE, const double* f, const double* g, double eps,
                        int n_steps, double lambda, double* R, double* x, double* step_norms) {
     double* grad = (double*)malloc(sizeof(double) * 6 * (N > 0 ? N : 1));
     double* H = (double*)malloc(sizeof(double) * 36 * (N > 0 ? N : 1));
     for (int it = 0; it < n_steps; ++it) {
-        orc_grain_gn(geom, w, omega, T, I_off, p, J_off, grain, plane, N, cE, rE, f, g, eps, R, x, grad, H, NULL);
+        orc_grain_gn(geom, w, omega, T, I_off, p, J_off, grain, plane, det, N, cE, rE, f, g, eps, R, x, grad, H,
+                     NULL);
         for (int n = 0; n < N; ++n) {
             double A[36], b[6], d[6];
             for (int k = 0; k < 36; ++k) A[k] = H[36 * n + k];
@@ -1655,7 +1718,7 @@ void orc_mstep_adjoint(const double* geom, const double* w, const double* omega,
  * against b, the model spots); the printed algorithm attaches the exponents the
  * other way round, and the scaling that solves Problem (B) is used here.  A row
  * (column) of an angle block with no columns (rows) keeps potential 0. */
-int orc_sinkhorn_unbalanced(double D, int T, const int* I_off, const double* p,
+int orc_sinkhorn_unbalanced(const double* Dj, int T, const int* I_off, const double* p,
                             const int* J_off, const double* c, const double* r,
                             double eps, double kappa, double lambda, int n_iter,
                             double* f, double* g) {
@@ -1670,14 +1733,14 @@ int orc_sinkhorn_unbalanced(double D, int T, const int* I_off, const double* p,
             for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
                 int n = 0;
                 for (int j = J_off[t]; j < J_off[t + 1]; ++j)
-                    buf[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                    buf[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, Dj[j])) / eps;
                 f[i] = n ? -ta * eps * lse(buf, n) : 0.0;
             }
         for (int t = 0; t < T; ++t)
             for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
                 int n = 0;
                 for (int i = I_off[t]; i < I_off[t + 1]; ++i)
-                    buf[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                    buf[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, Dj[j])) / eps;
                 g[j] = n ? -tb * eps * lse(buf, n) : 0.0;
             }
     }
@@ -1690,7 +1753,7 @@ int orc_sinkhorn_unbalanced(double D, int T, const int* I_off, const double* p,
  * to the lowest index), or -1 when r_i < 1/2 (reading: a spot that keeps less
  * than half its mass untransported is an outlier); margin = top1 - top2 of
  * the row's plan entries. */
-void orc_harvest_unbalanced(double D, int T, const int* I_off, const double* p,
+void orc_harvest_unbalanced(const double* Dj, int T, const int* I_off, const double* p,
                             const int* J_off, const double* c, const double* r, double eps,
                             const double* f, const double* g, int* assign, double* margin,
                             double* rowmass, double* q) {
@@ -1701,7 +1764,7 @@ void orc_harvest_unbalanced(double D, int T, const int* I_off, const double* p,
             double rs = 0.0, top1 = -1.0, top2 = -1.0;
             int arg = -1;
             for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
-                double Qij = exp((f[i] + g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps);
+                double Qij = exp((f[i] + g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, Dj[j])) / eps);
                 rs += Qij;
                 if (q) q[j] += Qij;
                 if (Qij > top1) { top2 = top1; top1 = Qij; arg = j; }
@@ -1848,7 +1911,7 @@ static int knn_cmp(const void* A, const void* B) {
  * Sinkhorn update costs rho |J| instead of |I| |J|; every other entry of the
  * plan between observed and model spots is 0, the dustbin row and column
  * stay dense.  nbr: |J| x rho observed indices, -1 past the block's size. */
-void orc_knn(double D, int T, const int* I_off, const double* p, const int* J_off, const double* c,
+void orc_knn(const double* Dj, int T, const int* I_off, const double* p, const int* J_off, const double* c,
              const double* r, int rho, int* nbr) {
     int big = 1;
     for (int t = 0; t < T; ++t)
@@ -1858,7 +1921,7 @@ void orc_knn(double D, int T, const int* I_off, const double* p, const int* J_of
         for (int j = J_off[t]; j < J_off[t + 1]; ++j) {
             int n = 0;
             for (int i = I_off[t]; i < I_off[t + 1]; ++i) {
-                buf[n].c = orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D);
+                buf[n].c = orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, Dj[j]);
                 buf[n].i = i;
                 ++n;
             }
@@ -1874,13 +1937,13 @@ void orc_knn(double D, int T, const int* I_off, const double* p, const int* J_of
  *   g_j = -eps LSE({(f_i - C_ij)/eps : i in N(j)} u {f_0 / eps})
  * and the dustbin updates of orc_sinkhorn.  Runs n_iter iterations from
  * f = g = 0. */
-int orc_sinkhorn_sparse(double D, int T, const int* I_off, const double* p, const int* J_off,
+int orc_sinkhorn_sparse(const double* Dj, int T, const int* I_off, const double* p, const int* J_off,
                         const double* c, const double* r, double eps, double c_out, int mode, double frac,
                         int n_iter, int rho, double* f, double* g, double* fd, double* gd) {
     int nI = I_off[T], nJ = J_off[T];
     int nd = mode ? T : 1;
     int* nbr = (int*)malloc(sizeof(int) * ((size_t)nJ * rho + 1));
-    orc_knn(D, T, I_off, p, J_off, c, r, rho, nbr);
+    orc_knn(Dj, T, I_off, p, J_off, c, r, rho, nbr);
     /* per observed spot: the model spots whose neighbour set holds it */
     int* rcount = (int*)calloc((size_t)nI + 1, sizeof(int));
     for (long e = 0; e < (long)nJ * rho; ++e)
@@ -1908,7 +1971,7 @@ int orc_sinkhorn_sparse(double D, int T, const int* I_off, const double* p, cons
                 int n = 0;
                 for (int e = rcount[i]; e < rcount[i + 1]; ++e) {
                     int j = rows[e];
-                    buf[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                    buf[n++] = (g[j] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, Dj[j])) / eps;
                 }
                 buf[n++] = (gd[dd] - c_out) / eps;
                 f[i] = -eps * lse(buf, n);
@@ -1928,7 +1991,7 @@ int orc_sinkhorn_sparse(double D, int T, const int* I_off, const double* p, cons
                 for (int k = 0; k < rho; ++k) {
                     int i = nbr[(long)j * rho + k];
                     if (i < 0) continue;
-                    buf[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, D)) / eps;
+                    buf[n++] = (f[i] - orc_pair_cost(p + 3 * i, c + 3 * j, r + 3 * j, Dj[j])) / eps;
                 }
                 buf[n++] = fd[dd] / eps;
                 g[j] = -eps * lse(buf, n);

@@ -29,6 +29,7 @@ int orc_reflections(double a, int hmax, int centering, int cap,
                     double* w, double* d0, int* nharm, int* hkl0);
 
 void orc_gamma(double omega, double G[9]);
+void orc_cost_lengths(const double* geom, int n, const int* det, double* out);
 
 long orc_forward(const double* geom, const double* w, const double* d0, const int* nharm, int M,
                  const double* R, const double* x, int N, const double* omega, int T,
@@ -46,12 +47,12 @@ void orc_pair_costs(int n, const double* p, const double* c, const double* r, do
 void orc_masses(int mode, double frac, int T, const int* I_off, const int* J_off,
                 double* U, double* O);
 
-int orc_sinkhorn(double D, int T, const int* I_off, const double* p,
+int orc_sinkhorn(const double* Dj, int T, const int* I_off, const double* p,
                  const int* J_off, const double* c, const double* r,
                  double eps, double c_out, int mode, double frac, int n_iter, double tol,
                  int warm, double* f, double* g, double* fd, double* gd);
 
-void orc_harvest(double D, int T, const int* I_off, const double* p,
+void orc_harvest(const double* Dj, int T, const int* I_off, const double* p,
                  const int* J_off, const double* c, const double* r,
                  double eps, double c_out, int mode, double frac,
                  const double* f, const double* g, const double* fd, const double* gd,
@@ -59,7 +60,7 @@ void orc_harvest(double D, int T, const int* I_off, const double* p,
 
 int orc_mstep(const double* geom, const double* w, const double* omega, int T,
               const int* I_off, const double* p, const int* J_off,
-              const int* grain, const int* plane, int N,
+              const int* grain, const int* plane, const int* det, int N,
               const double* cE, const double* rE,
               const double* f, const double* g, double eps,
               int n_newton, int n_mm, double tol_x, double tol_R, double hreg,
@@ -70,7 +71,7 @@ double orc_eps_schedule_f(double eps_final, int n_em, int k, double factor);
 
 int orc_em(const double* geom, const double* w, const double* d0, const int* nharm,
            const double* omega, int T, const int* I_off, const double* p,
-           const int* J_off, const int* grain, const int* plane, int N,
+           const int* J_off, const int* grain, const int* plane, const int* det, int N,
            double* R, double* x, double eps_final, int n_em, int n_sinkhorn,
            double c_out, int mode, double frac, int n_newton, int n_mm,
            double tol_x, double tol_R, double hreg, int mstep_kind,
@@ -96,14 +97,14 @@ int orc_kstar(int K, const double* gain);
 
 void orc_grain_objective(const double* geom, const double* w, const double* omega, int T,
                          const int* I_off, const double* p, const int* J_off,
-                         const int* grain, const int* plane, int N,
+                         const int* grain, const int* plane, const int* det, int N,
                          const double* cE, const double* rE,
                          const double* f, const double* g, double eps,
                          const double* R, const double* x, double* En);
 
 void orc_grain_grad(const double* geom, const double* w, const double* omega, int T,
                     const int* I_off, const double* p, const int* J_off,
-                    const int* grain, const int* plane, int N,
+                    const int* grain, const int* plane, const int* det, int N,
                     const double* f, const double* g, double eps,
                     const double* R, const double* x, double* grad);
 
@@ -113,19 +114,19 @@ int  orc_wahba(const double B[9], double R[9]);
 
 void orc_grain_gn(const double* geom, const double* w, const double* omega, int T,
                   const int* I_off, const double* p, const int* J_off,
-                  const int* grain, const int* plane, int N,
+                  const int* grain, const int* plane, const int* det, int N,
                   const double* cE, const double* rE, const double* f, const double* g, double eps,
                   const double* R, const double* x, double* grad, double* H, double* value);
 void orc_mstep_adjoint(const double* geom, const double* w, const double* omega, int T,
                        const int* I_off, const double* p, const int* J_off,
-                       const int* grain, const int* plane, int N,
+                       const int* grain, const int* plane, const int* det, int N,
                        const double* cE, const double* rE, const double* f, const double* g, double eps,
                        int n_steps, double lambda, double* R, double* x, double* step_norms);
-int orc_sinkhorn_unbalanced(double D, int T, const int* I_off, const double* p,
+int orc_sinkhorn_unbalanced(const double* Dj, int T, const int* I_off, const double* p,
                             const int* J_off, const double* c, const double* r,
                             double eps, double kappa, double lambda, int n_iter,
                             double* f, double* g);
-void orc_harvest_unbalanced(double D, int T, const int* I_off, const double* p,
+void orc_harvest_unbalanced(const double* Dj, int T, const int* I_off, const double* p,
                             const int* J_off, const double* c, const double* r, double eps,
                             const double* f, const double* g, int* assign, double* margin,
                             double* rowmass, double* q);
@@ -133,9 +134,9 @@ int orc_set_threads(int n);
 void orc_reciprocal_basis(double a, double b, double c, double alpha, double beta, double gamma, double B[9]);
 int orc_reflections_hkl(const double B[9], const int* hkl, int n, int cap,
                         double* w, double* d0, int* nharm, int* hkl0);
-void orc_knn(double D, int T, const int* I_off, const double* p, const int* J_off, const double* c,
+void orc_knn(const double* Dj, int T, const int* I_off, const double* p, const int* J_off, const double* c,
              const double* r, int rho, int* nbr);
-int orc_sinkhorn_sparse(double D, int T, const int* I_off, const double* p, const int* J_off,
+int orc_sinkhorn_sparse(const double* Dj, int T, const int* I_off, const double* p, const int* J_off,
                         const double* c, const double* r, double eps, double c_out, int mode, double frac,
                         int n_iter, int rho, double* f, double* g, double* fd, double* gd);
 long orc_start_grid(long n_full, int sym, int k, double cube, long cap, double* R_out, double* x_out);

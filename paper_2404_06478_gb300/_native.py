@@ -30,7 +30,8 @@ _pi = ctypes.POINTER(ctypes.c_int)
 
 class LaueGeometry(ctypes.Structure):
     _fields_ = [("beam", _f * 3), ("lam_min", _f), ("lam_max", _f), ("D", _f), ("n_det", _i),
-                ("det_centre", (_f * 3) * 4), ("det_normal", (_f * 3) * 4), ("det_half", _f * 4)]
+                ("det_centre", (_f * 3) * 4), ("det_normal", (_f * 3) * 4), ("det_half", _f * 4),
+                ("det_D", _f * 4)]
 
 
 class LaueLattice(ctypes.Structure):

@@ -57,6 +57,7 @@ def geometry_struct(geom) -> N.LaueGeometry:
         g.det_centre[k][:] = [float(v) for v in det.centre]
         g.det_normal[k][:] = [float(v) for v in det.normal]
         g.det_half[k] = float(det.half)
+        g.det_D[k] = float(getattr(det, "D", 0.0))
     return g
 
 

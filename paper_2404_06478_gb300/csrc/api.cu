@@ -46,6 +46,29 @@ GeomDev laue_geom_dev(const LaueGeometry& g) {
             d.nrm[k][a] = g.det_normal[k][a];
         }
         d.half[k] = g.det_half[k];
+        d.Dd[k] = g.det_D[k] > 0.0f ? g.det_D[k] : g.D;
+        // in-plane axes a1 = (y x n)/|y x n| (x when n is along y), a2 = n x a1
+        double nx = g.det_normal[k][0], ny = g.det_normal[k][1], nz = g.det_normal[k][2];
+        double nn = std::sqrt(nx * nx + ny * ny + nz * nz);
+        if (nn > 0.0) {
+            nx /= nn;
+            ny /= nn;
+            nz /= nn;
+        }
+        double a1[3] = {nz, 0.0, -nx};
+        double l1 = std::sqrt(a1[0] * a1[0] + a1[2] * a1[2]);
+        if (l1 < 1e-12) {
+            a1[0] = 1.0;
+            a1[2] = 0.0;
+        } else {
+            a1[0] /= l1;
+            a1[2] /= l1;
+        }
+        double a2[3] = {ny * a1[2] - nz * a1[1], nz * a1[0] - nx * a1[2], nx * a1[1] - ny * a1[0]};
+        for (int a = 0; a < 3; ++a) {
+            d.ax1[k][a] = (float)a1[a];
+            d.ax2[k][a] = (float)a2[a];
+        }
     }
     return d;
 }
@@ -56,8 +79,14 @@ int laue_check_geom(laue_handle* h, const LaueGeometry* g) {
     if (!(g->lam_min > 0.0f) || !(g->lam_max >= g->lam_min))
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "wavelength band must satisfy 0 < lam_min <= lam_max");
     if (!(g->D > 0.0f)) return laue_fail(h, LAUE_ERR_INVALID_ARG, "D must be positive");
-    for (int k = 0; k < g->n_det; ++k)
+    for (int k = 0; k < g->n_det; ++k) {
         if (!(g->det_half[k] > 0.0f)) return laue_fail(h, LAUE_ERR_INVALID_ARG, "detector half size must be > 0");
+        const float* n = g->det_normal[k];
+        if (!(n[0] * n[0] + n[1] * n[1] + n[2] * n[2] > 0.0f))
+            return laue_fail(h, LAUE_ERR_INVALID_ARG, "detector normal must be nonzero");
+        if (!(g->det_D[k] <= 0.0f || g->det_D[k] > 0.0f))
+            return laue_fail(h, LAUE_ERR_INVALID_ARG, "detector cost length must be a number");
+    }
     return LAUE_OK;
 }
 
@@ -446,6 +475,7 @@ int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* o
     a.obs_p = (const float4*)obs->p;
     a.mod_c = (const float4*)model->center;
     a.mod_r = (const float4*)model->ray;
+    a.mod_s = (const float4*)model->spot;
     a.obsX = (float4*)(ws + L.obsX);
     a.obsY = (float4*)(ws + L.obsY);
     a.modX = (float4*)(ws + L.modX);
@@ -485,6 +515,17 @@ int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* o
     a.tile_cols = sk_variant_threads(h->col_variant);
     double eps = prm->eps;
     a.negKD2 = (float)(-(double)geom->D * geom->D * 1.4426950408889634 / eps);
+    {
+        GeomDev G = laue_geom_dev(*geom);
+        double dmin = geom->D;
+        a.n_det = G.n_det;
+        for (int k = 0; k < 4; ++k) {
+            double Dk = k < G.n_det ? (double)G.Dd[k] : (double)geom->D;
+            a.negK_det[k] = (float)(-Dk * Dk * 1.4426950408889634 / eps);
+            if (k < G.n_det && Dk < dmin) dmin = Dk;
+        }
+        a.skipK = (float)(dmin * dmin * 1.4426950408889634 / eps);
+    }
     a.kc = (float)((double)prm->c_out * 1.4426950408889634 / eps);
     a.frac = prm->unmatched_frac;
     a.to_user = (float)(eps * 0.6931471805599453);
@@ -584,6 +625,15 @@ extern "C" int laue_cost_sinkhorn_sparse(laue_handle* h, const LaueGeometry* geo
     a.p = (const float4*)obs->p;
     a.c = (const float4*)model->center;
     a.r = (const float4*)model->ray;
+    a.s = (const float4*)model->spot;
+    {
+        GeomDev G = laue_geom_dev(*geom);
+        a.n_det = G.n_det;
+        for (int k = 0; k < 4; ++k) {
+            float dr = k < G.n_det ? G.Dd[k] / geom->D : 1.0f;
+            a.kdet[k] = dr * dr;
+        }
+    }
     a.ctrl = (int*)h->ws;
     const double eps = prm->eps;
     a.negK = (float)(-(double)geom->D * geom->D * 1.4426950408889634 / eps);
@@ -770,6 +820,10 @@ static int mstep_entry(laue_handle* h, const LaueGeometry* geom, const LaueLatti
     m.n_mm = prm->n_mm;
     for (int k = 0; k < 3; ++k) m.e[k] = geom->beam[k];
     m.D2 = geom->D * geom->D;
+    {
+        GeomDev G = laue_geom_dev(*geom);
+        for (int k = 0; k < 4; ++k) m.D2det[k] = k < G.n_det ? G.Dd[k] * G.Dd[k] : m.D2;
+    }
     if (adjoint)
         return laue_cuda_check(h, mstep_adjoint_run(m, lc, prm->n_newton, (cudaStream_t)stream),
                                "mstep_adjoint launch");
@@ -836,6 +890,10 @@ extern "C" int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, con
     m.gstate = (float*)(ws + L.gsum);
     for (int k = 0; k < 3; ++k) m.e[k] = geom->beam[k];
     m.D2 = geom->D * geom->D;
+    {
+        GeomDev G = laue_geom_dev(*geom);
+        for (int k = 0; k < 4; ++k) m.D2det[k] = k < G.n_det ? G.Dd[k] * G.Dd[k] : m.D2;
+    }
     m.grad = grad;
     m.value = value;
     return laue_cuda_check(h, grad_run(m, lc, (cudaStream_t)stream), "objective_grad launch");

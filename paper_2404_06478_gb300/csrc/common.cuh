@@ -37,6 +37,7 @@ enum CtrlSlot {
     CTRL_SLOTS = 64
 };
 
+constexpr int kSfSpotFloats = 11;     // single-fit scratch per listed spot: tm, rE (3), cE (3), v (3), kd
 constexpr size_t kCtrlBytes = 4096;  // status + counters + small scalars
 
 // ---------------------------------------------------------------------------
@@ -111,9 +112,10 @@ inline Layout make_layout(const LaueProblemDims& d, int sm_count) {
     L.jsum = take(sizeof(float) * 12 * (size_t)(d.n_model + 1));
     L.gsum = take(sizeof(float) * 16 * (size_t)(d.n_grains + 1));
     L.gidx = take(sizeof(int) * ((size_t)T * (d.n_grains + 1) + 16));
-    // single-grain fits: 10 floats per listed spot + cached row normalisers, per CTA
+    // single-grain fits: kSfSpotFloats per listed spot (2048 listed spots) + 4096
+    // cached row normalisers, per CTA (the slices of sf_slice in single.cu)
     size_t sf_ctas = d.n_starts > 0 ? (size_t)sm_count * 4 : 0;
-    L.sfs = take(sizeof(float) * ((size_t)2048 * 10 + 4096) * sf_ctas);
+    L.sfs = take(sizeof(float) * ((size_t)2048 * kSfSpotFloats + 4096) * sf_ctas);
     L.spot = take(d.n_candidates > 0 ? sizeof(int) * (4 * (size_t)d.n_candidates + 16 + 2 * (size_t)sm_count * 4 + 64) +
                                            sizeof(float) * (size_t)(d.n_obs + 1)
                                      : 0);

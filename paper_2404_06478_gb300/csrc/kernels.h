@@ -10,6 +10,8 @@ struct GeomDev {
     float lam_min, lam_max, D;
     int n_det;
     float ctr[4][3], nrm[4][3], half[4];
+    float Dd[4];                // cost length of each detector (D where none is set)
+    float ax1[4][3], ax2[4][3];  // in-plane axes of each detector
 };
 
 // ----------------------------------------------------------------- forward
@@ -65,13 +67,14 @@ struct SkArgs {
     const float4* obs_p;   // caller's observed spots (p, unused)
     const float4* mod_c;   // caller's centres (c, unused)
     const float4* mod_r;   // caller's rays (r, lambda)
+    const float4* mod_s;   // caller's model spots (s, detector index)
     // workspace, pair-interleaved (angle blocks padded to even counts):
     float4* obsX;          // {px_a, px_b, py_a, py_b}
     float4* obsY;          // {pz_a, pz_b, F_a, F_b}
     float4* modX;          // {-cx_a, -cx_b, -cy_a, -cy_b}
     float4* modY;          // {-cz_a, -cz_b, G_a, G_b}
     float4* modZ;          // {-rx_a, -rx_b, -ry_a, -ry_b}
-    float4* modW;          // {-rz_a, -rz_b, 0, 0}
+    float4* modW;          // {-rz_a, -rz_b, -K_a, -K_b}: K_j = D_j^2 log2(e) / eps of the spot's detector
     int* I2_off;           // T+1 pair offsets of the observed blocks
     int* J2_off;           // T+1 pair offsets of the model blocks
     // spatial order: within each angle block the spots are packed sorted by the
@@ -96,6 +99,9 @@ struct SkArgs {
     int max_row_tiles, max_col_tiles;
     int tile_rows, tile_cols;
     float negKD2;          // -D^2 log2(e) / eps
+    float negK_det[4];     // -D_k^2 log2(e) / eps of each detector k
+    int n_det;
+    float skipK;           // smallest K_j of any spot (the cone bounds take it)
     float kc;              // c_out log2(e) / eps
     double frac;           // unmatched-model fraction
     float to_user;         // eps ln 2: internal -> mm^2
@@ -125,8 +131,11 @@ struct SpArgs {
     const float4* p;       // observed spots (p, unused)
     const float4* c;       // model centres (c, unused)
     const float4* r;       // model rays (r, lambda)
+    const float4* s;       // model spots (s, detector index)
+    float kdet[4];         // (D_k / D)^2 of each detector k
+    int n_det;
     // workspace
-    int2* cent;            // n_model x rho: {observed index or -1, e2 bits}, by increasing e2
+    int2* cent;            // n_model x rho: {observed index or -1, e2 (D_j / D)^2 bits}, by increasing e2
     int2* rent;            // CSR rows: {model index, e2 bits}, ascending model index
     int* rptr;             // n_obs + 1 row starts
     int* rfill;            // n_obs fill counters
@@ -200,7 +209,8 @@ struct MsArgs {
     float tol_x, tol_R, hreg;
     int n_newton, n_mm;
     float e[3];
-    float D2;               // D^2 (adjoint)
+    float D2;               // D^2
+    float D2det[4];         // D_k^2 of each detector (the cost length of its spots)
     float* grad;            // N x 6 (adjoint)
     float* value;           // N (adjoint, optional)
 };
@@ -259,7 +269,6 @@ struct SpotArgs {
     int* kstar;
 };
 
-size_t single_fit_scratch_floats(int cap, int icap, int ctas);
 cudaError_t spot_matrix_run(const SfArgs& a, const SpotArgs& sp, int ctas, bool count_only, cudaStream_t s);
 cudaError_t spot_greedy_run(const SpotArgs& sp, int n_obs, int Nc, int k_max, int sm_count, cudaStream_t s);
 cudaError_t single_fit_run(const SfArgs& a, int ctas, cudaStream_t s);

@@ -125,7 +125,6 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
     init_stage(S);
     uint32_t parity[2] = {0u, 0u};
     const int n_tiles = a.ctrl[CTRL_N_COL_TILES];
-    const f2 K2 = dup(a.negKD2);
     const Srcs src{{a.obsX, a.obsY, nullptr, nullptr}, 2};
     while (true) {
         int tile = next_tile(S, a.ctrl + CTRL_GEN_NEXT, n_tiles);
@@ -183,8 +182,8 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
                 ulonglong2 X = *(const ulonglong2*)&sX[k];
                 ulonglong2 Y = *(const ulonglong2*)&sY[k];
                 // E-step plan exponents of the 2 x 2 pairs: F_i + G_j - K e2
-                f2 va = add2(pair_v2(X.x, X.y, Y.x, P.ncxa, P.ncya, P.ncza, P.nrxa, P.nrya, P.nrza, K2, Y.y), Gpa);
-                f2 vb = add2(pair_v2(X.x, X.y, Y.x, P.ncxb, P.ncyb, P.nczb, P.nrxb, P.nryb, P.nrzb, K2, Y.y), Gpb);
+                f2 va = add2(pair_v2(X.x, X.y, Y.x, P.ncxa, P.ncya, P.ncza, P.nrxa, P.nrya, P.nrza, P.ka, Y.y), Gpa);
+                f2 vb = add2(pair_v2(X.x, X.y, Y.x, P.ncxb, P.ncyb, P.nczb, P.nrxb, P.nryb, P.nrzb, P.kb, Y.y), Gpb);
                 float m4 = fmaxf(fmaxf(lo(va), hi(va)), fmaxf(lo(vb), hi(vb)));
                 if (m4 < kQSkip) continue;
                 float4 x4 = sX[k], y4 = sY[k];
@@ -202,11 +201,17 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
             for (int lane = 0; lane < 2; ++lane) {
                 MsCol& C = lane ? B : A;
                 if (lcol + lane >= nj) continue;
-                float* o = m.jsum + 12 * (size_t)a.mod_perm[a.J_off[t] + lcol + lane];
+                const int jc = a.mod_perm[a.J_off[t] + lcol + lane];
+                float* o = m.jsum + 12 * (size_t)jc;
+                // cost length of the spot's detector: C_ij = D_j^2 |rhat - r|^2, so the
+                // Newton and MM sums carry the weight (D_j / D)^2
+                const int det = a.mod_s ? (int)a.mod_s[jc].w : -1;
+                const float D2j = (det >= 0 && det < a.n_det) ? m.D2det[det] : m.D2;
+                const float kd = D2j / m.D2;
                 if (MODE >= 2) {
                     // per-spot gradient: x part Gamma^T dC/dc, rotation part
                     // v x (Gamma^T y), y = -2 ((gr.u) e + (u.e) gr), u = Gamma R w_m
-                    float D2x2 = 2.0f * m.D2;
+                    float D2x2 = 2.0f * D2j;
                     float gc[3] = {D2x2 * C.acc[0], D2x2 * C.acc[1], D2x2 * C.acc[2]};
                     float gr[3] = {D2x2 * C.acc[3], D2x2 * C.acc[4], D2x2 * C.acc[5]};
                     float gx[3];
@@ -227,25 +232,25 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
                     o[3] = gx[0];
                     o[4] = gx[1];
                     o[5] = gx[2];
-                    o[6] = m.D2 * C.acc[6];
-                    if (MODE == 3) {
-                        o[7] = C.acc[7];
-                        o[8] = C.acc[8];
-                        o[9] = C.acc[9];
+                    o[6] = D2j * C.acc[6];
+                    if (MODE == 3) {  // the Gauss-Newton sums, weighted (the grain kernel applies 2 D^2)
+                        o[7] = kd * C.acc[7];
+                        o[8] = kd * C.acc[8];
+                        o[9] = kd * C.acc[9];
                     }
                     if (!C.ok)
                         for (int k = 0; k < (MODE == 3 ? 10 : 7); ++k) o[k] = 0.0f;
                 } else if (MODE == 1) {
-                    o[9] = C.ok ? C.acc[0] : 0.0f;
-                    o[10] = C.ok ? C.acc[1] : 0.0f;
-                    o[11] = C.ok ? C.acc[2] : 0.0f;
+                    o[9] = C.ok ? kd * C.acc[0] : 0.0f;
+                    o[10] = C.ok ? kd * C.acc[1] : 0.0f;
+                    o[11] = C.ok ? kd * C.acc[2] : 0.0f;
                 } else if (C.ok) {
                     float gx[3];
                     gamT_apply(cg, sg, C.acc, gx);
                     float hx[6];
                     sym_gamT_gam(cg, sg, C.acc + 3, hx);
-                    for (int k = 0; k < 3; ++k) o[k] = gx[k];
-                    for (int k = 0; k < 6; ++k) o[3 + k] = hx[k];
+                    for (int k = 0; k < 3; ++k) o[k] = kd * gx[k];
+                    for (int k = 0; k < 6; ++k) o[3 + k] = kd * hx[k];
                 } else {
                     for (int k = 0; k < 9; ++k) o[k] = 0.0f;
                 }

@@ -383,6 +383,7 @@ __device__ __forceinline__ void lse_merge_into(float& m, float& s, float m2, flo
 struct ColPair {
     f2 ncxa, ncya, ncza, nrxa, nrya, nrza;
     f2 ncxb, ncyb, nczb, nrxb, nryb, nrzb;
+    f2 ka, kb;  // {-K_a, -K_a}, {-K_b, -K_b}: cost factors of the two model spots
     RowLse A, B;
 };
 
@@ -400,6 +401,8 @@ __device__ __forceinline__ void load_col_pair(const SkArgs& a, int q, ColPair& C
     C.nrxb = dup(Z.y);
     C.nryb = dup(Z.w);
     C.nrzb = dup(W.y);
+    C.ka = dup(W.z);
+    C.kb = dup(W.w);
 }
 
 }  // namespace laue

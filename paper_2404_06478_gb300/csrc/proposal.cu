@@ -1203,6 +1203,9 @@ extern "C" int laue_lp_scene(laue_handle* h, const LaueGeometry* geom, const Lau
         !(sigma_mm >= 0.0f) || !(outlier_ratio >= 0.0) || (uintptr_t)p % 16)
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "scene sizes");
     if (lat->M > 65535) return laue_fail(h, LAUE_ERR_INVALID_ARG, "too many planes");
+    for (int k = 0; k < geom->n_det; ++k)  // the scenes add noise and outliers in the detectors' x and y
+        if (geom->det_normal[k][0] != 0.0f || geom->det_normal[k][1] != 0.0f)
+            return laue_fail(h, LAUE_ERR_INVALID_ARG, "training scenes need detectors normal to z");
     SceneArgs a;
     a.G = laue_geom_dev(*geom);
     a.w_d0 = (const float4*)lat->w_d0;

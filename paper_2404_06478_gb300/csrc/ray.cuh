@@ -8,6 +8,39 @@
 
 namespace laue {
 
+// Plane point s inside detector k: |(s - centre).a| < half for both in-plane
+// axes a1, a2 (for a plane normal to z: |dx| < half and |dy| < half).
+__device__ __forceinline__ bool on_detector(const GeomDev& G, int k, float s0, float s1, float s2) {
+    float d0 = s0 - G.ctr[k][0], d1 = s1 - G.ctr[k][1], d2 = s2 - G.ctr[k][2];
+    float u = fmaf(d0, G.ax1[k][0], fmaf(d1, G.ax1[k][1], d2 * G.ax1[k][2]));
+    float v = fmaf(d0, G.ax2[k][0], fmaf(d1, G.ax2[k][1], d2 * G.ax2[k][2]));
+    return fabsf(u) < G.half[k] && fabsf(v) < G.half[k];
+}
+
+// Detector hit by the ray c + tau r: the smallest tau > 0 whose plane point is
+// on its detector; -1 when none.  s receives the point.
+__device__ __forceinline__ int hit_detector(const GeomDev& G, const float* r, const float* c, float* s) {
+    int det = -1;
+    float best = 3.0e38f;
+    for (int k = 0; k < G.n_det; ++k) {
+        float den = G.nrm[k][0] * r[0] + G.nrm[k][1] * r[1] + G.nrm[k][2] * r[2];
+        if (den == 0.0f) continue;
+        float num = G.nrm[k][0] * (G.ctr[k][0] - c[0]) + G.nrm[k][1] * (G.ctr[k][1] - c[1]) +
+                    G.nrm[k][2] * (G.ctr[k][2] - c[2]);
+        float tau = num / den;
+        if (!(tau > 0.0f)) continue;
+        float s0 = c[0] + tau * r[0], s1 = c[1] + tau * r[1], s2 = c[2] + tau * r[2];
+        if (on_detector(G, k, s0, s1, s2) && tau < best) {
+            best = tau;
+            det = k;
+            s[0] = s0;
+            s[1] = s1;
+            s[2] = s2;
+        }
+    }
+    return det;
+}
+
 struct RayOut {
     float r[3];
     float lam;
@@ -44,25 +77,7 @@ __device__ __forceinline__ bool ray_one(const GeomDev& G, float cg, float sg, co
             break;
         }
     }
-    o.det = -1;
-    float best = 3.0e38f;
-    for (int k = 0; k < G.n_det; ++k) {
-        float den = G.nrm[k][0] * o.r[0] + G.nrm[k][1] * o.r[1] + G.nrm[k][2] * o.r[2];
-        if (den == 0.0f) continue;
-        float num = G.nrm[k][0] * (G.ctr[k][0] - o.c[0]) + G.nrm[k][1] * (G.ctr[k][1] - o.c[1]) +
-                    G.nrm[k][2] * (G.ctr[k][2] - o.c[2]);
-        float tau = num / den;
-        if (!(tau > 0.0f)) continue;
-        float s0 = o.c[0] + tau * o.r[0], s1 = o.c[1] + tau * o.r[1], s2 = o.c[2] + tau * o.r[2];
-        float dist = fmaxf(fabsf(s0 - G.ctr[k][0]), fmaxf(fabsf(s1 - G.ctr[k][1]), fabsf(s2 - G.ctr[k][2])));
-        if (dist < G.half[k] && tau < best) {
-            best = tau;
-            o.det = k;
-            o.s[0] = s0;
-            o.s[1] = s1;
-            o.s[2] = s2;
-        }
-    }
+    o.det = hit_detector(G, o.r, o.c, o.s);
     return in_band && o.det >= 0;
 }
 

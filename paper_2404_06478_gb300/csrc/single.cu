@@ -22,6 +22,7 @@
 // Plan entries below 2^-40 are skipped.  Every reduction runs in a fixed order.
 #include "pairs.cuh"
 #include "mstep_common.cuh"
+#include "ray.cuh"
 
 namespace laue {
 
@@ -33,18 +34,20 @@ struct SfScratch {
     float* rE;   // cap x 3 E-step rays
     float* cE;   // cap x 3 E-step centres
     float* v;    // cap x 3 MM sums / filter column masses
+    float* kd;   // cap: (D_j / D)^2, the cost length of the spot's detector relative to D
     float* lse;  // icap row normalisers of one angle block (log2)
 };
 
 __device__ __forceinline__ SfScratch sf_slice(const SfArgs& a, int cta) {
     SfScratch s;
-    size_t per = (size_t)a.cap * 10 + a.icap;
+    size_t per = (size_t)a.cap * kSfSpotFloats + a.icap;
     float* base = a.scratch + per * cta;
     s.tm = (int*)base;
     s.rE = base + a.cap;
     s.cE = base + 4 * a.cap;
     s.v = base + 7 * a.cap;
-    s.lse = base + 10 * a.cap;
+    s.kd = base + 10 * a.cap;
+    s.lse = base + 11 * a.cap;
     return s;
 }
 
@@ -69,8 +72,9 @@ __device__ __forceinline__ void sf_ray(const SfArgs& a, const float* R, const fl
     if (nh) *nh = a.nharm[m];
 }
 
-// Visibility of a ray (same decisions as the forward kernel).
-__device__ __forceinline__ bool sf_visible(const GeomDev& G, const float* r, const float* c, float lam0, int nh) {
+// Detector of a visible ray, -1 when the ray is not visible (same decisions
+// as the forward kernel).
+__device__ __forceinline__ int sf_visible(const GeomDev& G, const float* r, const float* c, float lam0, int nh) {
     bool in_band = false;
     for (int n = 1; n <= nh; ++n) {
         float ln = lam0 / (float)n;
@@ -79,19 +83,9 @@ __device__ __forceinline__ bool sf_visible(const GeomDev& G, const float* r, con
             break;
         }
     }
-    if (!in_band) return false;
-    for (int k = 0; k < G.n_det; ++k) {
-        float den = G.nrm[k][0] * r[0] + G.nrm[k][1] * r[1] + G.nrm[k][2] * r[2];
-        if (den == 0.0f) continue;
-        float num = G.nrm[k][0] * (G.ctr[k][0] - c[0]) + G.nrm[k][1] * (G.ctr[k][1] - c[1]) +
-                    G.nrm[k][2] * (G.ctr[k][2] - c[2]);
-        float tau = num / den;
-        if (!(tau > 0.0f)) continue;
-        float s0 = c[0] + tau * r[0], s1 = c[1] + tau * r[1], s2 = c[2] + tau * r[2];
-        float dist = fmaxf(fabsf(s0 - G.ctr[k][0]), fmaxf(fabsf(s1 - G.ctr[k][1]), fabsf(s2 - G.ctr[k][2])));
-        if (dist < G.half[k]) return true;
-    }
-    return false;
+    if (!in_band) return -1;
+    float s[3];
+    return hit_detector(G, r, c, s);
 }
 
 struct SfShared {
@@ -114,14 +108,15 @@ __device__ void sf_cut(const SfArgs& a, SfShared& S, const SfScratch& Z) {
     for (long long base = 0; base < nr; base += kSfThreads) {
         long long id = base + threadIdx.x;
         bool vis = false;
-        int t = 0, m = 0;
+        int t = 0, m = 0, det = -1;
         if (id < nr) {
             t = (int)(id / a.M);
             m = (int)(id % a.M);
             float r[3], c[3], lam0;
             int nh;
             sf_ray(a, S.R, S.x, t, m, r, c, &lam0, &nh);
-            vis = sf_visible(a.G, r, c, lam0, nh);
+            det = sf_visible(a.G, r, c, lam0, nh);
+            vis = det >= 0;
         }
         unsigned ball = __ballot_sync(0xffffffffu, vis);
         int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -134,8 +129,13 @@ __device__ void sf_cut(const SfArgs& a, SfShared& S, const SfScratch& Z) {
         }
         int pos = S.n_spots + before + __popc(ball & ((1u << lane) - 1u));
         if (vis) {
-            if (pos < a.cap) Z.tm[pos] = (t << 16) | m;
-            else S.overflow = 1;
+            if (pos < a.cap) {
+                Z.tm[pos] = (t << 16) | m;
+                float dr = a.G.Dd[det] / a.G.D;
+                Z.kd[pos] = dr * dr;
+            } else {
+                S.overflow = 1;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) S.n_spots += total;
@@ -176,7 +176,7 @@ __device__ __forceinline__ float sf_row_lse(const SfArgs& a, const SfShared& S, 
     L.init(dust);
     npair += (unsigned)(S.t_off[t + 1] - S.t_off[t]);
     for (int j = S.t_off[t]; j < S.t_off[t + 1]; ++j) {
-        float v = negK * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j);
+        float v = negK * Z.kd[j] * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j);
         L.merge(v, 1.0f);
     }
     return L.value();
@@ -210,9 +210,9 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
             float l = sf_row_lse(a, S, Z, t, p, negK, dust, npair);
             npair += (unsigned)(j1 - j0);
             for (int j = j0; j < j1; ++j) {
-                float v = negK * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j) - l;
+                float v = negK * Z.kd[j] * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j) - l;
                 if (v < kSfSkip) continue;
-                float Q = ex2(v);
+                float Q = ex2(v) * Z.kd[j];  // M-step weight Q_ij (D_j / D)^2
                 const float* r = Z.rE + 3 * j;
                 float d0 = p.x - c[0], d1 = p.y - c[1], d2 = p.z - c[2];
                 float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
@@ -269,7 +269,7 @@ __device__ void sf_columns(const SfArgs& a, SfShared& S, const SfScratch& Z, flo
                 float4 p = a.p[i0 + k];
                 float l = k < nl ? Z.lse[k] : sf_row_lse(a, S, Z, t, p, negK, dust, npair);
                 ++npair;
-                float v = negK * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j) - l;
+                float v = negK * Z.kd[j] * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j) - l;
                 if (v < kSfSkip) continue;
                 float Q = ex2(v);
                 if (massonly) {
@@ -288,9 +288,10 @@ __device__ void sf_columns(const SfArgs& a, SfShared& S, const SfScratch& Z, flo
                 s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             }
             if (lane == 0) {
-                Z.v[3 * j] = s0;
-                Z.v[3 * j + 1] = s1;
-                Z.v[3 * j + 2] = s2;
+                const float w = massonly ? 1.0f : Z.kd[j];  // MM weight (D_j / D)^2
+                Z.v[3 * j] = s0 * w;
+                Z.v[3 * j + 1] = s1 * w;
+                Z.v[3 * j + 2] = s2 * w;
             }
         }
         __syncthreads();
@@ -449,7 +450,8 @@ __global__ void __launch_bounds__(kSfThreads) spot_matrix_kernel(SfArgs a, SpotA
                     Lse2 L;
                     L.m = kNegHuge;
                     L.s = 0.0f;
-                    for (int j = j0; j < j1; ++j) L.merge(negK * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j), 1.0f);
+                    for (int j = j0; j < j1; ++j)
+                        L.merge(negK * Z.kd[j] * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j), 1.0f);
                     val = (L.value() + kc) * 0.6931471805599453f;
                 }
                 bool nz = val > 0.0f;
@@ -619,7 +621,7 @@ cudaError_t spot_greedy_run(const SpotArgs& sp, int n_obs, int Nc, int k_max, in
     return cudaGetLastError();
 }
 
-size_t single_fit_scratch_floats(int cap, int icap, int ctas) { return ((size_t)cap * 10 + icap) * ctas; }
+static_assert(kSfCap == 2048 && kSfIcap == 4096, "the workspace layout reserves the single-fit scratch for these");
 
 cudaError_t single_fit_run(const SfArgs& a, int ctas, cudaStream_t s) {
     size_t shm = sizeof(float) * 6 * (size_t)a.M;

@@ -388,7 +388,8 @@ __global__ void sk_pack_kernel(SkArgs a) {
         Z[lane] = -r.x;
         Z[2 + lane] = -r.y;
         W[lane] = -r.z;
-        W[2 + lane] = 0.0f;
+        int det = a.mod_s ? (int)a.mod_s[k].w : -1;
+        W[2 + lane] = (det >= 0 && det < a.n_det) ? a.negK_det[det] : a.negKD2;
         if (lane == 0 && l + 1 == a.J_off[t + 1] - a.J_off[t]) {
             X[1] = 0.0f;
             X[3] = 0.0f;
@@ -453,36 +454,8 @@ struct RowPair {
     RowLse A, B;
 };
 
-__device__ __forceinline__ void row_chunk(RowPair& R, const float4* __restrict__ sX, const float4* __restrict__ sY,
-                                          const float4* __restrict__ sZ, const float4* __restrict__ sW, int n,
-                                          f2 K2) {
-    int k = 0;
-    for (; k + kGroup <= n; k += kGroup) {
-        f2 va[kGroup], vb[kGroup];
-#pragma unroll
-        for (int g = 0; g < kGroup; ++g) {
-            ulonglong2 X = *(const ulonglong2*)&sX[k + g];
-            ulonglong2 Y = *(const ulonglong2*)&sY[k + g];
-            ulonglong2 Z = *(const ulonglong2*)&sZ[k + g];
-            ulonglong2 W = *(const ulonglong2*)&sW[k + g];
-            va[g] = pair_v2(R.pxa, R.pya, R.pza, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y);
-            vb[g] = pair_v2(R.pxb, R.pyb, R.pzb, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y);
-        }
-        R.A.add4(va);
-        R.B.add4(vb);
-    }
-    for (; k < n; ++k) {
-        ulonglong2 X = *(const ulonglong2*)&sX[k];
-        ulonglong2 Y = *(const ulonglong2*)&sY[k];
-        ulonglong2 Z = *(const ulonglong2*)&sZ[k];
-        ulonglong2 W = *(const ulonglong2*)&sW[k];
-        R.A.add1(pair_v2(R.pxa, R.pya, R.pza, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y));
-        R.B.add1(pair_v2(R.pxb, R.pyb, R.pzb, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y));
-    }
-}
-
 __device__ __forceinline__ void col_chunk(ColPair& C, const float4* __restrict__ sX, const float4* __restrict__ sY,
-                                          int n, f2 K2) {
+                                          int n) {
     int k = 0;
     for (; k + kGroup <= n; k += kGroup) {
         f2 va[kGroup], vb[kGroup];
@@ -490,8 +463,8 @@ __device__ __forceinline__ void col_chunk(ColPair& C, const float4* __restrict__
         for (int g = 0; g < kGroup; ++g) {
             ulonglong2 X = *(const ulonglong2*)&sX[k + g];
             ulonglong2 Y = *(const ulonglong2*)&sY[k + g];
-            va[g] = pair_v2(X.x, X.y, Y.x, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, K2, Y.y);
-            vb[g] = pair_v2(X.x, X.y, Y.x, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, K2, Y.y);
+            va[g] = pair_v2(X.x, X.y, Y.x, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, C.ka, Y.y);
+            vb[g] = pair_v2(X.x, X.y, Y.x, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, C.kb, Y.y);
         }
         C.A.add4(va);
         C.B.add4(vb);
@@ -499,8 +472,8 @@ __device__ __forceinline__ void col_chunk(ColPair& C, const float4* __restrict__
     for (; k < n; ++k) {
         ulonglong2 X = *(const ulonglong2*)&sX[k];
         ulonglong2 Y = *(const ulonglong2*)&sY[k];
-        C.A.add1(pair_v2(X.x, X.y, Y.x, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, K2, Y.y));
-        C.B.add1(pair_v2(X.x, X.y, Y.x, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, K2, Y.y));
+        C.A.add1(pair_v2(X.x, X.y, Y.x, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, C.ka, Y.y));
+        C.B.add1(pair_v2(X.x, X.y, Y.x, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, C.kb, Y.y));
     }
 }
 
@@ -510,28 +483,28 @@ __device__ __forceinline__ void col_chunk(ColPair& C, const float4* __restrict__
 // packed adds for 4 pair evaluations.
 __device__ __forceinline__ void row_chunk_sum(const RowPair& R, const float4* __restrict__ sX,
                                               const float4* __restrict__ sY, const float4* __restrict__ sZ,
-                                              const float4* __restrict__ sW, int n, f2 K2, f2& Sa, f2& Sb) {
+                                              const float4* __restrict__ sW, int n, f2& Sa, f2& Sb) {
 #pragma unroll 4
     for (int k = 0; k < n; ++k) {
         ulonglong2 X = *(const ulonglong2*)&sX[k];
         ulonglong2 Y = *(const ulonglong2*)&sY[k];
         ulonglong2 Z = *(const ulonglong2*)&sZ[k];
         ulonglong2 W = *(const ulonglong2*)&sW[k];
-        f2 va = pair_v2(R.pxa, R.pya, R.pza, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y);
-        f2 vb = pair_v2(R.pxb, R.pyb, R.pzb, X.x, X.y, Y.x, Z.x, Z.y, W.x, K2, Y.y);
+        f2 va = pair_v2(R.pxa, R.pya, R.pza, X.x, X.y, Y.x, Z.x, Z.y, W.x, W.y, Y.y);
+        f2 vb = pair_v2(R.pxb, R.pyb, R.pzb, X.x, X.y, Y.x, Z.x, Z.y, W.x, W.y, Y.y);
         Sa = add2(Sa, pk(ex2(lo(va)), ex2(hi(va))));
         Sb = add2(Sb, pk(ex2(lo(vb)), ex2(hi(vb))));
     }
 }
 
 __device__ __forceinline__ void col_chunk_sum(const ColPair& C, const float4* __restrict__ sX,
-                                              const float4* __restrict__ sY, int n, f2 K2, f2& Sa, f2& Sb) {
+                                              const float4* __restrict__ sY, int n, f2& Sa, f2& Sb) {
 #pragma unroll 4
     for (int k = 0; k < n; ++k) {
         ulonglong2 X = *(const ulonglong2*)&sX[k];
         ulonglong2 Y = *(const ulonglong2*)&sY[k];
-        f2 va = pair_v2(X.x, X.y, Y.x, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, K2, Y.y);
-        f2 vb = pair_v2(X.x, X.y, Y.x, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, K2, Y.y);
+        f2 va = pair_v2(X.x, X.y, Y.x, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, C.ka, Y.y);
+        f2 vb = pair_v2(X.x, X.y, Y.x, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, C.kb, Y.y);
         Sa = add2(Sa, pk(ex2(lo(va)), ex2(hi(va))));
         Sb = add2(Sb, pk(ex2(lo(vb)), ex2(hi(vb))));
     }
@@ -541,14 +514,14 @@ constexpr float kTinySum = 1.0e-30f;  // below ~2^-100 the fast sum is recompute
 
 // Exact row log-sum-exp from global memory (running maximum), for rows whose
 // shifted sum underflowed.
-__device__ float row_exact(const SkArgs& a, int t, f2 px, f2 py, f2 pz, float dustv, f2 K2) {
+__device__ float row_exact(const SkArgs& a, int t, f2 px, f2 py, f2 pz, float dustv) {
     atomicAdd((unsigned*)a.ctrl + CTRL_EXACT_ROWS, 1u);
     RowLse L;
     L.init(dustv);
     for (int q = a.J2_off[t]; q < a.J2_off[t + 1]; ++q) {
         float4 x = a.modX[q], y = a.modY[q], z = a.modZ[q], w = a.modW[q];
         L.add1(pair_v2(px, py, pz, pk(x.x, x.y), pk(x.z, x.w), pk(y.x, y.y), pk(z.x, z.y), pk(z.z, z.w),
-                       pk(w.x, w.y), K2, pk(y.z, y.w)));
+                       pk(w.x, w.y), pk(w.z, w.w), pk(y.z, y.w)));
     }
     return L.value();
 }
@@ -584,7 +557,6 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
     uint32_t parity[2] = {0u, 0u};
     DustPtrs D = dust_ptrs(a.dust, a.T);
     const int n_tiles = a.ctrl[CTRL_N_ROW_TILES];
-    const f2 K2 = dup(a.negKD2);
     const Srcs src{{a.modX, a.modY, a.modZ, a.modW}, 4};
     while (true) {
         int tile = next_tile(S, a.ctrl + CTRL_ROW_NEXT, n_tiles);
@@ -617,7 +589,7 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
             }
         };
         auto body = [&](int st, int n, int) {
-            if (valid) row_chunk_sum(R, S.s[0][st], S.s[1][st], S.s[2][st], S.s[3][st], n, K2, Sa, Sb);
+            if (valid) row_chunk_sum(R, S.s[0][st], S.s[1][st], S.s[2][st], S.s[3][st], n, Sa, Sb);
         };
         // the model chunks this tile of observed spots can see (exact underflow skipping)
         const int nch = (nj + kChunk - 1) / kChunk;
@@ -628,7 +600,7 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
             const int g1 = a.obs_gbase[t] + (td.y + td.z - 1 - a.I2_off[t]) / kChunk;
             Cone O = load_cone(a.obs_cone, a.obs_ext, g0);
             if (g1 != g0) O = merge_cones(O, load_cone(a.obs_cone, a.obs_ext, g1), true);
-            const float K = -a.negKD2;
+            const float K = a.skipK;  // the smallest cost factor of any spot
             const int mg = a.mod_gbase[t];
             n_list = build_chunk_list(S, nch, [&](int c) {
                 return min_scaled_cost(O, load_cone(a.mod_cone, a.mod_ext, mg + c), K) <= kSkipLog2;
@@ -649,8 +621,8 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
             break;
         }
         float sa = lo(Sa) + hi(Sa), sb = lo(Sb) + hi(Sb);
-        float Fa = valid ? (sa > kTinySum ? -(shift + lg2(sa)) : -row_exact(a, t, R.pxa, R.pya, R.pza, dustv, K2)) : 0.0f;
-        float Fb = vb ? (sb > kTinySum ? -(shift + lg2(sb)) : -row_exact(a, t, R.pxb, R.pyb, R.pzb, dustv, K2)) : 0.0f;
+        float Fa = valid ? (sa > kTinySum ? -(shift + lg2(sa)) : -row_exact(a, t, R.pxa, R.pya, R.pza, dustv)) : 0.0f;
+        float Fb = vb ? (sb > kTinySum ? -(shift + lg2(sb)) : -row_exact(a, t, R.pxb, R.pyb, R.pzb, dustv)) : 0.0f;
         if (ub) {  // Algorithm UnbalancedOT: the balanced update raised to kappa / (kappa + eps)
             Fa = nj > 0 ? a.tau_row * Fa : 0.0f;
             Fb = nj > 0 ? a.tau_row * Fb : 0.0f;
@@ -712,7 +684,6 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
     uint32_t parity[2] = {0u, 0u};
     DustPtrs D = dust_ptrs(a.dust, a.T);
     const int n_tiles = a.ctrl[CTRL_N_COL_TILES];
-    const f2 K2 = dup(a.negKD2);
     const Srcs src{{a.obsX, a.obsY, nullptr, nullptr}, 2};
     while (true) {
         int tile = next_tile(S, a.ctrl + CTRL_COL_NEXT, n_tiles);
@@ -738,7 +709,7 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
             }
         };
         auto body = [&](int st, int n, int) {
-            if (valid) col_chunk_sum(C, S.s[0][st], S.s[1][st], n, K2, Sa, Sb);
+            if (valid) col_chunk_sum(C, S.s[0][st], S.s[1][st], n, Sa, Sb);
         };
         // the observed chunks this tile of model spots can see (exact underflow skipping)
         const int nch = (ni + kChunk - 1) / kChunk;
@@ -749,7 +720,7 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
             const int g1 = a.mod_gbase[t] + (td.y + td.z - 1 - a.J2_off[t]) / kChunk;
             Cone M = load_cone(a.mod_cone, a.mod_ext, g0);
             if (g1 != g0) M = merge_cones(M, load_cone(a.mod_cone, a.mod_ext, g1), false);
-            const float K = -a.negKD2;
+            const float K = a.skipK;  // the smallest cost factor of any spot
             const int og = a.obs_gbase[t];
             n_list = build_chunk_list(S, nch, [&](int c) {
                 return min_scaled_cost(load_cone(a.obs_cone, a.obs_ext, og + c), M, K) <= kSkipLog2;
@@ -771,10 +742,10 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
         }
         float sa = lo(Sa) + hi(Sa), sb = lo(Sb) + hi(Sb);
         float Ga = valid ? (sa > kTinySum ? -(shift + lg2(sa))
-                                          : -col_exact(a, t, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, dz, K2))
+                                          : -col_exact(a, t, C.ncxa, C.ncya, C.ncza, C.nrxa, C.nrya, C.nrza, dz, C.ka))
                          : 0.0f;
         float Gb = vb ? (sb > kTinySum ? -(shift + lg2(sb))
-                                       : -col_exact(a, t, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, dz, K2))
+                                       : -col_exact(a, t, C.ncxb, C.ncyb, C.nczb, C.nrxb, C.nryb, C.nrzb, dz, C.kb))
                       : 0.0f;
         if (ub) {  // raised to lambda / (lambda + eps)
             Ga = ni > 0 ? a.tau_col * Ga : 0.0f;
@@ -866,7 +837,6 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
     uint32_t parity[2] = {0u, 0u};
     DustPtrs D = dust_ptrs(a.dust, a.T);
     const int n_tiles = a.ctrl[CTRL_N_ROW_TILES];
-    const f2 K2 = dup(a.negKD2);
     const Srcs src{{a.modX, a.modY, a.modZ, a.modW}, 4};
     float my_err = 0.0f;
     while (true) {
@@ -894,8 +864,8 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_row_kernel(SkArgs a) {
                 ulonglong2 Ym = *(const ulonglong2*)&S.s[1][st][k];
                 ulonglong2 Zm = *(const ulonglong2*)&S.s[2][st][k];
                 ulonglong2 Wm = *(const ulonglong2*)&S.s[3][st][k];
-                f2 va = pair_v2(pxa, pya, pza, Xm.x, Xm.y, Ym.x, Zm.x, Zm.y, Wm.x, K2, Ym.y);
-                f2 vv = pair_v2(pxb, pyb, pzb, Xm.x, Xm.y, Ym.x, Zm.x, Zm.y, Wm.x, K2, Ym.y);
+                f2 va = pair_v2(pxa, pya, pza, Xm.x, Xm.y, Ym.x, Zm.x, Zm.y, Wm.x, Wm.y, Ym.y);
+                f2 vv = pair_v2(pxb, pyb, pzb, Xm.x, Xm.y, Ym.x, Zm.x, Zm.y, Wm.x, Wm.y, Ym.y);
                 int j = jbase + 2 * (off + k);
                 A.add(lo(va), j, a.mod_perm);
                 A.add(hi(va), j + 1, a.mod_perm);  // padding slots have -3e38 and never win
@@ -958,7 +928,6 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_col_kernel(SkArgs a) {
     uint32_t parity[2] = {0u, 0u};
     DustPtrs D = dust_ptrs(a.dust, a.T);
     const int n_tiles = a.ctrl[CTRL_N_COL_TILES];
-    const f2 K2 = dup(a.negKD2);
     const Srcs src{{a.obsX, a.obsY, nullptr, nullptr}, 2};
     float my_err = 0.0f;
     while (true) {
@@ -979,7 +948,7 @@ __global__ void __launch_bounds__(kTPB) sk_harvest_col_kernel(SkArgs a) {
         C.A.S = pk(0.0f, 0.0f);
         C.B.S = pk(0.0f, 0.0f);
         bool ok = stream_tile(S, parity, src, i0, ni, [&](int st, int n, int) {
-            if (valid) col_chunk(C, S.s[0][st], S.s[1][st], n, K2);
+            if (valid) col_chunk(C, S.s[0][st], S.s[1][st], n);
         });
         if (!ok) {
             if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);

@@ -4,9 +4,11 @@
 // |I| |J|).
 //
 // Support: each model spot j keeps the rho observed spots of its angle block
-// with the smallest pair cost C_ij = D^2 |rhat_ij - r_j|^2 (ties to the lower
-// observed index); every other observed-model entry of the plan is 0, the
-// outlier column and the unmatched-model row stay dense.  The neighbour lists
+// with the smallest pair cost C_ij = D_j^2 |rhat_ij - r_j|^2 (D_j the cost
+// length of the spot's detector; ties to the lower observed index); every
+// other observed-model entry of the plan is 0, the outlier column and the
+// unmatched-model row stay dense.  The records hold
+// e2_ij = (D_j / D)^2 |rhat_ij - r_j|^2.  The neighbour lists
 // are built once per call from the model list's rays and centres, then
 // transposed into rows (CSR by observed spot, ascending model index).  The
 // updates are those of the dense passes restricted to the support, in base 2
@@ -104,8 +106,11 @@ __global__ void __launch_bounds__(kKnnThreads) sp_knn_kernel(SpArgs a) {
             }
             L[q] = make_int2(i, __float_as_int(v));
         }
+        const int det = a.s ? (int)a.s[j].w : -1;
+        const float kd = (det >= 0 && det < a.n_det) ? a.kdet[det] : 1.0f;
         int2* out = a.cent + (size_t)j * a.rho;
-        for (int k = 0; k < a.rho; ++k) out[k] = k < n ? L[k] : make_int2(-1, 0);
+        for (int k = 0; k < a.rho; ++k)
+            out[k] = k < n ? make_int2(L[k].x, __float_as_int(__int_as_float(L[k].y) * kd)) : make_int2(-1, 0);
         if (a.nbr_out)
             for (int k = 0; k < a.rho; ++k) a.nbr_out[(size_t)j * a.rho + k] = k < n ? L[k].x : -1;
     }

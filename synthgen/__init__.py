@@ -19,9 +19,34 @@ import numpy as np
 
 @dataclasses.dataclass(frozen=True)
 class Detector:
+    """Flat square detector: centre (mm), plane normal, half side (mm) and
+    cost length D (mm; 0 takes the geometry's D).  Its in-plane axes are
+    a1 = (y x n)/|y x n| (x when n is along y) and a2 = n x a1, and it holds
+    the plane points s with |(s - centre).a| < half for both axes."""
+
     centre: tuple
     normal: tuple
     half: float
+    D: float = 0.0
+
+    def axes(self):
+        n = np.asarray(self.normal, np.float64)
+        n = n / np.linalg.norm(n)
+        a1 = np.array([n[2], 0.0, -n[0]])
+        a1 = a1 / np.linalg.norm(a1) if np.linalg.norm(a1) > 1e-12 else np.array([1.0, 0.0, 0.0])
+        return a1, np.cross(n, a1)
+
+
+def tilted_geometry():
+    """Two detectors at the distances of the paper's CoNiGa tomography
+    (backscatter at 165 mm, transmission at 125 mm), the backscatter plane
+    tilted by 8 degrees about x and the transmission plane offset 10 mm along
+    x; each detector's cost length is its distance."""
+    a = math.radians(8.0)
+    return Geometry(D=165.0, detectors=(
+        Detector((10.0, 0.0, 125.0), (0.0, 0.0, 1.0), 128.0, 125.0),
+        Detector((0.0, 165.0 * math.sin(a), -165.0 * math.cos(a)), (0.0, -math.sin(a), math.cos(a)), 128.0, 165.0),
+    ))
 
 
 @dataclasses.dataclass(frozen=True)
@@ -206,19 +231,19 @@ def observe(geom: Geometry, cfg: Config, t_true, det_true, s_true, rng: np.rando
     m_t ~ U(0.5, 2).  Within an angle the spot order is a random permutation."""
     sigma = cfg.sigma_mm if sigma_mm is None else sigma_mm
     frac = cfg.outlier_frac if outlier_frac is None else outlier_frac
-    for d in geom.detectors:
-        if abs(d.normal[0]) > 0 or abs(d.normal[1]) > 0:
-            raise ValueError("observe() supports detectors normal to the beam axis only")
     t_true = np.asarray(t_true, dtype=np.int64)
     det_true = np.asarray(det_true, dtype=np.int64)
     s_true = np.asarray(s_true, dtype=np.float64).reshape(-1, 3)
     n_true = len(t_true)
     z = rng.standard_normal((n_true, 2))
-    p = s_true.copy()
-    p[:, 0] += sigma * z[:, 0]
-    p[:, 1] += sigma * z[:, 1]
+    ax = [d.axes() for d in geom.detectors]
+    A1 = np.array([ax[k][0] for k in det_true]).reshape(-1, 3)
+    A2 = np.array([ax[k][1] for k in det_true]).reshape(-1, 3)
+    ctr = np.array([geom.detectors[k].centre for k in det_true], np.float64).reshape(-1, 3)
+    p = s_true + sigma * (z[:, :1] * A1 + z[:, 1:] * A2)
     half = np.array([geom.detectors[k].half for k in det_true]) if n_true else np.zeros(0)
-    keep = (np.abs(p[:, 0]) < half) & (np.abs(p[:, 1]) < half) if n_true else np.zeros(0, bool)
+    keep = ((np.abs(np.sum((p - ctr) * A1, 1)) < half) & (np.abs(np.sum((p - ctr) * A2, 1)) < half)
+            if n_true else np.zeros(0, bool))
     p, t_in, d_in = p[keep], t_true[keep], det_true[keep]
     truth = np.nonzero(keep)[0]
     T = cfg.T
@@ -236,9 +261,9 @@ def observe(geom: Geometry, cfg: Config, t_true, det_true, s_true, rng: np.rando
     p_out = np.zeros((n_out, 3))
     for k, det in enumerate(geom.detectors):
         sel = d_out == k
-        p_out[sel, 0] = det.centre[0] + det.half * uv[sel, 0]
-        p_out[sel, 1] = det.centre[1] + det.half * uv[sel, 1]
-        p_out[sel, 2] = det.centre[2]
+        a1, a2 = ax[k]
+        p_out[sel] = (np.asarray(det.centre, np.float64) + det.half * uv[sel, :1] * a1 +
+                      det.half * uv[sel, 1:] * a2)
     P = np.concatenate([p, p_out])
     Tt = np.concatenate([t_in, t_out]).astype(np.int64)
     Dd = np.concatenate([d_in, d_out]).astype(np.int64)

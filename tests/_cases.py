@@ -27,6 +27,16 @@ class Case:
     fw: dict                   # model list (float32-rounded vectors)
     obs: sg.Observed           # float32-rounded positions
     c_out: float
+    geom: sg.Geometry = GEOM
+
+
+def geom32(geom):
+    """The geometry with every number rounded to float32 (what the CUDA path
+    receives), so that both sides see the same detectors."""
+    r = lambda v: float(np.float32(v))
+    dets = tuple(sg.Detector(tuple(r(v) for v in d.centre), tuple(r(v) for v in d.normal), r(d.half), r(d.D))
+                 for d in geom.detectors)
+    return sg.Geometry(tuple(r(v) for v in geom.beam), r(geom.lam_min), r(geom.lam_max), r(geom.D), dets)
 
 
 def planes32(cfg):
@@ -34,7 +44,7 @@ def planes32(cfg):
     return oracle.Planes(f32(P.w), f32(P.d0), P.nharm, P.hkl0)
 
 
-def make_case(cfg, seed=None, n_grains=None, T=None, outlier_frac=None, sigma=None):
+def make_case(cfg, seed=None, n_grains=None, T=None, outlier_frac=None, sigma=None, geom=GEOM):
     if n_grains is not None or T is not None:
         cfg = dataclasses.replace(cfg, n_grains=n_grains or cfg.n_grains, T=T or cfg.T)
     rng = np.random.default_rng(cfg.seed if seed is None else seed)
@@ -42,13 +52,13 @@ def make_case(cfg, seed=None, n_grains=None, T=None, outlier_frac=None, sigma=No
     R, x = f32(R), f32(x)
     om = f32(sg.omegas(cfg))
     P = planes32(cfg)
-    fw = oracle.forward(GEOM, P, R, x, om)
+    fw = oracle.forward(geom, P, R, x, om)
     for k in ("ray", "spot", "center"):
         fw[k] = f32(fw[k])
-    obs = sg.observe(GEOM, cfg, fw["t"], fw["det"], fw["spot"], rng, sigma_mm=sigma,
+    obs = sg.observe(geom, cfg, fw["t"], fw["det"], fw["spot"], rng, sigma_mm=sigma,
                      outlier_frac=outlier_frac)
     obs.p = f32(obs.p)
-    return Case(cfg, P, R, x, om, fw, obs, float(np.float32(oracle.c_out_for(cfg.sigma_mm, GEOM.D))))
+    return Case(cfg, P, R, x, om, fw, obs, float(np.float32(oracle.c_out_for(cfg.sigma_mm, geom.D))), geom)
 
 
 def to_device(case, dev):

@@ -955,3 +955,154 @@ def test_sparse_sinkhorn_limits(tiny):
     np.testing.assert_allclose(gs, gd_, atol=1e-9)
     fs, gs, _, _ = oracle.sinkhorn_sparse(*args, rho=1)
     assert np.abs(fs - fd_).max() > 1e-6  # a one-neighbour support is a different plan
+
+
+# ------------------------------------- tilted detectors, per-detector lengths
+
+TILT = sg.tilted_geometry()
+
+
+@pytest.fixture(scope="module")
+def tilted():
+    planes = oracle.reflections(TINY.a, TINY.hmax, TINY.centering)
+    rng = np.random.default_rng(21)
+    R, x = sg.random_grains(TINY, rng)
+    om = sg.omegas(TINY)
+    fw = oracle.forward(TILT, planes, R, x, om)
+    obs = sg.observe(TILT, TINY, fw["t"], fw["det"], fw["spot"], rng)
+    return dict(planes=planes, R=R, x=x, om=om, fw=fw, obs=obs)
+
+
+def _plane_coords(det, s):
+    a1, a2 = det.axes()
+    d = np.asarray(s, np.float64) - np.asarray(det.centre)
+    n = np.asarray(det.normal, np.float64) / np.linalg.norm(det.normal)
+    return d @ a1, d @ a2, d @ n
+
+
+def test_tilted_forward_spots_lie_on_their_detector(tilted):
+    """Appendix "Experimental details": two detectors at different distances,
+    here one offset and one tilted.  Every visible spot lies on its detector's
+    plane, inside its square (in-plane axes), on the ray from the grain centre
+    at positive parameter, and no detector closer along the ray holds it;
+    both detectors receive spots; and every ray the forward model rejects
+    while in band misses both squares (brute force over all (t, n, m))."""
+    fw, P, R, x, om = tilted["fw"], tilted["planes"], tilted["R"], tilted["x"], tilted["om"]
+    counts = np.bincount(fw["det"], minlength=2)
+    assert counts.min() > 10, counts
+    for j in range(fw["J_off"][-1]):
+        det = TILT.detectors[fw["det"][j]]
+        u, v, w = _plane_coords(det, fw["spot"][j])
+        assert abs(w) < 1e-9 and abs(u) < det.half and abs(v) < det.half
+        d = fw["spot"][j] - fw["center"][j]
+        r = fw["ray"][j, :3]
+        assert np.linalg.norm(np.cross(d, r)) < 1e-9 and d @ r > 0
+    full = oracle.forward(TILT, P, R, x, om, with_all=True)
+    e = np.array(TILT.beam)
+    for t in range(len(om)):
+        Gm = oracle.gamma(om[t])
+        for n in range(len(R)):
+            c = Gm @ x[n]
+            for m in range(len(P.w)):
+                g = Gm @ R[n] @ P.w[m]
+                r = e - 2 * (e @ g) * g
+                hits = []
+                for k, det in enumerate(TILT.detectors):
+                    nv = np.asarray(det.normal) / np.linalg.norm(det.normal)
+                    den = nv @ r
+                    if den == 0:
+                        continue
+                    tau = nv @ (np.asarray(det.centre) - c) / den
+                    if tau <= 0:
+                        continue
+                    u, v, _ = _plane_coords(det, c + tau * r)
+                    if abs(u) < det.half and abs(v) < det.half:
+                        hits.append(tau)
+                lam0 = 2 * P.d0[m] * abs(e @ g)
+                in_band = any(TILT.lam_min <= lam0 / k <= TILT.lam_max for k in range(1, P.nharm[m] + 1))
+                want = bool(hits) and in_band
+                if full["margin_all"][t, n, m] > 1e-9:
+                    assert bool(full["vis_all"][t, n, m]) == want, (t, n, m)
+
+
+def test_cost_length_is_each_detectors_distance():
+    """The pair cost is the squared displacement on the detector the model ray
+    hits: for a ray along a detector's normal (to the foot of the
+    perpendicular) and an observed spot displaced by delta in the plane, the
+    rays differ by the angle atan(delta / D_k), so the cost with that
+    detector's length is 4 D_k^2 sin^2(atan(delta / D_k) / 2) = delta^2 (1 -
+    O(delta^2 / D_k^2)); with the geometry's single D it would be about
+    (D / D_k)^2 delta^2."""
+    Ls = oracle.cost_lengths(TILT, [0, 1, -1])
+    np.testing.assert_allclose(Ls, [125.0, 165.0, TILT.D])
+    for k, det in enumerate(TILT.detectors):
+        nv = np.asarray(det.normal, np.float64) / np.linalg.norm(det.normal)
+        foot = nv * (nv @ np.asarray(det.centre))
+        r = foot / np.linalg.norm(foot)
+        a1, a2 = det.axes()
+        for delta, ax in ((0.3, a1), (0.5, a2)):
+            p = foot + delta * ax
+            C = oracle.pair_cost(p, np.zeros(3), r, Ls[k])
+            exact = 4 * Ls[k] ** 2 * math.sin(0.5 * math.atan(delta / Ls[k])) ** 2
+            assert C == pytest.approx(exact, rel=1e-10), (k, C, exact)
+            assert C == pytest.approx(delta ** 2, rel=1e-4)
+            assert abs(np.linalg.norm(foot) - Ls[k]) < 1e-9
+
+
+def test_tilted_gradient_and_mstep_fixed_point(tilted):
+    """With per-detector lengths the adjoint gradient of sum Q_ij D_j^2 |rhat -
+    r|^2 equals central differences of the objective (Q held), and the plain
+    M-step (Newton on x, MM on R) run to convergence with Q held stops where
+    that gradient vanishes: its weights Q_ij (D_j / D)^2 are the objective's."""
+    P, fw, obs, om = tilted["planes"], tilted["fw"], tilted["obs"], tilted["om"]
+    c, r = fw["center"], fw["ray"][:, :3]
+    Dj = oracle.cost_lengths(TILT, fw["det"])
+    assert len(set(Dj.tolist())) == 2
+    f, g, *_ = oracle.sinkhorn(Dj, obs.p, obs.I_off, fw["J_off"], c, r, 2.0, 2.25, 0, 0.4, 30)
+    rng = np.random.default_rng(9)
+    R1 = np.array([_rotvec(rng.normal(size=3) * 0.004) @ a for a in tilted["R"]])
+    x1 = tilted["x"] + rng.normal(size=tilted["x"].shape) * 0.1
+    args = (TILT, P, om, obs.p, obs.I_off, fw["J_off"], fw["grain"], fw["plane"], c, r, f, g, 2.0)
+    G, H, val = oracle.grain_gn(*args, R1, x1, det=fw["det"])
+    np.testing.assert_allclose(val, oracle.grain_objective(*args, R1, x1, det=fw["det"]), rtol=1e-12)
+    h = 1e-6
+    FD = np.zeros_like(G)
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        Rp = np.array([_rotvec(e[:3]) @ a for a in R1])
+        Rm = np.array([_rotvec(-e[:3]) @ a for a in R1])
+        FD[:, k] = (oracle.grain_objective(*args, Rp, x1 + e[3:], det=fw["det"]) -
+                    oracle.grain_objective(*args, Rm, x1 - e[3:], det=fw["det"])) / (2 * h)
+    assert np.abs(G - FD).max() <= 1e-6 * np.abs(G).max()
+    # the M-step's fixed point with Q held at the E-step plan
+    Rk, xk = tilted["R"].copy(), tilted["x"].copy()
+    G0, *_ = oracle.grain_gn(*args, Rk, xk, det=fw["det"])
+    for _ in range(40):
+        Rk, xk, _ = oracle.mstep(TILT, P, om, obs.p, obs.I_off, fw["J_off"], fw["grain"], fw["plane"], c, r,
+                                 f, g, 2.0, Rk, xk, n_newton=8, n_mm=20, tol_x=1e-14, tol_R=1e-15,
+                                 det=fw["det"])
+    # MM maximises sum Q D_j^2 rhat(x).r(R) over R: the rotation part of the
+    # gradient vanishes at (Rk, xk); Newton maximises it over x with the E-step
+    # rays, i.e. the x part vanishes at (R_E, xk) where the rays are r(R_E)
+    Gk, *_ = oracle.grain_gn(*args, Rk, xk, det=fw["det"])
+    Gx, *_ = oracle.grain_gn(*args, tilted["R"], xk, det=fw["det"])
+    assert np.abs(Gk[:, :3]).max() <= 1e-7 * np.abs(G0[:, :3]).max(), (Gk[:, :3], G0[:, :3])
+    assert np.abs(Gx[:, 3:]).max() <= 1e-7 * np.abs(G0[:, 3:]).max(), (Gx[:, 3:], G0[:, 3:])
+    # without the (D_j / D)^2 weights the fixed point is elsewhere
+    Ru, xu = tilted["R"].copy(), tilted["x"].copy()
+    for _ in range(40):
+        Ru, xu, _ = oracle.mstep(TILT, P, om, obs.p, obs.I_off, fw["J_off"], fw["grain"], fw["plane"], c, r,
+                                 f, g, 2.0, Ru, xu, n_newton=8, n_mm=20, tol_x=1e-14, tol_R=1e-15)
+    Gu, *_ = oracle.grain_gn(*args, Ru, xu, det=fw["det"])
+    assert np.abs(Gu[:, :3]).max() > 1e3 * np.abs(Gk[:, :3]).max()
+
+
+def test_observe_on_tilted_detectors(tilted):
+    """The detected spots of the tilted geometry lie on their detector plane
+    and inside its square; the noise is in the plane."""
+    obs = tilted["obs"]
+    for i in range(len(obs.p)):
+        det = TILT.detectors[obs.det[i]]
+        u, v, w = _plane_coords(det, obs.p[i])
+        assert abs(w) < 1e-9 and abs(u) < det.half and abs(v) < det.half
