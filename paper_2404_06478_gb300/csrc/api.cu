@@ -974,6 +974,7 @@ extern "C" int laue_single_fit(laue_handle* h, const LaueGeometry* geom, const L
     a.scratch = (float*)(ws + L.sfs);
     a.cap = kSfCap;
     a.icap = kSfIcap;
+    a.ncap = (int)sf_near_cap(obs->n);
     a.ctrl = (int*)(ws + L.ctrl);
     a.queue = a.ctrl + CTRL_SF_NEXT;
     int ctas = h->sm_count * kSfCtasPerSm;
@@ -999,6 +1000,7 @@ static SfArgs fill_sf(laue_handle* h, const LaueGeometry* geom, const LaueLattic
     a.scratch = (float*)(ws + L.sfs);
     a.cap = kSfCap;
     a.icap = kSfIcap;
+    a.ncap = (int)sf_near_cap(obs->n);
     a.ctrl = (int*)(ws + L.ctrl);
     a.queue = a.ctrl + CTRL_SF_NEXT;
     return a;

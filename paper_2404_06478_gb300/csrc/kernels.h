@@ -220,9 +220,6 @@ cudaError_t mstep_adjoint_run(const MsArgs& m, const SkLaunch& l, int n_steps, c
 
 // ------------------------------------------------------- single-grain fits
 constexpr int kSfMaxT = 1024;       // angles a fit supports
-constexpr int kSfCtasPerSm = 4;
-constexpr int kSfCap = 2048;        // listed spots per start
-constexpr int kSfIcap = 4096;       // cached row normalisers per angle block
 
 struct SfArgs {
     GeomDev G;
@@ -246,6 +243,7 @@ struct SfArgs {
     int recut;     // re-list the visible spots at every step
     float* scratch;
     int cap, icap;
+    int ncap;      // near-row list capacity per CTA (sf_near_cap of the workspace's n_obs)
     int* queue;  // 2 ints: start queue head, completion ticket
     int* ctrl;
 };

@@ -30,32 +30,36 @@ constexpr int kSfThreads = 128;
 constexpr float kSfSkip = -40.0f;
 
 struct SfScratch {
+    float4* rk;  // cap: {-r_j, K_j} E-step ray and cost factor K_j = -D_j^2 log2(e) / eps
     int* tm;     // cap: (t << 16) | m of the listed spots
-    float* rE;   // cap x 3 E-step rays
-    float* cE;   // cap x 3 E-step centres
+    float* cE;   // cap x 3 E-step centres (one per angle: every listed spot is the grain's)
     float* v;    // cap x 3 MM sums / filter column masses
     float* kd;   // cap: (D_j / D)^2, the cost length of the spot's detector relative to D
     float* lse;  // icap row normalisers of one angle block (log2)
+    int* ni;     // near rows of the current E-step (ncap): observed index
+    float* nl;   // and row normaliser (log2)
 };
 
 __device__ __forceinline__ SfScratch sf_slice(const SfArgs& a, int cta) {
     SfScratch s;
-    size_t per = (size_t)a.cap * kSfSpotFloats + a.icap;
-    float* base = a.scratch + per * cta;
-    s.tm = (int*)base;
-    s.rE = base + a.cap;
+    size_t per = (size_t)a.cap * kSfSpotFloats + a.icap + 2 * (size_t)a.ncap;
+    float* base = a.scratch + per * cta;  // 16-byte aligned: per is a multiple of 4 floats
+    s.rk = (float4*)base;
     s.cE = base + 4 * a.cap;
     s.v = base + 7 * a.cap;
-    s.kd = base + 10 * a.cap;
-    s.lse = base + 11 * a.cap;
+    s.tm = (int*)(base + 10 * a.cap);
+    s.kd = base + 11 * a.cap;
+    s.lse = base + 12 * a.cap;
+    s.ni = (int*)(s.lse + a.icap);
+    s.nl = s.lse + a.icap + a.ncap;
     return s;
 }
 
-// ray / centre of plane m at angle t for pose (R, x)
-__device__ __forceinline__ void sf_ray(const SfArgs& a, const float* R, const float* x, int t, int m, float* r,
+// ray / centre of plane m at angle t for pose (R, x); cs[t] = {cos, sin} of omega_t
+__device__ __forceinline__ void sf_ray(const SfArgs& a, const float2* cs, const float* R, const float* x, int t, int m,
+                                       float* r,
                                        float* c, float* lam0, int* nh) {
-    float sg, cg;
-    sincosf(a.omega[t], &sg, &cg);
+    const float cg = cs[t].x, sg = cs[t].y;
     float4 wd = a.w_d0[m];
     float v0 = R[0] * wd.x + R[1] * wd.y + R[2] * wd.z;
     float v1 = R[3] * wd.x + R[4] * wd.y + R[5] * wd.z;
@@ -91,10 +95,25 @@ __device__ __forceinline__ int sf_visible(const GeomDev& G, const float* r, cons
 struct SfShared {
     float R[9], x[3];
     int n_spots, overflow, stop, t_off[kSfMaxT + 1];
+    // near rows of the E-step per angle: list entries [near_off[t], near_end[t]),
+    // near_off[t] = -1 when angle t did not fit in the list
+    int n_near, near_off[kSfMaxT], near_end[kSfMaxT];
     float red[kSfThreads * 9];
     int start;
     int last;
+    const float2* cs;  // {cos, sin} of each rotation angle (dynamic shared memory)
 };
+
+// Fills the angle table cs (T entries of dynamic shared memory) and points S.cs at it.
+__device__ __forceinline__ void sf_angles(const SfArgs& a, SfShared& S, float2* cs) {
+    for (int t = threadIdx.x; t < a.T; t += blockDim.x) {
+        float sg, cg;
+        sincosf(a.omega[t], &sg, &cg);
+        cs[t] = make_float2(cg, sg);
+    }
+    if (threadIdx.x == 0) S.cs = cs;
+    __syncthreads();
+}
 
 // Lists the spots visible at pose (R, x) sorted by (t, m); t_off per angle.
 __device__ void sf_cut(const SfArgs& a, SfShared& S, const SfScratch& Z) {
@@ -114,7 +133,7 @@ __device__ void sf_cut(const SfArgs& a, SfShared& S, const SfScratch& Z) {
             m = (int)(id % a.M);
             float r[3], c[3], lam0;
             int nh;
-            sf_ray(a, S.R, S.x, t, m, r, c, &lam0, &nh);
+            sf_ray(a, S.cs, S.R, S.x, t, m, r, c, &lam0, &nh);
             det = sf_visible(a.G, r, c, lam0, nh);
             vis = det >= 0;
         }
@@ -152,34 +171,129 @@ __device__ void sf_cut(const SfArgs& a, SfShared& S, const SfScratch& Z) {
     __syncthreads();
 }
 
-// E-step rays/centres of the listed spots at the current pose.
-__device__ void sf_refresh(const SfArgs& a, SfShared& S, const SfScratch& Z) {
+// E-step rays/centres of the listed spots at the current pose, with the cost
+// factors K_j = negK (D_j / D)^2 of the E-step temperature.
+__device__ void sf_refresh(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK) {
     for (int j = threadIdx.x; j < S.n_spots; j += blockDim.x) {
         int t = Z.tm[j] >> 16, m = Z.tm[j] & 0xffff;
-        sf_ray(a, S.R, S.x, t, m, Z.rE + 3 * j, Z.cE + 3 * j, nullptr, nullptr);
+        float r[3];
+        sf_ray(a, S.cs, S.R, S.x, t, m, r, Z.cE + 3 * j, nullptr, nullptr);
+        Z.rk[j] = make_float4(-r[0], -r[1], -r[2], negK * Z.kd[j]);
     }
     __syncthreads();
 }
 
-__device__ __forceinline__ float sf_e2(const float4& p, const float* c, const float* r) {
-    float d0 = p.x - c[0], d1 = p.y - c[1], d2 = p.z - c[2];
-    float s = rsq(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
-    float e0 = fmaf(d0, s, -r[0]), e1 = fmaf(d1, s, -r[1]), e2 = fmaf(d2, s, -r[2]);
-    return fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+// Direction of an observed spot seen from the grain centre c of its angle:
+// d = p - c and s = 1/|d|, computed once per row (every listed spot of the
+// angle shares c).
+struct SfRowG {
+    float d0, d1, d2, s;
+};
+
+__device__ __forceinline__ SfRowG sf_rowg(const float4& p, const float* c) {
+    SfRowG g;
+    g.d0 = p.x - c[0];
+    g.d1 = p.y - c[1];
+    g.d2 = p.z - c[2];
+    g.s = rsq(fmaf(g.d0, g.d0, fmaf(g.d1, g.d1, g.d2 * g.d2)));
+    return g;
 }
 
-// Row normaliser (log2) of observed spot p at angle t over the listed spots;
-// npair counts the pair evaluations of the calling thread.
+// Pair exponent K_j |rhat - r_j|^2 (<= 0) from the row's direction and the
+// spot's {-r_j, K_j}.
+__device__ __forceinline__ float sf_pair_v(const SfRowG& g, const float4& rk) {
+    float e0 = fmaf(g.d0, g.s, rk.x), e1 = fmaf(g.d1, g.s, rk.y), e2 = fmaf(g.d2, g.s, rk.z);
+    return rk.w * fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+}
+
+// Row normaliser l (log2) of observed spot p at angle t over the listed spots
+// and the outlier column, and the largest pair exponent vmax; npair counts the
+// pair evaluations of the calling thread.  Every pair exponent
+// v = negK kd e2 is <= 0, so while the outlier exponent dust is >= -100 the
+// sum is taken relative to it with no running maximum (no term exceeds 2^100,
+// the outlier term 1 never underflows); below that, with the running maximum.
 __device__ __forceinline__ float sf_row_lse(const SfArgs& a, const SfShared& S, const SfScratch& Z, int t,
-                                            const float4& p, float negK, float dust, unsigned long long& npair) {
+                                            const float4& p, float dust, unsigned long long& npair, float& vmax) {
+    const int j0 = S.t_off[t], j1 = S.t_off[t + 1];
+    npair += (unsigned)(j1 - j0);
+    vmax = kNegHuge;
+    if (j1 == j0) return dust;
+    const SfRowG g = sf_rowg(p, Z.cE + 3 * j0);
+    if (dust >= -100.0f) {
+        float s = 1.0f;
+#pragma unroll 4
+        for (int j = j0; j < j1; ++j) {
+            float v = sf_pair_v(g, Z.rk[j]);
+            vmax = fmaxf(vmax, v);
+            s += ex2(v - dust);
+        }
+        return dust + lg2(s);
+    }
     Lse2 L;
     L.init(dust);
-    npair += (unsigned)(S.t_off[t + 1] - S.t_off[t]);
-    for (int j = S.t_off[t]; j < S.t_off[t + 1]; ++j) {
-        float v = negK * Z.kd[j] * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j);
+    for (int j = j0; j < j1; ++j) {
+        float v = sf_pair_v(g, Z.rk[j]);
+        vmax = fmaxf(vmax, v);
         L.merge(v, 1.0f);
     }
     return L.value();
+}
+
+// Row normalisers of this EM step's E-step and the rows that carry plan mass.
+// A row is near when some pair keeps Q_ij >= 2^kSfSkip (v_ij - l_i >=
+// kSfSkip); every other row has all its plan entries below the cut-off that
+// the Newton and MM sums skip, so only near rows enter them.  The near rows of
+// each angle are listed with l (ascending row index) while the list has room;
+// an angle that does not fit is marked near_off = -1 and its rows are scanned
+// in full by the passes.  The plan stays the E-step's for the whole M-step,
+// so the list serves every Newton and MM pass of the step.
+__device__ void sf_near(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK, float dust,
+                        unsigned long long& npair) {
+    __shared__ int wcnt[kSfThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) S.n_near = 0;
+    __syncthreads();
+    for (int t = 0; t < a.T; ++t) {
+        const int base = S.n_near;
+        int cnt = 0;
+        if (S.t_off[t + 1] > S.t_off[t]) {
+            for (int i0 = a.I_off[t]; i0 < a.I_off[t + 1]; i0 += kSfThreads) {
+                const int i = i0 + threadIdx.x;
+                bool near = false;
+                float l = 0.0f;
+                if (i < a.I_off[t + 1]) {
+                    float vmax;
+                    l = sf_row_lse(a, S, Z, t, a.p[i], dust, npair, vmax);
+                    near = vmax - l >= kSfSkip;
+                }
+                const unsigned ball = __ballot_sync(0xffffffffu, near);
+                if (lane == 0) wcnt[w] = __popc(ball);
+                __syncthreads();
+                int before = 0, total = 0;
+                for (int k = 0; k < kSfThreads / 32; ++k) {
+                    if (k < w) before += wcnt[k];
+                    total += wcnt[k];
+                }
+                const int pos = base + cnt + before + __popc(ball & ((1u << lane) - 1u));
+                if (near && pos < a.ncap) {
+                    Z.ni[pos] = i;
+                    Z.nl[pos] = l;
+                }
+                cnt += total;
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) {
+            if (base + cnt <= a.ncap) {
+                S.near_off[t] = base;
+                S.near_end[t] = base + cnt;
+                S.n_near = base + cnt;
+            } else {
+                S.near_off[t] = -1;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 __device__ float sf_block_sum9(SfShared& S, float* v) {
@@ -193,7 +307,39 @@ __device__ float sf_block_sum9(SfShared& S, float* v) {
     return 0.0f;
 }
 
-// One Newton step on x with the plan of the E-step costs.
+// Newton sums of observed spot p with row normaliser l against the listed
+// spots [j0, j1) of its angle (centre c of the current position, Gamma_t of
+// cos/sin cg, sg), accumulated in the sample frame of x: with the directions
+// rotated back, hx = Gamma^T rhat and rx = Gamma^T r, the gradient and Hessian
+// of Q rhat.r w.r.t. x are the lab-frame expressions in hx, rx.
+__device__ __forceinline__ void sf_newton_row(const SfScratch& Z, int j0, int j1, const float4& p, float l,
+                                              const float* c, float cg, float sg, float* acc) {
+    const SfRowG g = sf_rowg(p, Z.cE + 3 * j0);  // E-step direction
+    // direction at the current position
+    const float d0 = p.x - c[0], d1 = p.y - c[1], d2 = p.z - c[2];
+    const float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+    const float hl[3] = {d0 * is, d1 * is, d2 * is};
+    float h[3];
+    gamT_apply(cg, sg, hl, h);
+    for (int j = j0; j < j1; ++j) {
+        const float4 rk = Z.rk[j];
+        float v = sf_pair_v(g, rk) - l;
+        if (v < kSfSkip) continue;
+        float Q = ex2(v) * Z.kd[j];  // M-step weight Q_ij (D_j / D)^2
+        const float rl[3] = {-rk.x, -rk.y, -rk.z};
+        float r[3];
+        gamT_apply(cg, sg, rl, r);
+        float rr = h[0] * r[0] + h[1] * r[1] + h[2] * r[2];
+        float qs = Q * is, q2 = qs * is;
+        for (int k = 0; k < 3; ++k) acc[k] -= qs * (r[k] - rr * h[k]);
+        int kk = 3;
+        for (int u = 0; u < 3; ++u)
+            for (int w = u; w < 3; ++w)
+                acc[kk++] += q2 * (3.0f * rr * h[u] * h[w] - h[u] * r[w] - r[u] * h[w] - (u == w ? rr : 0.0f));
+    }
+}
+
+// One Newton step on x with the plan of the E-step costs (near rows of sf_near).
 __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK, float dust,
                           unsigned long long& npair) {
     float acc[9];
@@ -201,36 +347,23 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
     for (int t = 0; t < a.T; ++t) {
         int j0 = S.t_off[t], j1 = S.t_off[t + 1];
         if (j0 == j1) continue;
-        float sg, cg;
-        sincosf(a.omega[t], &sg, &cg);
+        const float cg = S.cs[t].x, sg = S.cs[t].y;
         float c[3] = {cg * S.x[0] + sg * S.x[2], S.x[1], -sg * S.x[0] + cg * S.x[2]};
-        float gc[3] = {0, 0, 0}, hc[6] = {0, 0, 0, 0, 0, 0};
-        for (int i = a.I_off[t] + threadIdx.x; i < a.I_off[t + 1]; i += blockDim.x) {
-            float4 p = a.p[i];
-            float l = sf_row_lse(a, S, Z, t, p, negK, dust, npair);
-            npair += (unsigned)(j1 - j0);
-            for (int j = j0; j < j1; ++j) {
-                float v = negK * Z.kd[j] * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j) - l;
-                if (v < kSfSkip) continue;
-                float Q = ex2(v) * Z.kd[j];  // M-step weight Q_ij (D_j / D)^2
-                const float* r = Z.rE + 3 * j;
-                float d0 = p.x - c[0], d1 = p.y - c[1], d2 = p.z - c[2];
-                float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
-                float h[3] = {d0 * is, d1 * is, d2 * is};
-                float rr = h[0] * r[0] + h[1] * r[1] + h[2] * r[2];
-                float qs = Q * is, q2 = qs * is;
-                for (int k = 0; k < 3; ++k) gc[k] -= qs * (r[k] - rr * h[k]);
-                int kk = 0;
-                for (int u = 0; u < 3; ++u)
-                    for (int w = u; w < 3; ++w)
-                        hc[kk++] += q2 * (3.0f * rr * h[u] * h[w] - h[u] * r[w] - r[u] * h[w] - (u == w ? rr : 0.0f));
+        const int off = S.near_off[t];
+        if (off >= 0) {
+            for (int k = off + threadIdx.x; k < S.near_end[t]; k += blockDim.x) {
+                npair += (unsigned)(j1 - j0);
+                sf_newton_row(Z, j0, j1, a.p[Z.ni[k]], Z.nl[k], c, cg, sg, acc);
+            }
+        } else {
+            for (int i = a.I_off[t] + threadIdx.x; i < a.I_off[t + 1]; i += blockDim.x) {
+                float4 p = a.p[i];
+                float vmax;
+                float l = sf_row_lse(a, S, Z, t, p, dust, npair, vmax);
+                npair += (unsigned)(j1 - j0);
+                sf_newton_row(Z, j0, j1, p, l, c, cg, sg, acc);
             }
         }
-        float gx[3], hx[6];
-        gamT_apply(cg, sg, gc, gx);
-        sym_gamT_gam(cg, sg, hc, hx);
-        for (int k = 0; k < 3; ++k) acc[k] += gx[k];
-        for (int k = 0; k < 6; ++k) acc[3 + k] += hx[k];
     }
     sf_block_sum9(S, acc);
     if (threadIdx.x == 0) {
@@ -247,40 +380,72 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
     __syncthreads();
 }
 
+// Column sums of listed spot j over the rows given by row(k), k = lane, lane +
+// 32, ... < n: Q_ij rhat_ij, or with massonly the column mass.
+template <class Row>
+__device__ __forceinline__ void sf_column_sums(const SfScratch& Z, int j, int n, bool massonly, const float* c,
+                                               Row row, float& s0, float& s1, float& s2,
+                                               unsigned long long& npair) {
+    const int lane = threadIdx.x & 31;
+    const float4 rk = Z.rk[j];
+    for (int k = lane; k < n; k += 32) {
+        float4 p;
+        float l;
+        row(k, p, l);
+        ++npair;
+        float v = sf_pair_v(sf_rowg(p, Z.cE + 3 * j), rk) - l;
+        if (v < kSfSkip) continue;
+        float Q = ex2(v);
+        if (massonly) {
+            s0 += Q;
+            continue;
+        }
+        float d0 = p.x - c[0], d1 = p.y - c[1], d2 = p.z - c[2];
+        float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+        s0 += Q * d0 * is;
+        s1 += Q * d1 * is;
+        s2 += Q * d2 * is;
+    }
+}
+
 // v_j = sum_i Q_ij rhat_ij (rhat at the current x), or with massonly the
-// column mass q_j, for every listed spot; one warp per spot, fixed order.
+// column mass q_j, for every listed spot; one warp per spot, fixed order
+// (the near rows of sf_near, or every row of an angle not in that list).
 __device__ void sf_columns(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK, float dust, bool massonly,
                            unsigned long long& npair) {
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int t = 0; t < a.T; ++t) {
         int j0 = S.t_off[t], j1 = S.t_off[t + 1];
         if (j0 == j1) continue;
+        const int off = S.near_off[t];
         int i0 = a.I_off[t], ni = a.I_off[t + 1] - i0;
         int nl = min(ni, a.icap);
-        for (int k = threadIdx.x; k < nl; k += blockDim.x)
-            Z.lse[k] = sf_row_lse(a, S, Z, t, a.p[i0 + k], negK, dust, npair);
-        __syncthreads();
-        float sg, cg;
-        sincosf(a.omega[t], &sg, &cg);
+        if (off < 0) {
+            for (int k = threadIdx.x; k < nl; k += blockDim.x) {
+                float vmax;
+                Z.lse[k] = sf_row_lse(a, S, Z, t, a.p[i0 + k], dust, npair, vmax);
+            }
+            __syncthreads();
+        }
+        const float cg = S.cs[t].x, sg = S.cs[t].y;
         float c[3] = {cg * S.x[0] + sg * S.x[2], S.x[1], -sg * S.x[0] + cg * S.x[2]};
         for (int j = j0 + warp; j < j1; j += blockDim.x / 32) {
             float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-            for (int k = lane; k < ni; k += 32) {
-                float4 p = a.p[i0 + k];
-                float l = k < nl ? Z.lse[k] : sf_row_lse(a, S, Z, t, p, negK, dust, npair);
-                ++npair;
-                float v = negK * Z.kd[j] * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j) - l;
-                if (v < kSfSkip) continue;
-                float Q = ex2(v);
-                if (massonly) {
-                    s0 += Q;
-                    continue;
-                }
-                float d0 = p.x - c[0], d1 = p.y - c[1], d2 = p.z - c[2];
-                float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
-                s0 += Q * d0 * is;
-                s1 += Q * d1 * is;
-                s2 += Q * d2 * is;
+            if (off >= 0) {
+                sf_column_sums(Z, j, S.near_end[t] - off, massonly, c,
+                               [&](int k, float4& p, float& l) {
+                                   p = a.p[Z.ni[off + k]];
+                                   l = Z.nl[off + k];
+                               },
+                               s0, s1, s2, npair);
+            } else {
+                sf_column_sums(Z, j, ni, massonly, c,
+                               [&](int k, float4& p, float& l) {
+                                   p = a.p[i0 + k];
+                                   float vmax;
+                                   l = k < nl ? Z.lse[k] : sf_row_lse(a, S, Z, t, p, dust, npair, vmax);
+                               },
+                               s0, s1, s2, npair);
             }
             for (int o = 16; o > 0; o >>= 1) {
                 s0 += __shfl_xor_sync(0xffffffffu, s0, o);
@@ -305,8 +470,7 @@ __device__ void sf_mm(const SfArgs& a, SfShared& S, const SfScratch& Z, float* M
     for (int t = 0; t < a.T; ++t) {
         int j0 = S.t_off[t], j1 = S.t_off[t + 1];
         if (j0 == j1) continue;
-        float sg, cg;
-        sincosf(a.omega[t], &sg, &cg);
+        const float cg = S.cs[t].x, sg = S.cs[t].y;
         for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {  // distinct planes within one angle
             const float* v = Z.v + 3 * j;
             const float* e = a.G.e;
@@ -348,10 +512,11 @@ __device__ __forceinline__ float sf_eps(const SfArgs& a, int k) {
     return (float)anneal_eps(a.eps_final, a.k_max, k, a.anneal);
 }
 
-__global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
-    extern __shared__ float M6[];
+__global__ void __launch_bounds__(kSfThreads, kSfCtasPerSm) single_fit_kernel(SfArgs a) {
+    extern __shared__ float M6[];  // 6 M floats of MM matrices, then T float2 of the angle table
     __shared__ SfShared S;
     SfScratch Z = sf_slice(a, blockIdx.x);
+    sf_angles(a, S, (float2*)(M6 + 6 * a.M));
     const float log2e = 1.4426950408889634f;
     while (true) {
         if (threadIdx.x == 0) S.start = atomicAdd(a.queue, 1);
@@ -371,7 +536,8 @@ __global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
             }
             float eps = sf_eps(a, k);
             float negK = -a.G.D * a.G.D * log2e / eps, dust = -a.c_out * log2e / eps;
-            sf_refresh(a, S, Z);  // E-step pose
+            sf_refresh(a, S, Z, negK);  // E-step pose
+            sf_near(a, S, Z, negK, dust, npair);
             if (threadIdx.x == 0) S.stop = 0;
             __syncthreads();
             for (int q = 0; q < a.n_newton; ++q) {
@@ -387,8 +553,9 @@ __global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
         // candidate filter at the final pose
         sf_cut(a, S, Z);
         overflow |= S.overflow != 0;
-        sf_refresh(a, S, Z);
         float negK = -a.G.D * a.G.D * log2e / a.eps_final, dust = -a.c_out * log2e / a.eps_final;
+        sf_refresh(a, S, Z, negK);
+        sf_near(a, S, Z, negK, dust, npair);
         sf_columns(a, S, Z, negK, dust, true, npair);
         atomicAdd((unsigned long long*)(a.ctrl + CTRL_SF_PAIRS), npair);
         if (threadIdx.x == 0) {
@@ -424,10 +591,12 @@ __global__ void __launch_bounds__(kSfThreads) single_fit_kernel(SfArgs a) {
 
 // One candidate per CTA.  count_only: nnz per candidate; else fill the CSR.
 __global__ void __launch_bounds__(kSfThreads) spot_matrix_kernel(SfArgs a, SpotArgs sp, int count_only) {
+    extern __shared__ float2 sp_cs[];  // T float2: the angle table
     __shared__ SfShared S;
     __shared__ int wcnt[kSfThreads / 32];
     __shared__ int nnz;
     SfScratch Z = sf_slice(a, blockIdx.x);
+    sf_angles(a, S, sp_cs);
     const float log2e = 1.4426950408889634f;
     const float negK = -a.G.D * a.G.D * log2e / sp.eps_s, kc = a.c_out * log2e / sp.eps_s;
     for (int n = blockIdx.x; n < a.S; n += gridDim.x) {
@@ -437,7 +606,7 @@ __global__ void __launch_bounds__(kSfThreads) spot_matrix_kernel(SfArgs a, SpotA
         __syncthreads();
         sf_cut(a, S, Z);
         if (S.overflow && threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_CAPACITY);
-        sf_refresh(a, S, Z);
+        sf_refresh(a, S, Z, negK);
         int base = count_only ? 0 : sp.row_ptr[n];
         for (int t = 0; t < a.T; ++t) {
             int j0 = S.t_off[t], j1 = S.t_off[t + 1];
@@ -446,12 +615,11 @@ __global__ void __launch_bounds__(kSfThreads) spot_matrix_kernel(SfArgs a, SpotA
                 int i = i0 + threadIdx.x;
                 float val = 0.0f;
                 if (i < a.I_off[t + 1]) {
-                    float4 p = a.p[i];
+                    const SfRowG g = sf_rowg(a.p[i], Z.cE + 3 * j0);
                     Lse2 L;
                     L.m = kNegHuge;
                     L.s = 0.0f;
-                    for (int j = j0; j < j1; ++j)
-                        L.merge(negK * Z.kd[j] * sf_e2(p, Z.cE + 3 * j, Z.rE + 3 * j), 1.0f);
+                    for (int j = j0; j < j1; ++j) L.merge(sf_pair_v(g, Z.rk[j]), 1.0f);
                     val = (L.value() + kc) * 0.6931471805599453f;
                 }
                 bool nz = val > 0.0f;
@@ -604,7 +772,7 @@ __global__ void spot_kstar_kernel(SpotArgs sp, int K) {
 }
 
 cudaError_t spot_matrix_run(const SfArgs& a, const SpotArgs& sp, int ctas, bool count_only, cudaStream_t s) {
-    if (a.S > 0) spot_matrix_kernel<<<ctas, kSfThreads, 0, s>>>(a, sp, count_only ? 1 : 0);
+    if (a.S > 0) spot_matrix_kernel<<<ctas, kSfThreads, sizeof(float2) * (size_t)a.T, s>>>(a, sp, count_only ? 1 : 0);
     if (count_only) spot_scan_kernel<<<1, 1024, 0, s>>>(sp, a.S);
     return cudaGetLastError();
 }
@@ -621,10 +789,8 @@ cudaError_t spot_greedy_run(const SpotArgs& sp, int n_obs, int Nc, int k_max, in
     return cudaGetLastError();
 }
 
-static_assert(kSfCap == 2048 && kSfIcap == 4096, "the workspace layout reserves the single-fit scratch for these");
-
 cudaError_t single_fit_run(const SfArgs& a, int ctas, cudaStream_t s) {
-    size_t shm = sizeof(float) * 6 * (size_t)a.M;
+    size_t shm = sizeof(float) * 6 * (size_t)a.M + sizeof(float2) * (size_t)a.T;
     if (shm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(single_fit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         if (e != cudaSuccess) return e;
