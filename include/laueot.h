@@ -335,7 +335,7 @@ int laue_cost_sinkhorn_noalloc(const LaueGeometry* geom, const LaueObsSpots* obs
 
 /* Autotuner of the pair passes (no counterpart in the paper): times each
  * launch shape of the row and column passes of laue_cost_sinkhorn on this
- * problem (shape v: {256, 128, 256 with a 64-register cap, 128 with a
+ * problem (shape v: {256, 128, 128 with a 128-register cap, 128 with a
  * 64-register cap} threads per CTA, one row/column pair per thread; the tile
  * size follows the CTA width), n_iter passes each after one warm-up
  * iteration, and keeps the fastest row and column shapes in the handle for
@@ -359,10 +359,11 @@ int laue_read_counters(laue_handle* h, void* stream, long long* counts_host, int
 
 /* Exact underflow skipping in the Sinkhorn pair passes (no counterpart in the
  * paper; on by default): within each angle block the spots are ordered by
- * direction, each run of 128 pairs carries a cone bounding its directions,
- * and a pass skips a (tile, staged chunk) combination when the cones prove
- * that every shifted exponent is below -130, i.e. every plan entry flushes to
- * exactly 0; the potentials are bit-identical either way.  enable = 0 turns
+ * direction, each run of 64 pairs (half a staged chunk of 128) carries a
+ * cone bounding its directions, and a pass skips a (tile, half chunk)
+ * combination when the cones prove that every shifted exponent is below
+ * -130, i.e. every plan entry flushes to exactly 0; the potentials are
+ * bit-identical either way.  enable = 0 turns
  * the skipping off (the ordering stays).  Read the evaluated pairs with
  * laue_read_counters. */
 int laue_set_pair_skipping(laue_handle* h, int enable);

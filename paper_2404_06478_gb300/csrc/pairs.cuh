@@ -11,6 +11,7 @@ namespace laue {
 
 constexpr int kTPB = 256;     // widest CTA of the pair passes (one row/column pair per thread)
 constexpr int kChunk = 128;   // staged pairs per chunk (256 spots)
+constexpr int kGran = 64;     // pairs per cone granule of the exact skipping (half a chunk)
 constexpr int kGroup = 4;     // staged pairs per max-then-sum group
 constexpr float kPadFar = 1.0e6f;
 
@@ -203,11 +204,11 @@ template <class Prep, class Body>
 __device__ __forceinline__ bool stream_list_prep(Stage& S, uint32_t (&parity)[2], const Srcs& src, int base,
                                                  int n_total, int n_list, Prep prep, Body body) {
     if (threadIdx.x == 0) {
-        for (int c = 0; c < n_list && c < 2; ++c) issue_chunk_at(S, c & 1, S.list[c], src, base, n_total);
+        for (int c = 0; c < n_list && c < 2; ++c) issue_chunk_at(S, c & 1, S.list[c] & 0xffffff, src, base, n_total);
     }
     bool ok_all = true;
     for (int c = 0; c < n_list; ++c) {
-        int st = c & 1, ch = S.list[c];
+        int st = c & 1, ch = S.list[c] & 0xffffff, mask = S.list[c] >> 24;
         int n = min(kChunk, n_total - ch * kChunk);
         bool ok = mbar_wait_bounded(&S.bar[st], parity[st]);
         parity[st] ^= 1u;
@@ -219,16 +220,16 @@ __device__ __forceinline__ bool stream_list_prep(Stage& S, uint32_t (&parity)[2]
             }
             break;
         }
-        body(st, n, ch * kChunk);
+        body(st, n, ch * kChunk, mask);
         __syncthreads();
-        if (threadIdx.x == 0 && c + 2 < n_list) issue_chunk_at(S, st, S.list[c + 2], src, base, n_total);
+        if (threadIdx.x == 0 && c + 2 < n_list) issue_chunk_at(S, st, S.list[c + 2] & 0xffffff, src, base, n_total);
     }
     return ok_all;
 }
 
 // ------------------------------------- exact underflow skipping (cone bounds)
-// A granule is kChunk pairs of one angle block (the unit of the staged
-// chunks); its cone bounds the directions of its spots: for observed spots
+// A granule is kGran pairs of one angle block (half a staged chunk); its
+// cone bounds the directions of its spots: for observed spots
 // the unit vectors p / |p| and the smallest |p|, for model spots the rays r
 // and the largest |c|.  For an observed cone O and a model cone M, every pair
 // has an angle between rhat = (p - c)/|p - c| and r of at least
@@ -285,15 +286,17 @@ __device__ __forceinline__ float min_scaled_cost(const Cone& O, const Cone& M, f
 // bit-identical with or without the pair.
 constexpr float kSkipLog2 = 130.0f;
 
-// Ordered list (in Stage::list) of the chunks c < nch with need(c); returns
-// its length.  All threads of the CTA call it.
+// Ordered list (in Stage::list) of the chunks c < nch whose half mask
+// need(c) (bit h: granule h of the chunk can hold a plan entry) is nonzero,
+// each entry c | mask << 24; returns its length.  All threads of the CTA call it.
 template <class Need>
 __device__ __forceinline__ int build_chunk_list(Stage& S, int nch, Need need) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int base = 0;
     for (int c0 = 0; c0 < nch; c0 += blockDim.x) {
         int c = c0 + threadIdx.x;
-        bool nd = c < nch && need(c);
+        int mask = c < nch ? need(c) : 0;
+        bool nd = mask != 0;
         unsigned b = __ballot_sync(0xffffffffu, nd);
         if (lane == 0) S.wcnt[w] = __popc(b);
         __syncthreads();
@@ -302,11 +305,27 @@ __device__ __forceinline__ int build_chunk_list(Stage& S, int nch, Need need) {
             if (k < w) before += S.wcnt[k];
             total += S.wcnt[k];
         }
-        if (nd) S.list[base + before + __popc(b & ((1u << lane) - 1u))] = c;
+        if (nd) S.list[base + before + __popc(b & ((1u << lane) - 1u))] = c | (mask << 24);
         base += total;
         __syncthreads();
     }
     return base;
+}
+
+// Pairs of the halves of chunk ch selected by mask (n_total pairs in the block).
+__device__ __forceinline__ int list_pairs(int ch, int mask, int n_total) {
+    int n = min(kChunk, n_total - ch * kChunk);
+    return ((mask & 1) ? min(kGran, n) : 0) + ((mask & 2) ? max(0, n - kGran) : 0);
+}
+
+// Cone of the tile's own spots [first, first + count) pairs of a block whose
+// granules start at granule gb (pair offset p0): the merge of its granules.
+__device__ __forceinline__ Cone tile_cone(const float4* cone, const float* ext, int gb, int p0, int first, int count,
+                                          bool obs) {
+    const int g0 = gb + (first - p0) / kGran, g1 = gb + (first + count - 1 - p0) / kGran;
+    Cone c = load_cone(cone, ext, g0);
+    for (int g = g0 + 1; g <= g1; ++g) c = merge_cones(c, load_cone(cone, ext, g), obs);
+    return c;
 }
 
 // Same without a prep step.

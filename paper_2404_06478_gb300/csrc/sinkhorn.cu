@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(1024) sk_schedule_kernel(SkArgs a) {
         for (int t = 0; t < T; ++t) {
             a.obs_gbase[t] = go;
             a.mod_gbase[t] = gm;
-            go += (a.I2_off[t + 1] - a.I2_off[t] + kChunk - 1) / kChunk;
-            gm += (a.J2_off[t + 1] - a.J2_off[t] + kChunk - 1) / kChunk;
+            go += (a.I2_off[t + 1] - a.I2_off[t] + kGran - 1) / kGran;
+            gm += (a.J2_off[t + 1] - a.J2_off[t] + kGran - 1) / kGran;
         }
         a.obs_gbase[T] = go;
         a.mod_gbase[T] = gm;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(1024) sk_schedule_kernel(SkArgs a) {
 // Within each angle block the spots are ranked by a 23-bit key of their
 // direction (observed: p / |p|, model: the ray r): the cube-map face of the
 // direction and the Morton interleave of its two in-face coordinates at 10
-// bits each.  Spots close on a detector get close ranks, so runs of kChunk
+// bits each.  Spots close on a detector get close ranks, so runs of kGran
 // pairs are spatially compact and their cones are narrow.  One CTA sorts one
 // block (LSD radix sort, 4-bit digits, stable: ties keep the caller's order).
 __device__ __forceinline__ unsigned spread10(unsigned v) {
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kSortThreads) sk_sort_kernel(SkArgs a) {
     }
 }
 
-// Cone of each granule (kChunk pairs of one block), one warp per granule:
+// Cone of each granule (kGran pairs of one block), one warp per granule:
 // axis = normalised mean direction, half-angle = largest angle from it, and
 // the smallest |p| (observed) or largest |c| (model).
 __global__ void __launch_bounds__(256) sk_cone_kernel(SkArgs a) {
@@ -280,12 +280,12 @@ __global__ void __launch_bounds__(256) sk_cone_kernel(SkArgs a) {
     const int* off = mod ? a.J_off : a.I_off;
     const int* poff = mod ? a.J2_off : a.I2_off;
     const int nspots = off[t + 1] - off[t];
-    const int l0 = 2 * kChunk * (g - gb[t]);           // first spot rank of the granule
-    const int l1 = min(nspots, l0 + 2 * kChunk);
-    float d[2 * kChunk / 32][3];
+    const int l0 = 2 * kGran * (g - gb[t]);            // first spot rank of the granule
+    const int l1 = min(nspots, l0 + 2 * kGran);
+    float d[2 * kGran / 32][3];
     float sx = 0.f, sy = 0.f, sz = 0.f, ext = mod ? 0.0f : 3.0e38f;
     int cntv = 0;
-    for (int k = 0; k < 2 * kChunk / 32; ++k) {
+    for (int k = 0; k < 2 * kGran / 32; ++k) {
         int l = l0 + lane + 32 * k;
         d[k][0] = d[k][1] = d[k][2] = 0.0f;
         if (l >= l1) continue;
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(256) sk_cone_kernel(SkArgs a) {
         az = sz * r;
     }
     float beta = 0.0f;
-    for (int k = 0; k < 2 * kChunk / 32; ++k) {
+    for (int k = 0; k < 2 * kGran / 32; ++k) {
         int l = l0 + lane + 32 * k;
         if (l >= l1) continue;
         beta = fmaxf(beta, angle_between(ax, ay, az, d[k][0], d[k][1], d[k][2]));
@@ -588,22 +588,28 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
                 y.w -= shift;
             }
         };
-        auto body = [&](int st, int n, int) {
-            if (valid) row_chunk_sum(R, S.s[0][st], S.s[1][st], S.s[2][st], S.s[3][st], n, Sa, Sb);
+        // the halves (granules) of a staged chunk selected by mask
+        auto body = [&](int st, int n, int, int mask = 3) {
+            if (!valid) return;
+            const int h = (mask & 1) ? 0 : kGran, e = (mask & 2) ? n : min(n, kGran);
+            if (e > h)
+                row_chunk_sum(R, S.s[0][st] + h, S.s[1][st] + h, S.s[2][st] + h, S.s[3][st] + h, e - h, Sa, Sb);
         };
-        // the model chunks this tile of observed spots can see (exact underflow skipping)
+        // the model granules this tile of observed spots can see (exact underflow skipping)
         const int nch = (nj + kChunk - 1) / kChunk;
         const bool use_list = a.skip && nch > 0 && nch <= kMaxList;
         int n_list = nch;
         if (use_list) {
-            const int g0 = a.obs_gbase[t] + (td.y - a.I2_off[t]) / kChunk;
-            const int g1 = a.obs_gbase[t] + (td.y + td.z - 1 - a.I2_off[t]) / kChunk;
-            Cone O = load_cone(a.obs_cone, a.obs_ext, g0);
-            if (g1 != g0) O = merge_cones(O, load_cone(a.obs_cone, a.obs_ext, g1), true);
+            const Cone O = tile_cone(a.obs_cone, a.obs_ext, a.obs_gbase[t], a.I2_off[t], td.y, td.z, true);
             const float K = a.skipK;  // the smallest cost factor of any spot
-            const int mg = a.mod_gbase[t];
+            const int mg = a.mod_gbase[t], ng = (nj + kGran - 1) / kGran;
             n_list = build_chunk_list(S, nch, [&](int c) {
-                return min_scaled_cost(O, load_cone(a.mod_cone, a.mod_ext, mg + c), K) <= kSkipLog2;
+                int m = 0;
+                for (int hh = 0; hh < 2; ++hh)
+                    if (2 * c + hh < ng &&
+                        min_scaled_cost(O, load_cone(a.mod_cone, a.mod_ext, mg + 2 * c + hh), K) <= kSkipLog2)
+                        m |= 1 << hh;
+                return m;
             });
         }
         bool ok = use_list ? stream_list_prep(S, parity, src, j0, nj, n_list, prep, body)
@@ -611,7 +617,7 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
         if (threadIdx.x == 0) {
             long long np = 0;
             if (use_list)
-                for (int c = 0; c < n_list; ++c) np += min(kChunk, nj - S.list[c] * kChunk);
+                for (int c = 0; c < n_list; ++c) np += list_pairs(S.list[c] & 0xffffff, S.list[c] >> 24, nj);
             else
                 np = nj;
             atomicAdd((unsigned long long*)(a.ctrl + CTRL_SK_PAIRS), (unsigned long long)(4LL * td.z * np));
@@ -708,22 +714,26 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
                 y.w -= shift;
             }
         };
-        auto body = [&](int st, int n, int) {
-            if (valid) col_chunk_sum(C, S.s[0][st], S.s[1][st], n, Sa, Sb);
+        auto body = [&](int st, int n, int, int mask = 3) {
+            if (!valid) return;
+            const int h = (mask & 1) ? 0 : kGran, e = (mask & 2) ? n : min(n, kGran);
+            if (e > h) col_chunk_sum(C, S.s[0][st] + h, S.s[1][st] + h, e - h, Sa, Sb);
         };
-        // the observed chunks this tile of model spots can see (exact underflow skipping)
+        // the observed granules this tile of model spots can see (exact underflow skipping)
         const int nch = (ni + kChunk - 1) / kChunk;
         const bool use_list = a.skip && nch > 0 && nch <= kMaxList;
         int n_list = nch;
         if (use_list) {
-            const int g0 = a.mod_gbase[t] + (td.y - a.J2_off[t]) / kChunk;
-            const int g1 = a.mod_gbase[t] + (td.y + td.z - 1 - a.J2_off[t]) / kChunk;
-            Cone M = load_cone(a.mod_cone, a.mod_ext, g0);
-            if (g1 != g0) M = merge_cones(M, load_cone(a.mod_cone, a.mod_ext, g1), false);
+            const Cone M = tile_cone(a.mod_cone, a.mod_ext, a.mod_gbase[t], a.J2_off[t], td.y, td.z, false);
             const float K = a.skipK;  // the smallest cost factor of any spot
-            const int og = a.obs_gbase[t];
+            const int og = a.obs_gbase[t], ng = (ni + kGran - 1) / kGran;
             n_list = build_chunk_list(S, nch, [&](int c) {
-                return min_scaled_cost(load_cone(a.obs_cone, a.obs_ext, og + c), M, K) <= kSkipLog2;
+                int m = 0;
+                for (int hh = 0; hh < 2; ++hh)
+                    if (2 * c + hh < ng &&
+                        min_scaled_cost(load_cone(a.obs_cone, a.obs_ext, og + 2 * c + hh), M, K) <= kSkipLog2)
+                        m |= 1 << hh;
+                return m;
             });
         }
         bool ok = use_list ? stream_list_prep(S, parity, src, i0, ni, n_list, prep, body)
@@ -731,7 +741,7 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
         if (threadIdx.x == 0) {
             long long np = 0;
             if (use_list)
-                for (int c = 0; c < n_list; ++c) np += min(kChunk, ni - S.list[c] * kChunk);
+                for (int c = 0; c < n_list; ++c) np += list_pairs(S.list[c] & 0xffffff, S.list[c] >> 24, ni);
             else
                 np = ni;
             atomicAdd((unsigned long long*)(a.ctrl + CTRL_SK_PAIRS), (unsigned long long)(4LL * td.z * np));
@@ -1044,7 +1054,7 @@ cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s) {
     if (a.T > 0) sk_sort_kernel<<<2 * a.T, kSortThreads, 0, s>>>(a);
     sk_pack_kernel<<<blocks, 256, 0, s>>>(a);
     {
-        int max_gran = (a.n_obs + a.n_model) / (2 * kChunk) + 2 * a.T + 2;  // bound on the granule count
+        int max_gran = (a.n_obs + a.n_model) / (2 * kGran) + 2 * a.T + 2;  // bound on the granule count
         sk_cone_kernel<<<(max_gran * 32 + 255) / 256, 256, 0, s>>>(a);
     }
     if (a.mode != 2) sk_init_dust_kernel<<<1, 1024, 0, s>>>(a);
@@ -1055,12 +1065,12 @@ cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s) {
 // Launch shapes of the pair passes the autotuner chooses from:
 // {threads per CTA (= pairs per tile), minimum resident CTAs per SM}.
 typedef void (*SkKernel)(SkArgs);
-static const SkKernel kRowKernels[kSkVariants] = {sk_row_kernel<256, 1>, sk_row_kernel<128, 1>, sk_row_kernel<256, 4>,
+static const SkKernel kRowKernels[kSkVariants] = {sk_row_kernel<256, 1>, sk_row_kernel<128, 1>, sk_row_kernel<128, 4>,
                                                   sk_row_kernel<128, 8>};
-static const SkKernel kColKernels[kSkVariants] = {sk_col_kernel<256, 1>, sk_col_kernel<128, 1>, sk_col_kernel<256, 4>,
+static const SkKernel kColKernels[kSkVariants] = {sk_col_kernel<256, 1>, sk_col_kernel<128, 1>, sk_col_kernel<128, 4>,
                                                   sk_col_kernel<128, 8>};
 
-int sk_variant_threads(int v) { return (v == 1 || v == 3) ? 128 : 256; }
+int sk_variant_threads(int v) { return v == 0 ? 256 : 128; }
 
 void sinkhorn_row_pass(const SkArgs& a, const SkLaunch& l, cudaStream_t s) {
     kRowKernels[l.row_variant]<<<l.row_grid, sk_variant_threads(l.row_variant), 0, s>>>(a);

@@ -315,8 +315,11 @@ def test_sinkhorn_skipping_is_bit_identical(env, eps, mode):
     run of 128 pairs) changes no bit of the potentials, the dustbins or the
     read-out.  Workload: the 1000-grain density on 4 angles (about 14k
     observed and 8k model spots per block, so a tile's cone spans a few degrees
-    of a detector).  At eps <= 1 mm^2 a host model of the cone bounds predicts
-    that 45-47% of the pairs are skipped; at eps = 2000 none can be."""
+    of a detector).  At eps <= 1 mm^2 a host model of the cone bounds (64-pair
+    granules, 256-pair tiles) predicts that the row pass skips 53-55% of its
+    pairs; the column pass, whose 256-pair model tiles have wider cones, skips
+    fewer (about 40% of both passes' pairs are skipped); at eps = 2000 none
+    can be."""
     api, torch = env["api"], env["torch"]
     case = make_case(sg.CONFIGS["batched"], seed=0, T=4)
     ob, ms = to_device(case, env["dev"])
