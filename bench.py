@@ -154,14 +154,15 @@ def build_workload(dev, seed, api, sg, torch, grains=None, angles=None):
 
 
 def em_step(W, api, R, x, stream=None):
-    cfg, geom, h = W["cfg"], W["geom"], W["h"]
-    api.refresh(h, geom, W["lat"], R, x, W["om"], W["model"], stream=stream)
-    out = api.cost_sinkhorn(h, geom, W["ob"], W["model"], cfg.eps, W["c_out"], cfg.n_sinkhorn, harvest=True,
-                            stream=stream)
-    if hasattr(api, "mstep"):
-        api.mstep(h, geom, W["lat"], W["ob"], W["model"], out["f"], out["g"], cfg.eps, W["om"], R, x,
-                  stream=stream)
-    return out
+    """One EM iteration at eps_final (the last annealed step k = n_em - 1 of
+    Algorithm LaueOT: refresh, E-step with read-out, M-step) in one laue_em
+    call; the outputs are allocated once, so the call can be captured."""
+    cfg, h = W["cfg"], W["h"]
+    if "em_out" not in W:
+        W["em_out"] = api.em_outputs(W["ob"], W["model"])
+    k = cfg.n_em - 1
+    return api.em(h, W["geom"], W["lat"], W["ob"], W["model"], W["om"], R, x, cfg.eps, cfg.n_em, cfg.n_sinkhorn,
+                  W["c_out"], k_first=k, k_last=k, out=W["em_out"], stream=stream)
 
 
 def oracle_workload(seed=0):

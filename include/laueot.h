@@ -153,6 +153,24 @@ typedef struct {
     float hreg;     /* Hessian shift: iota = max(0, lmax(H) + hreg |H|_F) */
 } LaueMParams;
 
+/* Annealed multi-grain EM (paper Algorithm LaueOT; Section "Deterministic
+ * annealing") for laue_em: steps k = k_first .. k_last of an n_em-step
+ * schedule eps_k = eps_final anneal^(1 - k/K), K = ceil(0.75 n_em), eps_k =
+ * eps_final for k >= K. */
+typedef struct {
+    double unmatched_frac;
+    float eps_final;
+    float c_out;
+    float anneal;      /* eps_0 / eps_final; <= 0 means 100 */
+    int n_em;
+    int n_sinkhorn;    /* Sinkhorn iterations of each E-step (from f = g = 0) */
+    int dust_mode;     /* 0 global, 1 per-angle dustbins */
+    int mstep_kind;    /* 0 Newton + MM (laue_mstep), 1 adjoint (laue_mstep_adjoint:
+                          mstep.n_newton damped Gauss-Newton steps, mstep.hreg the damping) */
+    int k_first, k_last;
+    LaueMParams mstep; /* eps is set per step */
+} LaueEMParams;
+
 /* Sizes that bound a problem, for laue_workspace_size. */
 typedef struct {
     int T;
@@ -562,6 +580,22 @@ int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat,
                const LaueObsSpots* obs, const float* omega, const float* startR,
                const float* startX, int S, const LaueIndexParams* prm, float* R_out,
                float* x_out, int n_max, int* n_grains_host, int* assign, void* stream);
+
+/* Multi-grain EM on a frozen model-spot list (paper Algorithm LaueOT): for
+ * each step k = k_first .. k_last (0 <= k_first <= k_last <= n_em):
+ * laue_refresh at the current poses, laue_cost_sinkhorn at eps_k
+ * (n_sinkhorn iterations), then for k < n_em the M-step at eps_k (Newton +
+ * MM, or the adjoint Gauss-Newton step) updating R (N x 9) and x (N x 3) in
+ * place; step k = n_em is the final E-step alone.  f, g, dust receive the
+ * last E-step's potentials; assign and margin (optional) the read-out of
+ * the E-step of step k_last (as for laue_cost_sinkhorn).  The
+ * whole solve is k_first = 0, k_last = n_em.  Asynchronous and free of host
+ * synchronisation and allocation, so it can be captured in a CUDA graph.
+ * Needs the workspace of laue_workspace_size with T, n_obs, n_model and
+ * n_grains = N set. */
+int laue_em(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const LaueObsSpots* obs,
+            const float* omega, LaueModelSpots* model, float* R, float* x, int N, const LaueEMParams* prm,
+            float* f, float* g, float* dust, int* assign, float* margin, void* stream);
 
 /* ---- learned proposal (an addition beside the paper's method) ---------- */
 

@@ -66,6 +66,12 @@ class LaueSingleParams(ctypes.Structure):
                 ("anneal", _f), ("recut", _i)]
 
 
+class LaueEMParams(ctypes.Structure):
+    _fields_ = [("unmatched_frac", ctypes.c_double), ("eps_final", _f), ("c_out", _f), ("anneal", _f),
+                ("n_em", _i), ("n_sinkhorn", _i), ("dust_mode", _i), ("mstep_kind", _i), ("k_first", _i),
+                ("k_last", _i), ("mstep", LaueMParams)]
+
+
 class LaueIndexParams(ctypes.Structure):
     _fields_ = [("unmatched_frac", _d), ("eps_final", _f), ("c_out", _f), ("f_out", _f), ("n_em", _i),
                 ("n_sinkhorn", _i), ("k_single", _i), ("dust_mode", _i), ("mstep", LaueMParams),
@@ -98,6 +104,8 @@ SIGNATURES = {
                       _vp, _vp],
     "laue_set_launch_shape": [_vp, _i, _i],
     "laue_set_pair_skipping": [_vp, _i],
+    "laue_em": [_vp, _P(LaueGeometry), _P(LaueLattice), _P(LaueObsSpots), _vp, _P(LaueModelSpots), _vp, _vp, _i,
+                _P(LaueEMParams), _vp, _vp, _vp, _vp, _vp, _vp],
     "laue_sparse_workspace_size": [_i, _i, _i, _i, _P(ctypes.c_size_t)],
     "laue_cost_sinkhorn_sparse": [_vp, _P(LaueGeometry), _P(LaueObsSpots), _P(LaueModelSpots), _P(LaueOTParams),
                                   _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],

@@ -437,6 +437,40 @@ def mstep(h: Handle, geom, lat: Lattice, obs: ObsSpots, model: ModelSpots, f, g,
                            _ptr(step_norms), _stream(stream)), "laue_mstep")
 
 
+def em_outputs(obs: ObsSpots, model: ModelSpots, dust_mode=0, harvest=True):
+    """Output tensors of laue_em (f, g, dust, and assign, margin with harvest)."""
+    dev = obs.p.device
+    nI, nJ, nd = int(obs.p.shape[0]), model.n, obs.T if dust_mode else 1
+    out = dict(f=torch.zeros(max(nI, 1), device=dev), g=torch.zeros(max(nJ, 1), device=dev),
+               dust=torch.zeros(2 * nd, device=dev))
+    if harvest:
+        out["assign"] = torch.empty(max(nI, 1), dtype=torch.int32, device=dev)
+        out["margin"] = torch.empty(max(nI, 1), device=dev)
+    return out
+
+
+def em(h: Handle, geom, lat: Lattice, obs: ObsSpots, model: ModelSpots, omega, R, x, eps_final, n_em, n_sinkhorn,
+       c_out, k_first=0, k_last=None, anneal=100.0, dust_mode=0, unmatched_frac=0.4, mstep="plain", n_newton=4,
+       n_mm=4, tol_x=1e-6, tol_R=1e-9, hreg=1e-3, out=None, harvest=True, stream=None):
+    """laue_em: steps k_first .. k_last (default n_em: the whole solve and its
+    final E-step) of the annealed EM on the frozen model list, R (N, 9) and
+    x (N, 3) updated in place; returns dict f, g, dust (and assign, margin of
+    step k_last's E-step with harvest).  `out` reuses the output tensors of a
+    previous call (no allocation, e.g. under graph capture)."""
+    n_grains = int(x.shape[0])
+    if out is None:
+        out = em_outputs(obs, model, dust_mode, harvest)
+    prm = N.LaueEMParams(float(unmatched_frac), float(eps_final), float(c_out), float(anneal), int(n_em),
+                         int(n_sinkhorn), int(dust_mode), 1 if mstep == "adjoint" else 0, int(k_first),
+                         int(n_em if k_last is None else k_last), mparams(eps_final, n_newton, n_mm, tol_x, tol_R, hreg))
+    g_s, l_s, o_s, m_s = geometry_struct(geom), lat.struct(), obs.struct(), model.struct()
+    h.check(h.L.laue_em(h.h, ctypes.byref(g_s), ctypes.byref(l_s), ctypes.byref(o_s), _ptr(omega),
+                        ctypes.byref(m_s), _ptr(R), _ptr(x), n_grains, ctypes.byref(prm), _ptr(out["f"]), _ptr(out["g"]),
+                        _ptr(out["dust"]), _ptr(out.get("assign")), _ptr(out.get("margin")), _stream(stream)),
+            "laue_em")
+    return out
+
+
 def mstep_adjoint(h: Handle, geom, lat: Lattice, obs: ObsSpots, model: ModelSpots, f, g, eps, omega, R, x,
                   n_steps=4, lam=1e-3, step_norms=None, stream=None):
     """laue_mstep_adjoint: damped Gauss-Newton M-step on the OT-weighted cost

@@ -189,25 +189,46 @@ extern "C" int laue_index(laue_handle* h, const LaueGeometry* geom, const LaueLa
     int total = 0;
     if ((rc = laue_forward(h, geom, lat, R_out, x_out, kstar, omega, T, &ms, &total, stream))) return restore(rc);
     // 5. annealed EM (Algorithm LaueOT) with a final E-step for the assignment
-    LaueOTParams op{prm->unmatched_frac, 0.0f, prm->c_out, prm->n_sinkhorn, prm->dust_mode, 0, 0};
-    for (int k = 0; k <= prm->n_em; ++k) {
-        double eps = anneal_eps(prm->eps_final, prm->n_em, k, 100.0);
-        op.eps = (float)eps;
-        if ((rc = laue_refresh(h, geom, lat, R_out, x_out, omega, &ms, stream))) return restore(rc);
-        bool last = k == prm->n_em;
-        if ((rc = laue_cost_sinkhorn(h, geom, obs, &ms, &op, f, g, dust, last ? assign_j : nullptr, nullptr, nullptr,
-                                     nullptr, stream)))
-            return restore(rc);
-        if (last) break;
-        LaueMParams mp = prm->mstep;
-        mp.eps = (float)eps;
-        rc = prm->mstep_kind == 1
-                 ? laue_mstep_adjoint(h, geom, lat, obs, &ms, f, g, &mp, omega, R_out, x_out, kstar, nullptr, stream)
-                 : laue_mstep(h, geom, lat, obs, &ms, f, g, &mp, omega, R_out, x_out, kstar, nullptr, stream);
-        if (rc) return restore(rc);
-    }
+    LaueEMParams ep{prm->unmatched_frac, prm->eps_final, prm->c_out, 100.0f, prm->n_em, prm->n_sinkhorn,
+                    prm->dust_mode, prm->mstep_kind, 0, prm->n_em, prm->mstep};
+    if ((rc = laue_em(h, geom, lat, obs, omega, &ms, R_out, x_out, kstar, &ep, f, g, dust, assign_j, nullptr,
+                      stream)))
+        return restore(rc);
     if (obs->n > 0) spot_to_grain_kernel<<<(obs->n + 255) / 256, 256, 0, s>>>(assign_j, mgrain, obs->n, assign);
     if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "index synchronise"))) return restore(rc);
     *n_grains_host = kstar;
     return restore(LAUE_OK);
+}
+
+extern "C" int laue_em(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, const LaueObsSpots* obs,
+                       const float* omega, LaueModelSpots* model, float* R, float* x, int N, const LaueEMParams* prm,
+                       float* f, float* g, float* dust, int* assign, float* margin, void* stream) {
+    if (!h) return LAUE_ERR_INVALID_ARG;
+    if (!prm || !geom || !lat || !obs || !model || !omega || (N > 0 && (!R || !x)) || !f || !g || !dust)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG, "em: null argument");
+    if (prm->n_em < 0 || prm->k_first < 0 || prm->k_first > prm->k_last || prm->k_last > prm->n_em ||
+        prm->n_sinkhorn < 0 || !(prm->eps_final > 0.0f) || prm->dust_mode < 0 || prm->dust_mode > 1 ||
+        prm->mstep_kind < 0 || prm->mstep_kind > 1 || N < 0)
+        return laue_fail(h, LAUE_ERR_INVALID_ARG,
+                         "em: 0 <= k_first <= k_last <= n_em, eps_final > 0, dust_mode 0 or 1, mstep_kind 0 or 1");
+    const double anneal = prm->anneal > 0.0f ? prm->anneal : 100.0;
+    LaueOTParams op{prm->unmatched_frac, 0.0f, prm->c_out, prm->n_sinkhorn, prm->dust_mode, 0, 0.0f, 0.0f, 0};
+    int rc;
+    for (int k = prm->k_first; k <= prm->k_last; ++k) {
+        const double eps = anneal_eps(prm->eps_final, prm->n_em, k, anneal);
+        op.eps = (float)eps;
+        if ((rc = laue_refresh(h, geom, lat, R, x, omega, model, stream))) return rc;
+        const bool last = k == prm->k_last;  // the read-out of the call's last E-step
+        if ((rc = laue_cost_sinkhorn(h, geom, obs, model, &op, f, g, dust, last ? assign : nullptr,
+                                     last ? margin : nullptr, nullptr, nullptr, stream)))
+            return rc;
+        if (k == prm->n_em) break;  // the final E-step
+        LaueMParams mp = prm->mstep;
+        mp.eps = (float)eps;
+        rc = prm->mstep_kind == 1
+                 ? laue_mstep_adjoint(h, geom, lat, obs, model, f, g, &mp, omega, R, x, N, nullptr, stream)
+                 : laue_mstep(h, geom, lat, obs, model, f, g, &mp, omega, R, x, N, nullptr, stream);
+        if (rc) return rc;
+    }
+    return LAUE_OK;
 }

@@ -2,12 +2,13 @@
 solver") over the C ABI, with deterministic annealing (Section "Deterministic
 annealing") and optional capture of the whole solve as one CUDA graph.
 
-Each EM step: refresh the frozen model list at the current poses
-(laue_refresh), E-step at temperature eps_k (laue_cost_sinkhorn, fixed number
-of Sinkhorn iterations from f = g = 0), M-step (laue_mstep).  A final E-step
-at the last poses gives the hard assignment.  The temperature schedule starts
-at 100 eps_final and cools geometrically to eps_final at step ceil(0.75 n_em),
-then holds.  The host only enqueues work: no step reads device data back.
+The solve is one laue_em call.  Each EM step: refresh the frozen model list
+at the current poses (laue_refresh), E-step at temperature eps_k
+(laue_cost_sinkhorn, fixed number of Sinkhorn iterations from f = g = 0),
+M-step (laue_mstep, or laue_mstep_adjoint).  A final E-step at the last poses
+gives the hard assignment.  The temperature schedule starts at anneal_factor
+eps_final and cools geometrically to eps_final at step ceil(0.75 n_em), then
+holds.  The host only enqueues work: no step reads device data back.
 """
 from __future__ import annotations
 
@@ -43,7 +44,9 @@ class EMConfig:
 
 
 class EMSolver:
-    """Runs Algorithm LaueOT for fixed observed spots and a frozen model list.
+    """Runs Algorithm LaueOT for fixed observed spots and a frozen model list
+    through one laue_em call (refresh, E-step and M-step of every annealed
+    step, then the final E-step with the read-out).
 
     R (N, 9) and x (N, 3) float32 device tensors are updated in place."""
 
@@ -55,31 +58,14 @@ class EMSolver:
         self.graph = None
         self.out = None
 
-    def e_step(self, R, x, eps, harvest=False):
+    def em(self, R, x, k_first=0, k_last=None, out=None):
+        """laue_em over steps k_first .. k_last (default: the whole solve)."""
         c = self.cfg
-        api.refresh(self.h, self.geom, self.lat, R, x, self.omega, self.model)
-        return api.cost_sinkhorn(self.h, self.geom, self.obs, self.model, eps, c.c_out, c.n_sinkhorn,
-                                 dust_mode=c.dust_mode, unmatched_frac=c.unmatched_frac, harvest=harvest)
-
-    def m_step(self, R, x, out, eps):
-        c = self.cfg
-        if c.mstep == "adjoint":
-            api.mstep_adjoint(self.h, self.geom, self.lat, self.obs, self.model, out["f"], out["g"], eps, self.omega,
-                              R, x, n_steps=c.n_newton, lam=c.lm_damping)
-            return
-        api.mstep(self.h, self.geom, self.lat, self.obs, self.model, out["f"], out["g"], eps, self.omega, R, x,
-                  n_newton=c.n_newton, n_mm=c.n_mm, tol_x=c.tol_x, tol_R=c.tol_R, hreg=c.hreg)
-
-    def step(self, R, x, k):
-        eps = eps_schedule(self.cfg.eps_final, self.cfg.n_em, k, self.cfg.anneal_factor)
-        out = self.e_step(R, x, eps)
-        self.m_step(R, x, out, eps)
-        return out
-
-    def _run(self, R, x):
-        for k in range(self.cfg.n_em):
-            self.step(R, x, k)
-        return self.e_step(R, x, self.cfg.eps_final, harvest=True)
+        hreg = c.lm_damping if c.mstep == "adjoint" else c.hreg
+        return api.em(self.h, self.geom, self.lat, self.obs, self.model, self.omega, R, x, c.eps_final, c.n_em,
+                      c.n_sinkhorn, c.c_out, k_first=k_first, k_last=k_last, anneal=c.anneal_factor,
+                      dust_mode=c.dust_mode, unmatched_frac=c.unmatched_frac, mstep=c.mstep, n_newton=c.n_newton,
+                      n_mm=c.n_mm, tol_x=c.tol_x, tol_R=c.tol_R, hreg=hreg, out=out)
 
     def reserve(self, n_grains):
         """Size the workspace for every call of the solve (before any capture)."""
@@ -90,17 +76,18 @@ class EMSolver:
     def run(self, R, x, use_graph=False):
         """Full annealed solve; returns the final plan read-out (assign,
         margin, f, g, dust)."""
+        self.reserve(x.shape[0])
         if not use_graph:
-            return self._run(R, x)
+            return self.em(R, x)
         if self.graph is None:
-            self.reserve(x.shape[0])
             self._R, self._x = R, x
+            self.out = api.em_outputs(self.obs, self.model, self.cfg.dust_mode)  # allocated before the capture
             s = torch.cuda.Stream()
             s.wait_stream(torch.cuda.current_stream())
             with torch.cuda.stream(s):
                 g = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(g, stream=s):
-                    self.out = self._run(self._R, self._x)
+                    self.em(self._R, self._x, out=self.out)
             torch.cuda.current_stream().wait_stream(s)
             self.graph = g
         if R.data_ptr() != self._R.data_ptr():
@@ -113,16 +100,16 @@ class EMSolver:
         return self.out
 
 
-def step_graph(solver: EMSolver, R, x, eps):
-    """CUDA graph of one EM iteration at a fixed temperature (refresh,
-    E-step with read-out, M-step) on the tensors R, x."""
+def step_graph(solver: EMSolver, R, x, k):
+    """CUDA graph of one EM iteration (annealed step k < n_em: refresh, E-step
+    with read-out, M-step) on the tensors R, x; returns (graph, outputs)."""
     solver.reserve(x.shape[0])
+    out = api.em_outputs(solver.obs, solver.model, solver.cfg.dust_mode)  # allocated before the capture
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     g = torch.cuda.CUDAGraph()
     with torch.cuda.stream(s):
         with torch.cuda.graph(g, stream=s):
-            out = solver.e_step(R, x, eps, harvest=True)
-            solver.m_step(R, x, out, eps)
+            solver.em(R, x, k_first=k, k_last=k, out=out)
     torch.cuda.current_stream().wait_stream(s)
     return g, out
