@@ -29,10 +29,10 @@ METRIC = "cost-pair evals/s in Sinkhorn-EM at 1000 grains; time-to-index vs plai
 UNIT = "pairs/s"
 
 
-# DRAM bytes of one pair-pass launch on the 1000-grain workload, counted by ncu
+# DRAM bytes of one row-pass launch on the 1000-grain workload, counted by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) for the current kernels; None
-# until the current kernels are captured
-SK_PASS_DRAM_BYTES = None
+# after a kernel change until it is captured again
+SK_PASS_DRAM_BYTES = 41872640
 
 
 def max_over_ranks(value, world, device):
@@ -543,6 +543,9 @@ def main():
     ap.add_argument("--no-proposal", action="store_true", help="skip the learned-proposal measurements")
     ap.add_argument("--only-proposal-train", type=int, default=0,
                     help="run only this many set-encoder training steps (profiling; not a bench line)")
+    ap.add_argument("--only-fit-grid", type=int, default=0,
+                    help="run only the single-grain fits of the 100-grain workload from a start grid of this many "
+                         "spiral points (profiling; not a bench line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -562,6 +565,25 @@ def main():
         assert h.device_status() == 0
         print(json.dumps(dict(proposal_train_steps=args.only_proposal_train, sets_per_step=2048,
                               seconds=time.perf_counter() - t0)))
+        return 0
+    if args.only_fit_grid:
+        import torch
+        from paper_2404_06478_gb300 import api, build
+        import synthgen as sg
+        build.build()
+        dev = torch.device("cuda", 0)
+        h = api.Handle(dev)
+        M = _medium_workload(dev, api, sg, torch, h)
+        Rg, xg = api.start_grid(h, args.only_fit_grid, 24, 1, M["cfg"].cube_mm)
+        h.counters()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.single_fit(h, M["geom"], M["lat"], M["ob"], M["om"], Rg, xg, M["cfg"].eps, 40, M["c_out"], anneal=1000.0,
+                       recut=True)
+        torch.cuda.synchronize()
+        assert h.device_status() == 0
+        print(json.dumps(dict(fit_starts=int(Rg.shape[0]), seconds=time.perf_counter() - t0,
+                              pair_evaluations=h.counters()["fit_pairs"])))
         return 0
     rank, world, local = _dist_env()
     import torch
