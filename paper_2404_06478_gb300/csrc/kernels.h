@@ -148,6 +148,8 @@ struct SpArgs {
     int4* ctile;           // {angle, first column, end column, 0}
     int* rt_base;          // T + 1 first row tile of each angle (entry T = row tile count)
     int* ct_base;          // T + 1
+    float* gmax;           // T: largest G of each angle block (shift of the row pass)
+    float* fmax;           // T: largest F of each angle block (shift of the column pass)
     int max_rt, max_ct;
     int* ctrl;
     float negK;            // -D^2 log2(e) / eps

@@ -36,13 +36,12 @@ struct SfScratch {
     float* v;    // cap x 3 MM sums / filter column masses
     float* kd;   // cap: (D_j / D)^2, the cost length of the spot's detector relative to D
     float* lse;  // icap row normalisers of one angle block (log2)
-    int* ni;     // near rows of the current E-step (ncap): observed index
-    float* nl;   // and row normaliser (log2)
+    float4* near;  // near rows of the current E-step (ncap): {p, row normaliser (log2)}
 };
 
 __device__ __forceinline__ SfScratch sf_slice(const SfArgs& a, int cta) {
     SfScratch s;
-    size_t per = (size_t)a.cap * kSfSpotFloats + a.icap + 2 * (size_t)a.ncap;
+    size_t per = (size_t)a.cap * kSfSpotFloats + a.icap + 4 * (size_t)a.ncap;
     float* base = a.scratch + per * cta;  // 16-byte aligned: per is a multiple of 4 floats
     s.rk = (float4*)base;
     s.cE = base + 4 * a.cap;
@@ -50,8 +49,7 @@ __device__ __forceinline__ SfScratch sf_slice(const SfArgs& a, int cta) {
     s.tm = (int*)(base + 10 * a.cap);
     s.kd = base + 11 * a.cap;
     s.lse = base + 12 * a.cap;
-    s.ni = (int*)(s.lse + a.icap);
-    s.nl = s.lse + a.icap + a.ncap;
+    s.near = (float4*)(s.lse + a.icap);  // 16-byte aligned: cap, icap are multiples of 4
     return s;
 }
 
@@ -261,9 +259,11 @@ __device__ void sf_near(const SfArgs& a, SfShared& S, const SfScratch& Z, float 
                 const int i = i0 + threadIdx.x;
                 bool near = false;
                 float l = 0.0f;
+                float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (i < a.I_off[t + 1]) {
                     float vmax;
-                    l = sf_row_lse(a, S, Z, t, a.p[i], dust, npair, vmax);
+                    p = a.p[i];
+                    l = sf_row_lse(a, S, Z, t, p, dust, npair, vmax);
                     near = vmax - l >= kSfSkip;
                 }
                 const unsigned ball = __ballot_sync(0xffffffffu, near);
@@ -275,10 +275,7 @@ __device__ void sf_near(const SfArgs& a, SfShared& S, const SfScratch& Z, float 
                     total += wcnt[k];
                 }
                 const int pos = base + cnt + before + __popc(ball & ((1u << lane) - 1u));
-                if (near && pos < a.ncap) {
-                    Z.ni[pos] = i;
-                    Z.nl[pos] = l;
-                }
+                if (near && pos < a.ncap) Z.near[pos] = make_float4(p.x, p.y, p.z, l);
                 cnt += total;
                 __syncthreads();
             }
@@ -353,7 +350,8 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
         if (off >= 0) {
             for (int k = off + threadIdx.x; k < S.near_end[t]; k += blockDim.x) {
                 npair += (unsigned)(j1 - j0);
-                sf_newton_row(Z, j0, j1, a.p[Z.ni[k]], Z.nl[k], c, cg, sg, acc);
+                const float4 q = Z.near[k];
+                sf_newton_row(Z, j0, j1, q, q.w, c, cg, sg, acc);
             }
         } else {
             for (int i = a.I_off[t] + threadIdx.x; i < a.I_off[t + 1]; i += blockDim.x) {
@@ -434,8 +432,8 @@ __device__ void sf_columns(const SfArgs& a, SfShared& S, const SfScratch& Z, flo
             if (off >= 0) {
                 sf_column_sums(Z, j, S.near_end[t] - off, massonly, c,
                                [&](int k, float4& p, float& l) {
-                                   p = a.p[Z.ni[off + k]];
-                                   l = Z.nl[off + k];
+                                   p = Z.near[off + k];
+                                   l = p.w;
                                },
                                s0, s1, s2, npair);
             } else {

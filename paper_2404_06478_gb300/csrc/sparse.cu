@@ -272,34 +272,84 @@ __device__ __forceinline__ void sp_merge_parts(const float2* part, int k0, int k
 }
 
 // --------------------------------------------------------------- row pass
+// Each row is the sum of its support terms 2^(G_j - K e2 - shift) and the
+// outlier term, shifted by shift = max(largest G of the angle block, the
+// outlier exponent): every term is <= 1, so no running maximum is kept.  A row
+// whose shifted sum falls below kSpTiny is recomputed with the running maximum.
+// Eight lanes per row, four rows per warp; the lanes stride over the row's
+// records.
+constexpr float kSpTiny = 1.0e-30f;
+constexpr int kSpLanes = 8;  // lanes per spot
+
+__device__ float sp_row_exact(const SpArgs& a, int i, float dustv, bool ub) {
+    float m = kNegHuge, s = 0.0f;
+    if (!ub) acc_lse(m, s, dustv);
+    for (int e = a.rptr[i]; e < a.rptr[i + 1]; ++e) {
+        int2 v = a.rent[e];
+        acc_lse(m, s, a.G[v.x] + a.negK * __int_as_float(v.y));
+    }
+    return s > 0.0f ? m + lg2(s) : kNegHuge;
+}
+
+__device__ float sp_col_exact(const SpArgs& a, int j, float F0, bool ub) {
+    float m = kNegHuge, s = 0.0f;
+    if (!ub) acc_lse(m, s, F0);
+    const int2* ce = a.cent + (size_t)j * a.rho;
+    for (int k = 0; k < a.rho; ++k) {
+        int2 v = ce[k];
+        if (v.x >= 0) acc_lse(m, s, a.F[v.x] + a.negK * __int_as_float(v.y));
+    }
+    return s > 0.0f ? m + lg2(s) : kNegHuge;
+}
+
+// per-angle largest G of the starting potentials (one CTA per angle)
+__global__ void __launch_bounds__(256) sp_gmax_kernel(SpArgs a) {
+    __shared__ float red[8];
+    const int t = blockIdx.x;
+    float m = kNegHuge;
+    for (int j = a.J_off[t] + threadIdx.x; j < a.J_off[t + 1]; j += blockDim.x) m = fmaxf(m, a.G[j]);
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, red[k]);
+        a.gmax[t] = fmaxf(m, red[0]);
+    }
+}
+
 __global__ void __launch_bounds__(kSpThreads) sp_row_kernel(SpArgs a) {
     __shared__ float red_m[kSpWarps], red_s[kSpWarps];
     __shared__ int flag;
     const int nd = a.mode ? a.T : 1;
     SpDust D = sp_dust(a.dust, nd);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int grp = lane / kSpLanes, gl = lane % kSpLanes;
     const int n_tiles = a.rt_base[a.T];
-    float pm = kNegHuge, ps = 0.0f;  // lane 0 of each warp: LSE of F_i - kc over its rows
+    float pm = kNegHuge, ps = 0.0f;  // LSE of F_i - kc over this lane's rows
     if ((int)blockIdx.x < n_tiles) {
         const int4 td = a.rtile[blockIdx.x];
         const float dustv = D.G0[a.mode ? td.x : 0] - a.kc;
-        for (int i = td.y + w; i < td.z; i += kSpWarps) {
-            float m = kNegHuge, s = 0.0f;
-            for (int e = a.rptr[i] + lane; e < a.rptr[i + 1]; e += 32) {
-                int2 v = a.rent[e];
-                acc_lse(m, s, a.G[v.x] + a.negK * __int_as_float(v.y));
-            }
-            warp_lse_reduce(m, s);
-            if (lane == 0) {
-                Lse2 L{m, s};
-                L.merge(dustv, 1.0f);
-                float F = -L.value();
+        const float shift = fmaxf(a.gmax[td.x], dustv);
+        const float dterm = ex2(dustv - shift);
+        for (int ib = td.y + w * (32 / kSpLanes); ib < td.z; ib += kSpWarps * (32 / kSpLanes)) {
+            const int i = ib + grp;
+            const bool vr = i < td.z;
+            float sum = 0.0f;
+            if (vr)
+                for (int e = a.rptr[i] + gl; e < a.rptr[i + 1]; e += kSpLanes) {
+                    int2 v = a.rent[e];
+                    sum += ex2(a.G[v.x] + a.negK * __int_as_float(v.y) - shift);
+                }
+#pragma unroll
+            for (int o = kSpLanes / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (vr && gl == 0) {
+                sum += dterm;
+                float F = -(sum > kSpTiny ? shift + lg2(sum) : sp_row_exact(a, i, dustv, false));
                 a.F[i] = F;
                 acc_lse(pm, ps, F - a.kc);
             }
         }
     }
-    if (lane != 0) ps = 0.0f;
     sp_block_lse(pm, ps, red_m, red_s);
     if (threadIdx.x == 0 && (int)blockIdx.x < n_tiles) a.rpart[blockIdx.x] = make_float2(pm, ps);
     if (!sp_last(a.ctrl + CTRL_SP_DONE, &flag)) return;
@@ -315,6 +365,13 @@ __global__ void __launch_bounds__(kSpThreads) sp_row_kernel(SpArgs a) {
             D.G0[d] = D.log2O[d] - L.value();
         }
     }
+    // per-angle largest F for the column pass's shift (the tile partials keep max(F - kc))
+    for (int t = w; t < a.T; t += kSpWarps) {
+        float m = kNegHuge;
+        for (int k = a.rt_base[t] + lane; k < a.rt_base[t + 1]; k += 32) m = fmaxf(m, a.rpart[k].x);
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) a.fmax[t] = m > kNegHuge ? m + a.kc : kNegHuge;
+    }
 }
 
 // ------------------------------------------------------------ column pass
@@ -324,29 +381,35 @@ __global__ void __launch_bounds__(kSpThreads) sp_col_kernel(SpArgs a) {
     const int nd = a.mode ? a.T : 1;
     SpDust D = sp_dust(a.dust, nd);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int grp = lane / kSpLanes, gl = lane % kSpLanes;
     const int n_tiles = a.ct_base[a.T];
-    float pm = kNegHuge, ps = 0.0f;  // lane 0 of each warp: LSE of G_j over its columns
+    float pm = kNegHuge, ps = 0.0f;  // LSE of G_j over this lane's columns
     if ((int)blockIdx.x < n_tiles) {
         const int4 td = a.ctile[blockIdx.x];
         const float F0 = D.F0[a.mode ? td.x : 0];
-        for (int j = td.y + w; j < td.z; j += kSpWarps) {
-            const int2* ce = a.cent + (size_t)j * a.rho;
-            float m = kNegHuge, s = 0.0f;
-            for (int k = lane; k < a.rho; k += 32) {
-                int2 v = ce[k];
-                if (v.x >= 0) acc_lse(m, s, a.F[v.x] + a.negK * __int_as_float(v.y));
+        const float shift = fmaxf(a.fmax[td.x], F0);
+        const float dterm = ex2(F0 - shift);
+        for (int jb = td.y + w * (32 / kSpLanes); jb < td.z; jb += kSpWarps * (32 / kSpLanes)) {
+            const int j = jb + grp;
+            const bool vc = j < td.z;
+            float sum = 0.0f;
+            if (vc) {
+                const int2* ce = a.cent + (size_t)j * a.rho;
+                for (int k = gl; k < a.rho; k += kSpLanes) {
+                    int2 v = ce[k];
+                    if (v.x >= 0) sum += ex2(a.F[v.x] + a.negK * __int_as_float(v.y) - shift);
+                }
             }
-            warp_lse_reduce(m, s);
-            if (lane == 0) {
-                Lse2 L{m, s};
-                L.merge(F0, 1.0f);
-                float G = -L.value();
+#pragma unroll
+            for (int o = kSpLanes / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (vc && gl == 0) {
+                sum += dterm;
+                float G = -(sum > kSpTiny ? shift + lg2(sum) : sp_col_exact(a, j, F0, false));
                 a.G[j] = G;
                 acc_lse(pm, ps, G);
             }
         }
     }
-    if (lane != 0) ps = 0.0f;
     sp_block_lse(pm, ps, red_m, red_s);
     if (threadIdx.x == 0 && (int)blockIdx.x < n_tiles) a.cpart[blockIdx.x] = make_float2(pm, ps);
     if (!sp_last(a.ctrl + CTRL_SP_DONE, &flag)) return;
@@ -359,6 +422,13 @@ __global__ void __launch_bounds__(kSpThreads) sp_col_kernel(SpArgs a) {
             L.merge(D.G0[d] - a.kc, 1.0f);
             D.F0n[d] = D.log2U[d] - L.value();
         }
+    }
+    // per-angle largest G for the next row pass's shift (the tile partials keep max G)
+    for (int t = w; t < a.T; t += kSpWarps) {
+        float m = kNegHuge;
+        for (int k = a.ct_base[t] + lane; k < a.ct_base[t + 1]; k += 32) m = fmaxf(m, a.cpart[k].x);
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) a.gmax[t] = m;
     }
 }
 
@@ -523,6 +593,7 @@ size_t sparse_workspace_bytes(int T, int n_obs, int n_model, int rho) {
     add(sizeof(int4) * sp_max_tiles(n_obs, T));      // rtile
     add(sizeof(int4) * sp_max_tiles(n_model, T));    // ctile
     add(sizeof(int) * 2 * ((size_t)T + 1));          // rt_base, ct_base
+    add(sizeof(float) * 2 * ((size_t)T + 1));        // gmax, fmax
     return b;
 }
 
@@ -547,6 +618,8 @@ void sparse_carve(SpArgs& a, char* base, int T, int n_obs, int n_model, int rho)
     a.ctile = (int4*)take(sizeof(int4) * sp_max_tiles(n_model, T));
     a.rt_base = (int*)take(sizeof(int) * 2 * ((size_t)T + 1));
     a.ct_base = a.rt_base + T + 1;
+    a.gmax = (float*)take(sizeof(float) * 2 * ((size_t)T + 1));
+    a.fmax = a.gmax + T + 1;
     a.max_rt = (int)sp_max_tiles(n_obs, T);
     a.max_ct = (int)sp_max_tiles(n_model, T);
 }
@@ -574,6 +647,7 @@ cudaError_t sparse_sinkhorn_run(const SpArgs& a, int n_iter, bool rows, bool col
     const int blocks = std::max(1, (std::max(a.n_obs, a.n_model) + 255) / 256);
     sp_init_pot_kernel<<<blocks, 256, 0, s>>>(a);
     sp_init_dust_kernel<<<nd, 1024, 0, s>>>(a);
+    if (a.T > 0) sp_gmax_kernel<<<a.T, 256, 0, s>>>(a);
     for (int it = 0; it < n_iter; ++it) {
         sp_row_kernel<<<a.max_rt, kSpThreads, 0, s>>>(a);
         sp_col_kernel<<<a.max_ct, kSpThreads, 0, s>>>(a);
