@@ -84,6 +84,19 @@ __global__ void sp_schedule_kernel(SpArgs a) {
 }
 
 // ------------------------------------------------------------- neighbours
+// Inserts (i, v) into the sorted list L of n <= rho entries (an equal e2 goes
+// after: its index is larger); worst becomes the largest kept e2 once the list
+// is full.
+__device__ __forceinline__ void knn_insert(int2* L, int rho, int& n, float& worst, int i, float v) {
+    int q = n < rho ? n++ : rho - 1;
+    while (q > 0 && __int_as_float(L[q - 1].y) > v) {
+        L[q] = L[q - 1];
+        --q;
+    }
+    L[q] = make_int2(i, __float_as_int(v));
+    if (n == rho) worst = __int_as_float(L[rho - 1].y);
+}
+
 // One thread per model spot (column tiles): the rho smallest e2 over its
 // block's observed spots in shared memory, kept sorted by (e2, index).
 __global__ void __launch_bounds__(kKnnThreads) sp_knn_kernel(SpArgs a) {
@@ -95,16 +108,19 @@ __global__ void __launch_bounds__(kKnnThreads) sp_knn_kernel(SpArgs a) {
     for (int j = td.y + threadIdx.x; j < td.z; j += kKnnThreads) {
         const float4 c = a.c[j], r = a.r[j];
         int n = 0;
-        for (int i = i0; i < i1; ++i) {
+        float worst = 3.0e38f;  // the list's largest e2 once it holds rho entries
+        int i = i0;
+        for (; i + 4 <= i1; i += 4) {  // four independent costs, then the rare insertions in index order
+            float v0 = sp_e2(a.p[i], c, r), v1 = sp_e2(a.p[i + 1], c, r);
+            float v2 = sp_e2(a.p[i + 2], c, r), v3 = sp_e2(a.p[i + 3], c, r);
+            if (v0 < worst) knn_insert(L, a.rho, n, worst, i, v0);
+            if (v1 < worst) knn_insert(L, a.rho, n, worst, i + 1, v1);
+            if (v2 < worst) knn_insert(L, a.rho, n, worst, i + 2, v2);
+            if (v3 < worst) knn_insert(L, a.rho, n, worst, i + 3, v3);
+        }
+        for (; i < i1; ++i) {
             float v = sp_e2(a.p[i], c, r);
-            // insertion into the sorted list; an equal e2 goes after (its index is larger)
-            if (n == a.rho && !(v < __int_as_float(L[n - 1].y))) continue;
-            int q = n < a.rho ? n++ : a.rho - 1;
-            while (q > 0 && __int_as_float(L[q - 1].y) > v) {
-                L[q] = L[q - 1];
-                --q;
-            }
-            L[q] = make_int2(i, __float_as_int(v));
+            if (v < worst) knn_insert(L, a.rho, n, worst, i, v);
         }
         const int det = a.s ? (int)a.s[j].w : -1;
         const float kd = (det >= 0 && det < a.n_det) ? a.kdet[det] : 1.0f;
