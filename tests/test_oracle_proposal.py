@@ -332,3 +332,47 @@ def test_training_scene_noise_statistics(planes):
     d = np.array(d)
     assert len(d) > 0.95 * len(p1)
     assert abs(d.mean()) < 0.05 and d.std() == pytest.approx(0.5, rel=0.05)
+
+
+def test_bf16_mode_equals_exact_mode_when_no_rounding_occurs():
+    """The BF16 data path (operands, activations and back-propagated errors of
+    the per-spot layers rounded to BF16) is the FP64 path with rounding points
+    added.  On a network and sets whose every per-spot quantity has few
+    significant bits (signed permutation weights, dyadic inputs, biases and head
+    weights, 8 valid spots per set) no rounding changes a value, so both modes
+    give the same outputs and the same gradients bit for bit; the FP64 mode is
+    itself pinned by finite differences above."""
+    rng = np.random.default_rng(29)
+    B = 3
+    P = {}
+    for name, shape in op.PARAM_SHAPES:
+        P[name] = np.zeros(shape)
+    # per-spot layers: one signed power-of-two entry per row
+    P["W1"][np.arange(op.WIDTH), rng.integers(0, 14, op.WIDTH)] = rng.choice([-1.0, 1.0, 0.5], op.WIDTH)
+    for name in ("W2", "W3"):
+        perm = rng.permutation(op.WIDTH)
+        P[name][np.arange(op.WIDTH), perm] = rng.choice([-1.0, 1.0], op.WIDTH)
+    for name in ("b1", "b2", "b3"):
+        P[name] = rng.integers(-2, 3, op.WIDTH) / 16.0
+    # head (FP32 in both modes): one dyadic entry per column, so that the errors
+    # sent back into the per-spot layers keep few significant bits as well
+    for name in ("W4", "W5"):
+        rows, cols = P[name].shape
+        P[name][rng.integers(0, rows, cols), np.arange(cols)] = rng.choice([-0.25, -0.125, 0.125, 0.25], cols)
+    P["b4"] = rng.integers(0, 3, P["b4"].shape) / 8.0
+    X = np.zeros((B, op.KSET, op.NF))
+    X[:, :, :14] = rng.integers(-8, 9, (B, op.KSET, 14)) / 16.0
+    X[:, :, 12] = 0.0
+    X[:, :8, 12] = 1.0  # 8 valid spots per set: the mean divides by a power of two
+    O64, c64 = op.forward(P, X, bf16_ops=False)
+    O16, c16 = op.forward(P, X, bf16_ops=True)
+    np.testing.assert_array_equal(O16, O64)
+    for k in ("H1", "H2", "H3"):
+        np.testing.assert_array_equal(c16[k], c64[k])
+    assert np.count_nonzero(c64["H3"]) > 0.2 * c64["H3"].size
+    dO = rng.integers(-4, 5, O64.shape) / 64.0
+    G64 = op.backward(P, c64, dO)
+    G16 = op.backward(P, c16, dO)
+    for k in G64:
+        np.testing.assert_array_equal(G16[k], G64[k], err_msg=k)
+    assert all(np.count_nonzero(G64[k]) > 0 for k in ("W1", "W2", "W3"))
