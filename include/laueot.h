@@ -353,8 +353,8 @@ int laue_cost_sinkhorn_noalloc(const LaueGeometry* geom, const LaueObsSpots* obs
 
 /* Autotuner of the pair passes (no counterpart in the paper): times each
  * launch shape of the row and column passes of laue_cost_sinkhorn on this
- * problem (shape v: {256, 128, 128 with a 128-register cap, 128 with a
- * 64-register cap} threads per CTA, one row/column pair per thread; the tile
+ * problem (shape v: {256, 128, 128 with a 128-register cap, 64 with a
+ * 128-register cap} threads per CTA, one row/column pair per thread; the tile
  * size follows the CTA width), n_iter passes each after one warm-up
  * iteration, and keeps the fastest row and column shapes in the handle for
  * later calls.  choice_host (optional, 2 ints): the chosen row and column

@@ -1066,11 +1066,11 @@ cudaError_t sinkhorn_prepare(const SkArgs& a, cudaStream_t s) {
 // {threads per CTA (= pairs per tile), minimum resident CTAs per SM}.
 typedef void (*SkKernel)(SkArgs);
 static const SkKernel kRowKernels[kSkVariants] = {sk_row_kernel<256, 1>, sk_row_kernel<128, 1>, sk_row_kernel<128, 4>,
-                                                  sk_row_kernel<128, 8>};
+                                                  sk_row_kernel<64, 8>};
 static const SkKernel kColKernels[kSkVariants] = {sk_col_kernel<256, 1>, sk_col_kernel<128, 1>, sk_col_kernel<128, 4>,
-                                                  sk_col_kernel<128, 8>};
+                                                  sk_col_kernel<64, 8>};
 
-int sk_variant_threads(int v) { return v == 0 ? 256 : 128; }
+int sk_variant_threads(int v) { return v == 0 ? 256 : (v == 3 ? 64 : 128); }
 
 void sinkhorn_row_pass(const SkArgs& a, const SkLaunch& l, cudaStream_t s) {
     kRowKernels[l.row_variant]<<<l.row_grid, sk_variant_threads(l.row_variant), 0, s>>>(a);

@@ -231,8 +231,8 @@ def test_sinkhorn_full_size_global_rows_and_marginals(env, batched):
 
 @pytest.mark.parametrize("shape", [0, 1, 2, 3])
 def test_sinkhorn_every_launch_shape(env, shape):
-    """Each launch shape of the autotuner (CTA width 256/128, with and without
-    the 64-register cap) gives the same results."""
+    """Each launch shape of the autotuner (CTA width 256, 128 or 64 spot
+    pairs, with and without a register cap) gives the same results."""
     case = make_case(sg.CONFIGS["medium"], seed=12, n_grains=60, T=8)
     env["h"].set_launch_shape(shape, (shape + 1) % 4)
     try:
