@@ -377,8 +377,8 @@ int laue_read_counters(laue_handle* h, void* stream, long long* counts_host, int
 
 /* Exact underflow skipping in the Sinkhorn pair passes (no counterpart in the
  * paper; on by default): within each angle block the spots are ordered by
- * direction, each run of 64 pairs (half a staged chunk of 128) carries a
- * cone bounding its directions, and a pass skips a (tile, half chunk)
+ * direction, each run of 32 pairs (a quarter of a staged chunk of 128)
+ * carries a cone bounding its directions, and a pass skips a (tile, granule)
  * combination when the cones prove that every shifted exponent is below
  * -130, i.e. every plan entry flushes to exactly 0; the potentials are
  * bit-identical either way.  enable = 0 turns
@@ -411,7 +411,7 @@ int laue_cost_sinkhorn_sparse(laue_handle* h, const LaueGeometry* geom, const La
                               int* nbr, void* stream);
 
 /* Sets the launch shapes (0..3, as for laue_autotune) of the row and column
- * passes used by later calls on the handle; shape 0 is the default. */
+ * passes used by later calls on the handle; shape 3 is the default. */
 int laue_set_launch_shape(laue_handle* h, int row_shape, int col_shape);
 
 /* M-step (paper Section "The M-step updates", Appendix "M-steps"): with the

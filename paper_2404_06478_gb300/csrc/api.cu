@@ -142,7 +142,7 @@ extern "C" int laue_create(laue_handle** h, int device) {
     if (sinkhorn_occupancy(H->row_occ, H->col_occ) != 0)
         for (int v = 0; v < kSkVariants; ++v) H->row_occ[v] = H->col_occ[v] = 1;
     cudaSetDevice(prev);
-    H->row_variant = H->col_variant = 0;
+    H->row_variant = H->col_variant = kSkDefaultVariant;
     H->skip = 1;
     H->err[0] = 0;
     *h = H;

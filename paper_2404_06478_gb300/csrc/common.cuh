@@ -118,8 +118,8 @@ inline Layout make_layout(const LaueProblemDims& d, int sm_count) {
     size_t nsp = (size_t)d.n_obs + d.n_model + 2;
     L.perm = take(sizeof(int) * 2 * nsp);
     L.sortbuf = take(sizeof(int) * 4 * nsp);
-    L.max_obs_gran = (int)((ip + 63) / 64) + T + 1;  // cone granules of 64 pairs
-    L.max_mod_gran = (int)((jp + 63) / 64) + T + 1;
+    L.max_obs_gran = (int)((ip + 31) / 32) + T + 1;  // cone granules of 32 pairs
+    L.max_mod_gran = (int)((jp + 31) / 32) + T + 1;
     L.cone = take((sizeof(float4) + sizeof(float)) * (size_t)(L.max_obs_gran + L.max_mod_gran) + 64);
     L.fwd_blocks = take(sizeof(int) * (size_t)(2 * L.max_fwd_blocks + 2));
     L.jsum = take(sizeof(float) * 12 * (size_t)(d.n_model + 1));

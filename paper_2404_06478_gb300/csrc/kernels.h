@@ -174,7 +174,8 @@ size_t sparse_workspace_bytes(int T, int n_obs, int n_model, int rho);
 void sparse_carve(SpArgs& a, char* base, int T, int n_obs, int n_model, int rho);
 cudaError_t sparse_sinkhorn_run(const SpArgs& a, int n_iter, bool rows, bool cols, cudaStream_t s);
 
-constexpr int kSkVariants = 4;  // launch shapes of the pair passes (see sinkhorn.cu)
+constexpr int kSkVariants = 4;       // launch shapes of the pair passes (see sinkhorn.cu)
+constexpr int kSkDefaultVariant = 3;  // 64-pair tiles: the autotuner's usual pick
 
 struct SkLaunch {
     int row_grid, col_grid, hrv_grid, hcol_grid;

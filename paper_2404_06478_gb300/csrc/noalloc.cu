@@ -89,7 +89,7 @@ extern "C" int laue_cost_sinkhorn_noalloc(const LaueGeometry* geom, const LaueOb
         h.row_occ[v] = d->row_occ[v];
         h.col_occ[v] = d->col_occ[v];
     }
-    h.row_variant = h.col_variant = 0;
+    h.row_variant = h.col_variant = kSkDefaultVariant;
     h.skip = 1;
     h.ws = d->scratch;
     h.ws_bytes = kStaticScratchBytes;

@@ -11,7 +11,8 @@ namespace laue {
 
 constexpr int kTPB = 256;     // widest CTA of the pair passes (one row/column pair per thread)
 constexpr int kChunk = 128;   // staged pairs per chunk (256 spots)
-constexpr int kGran = 64;     // pairs per cone granule of the exact skipping (half a chunk)
+constexpr int kGran = 32;     // pairs per cone granule of the exact skipping
+constexpr int kParts = kChunk / kGran;  // granules per staged chunk
 constexpr int kGroup = 4;     // staged pairs per max-then-sum group
 constexpr float kPadFar = 1.0e6f;
 
@@ -228,7 +229,7 @@ __device__ __forceinline__ bool stream_list_prep(Stage& S, uint32_t (&parity)[2]
 }
 
 // ------------------------------------- exact underflow skipping (cone bounds)
-// A granule is kGran pairs of one angle block (half a staged chunk); its
+// A granule is kGran pairs of one angle block (a quarter of a staged chunk); its
 // cone bounds the directions of its spots: for observed spots
 // the unit vectors p / |p| and the smallest |p|, for model spots the rays r
 // and the largest |c|.  For an observed cone O and a model cone M, every pair
@@ -286,7 +287,7 @@ __device__ __forceinline__ float min_scaled_cost(const Cone& O, const Cone& M, f
 // bit-identical with or without the pair.
 constexpr float kSkipLog2 = 130.0f;
 
-// Ordered list (in Stage::list) of the chunks c < nch whose half mask
+// Ordered list (in Stage::list) of the chunks c < nch whose granule mask
 // need(c) (bit h: granule h of the chunk can hold a plan entry) is nonzero,
 // each entry c | mask << 24; returns its length.  All threads of the CTA call it.
 template <class Need>
@@ -312,10 +313,30 @@ __device__ __forceinline__ int build_chunk_list(Stage& S, int nch, Need need) {
     return base;
 }
 
-// Pairs of the halves of chunk ch selected by mask (n_total pairs in the block).
+// Pairs of the granules of chunk ch selected by mask (n_total pairs in the block).
 __device__ __forceinline__ int list_pairs(int ch, int mask, int n_total) {
-    int n = min(kChunk, n_total - ch * kChunk);
-    return ((mask & 1) ? min(kGran, n) : 0) + ((mask & 2) ? max(0, n - kGran) : 0);
+    int n = min(kChunk, n_total - ch * kChunk), np = 0;
+    for (int q = 0; q < kParts; ++q)
+        if ((mask >> q) & 1) np += max(0, min(kGran, n - q * kGran));
+    return np;
+}
+
+// Calls run(first, count) for each maximal run of selected granules of a
+// staged chunk of n pairs (mask bit q: granule q).
+template <class Run>
+__device__ __forceinline__ void for_each_run(int mask, int n, Run run) {
+    int q = 0;
+    while (q < kParts) {
+        if (!((mask >> q) & 1)) {
+            ++q;
+            continue;
+        }
+        int q1 = q;
+        while (q1 + 1 < kParts && ((mask >> (q1 + 1)) & 1)) ++q1;
+        const int h = q * kGran, e = min(n, (q1 + 1) * kGran);
+        if (e > h) run(h, e - h);
+        q = q1 + 1;
+    }
 }
 
 // Cone of the tile's own spots [first, first + count) pairs of a block whose

@@ -588,12 +588,12 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
                 y.w -= shift;
             }
         };
-        // the halves (granules) of a staged chunk selected by mask
-        auto body = [&](int st, int n, int, int mask = 3) {
+        // the granules of a staged chunk selected by mask
+        auto body = [&](int st, int n, int, int mask = (1 << kParts) - 1) {
             if (!valid) return;
-            const int h = (mask & 1) ? 0 : kGran, e = (mask & 2) ? n : min(n, kGran);
-            if (e > h)
-                row_chunk_sum(R, S.s[0][st] + h, S.s[1][st] + h, S.s[2][st] + h, S.s[3][st] + h, e - h, Sa, Sb);
+            for_each_run(mask, n, [&](int h, int m) {
+                row_chunk_sum(R, S.s[0][st] + h, S.s[1][st] + h, S.s[2][st] + h, S.s[3][st] + h, m, Sa, Sb);
+            });
         };
         // the model granules this tile of observed spots can see (exact underflow skipping)
         const int nch = (nj + kChunk - 1) / kChunk;
@@ -605,9 +605,9 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
             const int mg = a.mod_gbase[t], ng = (nj + kGran - 1) / kGran;
             n_list = build_chunk_list(S, nch, [&](int c) {
                 int m = 0;
-                for (int hh = 0; hh < 2; ++hh)
-                    if (2 * c + hh < ng &&
-                        min_scaled_cost(O, load_cone(a.mod_cone, a.mod_ext, mg + 2 * c + hh), K) <= kSkipLog2)
+                for (int hh = 0; hh < kParts; ++hh)
+                    if (kParts * c + hh < ng &&
+                        min_scaled_cost(O, load_cone(a.mod_cone, a.mod_ext, mg + kParts * c + hh), K) <= kSkipLog2)
                         m |= 1 << hh;
                 return m;
             });
@@ -714,10 +714,9 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
                 y.w -= shift;
             }
         };
-        auto body = [&](int st, int n, int, int mask = 3) {
+        auto body = [&](int st, int n, int, int mask = (1 << kParts) - 1) {
             if (!valid) return;
-            const int h = (mask & 1) ? 0 : kGran, e = (mask & 2) ? n : min(n, kGran);
-            if (e > h) col_chunk_sum(C, S.s[0][st] + h, S.s[1][st] + h, e - h, Sa, Sb);
+            for_each_run(mask, n, [&](int h, int m) { col_chunk_sum(C, S.s[0][st] + h, S.s[1][st] + h, m, Sa, Sb); });
         };
         // the observed granules this tile of model spots can see (exact underflow skipping)
         const int nch = (ni + kChunk - 1) / kChunk;
@@ -729,9 +728,9 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
             const int og = a.obs_gbase[t], ng = (ni + kGran - 1) / kGran;
             n_list = build_chunk_list(S, nch, [&](int c) {
                 int m = 0;
-                for (int hh = 0; hh < 2; ++hh)
-                    if (2 * c + hh < ng &&
-                        min_scaled_cost(load_cone(a.obs_cone, a.obs_ext, og + 2 * c + hh), M, K) <= kSkipLog2)
+                for (int hh = 0; hh < kParts; ++hh)
+                    if (kParts * c + hh < ng &&
+                        min_scaled_cost(load_cone(a.obs_cone, a.obs_ext, og + kParts * c + hh), M, K) <= kSkipLog2)
                         m |= 1 << hh;
                 return m;
             });

@@ -238,7 +238,7 @@ def test_sinkhorn_every_launch_shape(env, shape):
     try:
         gpu, ref, eps = _run_both(env, case, 40, mode=shape % 2, cols=True)
     finally:
-        env["h"].set_launch_shape(0, 0)
+        env["h"].set_launch_shape(3, 3)
     _check(gpu, ref, eps)
 
 
@@ -315,11 +315,10 @@ def test_sinkhorn_skipping_is_bit_identical(env, eps, mode):
     run of 128 pairs) changes no bit of the potentials, the dustbins or the
     read-out.  Workload: the 1000-grain density on 4 angles (about 14k
     observed and 8k model spots per block, so a tile's cone spans a few degrees
-    of a detector).  At eps <= 1 mm^2 a host model of the cone bounds (64-pair
-    granules, 256-pair tiles) predicts that the row pass skips 53-55% of its
-    pairs; the column pass, whose 256-pair model tiles have wider cones, skips
-    fewer (about 40% of both passes' pairs are skipped); at eps = 2000 none
-    can be."""
+    of a detector).  At eps <= 1 mm^2 a host model of the cone bounds (32-pair
+    granules, the default 64-pair tiles) predicts that the row pass keeps about
+    a quarter of its pairs, and the column pass keeps somewhat more; at
+    eps = 2000 none can be skipped."""
     api, torch = env["api"], env["torch"]
     case = make_case(sg.CONFIGS["batched"], seed=0, T=4)
     ob, ms = to_device(case, env["dev"])
@@ -344,6 +343,6 @@ def test_sinkhorn_skipping_is_bit_identical(env, eps, mode):
     dense = 2 * 30 * int(np.sum((nI + nI % 2) * (nJ + nJ % 2)))
     assert pa == dense
     if eps <= 1.0:
-        assert pb < 0.65 * pa, (pb, pa)
+        assert pb < 0.5 * pa, (pb, pa)
     else:
         assert pb == pa
