@@ -67,7 +67,7 @@ struct Layout {
     size_t pairoff;               // int: I2_off[T+1], J2_off[T+1] (pair offsets), granule bases (2 x (T+1))
     size_t perm;                  // int: observed and model sort permutations (order -> caller, caller -> order)
     size_t sortbuf;               // sort keys and indices (two buffers each)
-    size_t cone;                  // float4 + float per granule of kChunk pairs, observed then model
+    size_t cone;                  // float4 + float per granule of 32 pairs, observed then model
     size_t fwd_blocks;            // int per forward block (count, then offset)
     size_t jsum;                  // float per model spot x 12 (M-step sums)
     size_t gsum;                  // float per grain x 16

@@ -84,7 +84,7 @@ struct SkArgs {
     int *obs_perm, *obs_pos, *mod_perm, *mod_pos;
     unsigned* sort_key;    // 2 (n_obs + n_model) keys (ping-pong)
     int* sort_idx;         // 2 (n_obs + n_model) indices
-    // cones of the granules (kChunk pairs of one block) for the exact skipping
+    // cones of the granules (kGran pairs of one block) for the exact skipping
     float4 *obs_cone, *mod_cone;
     float *obs_ext, *mod_ext;
     int *obs_gbase, *mod_gbase;  // T+1 first granule of each block
