@@ -610,17 +610,20 @@ int laue_em(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, co
 
 /* BF16 GEMM on the tcgen05 tensor cores: D[m][n] = sum_k A[m][k] B[n][k].
  * A: M x K BF16, row-major with leading dimension lda (elements); B: N x K
- * BF16 with ldb.  M % 128 == 0, N % bn == 0 with bn in {64, 128, 256},
- * K % 64 == 0, (K / 64) % splits == 0, lda, ldb % 8 == 0, all pointers
- * 16-byte aligned.  mode 0: D_f32 receives `splits` FP32 partial products
+ * BF16 with ldb.  flags bit 1: A is stored MN-major instead, as the K x M
+ * array A^T (element (m, k) at A[k lda + m], lda >= M); flags bit 2: B is
+ * stored as the K x N array B^T (ldb >= N).  M % 128 == 0, N % bn == 0 with
+ * bn in {64, 128, 256}, K % 64 == 0, (K / 64) % splits == 0, lda, ldb % 8 ==
+ * 0, all pointers 16-byte aligned.  mode 0: D_f32 receives `splits` FP32 partial products
  * (split s covers K range [s K/splits, (s+1) K/splits)) at D_f32 + s M N,
  * row-major M x N.  mode 1: relu(acc + bias[n]) rounded to BF16 (nearest
  * even) into D_bf16 (M x N row-major) and/or DT_bf16 (N rows of leading
  * dimension ldt >= M: DT[n][m]); splits must be 1.  mode 2: acc where the
  * BF16 mask[m][n] (M x N row-major) is > 0, else 0, same outputs.
- * Modes 1 and 2 with N = 256, K in {64, 256} run a persistent,
- * warp-specialised kernel (weights resident in shared memory, two tensor-
- * memory accumulators); flags bit 0 forces the one-tile-per-CTA kernel.
+ * Modes 1 and 2 with N = 256, K in {64, 256} and both operands K-major run
+ * a persistent, warp-specialised kernel (weights resident in shared memory,
+ * two tensor-memory accumulators); flags bit 0 forces the one-tile-per-CTA
+ * kernel.
  * Asynchronous on `stream`; device memory is the caller's.  Needs the
  * workspace (status word).  Errors: LAUE_ERR_INVALID_ARG for shapes,
  * alignment or a missing output. */
@@ -638,7 +641,7 @@ int laue_gemm_bf16(laue_handle* h, const void* A, long long lda, const void* B, 
  * arrays); both 256-byte aligned and owned by the caller.
  * laue_lp_batch_offset(n_sets, region) is the byte offset of a region of
  * the batch buffer (-1 if unknown): 0 X (n_sets*set_size x 64 BF16 features),
- * 1 X^T, 2 seed frames F (n_sets x 9 FP32, row-major, columns n0 a1 a2),
+ * 1 unused (-1), 2 seed frames F (n_sets x 9 FP32, row-major, columns n0 a1 a2),
  * 3 valid elements per set (int), 4 R_loc targets (n_sets x 9), 5 position
  * targets (n_sets x 3, x / 2.5 mm), 6 set valid flags (FP32), 7 network
  * outputs O (n_sets x 72: 8 hypotheses of 6-D rotation + 3-D position),

@@ -23,10 +23,11 @@ What it computes is fixed here, in plain numpy:
 * The network.  A per-spot MLP of three 256-wide ReLU layers, masked mean and
   max pooling over the set, a two-layer head that emits NHYP hypotheses of
   (6-D rotation, 3-D position).  The 6-D output is turned into a rotation by
-  Gram-Schmidt.  The per-spot layers are BF16 with FP32 accumulation on the
-  GPU; with ``bf16=True`` this oracle rounds the same operands (weights of the
-  per-spot layers, their activations and their back-propagated errors) to
-  BF16 and accumulates in FP64.
+  Gram-Schmidt.  Every layer (the per-spot layers and the head) is BF16 with
+  FP32 accumulation on the GPU; with ``bf16=True`` this oracle rounds the
+  same operands (all weights, the per-spot activations, the pooled features,
+  the head's hidden activations and the back-propagated errors the GEMMs
+  read) to BF16 and accumulates in FP64.
 * The loss.  Per set and hypothesis the cubic-symmetry-aware rotation error
   min_S ||Rhat - R_loc S||_F^2 (S over the 24 proper rotations of the cube,
   R_loc = F0^T R) plus LAMBDA_X ||xhat - x / XSCALE||^2; the set loss is the
@@ -178,7 +179,7 @@ def set_targets(F, R, x):
 PARAM_SHAPES = [("W1", (WIDTH, NF)), ("b1", (WIDTH,)), ("W2", (WIDTH, WIDTH)), ("b2", (WIDTH,)),
                 ("W3", (WIDTH, WIDTH)), ("b3", (WIDTH,)), ("W4", (HEAD, 2 * WIDTH)), ("b4", (HEAD,)),
                 ("W5", (NOUT, HEAD)), ("b5", (NOUT,))]
-SPOT_LAYERS = ("W1", "W2", "W3")  # BF16 operands on the GPU
+BF16_WEIGHTS = ("W1", "W2", "W3", "W4", "W5")  # BF16 operands on the GPU
 
 
 def init_params(rng):
@@ -205,7 +206,7 @@ def forward(P, X, bf16_ops=True):
     B = X.shape[0]
     valid = X[:, :, 12] > 0.5
     x0 = rnd(X.reshape(B * KSET, NF))
-    W = {k: (rnd(P[k]) if k in SPOT_LAYERS else P[k]) for k in P}
+    W = {k: (rnd(P[k]) if k in BF16_WEIGHTS else P[k]) for k in P}
     Z1 = x0 @ W["W1"].T + P["b1"]
     H1 = rnd(_relu(Z1))
     Z2 = H1 @ W["W2"].T + P["b2"]
@@ -219,10 +220,10 @@ def forward(P, X, bf16_ops=True):
     amax = np.argmax(masked, axis=1)  # first index on ties
     mx = np.take_along_axis(H3s, amax[:, None, :], 1)[:, 0, :]
     mx = np.where(nv[:, None] > 0, mx, 0.0)
-    Pool = np.concatenate([mean, mx], 1)
-    Z4 = Pool @ P["W4"].T + P["b4"]
-    H4 = _relu(Z4)
-    O = H4 @ P["W5"].T + P["b5"]
+    Pool = rnd(np.concatenate([mean, mx], 1))
+    Z4 = Pool @ W["W4"].T + P["b4"]
+    H4 = rnd(_relu(Z4))
+    O = H4 @ W["W5"].T + P["b5"]
     cache = dict(x0=x0, W=W, H1=H1, H2=H2, H3=H3, valid=valid, nv=nv, amax=amax, Pool=Pool, Z4=Z4, H4=H4,
                  bf16_ops=bf16_ops)
     return O, cache
@@ -289,18 +290,20 @@ def set_loss(O, Rloc, xt, set_valid):
 
 def backward(P, cache, dO):
     """Gradients of all parameters given dL/dO.  With bf16 operands the
-    back-propagated errors of the per-spot layers are rounded to BF16 (as the
-    GPU stores them) and every product accumulates in FP64."""
+    back-propagated errors that a GEMM reads are rounded to BF16 (as the GPU
+    stores them; the output bias takes dL/dO unrounded) and every product
+    accumulates in FP64."""
     rnd = bf16 if cache["bf16_ops"] else (lambda a: np.asarray(a, np.float64))
     W = cache["W"]
     G = {}
     H4, Z4, Pool = cache["H4"], cache["Z4"], cache["Pool"]
-    G["W5"] = dO.T @ H4
+    dOr = rnd(dO)
+    G["W5"] = dOr.T @ H4
     G["b5"] = dO.sum(0)
-    dZ4 = (dO @ P["W5"]) * (Z4 > 0)
+    dZ4 = rnd((dOr @ W["W5"]) * (Z4 > 0))
     G["W4"] = dZ4.T @ Pool
     G["b4"] = dZ4.sum(0)
-    dPool = dZ4 @ P["W4"]
+    dPool = dZ4 @ W["W4"]
     B = dO.shape[0]
     valid, nv, amax = cache["valid"], cache["nv"], cache["amax"]
     dH3 = valid[:, :, None] * (dPool[:, None, :WIDTH] / np.maximum(nv, 1)[:, None, None])

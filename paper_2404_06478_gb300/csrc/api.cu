@@ -540,8 +540,9 @@ int laue_fill_sk(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* o
     int ct = std::max(1, std::min(h->sm_count * h->col_occ[h->col_variant], L.max_col_tiles));
     lc->row_grid = rt;
     lc->col_grid = ct;
-    lc->hrv_grid = std::max(1, std::min(h->sm_count * 3, L.max_row_tiles));
-    lc->hcol_grid = std::max(1, std::min(h->sm_count * 3, L.max_col_tiles));
+    // harvest passes: CTAs as wide as the tiles, about 768 threads per SM
+    lc->hrv_grid = std::max(1, std::min(h->sm_count * (768 / a.tile_rows), L.max_row_tiles));
+    lc->hcol_grid = std::max(1, std::min(h->sm_count * (768 / a.tile_cols), L.max_col_tiles));
     return LAUE_OK;
 }
 

@@ -2,7 +2,12 @@
 // (tcgen05) for the per-spot layers of the set encoder, with the epilogues
 // the encoder's forward and backward passes need fused in.
 //
-//   D[m][n] = sum_k A[m][k] B[n][k]     (both operands K-contiguous, "TN")
+//   D[m][n] = sum_k A[m][k] B[n][k]
+//
+// Each operand is either K-contiguous (A[m][k], B[n][k]) or MN-contiguous
+// (A stored as [k][m], B as [k][n]); the second form lets the weight
+// gradients dW = dZ^T H read the activations and errors in the row-major
+// layout the forward and backward layers write, with no transposed copies.
 //
 // One CTA computes one 128 x BN tile (BN = 64, 128 or 256) over a range of K
 // (split-K along gridDim.z).  Warp 0, lane 0 streams 128 x 64 and BN x 64
@@ -50,11 +55,28 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor of an MN-major operand tile with the
+// 128-byte swizzle.  TMA writes each 64-element (128-byte) MN slice of the
+// tile as kBK rows of 128 bytes, one row per k, slices kMnSlice bytes apart:
+// 8-row (8 k) core groups 1024 bytes apart (stride byte offset) and the
+// 64-element MN repeats kMnSlice bytes apart (leading byte offset).
+constexpr uint32_t kMnSlice = 64u * kBK * 2;  // one 64-wide MN slice of a stage
+__device__ __forceinline__ uint64_t sdesc_mn128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((kMnSlice >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1),
-// BF16 A and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// BF16 A and B (bits 7-9, 10-12 = 1), A and B major-ness (bits 15, 16:
+// 0 K-major, 1 MN-major), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N, int a_mn = 0, int b_mn = 0) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a_mn & 1) << 15) | ((uint32_t)(b_mn & 1) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -197,12 +219,22 @@ __global__ void __launch_bounds__(kThreads, kStages == 2 ? 2 : 1)
             }
             mbar_expect_tx(&full[s], kAStage + bStage);
             int kx = (kb0 + kb) * kBK;
-            tma_load_2d(sA + s * kAStage, &tmA, kx, m0, &full[s]);
-            tma_load_2d(sB + s * bStage, &tmB, kx, n0, &full[s]);
+            if (a.a_mn) {
+                for (int j = 0; j < kBM / 64; ++j)
+                    tma_load_2d(sA + s * kAStage + j * kMnSlice, &tmA, m0 + 64 * j, kx, &full[s]);
+            } else {
+                tma_load_2d(sA + s * kAStage, &tmA, kx, m0, &full[s]);
+            }
+            if (a.b_mn) {
+                for (int j = 0; j < BN / 64; ++j)
+                    tma_load_2d(sB + s * bStage + j * kMnSlice, &tmB, n0 + 64 * j, kx, &full[s]);
+            } else {
+                tma_load_2d(sB + s * bStage, &tmB, kx, n0, &full[s]);
+            }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        const uint32_t idesc = idesc_bf16(kBM, BN);
+        const uint32_t idesc = idesc_bf16(kBM, BN, a.a_mn, a.b_mn);
         for (int kb = 0; kb < nkb; ++kb) {
             int s = kb % kStages;
             uint32_t ph = (uint32_t)(kb / kStages) & 1u;
@@ -212,10 +244,14 @@ __global__ void __launch_bounds__(kThreads, kStages == 2 ? 2 : 1)
             }
             tc_fence_after();
             uint32_t aBase = smem_u32(sA + s * kAStage), bBase = smem_u32(sB + s * bStage);
+            // K = 16 per instruction: 32 bytes along a K-major row, or two
+            // 8-row core groups (2048 bytes) of an MN-major slice
 #pragma unroll
-            for (int k = 0; k < kBK / 16; ++k)
-                tc_mma(tmem, sdesc_sw128(aBase + 32u * k), sdesc_sw128(bBase + 32u * k), idesc,
-                       (kb > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < kBK / 16; ++k) {
+                uint64_t ad = a.a_mn ? sdesc_mn128(aBase + 2048u * k) : sdesc_sw128(aBase + 32u * k);
+                uint64_t bd = a.b_mn ? sdesc_mn128(bBase + 2048u * k) : sdesc_sw128(bBase + 32u * k);
+                tc_mma(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+            }
             tc_commit(&empty[s]);
         }
         tc_commit(&done);
@@ -414,7 +450,9 @@ int gemm_tc_check(const GemmOperands& op, const GemmArgs& a, int splits) {
     if (!(a.BN == 64 || a.BN == 128 || a.BN == 256)) return LAUE_ERR_INVALID_ARG;
     if (a.M <= 0 || a.N <= 0 || a.K <= 0 || a.M % kBM || a.N % a.BN || a.K % kBK) return LAUE_ERR_INVALID_ARG;
     if (splits < 1 || (a.K / kBK) % splits) return LAUE_ERR_INVALID_ARG;
-    if (op.lda < (uint64_t)a.K || op.ldb < (uint64_t)a.K || op.lda % 8 || op.ldb % 8) return LAUE_ERR_INVALID_ARG;
+    if (op.lda < (uint64_t)(a.a_mn ? a.M : a.K) || op.ldb < (uint64_t)(a.b_mn ? a.N : a.K) || op.lda % 8 ||
+        op.ldb % 8)
+        return LAUE_ERR_INVALID_ARG;
     if (((uintptr_t)op.A | (uintptr_t)op.B) & 15) return LAUE_ERR_INVALID_ARG;
     if (a.mode == 0 && !a.Df) return LAUE_ERR_INVALID_ARG;
     if (a.mode == 1 && !a.bias) return LAUE_ERR_INVALID_ARG;
@@ -460,10 +498,14 @@ static cudaError_t launch_persistent(const CUtensorMap& tA, const CUtensorMap& t
 
 cudaError_t gemm_tc_run(const GemmOperands& op, GemmArgs a, int splits, cudaStream_t s) {
     CUtensorMap tA, tB;
-    if (!make_tmap(&tA, op.A, (uint64_t)a.M, (uint64_t)a.K, op.lda, kBM) ||
-        !make_tmap(&tB, op.B, (uint64_t)a.N, (uint64_t)a.K, op.ldb, (uint32_t)a.BN))
-        return cudaErrorInvalidValue;
-    if (!a.simple && a.mode != 0 && splits == 1 && a.N == 256 && a.BN == 256) {
+    // an MN-major operand is the 2-D array [K][M] (or [K][N]) read in boxes of
+    // 64 MN elements x 64 k rows
+    bool okA = a.a_mn ? make_tmap(&tA, op.A, (uint64_t)a.K, (uint64_t)a.M, op.lda, kBK)
+                      : make_tmap(&tA, op.A, (uint64_t)a.M, (uint64_t)a.K, op.lda, kBM);
+    bool okB = a.b_mn ? make_tmap(&tB, op.B, (uint64_t)a.K, (uint64_t)a.N, op.ldb, kBK)
+                      : make_tmap(&tB, op.B, (uint64_t)a.N, (uint64_t)a.K, op.ldb, (uint32_t)a.BN);
+    if (!okA || !okB) return cudaErrorInvalidValue;
+    if (!a.simple && !a.a_mn && !a.b_mn && a.mode != 0 && splits == 1 && a.N == 256 && a.BN == 256) {
         if (a.K == 64) return launch_persistent<1>(tA, tB, a, s);
         if (a.K == 256) return launch_persistent<4>(tA, tB, a, s);
     }
@@ -510,6 +552,8 @@ extern "C" int laue_gemm_bf16(laue_handle* h, const void* A, long long lda, cons
     a.ldt = ldt;
     a.ctrl = (int*)h->ws;
     a.simple = (flags & 1) ? 1 : 0;
+    a.a_mn = (flags & 2) ? 1 : 0;
+    a.b_mn = (flags & 4) ? 1 : 0;
     if (gemm_tc_check(op, a, splits) != LAUE_OK)
         return laue_fail(h, LAUE_ERR_INVALID_ARG, "gemm: M %% 128, N %% bn, K %% 64, splits | K/64, ld %% 8, alignment");
     return laue_cuda_check(h, gemm_tc_run(op, a, splits, (cudaStream_t)stream), "gemm launch");

@@ -9,8 +9,8 @@
 namespace laue {
 
 struct GemmOperands {
-    const __nv_bfloat16* A;  // [M][lda], K-contiguous
-    const __nv_bfloat16* B;  // [N][ldb], K-contiguous
+    const __nv_bfloat16* A;  // [M][lda], K-contiguous; with GemmArgs::a_mn [K][lda], M-contiguous
+    const __nv_bfloat16* B;  // [N][ldb], K-contiguous; with GemmArgs::b_mn [K][ldb], N-contiguous
     uint64_t lda, ldb;
 };
 
@@ -27,6 +27,7 @@ struct GemmArgs {
     long long ldt;
     int* ctrl;                  // status word
     int simple;                 // 1: always the one-tile-per-CTA kernel
+    int a_mn, b_mn;             // 1: the operand is stored MN-contiguous (one-tile-per-CTA kernel)
 };
 
 size_t gemm_tc_smem(int BN, int stages);

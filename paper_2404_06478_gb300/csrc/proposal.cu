@@ -12,7 +12,7 @@
 //   sets             sample-frame spot axes (u parallel to rhat - e, n =
 //                    Gamma_t^T u), the KSET - 1 nearest axes to the seed's in its
 //                    rotation window by a three-round radix select, features
-//                    in the seed frame (BF16, row-major and transposed);
+//                    in the seed frame (BF16, row-major);
 //   network          per-spot layers on the tcgen05 GEMM (gemm_tc.cu),
 //                    masked mean/max pooling, FP32 head, symmetric
 //                    multi-hypothesis loss, backward, Adam.
@@ -301,8 +301,6 @@ struct SetsArgs {
     const float* gR;
     const float* gX;
     __nv_bfloat16* X;
-    __nv_bfloat16* Xt;
-    long long ldx;
     float* F;
     int* nvalid;
     float* Rt;
@@ -372,10 +370,7 @@ __global__ void __launch_bounds__(kSetThreads) sets_kernel(SetsArgs a) {
         }
         const size_t row0 = (size_t)b * KSET;
         if (i0 < 0) {
-            for (int j = threadIdx.x; j < KSET * NF; j += blockDim.x) {
-                a.X[row0 * NF + j] = __float2bfloat16_rn(0.0f);
-                a.Xt[(size_t)(j / KSET) * a.ldx + row0 + (j % KSET)] = __float2bfloat16_rn(0.0f);
-            }
+            for (int j = threadIdx.x; j < KSET * NF; j += blockDim.x) a.X[row0 * NF + j] = __float2bfloat16_rn(0.0f);
             if (a.ids)
                 for (int e = threadIdx.x; e < KSET; e += blockDim.x) a.ids[row0 + e] = -1;
             if (threadIdx.x < 9) a.F[9 * b + threadIdx.x] = 0.0f;
@@ -518,9 +513,6 @@ __global__ void __launch_bounds__(kSetThreads) sets_kernel(SetsArgs a) {
             x4[1] = make_uint4(w[4], w[5], w[6], w[7]);
 #pragma unroll
             for (int q = 2; q < NF / 8; ++q) x4[q] = make_uint4(0, 0, 0, 0);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) a.Xt[(size_t)q * a.ldx + row0 + e] = __float2bfloat16_rn(f[q]);
-            for (int q = 16; q < NF; ++q) a.Xt[(size_t)q * a.ldx + row0 + e] = __float2bfloat16_rn(0.0f);
             if (a.ids) a.ids[row0 + e] = id;
         }
         if (threadIdx.x == 0) {
@@ -548,11 +540,19 @@ __global__ void __launch_bounds__(kSetThreads) sets_kernel(SetsArgs a) {
 // ------------------------------------------------------------------ network
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
 
-// masked mean and max (first index on ties) of H3 over the valid rows
-__global__ void __launch_bounds__(WIDTH) pool_kernel(const __nv_bfloat16* H3, const int* nvalid, int B, float* pool,
-                                                     int* amax) {
-    for (int b = blockIdx.x; b < B; b += gridDim.x) {
-        int c = threadIdx.x, nv = nvalid[b];
+// masked mean and max (first index on ties) of H3 over the valid rows: FP32
+// into pool, rounded to BF16 into poolh (the head's operand; rows B .. Bp - 1
+// of poolh are zero)
+__global__ void __launch_bounds__(WIDTH) pool_kernel(const __nv_bfloat16* H3, const int* nvalid, int B, int Bp,
+                                                     float* pool, __nv_bfloat16* poolh, int* amax) {
+    for (int b = blockIdx.x; b < Bp; b += gridDim.x) {
+        int c = threadIdx.x;
+        if (b >= B) {
+            poolh[(size_t)b * 2 * WIDTH + c] = __float2bfloat16_rn(0.0f);
+            poolh[(size_t)b * 2 * WIDTH + WIDTH + c] = __float2bfloat16_rn(0.0f);
+            continue;
+        }
+        int nv = nvalid[b];
         float sum = 0.0f, best = 0.0f;
         int arg = 0;
         for (int e = 0; e < nv; ++e) {
@@ -563,122 +563,30 @@ __global__ void __launch_bounds__(WIDTH) pool_kernel(const __nv_bfloat16* H3, co
                 arg = e;
             }
         }
-        pool[(size_t)b * 2 * WIDTH + c] = nv > 0 ? sum / (float)nv : 0.0f;
-        pool[(size_t)b * 2 * WIDTH + WIDTH + c] = nv > 0 ? best : 0.0f;
+        float mean = nv > 0 ? sum / (float)nv : 0.0f, mx = nv > 0 ? best : 0.0f;
+        pool[(size_t)b * 2 * WIDTH + c] = mean;
+        pool[(size_t)b * 2 * WIDTH + WIDTH + c] = mx;
+        poolh[(size_t)b * 2 * WIDTH + c] = __float2bfloat16_rn(mean);
+        poolh[(size_t)b * 2 * WIDTH + WIDTH + c] = __float2bfloat16_rn(mx);
         amax[(size_t)b * WIDTH + c] = arg;
     }
 }
 
-// Small FP32 GEMM for the head: C[m][n] = epi(sum_k A(m, k) B(k, n)) with
-// A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn]; epilogue: + bias[n],
-// relu, multiply by (mask[m ldm + n] > 0); C[m ldc + n].  64 x 64 tiles, 4 x 4
-// outputs per thread; with splits > 1 each z-slice of the grid sums one K
-// range into part[z][m][n] and a second kernel adds the slices in order and
-// applies the epilogue.  Fixed-order sums throughout.
-struct SgemmArgs {
-    const float* A;
-    long long sam, sak;
-    const float* B;
-    long long sbk, sbn;
-    float* C;
-    long long ldc;
-    int M, N, K;
-    const float* bias;
-    int relu;
-    const float* mask;
-    long long ldm;
-    float* part;
-    int splits;
-};
-
-__device__ __forceinline__ float sg_epi(const SgemmArgs& g, int m, int n, float v) {
-    if (g.bias) v += g.bias[n];
-    if (g.relu) v = fmaxf(v, 0.0f);
-    if (g.mask && !(g.mask[m * g.ldm + n] > 0.0f)) v = 0.0f;
-    return v;
+// head output O[b][j] = Opad[b][j] + b5[j] (j < NOUT) for the B real sets
+__global__ void head_out_kernel(const float* Opad, const float* b5, int B, float* O) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * NOUT) return;
+    int b = idx / NOUT, j = idx % NOUT;
+    O[idx] = Opad[(size_t)b * NOUTP + j] + b5[j];
 }
 
-// 128 x 128 tile per CTA, 8 x 8 outputs per thread, K in steps of 8.
-__global__ void __launch_bounds__(256) sgemm_kernel(SgemmArgs g) {
-    __shared__ __align__(16) float As[8][128], Bs[8][128];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * 128;
-    const int kc = (g.K + g.splits - 1) / g.splits;
-    const int kbeg = blockIdx.z * kc, kend = min(g.K, kbeg + kc);
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-    for (int k0 = kbeg; k0 < kend; k0 += 8) {
-        // consecutive threads walk the contiguous index of each operand
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int idx = threadIdx.x + 256 * r;
-            int kk = g.sak == 1 ? (idx & 7) : (idx >> 7), mm = g.sak == 1 ? (idx >> 3) : (idx & 127), k = k0 + kk;
-            As[kk][mm] = (m0 + mm < g.M && k < kend) ? g.A[(m0 + mm) * g.sam + k * g.sak] : 0.0f;
-            kk = g.sbk == 1 ? (idx & 7) : (idx >> 7);
-            mm = g.sbk == 1 ? (idx >> 3) : (idx & 127);
-            k = k0 + kk;
-            Bs[kk][mm] = (n0 + mm < g.N && k < kend) ? g.B[k * g.sbk + (n0 + mm) * g.sbn] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
-            float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
-            float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
-            float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
-            float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        int m = m0 + ty * 8 + i;
-        if (m >= g.M) continue;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            int n = n0 + tx * 8 + j;
-            if (n >= g.N) continue;
-            if (g.splits > 1) g.part[((size_t)blockIdx.z * g.M + m) * g.N + n] = acc[i][j];
-            else g.C[m * g.ldc + n] = sg_epi(g, m, n, acc[i][j]);
-        }
-    }
-}
-
-__global__ void sgemm_finish_kernel(SgemmArgs g) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)g.M * g.N) return;
-    int m = (int)(idx / g.N), n = (int)(idx % g.N);
-    float v = 0.0f;
-    for (int z = 0; z < g.splits; ++z) v += g.part[((size_t)z * g.M + m) * g.N + n];
-    g.C[m * g.ldc + n] = sg_epi(g, m, n, v);
-}
-
-cudaError_t sgemm(const float* A, long long sam, long long sak, const float* B, long long sbk, long long sbn,
-                  float* C, long long ldc, int M, int N, int K, const float* bias, int relu, const float* mask,
-                  long long ldm, cudaStream_t s, float* part = nullptr, int splits = 1) {
-    // split K (when a scratch buffer is given) until the grid covers the SMs
-    // twice, keeping at least 64 K per split
-    if (part && splits <= 1) {
-        int tiles = ((N + 127) / 128) * ((M + 127) / 128);
-        splits = 1;
-        while (tiles * splits < 2 * 152 && K / (splits * 2) >= 64 && splits < 64) splits *= 2;
-    }
-    SgemmArgs g{A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, bias, relu, mask, ldm, part, part ? splits : 1};
-    dim3 grid((N + 127) / 128, (M + 127) / 128, g.splits);
-    sgemm_kernel<<<grid, 256, 0, s>>>(g);
-    if (g.splits > 1) {
-        long long n = (long long)M * N;
-        sgemm_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g);
-    }
-    return cudaGetLastError();
+// dL/dO rounded to BF16 into the zero-padded [Bp][NOUTP] operand of the
+// head's backward GEMMs
+__global__ void pack_dO_kernel(const float* dO, int B, int Bp, __nv_bfloat16* dOh) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= Bp * NOUTP) return;
+    int b = idx / NOUTP, j = idx % NOUTP;
+    dOh[idx] = __float2bfloat16_rn(b < B && j < NOUT ? dO[(size_t)b * NOUT + j] : 0.0f);
 }
 
 // column sums out[n] = sum_m A[m lda + n]: per z-slice partial sums over a
@@ -692,36 +600,38 @@ __global__ void colsum_partial_kernel(const float* A, long long lda, int M, int 
     part[(size_t)blockIdx.y * N + n] = s;
 }
 
-// row sums of a BF16 [rows][ld] array over its first n columns (n even):
-// blockIdx.y splits each row into equal chunks (BF16 pairs), one partial per
-// (row, chunk) in part[row][chunk]; the partials are added in order by
-// split_reduce over the transposed view
-__global__ void __launch_bounds__(256) rowsum_bf16_kernel(const __nv_bfloat16* A, long long ld, long long n,
-                                                          int chunks, float* part) {
-    __shared__ float red[256];
-    const __nv_bfloat162* r = reinterpret_cast<const __nv_bfloat162*>(A + (size_t)blockIdx.x * ld);
-    long long np = n / 2, cp = (np + chunks - 1) / chunks;
-    long long j0 = (long long)blockIdx.y * cp, j1 = min(np, j0 + cp);
-    float s = 0.0f;
-    for (long long j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-        float2 f = __bfloat1622float2(r[j]);
-        s += f.x + f.y;
+// column sums of a BF16 [rows][256] array (the bias gradients sum_m dZ[m][c]):
+// blockIdx.x takes rows [x rc, (x+1) rc); thread t adds channels 8 (t % 32)
+// .. + 7 of the rows t / 32, t / 32 + 8, ... with 16-byte loads, then the
+// eight row groups are added in order; one partial per (block, channel) in
+// part[block][256], added in order by split_reduce.
+constexpr int kColsumSplits = 256;
+__global__ void __launch_bounds__(256) colsum_bf16_kernel(const __nv_bfloat16* A, long long rows, float* part) {
+    __shared__ float red[8][WIDTH];
+    const int c8 = (threadIdx.x & 31) * 8, g = threadIdx.x >> 5;
+    const long long rc = (rows + gridDim.x - 1) / gridDim.x;
+    const long long r0 = (long long)blockIdx.x * rc, r1 = min(rows, r0 + rc);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (long long r = r0 + g; r < r1; r += 8) {
+        uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)r * WIDTH + c8);
+        const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += bf(hv[j]);
     }
-    red[threadIdx.x] = s;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[g][c8 + j] = acc[j];
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+    float t = 0.0f;
+    for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+    part[(size_t)blockIdx.x * WIDTH + threadIdx.x] = t;
 }
 
-// sum of split-K partials: out[j] = sum_s part[s n + j]
-__global__ void split_reduce_kernel(const float* part, int splits, long long n, float* out) {
+// sum of split-K partials: out[j] = sum_s part[s stride + j], j < n
+__global__ void split_reduce_kernel(const float* part, int splits, long long stride, long long n, float* out) {
     long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     float s = 0.0f;
-    for (int q = 0; q < splits; ++q) s += part[(size_t)q * n + j];
+    for (int q = 0; q < splits; ++q) s += part[(size_t)q * stride + j];
     out[j] = s;
 }
 
@@ -870,16 +780,11 @@ __global__ void loss_kernel(const float* O, const float* Rt, const float* xt, co
 }
 
 // dZ3 = (dmean / nv on valid rows + dmax at the argmax row) where H3 > 0,
-// rounded to BF16, written row-major and transposed.  Per set, 128 rows at a
-// time: each thread handles 8 channels of a row with 16-byte loads and
-// stores, the tile is staged in shared memory, and the transposed copy is
-// written as 16-byte runs of 8 consecutive rows of one channel.
-constexpr int kTileRows = 128;
-constexpr int kTileLd = WIDTH + 2;
+// rounded to BF16, row-major.  One CTA per set; each thread handles 8
+// channels of a row with 16-byte loads and stores.
 __global__ void __launch_bounds__(256) pool_backward_kernel(const __nv_bfloat16* H3, const int* nvalid,
-                                                            const int* amax, const float* dPool, int B, long long Ms,
-                                                            __nv_bfloat16* dZ3, __nv_bfloat16* dZ3t) {
-    extern __shared__ __nv_bfloat16 tile[];  // kTileRows x kTileLd
+                                                            const int* amax, const float* dPool, int B,
+                                                            __nv_bfloat16* dZ3) {
     __shared__ float dm_s[WIDTH], dx_s[WIDTH];
     __shared__ int am_s[WIDTH];
     const int c8 = (threadIdx.x & 31) * 8, r0 = threadIdx.x >> 5;
@@ -891,33 +796,20 @@ __global__ void __launch_bounds__(256) pool_backward_kernel(const __nv_bfloat16*
             am_s[c] = amax[(size_t)b * WIDTH + c];
         }
         __syncthreads();
-        for (int e0 = 0; e0 < KSET; e0 += kTileRows) {
-            for (int r = r0; r < kTileRows; r += 8) {
-                const int e = e0 + r;
-                const size_t row = (size_t)b * KSET + e;
-                uint4 hv = *reinterpret_cast<const uint4*>(H3 + row * WIDTH + c8);
-                const __nv_bfloat16* hh = reinterpret_cast<const __nv_bfloat16*>(&hv);
-                __align__(16) __nv_bfloat16 z[8];
+        for (int e = r0; e < KSET; e += 8) {
+            const size_t row = (size_t)b * KSET + e;
+            uint4 hv = *reinterpret_cast<const uint4*>(H3 + row * WIDTH + c8);
+            const __nv_bfloat16* hh = reinterpret_cast<const __nv_bfloat16*>(&hv);
+            __align__(16) __nv_bfloat16 z[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    int c = c8 + j;
-                    float v = (e < nv ? dm_s[c] : 0.0f) + (e == am_s[c] ? dx_s[c] : 0.0f);
-                    z[j] = __float2bfloat16_rn(bf(hh[j]) > 0.0f ? v : 0.0f);
-                    tile[r * kTileLd + c] = z[j];
-                }
-                *reinterpret_cast<uint4*>(dZ3 + row * WIDTH + c8) = *reinterpret_cast<const uint4*>(z);
+            for (int j = 0; j < 8; ++j) {
+                int c = c8 + j;
+                float v = (e < nv ? dm_s[c] : 0.0f) + (e == am_s[c] ? dx_s[c] : 0.0f);
+                z[j] = __float2bfloat16_rn(bf(hh[j]) > 0.0f ? v : 0.0f);
             }
-            __syncthreads();
-            for (int idx = threadIdx.x; idx < WIDTH * (kTileRows / 8); idx += blockDim.x) {
-                int c = idx / (kTileRows / 8), q0 = (idx % (kTileRows / 8)) * 8;
-                __align__(16) __nv_bfloat16 z[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) z[k] = tile[(q0 + k) * kTileLd + c];
-                *reinterpret_cast<uint4*>(dZ3t + (size_t)c * Ms + (size_t)b * KSET + e0 + q0) =
-                    *reinterpret_cast<const uint4*>(z);
-            }
-            __syncthreads();
+            *reinterpret_cast<uint4*>(dZ3 + row * WIDTH + c8) = *reinterpret_cast<const uint4*>(z);
         }
+        __syncthreads();
     }
 }
 
@@ -939,10 +831,12 @@ __global__ void step_kernel(int* step) {
     if (threadIdx.x == 0 && blockIdx.x == 0) step[0] += 1;
 }
 
-// BF16 copies of the per-spot weights: W1h, W2h, W3h row-major [out][in] and
-// W2t, W3t transposed [in][out]
+// BF16 copies of the weights: W1h, W2h, W3h, W4h row-major [out][in], W2t,
+// W3t transposed [in][out], W5h row-major with rows NOUT .. NOUTP - 1 zero
+constexpr int kRefreshThreads = HEADW * 2 * WIDTH;  // the largest copy (W4)
 __global__ void refresh_bf16_kernel(const float* P, __nv_bfloat16* W1h, __nv_bfloat16* W2h, __nv_bfloat16* W3h,
-                                    __nv_bfloat16* W2t, __nv_bfloat16* W3t) {
+                                    __nv_bfloat16* W2t, __nv_bfloat16* W3t, __nv_bfloat16* W4h,
+                                    __nv_bfloat16* W5h) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < WIDTH * NF) W1h[i] = __float2bfloat16_rn(P[oW1 + i]);
     if (i < WIDTH * WIDTH) {
@@ -952,6 +846,8 @@ __global__ void refresh_bf16_kernel(const float* P, __nv_bfloat16* W1h, __nv_bfl
         W2t[(size_t)n * WIDTH + o] = __float2bfloat16_rn(P[oW2 + i]);
         W3t[(size_t)n * WIDTH + o] = __float2bfloat16_rn(P[oW3 + i]);
     }
+    if (i < HEADW * 2 * WIDTH) W4h[i] = __float2bfloat16_rn(P[oW4 + i]);
+    if (i < NOUTP * HEADW) W5h[i] = __float2bfloat16_rn(i < NOUT * HEADW ? P[oW5 + i] : 0.0f);
 }
 
 // proposals: R = F0 GS(o_h), x = XSCALE o_h[6:9]
@@ -971,6 +867,14 @@ __global__ void decode_kernel(const float* O, const float* F, const int* nvalid,
     for (int q = 0; q < 3; ++q) xout[3 * (size_t)idx + q] = nvalid[b] > 0 ? XSCALE * o[6 + q] : 0.0f;
 }
 
+// split-K count of the head's weight gradients (K = Bp rows): the largest
+// power of two <= 8 dividing Bp / 64
+int head_splits(int Bp) {
+    int kb = Bp / 64, s = 1;
+    while (s * 2 <= 8 && kb % (s * 2) == 0) s *= 2;
+    return s;
+}
+
 int splits_for(int B) {
     // K = B KSET rows = B KSET / 64 blocks of 64; the largest power of two <= 128 dividing them
     long long kb = (long long)B * KSET / 64;
@@ -981,7 +885,7 @@ int splits_for(int B) {
 
 struct Net {
     float *P, *m, *v, *G, *part;
-    __nv_bfloat16 *W1h, *W2h, *W3h, *W2t, *W3t;
+    __nv_bfloat16 *W1h, *W2h, *W3h, *W2t, *W3t, *W4h, *W5h;
     int* step;
 };
 Net net_view(void* base) {
@@ -998,6 +902,8 @@ Net net_view(void* base) {
     n.W3h = (__nv_bfloat16*)(c + L.W3h);
     n.W2t = (__nv_bfloat16*)(c + L.W2t);
     n.W3t = (__nv_bfloat16*)(c + L.W3t);
+    n.W4h = (__nv_bfloat16*)(c + L.W4h);
+    n.W5h = (__nv_bfloat16*)(c + L.W5h);
     n.step = (int*)(c + L.step);
     return n;
 }
@@ -1020,33 +926,46 @@ cudaError_t forward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaStr
     g.N = WIDTH;
     g.BN = WIDTH;
     g.mode = 1;
-    g.ldt = Ms;
     g.ctrl = ctrl;
     cudaError_t e;
     // layer 1: X (K = 64)
     g.K = NF;
     g.bias = n.P + ob1;
     g.Dh = bfp(L.H1);
-    g.DhT = bfp(L.H1t);
     if ((e = gemm_tc_run(GemmOperands{bfp(L.X), n.W1h, NF, NF}, g, 1, s)) != cudaSuccess) return e;
     g.K = WIDTH;
     g.bias = n.P + ob2;
     g.Dh = bfp(L.H2);
-    g.DhT = bfp(L.H2t);
     if ((e = gemm_tc_run(GemmOperands{bfp(L.H1), n.W2h, WIDTH, WIDTH}, g, 1, s)) != cudaSuccess) return e;
     g.bias = n.P + ob3;
     g.Dh = bfp(L.H3);
-    g.DhT = nullptr;
     if ((e = gemm_tc_run(GemmOperands{bfp(L.H2), n.W3h, WIDTH, WIDTH}, g, 1, s)) != cudaSuccess) return e;
-    pool_kernel<<<B, WIDTH, 0, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), B, bt.at<float>(L.pool), bt.at<int>(L.amax));
+    const int Bp = L.Bp;
+    pool_kernel<<<Bp, WIDTH, 0, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), B, Bp, bt.at<float>(L.pool), bfp(L.poolh),
+                                     bt.at<int>(L.amax));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // head (FP32): H4 = relu(pool W4^T + b4), O = H4 W5^T + b5
-    float* hs = bt.at<float>(L.hscr);
-    if ((e = sgemm(bt.at<float>(L.pool), 2 * WIDTH, 1, n.P + oW4, 1, 2 * WIDTH, bt.at<float>(L.H4), HEADW, B, HEADW,
-                   2 * WIDTH, n.P + ob4, 1, nullptr, 0, s, hs, 0)) != cudaSuccess)
-        return e;
-    return sgemm(bt.at<float>(L.H4), HEADW, 1, n.P + oW5, 1, HEADW, bt.at<float>(L.O), NOUT, B, NOUT, HEADW,
-                 n.P + ob5, 0, nullptr, 0, s, hs, 0);
+    // head on the tensor cores: H4 = relu(pool W4^T + b4) (BF16), O = H4 W5^T + b5
+    GemmArgs hg{};
+    hg.M = Bp;
+    hg.N = HEADW;
+    hg.K = 2 * WIDTH;
+    hg.BN = 256;
+    hg.mode = 1;
+    hg.bias = n.P + ob4;
+    hg.Dh = bfp(L.H4h);
+    hg.ctrl = ctrl;
+    if ((e = gemm_tc_run(GemmOperands{bfp(L.poolh), n.W4h, 2 * WIDTH, 2 * WIDTH}, hg, 1, s)) != cudaSuccess) return e;
+    GemmArgs og{};
+    og.M = Bp;
+    og.N = NOUTP;
+    og.K = HEADW;
+    og.BN = NOUTP;
+    og.mode = 0;
+    og.Df = bt.at<float>(L.Opad);
+    og.ctrl = ctrl;
+    if ((e = gemm_tc_run(GemmOperands{bfp(L.H4h), n.W5h, HEADW, HEADW}, og, 1, s)) != cudaSuccess) return e;
+    head_out_kernel<<<(B * NOUT + 255) / 256, 256, 0, s>>>(bt.at<float>(L.Opad), n.P + ob5, B, bt.at<float>(L.O));
+    return cudaGetLastError();
 }
 
 cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaStream_t s) {
@@ -1055,31 +974,65 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
     auto bfp = [&](size_t off) { return bt.at<__nv_bfloat16>(off); };
     cudaError_t e;
     float* dO = bt.at<float>(L.dO);
-    float* H4 = bt.at<float>(L.H4);
-    float* dZ4 = bt.at<float>(L.dZ4);
-    float* pool = bt.at<float>(L.pool);
-    // head
-    float* hs = bt.at<float>(L.hscr);
-    if ((e = sgemm(dO, 1, NOUT, H4, HEADW, 1, n.G + oW5, HEADW, NOUT, HEADW, B, nullptr, 0, nullptr, 0, s, hs, 0)))
-        return e;
+    const int Bp = L.Bp;
+    const int hs = head_splits(Bp);
+    // head, on the tensor cores with BF16 operands: dW5 = dO^T H4, db5 = sum dO,
+    // dZ4 = (dO W5) * (H4 > 0), dW4 = dZ4^T pool, db4 = sum dZ4, dPool = dZ4 W4
+    pack_dO_kernel<<<(Bp * NOUTP + 255) / 256, 256, 0, s>>>(dO, B, Bp, bfp(L.dOh));
+    GemmArgs w5{};
+    w5.M = NOUTP;
+    w5.N = HEADW;
+    w5.K = Bp;
+    w5.BN = 256;
+    w5.mode = 0;
+    w5.Df = n.part;
+    w5.ctrl = ctrl;
+    w5.a_mn = 1;
+    w5.b_mn = 1;
+    if ((e = gemm_tc_run(GemmOperands{bfp(L.dOh), bfp(L.H4h), NOUTP, HEADW}, w5, hs, s))) return e;
+    split_reduce_kernel<<<(NOUT * HEADW + 255) / 256, 256, 0, s>>>(n.part, hs, (long long)NOUTP * HEADW,
+                                                                   (long long)NOUT * HEADW, n.G + oW5);
     colsum_partial_kernel<<<dim3(1, 32), NOUT, 0, s>>>(dO, NOUT, B, NOUT, 32, n.part);
-    split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, NOUT, n.G + ob5);
-    if ((e = sgemm(dO, NOUT, 1, n.P + oW5, HEADW, 1, dZ4, HEADW, B, HEADW, NOUT, nullptr, 0, H4, HEADW, s, hs, 0)))
-        return e;
-    if ((e = sgemm(dZ4, 1, HEADW, pool, 2 * WIDTH, 1, n.G + oW4, 2 * WIDTH, HEADW, 2 * WIDTH, B, nullptr, 0,
-                   nullptr, 0, s, hs, 0)))
-        return e;
-    colsum_partial_kernel<<<dim3(1, 32), HEADW, 0, s>>>(dZ4, HEADW, B, HEADW, 32, n.part);
-    split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, HEADW, n.G + ob4);
-    if ((e = sgemm(dZ4, HEADW, 1, n.P + oW4, 2 * WIDTH, 1, bt.at<float>(L.dPool), 2 * WIDTH, B, 2 * WIDTH, HEADW,
-                   nullptr, 0, nullptr, 0, s, hs, 0)))
-        return e;
+    split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, NOUT, NOUT, n.G + ob5);
+    GemmArgs d4{};
+    d4.M = Bp;
+    d4.N = HEADW;
+    d4.K = NOUTP;
+    d4.BN = 256;
+    d4.mode = 2;
+    d4.mask = bfp(L.H4h);
+    d4.Dh = bfp(L.dZ4h);
+    d4.ctrl = ctrl;
+    d4.b_mn = 1;  // W5 [out][hidden] is the [K][N] operand
+    if ((e = gemm_tc_run(GemmOperands{bfp(L.dOh), n.W5h, NOUTP, HEADW}, d4, 1, s))) return e;
+    GemmArgs w4{};
+    w4.M = HEADW;
+    w4.N = 2 * WIDTH;
+    w4.K = Bp;
+    w4.BN = 256;
+    w4.mode = 0;
+    w4.Df = n.part;
+    w4.ctrl = ctrl;
+    w4.a_mn = 1;
+    w4.b_mn = 1;
+    if ((e = gemm_tc_run(GemmOperands{bfp(L.dZ4h), bfp(L.poolh), HEADW, 2 * WIDTH}, w4, hs, s))) return e;
+    split_reduce_kernel<<<(HEADW * 2 * WIDTH + 255) / 256, 256, 0, s>>>(n.part, hs, (long long)HEADW * 2 * WIDTH,
+                                                                        (long long)HEADW * 2 * WIDTH, n.G + oW4);
+    colsum_bf16_kernel<<<kColsumSplits, 256, 0, s>>>(bfp(L.dZ4h), Bp, n.part);
+    split_reduce_kernel<<<1, 256, 0, s>>>(n.part, kColsumSplits, WIDTH, WIDTH, n.G + ob4);
+    GemmArgs dp{};
+    dp.M = Bp;
+    dp.N = 2 * WIDTH;
+    dp.K = HEADW;
+    dp.BN = 256;
+    dp.mode = 0;
+    dp.Df = bt.at<float>(L.dPool);
+    dp.ctrl = ctrl;
+    dp.b_mn = 1;  // W4 [hidden][pool] is the [K][N] operand
+    if ((e = gemm_tc_run(GemmOperands{bfp(L.dZ4h), n.W4h, HEADW, 2 * WIDTH}, dp, 1, s))) return e;
     // pooling -> dZ3
-    size_t tsm = (size_t)kTileRows * kTileLd * 2;
-    if ((e = cudaFuncSetAttribute(pool_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm)))
-        return e;
-    pool_backward_kernel<<<B, 256, tsm, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), bt.at<int>(L.amax),
-                                               bt.at<float>(L.dPool), B, Ms, bfp(L.dZ3), bfp(L.dZ3t));
+    pool_backward_kernel<<<B, 256, 0, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), bt.at<int>(L.amax),
+                                           bt.at<float>(L.dPool), B, bfp(L.dZ3));
     if ((e = cudaGetLastError())) return e;
     // dZ2 = (dZ3 W3) * (H2 > 0), dZ1 = (dZ2 W2) * (H1 > 0)
     GemmArgs g{};
@@ -1088,17 +1041,15 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
     g.K = WIDTH;
     g.BN = WIDTH;
     g.mode = 2;
-    g.ldt = Ms;
     g.ctrl = ctrl;
     g.mask = bfp(L.H2);
     g.Dh = bfp(L.dZ2);
-    g.DhT = bfp(L.dZ2t);
     if ((e = gemm_tc_run(GemmOperands{bfp(L.dZ3), n.W3t, WIDTH, WIDTH}, g, 1, s))) return e;
     g.mask = bfp(L.H1);
-    g.Dh = nullptr;
-    g.DhT = bfp(L.dZ1t);
+    g.Dh = bfp(L.dZ1);
     if ((e = gemm_tc_run(GemmOperands{bfp(L.dZ2), n.W2t, WIDTH, WIDTH}, g, 1, s))) return e;
-    // weight gradients: dW_l = dZ_l^T H_{l-1} (split K over the spots)
+    // weight gradients dW_l = dZ_l^T H_{l-1}, split K over the spots: both
+    // operands are the row-major [spots][channels] arrays, read MN-major
     int splits = splits_for(B);
     GemmArgs w{};
     w.M = WIDTH;
@@ -1106,23 +1057,27 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
     w.mode = 0;
     w.Df = n.part;
     w.ctrl = ctrl;
+    w.a_mn = 1;
+    w.b_mn = 1;
     struct {
         size_t A, Bop;
         int N, bn;
         size_t oW, ob;
-    } layers[3] = {{L.dZ3t, L.H2t, WIDTH, WIDTH, oW3, ob3},
-                   {L.dZ2t, L.H1t, WIDTH, WIDTH, oW2, ob2},
-                   {L.dZ1t, L.Xt, NF, NF, oW1, ob1}};
+    } layers[3] = {{L.dZ3, L.H2, WIDTH, WIDTH, oW3, ob3},
+                   {L.dZ2, L.H1, WIDTH, WIDTH, oW2, ob2},
+                   {L.dZ1, L.X, NF, NF, oW1, ob1}};
     for (int l = 0; l < 3; ++l) {
         w.N = layers[l].N;
         w.BN = layers[l].bn;
-        if ((e = gemm_tc_run(GemmOperands{bfp(layers[l].A), bfp(layers[l].Bop), (uint64_t)Ms, (uint64_t)Ms}, w,
-                             splits, s)))
+        if ((e = gemm_tc_run(GemmOperands{bfp(layers[l].A), bfp(layers[l].Bop), (uint64_t)WIDTH,
+                                          (uint64_t)layers[l].N},
+                             w, splits, s)))
             return e;
         long long nw = (long long)WIDTH * layers[l].N;
-        split_reduce_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(n.part, splits, nw, n.G + layers[l].oW);
-        rowsum_bf16_kernel<<<dim3(WIDTH, 32), 256, 0, s>>>(bfp(layers[l].A), Ms, Ms, 32, n.part);
-        split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, WIDTH, n.G + layers[l].ob);
+        split_reduce_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(n.part, splits, nw, nw,
+                                                                          n.G + layers[l].oW);
+        colsum_bf16_kernel<<<kColsumSplits, 256, 0, s>>>(bfp(layers[l].A), Ms, n.part);
+        split_reduce_kernel<<<1, 256, 0, s>>>(n.part, kColsumSplits, WIDTH, WIDTH, n.G + layers[l].ob);
         if ((e = cudaGetLastError())) return e;
     }
     return cudaSuccess;
@@ -1143,7 +1098,8 @@ extern "C" size_t laue_lp_batch_bytes(int n_sets) { return n_sets > 0 ? batch_la
 extern "C" long long laue_lp_batch_offset(int n_sets, int region) {
     if (n_sets <= 0) return -1;
     BatchLayout L = batch_layout(n_sets);
-    const size_t offs[] = {L.X, L.Xt, L.F, L.nvalid, L.Rt, L.xt, L.svalid, L.O, L.loss, L.dbest, L.hbest,
+    // region 1 (a transposed copy of X) is no longer kept: -1
+    const size_t offs[] = {L.X, (size_t)-1, L.F, L.nvalid, L.Rt, L.xt, L.svalid, L.O, L.loss, L.dbest, L.hbest,
                            L.H1, L.H3, L.pool, L.dO, L.dZ3};
     if (region < 0 || region >= (int)(sizeof(offs) / sizeof(offs[0]))) return -1;
     return (long long)offs[region];
@@ -1167,7 +1123,8 @@ extern "C" int laue_lp_net_init(laue_handle* h, void* net, const float* params_h
                               "net params")))
         return rc;
     if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "net init"))) return rc;
-    refresh_bf16_kernel<<<(WIDTH * WIDTH + 255) / 256, 256, 0, s>>>(n.P, n.W1h, n.W2h, n.W3h, n.W2t, n.W3t);
+    refresh_bf16_kernel<<<(kRefreshThreads + 255) / 256, 256, 0, s>>>(n.P, n.W1h, n.W2h, n.W3h, n.W2t, n.W3t,
+                                                                       n.W4h, n.W5h);
     return laue_cuda_check(h, cudaGetLastError(), "net refresh");
 }
 
@@ -1288,8 +1245,6 @@ extern "C" int laue_lp_sets(laue_handle* h, const LaueGeometry* geom, const floa
     a.gR = grainR;
     a.gX = grainX;
     a.X = bt.at<__nv_bfloat16>(L.X);
-    a.Xt = bt.at<__nv_bfloat16>(L.Xt);
-    a.ldx = L.Ms;
     a.F = bt.at<float>(L.F);
     a.nvalid = bt.at<int>(L.nvalid);
     a.Rt = label ? bt.at<float>(L.Rt) : nullptr;
@@ -1333,7 +1288,8 @@ extern "C" int laue_lp_train_step(laue_handle* h, void* net, void* batch, int n_
     adam_kernel<<<(unsigned)((kParams + 255) / 256), 256, 0, s>>>(n.P, n.m, n.v, n.G, (long long)kParams, n.step,
                                                                   lr, 0.9f, 0.999f, 1e-8f);
     step_kernel<<<1, 32, 0, s>>>(n.step);
-    refresh_bf16_kernel<<<(WIDTH * WIDTH + 255) / 256, 256, 0, s>>>(n.P, n.W1h, n.W2h, n.W3h, n.W2t, n.W3t);
+    refresh_bf16_kernel<<<(kRefreshThreads + 255) / 256, 256, 0, s>>>(n.P, n.W1h, n.W2h, n.W3h, n.W2t, n.W3t,
+                                                                       n.W4h, n.W5h);
     return laue_cuda_check(h, cudaGetLastError(), "adam");
 }
 

@@ -15,6 +15,7 @@ constexpr int WIDTH = 256;  // per-spot MLP width
 constexpr int HEADW = 256;  // head hidden width
 constexpr int NHYP = 8;     // hypotheses per set
 constexpr int NOUT = 9 * NHYP;
+constexpr int NOUTP = 128;  // NOUT padded to a tensor-core tile (zero rows / columns beyond NOUT)
 constexpr float XSCALE = 2.5f;
 constexpr float LAMBDA_X = 0.1f;
 constexpr float BETA = 0.05f;
@@ -39,10 +40,11 @@ constexpr size_t kParams = ob5 + NOUT;
 inline size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Network buffer (bytes): FP32 params, Adam moments m and v, gradients,
-// BF16 copies of the per-spot weights (row-major and transposed), split-K
-// partials, the Adam step counter.
+// BF16 copies of the weights (the per-spot ones row-major and transposed,
+// W4 row-major, W5 row-major padded to NOUTP rows), split-K partials, the
+// Adam step counter.
 struct NetLayout {
-    size_t params, adam_m, adam_v, grads, W1h, W2h, W3h, W2t, W3t, partial, step, total;
+    size_t params, adam_m, adam_v, grads, W1h, W2h, W3h, W2t, W3t, W4h, W5h, partial, step, total;
 };
 inline NetLayout net_layout() {
     NetLayout L;
@@ -57,18 +59,25 @@ inline NetLayout net_layout() {
     L.W3h = take((size_t)WIDTH * WIDTH * 2);
     L.W2t = take((size_t)WIDTH * WIDTH * 2);
     L.W3t = take((size_t)WIDTH * WIDTH * 2);
+    L.W4h = take((size_t)HEADW * 2 * WIDTH * 2);
+    L.W5h = take((size_t)NOUTP * HEADW * 2);
     L.partial = take((size_t)kMaxSplits * WIDTH * WIDTH * 4);
     L.step = take(256);
     L.total = o;
     return L;
 }
 
-// Batch buffer (bytes) for B sets of KSET spots (Ms = B KSET rows).
+// Batch buffer (bytes) for B sets of KSET spots (Ms = B KSET rows).  The
+// head's tensor-core operands have Bp = B rounded up to 128 rows; the rows
+// beyond B hold zero features and zero errors.
 struct BatchLayout {
-    size_t X, Xt, H1, H1t, H2, H2t, H3, dZ3, dZ3t, dZ2, dZ2t, dZ1t;  // BF16 per-spot arrays
-    size_t F, nvalid, Rt, xt, svalid, pool, amax, H4, O, dO, dZ4, dPool, loss, dbest, hbest, inv_nval, hscr;
+    size_t X, H1, H2, H3, dZ3, dZ2, dZ1;  // BF16 per-spot arrays, row-major [spots][channels]
+    size_t F, nvalid, Rt, xt, svalid, pool, amax, O, dO, loss, dbest, hbest, inv_nval;
+    size_t poolh, H4h, dZ4h, dOh;  // BF16 head operands [Bp][512], [Bp][256], [Bp][256], [Bp][NOUTP]
+    size_t Opad, dPool;            // FP32 [Bp][NOUTP], [Bp][512]
     size_t total;
     long long Ms;
+    int Bp;
 };
 inline BatchLayout batch_layout(int B) {
     BatchLayout L;
@@ -77,17 +86,12 @@ inline BatchLayout batch_layout(int B) {
     L.Ms = Ms;
     auto take = [&](size_t bytes) { size_t r = o; o = al256(o + bytes); return r; };
     L.X = take((size_t)Ms * NF * 2);
-    L.Xt = take((size_t)Ms * NF * 2);
     L.H1 = take((size_t)Ms * WIDTH * 2);
-    L.H1t = take((size_t)Ms * WIDTH * 2);
     L.H2 = take((size_t)Ms * WIDTH * 2);
-    L.H2t = take((size_t)Ms * WIDTH * 2);
     L.H3 = take((size_t)Ms * WIDTH * 2);
     L.dZ3 = take((size_t)Ms * WIDTH * 2);
-    L.dZ3t = take((size_t)Ms * WIDTH * 2);
     L.dZ2 = take((size_t)Ms * WIDTH * 2);
-    L.dZ2t = take((size_t)Ms * WIDTH * 2);
-    L.dZ1t = take((size_t)Ms * WIDTH * 2);
+    L.dZ1 = take((size_t)Ms * WIDTH * 2);
     L.F = take((size_t)B * 9 * 4);
     L.nvalid = take((size_t)B * 4);
     L.Rt = take((size_t)B * 9 * 4);
@@ -95,20 +99,20 @@ inline BatchLayout batch_layout(int B) {
     L.svalid = take((size_t)B * 4);
     L.pool = take((size_t)B * 2 * WIDTH * 4);
     L.amax = take((size_t)B * WIDTH * 4);
-    L.H4 = take((size_t)B * HEADW * 4);
     L.O = take((size_t)B * NOUT * 4);
     L.dO = take((size_t)B * NOUT * 4);
-    L.dZ4 = take((size_t)B * HEADW * 4);
-    L.dPool = take((size_t)B * 2 * WIDTH * 4);
     L.loss = take((size_t)B * 4);
     L.dbest = take((size_t)B * 4);
     L.hbest = take((size_t)B * 4);
     L.inv_nval = take(256);
-    // split-K partial sums of the head GEMMs: at most 8 x (B x 256), 4 x (B x 512)
-    // or 64 x (256 x 512) floats
-    size_t hs = (size_t)B * 2048;
-    if (hs < (size_t)64 * HEADW * 2 * WIDTH) hs = (size_t)64 * HEADW * 2 * WIDTH;
-    L.hscr = take(hs * 4);
+    const int Bp = (B + 127) / 128 * 128;
+    L.Bp = Bp;
+    L.poolh = take((size_t)Bp * 2 * WIDTH * 2);
+    L.H4h = take((size_t)Bp * HEADW * 2);
+    L.dZ4h = take((size_t)Bp * HEADW * 2);
+    L.dOh = take((size_t)Bp * NOUTP * 2);
+    L.Opad = take((size_t)Bp * NOUTP * 4);
+    L.dPool = take((size_t)Bp * 2 * WIDTH * 4);
     L.total = o;
     return L;
 }

@@ -1092,8 +1092,9 @@ cudaError_t sinkhorn_finish(const SkArgs& a, const SkLaunch& l, bool want_rows, 
     int blocks = (nmax + 255) / 256;
     if (blocks < 1) blocks = 1;
     if (want_rows || want_cols) sk_clear_err_kernel<<<1, 1, 0, s>>>(a);
-    if (want_rows) sk_harvest_row_kernel<<<l.hrv_grid, kTPB, 0, s>>>(a);
-    if (want_cols) sk_harvest_col_kernel<<<l.hcol_grid, kTPB, 0, s>>>(a);
+    // one thread per row (column) pair of the pass's tiles
+    if (want_rows) sk_harvest_row_kernel<<<l.hrv_grid, sk_variant_threads(l.row_variant), 0, s>>>(a);
+    if (want_cols) sk_harvest_col_kernel<<<l.hcol_grid, sk_variant_threads(l.col_variant), 0, s>>>(a);
     sk_finish_kernel<<<blocks, 256, 0, s>>>(a, want_rows ? 1 : 0, want_cols ? 1 : 0);
     return cudaGetLastError();
 }

@@ -13,27 +13,29 @@ from . import api
 
 def gemm_bf16(h: api.Handle, A: torch.Tensor, B: torch.Tensor, mode: int = 0, bn: int = 256, splits: int = 1,
               bias: torch.Tensor | None = None, mask: torch.Tensor | None = None, out_f32=None, out=None,
-              outT=None, simple: bool = False, stream=None):
+              outT=None, simple: bool = False, a_mn: bool = False, b_mn: bool = False, stream=None):
     """D[m][n] = sum_k A[m][k] B[n][k] on the tcgen05 tensor cores (BF16 in,
-    FP32 accumulate).  mode 0 writes `splits` FP32 partials into out_f32
-    (splits, M, N); mode 1 relu(D + bias) and mode 2 D * (mask > 0) as BF16
-    into out (M, N) and/or outT (N, ldt)."""
+    FP32 accumulate).  A is (M, K) and B (N, K), or, with a_mn / b_mn, the
+    stored arrays (K, M) / (K, N) read MN-major.  mode 0 writes `splits` FP32
+    partials into out_f32 (splits, M, N); mode 1 relu(D + bias) and mode 2
+    D * (mask > 0) as BF16 into out (M, N) and/or outT (N, ldt)."""
     assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and A.is_cuda and B.is_cuda
-    M, K = A.shape
-    N = B.shape[0]
+    K, M = A.shape if a_mn else A.shape[::-1]
+    N = B.shape[1] if b_mn else B.shape[0]
     if h.ws is None:
         h.reserve(1, stream=stream)
     ldt = outT.stride(0) if outT is not None else 0
+    flags = (1 if simple else 0) | (2 if a_mn else 0) | (4 if b_mn else 0)
     rc = h.L.laue_gemm_bf16(h.h, api._ptr(A), A.stride(0), api._ptr(B), B.stride(0), M, N, K, bn, splits, mode,
                             api._ptr(bias), api._ptr(mask), api._ptr(out_f32), api._ptr(out), api._ptr(outT), ldt,
-                            1 if simple else 0, api._stream(stream))
+                            flags, api._stream(stream))
     h.check(rc, "gemm_bf16")
 
 
 # ---------------------------------------------------------------- set encoder
 NF, NHYP, NOUT = 64, 8, 72
 KSET = 128  # spots per set; equals laue_lp_set_size() of the library (checked by the tests)
-REGIONS = dict(X=0, Xt=1, F=2, nvalid=3, Rt=4, xt=5, svalid=6, O=7, loss=8, dbest=9, hbest=10, H1=11, H3=12,
+REGIONS = dict(X=0, F=2, nvalid=3, Rt=4, xt=5, svalid=6, O=7, loss=8, dbest=9, hbest=10, H1=11, H3=12,
                pool=13, dO=14, dZ3=15)
 PARAM_SHAPES = [("W1", (256, 64)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),
                 ("b3", (256,)), ("W4", (256, 512)), ("b4", (256,)), ("W5", (72, 256)), ("b5", (72,))]

@@ -51,6 +51,30 @@ def test_gemm_f32_partials(env, M, N, K, bn, splits):
         assert np.all(np.abs(got[s] - ref[s]) <= bound), np.abs(got[s] - ref[s]).max()
 
 
+@pytest.mark.parametrize("a_mn,b_mn", [(True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("M,N,K,bn,splits", [(256, 256, 8192, 256, 8), (256, 64, 4096, 64, 4),
+                                              (384, 128, 192, 128, 1), (128, 256, 64, 256, 1)])
+def test_gemm_mn_major_operands(env, a_mn, b_mn, M, N, K, bn, splits):
+    """Operands stored MN-contiguous ([K][M], [K][N]) as the weight gradients
+    read the row-major activations and errors: the same partial products as
+    the K-major form, against the FP64 product of the same BF16 values."""
+    torch = env["torch"]
+    rng = np.random.default_rng(M + 3 * N + 5 * K + 7 * a_mn + 11 * b_mn)
+    A, B = _bf(rng, (M, K)), _bf(rng, (N, K))
+    Ad = _dev(env, A.T.copy() if a_mn else A)
+    Bd = _dev(env, B.T.copy() if b_mn else B)
+    D = torch.full((splits, M, N), float("nan"), device=env["dev"])
+    env["pr"].gemm_bf16(env["h"], Ad, Bd, mode=0, bn=bn, splits=splits, out_f32=D, a_mn=a_mn, b_mn=b_mn)
+    torch.cuda.synchronize()
+    assert env["h"].device_status() == 0
+    ref = op.gemm_tn(A, B, 0, splits=splits)
+    got = D.cpu().numpy().astype(np.float64)
+    ks = K // splits
+    for s in range(splits):
+        bound = _bound(A[:, s * ks:(s + 1) * ks], B[:, s * ks:(s + 1) * ks], 1)
+        assert np.all(np.abs(got[s] - ref[s]) <= bound), np.abs(got[s] - ref[s]).max()
+
+
 def _bf16_close(got, exact, bound):
     """A BF16 result of an FP32 accumulation: within the accumulation bound
     of the exact value, then rounded (relative 2^-8 covers one rounding).

@@ -335,13 +335,15 @@ def test_training_scene_noise_statistics(planes):
 
 
 def test_bf16_mode_equals_exact_mode_when_no_rounding_occurs():
-    """The BF16 data path (operands, activations and back-propagated errors of
-    the per-spot layers rounded to BF16) is the FP64 path with rounding points
-    added.  On a network and sets whose every per-spot quantity has few
-    significant bits (signed permutation weights, dyadic inputs, biases and head
-    weights, 8 valid spots per set) no rounding changes a value, so both modes
-    give the same outputs and the same gradients bit for bit; the FP64 mode is
-    itself pinned by finite differences above."""
+    """The BF16 data path (weights, activations, pooled features and the
+    back-propagated errors the GEMMs read, rounded to BF16) is the FP64 path
+    with rounding points added.  On a network and sets whose every such
+    quantity has at most 8 significant bits (signed permutation weights,
+    dyadic inputs and biases, 8 valid spots per set so that the mean divides
+    by a power of two, head weights with one dyadic entry per row of W4 and
+    per column of W5) no rounding changes a value, so both modes give the same
+    outputs and the same gradients bit for bit; the FP64 mode is itself
+    pinned by finite differences above."""
     rng = np.random.default_rng(29)
     B = 3
     P = {}
@@ -354,12 +356,14 @@ def test_bf16_mode_equals_exact_mode_when_no_rounding_occurs():
         P[name][np.arange(op.WIDTH), perm] = rng.choice([-1.0, 1.0], op.WIDTH)
     for name in ("b1", "b2", "b3"):
         P[name] = rng.integers(-2, 3, op.WIDTH) / 16.0
-    # head (FP32 in both modes): one dyadic entry per column, so that the errors
-    # sent back into the per-spot layers keep few significant bits as well
-    for name in ("W4", "W5"):
-        rows, cols = P[name].shape
-        P[name][rng.integers(0, rows, cols), np.arange(cols)] = rng.choice([-0.25, -0.125, 0.125, 0.25], cols)
-    P["b4"] = rng.integers(0, 3, P["b4"].shape) / 8.0
+    # head: W4 takes one pooled feature per hidden unit (one dyadic entry per
+    # row, distinct columns) and no bias, so the hidden activations stay
+    # exact; W5 one dyadic entry per column, so that every error sent back
+    # has a single term and few significant bits as well
+    dy = [-0.25, -0.125, 0.125, 0.25]
+    P["W4"][np.arange(op.HEAD), rng.permutation(2 * op.WIDTH)[:op.HEAD]] = rng.choice(dy, op.HEAD)
+    rows, cols = P["W5"].shape
+    P["W5"][rng.integers(0, rows, cols), np.arange(cols)] = rng.choice(dy, cols)
     X = np.zeros((B, op.KSET, op.NF))
     X[:, :, :14] = rng.integers(-8, 9, (B, op.KSET, 14)) / 16.0
     X[:, :, 12] = 0.0
@@ -375,4 +379,5 @@ def test_bf16_mode_equals_exact_mode_when_no_rounding_occurs():
     G16 = op.backward(P, c16, dO)
     for k in G64:
         np.testing.assert_array_equal(G16[k], G64[k], err_msg=k)
-    assert all(np.count_nonzero(G64[k]) > 0 for k in ("W1", "W2", "W3"))
+    assert all(np.count_nonzero(G64[k]) > 0 for k in ("W1", "W2", "W3", "W4", "W5"))
+    assert np.count_nonzero(c64["H4"]) > 0.2 * c64["H4"].size
