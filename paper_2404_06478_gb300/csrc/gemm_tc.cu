@@ -135,16 +135,20 @@ __device__ __forceinline__ void mbar_arrive1(uint64_t* bar) {
                  : "memory");
 }
 
-// Epilogue of 32 accumulator columns of row m (modes 1 and 2).  Measured:
-// staging these stores through shared memory for 16-byte coalesced writes
-// gains nothing here, because the layer is bound by HBM write bandwidth
-// (a plain fill of the same bytes runs at about 3.8 TB/s).
-__device__ __forceinline__ void epilogue32(const GemmArgs& a, int m, int n, float* v) {
+// The 32 mask values (BF16, 64 bytes) of row m, columns n .. n + 31 (mode 2).
+__device__ __forceinline__ void load_mask32(const GemmArgs& a, int m, int n, uint4* mk) {
+    const uint4* p = reinterpret_cast<const uint4*>(a.mask + (size_t)m * a.N + n);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mk[q] = p[q];
+}
+
+// Epilogue arithmetic of 32 accumulator columns n .. n + 31 of one row:
+// relu(acc + bias) (mode 1) or acc where the BF16 mask is > 0 (mode 2).
+__device__ __forceinline__ void epilogue_math32(const GemmArgs& a, int n, float* v, const uint4* mk) {
     if (a.mode == 1) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j] + a.bias[n + j], 0.0f);
     } else {
-        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + (size_t)m * a.N + n);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             uint4 w = mk[q];
@@ -157,12 +161,21 @@ __device__ __forceinline__ void epilogue32(const GemmArgs& a, int m, int n, floa
             }
         }
     }
+}
+
+__device__ __forceinline__ uint4 pack8(const float* v) {
+    return make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+}
+
+// Epilogue of 32 accumulator columns of row m with direct stores: four
+// 16-byte stores into the row-major output, one BF16 per column into the
+// transposed one.
+__device__ __forceinline__ void epilogue32(const GemmArgs& a, int m, int n, float* v, const uint4* mk) {
+    epilogue_math32(a, n, v, mk);
     if (a.Dh) {
         uint4* dst = reinterpret_cast<uint4*>(a.Dh + (size_t)m * a.N + n);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            dst[q] = make_uint4(pack_bf16(v[8 * q], v[8 * q + 1]), pack_bf16(v[8 * q + 2], v[8 * q + 3]),
-                                pack_bf16(v[8 * q + 4], v[8 * q + 5]), pack_bf16(v[8 * q + 6], v[8 * q + 7]));
+        for (int q = 0; q < 4; ++q) dst[q] = pack8(v + 8 * q);
     }
     if (a.DhT) {
 #pragma unroll
@@ -274,7 +287,9 @@ __global__ void __launch_bounds__(kThreads, kStages == 2 ? 2 : 1)
             for (int j = 0; j < 8; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
             continue;
         }
-        epilogue32(a, m, n, v);
+        uint4 mk[4];
+        if (a.mode == 2) load_mask32(a, m, n, mk);
+        epilogue32(a, m, n, v, mk);
     }
     tc_fence_before();
     __syncthreads();
@@ -290,9 +305,19 @@ __global__ void __launch_bounds__(kThreads, kStages == 2 ? 2 : 1)
 // CTA and stays in shared memory; 128-row tiles of A stream through a
 // four-stage ring; two 256-column FP32 accumulators fill all of tensor
 // memory, so the epilogue of one tile runs while the next is multiplied.
-// Warp 0 (one lane) loads, warp 1 (one lane) issues the MMAs, warps 2-5
-// drain the accumulators (warp w reads tensor-memory lanes 32 (w % 4) ..).
-constexpr int kPThreads = 192;
+// Warp 0 (one lane) loads, warp 1 (one lane) issues the MMAs, warps 2-9
+// drain the accumulators: warp w reads tensor-memory lanes 32 (w % 4) ..
+// + 31 (the lane quadrant its warp index allows), columns 128 ((w - 2) / 4)
+// .. + 127.  In mode 2 each epilogue thread loads its row's 128 mask values
+// for the tile before the first accumulator read, so the mask's DRAM latency
+// is paid once per tile rather than once per 32 columns.  The row-major
+// output goes out through a per-warp shared-memory slot of 32 rows x 32
+// columns: a thread writes its row's 64 bytes there (16-byte units swizzled
+// by row, conflict-free), then each store instruction of the warp writes 8
+// rows x 64 contiguous bytes (full 32-byte sectors) instead of 32 rows x 16
+// bytes (half sectors).
+constexpr int kPEpiWarps = 8;
+constexpr int kPThreads = 64 + 32 * kPEpiWarps;
 constexpr int kPStages = 4;
 constexpr uint32_t kBBlock = 256u * kBK * 2;  // one 64-wide k-block of the 256-row weight operand
 
@@ -303,6 +328,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t a_full[kPStages], a_empty[kPStages], b_full, acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base_s;
+    __shared__ __align__(16) uint4 out_slot[kPEpiWarps][32 * 4];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sB = smem;
     uint8_t* sA = smem + KB * kBBlock;
@@ -315,7 +341,7 @@ __global__ void __launch_bounds__(kPThreads, 1)
         mbar_init(&b_full, 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], 128);
+            mbar_init(&acc_empty[b], 32 * kPEpiWarps);
         }
         fence_mbar_init();
     }
@@ -383,20 +409,47 @@ __global__ void __launch_bounds__(kPThreads, 1)
         }
     } else if (warp >= 2) {
         const int q = warp & 3;
+        const int cbeg = 128 * ((warp - 2) >> 2);
         const int row = q * 32 + lane;
         int i = 0;
         for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++i) {
             int buf = i & 1, u = i >> 1;
+            const int m = tile * kBM + row;
+            uint4 mk[4][4];
+            if (a.mode == 2) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) load_mask32(a, m, cbeg + 32 * c, mk[c]);
+            }
             if (!mbar_wait_bounded(&acc_full[buf], (uint32_t)(u & 1))) {
                 if (lane == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
                 break;
             }
             tc_fence_after();
-            const int m = tile * kBM + row;
-            for (int c0 = 0; c0 < 256; c0 += 32) {
+            uint4* slot = out_slot[warp - 2];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int c0 = cbeg + 32 * c;
                 float v[32];
                 tc_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * 256u + (uint32_t)c0, v);
-                epilogue32(a, m, c0, v);
+                epilogue_math32(a, c0, v, mk[c]);
+                if (a.DhT) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) a.DhT[(size_t)(c0 + j) * a.ldt + m] = __float2bfloat16_rn(v[j]);
+                }
+                if (a.Dh) {
+                    // unit k of row r sits at slot[4 r + (k ^ ((r >> 1) & 3))]
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) slot[4 * lane + (k ^ ((lane >> 1) & 3))] = pack8(v + 8 * k);
+                    __syncwarp();
+                    const int k = lane & 3;
+#pragma unroll
+                    for (int it = 0; it < 4; ++it) {
+                        const int r = 8 * it + (lane >> 2);
+                        uint4 w = slot[4 * r + (k ^ ((r >> 1) & 3))];
+                        *reinterpret_cast<uint4*>(a.Dh + (size_t)(tile * kBM + q * 32 + r) * a.N + c0 + 8 * k) = w;
+                    }
+                    __syncwarp();
+                }
             }
             tc_fence_before();
             mbar_arrive1(&acc_empty[buf]);

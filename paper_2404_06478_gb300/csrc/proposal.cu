@@ -539,36 +539,75 @@ __global__ void __launch_bounds__(kSetThreads) sets_kernel(SetsArgs a) {
 
 // ------------------------------------------------------------------ network
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+static_assert(WIDTH == 256 && HEADW == 256, "the pooling and column-sum kernels map 256 threads to the channels");
 
 // masked mean and max (first index on ties) of H3 over the valid rows: FP32
 // into pool, rounded to BF16 into poolh (the head's operand; rows B .. Bp - 1
-// of poolh are zero)
-__global__ void __launch_bounds__(WIDTH) pool_kernel(const __nv_bfloat16* H3, const int* nvalid, int B, int Bp,
-                                                     float* pool, __nv_bfloat16* poolh, int* amax) {
+// of poolh are zero).  One CTA per set: thread t reads channels 8 (t % 32)
+// .. + 7 of rows t / 32, t / 32 + 8, ... with 16-byte loads; the eight row
+// groups are combined in order (sums added; the larger maximum, the lower
+// row on ties).
+__global__ void __launch_bounds__(256) pool_kernel(const __nv_bfloat16* __restrict__ H3,
+                                                   const int* __restrict__ nvalid, int B, int Bp,
+                                                   float* __restrict__ pool, __nv_bfloat16* __restrict__ poolh,
+                                                   int* __restrict__ amax) {
+    __shared__ float s_sum[8][WIDTH], s_best[8][WIDTH];
+    __shared__ int s_arg[8][WIDTH];
+    const int c8 = (threadIdx.x & 31) * 8, g = threadIdx.x >> 5, c = threadIdx.x;
     for (int b = blockIdx.x; b < Bp; b += gridDim.x) {
-        int c = threadIdx.x;
         if (b >= B) {
             poolh[(size_t)b * 2 * WIDTH + c] = __float2bfloat16_rn(0.0f);
             poolh[(size_t)b * 2 * WIDTH + WIDTH + c] = __float2bfloat16_rn(0.0f);
             continue;
         }
-        int nv = nvalid[b];
-        float sum = 0.0f, best = 0.0f;
-        int arg = 0;
-        for (int e = 0; e < nv; ++e) {
-            float h = bf(H3[((size_t)b * KSET + e) * WIDTH + c]);
-            sum += h;
-            if (e == 0 || h > best) {
-                best = h;
-                arg = e;
+        const int nv = nvalid[b];
+        float sum[8], best[8];
+        int arg[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            sum[j] = 0.0f;
+            best[j] = 0.0f;
+            arg[j] = -1;
+        }
+#pragma unroll 4
+        for (int e = g; e < nv; e += 8) {
+            uint4 v = *reinterpret_cast<const uint4*>(H3 + ((size_t)b * KSET + e) * WIDTH + c8);
+            const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float h = bf(hv[j]);
+                sum[j] += h;
+                if (arg[j] < 0 || h > best[j]) {
+                    best[j] = h;
+                    arg[j] = e;
+                }
             }
         }
-        float mean = nv > 0 ? sum / (float)nv : 0.0f, mx = nv > 0 ? best : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            s_sum[g][c8 + j] = sum[j];
+            s_best[g][c8 + j] = best[j];
+            s_arg[g][c8 + j] = arg[j];
+        }
+        __syncthreads();
+        float tsum = 0.0f, tbest = 0.0f;
+        int targ = -1;
+        for (int q = 0; q < 8; ++q) {
+            tsum += s_sum[q][c];
+            const int aq = s_arg[q][c];
+            const float bq = s_best[q][c];
+            if (aq >= 0 && (targ < 0 || bq > tbest || (bq == tbest && aq < targ))) {
+                tbest = bq;
+                targ = aq;
+            }
+        }
+        const float mean = nv > 0 ? tsum / (float)nv : 0.0f, mx = nv > 0 ? tbest : 0.0f;
         pool[(size_t)b * 2 * WIDTH + c] = mean;
         pool[(size_t)b * 2 * WIDTH + WIDTH + c] = mx;
         poolh[(size_t)b * 2 * WIDTH + c] = __float2bfloat16_rn(mean);
         poolh[(size_t)b * 2 * WIDTH + WIDTH + c] = __float2bfloat16_rn(mx);
-        amax[(size_t)b * WIDTH + c] = arg;
+        amax[(size_t)b * WIDTH + c] = targ < 0 ? 0 : targ;
+        __syncthreads();
     }
 }
 
@@ -602,17 +641,29 @@ __global__ void colsum_partial_kernel(const float* A, long long lda, int M, int 
 
 // column sums of a BF16 [rows][256] array (the bias gradients sum_m dZ[m][c]):
 // blockIdx.x takes rows [x rc, (x+1) rc); thread t adds channels 8 (t % 32)
-// .. + 7 of the rows t / 32, t / 32 + 8, ... with 16-byte loads, then the
-// eight row groups are added in order; one partial per (block, channel) in
-// part[block][256], added in order by split_reduce.
-constexpr int kColsumSplits = 256;
+// .. + 7 of the rows t / 32, t / 32 + 8, ... (four 16-byte loads in flight),
+// then the eight row groups are added in order; one partial per (block,
+// channel) in part[block][256], added in order by reduce_partials.
+constexpr int kColsumSplits = 1024;
 __global__ void __launch_bounds__(256) colsum_bf16_kernel(const __nv_bfloat16* A, long long rows, float* part) {
     __shared__ float red[8][WIDTH];
     const int c8 = (threadIdx.x & 31) * 8, g = threadIdx.x >> 5;
     const long long rc = (rows + gridDim.x - 1) / gridDim.x;
     const long long r0 = (long long)blockIdx.x * rc, r1 = min(rows, r0 + rc);
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (long long r = r0 + g; r < r1; r += 8) {
+    long long r = r0 + g;
+    for (; r + 24 < r1; r += 32) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const uint4*>(A + (size_t)(r + 8 * u) * WIDTH + c8);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v[u]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += bf(hv[j]);
+        }
+    }
+    for (; r < r1; r += 8) {
         uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)r * WIDTH + c8);
         const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v);
 #pragma unroll
@@ -624,6 +675,28 @@ __global__ void __launch_bounds__(256) colsum_bf16_kernel(const __nv_bfloat16* A
     float t = 0.0f;
     for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
     part[(size_t)blockIdx.x * WIDTH + threadIdx.x] = t;
+}
+
+// out[j] = sum_s part[s n + j] for many partials and few outputs: block x
+// takes outputs 32 x .. + 31; warp w adds the partials s = w, w + 32, ...
+// of output 32 x + lane, then the 32 warp sums are added in order.
+constexpr int kReduceThreads = 1024;
+__global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(const float* __restrict__ part, int splits,
+                                                                         int n, float* __restrict__ out) {
+    constexpr int W = kReduceThreads / 32;
+    __shared__ float red[W][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, j = blockIdx.x * 32 + lane;
+    float t = 0.0f;
+    if (j < n)
+#pragma unroll 8
+        for (int q = w; q < splits; q += W) t += part[(size_t)q * n + j];
+    red[w][lane] = t;
+    __syncthreads();
+    if (w == 0 && j < n) {
+        float r = 0.0f;
+        for (int q = 0; q < W; ++q) r += red[q][lane];
+        out[j] = r;
+    }
 }
 
 // sum of split-K partials: out[j] = sum_s part[s stride + j], j < n
@@ -780,14 +853,23 @@ __global__ void loss_kernel(const float* O, const float* Rt, const float* xt, co
 }
 
 // dZ3 = (dmean / nv on valid rows + dmax at the argmax row) where H3 > 0,
-// rounded to BF16, row-major.  One CTA per set; each thread handles 8
-// channels of a row with 16-byte loads and stores.
-__global__ void __launch_bounds__(256) pool_backward_kernel(const __nv_bfloat16* H3, const int* nvalid,
-                                                            const int* amax, const float* dPool, int B,
-                                                            __nv_bfloat16* dZ3) {
+// rounded to BF16, row-major.  A CTA takes the sets b = x, x + gridDim.x,
+// ...; each thread handles 8 channels of a row with 16-byte loads and
+// stores.  The column sums of the CTA's rounded dZ3 rows (its share of the
+// bias gradient of layer 3) go to part[x][256], the sets and the eight row
+// groups added in order.
+constexpr int kPoolBwdBlocks = 1024;
+__global__ void __launch_bounds__(256) pool_backward_kernel(const __nv_bfloat16* __restrict__ H3,
+                                                            const int* __restrict__ nvalid,
+                                                            const int* __restrict__ amax,
+                                                            const float* __restrict__ dPool, int B,
+                                                            __nv_bfloat16* __restrict__ dZ3,
+                                                            float* __restrict__ part) {
     __shared__ float dm_s[WIDTH], dx_s[WIDTH];
     __shared__ int am_s[WIDTH];
+    __shared__ float red[8][WIDTH];
     const int c8 = (threadIdx.x & 31) * 8, r0 = threadIdx.x >> 5;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int b = blockIdx.x; b < B; b += gridDim.x) {
         const int nv = nvalid[b];
         for (int c = threadIdx.x; c < WIDTH; c += blockDim.x) {
@@ -796,6 +878,16 @@ __global__ void __launch_bounds__(256) pool_backward_kernel(const __nv_bfloat16*
             am_s[c] = amax[(size_t)b * WIDTH + c];
         }
         __syncthreads();
+        // this thread's 8 channels: the per-set constants in registers
+        float dm[8], dx[8];
+        int am[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            dm[j] = dm_s[c8 + j];
+            dx[j] = dx_s[c8 + j];
+            am[j] = am_s[c8 + j];
+        }
+#pragma unroll 4
         for (int e = r0; e < KSET; e += 8) {
             const size_t row = (size_t)b * KSET + e;
             uint4 hv = *reinterpret_cast<const uint4*>(H3 + row * WIDTH + c8);
@@ -803,14 +895,20 @@ __global__ void __launch_bounds__(256) pool_backward_kernel(const __nv_bfloat16*
             __align__(16) __nv_bfloat16 z[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                int c = c8 + j;
-                float v = (e < nv ? dm_s[c] : 0.0f) + (e == am_s[c] ? dx_s[c] : 0.0f);
+                float v = (e < nv ? dm[j] : 0.0f) + (e == am[j] ? dx[j] : 0.0f);
                 z[j] = __float2bfloat16_rn(bf(hh[j]) > 0.0f ? v : 0.0f);
+                acc[j] += bf(z[j]);
             }
             *reinterpret_cast<uint4*>(dZ3 + row * WIDTH + c8) = *reinterpret_cast<const uint4*>(z);
         }
         __syncthreads();
     }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[r0][c8 + j] = acc[j];
+    __syncthreads();
+    float t = 0.0f;
+    for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+    part[(size_t)blockIdx.x * WIDTH + threadIdx.x] = t;
 }
 
 __global__ void adam_kernel(float* p, float* m, float* v, const float* g, long long n, const int* step, float lr,
@@ -941,7 +1039,7 @@ cudaError_t forward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaStr
     g.Dh = bfp(L.H3);
     if ((e = gemm_tc_run(GemmOperands{bfp(L.H2), n.W3h, WIDTH, WIDTH}, g, 1, s)) != cudaSuccess) return e;
     const int Bp = L.Bp;
-    pool_kernel<<<Bp, WIDTH, 0, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), B, Bp, bt.at<float>(L.pool), bfp(L.poolh),
+    pool_kernel<<<Bp, 256, 0, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), B, Bp, bt.at<float>(L.pool), bfp(L.poolh),
                                      bt.at<int>(L.amax));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // head on the tensor cores: H4 = relu(pool W4^T + b4) (BF16), O = H4 W5^T + b5
@@ -993,7 +1091,7 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
     split_reduce_kernel<<<(NOUT * HEADW + 255) / 256, 256, 0, s>>>(n.part, hs, (long long)NOUTP * HEADW,
                                                                    (long long)NOUT * HEADW, n.G + oW5);
     colsum_partial_kernel<<<dim3(1, 32), NOUT, 0, s>>>(dO, NOUT, B, NOUT, 32, n.part);
-    split_reduce_kernel<<<1, 256, 0, s>>>(n.part, 32, NOUT, NOUT, n.G + ob5);
+    reduce_partials_kernel<<<(NOUT + 31) / 32, kReduceThreads, 0, s>>>(n.part, 32, NOUT, n.G + ob5);
     GemmArgs d4{};
     d4.M = Bp;
     d4.N = HEADW;
@@ -1018,8 +1116,9 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
     if ((e = gemm_tc_run(GemmOperands{bfp(L.dZ4h), bfp(L.poolh), HEADW, 2 * WIDTH}, w4, hs, s))) return e;
     split_reduce_kernel<<<(HEADW * 2 * WIDTH + 255) / 256, 256, 0, s>>>(n.part, hs, (long long)HEADW * 2 * WIDTH,
                                                                         (long long)HEADW * 2 * WIDTH, n.G + oW4);
-    colsum_bf16_kernel<<<kColsumSplits, 256, 0, s>>>(bfp(L.dZ4h), Bp, n.part);
-    split_reduce_kernel<<<1, 256, 0, s>>>(n.part, kColsumSplits, WIDTH, WIDTH, n.G + ob4);
+    const int cs4 = Bp / 8 < kColsumSplits ? Bp / 8 : kColsumSplits;
+    colsum_bf16_kernel<<<cs4, 256, 0, s>>>(bfp(L.dZ4h), Bp, n.part);
+    reduce_partials_kernel<<<WIDTH / 32, kReduceThreads, 0, s>>>(n.part, cs4, WIDTH, n.G + ob4);
     GemmArgs dp{};
     dp.M = Bp;
     dp.N = 2 * WIDTH;
@@ -1030,9 +1129,11 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
     dp.ctrl = ctrl;
     dp.b_mn = 1;  // W4 [hidden][pool] is the [K][N] operand
     if ((e = gemm_tc_run(GemmOperands{bfp(L.dZ4h), n.W4h, HEADW, 2 * WIDTH}, dp, 1, s))) return e;
-    // pooling -> dZ3
-    pool_backward_kernel<<<B, 256, 0, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), bt.at<int>(L.amax),
-                                           bt.at<float>(L.dPool), B, bfp(L.dZ3));
+    // pooling -> dZ3, with the bias gradient of layer 3 (per-set column sums)
+    const int pb = B < kPoolBwdBlocks ? B : kPoolBwdBlocks;
+    pool_backward_kernel<<<pb, 256, 0, s>>>(bfp(L.H3), bt.at<int>(L.nvalid), bt.at<int>(L.amax),
+                                            bt.at<float>(L.dPool), B, bfp(L.dZ3), n.part);
+    reduce_partials_kernel<<<WIDTH / 32, kReduceThreads, 0, s>>>(n.part, pb, WIDTH, n.G + ob3);
     if ((e = cudaGetLastError())) return e;
     // dZ2 = (dZ3 W3) * (H2 > 0), dZ1 = (dZ2 W2) * (H1 > 0)
     GemmArgs g{};
@@ -1076,8 +1177,9 @@ cudaError_t backward_run(const Net& n, const Batch& bt, int B, int* ctrl, cudaSt
         long long nw = (long long)WIDTH * layers[l].N;
         split_reduce_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(n.part, splits, nw, nw,
                                                                           n.G + layers[l].oW);
+        if (l == 0) continue;  // the bias gradient of layer 3 came with dZ3
         colsum_bf16_kernel<<<kColsumSplits, 256, 0, s>>>(bfp(layers[l].A), Ms, n.part);
-        split_reduce_kernel<<<1, 256, 0, s>>>(n.part, kColsumSplits, WIDTH, WIDTH, n.G + layers[l].ob);
+        reduce_partials_kernel<<<WIDTH / 32, kReduceThreads, 0, s>>>(n.part, kColsumSplits, WIDTH, n.G + layers[l].ob);
         if ((e = cudaGetLastError())) return e;
     }
     return cudaSuccess;

@@ -21,7 +21,7 @@ constexpr float LAMBDA_X = 0.1f;
 constexpr float BETA = 0.05f;
 constexpr float DSCALE = 200.0f;
 constexpr float HALFS = 128.0f;
-constexpr int kMaxSplits = 128;  // split-K partials of the weight gradients
+constexpr int kMaxSplits = 64;   // split-K partials of the weight gradients
 
 // FP32 parameter vector: W1 (256 x 64), b1, W2 (256 x 256), b2, W3, b3,
 // W4 (256 x 512), b4, W5 (72 x 256), b5; weights row-major [out][in].
