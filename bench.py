@@ -276,7 +276,7 @@ def proposal_bench(dev, api, sg, torch, peaks):
     # them, row-major [spots][channels], read MN-major by the GEMM
     dZ = torch.randn(Ms, 256, device=dev).to(torch.bfloat16)
     Hp = torch.randn(Ms, 256, device=dev).to(torch.bfloat16)
-    part = torch.empty(128, 256, 256, device=dev)
+    part = torch.empty(64, 256, 256, device=dev)
 
     def timed(fn, reps=20):
         for _ in range(3):
@@ -293,11 +293,11 @@ def proposal_bench(dev, api, sg, torch, peaks):
     t_fwd = timed(lambda: pr.gemm_bf16(h, A, B, mode=1, bias=bias, out=D))
     # context for write-heavy kernels: a plain fill of the same output bytes
     t_fill = timed(lambda: D.fill_(1.0))
-    t_wg = timed(lambda: pr.gemm_bf16(h, dZ, Hp, mode=0, splits=128, out_f32=part, a_mn=True, b_mn=True))
+    t_wg = timed(lambda: pr.gemm_bf16(h, dZ, Hp, mode=0, splits=64, out_f32=part, a_mn=True, b_mn=True))
     fl = 2.0 * Ms * 256 * 256
     # the method's bytes: A read and one output written
     by_fwd = Ms * 256 * 2 + Ms * 256 * 2 + 256 * 256 * 2
-    by_wg = 2 * 256 * Ms * 2 + 128 * 256 * 256 * 4
+    by_wg = 2 * 256 * Ms * 2 + 64 * 256 * 256 * 4
     hbm, bf = peaks.get("hbm_gbs", 6800.0), peaks.get("bf16_tflops", 1900.0)
     out["gemm"] = dict(
         kernel="gemm_tc_kernel (tcgen05, TMA, TMEM)",
@@ -306,7 +306,7 @@ def proposal_bench(dev, api, sg, torch, peaks):
                            roofline=dict(bound="hbm", achieved=by_fwd / t_fwd / 1e9, peak=hbm, unit="GB/s",
                                          frac=by_fwd / t_fwd / 1e9 / hbm, traffic=None,
                                          algorithmic_bytes=by_fwd)),
-        weight_grad=dict(shape="M=256 N=256 K=%d, split-K 128, FP32 partials, both operands MN-major" % Ms,
+        weight_grad=dict(shape="M=256 N=256 K=%d, split-K 64, FP32 partials, both operands MN-major" % Ms,
                          us=t_wg * 1e6,
                          tflops=fl / t_wg / 1e12, tensor_frac_of_measured=fl / t_wg / 1e12 / bf,
                          roofline=dict(bound="hbm", achieved=by_wg / t_wg / 1e9, peak=hbm, unit="GB/s",
