@@ -307,33 +307,45 @@ __device__ float sf_block_sum9(SfShared& S, float* v) {
 // Newton sums of observed spot p with row normaliser l against the listed
 // spots [j0, j1) of its angle (centre c of the current position, Gamma_t of
 // cos/sin cg, sg), accumulated in the sample frame of x: with the directions
-// rotated back, hx = Gamma^T rhat and rx = Gamma^T r, the gradient and Hessian
-// of Q rhat.r w.r.t. x are the lab-frame expressions in hx, rx.
+// rotated back, h = Gamma^T rhat and r_j = Gamma^T r_j(lab), the gradient and
+// Hessian of sum_j Q_ij rhat.r_j w.r.t. x are
+//   g = -s sum_j Q_ij (r_j - (h.r_j) h),
+//   H = s^2 sum_j Q_ij (3 (h.r_j) h h^T - h r_j^T - r_j h^T - (h.r_j) I),
+// s = 1 / |p - c|.  h and s belong to the row, so both are linear in
+// u = sum_j Q_ij r_j: the pair loop only accumulates u (in the lab frame,
+// rotated once per row), and the row adds g and H formed from u.  Q_ij carries
+// the M-step weight (D_j / D)^2 = K_j / negK.
 __device__ __forceinline__ void sf_newton_row(const SfScratch& Z, int j0, int j1, const float4& p, float l,
-                                              const float* c, float cg, float sg, float* acc) {
+                                              const float* c, float cg, float sg, float inv_negK, float* acc) {
     const SfRowG g = sf_rowg(p, Z.cE + 3 * j0);  // E-step direction
+    float ul[3] = {0.0f, 0.0f, 0.0f};
+    bool any = false;
+    for (int j = j0; j < j1; ++j) {
+        const float4 rk = Z.rk[j];
+        const float v = sf_pair_v(g, rk) - l;
+        if (v < kSfSkip) continue;
+        const float Q = ex2(v) * rk.w;  // times K_j; 1 / negK is applied per row
+        ul[0] = fmaf(-Q, rk.x, ul[0]);    // r_j = -rk.xyz
+        ul[1] = fmaf(-Q, rk.y, ul[1]);
+        ul[2] = fmaf(-Q, rk.z, ul[2]);
+        any = true;
+    }
+    if (!any) return;
+    for (int k = 0; k < 3; ++k) ul[k] *= inv_negK;
     // direction at the current position
     const float d0 = p.x - c[0], d1 = p.y - c[1], d2 = p.z - c[2];
     const float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
     const float hl[3] = {d0 * is, d1 * is, d2 * is};
-    float h[3];
+    float h[3], u[3];
     gamT_apply(cg, sg, hl, h);
-    for (int j = j0; j < j1; ++j) {
-        const float4 rk = Z.rk[j];
-        float v = sf_pair_v(g, rk) - l;
-        if (v < kSfSkip) continue;
-        float Q = ex2(v) * Z.kd[j];  // M-step weight Q_ij (D_j / D)^2
-        const float rl[3] = {-rk.x, -rk.y, -rk.z};
-        float r[3];
-        gamT_apply(cg, sg, rl, r);
-        float rr = h[0] * r[0] + h[1] * r[1] + h[2] * r[2];
-        float qs = Q * is, q2 = qs * is;
-        for (int k = 0; k < 3; ++k) acc[k] -= qs * (r[k] - rr * h[k]);
-        int kk = 3;
-        for (int u = 0; u < 3; ++u)
-            for (int w = u; w < 3; ++w)
-                acc[kk++] += q2 * (3.0f * rr * h[u] * h[w] - h[u] * r[w] - r[u] * h[w] - (u == w ? rr : 0.0f));
-    }
+    gamT_apply(cg, sg, ul, u);
+    const float hu = h[0] * u[0] + h[1] * u[1] + h[2] * u[2];
+    const float is2 = is * is;
+    for (int k = 0; k < 3; ++k) acc[k] -= is * (u[k] - hu * h[k]);
+    int kk = 3;
+    for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b)
+            acc[kk++] += is2 * (3.0f * hu * h[a] * h[b] - h[a] * u[b] - u[a] * h[b] - (a == b ? hu : 0.0f));
 }
 
 // One Newton step on x with the plan of the E-step costs (near rows of sf_near).
@@ -341,6 +353,7 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
                           unsigned long long& npair) {
     float acc[9];
     for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+    const float inv_negK = 1.0f / negK;
     for (int t = 0; t < a.T; ++t) {
         int j0 = S.t_off[t], j1 = S.t_off[t + 1];
         if (j0 == j1) continue;
@@ -351,7 +364,7 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
             for (int k = off + threadIdx.x; k < S.near_end[t]; k += blockDim.x) {
                 npair += (unsigned)(j1 - j0);
                 const float4 q = Z.near[k];
-                sf_newton_row(Z, j0, j1, q, q.w, c, cg, sg, acc);
+                sf_newton_row(Z, j0, j1, q, q.w, c, cg, sg, inv_negK, acc);
             }
         } else {
             for (int i = a.I_off[t] + threadIdx.x; i < a.I_off[t + 1]; i += blockDim.x) {
@@ -359,7 +372,7 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
                 float vmax;
                 float l = sf_row_lse(a, S, Z, t, p, dust, npair, vmax);
                 npair += (unsigned)(j1 - j0);
-                sf_newton_row(Z, j0, j1, p, l, c, cg, sg, acc);
+                sf_newton_row(Z, j0, j1, p, l, c, cg, sg, inv_negK, acc);
             }
         }
     }
