@@ -39,13 +39,15 @@ enum CtrlSlot {
 
 // single-grain fits: resident CTAs per SM, listed spots per start, cached row
 // normalisers per angle block, scratch floats per listed spot ({-r, K} (4),
-// centre (3), MM sums (3), tm, kd) and the largest capacity of the near-row list
-// (observed rows that carry plan mass in one EM step, {p, normaliser}; the
+// centre (3), MM sums (3), tm, kd), scratch floats per near row ({p,
+// normaliser} and the row's plan-weighted ray sum u) and the largest capacity
+// of the near-row list (observed rows that carry plan mass in one EM step; the
 // list holds min(n_obs, kSfNearMax) rows, sf_near_cap)
 constexpr int kSfCtasPerSm = 6;
 constexpr int kSfCap = 2048;
 constexpr int kSfIcap = 4096;
 constexpr int kSfSpotFloats = 12;
+constexpr int kSfNearFloats = 8;
 constexpr int kSfNearMax = 131072;
 inline size_t sf_near_cap(int n_obs) {
     size_t c = n_obs < kSfNearMax ? (size_t)(n_obs > 0 ? n_obs : 1) : (size_t)kSfNearMax;
@@ -127,7 +129,8 @@ inline Layout make_layout(const LaueProblemDims& d, int sm_count) {
     L.gidx = take(sizeof(int) * ((size_t)T * (d.n_grains + 1) + 16));
     // single-grain fits, per CTA (the slices of sf_slice in single.cu)
     size_t sf_ctas = d.n_starts > 0 ? (size_t)sm_count * kSfCtasPerSm : 0;
-    L.sfs = take(sizeof(float) * ((size_t)kSfCap * kSfSpotFloats + kSfIcap + 4 * sf_near_cap(d.n_obs)) * sf_ctas);
+    L.sfs = take(sizeof(float) * ((size_t)kSfCap * kSfSpotFloats + kSfIcap + kSfNearFloats * sf_near_cap(d.n_obs)) *
+                 sf_ctas);
     L.spot = take(d.n_candidates > 0 ? sizeof(int) * (4 * (size_t)d.n_candidates + 16 + 2 * (size_t)sm_count * 4 + 64) +
                                            sizeof(float) * (size_t)(d.n_obs + 1)
                                      : 0);

@@ -37,11 +37,12 @@ struct SfScratch {
     float* kd;   // cap: (D_j / D)^2, the cost length of the spot's detector relative to D
     float* lse;  // icap row normalisers of one angle block (log2)
     float4* near;  // near rows of the current E-step (ncap): {p, row normaliser (log2)}
+    float4* nearu; // ncap: {u, t}, u = sum_j Q_ij (D_j / D)^2 r_j of the near row (lab frame), t its angle
 };
 
 __device__ __forceinline__ SfScratch sf_slice(const SfArgs& a, int cta) {
     SfScratch s;
-    size_t per = (size_t)a.cap * kSfSpotFloats + a.icap + 4 * (size_t)a.ncap;
+    size_t per = (size_t)a.cap * kSfSpotFloats + a.icap + kSfNearFloats * (size_t)a.ncap;
     float* base = a.scratch + per * cta;  // 16-byte aligned: per is a multiple of 4 floats
     s.rk = (float4*)base;
     s.cE = base + 4 * a.cap;
@@ -50,6 +51,7 @@ __device__ __forceinline__ SfScratch sf_slice(const SfArgs& a, int cta) {
     s.kd = base + 11 * a.cap;
     s.lse = base + 12 * a.cap;
     s.near = (float4*)(s.lse + a.icap);  // 16-byte aligned: cap, icap are multiples of 4
+    s.nearu = s.near + a.ncap;           // ncap is a multiple of 4
     return s;
 }
 
@@ -237,6 +239,61 @@ __device__ __forceinline__ float sf_row_lse(const SfArgs& a, const SfShared& S, 
     return L.value();
 }
 
+// Row normaliser l of observed spot p (as sf_row_lse) together with the row's
+// plan-weighted ray sum u = sum_j Q_ij (D_j / D)^2 r_j (lab frame), Q_ij =
+// 2^(v_ij - l) over every listed spot of angle t: with the row's direction
+// fixed during the M-step, the Newton sums of the row are linear in u, so u
+// is formed once per E-step.  The weight (D_j / D)^2 = K_j / negK.
+__device__ __forceinline__ float sf_row_lse_u(const SfArgs& a, const SfShared& S, const SfScratch& Z, int t,
+                                              const float4& p, float dust, float inv_negK,
+                                              unsigned long long& npair, float& vmax, float* u) {
+    const int j0 = S.t_off[t], j1 = S.t_off[t + 1];
+    npair += (unsigned)(j1 - j0);
+    vmax = kNegHuge;
+    u[0] = u[1] = u[2] = 0.0f;
+    if (j1 == j0) return dust;
+    const SfRowG g = sf_rowg(p, Z.cE + 3 * j0);
+    float m = dust, s = 1.0f, u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
+    if (dust >= -100.0f) {  // relative to the outlier term, no running maximum
+#pragma unroll 4
+        for (int j = j0; j < j1; ++j) {
+            const float4 rk = Z.rk[j];
+            const float v = sf_pair_v(g, rk);
+            vmax = fmaxf(vmax, v);
+            const float w = ex2(v - dust), wk = w * rk.w;
+            s += w;
+            u0 = fmaf(-wk, rk.x, u0);  // r_j = -rk.xyz
+            u1 = fmaf(-wk, rk.y, u1);
+            u2 = fmaf(-wk, rk.z, u2);
+        }
+    } else {
+        for (int j = j0; j < j1; ++j) {
+            const float4 rk = Z.rk[j];
+            const float v = sf_pair_v(g, rk);
+            vmax = fmaxf(vmax, v);
+            if (v > m) {
+                const float f = ex2(m - v);
+                s = fmaf(s, f, 1.0f);
+                u0 = fmaf(u0, f, -rk.w * rk.x);
+                u1 = fmaf(u1, f, -rk.w * rk.y);
+                u2 = fmaf(u2, f, -rk.w * rk.z);
+                m = v;
+            } else {
+                const float w = ex2(v - m), wk = w * rk.w;
+                s += w;
+                u0 = fmaf(-wk, rk.x, u0);
+                u1 = fmaf(-wk, rk.y, u1);
+                u2 = fmaf(-wk, rk.z, u2);
+            }
+        }
+    }
+    const float sc = inv_negK / s;  // 2^(m - l) = 1 / s
+    u[0] = u0 * sc;
+    u[1] = u1 * sc;
+    u[2] = u2 * sc;
+    return m + lg2(s);
+}
+
 // Row normalisers of this EM step's E-step and the rows that carry plan mass.
 // A row is near when some pair keeps Q_ij >= 2^kSfSkip (v_ij - l_i >=
 // kSfSkip); every other row has all its plan entries below the cut-off that
@@ -246,7 +303,8 @@ __device__ __forceinline__ float sf_row_lse(const SfArgs& a, const SfShared& S, 
 // in full by the passes.  The plan stays the E-step's for the whole M-step,
 // so the list serves every Newton and MM pass of the step.
 __device__ void sf_near(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK, float dust,
-                        unsigned long long& npair) {
+                        unsigned long long& npair, bool with_u) {
+    const float inv_negK = 1.0f / negK;
     __shared__ int wcnt[kSfThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) S.n_near = 0;
@@ -259,11 +317,13 @@ __device__ void sf_near(const SfArgs& a, SfShared& S, const SfScratch& Z, float 
                 const int i = i0 + threadIdx.x;
                 bool near = false;
                 float l = 0.0f;
+                float u[3] = {0.0f, 0.0f, 0.0f};
                 float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (i < a.I_off[t + 1]) {
                     float vmax;
                     p = a.p[i];
-                    l = sf_row_lse(a, S, Z, t, p, dust, npair, vmax);
+                    l = with_u ? sf_row_lse_u(a, S, Z, t, p, dust, inv_negK, npair, vmax, u)
+                               : sf_row_lse(a, S, Z, t, p, dust, npair, vmax);
                     near = vmax - l >= kSfSkip;
                 }
                 const unsigned ball = __ballot_sync(0xffffffffu, near);
@@ -275,7 +335,10 @@ __device__ void sf_near(const SfArgs& a, SfShared& S, const SfScratch& Z, float 
                     total += wcnt[k];
                 }
                 const int pos = base + cnt + before + __popc(ball & ((1u << lane) - 1u));
-                if (near && pos < a.ncap) Z.near[pos] = make_float4(p.x, p.y, p.z, l);
+                if (near && pos < a.ncap) {
+                    Z.near[pos] = make_float4(p.x, p.y, p.z, l);
+                    if (with_u) Z.nearu[pos] = make_float4(u[0], u[1], u[2], __int_as_float(t));
+                }
                 cnt += total;
                 __syncthreads();
             }
@@ -304,34 +367,19 @@ __device__ float sf_block_sum9(SfShared& S, float* v) {
     return 0.0f;
 }
 
-// Newton sums of observed spot p with row normaliser l against the listed
-// spots [j0, j1) of its angle (centre c of the current position, Gamma_t of
-// cos/sin cg, sg), accumulated in the sample frame of x: with the directions
-// rotated back, h = Gamma^T rhat and r_j = Gamma^T r_j(lab), the gradient and
-// Hessian of sum_j Q_ij rhat.r_j w.r.t. x are
+// Newton sums of observed spot p against the listed spots of its angle,
+// accumulated in the sample frame of x (centre c of the current position,
+// Gamma_t of cos/sin cg, sg): with the directions rotated back, h = Gamma^T
+// rhat and r_j = Gamma^T r_j(lab), the gradient and Hessian of
+// sum_j Q_ij rhat.r_j w.r.t. x are
 //   g = -s sum_j Q_ij (r_j - (h.r_j) h),
 //   H = s^2 sum_j Q_ij (3 (h.r_j) h h^T - h r_j^T - r_j h^T - (h.r_j) I),
-// s = 1 / |p - c|.  h and s belong to the row, so both are linear in
-// u = sum_j Q_ij r_j: the pair loop only accumulates u (in the lab frame,
-// rotated once per row), and the row adds g and H formed from u.  Q_ij carries
-// the M-step weight (D_j / D)^2 = K_j / negK.
-__device__ __forceinline__ void sf_newton_row(const SfScratch& Z, int j0, int j1, const float4& p, float l,
-                                              const float* c, float cg, float sg, float inv_negK, float* acc) {
-    const SfRowG g = sf_rowg(p, Z.cE + 3 * j0);  // E-step direction
-    float ul[3] = {0.0f, 0.0f, 0.0f};
-    bool any = false;
-    for (int j = j0; j < j1; ++j) {
-        const float4 rk = Z.rk[j];
-        const float v = sf_pair_v(g, rk) - l;
-        if (v < kSfSkip) continue;
-        const float Q = ex2(v) * rk.w;  // times K_j; 1 / negK is applied per row
-        ul[0] = fmaf(-Q, rk.x, ul[0]);    // r_j = -rk.xyz
-        ul[1] = fmaf(-Q, rk.y, ul[1]);
-        ul[2] = fmaf(-Q, rk.z, ul[2]);
-        any = true;
-    }
-    if (!any) return;
-    for (int k = 0; k < 3; ++k) ul[k] *= inv_negK;
+// s = 1 / |p - c|.  h and s belong to the row, so both are linear in the
+// row's u = sum_j Q_ij (D_j / D)^2 r_j (lab frame, from sf_row_lse_u; the
+// weight is the M-step's), which the E-step plan fixes for the whole M-step.
+__device__ __forceinline__ void sf_newton_row(const float4& p, const float* ul, const float* c, float cg, float sg,
+                                              float* acc) {
+    if (ul[0] == 0.0f && ul[1] == 0.0f && ul[2] == 0.0f) return;
     // direction at the current position
     const float d0 = p.x - c[0], d1 = p.y - c[1], d2 = p.z - c[2];
     const float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
@@ -354,26 +402,39 @@ __device__ void sf_newton(const SfArgs& a, SfShared& S, const SfScratch& Z, floa
     float acc[9];
     for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
     const float inv_negK = 1.0f / negK;
-    for (int t = 0; t < a.T; ++t) {
-        int j0 = S.t_off[t], j1 = S.t_off[t + 1];
-        if (j0 == j1) continue;
+    // the listed near rows of every angle, [0, n_near): one flat loop, four
+    // rows per thread and step with their loads issued together (the rows sit
+    // in global memory and the pass is bound by their latency)
+    auto row = [&](const float4& q, const float4& uq) {
+        const int t = __float_as_int(uq.w);
         const float cg = S.cs[t].x, sg = S.cs[t].y;
-        float c[3] = {cg * S.x[0] + sg * S.x[2], S.x[1], -sg * S.x[0] + cg * S.x[2]};
-        const int off = S.near_off[t];
-        if (off >= 0) {
-            for (int k = off + threadIdx.x; k < S.near_end[t]; k += blockDim.x) {
-                npair += (unsigned)(j1 - j0);
-                const float4 q = Z.near[k];
-                sf_newton_row(Z, j0, j1, q, q.w, c, cg, sg, inv_negK, acc);
-            }
-        } else {
-            for (int i = a.I_off[t] + threadIdx.x; i < a.I_off[t + 1]; i += blockDim.x) {
-                float4 p = a.p[i];
-                float vmax;
-                float l = sf_row_lse(a, S, Z, t, p, dust, npair, vmax);
-                npair += (unsigned)(j1 - j0);
-                sf_newton_row(Z, j0, j1, p, l, c, cg, sg, inv_negK, acc);
-            }
+        const float c[3] = {cg * S.x[0] + sg * S.x[2], S.x[1], -sg * S.x[0] + cg * S.x[2]};
+        const float ul[3] = {uq.x, uq.y, uq.z};
+        sf_newton_row(q, ul, c, cg, sg, acc);
+    };
+    const int nn = S.n_near;
+    int k = threadIdx.x;
+    for (; k + 3 * kSfThreads < nn; k += 4 * kSfThreads) {
+        float4 q[4], uq[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            q[r] = Z.near[k + r * kSfThreads];
+            uq[r] = Z.nearu[k + r * kSfThreads];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) row(q[r], uq[r]);
+    }
+    for (; k < nn; k += kSfThreads) row(Z.near[k], Z.nearu[k]);
+    // angles whose near rows did not fit the list: every row, u recomputed
+    for (int t = 0; t < a.T; ++t) {
+        if (S.t_off[t + 1] == S.t_off[t] || S.near_off[t] >= 0) continue;
+        const float cg = S.cs[t].x, sg = S.cs[t].y;
+        const float c[3] = {cg * S.x[0] + sg * S.x[2], S.x[1], -sg * S.x[0] + cg * S.x[2]};
+        for (int i = a.I_off[t] + threadIdx.x; i < a.I_off[t + 1]; i += blockDim.x) {
+            const float4 p = a.p[i];
+            float vmax, ul[3];
+            sf_row_lse_u(a, S, Z, t, p, dust, inv_negK, npair, vmax, ul);
+            sf_newton_row(p, ul, c, cg, sg, acc);
         }
     }
     sf_block_sum9(S, acc);
@@ -399,23 +460,26 @@ __device__ __forceinline__ void sf_column_sums(const SfScratch& Z, int j, int n,
                                                unsigned long long& npair) {
     const int lane = threadIdx.x & 31;
     const float4 rk = Z.rk[j];
-    for (int k = lane; k < n; k += 32) {
-        float4 p;
-        float l;
-        row(k, p, l);
-        ++npair;
+    auto pair = [&](const float4& p, float l) {
         float v = sf_pair_v(sf_rowg(p, Z.cE + 3 * j), rk) - l;
-        if (v < kSfSkip) continue;
+        if (v < kSfSkip) return;
         float Q = ex2(v);
         if (massonly) {
             s0 += Q;
-            continue;
+            return;
         }
         float d0 = p.x - c[0], d1 = p.y - c[1], d2 = p.z - c[2];
         float is = rsqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
         s0 += Q * d0 * is;
         s1 += Q * d1 * is;
         s2 += Q * d2 * is;
+    };
+    for (int k = lane; k < n; k += 32) {
+        float4 p;
+        float l;
+        row(k, p, l);
+        ++npair;
+        pair(p, l);
     }
 }
 
@@ -548,7 +612,7 @@ __global__ void __launch_bounds__(kSfThreads, kSfCtasPerSm) single_fit_kernel(Sf
             float eps = sf_eps(a, k);
             float negK = -a.G.D * a.G.D * log2e / eps, dust = -a.c_out * log2e / eps;
             sf_refresh(a, S, Z, negK);  // E-step pose
-            sf_near(a, S, Z, negK, dust, npair);
+            sf_near(a, S, Z, negK, dust, npair, a.n_newton > 0);
             if (threadIdx.x == 0) S.stop = 0;
             __syncthreads();
             for (int q = 0; q < a.n_newton; ++q) {
@@ -566,7 +630,7 @@ __global__ void __launch_bounds__(kSfThreads, kSfCtasPerSm) single_fit_kernel(Sf
         overflow |= S.overflow != 0;
         float negK = -a.G.D * a.G.D * log2e / a.eps_final, dust = -a.c_out * log2e / a.eps_final;
         sf_refresh(a, S, Z, negK);
-        sf_near(a, S, Z, negK, dust, npair);
+        sf_near(a, S, Z, negK, dust, npair, false);
         sf_columns(a, S, Z, negK, dust, true, npair);
         atomicAdd((unsigned long long*)(a.ctrl + CTRL_SF_PAIRS), npair);
         if (threadIdx.x == 0) {
