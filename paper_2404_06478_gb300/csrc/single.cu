@@ -101,6 +101,7 @@ struct SfShared {
     float red[kSfThreads * 9];
     int start;
     int last;
+    int seg_total;  // visible rays of the current cut segment
     const float2* cs;  // {cos, sin} of each rotation angle (dynamic shared memory)
 };
 
@@ -116,48 +117,72 @@ __device__ __forceinline__ void sf_angles(const SfArgs& a, SfShared& S, float2* 
 }
 
 // Lists the spots visible at pose (R, x) sorted by (t, m); t_off per angle.
+// The rays (t, m) of the whole scan in (t, m) order are taken kSfCutSeg at a
+// time: every warp marks the visibility of 32 consecutive rays in one ballot
+// word, warp 0 scans the words' counts, and each visible ray is written at its
+// rank (its detector recomputed): four barriers per segment.
+constexpr int kSfCutSeg = 4096;
 __device__ void sf_cut(const SfArgs& a, SfShared& S, const SfScratch& Z) {
+    __shared__ unsigned vis_w[kSfCutSeg / 32];
+    __shared__ int w_off[kSfCutSeg / 32];
     if (threadIdx.x == 0) {
         S.n_spots = 0;
         S.overflow = 0;
     }
     __syncthreads();
-    long long nr = (long long)a.T * a.M;
-    __shared__ int warp_cnt[kSfThreads / 32];
-    for (long long base = 0; base < nr; base += kSfThreads) {
-        long long id = base + threadIdx.x;
-        bool vis = false;
-        int t = 0, m = 0, det = -1;
-        if (id < nr) {
-            t = (int)(id / a.M);
-            m = (int)(id % a.M);
-            float r[3], c[3], lam0;
-            int nh;
-            sf_ray(a, S.cs, S.R, S.x, t, m, r, c, &lam0, &nh);
-            det = sf_visible(a.G, r, c, lam0, nh);
-            vis = det >= 0;
+    const int nr = a.T * a.M;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto detector_of = [&](int id, int& t, int& m) {
+        t = id / a.M;
+        m = id - t * a.M;
+        float r[3], c[3], lam0;
+        int nh;
+        sf_ray(a, S.cs, S.R, S.x, t, m, r, c, &lam0, &nh);
+        return sf_visible(a.G, r, c, lam0, nh);
+    };
+    for (int base = 0; base < nr; base += kSfCutSeg) {
+        const int nseg = min(kSfCutSeg, nr - base), nw = (nseg + 31) / 32;
+        for (int w0 = 32 * warp; w0 < nseg; w0 += kSfThreads) {  // warp-uniform bounds
+            bool vis = false;
+            if (w0 + lane < nseg) {
+                int t, m;
+                vis = detector_of(base + w0 + lane, t, m) >= 0;
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, vis);
+            if (lane == 0) vis_w[w0 / 32] = ball;
         }
-        unsigned ball = __ballot_sync(0xffffffffu, vis);
-        int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        if (lane == 0) warp_cnt[w] = __popc(ball);
         __syncthreads();
-        int before = 0, total = 0;
-        for (int k = 0; k < kSfThreads / 32; ++k) {
-            if (k < w) before += warp_cnt[k];
-            total += warp_cnt[k];
+        if (warp == 0) {  // exclusive prefix of the words' counts, in word order
+            int run = 0;
+            for (int w0 = 0; w0 < nw; w0 += 32) {
+                const int c = w0 + lane < nw ? __popc(vis_w[w0 + lane]) : 0;
+                int incl = c;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (w0 + lane < nw) w_off[w0 + lane] = run + incl - c;
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) S.seg_total = run;
         }
-        int pos = S.n_spots + before + __popc(ball & ((1u << lane) - 1u));
-        if (vis) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < nseg; k += kSfThreads) {
+            const unsigned word = vis_w[k >> 5], bit = 1u << (k & 31);
+            if (!(word & bit)) continue;
+            const int pos = S.n_spots + w_off[k >> 5] + __popc(word & (bit - 1u));
             if (pos < a.cap) {
+                int t, m;
+                const int det = detector_of(base + k, t, m);
                 Z.tm[pos] = (t << 16) | m;
-                float dr = a.G.Dd[det] / a.G.D;
+                const float dr = det >= 0 ? a.G.Dd[det] / a.G.D : 1.0f;  // same decision as above
                 Z.kd[pos] = dr * dr;
             } else {
                 S.overflow = 1;
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) S.n_spots += total;
+        if (threadIdx.x == 0) S.n_spots += S.seg_total;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
