@@ -245,12 +245,15 @@ __device__ __forceinline__ float sf_row_lse(const SfArgs& a, const SfShared& S, 
     if (j1 == j0) return dust;
     const SfRowG g = sf_rowg(p, Z.cE + 3 * j0);
     if (dust >= -100.0f) {
+        // s >= 1 (the outlier term), so a term below 2^-25 (under half an ulp
+        // of s) leaves s unchanged: such terms are not evaluated
         float s = 1.0f;
 #pragma unroll 4
         for (int j = j0; j < j1; ++j) {
             float v = sf_pair_v(g, Z.rk[j]);
             vmax = fmaxf(vmax, v);
-            s += ex2(v - dust);
+            const float dv = v - dust;
+            if (dv >= -25.0f) s += ex2(dv);
         }
         return dust + lg2(s);
     }
@@ -280,12 +283,16 @@ __device__ __forceinline__ float sf_row_lse_u(const SfArgs& a, const SfShared& S
     const SfRowG g = sf_rowg(p, Z.cE + 3 * j0);
     float m = dust, s = 1.0f, u0 = 0.0f, u1 = 0.0f, u2 = 0.0f;
     if (dust >= -100.0f) {  // relative to the outlier term, no running maximum
+        // terms below 2^-25 leave s (>= 1) unchanged and are skipped; their
+        // share of u is below 2^-25 of the row's plan mass
 #pragma unroll 4
         for (int j = j0; j < j1; ++j) {
             const float4 rk = Z.rk[j];
             const float v = sf_pair_v(g, rk);
             vmax = fmaxf(vmax, v);
-            const float w = ex2(v - dust), wk = w * rk.w;
+            const float dv = v - dust;
+            if (dv < -25.0f) continue;
+            const float w = ex2(dv), wk = w * rk.w;
             s += w;
             u0 = fmaf(-wk, rk.x, u0);  // r_j = -rk.xyz
             u1 = fmaf(-wk, rk.y, u1);
@@ -338,15 +345,19 @@ __device__ void sf_near(const SfArgs& a, SfShared& S, const SfScratch& Z, float 
         const int base = S.n_near;
         int cnt = 0;
         if (S.t_off[t + 1] > S.t_off[t]) {
-            for (int i0 = a.I_off[t]; i0 < a.I_off[t + 1]; i0 += kSfThreads) {
+            const int i_end = a.I_off[t + 1];
+            // the next chunk's row is loaded while this one is summed
+            float4 p_next = a.I_off[t] + (int)threadIdx.x < i_end ? a.p[a.I_off[t] + threadIdx.x]
+                                                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int i0 = a.I_off[t]; i0 < i_end; i0 += kSfThreads) {
                 const int i = i0 + threadIdx.x;
                 bool near = false;
                 float l = 0.0f;
                 float u[3] = {0.0f, 0.0f, 0.0f};
-                float4 p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (i < a.I_off[t + 1]) {
+                const float4 p = p_next;
+                if (i + kSfThreads < i_end) p_next = a.p[i + kSfThreads];
+                if (i < i_end) {
                     float vmax;
-                    p = a.p[i];
                     l = with_u ? sf_row_lse_u(a, S, Z, t, p, dust, inv_negK, npair, vmax, u)
                                : sf_row_lse(a, S, Z, t, p, dust, npair, vmax);
                     near = vmax - l >= kSfSkip;
