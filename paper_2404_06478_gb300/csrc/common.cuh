@@ -53,6 +53,7 @@ inline size_t sf_near_cap(int n_obs) {
     size_t c = n_obs < kSfNearMax ? (size_t)(n_obs > 0 ? n_obs : 1) : (size_t)kSfNearMax;
     return (c + 3) / 4 * 4;  // keeps every CTA's slice 16-byte aligned
 }
+constexpr int kConeGran = 32;  // pairs per cone granule of the pair passes' exact skipping (kGran)
 constexpr size_t kCtrlBytes = 4096;  // status + counters + small scalars
 
 // ---------------------------------------------------------------------------
@@ -120,8 +121,8 @@ inline Layout make_layout(const LaueProblemDims& d, int sm_count) {
     size_t nsp = (size_t)d.n_obs + d.n_model + 2;
     L.perm = take(sizeof(int) * 2 * nsp);
     L.sortbuf = take(sizeof(int) * 4 * nsp);
-    L.max_obs_gran = (int)((ip + 31) / 32) + T + 1;  // cone granules of 32 pairs
-    L.max_mod_gran = (int)((jp + 31) / 32) + T + 1;
+    L.max_obs_gran = (int)((ip + kConeGran - 1) / kConeGran) + T + 1;  // cone granules of kConeGran pairs
+    L.max_mod_gran = (int)((jp + kConeGran - 1) / kConeGran) + T + 1;
     L.cone = take((sizeof(float4) + sizeof(float)) * (size_t)(L.max_obs_gran + L.max_mod_gran) + 64);
     L.fwd_blocks = take(sizeof(int) * (size_t)(2 * L.max_fwd_blocks + 2));
     L.jsum = take(sizeof(float) * 12 * (size_t)(d.n_model + 1));

@@ -11,7 +11,7 @@ namespace laue {
 
 constexpr int kTPB = 256;     // widest CTA of the pair passes (one row/column pair per thread)
 constexpr int kChunk = 128;   // staged pairs per chunk (256 spots)
-constexpr int kGran = 32;     // pairs per cone granule of the exact skipping
+constexpr int kGran = kConeGran;  // pairs per cone granule of the exact skipping
 constexpr int kParts = kChunk / kGran;  // granules per staged chunk
 constexpr int kGroup = 4;     // staged pairs per max-then-sum group
 constexpr float kPadFar = 1.0e6f;
@@ -209,7 +209,7 @@ __device__ __forceinline__ bool stream_list_prep(Stage& S, uint32_t (&parity)[2]
     }
     bool ok_all = true;
     for (int c = 0; c < n_list; ++c) {
-        int st = c & 1, ch = S.list[c] & 0xffffff, mask = S.list[c] >> 24;
+        int st = c & 1, ch = S.list[c] & 0xffffff, mask = (int)((unsigned)S.list[c] >> 24);
         int n = min(kChunk, n_total - ch * kChunk);
         bool ok = mbar_wait_bounded(&S.bar[st], parity[st]);
         parity[st] ^= 1u;
@@ -306,7 +306,7 @@ __device__ __forceinline__ int build_chunk_list(Stage& S, int nch, Need need) {
             if (k < w) before += S.wcnt[k];
             total += S.wcnt[k];
         }
-        if (nd) S.list[base + before + __popc(b & ((1u << lane) - 1u))] = c | (mask << 24);
+        if (nd) S.list[base + before + __popc(b & ((1u << lane) - 1u))] = (int)((unsigned)c | ((unsigned)mask << 24));
         base += total;
         __syncthreads();
     }

@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(TPB, MINB) sk_row_kernel(SkArgs a) {
         if (threadIdx.x == 0) {
             long long np = 0;
             if (use_list)
-                for (int c = 0; c < n_list; ++c) np += list_pairs(S.list[c] & 0xffffff, S.list[c] >> 24, nj);
+                for (int c = 0; c < n_list; ++c) np += list_pairs(S.list[c] & 0xffffff, (int)((unsigned)S.list[c] >> 24), nj);
             else
                 np = nj;
             atomicAdd((unsigned long long*)(a.ctrl + CTRL_SK_PAIRS), (unsigned long long)(4LL * td.z * np));
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(TPB, MINB) sk_col_kernel(SkArgs a) {
         if (threadIdx.x == 0) {
             long long np = 0;
             if (use_list)
-                for (int c = 0; c < n_list; ++c) np += list_pairs(S.list[c] & 0xffffff, S.list[c] >> 24, ni);
+                for (int c = 0; c < n_list; ++c) np += list_pairs(S.list[c] & 0xffffff, (int)((unsigned)S.list[c] >> 24), ni);
             else
                 np = ni;
             atomicAdd((unsigned long long*)(a.ctrl + CTRL_SK_PAIRS), (unsigned long long)(4LL * td.z * np));
