@@ -366,13 +366,15 @@ int laue_autotune(laue_handle* h, const LaueGeometry* geom, const LaueObsSpots* 
                   float* ms_host, void* stream);
 
 /* Device counters (no counterpart in the paper), accumulated since the last
- * call on the handle's workspace, then cleared; the first n (<= 3) go to
+ * call on the handle's workspace, then cleared; the first n (<= 5) go to
  * counts_host: [0] row and [1] column log-sum-exps of laue_cost_sinkhorn's pair
  * passes recomputed on the exact (running-maximum) path because their fast
  * sum, shifted by the angle block's largest potential, fell below 1e-30
  * (modulo 2^32); [2] pair evaluations (one cost and one exponential each) of
  * laue_single_fit; [3] pair evaluations of the row and column passes of
- * laue_cost_sinkhorn (after the exact skipping).  Synchronises `stream`. */
+ * laue_cost_sinkhorn (after the exact skipping); [4] pairs the M-step pair
+ * passes of laue_mstep, laue_mstep_adjoint and laue_objective_grad visit
+ * (after the exact skipping).  Synchronises `stream`. */
 int laue_read_counters(laue_handle* h, void* stream, long long* counts_host, int n);
 
 /* Exact underflow skipping in the Sinkhorn pair passes (no counterpart in the
@@ -381,7 +383,9 @@ int laue_read_counters(laue_handle* h, void* stream, long long* counts_host, int
  * carries a cone bounding its directions, and a pass skips a (tile, granule)
  * combination when the cones prove that every shifted exponent is below
  * -130, i.e. every plan entry flushes to exactly 0; the potentials are
- * bit-identical either way.  enable = 0 turns
+ * bit-identical either way.  The M-step pair passes skip, by the same cone
+ * bounds, the granules whose every plan entry is below 2^-40 (entries their
+ * sums leave out), so their results are bit-identical too.  enable = 0 turns
  * the skipping off (the ordering stays).  Read the evaluated pairs with
  * laue_read_counters. */
 int laue_set_pair_skipping(laue_handle* h, int enable);

@@ -276,9 +276,9 @@ class Handle:
 
     def counters(self, stream=None):
         """laue_read_counters: dict of the device counters since the last read."""
-        v = (ctypes.c_longlong * 4)()
-        self.check(self.L.laue_read_counters(self.h, _stream(stream), v, 4), "read_counters")
-        return dict(exact_rows=v[0], exact_cols=v[1], fit_pairs=v[2], pass_pairs=v[3])
+        v = (ctypes.c_longlong * 5)()
+        self.check(self.L.laue_read_counters(self.h, _stream(stream), v, 5), "read_counters")
+        return dict(exact_rows=v[0], exact_cols=v[1], fit_pairs=v[2], pass_pairs=v[3], mstep_pairs=v[4])
 
     def set_pair_skipping(self, enable: bool):
         self.check(self.L.laue_set_pair_skipping(self.h, 1 if enable else 0), "set_pair_skipping")

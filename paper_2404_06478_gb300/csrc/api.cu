@@ -660,21 +660,28 @@ extern "C" int laue_cost_sinkhorn_sparse(laue_handle* h, const LaueGeometry* geo
 // ------------------------------------------------------------- autotuner
 
 extern "C" int laue_read_counters(laue_handle* h, void* stream, long long* counts_host, int n) {
-    if (!h || !counts_host || n < 0 || n > 4) return LAUE_ERR_INVALID_ARG;
+    if (!h || !counts_host || n < 0 || n > 5) return LAUE_ERR_INVALID_ARG;
     if (!h->ws) return laue_fail(h, LAUE_ERR_WORKSPACE, "no workspace set");
     cudaStream_t s = (cudaStream_t)stream;
     unsigned v[6] = {0u, 0u, 0u, 0u, 0u, 0u};  // exact rows, exact columns, fit pairs, pass pairs (64 bits)
+    unsigned w[2] = {0u, 0u};                  // M-step pairs (64 bits)
     int* ctrl = (int*)h->ws;
     int rc;
     if ((rc = laue_cuda_check(h, cudaMemcpyAsync(v, ctrl + CTRL_EXACT_ROWS, sizeof(v), cudaMemcpyDeviceToHost, s),
                               "reading counts")))
         return rc;
+    if ((rc = laue_cuda_check(h, cudaMemcpyAsync(w, ctrl + CTRL_MS_PAIRS, sizeof(w), cudaMemcpyDeviceToHost, s),
+                              "reading counts")))
+        return rc;
     if ((rc = laue_cuda_check(h, cudaMemsetAsync(ctrl + CTRL_EXACT_ROWS, 0, sizeof(v), s), "clearing counts")))
         return rc;
+    if ((rc = laue_cuda_check(h, cudaMemsetAsync(ctrl + CTRL_MS_PAIRS, 0, sizeof(w), s), "clearing counts")))
+        return rc;
     if ((rc = laue_cuda_check(h, cudaStreamSynchronize(s), "synchronise"))) return rc;
-    long long all[4] = {(long long)v[0], (long long)v[1],
+    long long all[5] = {(long long)v[0], (long long)v[1],
                         (long long)((unsigned long long)v[2] | ((unsigned long long)v[3] << 32)),
-                        (long long)((unsigned long long)v[4] | ((unsigned long long)v[5] << 32))};
+                        (long long)((unsigned long long)v[4] | ((unsigned long long)v[5] << 32)),
+                        (long long)((unsigned long long)w[0] | ((unsigned long long)w[1] << 32))};
     for (int k = 0; k < n; ++k) counts_host[k] = all[k];
     return LAUE_OK;
 }
@@ -790,8 +797,9 @@ static int mstep_entry(laue_handle* h, const LaueGeometry* geom, const LaueLatti
     SkLaunch lc;
     LaueOTParams op{0.4, prm->eps, 0.0f, 0, 0, 1, 0};
     laue_fill_sk(h, geom, obs, model, &op, L, &m.sk, &lc);
-    m.sk.tile_cols = 256;  // the M-step pair kernel runs 256 threads per column tile
-    lc.col_grid = std::max(1, std::min(h->sm_count * 3, L.max_col_tiles));
+    // the M-step pair kernel runs one thread per column pair of the column
+    // pass's tiles (narrow tiles skip more), about 768 threads per SM
+    lc.col_grid = std::max(1, std::min(h->sm_count * (768 / m.sk.tile_cols), L.max_col_tiles));
     m.sk.f = const_cast<float*>(f);
     m.sk.g = const_cast<float*>(g);
     m.sk.dust_out = nullptr;
@@ -867,8 +875,9 @@ extern "C" int laue_objective_grad(laue_handle* h, const LaueGeometry* geom, con
     SkLaunch lc;
     LaueOTParams op{0.4, eps, 0.0f, 0, 0, 1, 0};
     laue_fill_sk(h, geom, obs, model, &op, L, &m.sk, &lc);
-    m.sk.tile_cols = 256;  // the M-step pair kernel runs 256 threads per column tile
-    lc.col_grid = std::max(1, std::min(h->sm_count * 3, L.max_col_tiles));
+    // the M-step pair kernel runs one thread per column pair of the column
+    // pass's tiles (narrow tiles skip more), about 768 threads per SM
+    lc.col_grid = std::max(1, std::min(h->sm_count * (768 / m.sk.tile_cols), L.max_col_tiles));
     m.sk.f = const_cast<float*>(f);
     m.sk.g = const_cast<float*>(g);
     m.sk.dust_out = nullptr;

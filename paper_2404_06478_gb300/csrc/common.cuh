@@ -34,6 +34,7 @@ enum CtrlSlot {
     CTRL_SF_PAIRS = 18,   // 64-bit count (slots 18-19) of single-fit pair evaluations
     CTRL_SK_PAIRS = 20,   // 64-bit count (slots 20-21) of pair evaluations of the Sinkhorn passes
     CTRL_SP_DONE = 22,    // finished-CTA ticket of the sparse passes
+    CTRL_MS_PAIRS = 24,   // 64-bit count (slots 24-25) of staged pairs the M-step pair kernel visits
     CTRL_SLOTS = 64
 };
 

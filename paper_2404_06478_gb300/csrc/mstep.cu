@@ -174,11 +174,11 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
             }
         }
         const f2 Gpa = dup(Ga), Gpb = dup(Gb);
-        bool ok = stream_tile(S, parity, src, i0, ni, [&](int st, int n, int) {
-            if (!valid) return;
+        // staged observed pairs [h, h + m) of stage st
+        auto run = [&](int st, int h, int m) {
             const float4* sX = S.s[0][st];
             const float4* sY = S.s[1][st];
-            for (int k = 0; k < n; ++k) {
+            for (int k = h; k < h + m; ++k) {
                 ulonglong2 X = *(const ulonglong2*)&sX[k];
                 ulonglong2 Y = *(const ulonglong2*)&sY[k];
                 // E-step plan exponents of the 2 x 2 pairs: F_i + G_j - K e2
@@ -192,7 +192,46 @@ __global__ void __launch_bounds__(kTPB) ms_pair_kernel(MsArgs m) {
                 ms_pair(B, MODE, x4.x, x4.z, y4.x, lo(vb));
                 ms_pair(B, MODE, x4.y, x4.w, y4.y, hi(vb));
             }
-        });
+        };
+        auto body = [&](int st, int n, int, int mask = (1 << kParts) - 1) {
+            if (!valid) return;
+            for_each_run(mask, n, [&](int h, int m) { run(st, h, m); });
+        };
+        // the observed granules that can hold a plan entry >= 2^kQSkip for this
+        // tile: log2 Q_ij = F_i + G_j - |K_j| e2 <= max_t F + max_tile G - the
+        // cones' cost bound, so a granule whose bound exceeds
+        // max F + max G - kQSkip holds only pairs the sums skip (exact)
+        const float gtile = block_max(S, fmaxf(Ga, Gb));
+        const int nch = (ni + kChunk - 1) / kChunk;
+        const bool use_list = a.skip && nch > 0 && nch <= kMaxList;
+        int n_list = nch;
+        if (use_list) {
+            const DustPtrs D = dust_ptrs(a.dust, a.T);
+            const Cone M = tile_cone(a.mod_cone, a.mod_ext, a.mod_gbase[t], a.J2_off[t], td.y, td.z, false);
+            const float K = a.skipK;  // the smallest cost factor of any spot
+            const float lim = D.Fmax[t] + gtile - kQSkip + 1.0f;
+            const int og = a.obs_gbase[t], ng = (ni + kGran - 1) / kGran;
+            n_list = build_chunk_list(S, nch, [&](int c) {
+                int msk = 0;
+                for (int hh = 0; hh < kParts; ++hh)
+                    if (kParts * c + hh < ng &&
+                        min_scaled_cost(load_cone(a.obs_cone, a.obs_ext, og + kParts * c + hh), M, K) <= lim)
+                        msk |= 1 << hh;
+                return msk;
+            });
+        }
+        auto no_prep = [](int, int) {};
+        bool ok = use_list ? stream_list_prep(S, parity, src, i0, ni, n_list, no_prep, body)
+                           : stream_tile(S, parity, src, i0, ni, [&](int st, int n, int) { body(st, n, 0); });
+        if (threadIdx.x == 0) {
+            long long np = 0;
+            if (use_list)
+                for (int c = 0; c < n_list; ++c)
+                    np += list_pairs(S.list[c] & 0xffffff, (int)((unsigned)S.list[c] >> 24), ni);
+            else
+                np = ni;
+            atomicAdd((unsigned long long*)(a.ctrl + CTRL_MS_PAIRS), (unsigned long long)(4LL * td.z * np));
+        }
         if (!ok) {
             if (threadIdx.x == 0) set_status(a.ctrl, LAUE_ERR_TIMEOUT);
             break;
@@ -526,7 +565,7 @@ cudaError_t grad_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if ((e = seg_table(m, s)) != cudaSuccess) return e;
     if (m.N > 0) ms_init_kernel<<<(m.N + 255) / 256, 256, 0, s>>>(m);
-    ms_pair_kernel<2><<<l.col_grid, kTPB, 0, s>>>(m);
+    ms_pair_kernel<2><<<l.col_grid, m.sk.tile_cols, 0, s>>>(m);
     if (m.N > 0) ms_grad_grain_kernel<<<(m.N * 32 + 127) / 128, 128, 0, s>>>(m);
     return cudaGetLastError();
 }
@@ -617,7 +656,7 @@ cudaError_t mstep_adjoint_run(const MsArgs& m, const SkLaunch& l, int n_steps, c
     if ((e = seg_table(m, s)) != cudaSuccess) return e;
     if (m.N > 0) ms_init_kernel<<<(m.N + 255) / 256, 256, 0, s>>>(m);
     for (int k = 0; k < n_steps; ++k) {
-        ms_pair_kernel<3><<<l.col_grid, kTPB, 0, s>>>(m);
+        ms_pair_kernel<3><<<l.col_grid, m.sk.tile_cols, 0, s>>>(m);
         if (m.N > 0) ms_adj_grain_kernel<<<(m.N * 32 + 127) / 128, 128, 0, s>>>(m);
     }
     if (m.N > 0) ms_norms_kernel<<<(m.N + 255) / 256, 256, 0, s>>>(m);
@@ -635,11 +674,11 @@ cudaError_t mstep_run(const MsArgs& m, const SkLaunch& l, cudaStream_t s) {
     if ((e = seg_table(m, s)) != cudaSuccess) return e;
     if (m.N > 0) ms_init_kernel<<<(m.N + 255) / 256, 256, 0, s>>>(m);
     for (int k = 0; k < m.n_newton; ++k) {
-        ms_pair_kernel<0><<<l.col_grid, kTPB, 0, s>>>(m);
+        ms_pair_kernel<0><<<l.col_grid, m.sk.tile_cols, 0, s>>>(m);
         if (m.N > 0) ms_newton_grain_kernel<<<(m.N * 32 + 127) / 128, 128, 0, s>>>(m);
     }
     if (m.n_mm > 0 && m.N > 0) {
-        ms_pair_kernel<1><<<l.col_grid, kTPB, 0, s>>>(m);
+        ms_pair_kernel<1><<<l.col_grid, m.sk.tile_cols, 0, s>>>(m);
         size_t shm = sizeof(float) * (6 * (size_t)m.M + 9 * kMmThreads);
         if (shm > 48 * 1024) {
             e = cudaFuncSetAttribute(ms_mm_grain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);

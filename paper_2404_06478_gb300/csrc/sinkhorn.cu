@@ -1027,21 +1027,37 @@ __global__ void sk_clear_err_kernel(SkArgs a) {
     D.err[0] = D.err[1] = D.err[2] = D.err[3] = 0.0f;
 }
 
-// Per-angle maximum of the starting G (padding excluded), for the first row pass.
+// Per-angle maxima of the starting G (for the first row pass) and F (for the
+// M-step's skipping bound), padding excluded.
 __global__ void __launch_bounds__(256) sk_init_gmax_kernel(SkArgs a) {
-    __shared__ float red[8];
+    __shared__ float red[8], redf[8];
     int t = blockIdx.x;
-    float m = kNegHuge;
+    float m = kNegHuge, f = kNegHuge;
     for (int q = a.J2_off[t] + threadIdx.x; q < a.J2_off[t + 1]; q += blockDim.x) {
         float4 y = a.modY[q];
         m = fmaxf(m, fmaxf(y.z, y.w));
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    for (int q = a.I2_off[t] + threadIdx.x; q < a.I2_off[t + 1]; q += blockDim.x) {
+        float4 y = a.obsY[q];
+        f = fmaxf(f, fmaxf(y.z, y.w));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        f = fmaxf(f, __shfl_xor_sync(0xffffffffu, f, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = m;
+        redf[threadIdx.x >> 5] = f;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 1; k < 8; ++k) m = fmaxf(m, red[k]);
-        dust_ptrs(a.dust, a.T).Gmax[t] = m;
+        for (int k = 1; k < 8; ++k) {
+            m = fmaxf(m, red[k]);
+            f = fmaxf(f, redf[k]);
+        }
+        DustPtrs D = dust_ptrs(a.dust, a.T);
+        D.Gmax[t] = m;
+        D.Fmax[t] = f;  // the M-step's skipping bound; a row pass rewrites it
     }
 }
 
