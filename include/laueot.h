@@ -608,8 +608,8 @@ int laue_em(laue_handle* h, const LaueGeometry* geom, const LaueLattice* lat, co
  * proposal: a set encoder (per-spot MLP of three 256-wide ReLU layers, masked
  * mean and max pooling, a two-layer head emitting 8 hypotheses of 6-D
  * rotation + 3-D position) that reads a seed-conditioned set of observed
- * spots and proposes poses for those fits.  Its per-spot layers run in BF16
- * on the tensor cores with FP32 accumulation.  The paper has no counterpart
+ * spots and proposes poses for those fits.  Its per-spot layers and head run
+ * in BF16 on the tensor cores with FP32 accumulation.  The paper has no counterpart
  * for any of these calls. */
 
 /* BF16 GEMM on the tcgen05 tensor cores: D[m][n] = sum_k A[m][k] B[n][k].
@@ -719,15 +719,18 @@ int laue_lp_sets(laue_handle* h, const LaueGeometry* geom, const float* p, const
 
 /* Network forward over the sets in the batch buffer: per-spot layers as
  * BF16 tcgen05 GEMMs with FP32 accumulation and fused bias + ReLU, masked
- * mean and max pooling, FP32 head; outputs O in batch region 7.
+ * mean and max pooling, the head as two more such GEMMs (the pooled
+ * features and hidden units rounded to BF16); outputs O (FP32) in batch
+ * region 7.
  * Asynchronous. */
 int laue_lp_forward(laue_handle* h, const void* net, void* batch, int n_sets, void* stream);
 
 /* One training step on the sets and targets in the batch buffer: forward;
  * per set the loss min_h L_h + 0.05 mean_h L_h with L_h = min over the 24
  * cube rotations S of ||GS(o_h) - R_loc S||_F^2 + 0.1 ||xhat_h - x||^2,
- * averaged over the valid sets; backward (head in FP32, per-spot layers on
- * the tensor cores, errors rounded to BF16); Adam (beta 0.9, 0.999,
+ * averaged over the valid sets; backward (every GEMM on the tensor cores,
+ * the errors they read rounded to BF16; weight gradients read the row-major
+ * activations MN-major); Adam (beta 0.9, 0.999,
  * eps 1e-8, learning rate lr; lr = 0 leaves the parameters unchanged).
  * Losses, best errors and hypotheses land in batch regions 8-10, gradients
  * in the network buffer.  Asynchronous. */

@@ -13,9 +13,10 @@
 //                    Gamma_t^T u), the KSET - 1 nearest axes to the seed's in its
 //                    rotation window by a three-round radix select, features
 //                    in the seed frame (BF16, row-major);
-//   network          per-spot layers on the tcgen05 GEMM (gemm_tc.cu),
-//                    masked mean/max pooling, FP32 head, symmetric
-//                    multi-hypothesis loss, backward, Adam.
+//   network          per-spot layers and the head on the tcgen05 GEMM
+//                    (gemm_tc.cu, BF16 operands, FP32 accumulation), masked
+//                    mean/max pooling, symmetric multi-hypothesis loss,
+//                    backward, Adam.
 // Every reduction runs in a fixed order: the same inputs give the same bits.
 #include <cuda_bf16.h>
 
