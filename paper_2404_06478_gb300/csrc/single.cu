@@ -326,6 +326,60 @@ __device__ __forceinline__ float sf_row_lse_u(const SfArgs& a, const SfShared& S
     return m + lg2(s);
 }
 
+// Two rows a and b of angle t at once (one pass over the listed spots, each
+// spot's record loaded once for both), each with the arithmetic of
+// sf_row_lse_u in the same order, so both results are bit-identical to it.
+// Rows whose outlier exponent is below -100 take sf_row_lse_u one by one.
+__device__ __forceinline__ void sf_row2_lse_u(const SfArgs& a, const SfShared& S, const SfScratch& Z, int t,
+                                              const float4& pa, const float4& pb, bool hb, float dust,
+                                              float inv_negK, unsigned long long& npair, float& la, float& lb,
+                                              float& vma, float& vmb, float* ua, float* ub) {
+    if (dust < -100.0f) {
+        la = sf_row_lse_u(a, S, Z, t, pa, dust, inv_negK, npair, vma, ua);
+        if (hb) lb = sf_row_lse_u(a, S, Z, t, pb, dust, inv_negK, npair, vmb, ub);
+        return;
+    }
+    const int j0 = S.t_off[t], j1 = S.t_off[t + 1];
+    npair += (unsigned)(j1 - j0) * (hb ? 2u : 1u);
+    vma = vmb = kNegHuge;
+    ua[0] = ua[1] = ua[2] = ub[0] = ub[1] = ub[2] = 0.0f;
+    la = lb = dust;
+    if (j1 == j0) return;
+    const SfRowG ga = sf_rowg(pa, Z.cE + 3 * j0), gb = sf_rowg(pb, Z.cE + 3 * j0);
+    float sa = 1.0f, sb = 1.0f, a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+#pragma unroll 2
+    for (int j = j0; j < j1; ++j) {
+        const float4 rk = Z.rk[j];
+        const float va = sf_pair_v(ga, rk), vb = sf_pair_v(gb, rk);
+        vma = fmaxf(vma, va);
+        vmb = fmaxf(vmb, vb);
+        const float dva = va - dust, dvb = vb - dust;
+        if (dva >= -25.0f) {
+            const float w = ex2(dva), wk = w * rk.w;
+            sa += w;
+            a0 = fmaf(-wk, rk.x, a0);
+            a1 = fmaf(-wk, rk.y, a1);
+            a2 = fmaf(-wk, rk.z, a2);
+        }
+        if (dvb >= -25.0f) {
+            const float w = ex2(dvb), wk = w * rk.w;
+            sb += w;
+            b0 = fmaf(-wk, rk.x, b0);
+            b1 = fmaf(-wk, rk.y, b1);
+            b2 = fmaf(-wk, rk.z, b2);
+        }
+    }
+    const float sca = inv_negK / sa, scb = inv_negK / sb;
+    ua[0] = a0 * sca;
+    ua[1] = a1 * sca;
+    ua[2] = a2 * sca;
+    ub[0] = b0 * scb;
+    ub[1] = b1 * scb;
+    ub[2] = b2 * scb;
+    la = dust + lg2(sa);
+    lb = dust + lg2(sb);
+}
+
 // Row normalisers of this EM step's E-step and the rows that carry plan mass.
 // A row is near when some pair keeps Q_ij >= 2^kSfSkip (v_ij - l_i >=
 // kSfSkip); every other row has all its plan entries below the cut-off that
@@ -337,7 +391,7 @@ __device__ __forceinline__ float sf_row_lse_u(const SfArgs& a, const SfShared& S
 __device__ void sf_near(const SfArgs& a, SfShared& S, const SfScratch& Z, float negK, float dust,
                         unsigned long long& npair, bool with_u) {
     const float inv_negK = 1.0f / negK;
-    __shared__ int wcnt[kSfThreads / 32];
+    __shared__ int wcnt[kSfThreads / 32], wcnt2[kSfThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) S.n_near = 0;
     __syncthreads();
@@ -345,37 +399,60 @@ __device__ void sf_near(const SfArgs& a, SfShared& S, const SfScratch& Z, float 
         const int base = S.n_near;
         int cnt = 0;
         if (S.t_off[t + 1] > S.t_off[t]) {
-            const int i_end = a.I_off[t + 1];
-            // the next chunk's row is loaded while this one is summed
-            float4 p_next = a.I_off[t] + (int)threadIdx.x < i_end ? a.p[a.I_off[t] + threadIdx.x]
-                                                                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            for (int i0 = a.I_off[t]; i0 < i_end; i0 += kSfThreads) {
-                const int i = i0 + threadIdx.x;
-                bool near = false;
-                float l = 0.0f;
-                float u[3] = {0.0f, 0.0f, 0.0f};
-                const float4 p = p_next;
-                if (i + kSfThreads < i_end) p_next = a.p[i + kSfThreads];
-                if (i < i_end) {
-                    float vmax;
-                    l = with_u ? sf_row_lse_u(a, S, Z, t, p, dust, inv_negK, npair, vmax, u)
-                               : sf_row_lse(a, S, Z, t, p, dust, npair, vmax);
-                    near = vmax - l >= kSfSkip;
+            const int i_beg = a.I_off[t], i_end = a.I_off[t + 1];
+            const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            // chunks of 2 kSfThreads rows, two rows per thread (i and i + kSfThreads,
+            // listed in row order); the next chunk's rows are loaded while this
+            // chunk's are summed
+            const int ia0 = i_beg + threadIdx.x, ib0 = ia0 + kSfThreads;
+            float4 pa_next = ia0 < i_end ? a.p[ia0] : zero4, pb_next = ib0 < i_end ? a.p[ib0] : zero4;
+            for (int i0 = i_beg; i0 < i_end; i0 += 2 * kSfThreads) {
+                const int ia = i0 + threadIdx.x, ib = ia + kSfThreads;
+                const bool ha = ia < i_end, hb = ib < i_end;
+                const float4 pa = pa_next, pb = pb_next;
+                if (ia + 2 * kSfThreads < i_end) pa_next = a.p[ia + 2 * kSfThreads];
+                if (ib + 2 * kSfThreads < i_end) pb_next = a.p[ib + 2 * kSfThreads];
+                bool near_a = false, near_b = false;
+                float la = 0.0f, lb = 0.0f;
+                float ua[3] = {0.0f, 0.0f, 0.0f}, ub[3] = {0.0f, 0.0f, 0.0f};
+                if (ha) {
+                    float vma, vmb = kNegHuge;
+                    if (with_u) {
+                        sf_row2_lse_u(a, S, Z, t, pa, pb, hb, dust, inv_negK, npair, la, lb, vma, vmb, ua, ub);
+                    } else {
+                        la = sf_row_lse(a, S, Z, t, pa, dust, npair, vma);
+                        if (hb) lb = sf_row_lse(a, S, Z, t, pb, dust, npair, vmb);
+                    }
+                    near_a = vma - la >= kSfSkip;
+                    near_b = hb && vmb - lb >= kSfSkip;
                 }
-                const unsigned ball = __ballot_sync(0xffffffffu, near);
-                if (lane == 0) wcnt[w] = __popc(ball);
+                const unsigned balla = __ballot_sync(0xffffffffu, near_a), ballb = __ballot_sync(0xffffffffu, near_b);
+                if (lane == 0) {
+                    wcnt[w] = __popc(balla);
+                    wcnt2[w] = __popc(ballb);
+                }
                 __syncthreads();
-                int before = 0, total = 0;
+                int before_a = 0, total_a = 0, before_b = 0, total_b = 0;
                 for (int k = 0; k < kSfThreads / 32; ++k) {
-                    if (k < w) before += wcnt[k];
-                    total += wcnt[k];
+                    if (k < w) {
+                        before_a += wcnt[k];
+                        before_b += wcnt2[k];
+                    }
+                    total_a += wcnt[k];
+                    total_b += wcnt2[k];
                 }
-                const int pos = base + cnt + before + __popc(ball & ((1u << lane) - 1u));
-                if (near && pos < a.ncap) {
-                    Z.near[pos] = make_float4(p.x, p.y, p.z, l);
-                    if (with_u) Z.nearu[pos] = make_float4(u[0], u[1], u[2], __int_as_float(t));
+                const unsigned below = (1u << lane) - 1u;
+                const int pos_a = base + cnt + before_a + __popc(balla & below);
+                const int pos_b = base + cnt + total_a + before_b + __popc(ballb & below);
+                if (near_a && pos_a < a.ncap) {
+                    Z.near[pos_a] = make_float4(pa.x, pa.y, pa.z, la);
+                    if (with_u) Z.nearu[pos_a] = make_float4(ua[0], ua[1], ua[2], __int_as_float(t));
                 }
-                cnt += total;
+                if (near_b && pos_b < a.ncap) {
+                    Z.near[pos_b] = make_float4(pb.x, pb.y, pb.z, lb);
+                    if (with_u) Z.nearu[pos_b] = make_float4(ub[0], ub[1], ub[2], __int_as_float(t));
+                }
+                cnt += total_a + total_b;
                 __syncthreads();
             }
         }
