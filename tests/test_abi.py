@@ -166,3 +166,23 @@ def test_general_lattice_tables_match_oracle(native):
         oracle.reflections_hkl(np.eye(3), [[1, 0, 0], [3, 0, 0]])
     with pytest.raises(Exception):
         api.reciprocal_basis(5.0, 5.0, 5.0, 10.0, 10.0, 170.0)  # angles that close no cell
+
+
+@pytest.mark.parametrize("B", [1, 24, 128, 2048, 3001])
+def test_set_encoder_batch_regions_are_disjoint(native, B):
+    """The batch buffer's public regions lie inside laue_lp_batch_bytes, are
+    256-byte aligned and do not overlap; region 1 (a transposed copy of the
+    features that the weight gradients no longer need) is reported as -1."""
+    L = native.lib()
+    K, W, NOUT = 128, 256, 72
+    sizes = {0: B * K * 64 * 2, 2: B * 9 * 4, 3: B * 4, 4: B * 9 * 4, 5: B * 3 * 4, 6: B * 4, 7: B * NOUT * 4,
+             8: B * 4, 9: B * 4, 10: B * 4, 11: B * K * W * 2, 12: B * K * W * 2, 13: B * 2 * W * 4,
+             14: B * NOUT * 4, 15: B * K * W * 2}
+    total = L.laue_lp_batch_bytes(B)
+    assert L.laue_lp_batch_offset(B, 1) == -1
+    assert L.laue_lp_batch_offset(B, 16) == -1 and L.laue_lp_batch_offset(B, -1) == -1
+    spans = sorted((L.laue_lp_batch_offset(B, r), sizes[r]) for r in sizes)
+    for off, size in spans:
+        assert off >= 0 and off % 256 == 0 and off + size <= total
+    for (o1, s1), (o2, _) in zip(spans, spans[1:]):
+        assert o1 + s1 <= o2
